@@ -1,0 +1,774 @@
+/*
+ * cfdem_oracle.c -- plain FP64 CPU oracle of the CFD-DEM coupling step of
+ * "Towards High-Order CFD-DEM: Development and Validation" (arXiv 2211.01185).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file: only the tests, the package's smoke() check and the CPU
+ * baseline leg of bench.py use it.  It shares no code, header, table or
+ * constant generator with the CUDA library.
+ *
+ * It is written for a reader checking it against the paper by eye: every
+ * quantity is computed from its definition, loops follow the order of the
+ * sums, nothing is blocked or fused.  Built with -O2 -ffp-contract=off so that
+ * no multiply-add is contracted (the neighbour predicate and the element
+ * location must be decided exactly as written).
+ *
+ * What each function follows:
+ *   or_locate          Sec. 2.3 (particle and fluid share one mesh: the element
+ *                      containing a particle is found directly from its position)
+ *   or_bin             the same localisation on a coarser grid of bins, stable
+ *   or_lens_volume     sphere-sphere intersection volume (textbook geometry)
+ *   or_qcm             Eq. (void_fraction) evaluated with averaging spheres
+ *                      centred at the quadrature points (quadrature-centred
+ *                      reading of the deferred void-fraction scheme)
+ *   or_pcm             Eq. (void_fraction), particle-centroid method
+ *   or_rhs / or_apply  smoothed L2 projection (M + L^2 K) eps_h = b, the
+ *   or_cg              reading of the "void fraction smoothing factor L^2"
+ *                      (Tables setup1, setup2, setup4)
+ *   or_drag_*          Eqs. (drag) .. Di Felice, Dallavalle, Re_p (Sec. 2.3.2)
+ *   or_forces          drag + buoyancy + pressure gradient per particle,
+ *                      f_fp,i of Eqs. (fb)/(fa) without the shear term
+ *   or_fluid_source    F_pf of Eqs. (fb)/(fa), with the minus sign that
+ *                      Newton's third law requires (Sec. 2.3.2)
+ * Parity is pinned by the tests: closed forms, limits, brute force,
+ * conservation laws and the worked numbers the paper prints.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------ */
+/* 1D tables                                                          */
+/* ------------------------------------------------------------------ */
+
+/* Legendre polynomial P_n(s) and its derivative, three-term recurrence. */
+static void legendre(int n, double s, double *p, double *dp)
+{
+    double p0 = 1.0, p1 = s;
+    if (n == 0) { *p = 1.0; *dp = 0.0; return; }
+    for (int m = 2; m <= n; ++m) {
+        double p2 = ((2.0 * m - 1.0) * s * p1 - (m - 1.0) * p0) / m;
+        p0 = p1;
+        p1 = p2;
+    }
+    *p = p1;
+    /* (1 - s^2) P_n' = n (P_{n-1} - s P_n) */
+    *dp = n * (p0 - s * p1) / (1.0 - s * s);
+}
+
+/* n-point Gauss-Legendre rule mapped to [0,1]: Newton on the roots of P_n,
+ * weights 2/((1-s^2) P_n'(s)^2) halved for the unit interval. */
+void or_gauss_rule(int n, double *pts, double *wts)
+{
+    for (int i = 0; i < n; ++i) {
+        double s = cos(OR_PI * (i + 0.75) / (n + 0.5));
+        double p, dp;
+        for (int it = 0; it < 100; ++it) {
+            legendre(n, s, &p, &dp);
+            double ds = p / dp;
+            s -= ds;
+            if (fabs(ds) < 1e-17) break;
+        }
+        legendre(n, s, &p, &dp);
+        /* s descends with i, so 0.5 (1 - s) ascends on [0,1]; the weight
+         * 2 / ((1 - s^2) P_n'(s)^2) of [-1,1] is halved on [0,1] */
+        pts[i] = 0.5 * (1.0 - s);
+        wts[i] = 1.0 / ((1.0 - s * s) * dp * dp);
+    }
+}
+
+/* Gauss-Lobatto-Legendre nodes of degree k on [0,1]: the end points and the
+ * roots of P_k'. */
+void or_gll_nodes(int k, double *z)
+{
+    z[0] = 0.0;
+    z[k] = 1.0;
+    for (int i = 1; i < k; ++i) {
+        /* Chebyshev-Gauss-Lobatto start, Newton on P_k' using
+         * (1-s^2) P_k'' = 2 s P_k' - k(k+1) P_k */
+        double s = -cos(OR_PI * i / k);
+        for (int it = 0; it < 100; ++it) {
+            double p, dp;
+            legendre(k, s, &p, &dp);
+            double d2p = (2.0 * s * dp - k * (k + 1.0) * p) / (1.0 - s * s);
+            double ds = dp / d2p;
+            s -= ds;
+            if (fabs(ds) < 1e-17) break;
+        }
+        z[i] = 0.5 * (1.0 + s);
+    }
+}
+
+/* Lagrange basis on the nodes z[0..k] and its derivative at t. */
+static void lagrange(int k, const double *z, double t, double *l, double *dl)
+{
+    for (int a = 0; a <= k; ++a) {
+        double v = 1.0, dv = 0.0;
+        for (int b = 0; b <= k; ++b) {
+            if (b == a) continue;
+            double den = z[a] - z[b];
+            /* product rule: d/dt prod (t - z_b)/den */
+            dv = dv * (t - z[b]) / den + v / den;
+            v = v * (t - z[b]) / den;
+        }
+        l[a] = v;
+        if (dl) dl[a] = dv;
+    }
+}
+
+void or_lagrange(int k, double t, double *l, double *dl)
+{
+    double z[8];
+    or_gll_nodes(k, z);
+    lagrange(k, z, t, l, dl);
+}
+
+/* ------------------------------------------------------------------ */
+/* Mesh                                                               */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    double x0[3], L[3], h[3];
+    int ne[3];
+    int k;
+} omesh;
+
+static omesh make_mesh(const double *origin, const double *extent, const int *n_el, int k)
+{
+    omesh m;
+    for (int a = 0; a < 3; ++a) {
+        m.x0[a] = origin[a];
+        m.L[a] = extent[a];
+        m.ne[a] = n_el[a];
+        m.h[a] = extent[a] / n_el[a];
+    }
+    m.k = k;
+    return m;
+}
+
+static int64_t n_elem(const omesh *m) { return (int64_t)m->ne[0] * m->ne[1] * m->ne[2]; }
+
+/* number of nodes per axis of the Q_deg grid */
+static int nn_axis(const omesh *m, int a, int deg) { return m->ne[a] * deg + 1; }
+
+/* ------------------------------------------------------------------ */
+/* Locate                                                             */
+/* ------------------------------------------------------------------ */
+
+/* Element index along one axis: floor of (x - x0)/h with IEEE division,
+ * clamped to [0, N-1]; a particle on an interior face belongs to the upper
+ * element, one on the top wall to the last element.  Returns 0 when x lies
+ * outside [x0, x0+L] by more than 1e-12 L (NaN included). */
+static int locate_axis(double x, double x0, double L, double h, int N, int *ie, double *xi)
+{
+    double lo = x0 - 1e-12 * L;
+    double hi = (x0 + L) + 1e-12 * L;
+    if (!(x >= lo && x <= hi)) return 0;
+    double t = (x - x0) / h;
+    double f = floor(t);
+    int i = (int)f;
+    if (i < 0) i = 0;
+    if (i > N - 1) i = N - 1;
+    *ie = i;
+    *xi = t - (double)i;
+    return 1;
+}
+
+/* elem[n] = ex + Nx (ey + Ny ez); xi[n][3] reference coordinates in [0,1].
+ * Returns -1 if every particle is inside, else the first bad index. */
+int64_t or_locate(const double *origin, const double *extent, const int *n_el, int k,
+                  int64_t n, const double *x, int32_t *elem, double *xi)
+{
+    omesh m = make_mesh(origin, extent, n_el, k);
+    int64_t bad = -1;
+    for (int64_t i = 0; i < n; ++i) {
+        int ie[3];
+        double t[3];
+        int ok = 1;
+        for (int a = 0; a < 3; ++a)
+            ok &= locate_axis(x[3 * i + a], m.x0[a], m.L[a], m.h[a], m.ne[a], &ie[a], &t[a]);
+        if (!ok) {
+            if (bad < 0) bad = i;
+            elem[i] = -1;
+            if (xi) xi[3 * i] = xi[3 * i + 1] = xi[3 * i + 2] = 0.0;
+            continue;
+        }
+        elem[i] = ie[0] + m.ne[0] * (ie[1] + m.ne[1] * ie[2]);
+        if (xi) for (int a = 0; a < 3; ++a) xi[3 * i + a] = t[a];
+    }
+    return bad;
+}
+
+/* ------------------------------------------------------------------ */
+/* Bins                                                               */
+/* ------------------------------------------------------------------ */
+
+/* Bin of a particle on a grid of nb[a] equal bins per axis over the box:
+ * floor((x - x0)/(L/nb)), clamped. */
+static int bin_axis(double x, double x0, double L, int nb)
+{
+    double be = L / nb;
+    double t = (x - x0) / be;
+    double f = floor(t);
+    int i;
+    if (!(f >= 0.0)) i = 0;            /* also catches NaN */
+    else if (f > (double)(nb - 1)) i = nb - 1;
+    else i = (int)f;
+    return i;
+}
+
+/* Stable counting sort of the particles into bins (bx fastest):
+ * bin_start[nbins+1] exclusive prefix of the counts, perm[n] the particle
+ * ids in bin order, ascending id inside a bin. */
+void or_bin(const double *origin, const double *extent, const int *nb,
+            int64_t n, const double *x, int32_t *bin_of, int32_t *bin_start, int32_t *perm)
+{
+    int64_t nbins = (int64_t)nb[0] * nb[1] * nb[2];
+    memset(bin_start, 0, sizeof(int32_t) * (nbins + 1));
+    for (int64_t i = 0; i < n; ++i) {
+        int b[3];
+        for (int a = 0; a < 3; ++a) b[a] = bin_axis(x[3 * i + a], origin[a], extent[a], nb[a]);
+        int32_t id = b[0] + nb[0] * (b[1] + nb[1] * b[2]);
+        bin_of[i] = id;
+        bin_start[id + 1] += 1;
+    }
+    for (int64_t j = 0; j < nbins; ++j) bin_start[j + 1] += bin_start[j];
+    int32_t *fill = (int32_t *)malloc(sizeof(int32_t) * (nbins > 0 ? nbins : 1));
+    for (int64_t j = 0; j < nbins; ++j) fill[j] = bin_start[j];
+    for (int64_t i = 0; i < n; ++i) perm[fill[bin_of[i]]++] = (int32_t)i; /* ascending i */
+    free(fill);
+}
+
+/* ------------------------------------------------------------------ */
+/* Void fraction                                                      */
+/* ------------------------------------------------------------------ */
+
+/* Volume of the intersection of two spheres of radii R and r whose centres
+ * are d apart. */
+double or_lens_volume(double R, double r, double d)
+{
+    if (d >= R + r) return 0.0;
+    double mn = R < r ? R : r;
+    if (d <= fabs(R - r)) return 4.0 / 3.0 * OR_PI * mn * mn * mn;
+    double s = R + r - d;
+    double dm = R - r;
+    return OR_PI * s * s * (d * d + 2.0 * d * (R + r) - 3.0 * dm * dm) / (12.0 * d);
+}
+
+/* physical coordinate of Gauss point g of element index ie along an axis */
+static double qp_coord(double x0, double h, int ie, double g)
+{
+    double t1 = (double)ie + g;
+    double t2 = h * t1;
+    return x0 + t2;
+}
+
+static int cmp_i32(const void *a, const void *b)
+{
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* Quadrature-centred void fraction: for every Gauss point x_q of every
+ * element, eps_q = 1 - sum_i V_lens(R, r_i, |x_q - x_i|) / (4/3 pi R^3) over
+ * the particles with |x_q - x_i|^2 < (R + r_i)^2, summed in ascending id.
+ * Neighbour sets come from a cell list of edge >= R + max r (or from brute
+ * force when brute != 0).  Optional outputs: neighbour count and id sum per
+ * quadrature point. */
+void or_qcm(const double *origin, const double *extent, const int *n_el, int k, double R,
+            int64_t n, const double *x, const double *r, int brute,
+            double *eps_q, int32_t *nb_count, int64_t *nb_idsum)
+{
+    omesh m = make_mesh(origin, extent, n_el, k);
+    int nq = k + 1;
+    double g[8], w[8];
+    or_gauss_rule(nq, g, w);
+    double VR = 4.0 / 3.0 * OR_PI * R * R * R;
+    double rmax = 0.0;
+    for (int64_t i = 0; i < n; ++i) if (r[i] > rmax) rmax = r[i];
+    double cut = R + rmax;
+
+    int nc[3];
+    for (int a = 0; a < 3; ++a) {
+        nc[a] = (int)floor(m.L[a] / cut);
+        if (nc[a] < 1) nc[a] = 1;
+    }
+    int64_t ncell = (int64_t)nc[0] * nc[1] * nc[2];
+    int32_t *cell_of = (int32_t *)malloc(sizeof(int32_t) * (n > 0 ? n : 1));
+    int32_t *cstart = (int32_t *)malloc(sizeof(int32_t) * (ncell + 1));
+    int32_t *cperm = (int32_t *)malloc(sizeof(int32_t) * (n > 0 ? n : 1));
+    or_bin(m.x0, m.L, nc, n, x, cell_of, cstart, cperm);
+
+    int64_t E = n_elem(&m);
+    int Q = nq * nq * nq;
+#pragma omp parallel
+    {
+        int32_t *list = (int32_t *)malloc(sizeof(int32_t) * (n > 0 ? n : 1));
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t e = 0; e < E; ++e) {
+            int ex = (int)(e % m.ne[0]);
+            int ey = (int)((e / m.ne[0]) % m.ne[1]);
+            int ez = (int)(e / ((int64_t)m.ne[0] * m.ne[1]));
+            for (int qz = 0; qz < nq; ++qz)
+            for (int qy = 0; qy < nq; ++qy)
+            for (int qx = 0; qx < nq; ++qx) {
+                int q = qx + nq * (qy + nq * qz);
+                double xq = qp_coord(m.x0[0], m.h[0], ex, g[qx]);
+                double yq = qp_coord(m.x0[1], m.h[1], ey, g[qy]);
+                double zq = qp_coord(m.x0[2], m.h[2], ez, g[qz]);
+                int cnt = 0;
+                if (brute) {
+                    for (int64_t i = 0; i < n; ++i) {
+                        double dx = x[3 * i] - xq, dy = x[3 * i + 1] - yq, dz = x[3 * i + 2] - zq;
+                        double d2 = dx * dx + dy * dy + dz * dz;
+                        double c = R + r[i];
+                        if (d2 < c * c) list[cnt++] = (int32_t)i;
+                    }
+                } else {
+                    int cq[3];
+                    cq[0] = bin_axis(xq, m.x0[0], m.L[0], nc[0]);
+                    cq[1] = bin_axis(yq, m.x0[1], m.L[1], nc[1]);
+                    cq[2] = bin_axis(zq, m.x0[2], m.L[2], nc[2]);
+                    for (int cz = cq[2] - 1; cz <= cq[2] + 1; ++cz) {
+                        if (cz < 0 || cz >= nc[2]) continue;
+                        for (int cy = cq[1] - 1; cy <= cq[1] + 1; ++cy) {
+                            if (cy < 0 || cy >= nc[1]) continue;
+                            for (int cx = cq[0] - 1; cx <= cq[0] + 1; ++cx) {
+                                if (cx < 0 || cx >= nc[0]) continue;
+                                int64_t c = cx + (int64_t)nc[0] * (cy + (int64_t)nc[1] * cz);
+                                for (int32_t s = cstart[c]; s < cstart[c + 1]; ++s) {
+                                    int32_t i = cperm[s];
+                                    double dx = x[3 * i] - xq, dy = x[3 * i + 1] - yq,
+                                           dz = x[3 * i + 2] - zq;
+                                    double d2 = dx * dx + dy * dy + dz * dz;
+                                    double cc = R + r[i];
+                                    if (d2 < cc * cc) list[cnt++] = i;
+                                }
+                            }
+                        }
+                    }
+                    qsort(list, cnt, sizeof(int32_t), cmp_i32);
+                }
+                double vs = 0.0;
+                int64_t ids = 0;
+                for (int j = 0; j < cnt; ++j) {
+                    int32_t i = list[j];
+                    double dx = x[3 * i] - xq, dy = x[3 * i + 1] - yq, dz = x[3 * i + 2] - zq;
+                    double d = sqrt(dx * dx + dy * dy + dz * dz);
+                    vs += or_lens_volume(R, r[i], d);
+                    ids += i;
+                }
+                eps_q[e * Q + q] = 1.0 - vs / VR;
+                if (nb_count) nb_count[e * Q + q] = cnt;
+                if (nb_idsum) nb_idsum[e * Q + q] = ids;
+            }
+        }
+        free(list);
+    }
+    free(cell_of);
+    free(cstart);
+    free(cperm);
+}
+
+/* Particle-centroid void fraction, Eq. (void_fraction): eps_e = (V_e -
+ * sum_{i in e} V_p,i) / V_e with the particle assigned to the element holding
+ * its centre; copied to all quadrature points of e. */
+int64_t or_pcm(const double *origin, const double *extent, const int *n_el, int k,
+               int64_t n, const double *x, const double *r, double *eps_q)
+{
+    omesh m = make_mesh(origin, extent, n_el, k);
+    int64_t E = n_elem(&m);
+    int nq = k + 1, Q = nq * nq * nq;
+    double Ve = m.h[0] * m.h[1] * m.h[2];
+    int32_t *elem = (int32_t *)malloc(sizeof(int32_t) * (n > 0 ? n : 1));
+    int64_t bad = or_locate(origin, extent, n_el, k, n, x, elem, NULL);
+    double *vs = (double *)calloc(E, sizeof(double));
+    for (int64_t i = 0; i < n; ++i) {
+        if (elem[i] < 0) continue;
+        vs[elem[i]] += 4.0 / 3.0 * OR_PI * r[i] * r[i] * r[i];
+    }
+    for (int64_t e = 0; e < E; ++e) {
+        double eps = (Ve - vs[e]) / Ve;
+        for (int q = 0; q < Q; ++q) eps_q[e * Q + q] = eps;
+    }
+    free(vs);
+    free(elem);
+    return bad;
+}
+
+/* ------------------------------------------------------------------ */
+/* Smoothed L2 projection                                             */
+/* ------------------------------------------------------------------ */
+
+/* global node of local node (a,b,c) of element (ex,ey,ez) on the Q_deg grid */
+static int64_t gnode(const omesh *m, int deg, int ex, int ey, int ez, int a, int b, int c)
+{
+    int64_t nx = nn_axis(m, 0, deg), ny = nn_axis(m, 1, deg);
+    return (int64_t)(ex * deg + a) + nx * ((int64_t)(ey * deg + b) + ny * (int64_t)(ez * deg + c));
+}
+
+/* Element matrix A_e = M_e + L2 K_e of an axis-aligned box element, by 3D
+ * Gauss quadrature of the basis products:
+ *   M_e[i][j] = sum_q phi_i phi_j w_q |J|,
+ *   K_e[i][j] = sum_q grad phi_i . grad phi_j w_q |J|,
+ * local node i = a + (k+1)(b + (k+1) c). */
+void or_element_matrix(int k, const double *h, double *Me, double *Ke)
+{
+    int np = k + 1, nq = k + 1;
+    int nloc = np * np * np;
+    double g[8], w[8], z[8];
+    or_gauss_rule(nq, g, w);
+    or_gll_nodes(k, z);
+    double l[8][8], dl[8][8];
+    for (int q = 0; q < nq; ++q) lagrange(k, z, g[q], l[q], dl[q]);
+    double detJ = h[0] * h[1] * h[2];
+    for (int i = 0; i < nloc * nloc; ++i) { Me[i] = 0.0; Ke[i] = 0.0; }
+    for (int qz = 0; qz < nq; ++qz)
+    for (int qy = 0; qy < nq; ++qy)
+    for (int qx = 0; qx < nq; ++qx) {
+        double wq = w[qx] * w[qy] * w[qz] * detJ;
+        for (int i = 0; i < nloc; ++i) {
+            int ia = i % np, ib = (i / np) % np, ic = i / (np * np);
+            double pi = l[qx][ia] * l[qy][ib] * l[qz][ic];
+            double gi0 = dl[qx][ia] / h[0] * l[qy][ib] * l[qz][ic];
+            double gi1 = l[qx][ia] * dl[qy][ib] / h[1] * l[qz][ic];
+            double gi2 = l[qx][ia] * l[qy][ib] * dl[qz][ic] / h[2];
+            for (int j = 0; j < nloc; ++j) {
+                int ja = j % np, jb = (j / np) % np, jc = j / (np * np);
+                double pj = l[qx][ja] * l[qy][jb] * l[qz][jc];
+                double gj0 = dl[qx][ja] / h[0] * l[qy][jb] * l[qz][jc];
+                double gj1 = l[qx][ja] * dl[qy][jb] / h[1] * l[qz][jc];
+                double gj2 = l[qx][ja] * l[qy][jb] * dl[qz][jc] / h[2];
+                Me[i * nloc + j] += pi * pj * wq;
+                Ke[i * nloc + j] += (gi0 * gj0 + gi1 * gj1 + gi2 * gj2) * wq;
+            }
+        }
+    }
+}
+
+/* b_j = sum_e sum_q phi_j(x_q) w_q |J_e| eps_q */
+void or_rhs(const double *origin, const double *extent, const int *n_el, int k,
+            const double *eps_q, double *b)
+{
+    omesh m = make_mesh(origin, extent, n_el, k);
+    int np = k + 1, nq = k + 1, Q = nq * nq * nq;
+    double g[8], w[8], z[8], l[8][8];
+    or_gauss_rule(nq, g, w);
+    or_gll_nodes(k, z);
+    for (int q = 0; q < nq; ++q) lagrange(k, z, g[q], l[q], NULL);
+    int64_t nnodes = (int64_t)nn_axis(&m, 0, k) * nn_axis(&m, 1, k) * nn_axis(&m, 2, k);
+    for (int64_t j = 0; j < nnodes; ++j) b[j] = 0.0;
+    double detJ = m.h[0] * m.h[1] * m.h[2];
+    for (int color = 0; color < 2; ++color) {
+#pragma omp parallel for schedule(static)
+        for (int ez = color; ez < m.ne[2]; ez += 2)
+        for (int ey = 0; ey < m.ne[1]; ++ey)
+        for (int ex = 0; ex < m.ne[0]; ++ex) {
+            int64_t e = ex + (int64_t)m.ne[0] * (ey + (int64_t)m.ne[1] * ez);
+            for (int qz = 0; qz < nq; ++qz)
+            for (int qy = 0; qy < nq; ++qy)
+            for (int qx = 0; qx < nq; ++qx) {
+                int q = qx + nq * (qy + nq * qz);
+                double wq = w[qx] * w[qy] * w[qz] * detJ;
+                double val = eps_q[e * Q + q];
+                for (int c = 0; c < np; ++c)
+                for (int bb = 0; bb < np; ++bb)
+                for (int a = 0; a < np; ++a) {
+                    double phi = l[qx][a] * l[qy][bb] * l[qz][c];
+                    b[gnode(&m, k, ex, ey, ez, a, bb, c)] += phi * wq * val;
+                }
+            }
+        }
+    }
+}
+
+/* y = (M + L2 K) x, assembled element by element from the element matrix.
+ * Elements are visited in slabs of even then odd ez so that no two threads
+ * add into the same node. */
+void or_apply(const double *origin, const double *extent, const int *n_el, int k, double L2,
+              const double *xv, double *y)
+{
+    omesh m = make_mesh(origin, extent, n_el, k);
+    int np = k + 1, nloc = np * np * np;
+    double *Me = (double *)malloc(sizeof(double) * nloc * nloc);
+    double *Ke = (double *)malloc(sizeof(double) * nloc * nloc);
+    or_element_matrix(k, m.h, Me, Ke);
+    double *Ae = (double *)malloc(sizeof(double) * nloc * nloc);
+    for (int i = 0; i < nloc * nloc; ++i) Ae[i] = Me[i] + L2 * Ke[i];
+    int64_t nnodes = (int64_t)nn_axis(&m, 0, k) * nn_axis(&m, 1, k) * nn_axis(&m, 2, k);
+    for (int64_t j = 0; j < nnodes; ++j) y[j] = 0.0;
+    for (int color = 0; color < 2; ++color) {
+#pragma omp parallel for schedule(static)
+        for (int ez = color; ez < m.ne[2]; ez += 2) {
+            int64_t idx[64];
+            double xl[64];
+            for (int ey = 0; ey < m.ne[1]; ++ey)
+            for (int ex = 0; ex < m.ne[0]; ++ex) {
+                for (int i = 0; i < nloc; ++i) {
+                    int a = i % np, b = (i / np) % np, c = i / (np * np);
+                    idx[i] = gnode(&m, k, ex, ey, ez, a, b, c);
+                    xl[i] = xv[idx[i]];
+                }
+                for (int i = 0; i < nloc; ++i) {
+                    double s = 0.0;
+                    for (int j = 0; j < nloc; ++j) s += Ae[i * nloc + j] * xl[j];
+                    y[idx[i]] += s;
+                }
+            }
+        }
+    }
+    free(Me);
+    free(Ke);
+    free(Ae);
+}
+
+/* diagonal of the assembled (M + L2 K) */
+void or_diag(const double *origin, const double *extent, const int *n_el, int k, double L2,
+             double *dg)
+{
+    omesh m = make_mesh(origin, extent, n_el, k);
+    int np = k + 1, nloc = np * np * np;
+    double *Me = (double *)malloc(sizeof(double) * nloc * nloc);
+    double *Ke = (double *)malloc(sizeof(double) * nloc * nloc);
+    or_element_matrix(k, m.h, Me, Ke);
+    int64_t nnodes = (int64_t)nn_axis(&m, 0, k) * nn_axis(&m, 1, k) * nn_axis(&m, 2, k);
+    for (int64_t j = 0; j < nnodes; ++j) dg[j] = 0.0;
+    for (int ez = 0; ez < m.ne[2]; ++ez)
+    for (int ey = 0; ey < m.ne[1]; ++ey)
+    for (int ex = 0; ex < m.ne[0]; ++ex)
+    for (int i = 0; i < nloc; ++i) {
+        int a = i % np, b = (i / np) % np, c = i / (np * np);
+        dg[gnode(&m, k, ex, ey, ez, a, b, c)] += Me[i * nloc + i] + L2 * Ke[i * nloc + i];
+    }
+    free(Me);
+    free(Ke);
+}
+
+static double dot(int64_t n, const double *a, const double *b)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
+    return s;
+}
+
+/* Jacobi-preconditioned conjugate gradients on (M + L2 K) x = b; x holds the
+ * start vector on entry.  Stops when ||r||_2 <= rtol ||b||_2.  Returns the
+ * number of iterations, or -1 if maxit was reached first. */
+int or_cg(const double *origin, const double *extent, const int *n_el, int k, double L2,
+          const double *b, double *xv, double rtol, int maxit, double *relres)
+{
+    omesh m = make_mesh(origin, extent, n_el, k);
+    int64_t nn = (int64_t)nn_axis(&m, 0, k) * nn_axis(&m, 1, k) * nn_axis(&m, 2, k);
+    double *dg = (double *)malloc(sizeof(double) * nn);
+    double *rv = (double *)malloc(sizeof(double) * nn);
+    double *zv = (double *)malloc(sizeof(double) * nn);
+    double *pv = (double *)malloc(sizeof(double) * nn);
+    double *Ap = (double *)malloc(sizeof(double) * nn);
+    or_diag(origin, extent, n_el, k, L2, dg);
+    or_apply(origin, extent, n_el, k, L2, xv, Ap);
+    for (int64_t i = 0; i < nn; ++i) rv[i] = b[i] - Ap[i];
+    double bn = sqrt(dot(nn, b, b));
+    if (bn == 0.0) bn = 1.0;
+    for (int64_t i = 0; i < nn; ++i) zv[i] = rv[i] / dg[i];
+    for (int64_t i = 0; i < nn; ++i) pv[i] = zv[i];
+    double rz = dot(nn, rv, zv);
+    double res = sqrt(dot(nn, rv, rv)) / bn;
+    int it = 0;
+    while (res > rtol && it < maxit) {
+        or_apply(origin, extent, n_el, k, L2, pv, Ap);
+        double alpha = rz / dot(nn, pv, Ap);
+        for (int64_t i = 0; i < nn; ++i) xv[i] += alpha * pv[i];
+        for (int64_t i = 0; i < nn; ++i) rv[i] -= alpha * Ap[i];
+        for (int64_t i = 0; i < nn; ++i) zv[i] = rv[i] / dg[i];
+        double rz_new = dot(nn, rv, zv);
+        double beta = rz_new / rz;
+        rz = rz_new;
+        for (int64_t i = 0; i < nn; ++i) pv[i] = zv[i] + beta * pv[i];
+        res = sqrt(dot(nn, rv, rv)) / bn;
+        ++it;
+    }
+    if (relres) *relres = res;
+    free(dg);
+    free(rv);
+    free(zv);
+    free(pv);
+    free(Ap);
+    return res <= rtol ? it : -1;
+}
+
+/* ------------------------------------------------------------------ */
+/* Particle-fluid forces                                              */
+/* ------------------------------------------------------------------ */
+
+/* C_D |U| of the Dallavalle correlation, C_D = (0.63 + 4.8/sqrt(Re_p))^2
+ * with Re_p = rho eps |U| d / mu, written as
+ * (0.63 sqrt|U| + 4.8 sqrt(mu / (rho eps d)))^2 so that |U| -> 0 is finite. */
+double or_cd_times_speed_dallavalle(double rho, double mu, double eps, double speed, double dp)
+{
+    double a = 0.63 * sqrt(speed) + 4.8 * sqrt(mu / (rho * eps * dp));
+    return a * a;
+}
+
+double or_reynolds(double rho, double mu, double eps, double speed, double dp)
+{
+    return rho * eps * speed * dp / mu;
+}
+
+/* Di Felice exponent chi = 3.7 - 0.65 exp(-(1.5 - log10 Re)^2 / 2) */
+double or_difelice_chi(double Re)
+{
+    double re = Re > 1e-300 ? Re : 1e-300;
+    double t = 1.5 - log10(re);
+    return 3.7 - 0.65 * exp(-(t * t) / 2.0);
+}
+
+/* Drag force on one particle of radius rp with slip U = u_f - u_p:
+ * F_D = 1/2 rho C_D pi rp^2 |U| U, C_D Dallavalle (model 1) or Di Felice
+ * (model 0, Dallavalle times eps^(2 - chi)); divided by eps when
+ * beta_over_eps (beta_B = beta_A / eps). */
+void or_drag_force(int model, int beta_over_eps, double rho, double mu, double eps,
+                   const double *U, double rp, double *fd)
+{
+    double speed = sqrt(U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
+    if (speed == 0.0) { fd[0] = fd[1] = fd[2] = 0.0; return; }
+    double dp = 2.0 * rp;
+    double cds = or_cd_times_speed_dallavalle(rho, mu, eps, speed, dp);
+    if (model == 0) {
+        double Re = or_reynolds(rho, mu, eps, speed, dp);
+        cds = cds * pow(eps, 2.0 - or_difelice_chi(Re));
+    }
+    double coef = 0.5 * rho * cds * OR_PI * rp * rp;
+    if (beta_over_eps) coef = coef / eps;
+    for (int a = 0; a < 3; ++a) fd[a] = coef * U[a];
+}
+
+/* Per-particle forces (Sec. 2.3.2):
+ *   u_f, eps at x_i by Q_k interpolation, grad p by Q_kp interpolation;
+ *   eps_c = min(max(eps, eps_floor), 1) used in the closures only;
+ *   f_D (drag), f_B = -rho V_p g, f_gradp = -V_p grad p,
+ *   f = f_D + f_B + f_gradp.
+ * Outputs may be NULL except f.  Returns the first particle outside the
+ * mesh, or -1. */
+int64_t or_forces(const double *origin, const double *extent, const int *n_el, int k, int kp,
+                  double rho, double mu, const double *grav, int drag_model, int beta_over_eps,
+                  double eps_floor, int64_t n, const double *x, const double *r,
+                  const double *u_p, const double *u_nodal, const double *p_nodal,
+                  const double *eps_nodal, double *f, double *f_drag, double *f_gradp,
+                  double *eps_at_p)
+{
+    omesh m = make_mesh(origin, extent, n_el, k);
+    double z[8], zp[8];
+    or_gll_nodes(k, z);
+    or_gll_nodes(kp, zp);
+    int64_t bad = -1;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        int ie[3];
+        double xi[3];
+        int ok = 1;
+        for (int a = 0; a < 3; ++a)
+            ok &= locate_axis(x[3 * i + a], m.x0[a], m.L[a], m.h[a], m.ne[a], &ie[a], &xi[a]);
+        if (!ok) {
+#pragma omp critical
+            { if (bad < 0 || i < bad) bad = i; }
+            for (int a = 0; a < 3; ++a) f[3 * i + a] = 0.0;
+            continue;
+        }
+        double lx[8], ly[8], lz[8];
+        lagrange(k, z, xi[0], lx, NULL);
+        lagrange(k, z, xi[1], ly, NULL);
+        lagrange(k, z, xi[2], lz, NULL);
+        double uf[3] = {0.0, 0.0, 0.0}, eps = 0.0;
+        for (int c = 0; c <= k; ++c)
+        for (int b = 0; b <= k; ++b)
+        for (int a = 0; a <= k; ++a) {
+            double phi = lx[a] * ly[b] * lz[c];
+            int64_t nd = gnode(&m, k, ie[0], ie[1], ie[2], a, b, c);
+            uf[0] += phi * u_nodal[3 * nd];
+            uf[1] += phi * u_nodal[3 * nd + 1];
+            uf[2] += phi * u_nodal[3 * nd + 2];
+            eps += phi * eps_nodal[nd];
+        }
+        double px[8], py[8], pz[8], dpx[8], dpy[8], dpz[8];
+        lagrange(kp, zp, xi[0], px, dpx);
+        lagrange(kp, zp, xi[1], py, dpy);
+        lagrange(kp, zp, xi[2], pz, dpz);
+        double gp[3] = {0.0, 0.0, 0.0};
+        for (int c = 0; c <= kp; ++c)
+        for (int b = 0; b <= kp; ++b)
+        for (int a = 0; a <= kp; ++a) {
+            double pv = p_nodal[gnode(&m, kp, ie[0], ie[1], ie[2], a, b, c)];
+            gp[0] += dpx[a] / m.h[0] * py[b] * pz[c] * pv;
+            gp[1] += px[a] * dpy[b] / m.h[1] * pz[c] * pv;
+            gp[2] += px[a] * py[b] * dpz[c] / m.h[2] * pv;
+        }
+        double epsc = eps;
+        if (epsc < eps_floor) epsc = eps_floor;
+        if (epsc > 1.0) epsc = 1.0;
+        double U[3] = {uf[0] - u_p[3 * i], uf[1] - u_p[3 * i + 1], uf[2] - u_p[3 * i + 2]};
+        double fd[3];
+        or_drag_force(drag_model, beta_over_eps, rho, mu, epsc, U, r[i], fd);
+        double Vp = 4.0 / 3.0 * OR_PI * r[i] * r[i] * r[i];
+        for (int a = 0; a < 3; ++a) {
+            double fb = -rho * Vp * grav[a];
+            double fg = -Vp * gp[a];
+            f[3 * i + a] = fd[a] + fb + fg;
+            if (f_drag) f_drag[3 * i + a] = fd[a];
+            if (f_gradp) f_gradp[3 * i + a] = fg;
+        }
+        if (eps_at_p) eps_at_p[i] = eps;
+    }
+    return bad;
+}
+
+/* Fluid source per element, Eqs. (fa)/(fb): F_pf,e = -(1/V_e) sum_{i in e} S_i
+ * with S_i = f_D,i (model A, vans_model 0) or f_D,i + f_gradp,i (model B).
+ * F_e[E][3]; the same value holds at every quadrature point of e. */
+int64_t or_fluid_source(const double *origin, const double *extent, const int *n_el, int k,
+                        int vans_model, int64_t n, const double *x, const double *f_drag,
+                        const double *f_gradp, double *F_e)
+{
+    omesh m = make_mesh(origin, extent, n_el, k);
+    int64_t E = n_elem(&m);
+    double Ve = m.h[0] * m.h[1] * m.h[2];
+    int32_t *elem = (int32_t *)malloc(sizeof(int32_t) * (n > 0 ? n : 1));
+    int64_t bad = or_locate(origin, extent, n_el, k, n, x, elem, NULL);
+    double *S = (double *)calloc(3 * E, sizeof(double));
+    for (int64_t i = 0; i < n; ++i) {
+        if (elem[i] < 0) continue;
+        for (int a = 0; a < 3; ++a) {
+            double s = f_drag[3 * i + a];
+            if (vans_model == 1) s += f_gradp[3 * i + a];
+            S[3 * (int64_t)elem[i] + a] += s;
+        }
+    }
+    for (int64_t e = 0; e < 3 * E; ++e) F_e[e] = -S[e] / Ve;
+    free(S);
+    free(elem);
+    return bad;
+}
+
+int or_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void or_set_num_threads(int t)
+{
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}

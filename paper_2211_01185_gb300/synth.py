@@ -1,0 +1,234 @@
+"""Seeded synthetic inputs shaped like the paper's beds.
+
+This module only draws inputs: particle positions and radii, particle
+velocities and nodal fluid fields.  It holds none of the coupling method's
+arithmetic (no void fraction, projection, interpolation or closure), and both
+the CUDA path and the CPU oracle receive exactly the arrays it returns.
+
+Workloads (seed = 2211011850 + workload index):
+
+* ``q1_8x8x32_2k``   box 0.02 x 0.02 x 0.08 m, 8x8x32 Q1, 2,000 spheres of
+  d = 1 mm by random sequential addition (no overlap) in the lower half;
+  u = (0, 0, 0.5 + 0.05 sin(2 pi x / L_x)), p linear in z.
+* ``q2_32x32x128_100k`` box 0.1 x 0.1 x 0.4 m, 32x32x128 Q2, 100,000 spheres
+  with d ~ U[2, 3] mm on a jittered FCC lattice in the lower 40 % (solid
+  fraction ~0.53), pushed apart until the worst overlap is below 1 % of the
+  smallest diameter; u = (0, 0, 1) + 5 % seeded noise per nodal component.
+* ``q3_24x24x96_1m`` box 0.144 x 0.144 x 0.576 m, 24x24x96 Q3, 1,000,000
+  spheres of d = 1 mm on a jittered FCC lattice at solid fraction 0.6 (the
+  bottom ~43 mm), no overlap by construction.
+
+Fluid properties are those of a gas (rho_f = 1.2 kg/m^3, mu_f = 1.8e-5 Pa s),
+g = (0, 0, -9.81); particle velocities are uniform in [-0.05, 0.05]^3 m/s;
+the pressure is p = G (L_z - z) with G = phi (rho_p - rho_f) |g|, rho_p =
+2500 kg/m^3 (glass); the smoothing length is L^2 = 4 mean(d)^2.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+SEED0 = 2211011850
+RHO_P = 2500.0
+
+WORKLOADS = {
+    "q1_8x8x32_2k": dict(index=1, origin=(0.0, 0.0, 0.0), extent=(0.02, 0.02, 0.08),
+                          n_el=(8, 8, 32), k=1, n=2000, d=(1e-3, 1e-3), phi=0.065,
+                          packing="rsa", bed_frac=0.5, field="sine", u_mean=0.5),
+    "q2_32x32x128_100k": dict(index=2, origin=(0.0, 0.0, 0.0), extent=(0.1, 0.1, 0.4),
+                               n_el=(32, 32, 128), k=2, n=100_000, d=(2e-3, 3e-3), phi=0.53,
+                               packing="fcc_relax", bed_frac=0.4, field="noise", u_mean=1.0),
+    "q3_24x24x96_1m": dict(index=3, origin=(0.0, 0.0, 0.0), extent=(0.144, 0.144, 0.576),
+                            n_el=(24, 24, 96), k=3, n=1_000_000, d=(1e-3, 1e-3), phi=0.6,
+                            packing="fcc", bed_frac=0.5, field="noise", u_mean=1.0),
+}
+
+
+def gas_params(mean_d: float, k: int) -> dict:
+    """Physical and numerical parameters shared by the workloads."""
+    return dict(rho_f=1.2, mu_f=1.8e-5, g=(0.0, 0.0, -9.81), scheme=0, qcm_radius=0.0,
+                l2_smoothing=4.0 * mean_d * mean_d, drag_model=0, vans_model=0,
+                beta_over_eps=0, eps_floor=0.05, pressure_degree=max(1, k - 1))
+
+
+# --------------------------------------------------------------- particles
+
+def rsa(rng, n, d, lo, hi, max_tries=200):
+    """Random sequential addition of n equal spheres of diameter d with
+    centres in the box [lo, hi] (no overlap)."""
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    pts = np.zeros((0, 3))
+    tries = 0
+    while pts.shape[0] < n:
+        tries += 1
+        if tries > max_tries * n:
+            raise RuntimeError("random sequential addition jammed")
+        c = lo + (hi - lo) * rng.random(3)
+        if pts.shape[0]:
+            dd = np.sum((pts - c) ** 2, axis=1)
+            if np.any(dd < d * d):
+                continue
+        pts = np.vstack([pts, c])
+    return pts
+
+
+def fcc_sites(a_nn, lo, hi, n):
+    """The n lowest sites (by z, then y, then x) of an FCC lattice of
+    nearest-neighbour distance a_nn filling the box [lo, hi]."""
+    a = a_nn * math.sqrt(2.0)
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    nc = np.floor((hi - lo) / a + 1e-9).astype(int)
+    basis = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]]) + 0.25
+    per_layer = 4 * nc[0] * nc[1]
+    nz = int(math.ceil(n / per_layer)) + 1
+    iz, iy, ix = np.meshgrid(np.arange(nz), np.arange(nc[1]), np.arange(nc[0]), indexing="ij")
+    cells = np.stack([ix.ravel(), iy.ravel(), iz.ravel()], axis=1).astype(np.float64)
+    sites = (cells[:, None, :] + basis[None, :, :]).reshape(-1, 3) * a + lo
+    order = np.lexsort((sites[:, 0], sites[:, 1], sites[:, 2]))
+    sites = sites[order]
+    if sites.shape[0] < n:
+        raise RuntimeError("lattice too small")
+    return sites[:n]
+
+
+def push_apart(rng, x, r, lo, hi, tol, iters=400):
+    """Soft relaxation: move every overlapping pair apart along the line of
+    centres and keep centres at least a radius inside the side walls and the
+    floor, until the largest overlap is below tol."""
+    from scipy.spatial import cKDTree
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    rmax = float(r.max())
+    for _ in range(iters):
+        tree = cKDTree(x)
+        pairs = tree.query_pairs(2.0 * rmax, output_type="ndarray")
+        if pairs.shape[0] == 0:
+            break
+        i, j = pairs[:, 0], pairs[:, 1]
+        dv = x[j] - x[i]
+        dist = np.sqrt(np.sum(dv * dv, axis=1))
+        ov = r[i] + r[j] - dist
+        m = ov > 0
+        worst = float(ov[m].max()) if np.any(m) else 0.0
+        if worst <= tol:
+            break
+        i, j, dv, dist, ov = i[m], j[m], dv[m], dist[m], ov[m]
+        nrm = dv / np.maximum(dist, 1e-12)[:, None]
+        step = 0.55 * ov[:, None] * nrm
+        disp = np.zeros_like(x)
+        np.add.at(disp, i, -step)
+        np.add.at(disp, j, step)
+        x = x + disp
+        x[:, 0] = np.clip(x[:, 0], lo[0] + r, hi[0] - r)
+        x[:, 1] = np.clip(x[:, 1], lo[1] + r, hi[1] - r)
+        x[:, 2] = np.clip(x[:, 2], lo[2] + r, hi[2] - r)
+    return x
+
+
+def make_particles(spec: dict, rng):
+    n = int(spec["n"])
+    dlo, dhi = spec["d"]
+    origin = np.asarray(spec["origin"], dtype=np.float64)
+    extent = np.asarray(spec["extent"], dtype=np.float64)
+    if dlo == dhi:
+        d = np.full(n, dlo)
+    else:
+        d = dlo + (dhi - dlo) * rng.random(n)
+    r = 0.5 * d
+    top = origin[2] + spec["bed_frac"] * extent[2]
+    if spec["packing"] == "rsa":
+        rr = 0.5 * dlo
+        x = rsa(rng, n, dlo, origin + rr, np.array([origin[0] + extent[0] - rr,
+                                                   origin[1] + extent[1] - rr, top - rr]))
+    elif spec["packing"] == "fcc":
+        a_nn = dhi * (0.74048 / spec["phi"]) ** (1.0 / 3.0)
+        x = fcc_sites(a_nn, origin, origin + extent, n)
+        jit = 0.5 * (a_nn - dhi)
+        u = rng.normal(size=(n, 3))
+        u /= np.linalg.norm(u, axis=1)[:, None]
+        x = x + u * (jit * rng.random(n) ** (1.0 / 3.0))[:, None]
+    elif spec["packing"] == "fcc_relax":
+        vol = extent[0] * extent[1] * spec["bed_frac"] * extent[2]
+        density = n / vol
+        a_nn = (math.sqrt(2.0) / density) ** (1.0 / 3.0)
+        x = fcc_sites(a_nn, origin, origin + extent, n)
+        x = x + (0.05 * a_nn) * (rng.random((n, 3)) - 0.5)
+        x = push_apart(rng, x, r, origin, origin + extent, tol=0.01 * dlo)
+    else:
+        raise ValueError(spec["packing"])
+    return np.ascontiguousarray(x), np.ascontiguousarray(r)
+
+
+# --------------------------------------------------------------- fields
+
+_GLL = {1: [0.0, 1.0], 2: [0.0, 0.5, 1.0],
+        3: [0.0, 0.5 - 0.5 / math.sqrt(5.0), 0.5 + 0.5 / math.sqrt(5.0), 1.0]}
+
+
+def node_axes(origin, extent, n_el, deg):
+    """1D node coordinates of the Q_deg grid per axis (GLL points in each
+    element), used only to sample the analytic input fields."""
+    z = np.asarray(_GLL[deg])
+    out = []
+    for a in range(3):
+        h = extent[a] / n_el[a]
+        t = (np.arange(n_el[a])[:, None] + z[None, :-1]).reshape(-1)
+        t = np.concatenate([t, [float(n_el[a])]])
+        out.append(origin[a] + h * t)
+    return out
+
+
+def make_fields(spec: dict, rng, n_particles: int):
+    k = spec["k"]
+    kp = max(1, k - 1)
+    origin = np.asarray(spec["origin"], dtype=np.float64)
+    extent = np.asarray(spec["extent"], dtype=np.float64)
+    n_el = spec["n_el"]
+    ax, ay, az = node_axes(origin, extent, n_el, k)
+    Z, Y, X = np.meshgrid(az, ay, ax, indexing="ij")
+    nn = X.size
+    u = np.zeros((nn, 3))
+    if spec["field"] == "sine":
+        u[:, 2] = spec["u_mean"] + 0.05 * np.sin(2.0 * math.pi * (X.ravel() - origin[0]) / extent[0])
+    else:
+        u[:, 2] = spec["u_mean"]
+        u += 0.05 * spec["u_mean"] * (2.0 * rng.random((nn, 3)) - 1.0)
+    px, py, pz = node_axes(origin, extent, n_el, kp)
+    PZ, PY, PX = np.meshgrid(pz, py, px, indexing="ij")
+    G = spec["phi"] * (RHO_P - 1.2) * 9.81
+    p = G * (origin[2] + extent[2] - PZ.ravel())
+    u_p = 0.1 * rng.random((n_particles, 3)) - 0.05
+    return np.ascontiguousarray(u), np.ascontiguousarray(p), np.ascontiguousarray(u_p)
+
+
+def make_workload(name: str, seed: int | None = None) -> dict:
+    """All inputs of one coupling step of the named workload."""
+    spec = dict(WORKLOADS[name])
+    rng = np.random.default_rng(SEED0 + spec["index"] if seed is None else seed)
+    x, r = make_particles(spec, rng)
+    u, p, u_p = make_fields(spec, rng, x.shape[0])
+    params = gas_params(float(np.mean(spec["d"])), spec["k"])
+    return dict(name=name, origin=tuple(spec["origin"]), extent=tuple(spec["extent"]),
+                n_el=tuple(spec["n_el"]), k=spec["k"], x=x, r=r, u_p=u_p, u_nodal=u,
+                p_nodal=p, params=params)
+
+
+def make_random_case(seed: int, n_el=(3, 4, 5), k=2, n=150, extent=(0.03, 0.04, 0.05),
+                     d=(2e-3, 6e-3), origin=(0.0, 0.0, 0.0), overlap_ok=True) -> dict:
+    """Small uneven case for parity tests: uniform random centres over the
+    whole box (overlaps allowed), diameters uniform in d."""
+    rng = np.random.default_rng(seed)
+    origin = np.asarray(origin, dtype=np.float64)
+    extent = np.asarray(extent, dtype=np.float64)
+    x = origin + extent * rng.random((n, 3))
+    r = 0.5 * (d[0] + (d[1] - d[0]) * rng.random(n))
+    spec = dict(origin=origin, extent=extent, n_el=n_el, k=k, field="noise", u_mean=1.0,
+                phi=0.3)
+    u, p, u_p = make_fields(spec, rng, n)
+    params = gas_params(float(np.mean(d)), k)
+    return dict(name="random%d" % seed, origin=tuple(origin), extent=tuple(extent),
+                n_el=tuple(n_el), k=k, x=np.ascontiguousarray(x), r=np.ascontiguousarray(r),
+                u_p=u_p, u_nodal=u, p_nodal=p, params=params)
