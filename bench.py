@@ -1,0 +1,360 @@
+"""Benchmark of the CFD-DEM coupling step on GB300.
+
+One step = the whole hot path on one synthetic bed: particle location and
+counting-sort binning, quadrature-centred void fraction, its smoothed L2
+projection (CG), per-particle forces and the fluid source term.  Workload:
+the Q2 32x32x128 mesh (0.1 x 0.1 x 0.4 m, 3x3x3 Gauss points, 1,085,825
+nodes) with 100,000 spheres of d ~ U[2, 3] mm packed to a solid fraction of
+~0.53 in the lower 40 % (synthetic, seeded).
+
+The headline `value` is the mixed path (FP32 work, FP64 refinement of the
+projection), in particle-coupling updates per second; the FP64 path is
+reported beside it with the error of the mixed results against it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs an independent replica of the step on its own
+GPU (the step has no exchange between beds); value = all particles / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-coupling updates/s (eps+L2 proj+forces), mixed vs FP64 at stated err"
+WORKLOAD = "q2_32x32x128_100k"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+FP32_TFLOPS = 73.13    # measured FMA peak on this GB300 (profiles/alu_peaks_gb300.md)
+FP64_TFLOPS = 1.197
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(p)), "measured"
+    except Exception:
+        return PEAKS_FALLBACK, "fallback"
+
+
+def rel_err(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    floor = 1e-3 * np.max(np.abs(b)) if b.size else 1.0
+    den = np.maximum(np.abs(b), floor if floor > 0 else 1e-300)
+    return float(np.max(np.abs(a - b) / den)) if b.size else 0.0
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons."""
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_baseline(w, steps=None, budget_s=20.0):
+    """The FP64 oracle as it stands on the host cores, timed on whole steps of
+    the same workload until about budget_s seconds have been spent."""
+    from oracle import oracle as O
+    m = O.Mesh(w["origin"], w["extent"], w["n_el"], w["k"])
+    prm = dict(w["params"], oracle_rtol=1e-13)
+    n = w["x"].shape[0]
+    times = []
+    t_all = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        O.coupling_step(m, prm, w["x"], w["r"], w["u_p"], w["u_nodal"], w["p_nodal"])
+        times.append(time.perf_counter() - t0)
+        if steps is not None and len(times) >= steps:
+            break
+        if steps is None and time.perf_counter() - t_all > budget_s:
+            break
+    per = float(np.mean(times))
+    return {"value": n / per, "unit": "particle updates/s", "cores": O.num_threads(),
+            "kind": "oracle", "sample": "%d whole coupling steps of %s (FP64, C + OpenMP)"
+            % (len(times), WORKLOAD), "s_per_step": per}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2211_01185_gb300 import synth
+    w = synth.make_workload(WORKLOAD)
+    from oracle import oracle as O
+    O.build()
+    m = O.Mesh(w["origin"], w["extent"], w["n_el"], w["k"])
+    prm = dict(w["params"], oracle_rtol=1e-13)
+    for _ in range(args.warmup):
+        O.coupling_step(m, prm, w["x"], w["r"], w["u_p"], w["u_nodal"], w["p_nodal"])
+    t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.coupling_step(m, prm, w["x"], w["r"], w["u_p"], w["u_nodal"], w["p_nodal"])
+        t.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.mean(t))
+    n = w["x"].shape[0]
+    val = n / (ms * 1e-3)
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "particle updates/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "mesh": "Q2 32x32x128", "particles": n,
+                      "precision": "fp64", "parallelism": "host cores (OpenMP)"},
+           "cpu_baseline": {"value": val, "unit": "particle updates/s",
+                            "cores": O.num_threads(), "kind": "oracle",
+                            "sample": "%d whole coupling steps of %s" % (args.steps, WORKLOAD)},
+           "e2e": {"value": val, "unit": "particle updates/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2211_01185_gb300 import build as B
+    from paper_2211_01185_gb300 import cfdem as cf
+    from paper_2211_01185_gb300 import synth
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.build()
+
+    w = synth.make_workload(WORKLOAD)
+    n = w["x"].shape[0]
+    stream = torch.cuda.Stream(device=dev)
+    t = lambda a: torch.as_tensor(a, dtype=torch.float64).to(dev).contiguous()  # noqa: E731
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def make_ctx(precision):
+        prm = dict(w["params"], precision=precision, max_radius=float(w["r"].max()),
+                   cg_rtol=1e-13 if precision == 0 else 1e-12)
+        return cf.Context(w["origin"], w["extent"], w["n_el"], w["k"], prm, device=local,
+                          stream=stream.cuda_stream)
+
+    with torch.cuda.stream(stream):
+        x, r, up, un, pn = t(w["x"]), t(w["r"]), t(w["u_p"]), t(w["u_nodal"]), t(w["p_nodal"])
+        nn = un.shape[0]
+        ctxs = {0: make_ctx(0), 1: make_ctx(1)}
+        st0 = ctxs[0].stats()
+        E, Q, n_nodes = st0.n_elem, st0.n_qp // st0.n_elem, st0.n_nodes
+        outs = {}
+        for p in (0, 1):
+            outs[p] = {"eps_h": torch.zeros(n_nodes, dtype=torch.float64, device=dev),
+                       "f": torch.empty((n, 3), dtype=torch.float64, device=dev),
+                       "fd": torch.empty((n, 3), dtype=torch.float64, device=dev),
+                       "Fe": torch.empty((E, 3), dtype=torch.float64, device=dev)}
+
+    def step(p):
+        o = outs[p]
+        o["eps_h"].zero_()   # cold start of the projection every step
+        cf.cfdem_coupling_step(ctxs[p].h, n, x, r, up, un, pn, o["eps_h"], o["f"], o["fd"],
+                               o["Fe"])
+
+    def timed(p, k):
+        ev = []
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                step(p)
+            cf.cfdem_synchronize(ctxs[p].h)
+            cf.cfdem_set_timing(ctxs[p].h, 1)
+            if dist is not None:
+                dist.barrier()
+            torch.cuda.synchronize(dev)
+            clk = Clocks(local)
+            for _ in range(k):
+                flush.zero_()                     # evict L2 (256 MiB > 129 MB) between steps
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                step(p)
+                b.record(stream)
+                ev.append((a, b))
+            torch.cuda.synchronize(dev)
+            clocks = clk.stop()
+            st = ctxs[p].stats()
+            cf.cfdem_synchronize(ctxs[p].h)
+        ms = [a.elapsed_time(b) for a, b in ev]
+        tot = float(np.sum(ms))
+        if dist is not None:
+            tt = torch.tensor([tot], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            tot = float(tt.item())
+        return tot / k, st, clocks
+
+    ms64, st64, clk64 = timed(0, max(3, args.steps // 2))
+    ms_mx, st_mx, clk_mx = timed(1, args.steps)
+
+    # error of the mixed path against the FP64 path (same inputs)
+    err = {"eps_h": rel_err(outs[1]["eps_h"].cpu().numpy(), outs[0]["eps_h"].cpu().numpy()),
+           "f": rel_err(outs[1]["f"].cpu().numpy(), outs[0]["f"].cpu().numpy()),
+           "f_drag": rel_err(outs[1]["fd"].cpu().numpy(), outs[0]["fd"].cpu().numpy()),
+           "F_e": rel_err(outs[1]["Fe"].cpu().numpy(), outs[0]["Fe"].cpu().numpy())}
+
+    # end to end through the C ABI with host buffers: pinned H2D of the step's
+    # inputs, the step, D2H of the forces and the fluid source
+    hx = {k: torch.as_tensor(w[k], dtype=torch.float64).pin_memory()
+          for k in ("x", "r", "u_p", "u_nodal", "p_nodal")}
+    hf = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    hF = torch.empty((E, 3), dtype=torch.float64).pin_memory()
+    h2d = sum(v.numel() * 8 for v in hx.values())
+    d2h = (hf.numel() + hF.numel()) * 8
+    ev = []
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup + args.steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            x.copy_(hx["x"], non_blocking=True)
+            r.copy_(hx["r"], non_blocking=True)
+            up.copy_(hx["u_p"], non_blocking=True)
+            un.copy_(hx["u_nodal"], non_blocking=True)
+            pn.copy_(hx["p_nodal"], non_blocking=True)
+            step(1)
+            hf.copy_(outs[1]["f"], non_blocking=True)
+            hF.copy_(outs[1]["Fe"], non_blocking=True)
+            b.record(stream)
+            if i >= args.warmup:
+                ev.append((a, b))
+        torch.cuda.synchronize(dev)
+    e2e_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+    # roofline of the dominant kernel group of the mixed step
+    peaks, peak_kind = _peaks()
+    stages = {name: st_mx.stage_ms[i] / args.steps for i, name in enumerate(cf.STAGES)}
+    calls = {name: st_mx.stage_calls[i] / args.steps for i, name in enumerate(cf.STAGES)}
+    k = w["k"]
+    # algorithmic work per unit (stated in the design doc):
+    #   operator: 7 banded 1D applies x (2k+1) taps x 2 flops + 5 = flops per node
+    #   QCM: per neighbour pair 8 flops (distance) + 20 flops (lens volume)
+    op_flops_node = 7 * (2 * k + 1) * 2 + 5
+    candidates = {
+        "op64": ("alu", op_flops_node * n_nodes, FP64_TFLOPS, "k_apply<double> (FP64 residual)"),
+        "op32": ("hbm", 16.0 * n_nodes, peaks.get("hbm_gbs", 6800.0) / 1e3,
+                 "k_cg_apply<float> (FP32 CG operator)"),
+        "void_fraction": ("alu", None, FP32_TFLOPS, "k_qcm<2,false> (FP32 QCM)"),
+        "forces": ("hbm", 180.0 * n, peaks.get("hbm_gbs", 6800.0) / 1e3, "k_forces<2,1,float>"),
+    }
+    # neighbour pairs of this bed for the QCM flop count (outside the timed region)
+    with torch.cuda.stream(stream):
+        cnt = torch.zeros(E * Q, dtype=torch.int32, device=dev)
+        cf.cfdem_void_fraction(ctxs[0].h, n, x, r, None, cnt, None)
+        cf.cfdem_synchronize(ctxs[0].h)
+        pairs = float(cnt.sum().item())
+    candidates["void_fraction"] = ("alu", 28.0 * pairs, FP32_TFLOPS, "k_qcm<2,false> (FP32 QCM)")
+    dom = max(candidates, key=lambda s: stages[s])
+    bound, work, peak, kname = candidates[dom]
+    per_launch_ms = stages[dom] / max(calls[dom], 1.0)
+    if bound == "alu":
+        achieved = work / (per_launch_ms * 1e-3) / 1e12
+        unit, peak_v = "TFLOP/s", peak
+    else:
+        achieved = work / (per_launch_ms * 1e-3) / 1e9
+        unit, peak_v = "GB/s", peaks.get("hbm_gbs", 6800.0)
+    roof = {"bound": bound, "kernel": kname, "achieved": achieved, "peak": peak_v,
+            "unit": unit, "frac": achieved / peak_v, "traffic": None,
+            "peak_source": ("measured FMA loop (profiles/alu_peaks_gb300.md)" if bound == "alu"
+                            else "%s MEASURED_PEAKS.json hbm_gbs" % peak_kind),
+            "launches_per_step": calls[dom], "ms_per_launch": per_launch_ms}
+
+    value = world * n / (ms_mx * 1e-3)
+    res = {"metric": METRIC, "value": value, "unit": "particle updates/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mx,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "mesh": "Q2 32x32x128, 3x3x3 Gauss",
+                      "particles": n, "nodes": n_nodes, "precision": "mixed",
+                      "l2": "256 MiB buffer written between timed steps",
+                      "cg_rtol": 1e-12, "cold_start": True,
+                      "parallelism": "replicas" if world > 1 else "single GPU"},
+           "fp64": {"value": world * n / (ms64 * 1e-3), "ms_per_step": ms64, "dtype": "f64",
+                    "cg_iterations": st64.cg_iterations,
+                    "stages_ms": {nm: st64.stage_ms[i] / max(3, args.steps // 2)
+                                  for i, nm in enumerate(cf.STAGES)}},
+           "err_mixed_vs_fp64": err,
+           "stages_ms": stages,
+           "cg": {"mixed_inner_iterations": st_mx.cg_iterations, "mixed_outer": st_mx.cg_outer,
+                  "mixed_relres": st_mx.cg_relres, "fp64_iterations": st64.cg_iterations,
+                  "fp64_relres": st64.cg_relres},
+           "roofline": roof,
+           "e2e": {"value": world * n / (e2e_ms * 1e-3), "unit": "particle updates/s",
+                   "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+           "gpu_launches": int(st_mx.kernel_launches),
+           "clocks": clk_mx}
+    if rank == 0 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(w)
+    if dist is not None:
+        dist.barrier()
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    for c in ctxs.values():
+        c.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,218 @@
+/*
+ * cfdem.h -- C ABI of the GB300 CFD-DEM coupling library.
+ *
+ * One coupling step of unresolved CFD-DEM on a Q_k (k = 1..3) Lagrange
+ * hexahedral mesh, as stated in "Towards High-Order CFD-DEM: Development and
+ * Validation" (arXiv 2211.01185):
+ *   - void fraction from particle positions and radii (Eq. void_fraction,
+ *     Sec. 2.1), quadrature-centred (QCM) or particle-centroid (PCM);
+ *   - its smoothed L2 projection onto the nodal Q_k space, with smoothing
+ *     length L^2 (the "void fraction smoothing factor" of Tables setup1,
+ *     setup2 and setup4): (M + L^2 K) eps_h = b;
+ *   - per-particle drag, buoyancy and pressure-gradient forces (Sec. 2.3.2,
+ *     Eqs. drag, beta, the Dallavalle and Di Felice C_D, buoyancy and
+ *     undisturbed-flow forces) and the fluid source term F_pf (Eqs. fb, fa).
+ *
+ * Conventions shared by every call:
+ *   - Pointers named *_dev are device pointers on the context's device; the
+ *     caller owns them.  Arrays are C-contiguous FP64 unless stated:
+ *     positions x[n][3], radii r[n], particle velocities u_p[n][3], nodal
+ *     velocities u[n_nodes][3], nodal pressure p[n_pnodes].
+ *   - Element e = ex + Nx (ey + Ny ez); quadrature point q = qx + nq (qy + nq
+ *     qz) with nq = k + 1 Gauss-Legendre points per axis; node n = ix + (Nx k
+ *     + 1)(iy + (Ny k + 1) iz) with GLL points inside each element.  The
+ *     pressure space is Q_kp on the same elements (kp = pressure_degree).
+ *   - Every call is ordered on the context's CUDA stream and returns without
+ *     synchronising.  Errors found on the device (a particle outside the
+ *     mesh, an unconverged solve) are reported by the next cfdem_synchronize
+ *     or cfdem_get_stats.  No call aborts the process or traps the GPU.
+ *   - The context owns its scratch memory and grows it on demand; a call that
+ *     needs to grow it must not be inside stream capture.
+ *   - Results of the FP64 path match the FP64 CPU oracle within 1e-10
+ *     (relative to max(|b_i|, 1e-3 max|b|)); indices (element, bin, sort
+ *     order, neighbour counts) are bit-exact.  The mixed path matches within
+ *     1e-5.
+ */
+#ifndef CFDEM_H
+#define CFDEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cfdem_ctx *cfdem_t;
+
+typedef enum {
+    CFDEM_OK = 0,
+    CFDEM_EINVAL = -1,          /* bad argument; nothing was launched */
+    CFDEM_OUT_OF_DOMAIN = -2,   /* a particle centre lies outside the mesh */
+    CFDEM_NOT_CONVERGED = -3,   /* CG stopped at cg_maxit; last iterate kept */
+    CFDEM_ENOMEM = -4,          /* device allocation failed */
+    CFDEM_ECUDA = -5,           /* a CUDA runtime call failed */
+    CFDEM_ESTATE = -6           /* call needs set_mesh / a previous stage */
+} cfdem_status;
+
+/* Physical and numerical parameters.  cfdem_params_default fills them. */
+typedef struct {
+    double rho_f;          /* fluid density [kg/m^3] */
+    double mu_f;           /* fluid dynamic viscosity [Pa s] */
+    double g[3];           /* gravity [m/s^2]; buoyancy f_B = -rho_f V_p g */
+    int scheme;            /* 0 = QCM (quadrature-centred), 1 = PCM */
+    double qcm_radius;     /* averaging-sphere radius R; 0 => (3 V_e / 4 pi)^(1/3) */
+    double l2_smoothing;   /* L^2 [m^2]; 0 => plain L2 (mass) projection */
+    int drag_model;        /* 0 = Di Felice, 1 = Dallavalle */
+    int vans_model;        /* 0 = model A (F_pf from drag), 1 = model B (drag + grad p) */
+    int beta_over_eps;     /* 1 => beta_B = beta_A / eps (Eq. beta) */
+    int precision;         /* 0 = FP64, 1 = mixed (FP32 work, FP64 refinement) */
+    double cg_rtol;        /* stop when ||b - A x||_2 <= cg_rtol ||b||_2 */
+    int cg_maxit;          /* iteration cap of the solve */
+    double eps_floor;      /* closures use eps_c = min(max(eps, eps_floor), 1) */
+    int pressure_degree;   /* kp; 0 => max(1, k - 1) */
+    double max_radius;     /* hint for the bin size (largest particle radius); 0 => R */
+    double bin_edge;       /* bin edge [m]; 0 => R + max_radius */
+} cfdem_params;
+
+/* Counters of the last calls on a context. */
+typedef struct {
+    int64_t first_bad_particle;   /* -1 or the lowest index found outside the mesh */
+    int32_t cg_iterations;        /* total (inner) iterations of the last solve */
+    int32_t cg_outer;             /* refinement steps of the last mixed solve */
+    double cg_relres;             /* ||b - A x|| / ||b|| at exit */
+    int32_t converged;            /* 1 if the last solve met cg_rtol */
+    int32_t nb[3];                /* bins per axis */
+    double bin_edge[3];           /* bin edges [m] */
+    double qcm_radius;            /* resolved averaging radius [m] */
+    int64_t n_elem, n_qp, n_nodes, n_pnodes;
+    /* with cfdem_set_timing(ctx, 1): device time [ms] and calls per stage
+     * since the last cfdem_set_timing: 0 locate+bin (a1-a2), 1 void fraction
+     * kernel (a3), 2 right-hand side (a4), 3 whole solve (a5), 4 forces (a6),
+     * 5 fluid source (a7), 6 FP32 operator launches, 7 FP64 operator
+     * launches */
+    double stage_ms[8];
+    int64_t stage_calls[8];
+    int32_t timer_overflow;       /* 1 if more than 4096 pairs per stage were asked */
+    int64_t kernel_launches;      /* kernels launched by the library since set_timing */
+} cfdem_stats;
+
+/* Create a context on CUDA device `device`, ordering all work on `stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * handle.  Returns CFDEM_ECUDA if the device cannot be used. */
+cfdem_status cfdem_create(cfdem_t *out, int device, void *stream);
+
+/* Free the context and all scratch memory it owns.  NULL is accepted. */
+cfdem_status cfdem_destroy(cfdem_t ctx);
+
+/* Fill *p with the defaults: gas (rho_f 1.2, mu_f 1.8e-5), g = (0,0,-9.81),
+ * QCM, Di Felice, model A, FP64, cg_rtol 1e-13, cg_maxit 2000, eps_floor
+ * 0.05, everything else 0 (resolved from the mesh). */
+void cfdem_params_default(cfdem_params *p);
+
+/* Mesh: the axis-aligned box [origin, origin + extent] cut into n_el[0] x
+ * n_el[1] x n_el[2] equal hexahedra carrying Q_degree (degree 1..3).  The
+ * paper couples both phases on this one mesh (Sec. 2.3).  Host pointers. */
+cfdem_status cfdem_set_mesh(cfdem_t ctx, const double origin[3], const double extent[3],
+                            const int n_el[3], int degree);
+
+/* Parameters (host struct, copied).  Resolves R, kp and the bin grid. */
+cfdem_status cfdem_set_params(cfdem_t ctx, const cfdem_params *p);
+
+/* The resolved parameters (qcm_radius, pressure_degree, bin_edge filled). */
+cfdem_status cfdem_get_params(cfdem_t ctx, cfdem_params *p);
+
+/* Step a1 -- element location (Sec. 2.3: particles live on the fluid mesh).
+ * elem_dev[n] (int32) = element of each centre: per axis floor((x - x0)/h)
+ * with IEEE division, clamped to [0, N-1] (a centre on an interior face
+ * belongs to the upper element); xi_dev[n][3] = reference coordinates
+ * (x - x0)/h - e_axis.  Either output may be NULL.  A centre outside the box
+ * by more than 1e-12 of its extent gets elem = -1 and sets
+ * CFDEM_OUT_OF_DOMAIN. */
+cfdem_status cfdem_locate(cfdem_t ctx, int64_t n, const double *x_dev, int32_t *elem_dev,
+                          double *xi_dev);
+
+/* Step a2 -- stable counting sort of the particles into the context's bin
+ * grid (bin = per-axis floor((x - x0)/b), clamped; bx fastest).  Outputs
+ * (device, optional): bin_start_dev[nbins + 1] exclusive prefix of the bin
+ * counts, perm_dev[n] particle ids in bin order, ascending inside a bin. */
+cfdem_status cfdem_bin(cfdem_t ctx, int64_t n, const double *x_dev, int32_t *bin_start_dev,
+                       int32_t *perm_dev);
+
+/* Steps a1-a3 -- void fraction at every quadrature point, eps_q_dev[E][Q].
+ * QCM: eps_q = 1 - sum_i V_lens(R, r_i, |x_q - x_i|) / (4/3 pi R^3) over the
+ * particles with |x_q - x_i|^2 < (R + r_i)^2 (a reading of the deferred
+ * void-fraction scheme; Eq. void_fraction gives its particle-centroid
+ * limit).  PCM: eps_e = (V_e - sum_{i in e} V_p,i) / V_e (Eq.
+ * void_fraction), copied to all Q points.  eps_q_dev may be NULL: the
+ * result is then kept inside the context for cfdem_project.  nb_count_dev
+ * [E][Q] (int32) and nb_idsum_dev [E][Q] (int64), optional, receive the
+ * QCM neighbour count and the sum of neighbour ids per point. */
+cfdem_status cfdem_void_fraction(cfdem_t ctx, int64_t n, const double *x_dev,
+                                 const double *r_dev, double *eps_q_dev, int32_t *nb_count_dev,
+                                 int64_t *nb_idsum_dev);
+
+/* Step a4 -- projection right-hand side b_j = sum_e sum_q phi_j(x_q) w_q
+ * |J_e| eps_q from eps_q_dev[E][Q] (NULL = the context's last void
+ * fraction); b_dev[n_nodes]. */
+cfdem_status cfdem_project_rhs(cfdem_t ctx, const double *eps_q_dev, double *b_dev);
+
+/* The projection operator y = (M + L^2 K) x on nodal vectors (device,
+ * n_nodes), matrix-free and sum-factorised. */
+cfdem_status cfdem_apply(cfdem_t ctx, const double *x_dev, double *y_dev);
+
+/* Steps a4-a5 -- smoothed L2 projection: solves (M + L^2 K) eps_h = b by
+ * Jacobi-preconditioned CG (FP64) or FP32 CG inside FP64 iterative
+ * refinement (mixed).  eps_q_dev: NULL = the context's last void fraction.
+ * eps_nodal_dev[n_nodes]: start vector on entry, solution on exit.  The
+ * iteration count and relative residual go to cfdem_get_stats. */
+cfdem_status cfdem_project(cfdem_t ctx, const double *eps_q_dev, double *eps_nodal_dev);
+
+/* Steps a6-a7 -- particle forces and fluid source.  Per particle i: u_f,
+ * eps (Q_k) and grad p (Q_kp) interpolated at x_i; eps_c clamped to
+ * [eps_floor, 1] for the closures; Re_p = rho_f eps_c |u_f - u_p| d_p /
+ * mu_f; f_D = 1/2 rho_f C_D pi r^2 |U| U (Dallavalle, or Di Felice's
+ * C_D eps_c^(2 - chi)), divided by eps_c if beta_over_eps; f_B = -rho_f V_p
+ * g; f_gradp = -V_p grad p; f = f_D + f_B + f_gradp.  Fluid source per
+ * element F_e = -(1/V_e) sum_{i in e} S_i with S_i = f_D (model A) or f_D +
+ * f_gradp (model B).  Outputs (device): f_dev[n][3] required; f_drag_dev
+ * [n][3], F_elem_dev[E][3] and F_q_dev[E][Q][3] (F_e at every quadrature
+ * point) optional. */
+cfdem_status cfdem_forces(cfdem_t ctx, int64_t n, const double *x_dev, const double *r_dev,
+                          const double *u_p_dev, const double *u_nodal_dev,
+                          const double *p_nodal_dev, const double *eps_nodal_dev,
+                          double *f_dev, double *f_drag_dev, double *F_elem_dev,
+                          double *F_q_dev);
+
+/* Steps a1-a7 in one call: void fraction, projection (eps_nodal_dev is the
+ * start vector and receives eps_h), forces and fluid source.  Outputs as in
+ * cfdem_forces. */
+cfdem_status cfdem_coupling_step(cfdem_t ctx, int64_t n, const double *x_dev,
+                                 const double *r_dev, const double *u_p_dev,
+                                 const double *u_nodal_dev, const double *p_nodal_dev,
+                                 double *eps_nodal_dev, double *f_dev, double *f_drag_dev,
+                                 double *F_elem_dev, double *F_q_dev);
+
+/* Wait for the context's stream and return the first device-side error of
+ * the calls since the last synchronize (CFDEM_OUT_OF_DOMAIN,
+ * CFDEM_NOT_CONVERGED) or CFDEM_OK. */
+cfdem_status cfdem_synchronize(cfdem_t ctx);
+
+/* Synchronize, then copy the counters into *out. */
+cfdem_status cfdem_get_stats(cfdem_t ctx, cfdem_stats *out);
+
+/* Turn the per-stage CUDA-event timers on (1) or off (0) and reset them and
+ * the launch counter.  Synchronizes the stream.  Timers record an event pair
+ * per stage and per operator launch; they do not change results. */
+cfdem_status cfdem_set_timing(cfdem_t ctx, int enable);
+
+/* Text of the last error on this context ("" if none).  Owned by ctx. */
+const char *cfdem_last_error(cfdem_t ctx);
+
+/* Library version string. */
+const char *cfdem_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CFDEM_H */

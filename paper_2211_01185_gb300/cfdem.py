@@ -1,0 +1,270 @@
+"""Thin ctypes binding of the C ABI in ``include/cfdem.h``.
+
+Argument marshalling only: every step of the coupling path runs in the CUDA
+library ``_lib/libcfdem.so``.  Functions keep the C names; device buffers are
+passed as integer addresses (``tensor.data_ptr()``), so PyTorch serves only
+as the device allocator and stream provider.  There is no CPU fallback: if
+the library is missing the import of any entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libcfdem.so")
+HEADER = os.path.join(_HERE, "..", "include", "cfdem.h")
+
+OK = 0
+EINVAL = -1
+OUT_OF_DOMAIN = -2
+NOT_CONVERGED = -3
+ENOMEM = -4
+ECUDA = -5
+ESTATE = -6
+STATUS_NAMES = {0: "CFDEM_OK", -1: "CFDEM_EINVAL", -2: "CFDEM_OUT_OF_DOMAIN",
+                -3: "CFDEM_NOT_CONVERGED", -4: "CFDEM_ENOMEM", -5: "CFDEM_ECUDA",
+                -6: "CFDEM_ESTATE"}
+
+
+class cfdem_params(C.Structure):
+    _fields_ = [("rho_f", C.c_double), ("mu_f", C.c_double), ("g", C.c_double * 3),
+                ("scheme", C.c_int), ("qcm_radius", C.c_double), ("l2_smoothing", C.c_double),
+                ("drag_model", C.c_int), ("vans_model", C.c_int), ("beta_over_eps", C.c_int),
+                ("precision", C.c_int), ("cg_rtol", C.c_double), ("cg_maxit", C.c_int),
+                ("eps_floor", C.c_double), ("pressure_degree", C.c_int),
+                ("max_radius", C.c_double), ("bin_edge", C.c_double)]
+
+
+class cfdem_stats(C.Structure):
+    _fields_ = [("first_bad_particle", C.c_int64), ("cg_iterations", C.c_int32),
+                ("cg_outer", C.c_int32), ("cg_relres", C.c_double), ("converged", C.c_int32),
+                ("nb", C.c_int32 * 3), ("bin_edge", C.c_double * 3), ("qcm_radius", C.c_double),
+                ("n_elem", C.c_int64), ("n_qp", C.c_int64), ("n_nodes", C.c_int64),
+                ("n_pnodes", C.c_int64), ("stage_ms", C.c_double * 8),
+                ("stage_calls", C.c_int64 * 8), ("timer_overflow", C.c_int32),
+                ("kernel_launches", C.c_int64)]
+
+STAGES = ("bin", "void_fraction", "rhs", "solve", "forces", "fluid_source", "op32", "op64")
+
+
+_lib = None
+
+
+def header_functions():
+    """Names of the functions that include/cfdem.h declares."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(cfdem_\w+)\s*\(", txt, re.M)))
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libcfdem.so is not built (run __graft_entry__.build() or "
+                           "python -m paper_2211_01185_gb300.build)")
+    try:  # share PyTorch's CUDA runtime when it is loaded
+        import torch  # noqa: F401
+    except Exception:  # pragma: no cover
+        pass
+    L = C.CDLL(LIB_PATH)
+    vp, i64, dbl, cint = C.c_void_p, C.c_int64, C.c_double, C.c_int
+    d3 = C.POINTER(C.c_double)
+    L.cfdem_version.restype = C.c_char_p
+    L.cfdem_create.argtypes = [C.POINTER(vp), cint, vp]
+    L.cfdem_destroy.argtypes = [vp]
+    L.cfdem_params_default.argtypes = [C.POINTER(cfdem_params)]
+    L.cfdem_params_default.restype = None
+    L.cfdem_set_mesh.argtypes = [vp, d3, d3, C.POINTER(cint), cint]
+    L.cfdem_set_params.argtypes = [vp, C.POINTER(cfdem_params)]
+    L.cfdem_get_params.argtypes = [vp, C.POINTER(cfdem_params)]
+    L.cfdem_locate.argtypes = [vp, i64, vp, vp, vp]
+    L.cfdem_bin.argtypes = [vp, i64, vp, vp, vp]
+    L.cfdem_void_fraction.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+    L.cfdem_project_rhs.argtypes = [vp, vp, vp]
+    L.cfdem_apply.argtypes = [vp, vp, vp]
+    L.cfdem_project.argtypes = [vp, vp, vp]
+    L.cfdem_forces.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.cfdem_coupling_step.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.cfdem_synchronize.argtypes = [vp]
+    L.cfdem_get_stats.argtypes = [vp, C.POINTER(cfdem_stats)]
+    L.cfdem_set_timing.argtypes = [vp, cint]
+    L.cfdem_last_error.argtypes = [vp]
+    L.cfdem_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+class CfdemError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return C.c_void_p(int(t.data_ptr()) if hasattr(t, "data_ptr") else int(t))
+
+
+def _check(h, st):
+    if st != OK:
+        raise CfdemError(st, lib().cfdem_last_error(h).decode())
+    return st
+
+
+# ------------------------------------------------------------------ C names
+
+def cfdem_version():
+    return lib().cfdem_version().decode()
+
+
+def cfdem_params_default():
+    p = cfdem_params()
+    lib().cfdem_params_default(C.byref(p))
+    return p
+
+
+def cfdem_create(device=0, stream=None):
+    h = C.c_void_p()
+    st = lib().cfdem_create(C.byref(h), int(device), C.c_void_p(stream or 0))
+    if st != OK:
+        raise CfdemError(st, "cfdem_create failed")
+    return h
+
+
+def cfdem_destroy(h):
+    return lib().cfdem_destroy(h)
+
+
+def cfdem_set_mesh(h, origin, extent, n_el, degree):
+    o = (C.c_double * 3)(*[float(v) for v in origin])
+    e = (C.c_double * 3)(*[float(v) for v in extent])
+    n = (C.c_int * 3)(*[int(v) for v in n_el])
+    return _check(h, lib().cfdem_set_mesh(h, o, e, n, int(degree)))
+
+
+def cfdem_set_params(h, p):
+    return _check(h, lib().cfdem_set_params(h, C.byref(p)))
+
+
+def cfdem_get_params(h):
+    p = cfdem_params()
+    _check(h, lib().cfdem_get_params(h, C.byref(p)))
+    return p
+
+
+def cfdem_locate(h, n, x, elem, xi):
+    return _check(h, lib().cfdem_locate(h, int(n), _ptr(x), _ptr(elem), _ptr(xi)))
+
+
+def cfdem_bin(h, n, x, bin_start, perm):
+    return _check(h, lib().cfdem_bin(h, int(n), _ptr(x), _ptr(bin_start), _ptr(perm)))
+
+
+def cfdem_void_fraction(h, n, x, r, eps_q=None, nb_count=None, nb_idsum=None):
+    return _check(h, lib().cfdem_void_fraction(h, int(n), _ptr(x), _ptr(r), _ptr(eps_q),
+                                               _ptr(nb_count), _ptr(nb_idsum)))
+
+
+def cfdem_project_rhs(h, eps_q, b):
+    return _check(h, lib().cfdem_project_rhs(h, _ptr(eps_q), _ptr(b)))
+
+
+def cfdem_apply(h, x, y):
+    return _check(h, lib().cfdem_apply(h, _ptr(x), _ptr(y)))
+
+
+def cfdem_project(h, eps_q, eps_nodal):
+    return _check(h, lib().cfdem_project(h, _ptr(eps_q), _ptr(eps_nodal)))
+
+
+def cfdem_forces(h, n, x, r, u_p, u_nodal, p_nodal, eps_nodal, f, f_drag=None, F_elem=None,
+                 F_q=None):
+    return _check(h, lib().cfdem_forces(h, int(n), _ptr(x), _ptr(r), _ptr(u_p), _ptr(u_nodal),
+                                        _ptr(p_nodal), _ptr(eps_nodal), _ptr(f), _ptr(f_drag),
+                                        _ptr(F_elem), _ptr(F_q)))
+
+
+def cfdem_coupling_step(h, n, x, r, u_p, u_nodal, p_nodal, eps_nodal, f, f_drag=None,
+                        F_elem=None, F_q=None):
+    return _check(h, lib().cfdem_coupling_step(h, int(n), _ptr(x), _ptr(r), _ptr(u_p),
+                                               _ptr(u_nodal), _ptr(p_nodal), _ptr(eps_nodal),
+                                               _ptr(f), _ptr(f_drag), _ptr(F_elem), _ptr(F_q)))
+
+
+def cfdem_synchronize(h, raise_on_error=True):
+    st = lib().cfdem_synchronize(h)
+    if raise_on_error:
+        _check(h, st)
+    return st
+
+
+def cfdem_get_stats(h):
+    s = cfdem_stats()
+    _check(h, lib().cfdem_get_stats(h, C.byref(s)))
+    return s
+
+
+def cfdem_set_timing(h, enable):
+    return _check(h, lib().cfdem_set_timing(h, int(bool(enable))))
+
+
+def cfdem_last_error(h):
+    return lib().cfdem_last_error(h).decode()
+
+
+# ------------------------------------------------------------------ helpers
+
+def make_params(**kw):
+    """cfdem_params from keyword arguments on top of the library defaults."""
+    p = cfdem_params_default()
+    for k, v in kw.items():
+        if k == "g":
+            for a in range(3):
+                p.g[a] = float(v[a])
+        elif k == "oracle_rtol":
+            continue
+        else:
+            setattr(p, k, v)
+    return p
+
+
+class Context:
+    """Owns one library context; tensors are torch CUDA tensors."""
+
+    def __init__(self, origin, extent, n_el, degree, params=None, device=0, stream=None):
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream(device).cuda_stream
+        self.h = cfdem_create(device, stream)
+        cfdem_set_mesh(self.h, origin, extent, n_el, degree)
+        if params is not None:
+            self.set_params(params)
+
+    def set_params(self, params):
+        p = params if isinstance(params, cfdem_params) else make_params(**params)
+        cfdem_set_params(self.h, p)
+
+    def stats(self):
+        return cfdem_get_stats(self.h)
+
+    def close(self):
+        if self.h is not None:
+            cfdem_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass

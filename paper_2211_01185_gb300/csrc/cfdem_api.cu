@@ -1,0 +1,736 @@
+// cfdem_api.cu -- host runtime behind the C ABI of include/cfdem.h.
+//
+// A context owns: the mesh and its 1D reference tables, the resolved
+// parameters, the bin grid, the scratch arenas (grown on demand) and the
+// device status words.  Every call is ordered on the context's stream.
+#include <atomic>
+#include <cfloat>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/cfdem.h"
+#include "internal.h"
+
+using namespace cfdem;
+
+// ---------------------------------------------------------------- timers
+namespace cfdem {
+
+static std::atomic<long long> g_launches{0};
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
+
+void Timer::begin(int s, cudaStream_t st) {
+  if (!on) return;
+  if (!ev[s]) {
+    ev[s] = new cudaEvent_t[2 * kCap];
+    for (int i = 0; i < 2 * kCap; ++i) cudaEventCreate(&ev[s][i]);
+  }
+  if (count[s] >= kCap) {
+    overflow = true;
+    return;
+  }
+  cudaEventRecord(ev[s][2 * count[s]], st);
+}
+
+void Timer::end(int s, cudaStream_t st) {
+  if (!on || !ev[s] || count[s] >= kCap) return;
+  cudaEventRecord(ev[s][2 * count[s] + 1], st);
+  ++count[s];
+  ++calls[s];
+}
+
+void Timer::collect() {
+  for (int s = 0; s < kStages; ++s) {
+    for (int i = 0; i < count[s]; ++i) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, ev[s][2 * i], ev[s][2 * i + 1]) == cudaSuccess) ms[s] += t;
+    }
+    count[s] = 0;
+  }
+}
+
+void Timer::release() {
+  for (int s = 0; s < kStages; ++s) {
+    if (!ev[s]) continue;
+    for (int i = 0; i < 2 * kCap; ++i) cudaEventDestroy(ev[s][i]);
+    delete[] ev[s];
+    ev[s] = nullptr;
+  }
+}
+
+}  // namespace cfdem
+
+struct cfdem_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool have_mesh = false;
+  MeshDev mesh{};
+  Tables tab{};
+  BinDev bins{};
+  cfdem_params prm{};
+  double R = 0.0;  // resolved averaging radius
+  double coef[4] = {0, 0, 0, 0};
+  // device memory
+  DevStatus* st = nullptr;
+  double* bands64 = nullptr;
+  float* bands32 = nullptr;
+  // particle arena
+  int64_t cap_n = 0;
+  int32_t *bin_of = nullptr, *slot = nullptr, *perm = nullptr;
+  double* xs64 = nullptr;
+  float* xs32 = nullptr;
+  int64_t cap_bins = 0;
+  int32_t *bin_count = nullptr, *bin_start = nullptr, *scan_tmp = nullptr;
+  // mesh arena
+  double* eps64 = nullptr;     // internal eps_q (FP64 path)
+  float* eps32 = nullptr;      // internal eps_q (mixed path)
+  double* b = nullptr;
+  double* S = nullptr;         // per-element source accumulator [E][3]
+  double* vol = nullptr;       // per-element particle volume (PCM)
+  CgWork cg{};
+  int eps_state = 0;           // 0 none, 1 eps64 valid, 2 eps32 valid
+  // host-side record
+  int last_iters = 0, last_outer = 0, last_converged = 1;
+  double last_relres = 0.0;
+  int pending_not_converged = 0;
+  Timer timer;
+  long long launches_at_reset = 0;
+  std::string err;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+cfdem_status fail(cfdem_t c, cfdem_status s, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return s;
+}
+
+cfdem_status cuda_fail(cfdem_t c, cudaError_t e, const char* where) {
+  if (e == cudaErrorMemoryAllocation)
+    return fail(c, CFDEM_ENOMEM, "%s: out of device memory", where);
+  return fail(c, CFDEM_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(expr, where)                                  \
+  do {                                                   \
+    cudaError_t e_ = (expr);                             \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
+  } while (0)
+
+template <typename T>
+cudaError_t grow(T** p, size_t count) {
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+// ---------------------------------------------------------------- 1D tables
+// Gauss-Legendre points and weights on [-1,1] in closed form (n <= 4), GLL
+// nodes (roots of P_k' plus end points) in closed form (k <= 3).
+void gauss_closed_form(int n, double* s, double* w) {
+  switch (n) {
+    case 1:
+      s[0] = 0.0;
+      w[0] = 2.0;
+      break;
+    case 2: {
+      double a = 1.0 / std::sqrt(3.0);
+      s[0] = -a;
+      s[1] = a;
+      w[0] = w[1] = 1.0;
+      break;
+    }
+    case 3: {
+      double a = std::sqrt(0.6);
+      s[0] = -a;
+      s[1] = 0.0;
+      s[2] = a;
+      w[0] = w[2] = 5.0 / 9.0;
+      w[1] = 8.0 / 9.0;
+      break;
+    }
+    default: {  // 4
+      double r = 2.0 / 7.0 * std::sqrt(6.0 / 5.0);
+      double a = std::sqrt(3.0 / 7.0 - r), bb = std::sqrt(3.0 / 7.0 + r);
+      double wa = (18.0 + std::sqrt(30.0)) / 36.0, wb = (18.0 - std::sqrt(30.0)) / 36.0;
+      s[0] = -bb;
+      s[1] = -a;
+      s[2] = a;
+      s[3] = bb;
+      w[0] = w[3] = wb;
+      w[1] = w[2] = wa;
+      break;
+    }
+  }
+}
+
+void gll_closed_form(int k, double* z) {
+  z[0] = 0.0;
+  z[k] = 1.0;
+  if (k == 2) z[1] = 0.5;
+  if (k == 3) {
+    double a = 0.5 / std::sqrt(5.0);
+    z[1] = 0.5 - a;
+    z[2] = 0.5 + a;
+  }
+}
+
+void bary_weights(int k, const double* z, double* lw) {
+  for (int a = 0; a <= k; ++a) {
+    double p = 1.0;
+    for (int bb = 0; bb <= k; ++bb)
+      if (bb != a) p *= (z[a] - z[bb]);
+    lw[a] = 1.0 / p;
+  }
+}
+
+void lagr(int k, const double* z, const double* lw, double t, double* l, double* dl) {
+  for (int a = 0; a <= k; ++a) {
+    double v = 1.0, dv = 0.0;
+    for (int bb = 0; bb <= k; ++bb) {
+      if (bb == a) continue;
+      dv = dv * (t - z[bb]) + v;
+      v = v * (t - z[bb]);
+    }
+    l[a] = v * lw[a];
+    dl[a] = dv * lw[a];
+  }
+}
+
+void build_tables(int k, int kp, Tables* t) {
+  std::memset(t, 0, sizeof(Tables));
+  int nq = k + 1;
+  double s[4], w[4];
+  gauss_closed_form(nq, s, w);
+  for (int q = 0; q < nq; ++q) {
+    t->g[q] = 0.5 * (1.0 + s[q]);
+    t->w[q] = 0.5 * w[q];
+  }
+  gll_closed_form(k, t->z);
+  gll_closed_form(kp, t->zp);
+  bary_weights(k, t->z, t->lw);
+  bary_weights(kp, t->zp, t->lwp);
+  double l[4][4], dl[4][4];  // [q][a]
+  for (int q = 0; q < nq; ++q) lagr(k, t->z, t->lw, t->g[q], l[q], dl[q]);
+  for (int a = 0; a <= k; ++a)
+    for (int q = 0; q < nq; ++q) t->Bw[a][q] = l[q][a] * t->w[q];
+  // exact with nq = k + 1 Gauss points (degree 2k integrands)
+  for (int a = 0; a <= k; ++a)
+    for (int bb = 0; bb <= k; ++bb) {
+      double m = 0.0, kk = 0.0;
+      for (int q = 0; q < nq; ++q) {
+        m += t->w[q] * l[q][a] * l[q][bb];
+        kk += t->w[q] * dl[q][a] * dl[q][bb];
+      }
+      t->Mh[a][bb] = m;
+      t->Kh[a][bb] = kk;
+    }
+}
+
+bool is_finite_d(double v) { return std::isfinite(v); }
+
+// resolve R, kp, coefficients and the bin grid once mesh and params exist
+cfdem_status resolve(cfdem_t c) {
+  if (!c->have_mesh) return CFDEM_OK;
+  MeshDev& m = c->mesh;
+  cfdem_params& p = c->prm;
+  int kp = p.pressure_degree > 0 ? p.pressure_degree : (m.k > 1 ? m.k - 1 : 1);
+  if (kp < 1 || kp > 3) return fail(c, CFDEM_EINVAL, "pressure_degree must be 1..3");
+  m.kp = kp;
+  for (int a = 0; a < 3; ++a) m.np[a] = m.ne[a] * kp + 1;
+  m.n_pnodes = (int64_t)m.np[0] * m.np[1] * m.np[2];
+  build_tables(m.k, kp, &c->tab);
+  c->R = p.qcm_radius > 0 ? p.qcm_radius : std::cbrt(3.0 * m.Ve / (4.0 * kPi));
+  double L2 = p.l2_smoothing;
+  c->coef[0] = m.h[0] * m.h[1] * m.h[2];
+  c->coef[1] = L2 * m.h[1] * m.h[2] / m.h[0];
+  c->coef[2] = L2 * m.h[0] * m.h[2] / m.h[1];
+  c->coef[3] = L2 * m.h[0] * m.h[1] / m.h[2];
+  double edge = p.bin_edge > 0 ? p.bin_edge : c->R + (p.max_radius > 0 ? p.max_radius : c->R);
+  for (;;) {
+    int64_t tot = 1;
+    for (int a = 0; a < 3; ++a) {
+      double f = std::floor(m.L[a] / edge);
+      int nb = f < 1.0 ? 1 : (f > 1e6 ? 1000000 : (int)f);
+      c->bins.nb[a] = nb;
+      c->bins.be[a] = m.L[a] / nb;
+      tot *= nb;
+    }
+    c->bins.nbins = tot;
+    if (tot <= (int64_t)1 << 26) break;
+    edge *= 1.5;
+  }
+  DeviceGuard g(c->device);
+  CK(upload_bands(m, c->tab, L2, &c->bands64, &c->bands32), "upload_bands");
+  if (c->bins.nbins + 1 > c->cap_bins) {
+    int64_t nb = c->bins.nbins + 1;
+    CK(grow(&c->bin_count, nb), "bins");
+    CK(grow(&c->bin_start, nb), "bins");
+    CK(grow(&c->scan_tmp, nb / 2048 + 2), "bins");
+    c->cap_bins = nb;
+  }
+  c->eps_state = 0;
+  return CFDEM_OK;
+}
+
+cfdem_status ensure_particles(cfdem_t c, int64_t n) {
+  if (n <= c->cap_n) return CFDEM_OK;
+  int64_t cap = n + n / 4 + 1024;
+  CK(grow(&c->bin_of, cap), "particle arena");
+  CK(grow(&c->slot, cap), "particle arena");
+  CK(grow(&c->perm, cap), "particle arena");
+  CK(grow(&c->xs64, 4 * cap), "particle arena");
+  CK(grow(&c->xs32, 8 * cap), "particle arena");
+  c->cap_n = cap;
+  return CFDEM_OK;
+}
+
+void free_mesh_arena(cfdem_t c) {
+  void* ps[] = {c->eps64, c->eps32, c->b, c->S, c->vol, c->cg.r, c->cg.z, c->cg.p0,
+                c->cg.p1, c->cg.Ap, c->cg.dinv, c->cg.xcor, c->cg.r32, c->cg.z32,
+                c->cg.q0, c->cg.q1, c->cg.Aq, c->cg.dinv32, c->cg.d32, c->cg.partials,
+                c->cg.sc};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  c->eps64 = nullptr;
+  c->eps32 = nullptr;
+  c->b = nullptr;
+  c->S = nullptr;
+  c->vol = nullptr;
+  c->cg = CgWork{};
+}
+
+cfdem_status alloc_mesh_arena(cfdem_t c) {
+  const MeshDev& m = c->mesh;
+  int64_t eq = m.E * m.Q, nn = m.n_nodes;
+  CK(grow(&c->eps64, eq), "mesh arena");
+  CK(grow(&c->eps32, eq), "mesh arena");
+  CK(grow(&c->b, nn), "mesh arena");
+  CK(grow(&c->S, 3 * m.E), "mesh arena");
+  CK(grow(&c->vol, m.E), "mesh arena");
+  CgWork& w = c->cg;
+  CK(grow(&w.r, nn), "cg");
+  CK(grow(&w.z, nn), "cg");
+  CK(grow(&w.p0, nn), "cg");
+  CK(grow(&w.p1, nn), "cg");
+  CK(grow(&w.Ap, nn), "cg");
+  CK(grow(&w.dinv, nn), "cg");
+  CK(grow(&w.r32, nn), "cg");
+  CK(grow(&w.z32, nn), "cg");
+  CK(grow(&w.q0, nn), "cg");
+  CK(grow(&w.q1, nn), "cg");
+  CK(grow(&w.Aq, nn), "cg");
+  CK(grow(&w.dinv32, nn), "cg");
+  CK(grow(&w.d32, nn), "cg");
+  w.nblocks = cg_blocks(m);
+  CK(grow(&w.partials, 4 * (size_t)w.nblocks), "cg");
+  CK(grow(&w.sc, 1), "cg");
+  return CFDEM_OK;
+}
+
+cfdem_status need_mesh(cfdem_t c) {
+  if (!c) return CFDEM_EINVAL;
+  if (!c->have_mesh) return fail(c, CFDEM_ESTATE, "cfdem_set_mesh has not been called");
+  return CFDEM_OK;
+}
+
+// bin the particles into the context arena (step a2)
+cfdem_status do_bin(cfdem_t c, int64_t n, const double* x, const double* r) {
+  cfdem_status s = ensure_particles(c, n);
+  if (s != CFDEM_OK) return s;
+  c->timer.begin(kStageBin, c->stream);
+  CK(cudaMemsetAsync(&c->st->rmax_bits, 0, sizeof(unsigned long long), c->stream), "bin");
+  CK(launch_bin(c->mesh, c->bins, n, x, r, c->bin_of, c->slot, c->bin_count, c->bin_start,
+                c->perm, c->scan_tmp, c->xs64, c->xs32, c->st, c->stream),
+     "bin");
+  c->timer.end(kStageBin, c->stream);
+  return CFDEM_OK;
+}
+
+}  // namespace
+
+// ============================================================== public API
+
+extern "C" {
+
+const char* cfdem_version(void) { return "cfdem-gb300 0.1 (sm_103a)"; }
+
+void cfdem_params_default(cfdem_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof *p);
+  p->rho_f = 1.2;
+  p->mu_f = 1.8e-5;
+  p->g[0] = 0.0;
+  p->g[1] = 0.0;
+  p->g[2] = -9.81;
+  p->scheme = 0;
+  p->drag_model = 0;
+  p->vans_model = 0;
+  p->precision = 0;
+  p->cg_rtol = 1e-13;
+  p->cg_maxit = 2000;
+  p->eps_floor = 0.05;
+}
+
+cfdem_status cfdem_create(cfdem_t* out, int device, void* stream) {
+  if (!out) return CFDEM_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+    return CFDEM_ECUDA;
+  cfdem_t c = new cfdem_ctx();
+  c->device = device;
+  c->stream = (cudaStream_t)stream;
+  cfdem_params_default(&c->prm);
+  DeviceGuard g(device);
+  if (cudaMalloc((void**)&c->st, sizeof(DevStatus)) != cudaSuccess) {
+    delete c;
+    return CFDEM_ENOMEM;
+  }
+  DevStatus init{};
+  init.first_bad = ~0ull;
+  if (cudaMemcpy(c->st, &init, sizeof init, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(c->st);
+    delete c;
+    return CFDEM_ECUDA;
+  }
+  *out = c;
+  return CFDEM_OK;
+}
+
+cfdem_status cfdem_destroy(cfdem_t c) {
+  if (!c) return CFDEM_OK;
+  DeviceGuard g(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  free_mesh_arena(c);
+  c->timer.release();
+  void* ps[] = {c->st, c->bands64, c->bands32, c->bin_of, c->slot, c->perm, c->xs64,
+                c->xs32, c->bin_count, c->bin_start, c->scan_tmp};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  delete c;
+  return CFDEM_OK;
+}
+
+cfdem_status cfdem_set_mesh(cfdem_t c, const double origin[3], const double extent[3],
+                            const int n_el[3], int degree) {
+  if (!c || !origin || !extent || !n_el) return fail(c, CFDEM_EINVAL, "null argument");
+  if (degree < 1 || degree > 3) return fail(c, CFDEM_EINVAL, "degree must be 1, 2 or 3");
+  MeshDev m{};
+  for (int a = 0; a < 3; ++a) {
+    if (!is_finite_d(origin[a]) || !is_finite_d(extent[a]) || !(extent[a] > 0))
+      return fail(c, CFDEM_EINVAL, "origin/extent must be finite, extent > 0");
+    if (n_el[a] < 1 || n_el[a] > (1 << 20)) return fail(c, CFDEM_EINVAL, "bad n_el");
+    m.x0[a] = origin[a];
+    m.L[a] = extent[a];
+    m.ne[a] = n_el[a];
+    m.h[a] = extent[a] / n_el[a];
+    m.nn[a] = n_el[a] * degree + 1;
+  }
+  m.k = degree;
+  m.nq = degree + 1;
+  m.Q = m.nq * m.nq * m.nq;
+  m.E = (int64_t)m.ne[0] * m.ne[1] * m.ne[2];
+  m.n_nodes = (int64_t)m.nn[0] * m.nn[1] * m.nn[2];
+  m.Ve = m.h[0] * m.h[1] * m.h[2];
+  if (m.E * m.Q > ((int64_t)1 << 31) || m.n_nodes > ((int64_t)1 << 31))
+    return fail(c, CFDEM_EINVAL, "mesh too large");
+  DeviceGuard g(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  free_mesh_arena(c);
+  c->mesh = m;
+  c->have_mesh = true;
+  cfdem_status s = alloc_mesh_arena(c);
+  if (s != CFDEM_OK) {
+    c->have_mesh = false;
+    return s;
+  }
+  return resolve(c);
+}
+
+cfdem_status cfdem_set_params(cfdem_t c, const cfdem_params* p) {
+  if (!c || !p) return fail(c, CFDEM_EINVAL, "null argument");
+  if (!(p->rho_f > 0) || !(p->mu_f > 0) || !is_finite_d(p->g[0]) || !is_finite_d(p->g[1]) ||
+      !is_finite_d(p->g[2]))
+    return fail(c, CFDEM_EINVAL, "rho_f, mu_f must be > 0 and g finite");
+  if (p->scheme < 0 || p->scheme > 1) return fail(c, CFDEM_EINVAL, "scheme must be 0 or 1");
+  if (p->drag_model < 0 || p->drag_model > 1)
+    return fail(c, CFDEM_EINVAL, "drag_model must be 0 (Di Felice) or 1 (Dallavalle)");
+  if (p->vans_model < 0 || p->vans_model > 1) return fail(c, CFDEM_EINVAL, "vans_model 0|1");
+  if (p->precision < 0 || p->precision > 1) return fail(c, CFDEM_EINVAL, "precision 0|1");
+  if (!(p->qcm_radius >= 0) || !(p->l2_smoothing >= 0) || !(p->cg_rtol > 0) ||
+      p->cg_maxit < 1 || !(p->eps_floor > 0 && p->eps_floor <= 1) || !(p->max_radius >= 0) ||
+      !(p->bin_edge >= 0))
+    return fail(c, CFDEM_EINVAL, "numerical parameter out of range");
+  if (p->pressure_degree < 0 || p->pressure_degree > 3)
+    return fail(c, CFDEM_EINVAL, "pressure_degree must be 0..3");
+  c->prm = *p;
+  return resolve(c);
+}
+
+cfdem_status cfdem_get_params(cfdem_t c, cfdem_params* p) {
+  if (!c || !p) return CFDEM_EINVAL;
+  *p = c->prm;
+  if (c->have_mesh) {
+    p->qcm_radius = c->R;
+    p->pressure_degree = c->mesh.kp;
+    p->bin_edge = c->bins.be[0];
+  }
+  return CFDEM_OK;
+}
+
+cfdem_status cfdem_locate(cfdem_t c, int64_t n, const double* x, int32_t* elem, double* xi) {
+  cfdem_status s = need_mesh(c);
+  if (s != CFDEM_OK) return s;
+  if (n < 0 || (n > 0 && !x)) return fail(c, CFDEM_EINVAL, "bad particle arrays");
+  DeviceGuard g(c->device);
+  CK(launch_locate(c->mesh, n, x, elem, xi, c->st, c->stream), "locate");
+  return CFDEM_OK;
+}
+
+cfdem_status cfdem_bin(cfdem_t c, int64_t n, const double* x, int32_t* bin_start,
+                       int32_t* perm) {
+  cfdem_status s = need_mesh(c);
+  if (s != CFDEM_OK) return s;
+  if (n < 0 || n >= ((int64_t)1 << 31) || (n > 0 && !x))
+    return fail(c, CFDEM_EINVAL, "bad particle arrays");
+  DeviceGuard g(c->device);
+  s = do_bin(c, n, x, nullptr);  // radii are not needed for the sort itself
+  if (s != CFDEM_OK) return s;
+  if (bin_start)
+    CK(cudaMemcpyAsync(bin_start, c->bin_start, sizeof(int32_t) * (c->bins.nbins + 1),
+                       cudaMemcpyDeviceToDevice, c->stream),
+       "bin copy");
+  if (perm && n > 0)
+    CK(cudaMemcpyAsync(perm, c->perm, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, c->stream),
+       "bin copy");
+  return CFDEM_OK;
+}
+
+cfdem_status cfdem_void_fraction(cfdem_t c, int64_t n, const double* x, const double* r,
+                                 double* eps_q, int32_t* nb_count, int64_t* nb_idsum) {
+  cfdem_status s = need_mesh(c);
+  if (s != CFDEM_OK) return s;
+  if (n < 0 || n >= ((int64_t)1 << 31) || (n > 0 && (!x || !r)))
+    return fail(c, CFDEM_EINVAL, "bad particle arrays");
+  DeviceGuard g(c->device);
+  const MeshDev& m = c->mesh;
+  bool mixed = c->prm.precision == 1;
+  double* out64 = eps_q ? eps_q : (mixed ? nullptr : c->eps64);
+  float* out32 = mixed ? c->eps32 : nullptr;
+  if (c->prm.scheme == 1) {
+    c->timer.begin(kStageVoid, c->stream);
+    CK(launch_pcm(m, n, x, r, c->vol, out64, out32, c->st, c->stream), "pcm");
+    c->timer.end(kStageVoid, c->stream);
+    if (nb_count) CK(cudaMemsetAsync(nb_count, 0, sizeof(int32_t) * m.E * m.Q, c->stream), "pcm");
+    if (nb_idsum) CK(cudaMemsetAsync(nb_idsum, 0, sizeof(int64_t) * m.E * m.Q, c->stream), "pcm");
+  } else {
+    s = do_bin(c, n, x, r);
+    if (s != CFDEM_OK) return s;
+    c->timer.begin(kStageVoid, c->stream);
+    CK(launch_qcm(m, c->tab, c->bins, mixed ? 1 : 0, c->R, c->bin_start, c->perm, c->xs64,
+                  c->xs32, c->st, out64, out32, nb_count, nb_idsum, c->stream),
+       "qcm");
+    c->timer.end(kStageVoid, c->stream);
+  }
+  if (mixed) {
+    c->eps_state = 2;
+  } else {
+    if (out64 != c->eps64)
+      CK(cudaMemcpyAsync(c->eps64, out64, sizeof(double) * m.E * m.Q, cudaMemcpyDeviceToDevice,
+                         c->stream),
+         "eps copy");
+    c->eps_state = 1;
+  }
+  return CFDEM_OK;
+}
+
+cfdem_status cfdem_project_rhs(cfdem_t c, const double* eps_q, double* b) {
+  cfdem_status s = need_mesh(c);
+  if (s != CFDEM_OK) return s;
+  if (!b) return fail(c, CFDEM_EINVAL, "b is NULL");
+  DeviceGuard g(c->device);
+  if (!eps_q && c->eps_state == 0) return fail(c, CFDEM_ESTATE, "no void fraction computed yet");
+  c->timer.begin(kStageRhs, c->stream);
+  if (eps_q) {
+    CK(launch_rhs(c->mesh, c->tab, eps_q, nullptr, b, c->stream), "rhs");
+  } else {
+    CK(launch_rhs(c->mesh, c->tab, c->eps64, c->eps_state == 2 ? c->eps32 : nullptr, b,
+                  c->stream),
+       "rhs");
+  }
+  c->timer.end(kStageRhs, c->stream);
+  return CFDEM_OK;
+}
+
+cfdem_status cfdem_apply(cfdem_t c, const double* x, double* y) {
+  cfdem_status s = need_mesh(c);
+  if (s != CFDEM_OK) return s;
+  if (!x || !y) return fail(c, CFDEM_EINVAL, "null vector");
+  DeviceGuard g(c->device);
+  CK(launch_apply64(c->mesh, c->bands64, c->coef, x, y, c->stream), "apply");
+  return CFDEM_OK;
+}
+
+cfdem_status cfdem_project(cfdem_t c, const double* eps_q, double* eps_nodal) {
+  cfdem_status s = need_mesh(c);
+  if (s != CFDEM_OK) return s;
+  if (!eps_nodal) return fail(c, CFDEM_EINVAL, "eps_nodal is NULL");
+  s = cfdem_project_rhs(c, eps_q, c->b);
+  if (s != CFDEM_OK) return s;
+  DeviceGuard g(c->device);
+  int it = 0, outer = 0, conv = 0;
+  double rel = 0.0;
+  cudaError_t e;
+  c->cg.timer = c->timer.on ? &c->timer : nullptr;
+  c->timer.begin(kStageSolve, c->stream);
+  if (c->prm.precision == 1)
+    e = run_cg_mixed(c->mesh, c->bands64, c->bands32, c->coef, c->b, eps_nodal,
+                     c->prm.cg_rtol, c->prm.cg_maxit, c->cg, c->stream, &it, &outer, &rel, &conv);
+  else
+    e = run_cg64(c->mesh, c->bands64, c->coef, c->b, eps_nodal, c->prm.cg_rtol,
+                 c->prm.cg_maxit, c->cg, c->stream, &it, &rel, &conv);
+  if (e != cudaSuccess) return cuda_fail(c, e, "project");
+  c->timer.end(kStageSolve, c->stream);
+  c->last_iters = it;
+  c->last_outer = outer;
+  c->last_relres = rel;
+  c->last_converged = conv;
+  if (!conv) c->pending_not_converged = 1;
+  return CFDEM_OK;
+}
+
+cfdem_status cfdem_forces(cfdem_t c, int64_t n, const double* x, const double* r,
+                          const double* u_p, const double* u_nodal, const double* p_nodal,
+                          const double* eps_nodal, double* f, double* f_drag, double* F_elem,
+                          double* F_q) {
+  cfdem_status s = need_mesh(c);
+  if (s != CFDEM_OK) return s;
+  if (n < 0 || (n > 0 && (!x || !r || !u_p || !f)) || !u_nodal || !p_nodal || !eps_nodal)
+    return fail(c, CFDEM_EINVAL, "null input");
+  DeviceGuard g(c->device);
+  const MeshDev& m = c->mesh;
+  bool want_src = F_elem || F_q;
+  if (want_src) CK(cudaMemsetAsync(c->S, 0, sizeof(double) * 3 * m.E, c->stream), "forces");
+  c->timer.begin(kStageForces, c->stream);
+  CK(launch_forces(m, c->tab, c->prm.precision, c->prm.rho_f, c->prm.mu_f, c->prm.g,
+                   c->prm.drag_model, c->prm.beta_over_eps, c->prm.eps_floor,
+                   c->prm.vans_model, n, x, r, u_p, u_nodal, p_nodal, eps_nodal, f, f_drag,
+                   want_src ? c->S : nullptr, c->st, c->stream),
+     "forces");
+  c->timer.end(kStageForces, c->stream);
+  if (want_src) {
+    c->timer.begin(kStageSource, c->stream);
+    CK(launch_fluid_source(m, c->S, F_elem, F_q, c->stream), "fluid source");
+    c->timer.end(kStageSource, c->stream);
+  }
+  return CFDEM_OK;
+}
+
+cfdem_status cfdem_coupling_step(cfdem_t c, int64_t n, const double* x, const double* r,
+                                 const double* u_p, const double* u_nodal,
+                                 const double* p_nodal, double* eps_nodal, double* f,
+                                 double* f_drag, double* F_elem, double* F_q) {
+  cfdem_status s = cfdem_void_fraction(c, n, x, r, nullptr, nullptr, nullptr);
+  if (s != CFDEM_OK) return s;
+  s = cfdem_project(c, nullptr, eps_nodal);
+  if (s != CFDEM_OK) return s;
+  return cfdem_forces(c, n, x, r, u_p, u_nodal, p_nodal, eps_nodal, f, f_drag, F_elem, F_q);
+}
+
+cfdem_status cfdem_synchronize(cfdem_t c) {
+  if (!c) return CFDEM_EINVAL;
+  DeviceGuard g(c->device);
+  cudaError_t e = c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(c, e, "synchronize");
+  DevStatus h;
+  CK(cudaMemcpy(&h, c->st, sizeof h, cudaMemcpyDeviceToHost), "status");
+  cfdem_status s = CFDEM_OK;
+  if (h.first_bad != ~0ull) {
+    s = fail(c, CFDEM_OUT_OF_DOMAIN, "particle %llu lies outside the mesh", h.first_bad);
+    unsigned long long reset = ~0ull;
+    CK(cudaMemcpy(&c->st->first_bad, &reset, sizeof reset, cudaMemcpyHostToDevice), "status");
+  } else if (c->pending_not_converged) {
+    s = fail(c, CFDEM_NOT_CONVERGED, "CG stopped at %d iterations, relative residual %.3e",
+             c->last_iters, c->last_relres);
+  }
+  c->pending_not_converged = 0;
+  return s;
+}
+
+cfdem_status cfdem_get_stats(cfdem_t c, cfdem_stats* out) {
+  if (!c || !out) return CFDEM_EINVAL;
+  std::memset(out, 0, sizeof *out);
+  DeviceGuard g(c->device);
+  cudaError_t e = c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(c, e, "get_stats");
+  DevStatus h;
+  CK(cudaMemcpy(&h, c->st, sizeof h, cudaMemcpyDeviceToHost), "status");
+  out->first_bad_particle = h.first_bad == ~0ull ? -1 : (int64_t)h.first_bad;
+  out->cg_iterations = c->last_iters;
+  out->cg_outer = c->last_outer;
+  out->cg_relres = c->last_relres;
+  out->converged = c->last_converged;
+  for (int a = 0; a < 3; ++a) {
+    out->nb[a] = c->bins.nb[a];
+    out->bin_edge[a] = c->bins.be[a];
+  }
+  out->qcm_radius = c->R;
+  out->n_elem = c->mesh.E;
+  out->n_qp = c->mesh.E * c->mesh.Q;
+  out->n_nodes = c->mesh.n_nodes;
+  out->n_pnodes = c->mesh.n_pnodes;
+  c->timer.collect();
+  for (int s = 0; s < kStages && s < 8; ++s) {
+    out->stage_ms[s] = c->timer.ms[s];
+    out->stage_calls[s] = c->timer.calls[s];
+  }
+  out->timer_overflow = c->timer.overflow ? 1 : 0;
+  out->kernel_launches = launches_total() - c->launches_at_reset;
+  return CFDEM_OK;
+}
+
+cfdem_status cfdem_set_timing(cfdem_t c, int enable) {
+  if (!c) return CFDEM_EINVAL;
+  DeviceGuard g(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  c->timer.collect();
+  for (int s = 0; s < kStages; ++s) {
+    c->timer.ms[s] = 0.0;
+    c->timer.calls[s] = 0;
+  }
+  c->timer.overflow = false;
+  c->timer.on = enable != 0;
+  c->launches_at_reset = launches_total();
+  return CFDEM_OK;
+}
+
+const char* cfdem_last_error(cfdem_t c) { return c ? c->err.c_str() : "null context"; }
+
+}  // extern "C"

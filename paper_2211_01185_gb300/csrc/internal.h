@@ -1,0 +1,162 @@
+// internal.h -- declarations shared by the CUDA translation units of the
+// coupling library.  Nothing here is part of the public C ABI (cfdem.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cfdem {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// One sorted particle in FP64: position and radius (32-byte aligned).
+struct __align__(32) P4 {
+  double x, y, z, w;
+};
+
+// Mesh geometry as the kernels see it.  Axis-aligned box of equal hexahedra.
+struct MeshDev {
+  double x0[3];      // origin
+  double L[3];       // extent
+  double h[3];       // element size, L / ne (IEEE division, as the oracle)
+  int ne[3];         // elements per axis
+  int k;             // Q_k degree of velocity / void fraction
+  int kp;            // Q_kp degree of pressure
+  int nq;            // Gauss points per axis (k + 1)
+  int Q;             // nq^3
+  int nn[3];         // Q_k nodes per axis (ne k + 1)
+  int np[3];         // Q_kp nodes per axis (ne kp + 1)
+  int64_t E;         // elements
+  int64_t n_nodes;   // Q_k nodes
+  int64_t n_pnodes;  // Q_kp nodes
+  double Ve;         // element volume hx hy hz
+};
+
+// 1D reference tables on [0,1] (degree <= 3).  Built on the host from
+// closed forms (Gauss-Legendre points, GLL nodes) and exact quadrature.
+struct Tables {
+  double g[4], w[4];        // Gauss points and weights, nq = k + 1 of them
+  double z[4];              // GLL nodes of degree k
+  double zp[4];             // GLL nodes of degree kp
+  double lw[4], lwp[4];     // 1 / prod_{b != a} (z_a - z_b) for z and zp
+  double Bw[4][4];          // Bw[a][q] = l_a(g_q) w_q  (k basis, Gauss weight folded in)
+  double Mh[4][4];          // reference mass     int_0^1 l_a l_b
+  double Kh[4][4];          // reference stiffness int_0^1 l_a' l_b'
+};
+
+// Bin grid over the box.
+struct BinDev {
+  int nb[3];
+  double be[3];      // bin edge per axis, L / nb
+  int64_t nbins;
+};
+
+// Device-side status words of one context (one allocation).
+struct DevStatus {
+  unsigned long long first_bad;   // lowest out-of-domain particle index, or ~0ull
+  unsigned long long rmax_bits;   // bits of max radius (non-negative double)
+  int not_converged;
+  int pad;
+};
+
+// Scalars of the CG solver kept on the device.
+struct CgScalars {
+  double rz;        // r . z (current)
+  double pAp;
+  double alpha, beta;
+  double rr;        // r . r
+  double bb;        // b . b
+  double tol2;      // (rtol)^2 * bb
+  int it;           // iterations done
+  int done;         // 1 once converged (kernels then return at once)
+  unsigned int ticket;  // last-block counter
+  int pad;
+};
+
+// Optional per-stage CUDA-event timers of a context (off by default).  A
+// stage is a group of launches on the context's stream; begin/end record an
+// event pair, collect() (after a synchronize) adds up the elapsed times.
+enum Stage {
+  kStageBin = 0,      // a1-a2 locate + counting sort + sorted copies
+  kStageVoid = 1,     // a3 void-fraction kernel (QCM or PCM)
+  kStageRhs = 2,      // a4 projection right-hand side
+  kStageSolve = 3,    // a5 whole solve
+  kStageForces = 4,   // a6 forces kernel
+  kStageSource = 5,   // a7 fluid source
+  kStageOp32 = 6,     // operator launches of the FP32 CG (one per iteration)
+  kStageOp64 = 7,     // operator launches in FP64 (FP64 CG or refinement residuals)
+  kStages = 8
+};
+
+struct Timer {
+  static constexpr int kCap = 4096;
+  bool on = false;
+  cudaEvent_t* ev[kStages] = {};  // 2 * kCap events per stage, created on first use
+  int count[kStages] = {};
+  long long calls[kStages] = {};
+  double ms[kStages] = {};
+  bool overflow = false;
+  void begin(int s, cudaStream_t st);
+  void end(int s, cudaStream_t st);
+  void collect();
+  void release();
+};
+
+// process-wide count of kernel launches made by the library
+void count_launches(int n);
+long long launches_total();
+
+// ---------------------------------------------------------------- launchers
+// particles.cu
+cudaError_t launch_locate(const MeshDev& m, int64_t n, const double* x, int32_t* elem,
+                          double* xi, DevStatus* st, cudaStream_t s);
+cudaError_t launch_bin(const MeshDev& m, const BinDev& b, int64_t n, const double* x,
+                       const double* r, int32_t* bin_of, int32_t* slot, int32_t* bin_count,
+                       int32_t* bin_start, int32_t* perm, int32_t* scan_tmp, double* xs64,
+                       float* xs32, DevStatus* st, cudaStream_t s);
+cudaError_t launch_forces(const MeshDev& m, const Tables& t, int precision, double rho,
+                          double mu, const double g[3], int drag_model, int beta_over_eps,
+                          double eps_floor, int vans_model, int64_t n, const double* x,
+                          const double* r, const double* u_p, const double* u_nodal,
+                          const double* p_nodal, const double* eps_nodal, double* f,
+                          double* f_drag, double* S_elem, DevStatus* st, cudaStream_t s);
+cudaError_t launch_fluid_source(const MeshDev& m, const double* S_elem, double* F_elem,
+                                double* F_q, cudaStream_t s);
+
+// voidfrac.cu
+cudaError_t launch_qcm(const MeshDev& m, const Tables& t, const BinDev& b, int precision,
+                       double R, const int32_t* bin_start, const int32_t* perm,
+                       const double* xs64, const float* xs32, const DevStatus* st,
+                       double* eps_q64, float* eps_q32, int32_t* nb_count, int64_t* nb_idsum,
+                       cudaStream_t s);
+cudaError_t launch_pcm(const MeshDev& m, int64_t n, const double* x, const double* r,
+                       double* vol_elem, double* eps_q64, float* eps_q32, DevStatus* st,
+                       cudaStream_t s);
+
+// projection.cu
+cudaError_t launch_rhs(const MeshDev& m, const Tables& t, const double* eps_q64,
+                       const float* eps_q32, double* b, cudaStream_t s);
+cudaError_t upload_bands(const MeshDev& m, const Tables& t, double L2, double** bands64,
+                         float** bands32);
+cudaError_t launch_apply64(const MeshDev& m, const double* bands, const double* coef,
+                           const double* x, double* y, cudaStream_t s);
+struct CgWork {
+  // FP64 vectors
+  double *r, *z, *p0, *p1, *Ap, *dinv, *xcor;
+  // FP32 vectors (mixed inner solve)
+  float *r32, *z32, *q0, *q1, *Aq, *dinv32, *d32;
+  double* partials;   // per-block partial sums
+  CgScalars* sc;      // device scalars
+  int nblocks;
+  Timer* timer;       // may be null
+};
+int cg_blocks(const MeshDev& m);
+cudaError_t run_cg64(const MeshDev& m, const double* bands, const double* coef,
+                     const double* b, double* x, double rtol, int maxit, CgWork& w,
+                     cudaStream_t s, int* iters_host, double* relres_host, int* converged);
+cudaError_t run_cg_mixed(const MeshDev& m, const double* bands64, const float* bands32,
+                         const double* coef, const double* b, double* x, double rtol,
+                         int maxit, CgWork& w, cudaStream_t s, int* iters_host,
+                         int* outer_host, double* relres_host, int* converged);
+
+}  // namespace cfdem

@@ -1,0 +1,565 @@
+// particles.cu -- per-particle kernels of the coupling step:
+//   a1 element location (Sec. 2.3: particles are located on the fluid mesh),
+//   a2 stable counting sort into bins and the sorted particle copies,
+//   a6 particle-fluid forces (Sec. 2.3.2), a7 fluid source (Eqs. fb, fa).
+#include <cfloat>
+#include <cstdint>
+
+#include "internal.h"
+
+namespace cfdem {
+
+// ----------------------------------------------------------------------------
+// exact location arithmetic (no contraction into FMA: same rounding as the
+// plain IEEE definition)
+
+__device__ __forceinline__ bool in_box(double x, double x0, double L) {
+  double slack = __dmul_rn(1e-12, L);
+  double lo = __dsub_rn(x0, slack);
+  double hi = __dadd_rn(__dadd_rn(x0, L), slack);
+  return x >= lo && x <= hi;  // false for NaN
+}
+
+// element index along one axis and the reference coordinate; caller checked
+// in_box so t is finite
+__device__ __forceinline__ int elem_axis(double x, double x0, double h, int N, double* xi) {
+  double t = __ddiv_rn(__dsub_rn(x, x0), h);
+  double f = floor(t);
+  int i = (int)f;
+  i = i < 0 ? 0 : (i > N - 1 ? N - 1 : i);
+  *xi = __dsub_rn(t, (double)i);
+  return i;
+}
+
+__device__ __forceinline__ int bin_axis(double x, double x0, double be, int nb) {
+  double t = __ddiv_rn(__dsub_rn(x, x0), be);
+  double f = floor(t);
+  if (!(f >= 0.0)) return 0;
+  if (f > (double)(nb - 1)) return nb - 1;
+  return (int)f;
+}
+
+__device__ __forceinline__ void report_bad(DevStatus* st, int64_t i) {
+  atomicMin(&st->first_bad, (unsigned long long)i);
+}
+
+// ----------------------------------------------------------------------------
+// a1: locate
+
+__global__ void k_locate(MeshDev m, int64_t n, const double* __restrict__ x,
+                         int32_t* __restrict__ elem, double* __restrict__ xi,
+                         DevStatus* st) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double p[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+  bool ok = in_box(p[0], m.x0[0], m.L[0]) && in_box(p[1], m.x0[1], m.L[1]) &&
+            in_box(p[2], m.x0[2], m.L[2]);
+  if (!ok) {
+    report_bad(st, i);
+    if (elem) elem[i] = -1;
+    if (xi) xi[3 * i] = xi[3 * i + 1] = xi[3 * i + 2] = 0.0;
+    return;
+  }
+  double t[3];
+  int ie[3];
+  for (int a = 0; a < 3; ++a) ie[a] = elem_axis(p[a], m.x0[a], m.h[a], m.ne[a], &t[a]);
+  if (elem) elem[i] = ie[0] + m.ne[0] * (ie[1] + m.ne[1] * ie[2]);
+  if (xi) {
+    xi[3 * i] = t[0];
+    xi[3 * i + 1] = t[1];
+    xi[3 * i + 2] = t[2];
+  }
+}
+
+cudaError_t launch_locate(const MeshDev& m, int64_t n, const double* x, int32_t* elem,
+                          double* xi, DevStatus* st, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int bs = 256;
+  k_locate<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(m, n, x, elem, xi, st);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// a2: counting sort into bins
+
+__global__ void k_bin_count(MeshDev m, BinDev b, int64_t n, const double* __restrict__ x,
+                           const double* __restrict__ r, int32_t* __restrict__ bin_of,
+                           int32_t* __restrict__ slot, int32_t* __restrict__ count,
+                           DevStatus* st) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double p[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+  if (!(in_box(p[0], m.x0[0], m.L[0]) && in_box(p[1], m.x0[1], m.L[1]) &&
+        in_box(p[2], m.x0[2], m.L[2])))
+    report_bad(st, i);
+  int bx = bin_axis(p[0], m.x0[0], b.be[0], b.nb[0]);
+  int by = bin_axis(p[1], m.x0[1], b.be[1], b.nb[1]);
+  int bz = bin_axis(p[2], m.x0[2], b.be[2], b.nb[2]);
+  int32_t id = bx + b.nb[0] * (by + b.nb[1] * bz);
+  bin_of[i] = id;
+  slot[i] = atomicAdd(&count[id], 1);
+  if (r) {
+    double ri = r[i];
+    if (ri >= 0.0) atomicMax(&st->rmax_bits, (unsigned long long)__double_as_longlong(ri));
+  }
+}
+
+// exclusive scan of count[0..nb) into start[0..nb], start[nb] = total.
+// Three passes: per-tile sums, scan of the tile sums, per-tile scan.
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int32_t block_excl_scan(int32_t v, int32_t* sh, int32_t* total) {
+  // sh: kScanThreads / 32 words
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) sh[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    int32_t w = lane < kScanThreads / 32 ? sh[lane] : 0;
+    int32_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    if (lane < kScanThreads / 32) sh[lane] = wi - w;
+    if (lane == kScanThreads / 32 - 1) sh[kScanThreads / 32] = wi;
+  }
+  __syncthreads();
+  int32_t res = sh[warp] + inc - v;
+  *total = sh[kScanThreads / 32];
+  __syncthreads();
+  return res;
+}
+
+__global__ void k_scan_tiles(const int32_t* __restrict__ in, int64_t nb,
+                             int32_t* __restrict__ tile_sum) {
+  __shared__ int32_t sh[kScanThreads / 32 + 1];
+  int64_t base = blockIdx.x * (int64_t)kScanTile;
+  int32_t s = 0;
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    int64_t idx = base + j * kScanThreads + threadIdx.x;
+    if (idx < nb) s += in[idx];
+  }
+  int32_t total;
+  block_excl_scan(s, sh, &total);
+  if (threadIdx.x == 0) tile_sum[blockIdx.x] = total;
+}
+
+__global__ void k_scan_sums(int32_t* __restrict__ tile_sum, int ntiles) {
+  __shared__ int32_t sh[kScanThreads / 32 + 1];
+  int32_t carry = 0;
+  for (int base = 0; base < ntiles; base += kScanThreads) {
+    int idx = base + threadIdx.x;
+    int32_t v = idx < ntiles ? tile_sum[idx] : 0;
+    int32_t total;
+    int32_t ex = block_excl_scan(v, sh, &total);
+    if (idx < ntiles) tile_sum[idx] = ex + carry;
+    carry += total;
+  }
+}
+
+__global__ void k_scan_final(const int32_t* __restrict__ in, int64_t nb,
+                             const int32_t* __restrict__ tile_off, int32_t* __restrict__ out) {
+  __shared__ int32_t sh[kScanThreads / 32 + 1];
+  int64_t base = blockIdx.x * (int64_t)kScanTile + threadIdx.x * (int64_t)kScanItems;
+  int32_t v[kScanItems];
+  int32_t s = 0;
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    int64_t idx = base + j;
+    v[j] = idx < nb ? in[idx] : 0;
+    s += v[j];
+  }
+  int32_t total;
+  int32_t ex = block_excl_scan(s, sh, &total) + tile_off[blockIdx.x];
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    int64_t idx = base + j;
+    if (idx < nb) out[idx] = ex;
+    ex += v[j];
+    if (idx == nb - 1) out[nb] = ex;
+  }
+}
+
+__global__ void k_scatter(int64_t n, const int32_t* __restrict__ bin_of,
+                          const int32_t* __restrict__ slot, const int32_t* __restrict__ start,
+                          int32_t* __restrict__ perm) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  perm[start[bin_of[i]] + slot[i]] = (int32_t)i;
+}
+
+// restore ascending particle id inside every bin (the atomic slots above
+// arrive in any order): insertion sort of each bin's segment
+__global__ void k_sort_bins(int64_t nbins, const int32_t* __restrict__ start,
+                            int32_t* __restrict__ perm) {
+  int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b >= nbins) return;
+  int32_t s0 = start[b], s1 = start[b + 1];
+  for (int32_t i = s0 + 1; i < s1; ++i) {
+    int32_t v = perm[i];
+    int32_t j = i - 1;
+    while (j >= s0 && perm[j] > v) {
+      perm[j + 1] = perm[j];
+      --j;
+    }
+    perm[j + 1] = v;
+  }
+}
+
+// sorted copies: xs64[s] = (x, y, z, r); xs32[s] = float-float split of the
+// position relative to the mesh origin, hi part in [0..2], radius in [3],
+// lo part in [4..6]
+__global__ void k_gather_sorted(MeshDev m, int64_t n, const int32_t* __restrict__ perm,
+                                const double* __restrict__ x, const double* __restrict__ r,
+                                double* __restrict__ xs64, float* __restrict__ xs32) {
+  int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  int64_t i = perm[s];
+  double p[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+  double ri = r ? r[i] : 0.0;
+  P4 d;
+  d.x = p[0];
+  d.y = p[1];
+  d.z = p[2];
+  d.w = ri;
+  reinterpret_cast<P4*>(xs64)[s] = d;
+  float hi[3], lo[3];
+  for (int a = 0; a < 3; ++a) {
+    double rel = p[a] - m.x0[a];
+    hi[a] = (float)rel;
+    lo[a] = (float)(rel - (double)hi[a]);
+  }
+  float4* o = reinterpret_cast<float4*>(xs32) + 2 * s;
+  o[0] = make_float4(hi[0], hi[1], hi[2], (float)ri);
+  o[1] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+}
+
+cudaError_t launch_bin(const MeshDev& m, const BinDev& b, int64_t n, const double* x,
+                       const double* r, int32_t* bin_of, int32_t* slot, int32_t* bin_count,
+                       int32_t* bin_start, int32_t* perm, int32_t* scan_tmp, double* xs64,
+                       float* xs32, DevStatus* st, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(bin_count, 0, sizeof(int32_t) * b.nbins, s);
+  if (e != cudaSuccess) return e;
+  int bs = 256;
+  unsigned gp = (unsigned)((n + bs - 1) / bs);
+  if (n > 0) k_bin_count<<<gp, bs, 0, s>>>(m, b, n, x, r, bin_of, slot, bin_count, st);
+  int ntiles = (int)((b.nbins + kScanTile - 1) / kScanTile);
+  k_scan_tiles<<<ntiles, kScanThreads, 0, s>>>(bin_count, b.nbins, scan_tmp);
+  k_scan_sums<<<1, kScanThreads, 0, s>>>(scan_tmp, ntiles);
+  k_scan_final<<<ntiles, kScanThreads, 0, s>>>(bin_count, b.nbins, scan_tmp, bin_start);
+  if (n > 0) {
+    k_scatter<<<gp, bs, 0, s>>>(n, bin_of, slot, bin_start, perm);
+    k_sort_bins<<<(unsigned)((b.nbins + bs - 1) / bs), bs, 0, s>>>(b.nbins, bin_start, perm);
+    k_gather_sorted<<<gp, bs, 0, s>>>(m, n, perm, x, r, xs64, xs32);
+  }
+  count_launches(n > 0 ? 7 : 3);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// a6: forces
+
+template <typename T>
+__device__ __forceinline__ T t_sqrt(T v);
+template <>
+__device__ __forceinline__ double t_sqrt<double>(double v) { return sqrt(v); }
+template <>
+__device__ __forceinline__ float t_sqrt<float>(float v) { return sqrtf(v); }
+
+// Lagrange basis of degree D on nodes z and its derivative at t; lw[a] =
+// 1 / prod_{b != a} (z_a - z_b) comes from the host so that no division is
+// done here
+template <int D, typename T>
+__device__ __forceinline__ void lagrange(const double* zz, const double* lw, T t, T* l, T* dl) {
+  T d[D + 1];
+#pragma unroll
+  for (int a = 0; a <= D; ++a) d[a] = t - (T)zz[a];
+#pragma unroll
+  for (int a = 0; a <= D; ++a) {
+    T v = (T)1, dv = (T)0;
+#pragma unroll
+    for (int b = 0; b <= D; ++b) {
+      if (b == a) continue;
+      dv = dv * d[b] + v;
+      v = v * d[b];
+    }
+    l[a] = v * (T)lw[a];
+    if (dl) dl[a] = dv * (T)lw[a];
+  }
+}
+
+template <typename T>
+struct Closure {
+  static __device__ __forceinline__ T log10_(T v);
+  static __device__ __forceinline__ T exp_(T v);
+  static __device__ __forceinline__ T logn(T v);
+  static __device__ __forceinline__ T tiny();
+};
+template <>
+struct Closure<double> {
+  static __device__ __forceinline__ double log10_(double v) { return log10(v); }
+  static __device__ __forceinline__ double exp_(double v) { return exp(v); }
+  static __device__ __forceinline__ double logn(double v) { return log(v); }
+  static __device__ __forceinline__ double tiny() { return 1e-300; }
+};
+template <>
+struct Closure<float> {
+  static __device__ __forceinline__ float log10_(float v) { return log10f(v); }
+  static __device__ __forceinline__ float exp_(float v) { return expf(v); }
+  static __device__ __forceinline__ float logn(float v) { return logf(v); }
+  static __device__ __forceinline__ float tiny() { return 1e-37f; }
+};
+
+struct ForceParams {
+  double rho, mu, g[3], eps_floor;
+  int drag_model, beta_over_eps, vans_model;
+};
+
+template <int K, int KP, typename T>
+__global__ void __launch_bounds__(128)
+k_forces(MeshDev m, Tables tb, ForceParams fp, int64_t n, const double* __restrict__ x,
+         const double* __restrict__ r, const double* __restrict__ u_p,
+         const double* __restrict__ u_nodal, const double* __restrict__ p_nodal,
+         const double* __restrict__ eps_nodal, double* __restrict__ f,
+         double* __restrict__ f_drag, double* __restrict__ S_elem, DevStatus* st) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double p[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+  if (!(in_box(p[0], m.x0[0], m.L[0]) && in_box(p[1], m.x0[1], m.L[1]) &&
+        in_box(p[2], m.x0[2], m.L[2]))) {
+    report_bad(st, i);
+    for (int a = 0; a < 3; ++a) {
+      f[3 * i + a] = 0.0;
+      if (f_drag) f_drag[3 * i + a] = 0.0;
+    }
+    return;
+  }
+  int ie[3];
+  double xid[3];
+  for (int a = 0; a < 3; ++a) ie[a] = elem_axis(p[a], m.x0[a], m.h[a], m.ne[a], &xid[a]);
+  T xi[3] = {(T)xid[0], (T)xid[1], (T)xid[2]};
+
+  // u_f and eps at the particle: Q_k interpolation
+  T lx[K + 1], ly[K + 1], lz[K + 1];
+  lagrange<K, T>(tb.z, tb.lw, xi[0], lx, (T*)nullptr);
+  lagrange<K, T>(tb.z, tb.lw, xi[1], ly, (T*)nullptr);
+  lagrange<K, T>(tb.z, tb.lw, xi[2], lz, (T*)nullptr);
+  T uf0 = 0, uf1 = 0, uf2 = 0, eps = 0;
+  int64_t nx = m.nn[0], nxy = (int64_t)m.nn[0] * m.nn[1];
+  int64_t base = (int64_t)ie[0] * K + nx * ((int64_t)ie[1] * K) + nxy * ((int64_t)ie[2] * K);
+#pragma unroll
+  for (int c = 0; c <= K; ++c) {
+#pragma unroll
+    for (int b = 0; b <= K; ++b) {
+      T lyz = ly[b] * lz[c];
+#pragma unroll
+      for (int a = 0; a <= K; ++a) {
+        T phi = lx[a] * lyz;
+        int64_t nd = base + a + nx * b + nxy * c;
+        uf0 += phi * (T)__ldg(u_nodal + 3 * nd);
+        uf1 += phi * (T)__ldg(u_nodal + 3 * nd + 1);
+        uf2 += phi * (T)__ldg(u_nodal + 3 * nd + 2);
+        eps += phi * (T)__ldg(eps_nodal + nd);
+      }
+    }
+  }
+  // grad p at the particle: Q_kp.  Each derivative is taken from nodal
+  // differences along its own axis, formed in FP64 (d/dx uses p_abc - p_0bc,
+  // and so on): the shape-function derivatives sum to zero only up to
+  // rounding in FP32, so a large pressure varying along one axis would
+  // otherwise leak into the other two components of the gradient
+  T px[KP + 1], py[KP + 1], pz[KP + 1], dpx[KP + 1], dpy[KP + 1], dpz[KP + 1];
+  lagrange<KP, T>(tb.zp, tb.lwp, xi[0], px, dpx);
+  lagrange<KP, T>(tb.zp, tb.lwp, xi[1], py, dpy);
+  lagrange<KP, T>(tb.zp, tb.lwp, xi[2], pz, dpz);
+  int64_t pnx = m.np[0], pnxy = (int64_t)m.np[0] * m.np[1];
+  int64_t pbase =
+      (int64_t)ie[0] * KP + pnx * ((int64_t)ie[1] * KP) + pnxy * ((int64_t)ie[2] * KP);
+  double pv[KP + 1][KP + 1][KP + 1];
+#pragma unroll
+  for (int c = 0; c <= KP; ++c)
+#pragma unroll
+    for (int b = 0; b <= KP; ++b)
+#pragma unroll
+      for (int a = 0; a <= KP; ++a) pv[c][b][a] = __ldg(p_nodal + pbase + a + pnx * b + pnxy * c);
+  T gp0 = 0, gp1 = 0, gp2 = 0;
+#pragma unroll
+  for (int c = 0; c <= KP; ++c) {
+#pragma unroll
+    for (int b = 0; b <= KP; ++b) {
+#pragma unroll
+      for (int a = 0; a <= KP; ++a) {
+        gp0 += dpx[a] * py[b] * pz[c] * (T)(pv[c][b][a] - pv[c][b][0]);
+        gp1 += px[a] * dpy[b] * pz[c] * (T)(pv[c][b][a] - pv[c][0][a]);
+        gp2 += px[a] * py[b] * dpz[c] * (T)(pv[c][b][a] - pv[0][b][a]);
+      }
+    }
+  }
+  gp0 = gp0 / (T)m.h[0];
+  gp1 = gp1 / (T)m.h[1];
+  gp2 = gp2 / (T)m.h[2];
+
+  // closures
+  T rp = (T)r[i];
+  T U0 = uf0 - (T)u_p[3 * i], U1 = uf1 - (T)u_p[3 * i + 1], U2 = uf2 - (T)u_p[3 * i + 2];
+  T speed = t_sqrt<T>(U0 * U0 + U1 * U1 + U2 * U2);
+  T epsc = eps < (T)fp.eps_floor ? (T)fp.eps_floor : eps;
+  epsc = epsc > (T)1 ? (T)1 : epsc;
+  T fd0 = 0, fd1 = 0, fd2 = 0;
+  if (speed > (T)0) {
+    T rho = (T)fp.rho, mu = (T)fp.mu;
+    T dp = (T)2 * rp;
+    T a = (T)0.63 * t_sqrt<T>(speed) + (T)4.8 * t_sqrt<T>(mu / (rho * epsc * dp));
+    T cds = a * a;
+    if (fp.drag_model == 0) {
+      T Re = rho * epsc * speed * dp / mu;
+      T re = Re > Closure<T>::tiny() ? Re : Closure<T>::tiny();
+      T tt = (T)1.5 - Closure<T>::log10_(re);
+      T chi = (T)3.7 - (T)0.65 * Closure<T>::exp_(-(tt * tt) / (T)2);
+      cds = cds * Closure<T>::exp_(((T)2 - chi) * Closure<T>::logn(epsc));
+    }
+    T coef = (T)0.5 * rho * cds * (T)kPi * rp * rp;
+    if (fp.beta_over_eps) coef = coef / epsc;
+    fd0 = coef * U0;
+    fd1 = coef * U1;
+    fd2 = coef * U2;
+  }
+  T Vp = (T)(4.0 / 3.0 * kPi) * rp * rp * rp;
+  T fg0 = -Vp * gp0, fg1 = -Vp * gp1, fg2 = -Vp * gp2;
+  T rv = (T)fp.rho * Vp;
+  f[3 * i] = (double)(fd0 + (-rv * (T)fp.g[0]) + fg0);
+  f[3 * i + 1] = (double)(fd1 + (-rv * (T)fp.g[1]) + fg1);
+  f[3 * i + 2] = (double)(fd2 + (-rv * (T)fp.g[2]) + fg2);
+  if (f_drag) {
+    f_drag[3 * i] = (double)fd0;
+    f_drag[3 * i + 1] = (double)fd1;
+    f_drag[3 * i + 2] = (double)fd2;
+  }
+  if (S_elem) {
+    int64_t e = ie[0] + (int64_t)m.ne[0] * (ie[1] + (int64_t)m.ne[1] * ie[2]);
+    T s0 = fd0, s1 = fd1, s2 = fd2;
+    if (fp.vans_model == 1) {
+      s0 += fg0;
+      s1 += fg1;
+      s2 += fg2;
+    }
+    atomicAdd(S_elem + 3 * e, (double)s0);
+    atomicAdd(S_elem + 3 * e + 1, (double)s1);
+    atomicAdd(S_elem + 3 * e + 2, (double)s2);
+  }
+}
+
+template <int K, int KP, typename T>
+static void launch_forces_t(const MeshDev& m, const Tables& t, const ForceParams& fp,
+                            int64_t n, const double* x, const double* r, const double* u_p,
+                            const double* u_nodal, const double* p_nodal,
+                            const double* eps_nodal, double* f, double* f_drag, double* S,
+                            DevStatus* st, cudaStream_t s) {
+  int bs = 128;
+  k_forces<K, KP, T><<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(
+      m, t, fp, n, x, r, u_p, u_nodal, p_nodal, eps_nodal, f, f_drag, S, st);
+  count_launches(1);
+}
+
+cudaError_t launch_forces(const MeshDev& m, const Tables& t, int precision, double rho,
+                          double mu, const double g[3], int drag_model, int beta_over_eps,
+                          double eps_floor, int vans_model, int64_t n, const double* x,
+                          const double* r, const double* u_p, const double* u_nodal,
+                          const double* p_nodal, const double* eps_nodal, double* f,
+                          double* f_drag, double* S_elem, DevStatus* st, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  ForceParams fp;
+  fp.rho = rho;
+  fp.mu = mu;
+  fp.g[0] = g[0];
+  fp.g[1] = g[1];
+  fp.g[2] = g[2];
+  fp.eps_floor = eps_floor;
+  fp.drag_model = drag_model;
+  fp.beta_over_eps = beta_over_eps;
+  fp.vans_model = vans_model;
+#define CFDEM_FORCES(K, KP)                                                                  \
+  if (m.k == K && m.kp == KP) {                                                              \
+    if (precision == 0)                                                                      \
+      launch_forces_t<K, KP, double>(m, t, fp, n, x, r, u_p, u_nodal, p_nodal, eps_nodal, f, \
+                                     f_drag, S_elem, st, s);                                 \
+    else                                                                                     \
+      launch_forces_t<K, KP, float>(m, t, fp, n, x, r, u_p, u_nodal, p_nodal, eps_nodal, f,  \
+                                    f_drag, S_elem, st, s);                                  \
+    return cudaGetLastError();                                                               \
+  }
+  CFDEM_FORCES(1, 1)
+  CFDEM_FORCES(2, 1)
+  CFDEM_FORCES(2, 2)
+  CFDEM_FORCES(3, 1)
+  CFDEM_FORCES(3, 2)
+  CFDEM_FORCES(3, 3)
+  CFDEM_FORCES(1, 2)
+  CFDEM_FORCES(1, 3)
+  CFDEM_FORCES(2, 3)
+#undef CFDEM_FORCES
+  return cudaErrorInvalidValue;
+}
+
+// ----------------------------------------------------------------------------
+// a7: fluid source F_e = -S_e / V_e, optionally broadcast to the quadrature
+// points
+
+__global__ void k_fluid_source(int64_t E, int Q, double inv_ve, const double* __restrict__ S,
+                               double* __restrict__ F_e, double* __restrict__ F_q) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  double f0 = -S[3 * e] * inv_ve, f1 = -S[3 * e + 1] * inv_ve, f2 = -S[3 * e + 2] * inv_ve;
+  if (F_e) {
+    F_e[3 * e] = f0;
+    F_e[3 * e + 1] = f1;
+    F_e[3 * e + 2] = f2;
+  }
+  if (F_q) {
+    double* o = F_q + 3 * e * (int64_t)Q;
+    for (int q = 0; q < Q; ++q) {
+      o[3 * q] = f0;
+      o[3 * q + 1] = f1;
+      o[3 * q + 2] = f2;
+    }
+  }
+}
+
+// wide broadcast for F_q: one thread per (element, quadrature point)
+__global__ void k_fluid_source_q(int64_t E, int Q, double inv_ve, const double* __restrict__ S,
+                                 double* __restrict__ F_q) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= E * Q * 3) return;
+  int64_t e = t / (3 * (int64_t)Q);
+  int c = (int)(t % 3);
+  F_q[t] = -S[3 * e + c] * inv_ve;
+}
+
+cudaError_t launch_fluid_source(const MeshDev& m, const double* S_elem, double* F_elem,
+                                double* F_q, cudaStream_t s) {
+  int bs = 256;
+  double inv_ve = 1.0 / m.Ve;
+  if (F_elem)
+    k_fluid_source<<<(unsigned)((m.E + bs - 1) / bs), bs, 0, s>>>(m.E, m.Q, inv_ve, S_elem,
+                                                                  F_elem, nullptr);
+  if (F_q) {
+    int64_t tot = m.E * m.Q * 3;
+    k_fluid_source_q<<<(unsigned)((tot + bs - 1) / bs), bs, 0, s>>>(m.E, m.Q, inv_ve, S_elem,
+                                                                    F_q);
+  }
+  count_launches((F_elem ? 1 : 0) + (F_q ? 1 : 0));
+  return cudaGetLastError();
+}
+
+}  // namespace cfdem

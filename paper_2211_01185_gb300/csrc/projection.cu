@@ -1,0 +1,748 @@
+// projection.cu -- smoothed L2 projection of the void fraction (steps a4, a5).
+//
+// The "void fraction smoothing factor L^2" of the paper's parameter tables is
+// read as the Helmholtz-smoothed L2 projection: find eps_h in Q_k with
+//   int phi_j eps_h + L^2 int grad phi_j . grad eps_h = int phi_j eps_q
+// for every nodal basis function phi_j, i.e. (M + L^2 K) eps_h = b.
+//
+// Matrix-free operator.  On an axis-aligned box of equal elements the
+// assembled operator is the Kronecker sum
+//   A = cM  Mz(x)My(x)Mx + cKx Mz(x)My(x)Kx + cKy Mz(x)Ky(x)Mx + cKz Kz(x)My(x)Mx
+// of assembled 1D reference matrices (bandwidth k) with cM = hx hy hz and
+// cKx = L^2 hy hz / hx etc.  k_apply evaluates it node by node with sum
+// factorisation over a shared-memory tile with a halo of k nodes:
+//   t1 = Mz x, t2 = Kz x          (z pass)
+//   s1 = My t1, s2 = Ky t1, s3 = My t2
+//   U = cM s1 + cKy s2 + cKz s3, V = cKx s1   (y pass)
+//   y = Mx U + Kx V               (x pass)
+// seven banded 1D applies per node, no atomics, deterministic.
+//
+// The right-hand side b_j = sum_e sum_q phi_j(x_q) w_q |J| eps_q is
+// assembled element by element with sum factorisation (three 1D contractions)
+// and atomic adds into the nodes.
+//
+// CG: Jacobi-preconditioned conjugate gradients with the scalars on the
+// device.  Each kernel reduces its block partial sums in fixed order in the
+// last block to finish, so dot products are deterministic, and every kernel
+// returns at once after convergence.  The mixed path runs the same CG in FP32
+// on the correction equation inside FP64 iterative refinement.
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <vector>
+
+#include "internal.h"
+
+namespace cfdem {
+
+// ---------------------------------------------------------------------------
+// right-hand side
+
+template <int K, typename T>
+constexpr int rhs_block() {
+  return ((K + 1) * (K + 1) * (K + 1) * (int)sizeof(T) * 128 <= 40 * 1024) ? 128 : 64;
+}
+
+template <int K, typename T>
+__global__ void __launch_bounds__(128)
+k_rhs(MeshDev m, Tables tb, const T* __restrict__ eps_q, double* __restrict__ b) {
+  constexpr int NQ = K + 1;
+  constexpr int Q = NQ * NQ * NQ;
+  constexpr int NB = (Q * (int)sizeof(T) * 128 <= 40 * 1024) ? 128 : 64;
+  __shared__ T sh[NB * Q];
+  int64_t e0 = blockIdx.x * (int64_t)NB;
+  int64_t tot = m.E - e0 < NB ? (m.E - e0) * Q : (int64_t)NB * Q;
+  for (int64_t t = threadIdx.x; t < tot; t += blockDim.x) sh[t] = eps_q[e0 * Q + t];
+  __syncthreads();
+  int64_t e = e0 + threadIdx.x;
+  if (e >= m.E) return;
+  T B[NQ][NQ];  // B[a][q] = l_a(g_q) w_q
+#pragma unroll
+  for (int a = 0; a < NQ; ++a)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) B[a][q] = (T)tb.Bw[a][q];
+  const T* ev = sh + threadIdx.x * Q;
+  T t1[NQ][NQ][NQ];  // [qz][qy][a]
+#pragma unroll
+  for (int qz = 0; qz < NQ; ++qz)
+#pragma unroll
+    for (int qy = 0; qy < NQ; ++qy)
+#pragma unroll
+      for (int a = 0; a < NQ; ++a) {
+        T s = 0;
+#pragma unroll
+        for (int qx = 0; qx < NQ; ++qx) s += B[a][qx] * ev[qx + NQ * (qy + NQ * qz)];
+        t1[qz][qy][a] = s;
+      }
+  T t2[NQ][NQ][NQ];  // [qz][b][a]
+#pragma unroll
+  for (int qz = 0; qz < NQ; ++qz)
+#pragma unroll
+    for (int bb = 0; bb < NQ; ++bb)
+#pragma unroll
+      for (int a = 0; a < NQ; ++a) {
+        T s = 0;
+#pragma unroll
+        for (int qy = 0; qy < NQ; ++qy) s += B[bb][qy] * t1[qz][qy][a];
+        t2[qz][bb][a] = s;
+      }
+  int ex = (int)(e % m.ne[0]);
+  int ey = (int)((e / m.ne[0]) % m.ne[1]);
+  int ez = (int)(e / ((int64_t)m.ne[0] * m.ne[1]));
+  int64_t nx = m.nn[0], nxy = (int64_t)m.nn[0] * m.nn[1];
+  int64_t base = (int64_t)ex * K + nx * ((int64_t)ey * K) + nxy * ((int64_t)ez * K);
+  double detJ = m.Ve;
+#pragma unroll
+  for (int c = 0; c < NQ; ++c)
+#pragma unroll
+    for (int bb = 0; bb < NQ; ++bb)
+#pragma unroll
+      for (int a = 0; a < NQ; ++a) {
+        T s = 0;
+#pragma unroll
+        for (int qz = 0; qz < NQ; ++qz) s += B[c][qz] * t2[qz][bb][a];
+        atomicAdd(b + base + a + nx * bb + nxy * c, (double)s * detJ);
+      }
+}
+
+cudaError_t launch_rhs(const MeshDev& m, const Tables& t, const double* eps_q64,
+                       const float* eps_q32, double* b, cudaStream_t s) {
+  cudaError_t err = cudaMemsetAsync(b, 0, sizeof(double) * m.n_nodes, s);
+  if (err != cudaSuccess) return err;
+#define CFDEM_RHS(KK)                                                                  \
+  if (m.k == KK) {                                                                     \
+    if (eps_q32) {                                                                     \
+      constexpr int nb = rhs_block<KK, float>();                                       \
+      k_rhs<KK, float><<<(unsigned)((m.E + nb - 1) / nb), nb, 0, s>>>(m, t, eps_q32, b); \
+    } else {                                                                           \
+      constexpr int nb = rhs_block<KK, double>();                                      \
+      k_rhs<KK, double><<<(unsigned)((m.E + nb - 1) / nb), nb, 0, s>>>(m, t, eps_q64, b); \
+    }                                                                                  \
+    count_launches(1);                                                                 \
+    return cudaGetLastError();                                                         \
+  }
+  CFDEM_RHS(1)
+  CFDEM_RHS(2)
+  CFDEM_RHS(3)
+#undef CFDEM_RHS
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// assembled 1D band tables: for axis a and node i, coefficients t = -k..k of
+// the reference (unit element length) mass and stiffness rows
+
+static void band_rows(int ne, int k, const double Mh[4][4], double* out /*[n][2k+1]*/) {
+  int n = ne * k + 1, w = 2 * k + 1;
+  for (int i = 0; i < n * w; ++i) out[i] = 0.0;
+  for (int el = 0; el < ne; ++el)
+    for (int a = 0; a <= k; ++a)
+      for (int bb = 0; bb <= k; ++bb) {
+        int i = el * k + a, j = el * k + bb;
+        out[i * w + (j - i + k)] += Mh[a][bb];
+      }
+}
+
+// layout: for axis a: [M rows n_a x w][K rows n_a x w], axes one after another
+cudaError_t upload_bands(const MeshDev& m, const Tables& t, double /*L2*/, double** bands64,
+                         float** bands32) {
+  int k = m.k, w = 2 * k + 1;
+  size_t tot = 0;
+  for (int a = 0; a < 3; ++a) tot += 2 * (size_t)m.nn[a] * w;
+  std::vector<double> h(tot);
+  size_t off = 0;
+  for (int a = 0; a < 3; ++a) {
+    band_rows(m.ne[a], k, t.Mh, h.data() + off);
+    off += (size_t)m.nn[a] * w;
+    band_rows(m.ne[a], k, t.Kh, h.data() + off);
+    off += (size_t)m.nn[a] * w;
+  }
+  std::vector<float> hf(tot);
+  for (size_t i = 0; i < tot; ++i) hf[i] = (float)h[i];
+  cudaError_t e;
+  if (*bands64) cudaFree(*bands64);
+  if (*bands32) cudaFree(*bands32);
+  *bands64 = nullptr;
+  *bands32 = nullptr;
+  if ((e = cudaMalloc(bands64, tot * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(bands32, tot * sizeof(float))) != cudaSuccess) return e;
+  if ((e = cudaMemcpy(*bands64, h.data(), tot * sizeof(double), cudaMemcpyHostToDevice)) !=
+      cudaSuccess)
+    return e;
+  return cudaMemcpy(*bands32, hf.data(), tot * sizeof(float), cudaMemcpyHostToDevice);
+}
+
+// ---------------------------------------------------------------------------
+// operator
+
+constexpr int TX = 16, TY = 8, TZ = 8;
+constexpr int kApplyThreads = 256;
+
+template <int K>
+struct Tile {
+  static constexpr int H = K;
+  static constexpr int XW = TX + 2 * H, YW = TY + 2 * H, ZW = TZ + 2 * H;
+  static constexpr int NX = ZW * YW * XW;     // input with halo
+  static constexpr int NT = TZ * YW * XW;     // after the z pass (each of t1, t2)
+  static constexpr int NU = TZ * TY * XW;     // after the y pass (each of U, V)
+};
+
+template <typename T>
+struct Coefs {
+  T cM, cKx, cKy, cKz;
+};
+
+// y = A x on one tile; x_eff(node) = x[node] (+ beta * p_old[node] when
+// p_old != nullptr, the CG direction update p = z + beta p fused into the
+// load, with the updated direction written to p_new for owned nodes).
+// Returns the tile's partial dot x_eff . y for owned nodes if want_dot.
+template <int K, typename T>
+__device__ __forceinline__ double apply_tile(const MeshDev& m, const T* __restrict__ bands,
+                                             const Coefs<T>& cf, const T* __restrict__ x,
+                                             const T* __restrict__ p_old, T beta,
+                                             T* __restrict__ p_new, T* __restrict__ y,
+                                             T* sm) {
+  using TL = Tile<K>;
+  constexpr int H = K, W = 2 * K + 1;
+  const int nx = m.nn[0], ny = m.nn[1], nz = m.nn[2];
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+  const int64_t sxy = (int64_t)nx * ny;
+  T* X = sm;                 // [ZW][YW][XW]
+  T* T1 = sm + TL::NX;       // [TZ][YW][XW]
+  T* T2 = T1 + TL::NT;
+  T* U = T2 + TL::NT;        // [TZ][TY][XW]
+  T* V = U + TL::NU;
+  const T* bMx = bands;
+  const T* bKx = bMx + (size_t)nx * W;
+  const T* bMy = bKx + (size_t)nx * W;
+  const T* bKy = bMy + (size_t)ny * W;
+  const T* bMz = bKy + (size_t)ny * W;
+  const T* bKz = bMz + (size_t)nz * W;
+
+  // load with halo
+  for (int t = threadIdx.x; t < TL::NX; t += blockDim.x) {
+    int lx = t % TL::XW, ly = (t / TL::XW) % TL::YW, lz = t / (TL::XW * TL::YW);
+    int gx = x0 + lx - H, gy = y0 + ly - H, gz = z0 + lz - H;
+    T v = 0;
+    if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz) {
+      int64_t g = gx + (int64_t)nx * gy + sxy * gz;
+      v = x[g];
+      if (p_old) {
+        v = v + beta * p_old[g];
+        bool own = lx >= H && lx < H + TX && ly >= H && ly < H + TY && lz >= H && lz < H + TZ;
+        if (own && p_new) p_new[g] = v;
+      }
+    }
+    X[t] = v;
+  }
+  __syncthreads();
+  // z pass
+  for (int t = threadIdx.x; t < TL::NT; t += blockDim.x) {
+    int lx = t % TL::XW, ly = (t / TL::XW) % TL::YW, lz = t / (TL::XW * TL::YW);
+    int gz = z0 + lz;
+    T a1 = 0, a2 = 0;
+    if (gz < nz) {
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        T xv = X[(lz + w) * TL::YW * TL::XW + ly * TL::XW + lx];
+        a1 += bMz[(size_t)gz * W + w] * xv;
+        a2 += bKz[(size_t)gz * W + w] * xv;
+      }
+    }
+    T1[t] = a1;
+    T2[t] = a2;
+  }
+  __syncthreads();
+  // y pass
+  for (int t = threadIdx.x; t < TL::NU; t += blockDim.x) {
+    int lx = t % TL::XW, ly = (t / TL::XW) % TY, lz = t / (TL::XW * TY);
+    int gy = y0 + ly;
+    T s1 = 0, s2 = 0, s3 = 0;
+    if (gy < ny) {
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        int src = lz * TL::YW * TL::XW + (ly + w) * TL::XW + lx;
+        T mv = bMy[(size_t)gy * W + w], kv = bKy[(size_t)gy * W + w];
+        T t1 = T1[src];
+        s1 += mv * t1;
+        s2 += kv * t1;
+        s3 += mv * T2[src];
+      }
+    }
+    U[t] = cf.cM * s1 + cf.cKy * s2 + cf.cKz * s3;
+    V[t] = cf.cKx * s1;
+  }
+  __syncthreads();
+  // x pass + output
+  double dot = 0.0;
+  for (int t = threadIdx.x; t < TX * TY * TZ; t += blockDim.x) {
+    int lx = t % TX, ly = (t / TX) % TY, lz = t / (TX * TY);
+    int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
+    if (gx >= nx || gy >= ny || gz >= nz) continue;
+    T acc = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      int src = lz * TY * TL::XW + ly * TL::XW + lx + w;
+      acc += bMx[(size_t)gx * W + w] * U[src] + bKx[(size_t)gx * W + w] * V[src];
+    }
+    int64_t g = gx + (int64_t)nx * gy + sxy * gz;
+    y[g] = acc;
+    T xe = X[(lz + H) * TL::YW * TL::XW + (ly + H) * TL::XW + lx + H];
+    dot += (double)(xe * acc);
+  }
+  return dot;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  // red: >= 32 doubles of shared memory
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (warp == 0) {
+    s = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  }
+  return s;  // valid in thread 0
+}
+
+// last block to finish reduces partials[0..nb) (nvals interleaved values) in
+// fixed order; returns true in the last block (results in out[0..nvals))
+__device__ bool last_block_reduce(double* partials, int nvals, const double* vals,
+                                  unsigned int* ticket, double* out, double* red) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    for (int v = 0; v < nvals; ++v) partials[(size_t)v * gridDim.x * gridDim.y * gridDim.z +
+                                             blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = vals[v];
+    __threadfence();
+    unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
+    unsigned t = atomicInc(ticket, nblk - 1);
+    last = (t == nblk - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
+  for (int v = 0; v < nvals; ++v) {
+    double s = 0.0;
+    for (unsigned i = threadIdx.x; i < nblk; i += blockDim.x)
+      s += ((volatile double*)partials)[(size_t)v * nblk + i];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) out[v] = s;
+  }
+  return true;
+}
+
+template <int K, typename T>
+__global__ void __launch_bounds__(kApplyThreads)
+k_apply(MeshDev m, const T* __restrict__ bands, Coefs<T> cf, const T* __restrict__ x,
+        T* __restrict__ y) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  apply_tile<K, T>(m, bands, cf, x, nullptr, (T)0, nullptr, y, reinterpret_cast<T*>(smraw));
+}
+
+// CG step 1: p = z + beta p_old (fused into the load) ; Ap = A p ; alpha =
+// rz / (p . Ap)
+template <int K, typename T>
+__global__ void __launch_bounds__(kApplyThreads)
+k_cg_apply(MeshDev m, const T* __restrict__ bands, Coefs<T> cf, const T* __restrict__ z,
+           const T* __restrict__ p_old, T* __restrict__ p_new, T* __restrict__ Ap,
+           double* partials, CgScalars* sc, int first) {
+  if (((volatile CgScalars*)sc)->done) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double red[32];
+  T beta = first ? (T)0 : (T)sc->beta;
+  double d = apply_tile<K, T>(m, bands, cf, z, first ? nullptr : p_old, beta, p_new, Ap,
+                              reinterpret_cast<T*>(smraw));
+  if (first) {
+    // p = z: copy owned nodes
+    const int nx = m.nn[0], ny = m.nn[1], nz = m.nn[2];
+    for (int t = threadIdx.x; t < TX * TY * TZ; t += blockDim.x) {
+      int gx = blockIdx.x * TX + t % TX, gy = blockIdx.y * TY + (t / TX) % TY,
+          gz = blockIdx.z * TZ + t / (TX * TY);
+      if (gx < nx && gy < ny && gz < nz) {
+        int64_t g = gx + (int64_t)nx * gy + (int64_t)nx * ny * gz;
+        p_new[g] = z[g];
+      }
+    }
+  }
+  double s = block_sum(d, red);
+  double vals[1] = {s};
+  double out[1];
+  if (last_block_reduce(partials, 1, vals, &sc->ticket, out, red) && threadIdx.x == 0) {
+    sc->pAp = out[0];
+    sc->alpha = sc->rz / out[0];
+  }
+}
+
+// CG step 2: x += alpha p ; r -= alpha Ap ; z = D^-1 r ; beta ; convergence
+template <typename T, typename TX_>
+__global__ void __launch_bounds__(256)
+k_cg_update(int64_t n, TX_* __restrict__ xv, T* __restrict__ r, T* __restrict__ z,
+            const T* __restrict__ p, const T* __restrict__ Ap, const T* __restrict__ dinv,
+            double* partials, CgScalars* sc, int maxit) {
+  if (((volatile CgScalars*)sc)->done) return;
+  __shared__ double red[32];
+  T alpha = (T)sc->alpha;
+  double rz = 0.0, rr = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    xv[i] += (TX_)(alpha * p[i]);
+    T ri = r[i] - alpha * Ap[i];
+    T zi = ri * dinv[i];
+    r[i] = ri;
+    z[i] = zi;
+    rz += (double)(ri * zi);
+    rr += (double)(ri * ri);
+  }
+  double s1 = block_sum(rz, red);
+  double s2 = block_sum(rr, red);
+  double vals[2] = {s1, s2};
+  double out[2];
+  if (last_block_reduce(partials, 2, vals, &sc->ticket, out, red) && threadIdx.x == 0) {
+    sc->beta = out[0] / sc->rz;
+    sc->rz = out[0];
+    sc->rr = out[1];
+    sc->it += 1;
+    if (out[1] <= sc->tol2 || sc->it >= maxit) sc->done = 1;
+  }
+}
+
+// start: r = b - Ax ; z = D^-1 r ; rz, rr, bb
+template <typename T, typename TB>
+__global__ void __launch_bounds__(256)
+k_cg_start(int64_t n, const TB* __restrict__ b, const T* __restrict__ Ax, T* __restrict__ r,
+           T* __restrict__ z, const T* __restrict__ dinv, double* partials, CgScalars* sc,
+           double rtol) {
+  __shared__ double red[32];
+  double rz = 0.0, rr = 0.0, bb = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    T ri = (T)b[i] - Ax[i];
+    T zi = ri * dinv[i];
+    r[i] = ri;
+    z[i] = zi;
+    rz += (double)(ri * zi);
+    rr += (double)(ri * ri);
+    bb += (double)b[i] * (double)b[i];
+  }
+  double s1 = block_sum(rz, red);
+  double s2 = block_sum(rr, red);
+  double s3 = block_sum(bb, red);
+  double vals[3] = {s1, s2, s3};
+  double out[3];
+  if (last_block_reduce(partials, 3, vals, &sc->ticket, out, red) && threadIdx.x == 0) {
+    sc->rz = out[0];
+    sc->rr = out[1];
+    sc->bb = out[2];
+    double bbv = out[2] > 0.0 ? out[2] : 1.0;
+    sc->tol2 = rtol * rtol * bbv;
+    sc->it = 0;
+    sc->done = out[1] <= sc->tol2 ? 1 : 0;
+    sc->beta = 0.0;
+  }
+}
+
+// inverse diagonal of A: cM Mx_ii My_jj Mz_kk + cKx Kx_ii My_jj Mz_kk + ...
+template <int K, typename T>
+__global__ void k_dinv(MeshDev m, const double* __restrict__ bands, double cM, double cKx,
+                       double cKy, double cKz, T* __restrict__ dinv) {
+  constexpr int W = 2 * K + 1;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= m.n_nodes) return;
+  int nx = m.nn[0], ny = m.nn[1], nz = m.nn[2];
+  int ix = (int)(i % nx), iy = (int)((i / nx) % ny), iz = (int)(i / ((int64_t)nx * ny));
+  const double* bMx = bands;
+  const double* bKx = bMx + (size_t)nx * W;
+  const double* bMy = bKx + (size_t)nx * W;
+  const double* bKy = bMy + (size_t)ny * W;
+  const double* bMz = bKy + (size_t)ny * W;
+  const double* bKz = bMz + (size_t)nz * W;
+  double mx = bMx[(size_t)ix * W + K], kx = bKx[(size_t)ix * W + K];
+  double my = bMy[(size_t)iy * W + K], ky = bKy[(size_t)iy * W + K];
+  double mz = bMz[(size_t)iz * W + K], kz = bKz[(size_t)iz * W + K];
+  double d = cM * mx * my * mz + cKx * kx * my * mz + cKy * mx * ky * mz + cKz * mx * my * kz;
+  dinv[i] = (T)(1.0 / d);
+}
+
+template <typename T>
+__global__ void k_residual(int64_t n, const double* __restrict__ b, const double* __restrict__ Ax,
+                           double* __restrict__ r, double* partials, CgScalars* sc) {
+  __shared__ double red[32];
+  double rr = 0.0, bb = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double ri = b[i] - Ax[i];
+    r[i] = ri;
+    rr += ri * ri;
+    bb += b[i] * b[i];
+  }
+  double s1 = block_sum(rr, red);
+  double s2 = block_sum(bb, red);
+  double vals[2] = {s1, s2};
+  double out[2];
+  if (last_block_reduce(partials, 2, vals, &sc->ticket, out, red) && threadIdx.x == 0) {
+    sc->rr = out[0];
+    sc->bb = out[1];
+  }
+}
+
+__global__ void k_to_f32(int64_t n, const double* __restrict__ a, double scale,
+                         float* __restrict__ o, float* __restrict__ zero) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    o[i] = (float)(a[i] * scale);
+    zero[i] = 0.0f;
+  }
+}
+
+__global__ void k_add_scaled(int64_t n, double* __restrict__ x, const float* __restrict__ d,
+                             double scale) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += (double)d[i] * scale;
+}
+
+// ---------------------------------------------------------------------------
+// host side
+
+template <int K, typename T>
+static size_t apply_smem() {
+  using TL = Tile<K>;
+  return ((size_t)TL::NX + 2 * (size_t)TL::NT + 2 * (size_t)TL::NU) * sizeof(T);
+}
+
+static dim3 apply_grid(const MeshDev& m) {
+  return dim3((m.nn[0] + TX - 1) / TX, (m.nn[1] + TY - 1) / TY, (m.nn[2] + TZ - 1) / TZ);
+}
+
+int cg_blocks(const MeshDev& m) {
+  dim3 g = apply_grid(m);
+  int na = (int)(g.x * g.y * g.z);
+  return na > 1216 ? na : 1216;
+}
+
+template <typename T>
+static Coefs<T> make_coefs(const double* c) {
+  Coefs<T> cf;
+  cf.cM = (T)c[0];
+  cf.cKx = (T)c[1];
+  cf.cKy = (T)c[2];
+  cf.cKz = (T)c[3];
+  return cf;
+}
+
+template <int K, typename T>
+static cudaError_t set_smem() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  size_t sm = apply_smem<K, T>();
+  cudaError_t e = cudaFuncSetAttribute(k_apply<K, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sm);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_cg_apply<K, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sm);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
+template <typename T>
+static cudaError_t apply_t(const MeshDev& m, const T* bands, const double* coef, const T* x,
+                           T* y, cudaStream_t s) {
+  dim3 g = apply_grid(m);
+  Coefs<T> cf = make_coefs<T>(coef);
+  cudaError_t e;
+#define CFDEM_APPLY(KK)                                                                    \
+  if (m.k == KK) {                                                                         \
+    if ((e = set_smem<KK, T>()) != cudaSuccess) return e;                                  \
+    k_apply<KK, T><<<g, kApplyThreads, apply_smem<KK, T>(), s>>>(m, bands, cf, x, y);      \
+    count_launches(1);                                                                     \
+    return cudaGetLastError();                                                             \
+  }
+  CFDEM_APPLY(1)
+  CFDEM_APPLY(2)
+  CFDEM_APPLY(3)
+#undef CFDEM_APPLY
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+static cudaError_t cg_apply_t(const MeshDev& m, const T* bands, const double* coef, const T* z,
+                              const T* p_old, T* p_new, T* Ap, double* partials, CgScalars* sc,
+                              int first, cudaStream_t s) {
+  dim3 g = apply_grid(m);
+  Coefs<T> cf = make_coefs<T>(coef);
+  cudaError_t e;
+#define CFDEM_CGA(KK)                                                                       \
+  if (m.k == KK) {                                                                          \
+    if ((e = set_smem<KK, T>()) != cudaSuccess) return e;                                   \
+    k_cg_apply<KK, T><<<g, kApplyThreads, apply_smem<KK, T>(), s>>>(m, bands, cf, z, p_old, \
+                                                                    p_new, Ap, partials, sc,\
+                                                                    first);                 \
+    count_launches(1);                                                                      \
+    return cudaGetLastError();                                                              \
+  }
+  CFDEM_CGA(1)
+  CFDEM_CGA(2)
+  CFDEM_CGA(3)
+#undef CFDEM_CGA
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_apply64(const MeshDev& m, const double* bands, const double* coef,
+                           const double* x, double* y, cudaStream_t s) {
+  return apply_t<double>(m, bands, coef, x, y, s);
+}
+
+template <typename T>
+static cudaError_t make_dinv(const MeshDev& m, const double* bands64, const double* coef,
+                             T* dinv, cudaStream_t s) {
+  unsigned g = (unsigned)((m.n_nodes + 255) / 256);
+#define CFDEM_DINV(KK)                                                                      \
+  if (m.k == KK) {                                                                          \
+    k_dinv<KK, T><<<g, 256, 0, s>>>(m, bands64, coef[0], coef[1], coef[2], coef[3], dinv);  \
+    count_launches(1);                                                                      \
+    return cudaGetLastError();                                                              \
+  }
+  CFDEM_DINV(1)
+  CFDEM_DINV(2)
+  CFDEM_DINV(3)
+#undef CFDEM_DINV
+  return cudaErrorInvalidValue;
+}
+
+static int vec_blocks(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return (int)(b < 1216 ? (b < 1 ? 1 : b) : 1216);
+}
+
+// one CG solve of A x = b in precision T from the start vector x (in T, or
+// FP64 for the outer vector when TX_ = double); iterations run in chunks
+// between host checks of the device flag
+template <typename T, typename TX_, typename TB>
+static cudaError_t cg_solve(const MeshDev& m, const T* bands, const double* coef, const TB* b,
+                            TX_* x, const T* x_as_T, double rtol, int maxit, T* r, T* z,
+                            T* p0, T* p1, T* Ap, const T* dinv, double* partials,
+                            CgScalars* sc, cudaStream_t s, int* iters, double* relres,
+                            Timer* tm) {
+  cudaError_t e;
+  int64_t n = m.n_nodes;
+  int vb = vec_blocks(n);
+  const int op_stage = sizeof(T) == 8 ? kStageOp64 : kStageOp32;
+  // Ax for the start vector
+  if (tm) tm->begin(op_stage, s);
+  if ((e = apply_t<T>(m, bands, coef, x_as_T, Ap, s)) != cudaSuccess) return e;
+  if (tm) tm->end(op_stage, s);
+  k_cg_start<T, TB><<<vb, 256, 0, s>>>(n, b, Ap, r, z, dinv, partials, sc, rtol);
+  count_launches(1);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  T* pc = p0;
+  T* pn = p1;
+  int launched = 0;
+  CgScalars hs;
+  const int chunk = 16;
+  while (launched < maxit) {
+    int todo = maxit - launched < chunk ? maxit - launched : chunk;
+    for (int it = 0; it < todo; ++it) {
+      int first = launched + it == 0;
+      if (tm) tm->begin(op_stage, s);
+      if ((e = cg_apply_t<T>(m, bands, coef, z, pc, pn, Ap, partials, sc, first, s)) !=
+          cudaSuccess)
+        return e;
+      if (tm) tm->end(op_stage, s);
+      k_cg_update<T, TX_><<<vb, 256, 0, s>>>(n, x, r, z, pn, Ap, dinv, partials, sc, maxit);
+      count_launches(1);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      T* t = pc;
+      pc = pn;
+      pn = t;
+    }
+    launched += todo;
+    if ((e = cudaMemcpyAsync(&hs, sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s)) !=
+        cudaSuccess)
+      return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    if (hs.done) break;
+  }
+  if ((e = cudaMemcpyAsync(&hs, sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+  *iters = hs.it;
+  double bb = hs.bb > 0 ? hs.bb : 1.0;
+  *relres = std::sqrt(hs.rr / bb);
+  return cudaSuccess;
+}
+
+cudaError_t run_cg64(const MeshDev& m, const double* bands, const double* coef,
+                     const double* b, double* x, double rtol, int maxit, CgWork& w,
+                     cudaStream_t s, int* iters_host, double* relres_host, int* converged) {
+  cudaError_t e;
+  if ((e = make_dinv<double>(m, bands, coef, w.dinv, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(w.sc, 0, sizeof(CgScalars), s)) != cudaSuccess) return e;
+  e = cg_solve<double, double, double>(m, bands, coef, b, x, x, rtol, maxit, w.r, w.z, w.p0,
+                                       w.p1, w.Ap, w.dinv, w.partials, w.sc, s, iters_host,
+                                       relres_host, w.timer);
+  if (e != cudaSuccess) return e;
+  *converged = *relres_host <= rtol;
+  return cudaSuccess;
+}
+
+cudaError_t run_cg_mixed(const MeshDev& m, const double* bands64, const float* bands32,
+                         const double* coef, const double* b, double* x, double rtol,
+                         int maxit, CgWork& w, cudaStream_t s, int* iters_host,
+                         int* outer_host, double* relres_host, int* converged) {
+  cudaError_t e;
+  int64_t n = m.n_nodes;
+  int vb = vec_blocks(n);
+  if ((e = make_dinv<float>(m, bands64, coef, w.dinv32, s)) != cudaSuccess) return e;
+  int total_it = 0, outer = 0;
+  double relres = 1.0;
+  const int max_outer = 8;
+  const double inner_rtol = 1e-6;
+  CgScalars hs;
+  for (;;) {
+    // r = b - A x in FP64
+    if (w.timer) w.timer->begin(kStageOp64, s);
+    if ((e = apply_t<double>(m, bands64, coef, x, w.Ap, s)) != cudaSuccess) return e;
+    if (w.timer) w.timer->end(kStageOp64, s);
+    if ((e = cudaMemsetAsync(w.sc, 0, sizeof(CgScalars), s)) != cudaSuccess) return e;
+    k_residual<double><<<vb, 256, 0, s>>>(n, b, w.Ap, w.r, w.partials, w.sc);
+    count_launches(1);
+    if ((e = cudaMemcpyAsync(&hs, w.sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s)) !=
+        cudaSuccess)
+      return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    double bb = hs.bb > 0 ? hs.bb : 1.0;
+    relres = std::sqrt(hs.rr / bb);
+    if (relres <= rtol || outer >= max_outer || total_it >= maxit) break;
+    // FP32 correction solve A d = r / |r|
+    double rn = std::sqrt(hs.rr);
+    double scale = rn > 0 ? 1.0 / rn : 1.0;
+    k_to_f32<<<vb, 256, 0, s>>>(n, w.r, scale, w.r32, w.d32);
+    count_launches(1);
+    if ((e = cudaMemsetAsync(w.sc, 0, sizeof(CgScalars), s)) != cudaSuccess) return e;
+    int it = 0;
+    double rr = 0;
+    e = cg_solve<float, float, float>(m, bands32, coef, w.r32, w.d32, w.d32, inner_rtol,
+                                      maxit - total_it, w.r32 + 0 * n, w.z32, w.q0, w.q1,
+                                      w.Aq, w.dinv32, w.partials, w.sc, s, &it, &rr, w.timer);
+    if (e != cudaSuccess) return e;
+    total_it += it;
+    k_add_scaled<<<vb, 256, 0, s>>>(n, x, w.d32, rn);
+    count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    ++outer;
+  }
+  *iters_host = total_it;
+  *outer_host = outer;
+  *relres_host = relres;
+  *converged = relres <= rtol;
+  return cudaSuccess;
+}
+
+}  // namespace cfdem

@@ -54,9 +54,9 @@ def gas_params(mean_d: float, k: int) -> dict:
 
 # --------------------------------------------------------------- particles
 
-def rsa(rng, n, d, lo, hi, max_tries=200):
-    """Random sequential addition of n equal spheres of diameter d with
-    centres in the box [lo, hi] (no overlap)."""
+def rsa(rng, n, d, lo, hi, max_tries=200, radii=None):
+    """Random sequential addition of n spheres with centres in the box
+    [lo, hi] and no overlap: equal diameter d, or the given radii."""
     lo = np.asarray(lo, dtype=np.float64)
     hi = np.asarray(hi, dtype=np.float64)
     pts = np.zeros((0, 3))
@@ -68,7 +68,11 @@ def rsa(rng, n, d, lo, hi, max_tries=200):
         c = lo + (hi - lo) * rng.random(3)
         if pts.shape[0]:
             dd = np.sum((pts - c) ** 2, axis=1)
-            if np.any(dd < d * d):
+            if radii is None:
+                lim = d * d
+            else:
+                lim = (radii[:pts.shape[0]] + radii[pts.shape[0]]) ** 2
+            if np.any(dd < lim):
                 continue
         pts = np.vstack([pts, c])
     return pts
@@ -219,12 +223,16 @@ def make_workload(name: str, seed: int | None = None) -> dict:
 def make_random_case(seed: int, n_el=(3, 4, 5), k=2, n=150, extent=(0.03, 0.04, 0.05),
                      d=(2e-3, 6e-3), origin=(0.0, 0.0, 0.0), overlap_ok=True) -> dict:
     """Small uneven case for parity tests: uniform random centres over the
-    whole box (overlaps allowed), diameters uniform in d."""
+    whole box with overlaps allowed (overlap_ok), or placed by random
+    sequential addition without overlap; diameters uniform in d."""
     rng = np.random.default_rng(seed)
     origin = np.asarray(origin, dtype=np.float64)
     extent = np.asarray(extent, dtype=np.float64)
-    x = origin + extent * rng.random((n, 3))
     r = 0.5 * (d[0] + (d[1] - d[0]) * rng.random(n))
+    if overlap_ok:
+        x = origin + extent * rng.random((n, 3))
+    else:
+        x = rsa(rng, n, 0.0, origin, origin + extent, radii=r)
     spec = dict(origin=origin, extent=extent, n_el=n_el, k=k, field="noise", u_mean=1.0,
                 phi=0.3)
     u, p, u_p = make_fields(spec, rng, n)
