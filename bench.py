@@ -160,6 +160,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"],
+                    help="paths to time (profiling runs use one)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -243,8 +246,18 @@ def main():
             tot = float(tt.item())
         return tot / k, st, clocks
 
-    ms64, st64, clk64 = timed(0, max(3, args.steps // 2))
+    k64 = max(3, args.steps // 2)
+    if args.precision in ("both", "fp64"):
+        ms64, st64, clk64 = timed(0, k64)
+    if args.precision == "fp64":
+        print(json.dumps({"fp64_ms_per_step": ms64, "stages_ms": {
+            nm: st64.stage_ms[i] / k64 for i, nm in enumerate(cf.STAGES)}}), flush=True)
+        return 0
     ms_mx, st_mx, clk_mx = timed(1, args.steps)
+    if args.precision == "mixed":
+        print(json.dumps({"mixed_ms_per_step": ms_mx, "stages_ms": {
+            nm: st_mx.stage_ms[i] / args.steps for i, nm in enumerate(cf.STAGES)}}), flush=True)
+        return 0
 
     # error of the mixed path against the FP64 path (same inputs)
     err = {"eps_h": rel_err(outs[1]["eps_h"].cpu().numpy(), outs[0]["eps_h"].cpu().numpy()),
@@ -261,8 +274,9 @@ def main():
     h2d = sum(v.numel() * 8 for v in hx.values())
     d2h = (hf.numel() + hF.numel()) * 8
     ev = []
+    e2e_steps = 0 if args.no_e2e else args.warmup + args.steps
     with torch.cuda.stream(stream):
-        for i in range(args.warmup + args.steps):
+        for i in range(e2e_steps):
             flush.zero_()
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
@@ -279,7 +293,7 @@ def main():
             if i >= args.warmup:
                 ev.append((a, b))
         torch.cuda.synchronize(dev)
-    e2e_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    e2e_ms = float(np.mean([a.elapsed_time(b) for a, b in ev])) if ev else float("nan")
 
     # roofline of the dominant kernel group of the mixed step
     peaks, peak_kind = _peaks()
@@ -331,8 +345,7 @@ def main():
                       "parallelism": "replicas" if world > 1 else "single GPU"},
            "fp64": {"value": world * n / (ms64 * 1e-3), "ms_per_step": ms64, "dtype": "f64",
                     "cg_iterations": st64.cg_iterations,
-                    "stages_ms": {nm: st64.stage_ms[i] / max(3, args.steps // 2)
-                                  for i, nm in enumerate(cf.STAGES)}},
+                    "stages_ms": {nm: st64.stage_ms[i] / k64 for i, nm in enumerate(cf.STAGES)}},
            "err_mixed_vs_fp64": err,
            "stages_ms": stages,
            "cg": {"mixed_inner_iterations": st_mx.cg_iterations, "mixed_outer": st_mx.cg_outer,

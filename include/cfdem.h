@@ -72,6 +72,8 @@ typedef struct {
     int pressure_degree;   /* kp; 0 => max(1, k - 1) */
     double max_radius;     /* hint for the bin size (largest particle radius); 0 => R */
     double bin_edge;       /* bin edge [m]; 0 => R + max_radius */
+    int cg_precond;        /* 0 = Jacobi, 1 = fast diagonalisation (exact inverse of the
+                              Kronecker-sum operator, applied in FP32; default) */
 } cfdem_params;
 
 /* Counters of the last calls on a context. */
@@ -94,6 +96,7 @@ typedef struct {
     int64_t stage_calls[8];
     int32_t timer_overflow;       /* 1 if more than 4096 pairs per stage were asked */
     int64_t kernel_launches;      /* kernels launched by the library since set_timing */
+    int32_t precond;              /* preconditioner in use: 0 Jacobi, 1 FDM */
 } cfdem_stats;
 
 /* Create a context on CUDA device `device`, ordering all work on `stream`
@@ -106,7 +109,7 @@ cfdem_status cfdem_destroy(cfdem_t ctx);
 
 /* Fill *p with the defaults: gas (rho_f 1.2, mu_f 1.8e-5), g = (0,0,-9.81),
  * QCM, Di Felice, model A, FP64, cg_rtol 1e-13, cg_maxit 2000, eps_floor
- * 0.05, everything else 0 (resolved from the mesh). */
+ * 0.05, FDM preconditioner, everything else 0 (resolved from the mesh). */
 void cfdem_params_default(cfdem_params *p);
 
 /* Mesh: the axis-aligned box [origin, origin + extent] cut into n_el[0] x
@@ -161,8 +164,8 @@ cfdem_status cfdem_project_rhs(cfdem_t ctx, const double *eps_q_dev, double *b_d
 cfdem_status cfdem_apply(cfdem_t ctx, const double *x_dev, double *y_dev);
 
 /* Steps a4-a5 -- smoothed L2 projection: solves (M + L^2 K) eps_h = b by
- * Jacobi-preconditioned CG (FP64) or FP32 CG inside FP64 iterative
- * refinement (mixed).  eps_q_dev: NULL = the context's last void fraction.
+ * preconditioned CG (FP64) or FP32 CG inside FP64 iterative refinement
+ * (mixed); preconditioner Jacobi or fast diagonalisation (cg_precond).  eps_q_dev: NULL = the context's last void fraction.
  * eps_nodal_dev[n_nodes]: start vector on entry, solution on exit.  The
  * iteration count and relative residual go to cfdem_get_stats. */
 cfdem_status cfdem_project(cfdem_t ctx, const double *eps_q_dev, double *eps_nodal_dev);

@@ -65,7 +65,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 print(msg)
     if force or _stale(LIB, objs):
         tmp = LIB + ".tmp%d" % os.getpid()
-        run([nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs)
+        run([nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + ["-lcublas"])
         os.replace(tmp, LIB)
     return LIB
 

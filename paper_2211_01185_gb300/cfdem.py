@@ -34,7 +34,8 @@ class cfdem_params(C.Structure):
                 ("drag_model", C.c_int), ("vans_model", C.c_int), ("beta_over_eps", C.c_int),
                 ("precision", C.c_int), ("cg_rtol", C.c_double), ("cg_maxit", C.c_int),
                 ("eps_floor", C.c_double), ("pressure_degree", C.c_int),
-                ("max_radius", C.c_double), ("bin_edge", C.c_double)]
+                ("max_radius", C.c_double), ("bin_edge", C.c_double),
+                ("cg_precond", C.c_int)]
 
 
 class cfdem_stats(C.Structure):
@@ -44,7 +45,7 @@ class cfdem_stats(C.Structure):
                 ("n_elem", C.c_int64), ("n_qp", C.c_int64), ("n_nodes", C.c_int64),
                 ("n_pnodes", C.c_int64), ("stage_ms", C.c_double * 8),
                 ("stage_calls", C.c_int64 * 8), ("timer_overflow", C.c_int32),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("precond", C.c_int32)]
 
 STAGES = ("bin", "void_fraction", "rhs", "solve", "forces", "fluid_source", "op32", "op64")
 

@@ -92,6 +92,8 @@ struct cfdem_ctx {
   double* S = nullptr;         // per-element source accumulator [E][3]
   double* vol = nullptr;       // per-element particle volume (PCM)
   CgWork cg{};
+  FdmPlan* fdm = nullptr;
+  const char* fdm_note = "";
   int eps_state = 0;           // 0 none, 1 eps64 valid, 2 eps32 valid
   // host-side record
   int last_iters = 0, last_outer = 0, last_converged = 1;
@@ -286,6 +288,18 @@ cfdem_status resolve(cfdem_t c) {
   }
   DeviceGuard g(c->device);
   CK(upload_bands(m, c->tab, L2, &c->bands64, &c->bands32), "upload_bands");
+  if (c->fdm) {
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    fdm_destroy(c->fdm);
+    c->fdm = nullptr;
+  }
+  c->fdm_note = "";
+  if (p.cg_precond == 1) {
+    const char* why = nullptr;
+    CK(fdm_create(m, c->tab, c->coef, &c->fdm, &why), "fdm_create");
+    if (!c->fdm) c->fdm_note = why ? why : "FDM unavailable";
+  }
+  c->cg.fdm = c->fdm;
   if (c->bins.nbins + 1 > c->cap_bins) {
     int64_t nb = c->bins.nbins + 1;
     CK(grow(&c->bin_count, nb), "bins");
@@ -313,7 +327,7 @@ void free_mesh_arena(cfdem_t c) {
   void* ps[] = {c->eps64, c->eps32, c->b, c->S, c->vol, c->cg.r, c->cg.z, c->cg.p0,
                 c->cg.p1, c->cg.Ap, c->cg.dinv, c->cg.xcor, c->cg.r32, c->cg.z32,
                 c->cg.q0, c->cg.q1, c->cg.Aq, c->cg.dinv32, c->cg.d32, c->cg.partials,
-                c->cg.sc};
+                c->cg.sc, c->cg.zn, c->cg.zn32, c->cg.rin32};
   for (void* p : ps)
     if (p) cudaFree(p);
   c->eps64 = nullptr;
@@ -321,7 +335,9 @@ void free_mesh_arena(cfdem_t c) {
   c->b = nullptr;
   c->S = nullptr;
   c->vol = nullptr;
+  FdmPlan* keep = c->cg.fdm;
   c->cg = CgWork{};
+  c->cg.fdm = keep;
 }
 
 cfdem_status alloc_mesh_arena(cfdem_t c) {
@@ -346,6 +362,9 @@ cfdem_status alloc_mesh_arena(cfdem_t c) {
   CK(grow(&w.Aq, nn), "cg");
   CK(grow(&w.dinv32, nn), "cg");
   CK(grow(&w.d32, nn), "cg");
+  CK(grow(&w.zn, nn), "cg");
+  CK(grow(&w.zn32, nn), "cg");
+  CK(grow(&w.rin32, nn), "cg");
   w.nblocks = cg_blocks(m);
   CK(grow(&w.partials, 4 * (size_t)w.nblocks), "cg");
   CK(grow(&w.sc, 1), "cg");
@@ -394,6 +413,7 @@ void cfdem_params_default(cfdem_params* p) {
   p->cg_rtol = 1e-13;
   p->cg_maxit = 2000;
   p->eps_floor = 0.05;
+  p->cg_precond = 1;
 }
 
 cfdem_status cfdem_create(cfdem_t* out, int device, void* stream) {
@@ -428,6 +448,8 @@ cfdem_status cfdem_destroy(cfdem_t c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
   free_mesh_arena(c);
+  if (c->fdm) fdm_destroy(c->fdm);
+  c->fdm = nullptr;
   c->timer.release();
   void* ps[] = {c->st, c->bands64, c->bands32, c->bin_of, c->slot, c->perm, c->xs64,
                 c->xs32, c->bin_count, c->bin_start, c->scan_tmp};
@@ -489,6 +511,8 @@ cfdem_status cfdem_set_params(cfdem_t c, const cfdem_params* p) {
     return fail(c, CFDEM_EINVAL, "numerical parameter out of range");
   if (p->pressure_degree < 0 || p->pressure_degree > 3)
     return fail(c, CFDEM_EINVAL, "pressure_degree must be 0..3");
+  if (p->cg_precond < 0 || p->cg_precond > 1)
+    return fail(c, CFDEM_EINVAL, "cg_precond must be 0 (Jacobi) or 1 (FDM)");
   c->prm = *p;
   return resolve(c);
 }
@@ -712,6 +736,7 @@ cfdem_status cfdem_get_stats(cfdem_t c, cfdem_stats* out) {
   }
   out->timer_overflow = c->timer.overflow ? 1 : 0;
   out->kernel_launches = launches_total() - c->launches_at_reset;
+  out->precond = c->fdm ? 1 : 0;
   return CFDEM_OK;
 }
 

@@ -140,11 +140,18 @@ cudaError_t upload_bands(const MeshDev& m, const Tables& t, double L2, double** 
                          float** bands32);
 cudaError_t launch_apply64(const MeshDev& m, const double* bands, const double* coef,
                            const double* x, double* y, cudaStream_t s);
+struct FdmPlan;
+cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4],
+                       FdmPlan** out, const char** why);
+cudaError_t fdm_apply(FdmPlan* p, const float* r, float* z, cudaStream_t s);
+void fdm_destroy(FdmPlan* p);
+
 struct CgWork {
   // FP64 vectors
-  double *r, *z, *p0, *p1, *Ap, *dinv, *xcor;
-  // FP32 vectors (mixed inner solve)
-  float *r32, *z32, *q0, *q1, *Aq, *dinv32, *d32;
+  double *r, *z, *p0, *p1, *Ap, *dinv, *xcor, *zn;
+  // FP32 vectors (mixed inner solve, FDM conversions)
+  float *r32, *z32, *q0, *q1, *Aq, *dinv32, *d32, *zn32, *rin32;
+  FdmPlan* fdm;       // fast-diagonalisation preconditioner, or null (Jacobi)
   double* partials;   // per-block partial sums
   CgScalars* sc;      // device scalars
   int nblocks;

@@ -350,27 +350,31 @@ k_forces(MeshDev m, Tables tb, ForceParams fp, int64_t n, const double* __restri
   for (int a = 0; a < 3; ++a) ie[a] = elem_axis(p[a], m.x0[a], m.h[a], m.ne[a], &xid[a]);
   T xi[3] = {(T)xid[0], (T)xid[1], (T)xid[2]};
 
-  // u_f and eps at the particle: Q_k interpolation
-  T lx[K + 1], ly[K + 1], lz[K + 1];
-  lagrange<K, T>(tb.z, tb.lw, xi[0], lx, (T*)nullptr);
-  lagrange<K, T>(tb.z, tb.lw, xi[1], ly, (T*)nullptr);
-  lagrange<K, T>(tb.z, tb.lw, xi[2], lz, (T*)nullptr);
-  T uf0 = 0, uf1 = 0, uf2 = 0, eps = 0;
+  // u_f and eps at the particle: Q_k interpolation.  The velocity is
+  // interpolated in FP64 on both paths: the slip u_f - u_p of a component
+  // that is small against the others cancels, and FP32 shape functions would
+  // leave an absolute error of ~1e-7 |u| in it.  eps uses the same weights.
+  double lxd[K + 1], lyd[K + 1], lzd[K + 1];
+  lagrange<K, double>(tb.z, tb.lw, xid[0], lxd, (double*)nullptr);
+  lagrange<K, double>(tb.z, tb.lw, xid[1], lyd, (double*)nullptr);
+  lagrange<K, double>(tb.z, tb.lw, xid[2], lzd, (double*)nullptr);
+  double ufd0 = 0, ufd1 = 0, ufd2 = 0;
+  T eps = 0;
   int64_t nx = m.nn[0], nxy = (int64_t)m.nn[0] * m.nn[1];
   int64_t base = (int64_t)ie[0] * K + nx * ((int64_t)ie[1] * K) + nxy * ((int64_t)ie[2] * K);
 #pragma unroll
   for (int c = 0; c <= K; ++c) {
 #pragma unroll
     for (int b = 0; b <= K; ++b) {
-      T lyz = ly[b] * lz[c];
+      double lyz = lyd[b] * lzd[c];
 #pragma unroll
       for (int a = 0; a <= K; ++a) {
-        T phi = lx[a] * lyz;
+        double phi = lxd[a] * lyz;
         int64_t nd = base + a + nx * b + nxy * c;
-        uf0 += phi * (T)__ldg(u_nodal + 3 * nd);
-        uf1 += phi * (T)__ldg(u_nodal + 3 * nd + 1);
-        uf2 += phi * (T)__ldg(u_nodal + 3 * nd + 2);
-        eps += phi * (T)__ldg(eps_nodal + nd);
+        ufd0 += phi * __ldg(u_nodal + 3 * nd);
+        ufd1 += phi * __ldg(u_nodal + 3 * nd + 1);
+        ufd2 += phi * __ldg(u_nodal + 3 * nd + 2);
+        eps += (T)phi * (T)__ldg(eps_nodal + nd);
       }
     }
   }
@@ -412,7 +416,8 @@ k_forces(MeshDev m, Tables tb, ForceParams fp, int64_t n, const double* __restri
 
   // closures
   T rp = (T)r[i];
-  T U0 = uf0 - (T)u_p[3 * i], U1 = uf1 - (T)u_p[3 * i + 1], U2 = uf2 - (T)u_p[3 * i + 2];
+  T U0 = (T)(ufd0 - u_p[3 * i]), U1 = (T)(ufd1 - u_p[3 * i + 1]),
+    U2 = (T)(ufd2 - u_p[3 * i + 2]);
   T speed = t_sqrt<T>(U0 * U0 + U1 * U1 + U2 * U2);
   T epsc = eps < (T)fp.eps_floor ? (T)fp.eps_floor : eps;
   epsc = epsc > (T)1 ? (T)1 : epsc;

@@ -447,6 +447,96 @@ k_cg_start(int64_t n, const TB* __restrict__ b, const T* __restrict__ Ax, T* __r
   }
 }
 
+// --- preconditioned by the fast diagonalisation (FDM) ---------------------
+// update without preconditioning: x += alpha p ; r -= alpha Ap ; rf = (float) r
+// for the FDM ; r . r and the convergence flag
+template <typename T, typename TX_>
+__global__ void __launch_bounds__(256)
+k_cg_update_fdm(int64_t n, TX_* __restrict__ xv, T* __restrict__ r, const T* __restrict__ p,
+                const T* __restrict__ Ap, float* __restrict__ rf, double* partials,
+                CgScalars* sc, int maxit) {
+  if (((volatile CgScalars*)sc)->done) return;
+  __shared__ double red[32];
+  T alpha = (T)sc->alpha;
+  double rr = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    xv[i] += (TX_)(alpha * p[i]);
+    T ri = r[i] - alpha * Ap[i];
+    r[i] = ri;
+    if (rf) rf[i] = (float)ri;
+    rr += (double)(ri * ri);
+  }
+  double s = block_sum(rr, red);
+  double vals[1] = {s};
+  double out[1];
+  if (last_block_reduce(partials, 1, vals, &sc->ticket, out, red) && threadIdx.x == 0) {
+    sc->rr = out[0];
+    sc->it += 1;
+    if (out[0] <= sc->tol2 || sc->it >= maxit) sc->done = 1;
+  }
+}
+
+// after z_new = P^-1 r: z_new (from the FP32 FDM output zf) ; rz_new = r . z_new ;
+// Polak-Ribiere beta = (rz_new - r . z_old) / rz_old (robust to the rounding
+// of the FP32 preconditioner) ; first: plain rz
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_cg_dot_fdm(int64_t n, const T* __restrict__ r, const float* __restrict__ zf,
+             const T* __restrict__ z_old, T* __restrict__ z_new, double* partials,
+             CgScalars* sc, int first, int ignore_done) {
+  if (!ignore_done && ((volatile CgScalars*)sc)->done) return;
+  __shared__ double red[32];
+  double rz = 0.0, rzo = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    T zi = zf ? (T)zf[i] : z_new[i];
+    if (zf) z_new[i] = zi;
+    T ri = r[i];
+    rz += (double)(ri * zi);
+    if (!first) rzo += (double)(ri * z_old[i]);
+  }
+  double s1 = block_sum(rz, red);
+  double s2 = block_sum(rzo, red);
+  double vals[2] = {s1, s2};
+  double out[2];
+  if (last_block_reduce(partials, 2, vals, &sc->ticket, out, red) && threadIdx.x == 0) {
+    if (!first) sc->beta = (out[0] - out[1]) / sc->rz;
+    sc->rz = out[0];
+  }
+}
+
+// start: r = b - Ax ; rf = (float) r ; rr, bb, tolerance
+template <typename T, typename TB>
+__global__ void __launch_bounds__(256)
+k_cg_start_fdm(int64_t n, const TB* __restrict__ b, const T* __restrict__ Ax,
+               T* __restrict__ r, float* __restrict__ rf, double* partials, CgScalars* sc,
+               double rtol) {
+  __shared__ double red[32];
+  double rr = 0.0, bb = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    T ri = (T)b[i] - Ax[i];
+    r[i] = ri;
+    if (rf) rf[i] = (float)ri;
+    rr += (double)(ri * ri);
+    bb += (double)b[i] * (double)b[i];
+  }
+  double s1 = block_sum(rr, red);
+  double s2 = block_sum(bb, red);
+  double vals[2] = {s1, s2};
+  double out[2];
+  if (last_block_reduce(partials, 2, vals, &sc->ticket, out, red) && threadIdx.x == 0) {
+    sc->rr = out[0];
+    sc->bb = out[1];
+    double bbv = out[1] > 0.0 ? out[1] : 1.0;
+    sc->tol2 = rtol * rtol * bbv;
+    sc->it = 0;
+    sc->done = out[0] <= sc->tol2 ? 1 : 0;
+    sc->beta = 0.0;
+  }
+}
+
 // inverse diagonal of A: cM Mx_ii My_jj Mz_kk + cKx Kx_ii My_jj Mz_kk + ...
 template <int K, typename T>
 __global__ void k_dinv(MeshDev m, const double* __restrict__ bands, double cM, double cKx,
@@ -678,12 +768,96 @@ static cudaError_t cg_solve(const MeshDev& m, const T* bands, const double* coef
   return cudaSuccess;
 }
 
+// PCG with the FDM preconditioner.  T = vector precision; the preconditioner
+// always runs in FP32 (rf: FP32 copy of r when T = double, else r itself).
+template <typename T, typename TX_, typename TB>
+static cudaError_t cg_solve_fdm(const MeshDev& m, const T* bands, const double* coef,
+                                const TB* b, TX_* x, const T* x_as_T, double rtol, int maxit,
+                                T* r, T* z, T* zn, T* p0, T* p1, T* Ap, float* rf, float* zf,
+                                FdmPlan* fdm, double* partials, CgScalars* sc,
+                                cudaStream_t s, int* iters, double* relres, Timer* tm,
+                                bool x_is_zero) {
+  cudaError_t e;
+  int64_t n = m.n_nodes;
+  int vb = vec_blocks(n);
+  const int op_stage = sizeof(T) == 8 ? kStageOp64 : kStageOp32;
+  const bool conv = sizeof(T) == 8;  // FP32 copies needed for the preconditioner
+  float* rin = conv ? rf : reinterpret_cast<float*>(r);
+  if (x_is_zero) {
+    if ((e = cudaMemsetAsync(Ap, 0, sizeof(T) * n, s)) != cudaSuccess) return e;
+  } else {
+    if (tm) tm->begin(op_stage, s);
+    if ((e = apply_t<T>(m, bands, coef, x_as_T, Ap, s)) != cudaSuccess) return e;
+    if (tm) tm->end(op_stage, s);
+  }
+  k_cg_start_fdm<T, TB><<<vb, 256, 0, s>>>(n, b, Ap, r, conv ? rf : nullptr, partials, sc, rtol);
+  count_launches(1);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // z = P^-1 r
+  float* zout = conv ? zf : reinterpret_cast<float*>(z);
+  if ((e = fdm_apply(fdm, rin, zout, s)) != cudaSuccess) return e;
+  k_cg_dot_fdm<T><<<vb, 256, 0, s>>>(n, r, conv ? zf : nullptr, z, z, partials, sc, 1, 1);
+  count_launches(1);
+  T* pc = p0;
+  T* pn = p1;
+  T* zc = z;   // current preconditioned residual
+  T* zo = zn;  // spare buffer
+  CgScalars hs;
+  if ((e = cudaMemcpyAsync(&hs, sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return e;
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+  int it = 0;
+  while (!hs.done && it < maxit) {
+    int first = it == 0;
+    if (tm) tm->begin(op_stage, s);
+    if ((e = cg_apply_t<T>(m, bands, coef, zc, pc, pn, Ap, partials, sc, first, s)) !=
+        cudaSuccess)
+      return e;
+    if (tm) tm->end(op_stage, s);
+    k_cg_update_fdm<T, TX_><<<vb, 256, 0, s>>>(n, x, r, pn, Ap, conv ? rf : nullptr, partials,
+                                               sc, maxit);
+    count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    ++it;
+    if ((e = cudaMemcpyAsync(&hs, sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s)) !=
+        cudaSuccess)
+      return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    if (hs.done) break;
+    // z_new = P^-1 r, beta
+    float* zo_f = conv ? zf : reinterpret_cast<float*>(zo);
+    if ((e = fdm_apply(fdm, rin, zo_f, s)) != cudaSuccess) return e;
+    k_cg_dot_fdm<T><<<vb, 256, 0, s>>>(n, r, conv ? zf : nullptr, zc, zo, partials, sc, 0, 0);
+    count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    T* t = zc;
+    zc = zo;
+    zo = t;
+    t = pc;
+    pc = pn;
+    pn = t;
+  }
+  *iters = hs.it;
+  double bb = hs.bb > 0 ? hs.bb : 1.0;
+  *relres = std::sqrt(hs.rr / bb);
+  return cudaSuccess;
+}
+
 cudaError_t run_cg64(const MeshDev& m, const double* bands, const double* coef,
                      const double* b, double* x, double rtol, int maxit, CgWork& w,
                      cudaStream_t s, int* iters_host, double* relres_host, int* converged) {
   cudaError_t e;
-  if ((e = make_dinv<double>(m, bands, coef, w.dinv, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(w.sc, 0, sizeof(CgScalars), s)) != cudaSuccess) return e;
+  if (w.fdm) {
+    e = cg_solve_fdm<double, double, double>(m, bands, coef, b, x, x, rtol, maxit, w.r, w.z,
+                                             w.zn, w.p0, w.p1, w.Ap, w.r32, w.z32, w.fdm,
+                                             w.partials, w.sc, s, iters_host, relres_host,
+                                             w.timer, false);
+    if (e != cudaSuccess) return e;
+    *converged = *relres_host <= rtol;
+    return cudaSuccess;
+  }
+  if ((e = make_dinv<double>(m, bands, coef, w.dinv, s)) != cudaSuccess) return e;
   e = cg_solve<double, double, double>(m, bands, coef, b, x, x, rtol, maxit, w.r, w.z, w.p0,
                                        w.p1, w.Ap, w.dinv, w.partials, w.sc, s, iters_host,
                                        relres_host, w.timer);
@@ -699,7 +873,7 @@ cudaError_t run_cg_mixed(const MeshDev& m, const double* bands64, const float* b
   cudaError_t e;
   int64_t n = m.n_nodes;
   int vb = vec_blocks(n);
-  if ((e = make_dinv<float>(m, bands64, coef, w.dinv32, s)) != cudaSuccess) return e;
+  if (!w.fdm && (e = make_dinv<float>(m, bands64, coef, w.dinv32, s)) != cudaSuccess) return e;
   int total_it = 0, outer = 0;
   double relres = 1.0;
   const int max_outer = 8;
@@ -723,14 +897,20 @@ cudaError_t run_cg_mixed(const MeshDev& m, const double* bands64, const float* b
     // FP32 correction solve A d = r / |r|
     double rn = std::sqrt(hs.rr);
     double scale = rn > 0 ? 1.0 / rn : 1.0;
-    k_to_f32<<<vb, 256, 0, s>>>(n, w.r, scale, w.r32, w.d32);
+    k_to_f32<<<vb, 256, 0, s>>>(n, w.r, scale, w.rin32, w.d32);
     count_launches(1);
     if ((e = cudaMemsetAsync(w.sc, 0, sizeof(CgScalars), s)) != cudaSuccess) return e;
     int it = 0;
     double rr = 0;
-    e = cg_solve<float, float, float>(m, bands32, coef, w.r32, w.d32, w.d32, inner_rtol,
-                                      maxit - total_it, w.r32 + 0 * n, w.z32, w.q0, w.q1,
-                                      w.Aq, w.dinv32, w.partials, w.sc, s, &it, &rr, w.timer);
+    if (w.fdm)
+      e = cg_solve_fdm<float, float, float>(m, bands32, coef, w.rin32, w.d32, w.d32, inner_rtol,
+                                            maxit - total_it, w.r32, w.z32, w.zn32, w.q0, w.q1,
+                                            w.Aq, nullptr, nullptr, w.fdm, w.partials, w.sc, s,
+                                            &it, &rr, w.timer, true);
+    else
+      e = cg_solve<float, float, float>(m, bands32, coef, w.rin32, w.d32, w.d32, inner_rtol,
+                                        maxit - total_it, w.r32, w.z32, w.q0, w.q1, w.Aq,
+                                        w.dinv32, w.partials, w.sc, s, &it, &rr, w.timer);
     if (e != cudaSuccess) return e;
     total_it += it;
     k_add_scaled<<<vb, 256, 0, s>>>(n, x, w.d32, rn);

@@ -56,13 +56,17 @@ __device__ __forceinline__ float ff_two_prod_sum(float a, float b_hi, float b_lo
 }
 
 __device__ __forceinline__ double lens64(double R, double r, double d2) {
-  // intersection volume of spheres of radii R, r at squared distance d2 < (R+r)^2
+  // intersection volume of spheres of radii R, r at squared distance d2 < (R+r)^2:
+  // pi s^2 (d^2 + 2 d (R+r) - 3 (R-r)^2) / (12 d), s = R + r - d, written with
+  // y = 1/d from one reciprocal square root (d = d2 y) to spare the FP64
+  // square root and division
   double dm = R - r;
   double mn = R < r ? R : r;
-  double d = sqrt(d2);
-  if (d <= fabs(dm)) return (4.0 / 3.0 * kPi) * mn * mn * mn;
+  if (d2 <= dm * dm) return (4.0 / 3.0 * kPi) * mn * mn * mn;
+  double y = rsqrt(d2);
+  double d = d2 * y;
   double s = (R + r) - d;
-  return kPi * s * s * (d2 + 2.0 * d * (R + r) - 3.0 * dm * dm) / (12.0 * d);
+  return (kPi / 12.0) * s * s * (d + 2.0 * (R + r) - 3.0 * dm * dm * y);
 }
 
 __device__ __forceinline__ float lens32(float R, float r, float d2) {
@@ -86,6 +90,7 @@ __device__ __forceinline__ void neumaier(float& s, float& c, float v) {
 
 template <int K, bool FP64>
 struct QcmSmem {
+  float qrel[(K + 1) * (K + 1) * (K + 1)][3];  // Gauss point minus element centre
   float4 cand[kQcmWarps][kQcmChunk];     // rel. position (to element centre), radius
   int32_t cslot[kQcmWarps][kQcmChunk];   // sorted slot
   int32_t queue[kQcmWarps][64];
@@ -103,6 +108,10 @@ k_qcm(MeshDev m, QcmParams P, BinDev b, const int32_t* __restrict__ bin_start,
   constexpr int Q = NQ * NQ * NQ;
   __shared__ QcmSmem<K, FP64> sm;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // per-lane quadrature offsets are read with lane-varying indices: keep them
+  // in shared memory (the kernel-parameter bank would serialise them)
+  for (int t = threadIdx.x; t < Q * 3; t += blockDim.x) sm.qrel[t / 3][t % 3] = P.qrel[t / 3][t % 3];
+  __syncthreads();
   const int64_t e = blockIdx.x * (int64_t)kQcmWarps + warp;
   if (e >= m.E) return;  // whole warp leaves together
   const unsigned FULL = 0xffffffffu;
@@ -174,7 +183,7 @@ k_qcm(MeshDev m, QcmParams P, BinDev b, const int32_t* __restrict__ bin_start,
         v64 = lens64(P.R, pj.w, d2);
       } else {
         float4 cj = cand[j];
-        float dx = cj.x - P.qrel[q][0], dy = cj.y - P.qrel[q][1], dz = cj.z - P.qrel[q][2];
+        float dx = cj.x - sm.qrel[q][0], dy = cj.y - sm.qrel[q][1], dz = cj.z - sm.qrel[q][2];
         v32 = lens32(R32, cj.w, dx * dx + dy * dy + dz * dz);
       }
       if (want_ids) pid = perm[cslot[j]];
@@ -206,7 +215,7 @@ k_qcm(MeshDev m, QcmParams P, BinDev b, const int32_t* __restrict__ bin_start,
         j = idx / Q;
         q = idx - j * Q;
         float4 cj = cand[j];
-        float dx = cj.x - P.qrel[q][0], dy = cj.y - P.qrel[q][1], dz = cj.z - P.qrel[q][2];
+        float dx = cj.x - sm.qrel[q][0], dy = cj.y - sm.qrel[q][1], dz = cj.z - sm.qrel[q][2];
         float d2 = dx * dx + dy * dy + dz * dz;
         float c = R32 + cj.w;
         float c2 = c * c;

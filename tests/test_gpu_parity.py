@@ -189,20 +189,24 @@ def test_rhs_and_operator(c):
     assert np.max(np.abs(host(y) - O.apply(m, L2, xv))) <= 1e-12 * np.max(np.abs(O.apply(m, L2, xv)))
 
 
+@pytest.mark.parametrize("precond", [0, 1])
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("c", CASES[:4])
-def test_projection(c, precision):
+def test_projection(c, precision, precond):
     case = _case(*c)
     m = _mesh(case)
     rng = np.random.default_rng(c[0] + 1)
     eps_q = 0.3 + 0.7 * rng.random((m.n_elem, m.Q))
     L2 = case["params"]["l2_smoothing"]
-    with _ctx(case, precision=precision, cg_rtol=1e-13) as ctx:
+    with _ctx(case, precision=precision, cg_rtol=1e-13, cg_precond=precond) as ctx:
         x = _zeros(m.n_nodes())
         cf.cfdem_project(ctx.h, dev(eps_q), x)
         cf.cfdem_synchronize(ctx.h)
         st = ctx.stats()
         assert st.converged == 1 and st.cg_relres <= 1e-13
+        assert st.precond == precond
+        if precond == 1 and precision == 0:
+            assert st.cg_iterations <= 8     # an exact inverse up to FP32 rounding
     ref = O.fdm_solve(m, L2, O.rhs(m, eps_q))
     assert rel_err(host(x), ref) <= 1e-10
 
@@ -300,12 +304,14 @@ def bed():
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-def test_full_size_q2_bed(bed, precision):
+@pytest.mark.parametrize("precond", [1, 0])
+def test_full_size_q2_bed(bed, precision, precond):
     """The Q2 32x32x128 mesh with 100,000 spheres at the bench launch
     configuration: QCM neighbour counts bit-exact, every output compared."""
     import torch
     w, m = bed
-    prm = dict(w["params"], precision=precision, max_radius=float(w["r"].max()))
+    prm = dict(w["params"], precision=precision, max_radius=float(w["r"].max()),
+               cg_precond=precond)
     n = w["x"].shape[0]
     with cf.Context(w["origin"], w["extent"], w["n_el"], w["k"], prm) as ctx:
         eps = _zeros(m.n_elem, m.Q)
