@@ -220,6 +220,7 @@ __device__ __forceinline__ double apply_tile(const MeshDev& m, const T* __restri
   const T* bKz = bMz + (size_t)nz * W;
 
   // load with halo
+  int nonzero = 0;
   for (int t = threadIdx.x; t < TL::NX; t += blockDim.x) {
     int lx = t % TL::XW, ly = (t / TL::XW) % TL::YW, lz = t / (TL::XW * TL::YW);
     int gx = x0 + lx - H, gy = y0 + ly - H, gz = z0 + lz - H;
@@ -234,8 +235,17 @@ __device__ __forceinline__ double apply_tile(const MeshDev& m, const T* __restri
       }
     }
     X[t] = v;
+    nonzero |= (v != (T)0);
   }
-  __syncthreads();
+  // a tile whose input (halo included) is zero has a zero image: skip the
+  // passes (a cold start of the projection begins with x = 0)
+  if (!__syncthreads_or(nonzero)) {
+    for (int t = threadIdx.x; t < TX * TY * TZ; t += blockDim.x) {
+      int gx = x0 + t % TX, gy = y0 + (t / TX) % TY, gz = z0 + t / (TX * TY);
+      if (gx < nx && gy < ny && gz < nz) y[gx + (int64_t)nx * gy + sxy * gz] = (T)0;
+    }
+    return 0.0;
+  }
   // z pass
   for (int t = threadIdx.x; t < TL::NT; t += blockDim.x) {
     int lx = t % TL::XW, ly = (t / TL::XW) % TL::YW, lz = t / (TL::XW * TL::YW);

@@ -90,15 +90,151 @@ __device__ __forceinline__ void neumaier(float& s, float& c, float v) {
 
 template <int K, bool FP64>
 struct QcmSmem {
-  float qrel[(K + 1) * (K + 1) * (K + 1)][3];  // Gauss point minus element centre
-  float4 cand[kQcmWarps][kQcmChunk];     // rel. position (to element centre), radius
-  int32_t cslot[kQcmWarps][kQcmChunk];   // sorted slot
-  int32_t queue[kQcmWarps][64];
-  double xq[kQcmWarps][FP64 ? (K + 1) * (K + 1) * (K + 1) : 1][3];
+  static constexpr int Q = (K + 1) * (K + 1) * (K + 1);
+  float4 qrel[Q];                          // Gauss point minus element centre
+  float4 buf[kQcmWarps][64];               // culled candidates not yet tested
+  int32_t bslot[kQcmWarps][64];            // their sorted slots
+  float4 grp[kQcmWarps][32];               // the group under test (one per lane)
+  int32_t gslot[kQcmWarps][32];
+  int32_t queue[kQcmWarps][64];            // hits (lane of the group << 6) | q, q-sorted
+  float acc[kQcmWarps][Q], cmp[kQcmWarps][Q];       // mixed: Neumaier sums
+  double acc64[kQcmWarps][FP64 ? Q : 1];            // FP64 sums
+  int32_t cnt[kQcmWarps][Q];
+  long long ids[kQcmWarps][Q];
+  double xq[kQcmWarps][FP64 ? Q : 1][3];            // FP64 Gauss points
+  P4 g64[kQcmWarps][FP64 ? 32 : 1];                 // FP64 positions of the group
 };
 
+struct QcmWarp {
+  int warp, lane;
+  unsigned lt_mask;
+  double R;
+  float R32, band;
+  bool want_ids;
+};
+
+// Evaluate the first cnt queued hits (q-sorted) and add each quadrature
+// point's share with one segmented warp scan; the last lane of a segment
+// updates that point's sum, so every sum is accumulated in a fixed order.
 template <int K, bool FP64>
-__global__ void __launch_bounds__(kQcmWarps * 32)
+__device__ __forceinline__ void qcm_flush(QcmSmem<K, FP64>& sm, const QcmWarp& w, int cnt,
+                                          const int32_t* __restrict__ perm) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = w.lane, wp = w.warp;
+  int q = -1 - lane;  // distinct sentinels for idle lanes
+  double v64 = 0.0;
+  float v32 = 0.f;
+  long long id = 0;
+  int one = 0;
+  if (lane < cnt) {
+    int pk = sm.queue[wp][lane];
+    q = pk & 63;
+    int j = pk >> 6;
+    one = 1;
+    if (FP64) {
+      P4 pj = sm.g64[wp][j];
+      double dx = __dsub_rn(pj.x, sm.xq[wp][q][0]);
+      double dy = __dsub_rn(pj.y, sm.xq[wp][q][1]);
+      double dz = __dsub_rn(pj.z, sm.xq[wp][q][2]);
+      double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+      v64 = lens64(w.R, pj.w, d2);
+    } else {
+      float4 cj = sm.grp[wp][j];
+      float4 qq = sm.qrel[q];
+      float dx = cj.x - qq.x, dy = cj.y - qq.y, dz = cj.z - qq.z;
+      v32 = lens32(w.R32, cj.w, dx * dx + dy * dy + dz * dz);
+    }
+    if (w.want_ids) id = perm[sm.gslot[wp][j]];
+  }
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    int qu = __shfl_up_sync(FULL, q, off);
+    int nu = __shfl_up_sync(FULL, one, off);
+    double vu64 = FP64 ? __shfl_up_sync(FULL, v64, off) : 0.0;
+    float vu32 = FP64 ? 0.f : __shfl_up_sync(FULL, v32, off);
+    long long iu = w.want_ids ? __shfl_up_sync(FULL, id, off) : 0;
+    if (lane >= off && qu == q) {
+      one += nu;
+      if (FP64) v64 += vu64; else v32 += vu32;
+      id += iu;
+    }
+  }
+  int qn = __shfl_down_sync(FULL, q, 1);
+  bool last = lane < cnt && (lane == cnt - 1 || qn != q);
+  if (last) {
+    if (FP64) {
+      sm.acc64[wp][q] += v64;
+    } else {
+      neumaier(sm.acc[wp][q], sm.cmp[wp][q], v32);
+    }
+    sm.cnt[wp][q] += one;
+    sm.ids[wp][q] += id;
+  }
+  __syncwarp();
+}
+
+// test the cnt (<= 32) buffered candidates against every quadrature point
+template <int K, bool FP64>
+__device__ __forceinline__ void qcm_group(QcmSmem<K, FP64>& sm, const QcmWarp& w, int cnt,
+                                          const double* __restrict__ xs64,
+                                          const int32_t* __restrict__ perm) {
+  constexpr int Q = QcmSmem<K, FP64>::Q;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = w.lane, wp = w.warp;
+  const bool valid = lane < cnt;
+  float4 my = make_float4(0.f, 0.f, 0.f, 0.f);
+  int myslot = 0;
+  if (valid) {
+    my = sm.buf[wp][lane];
+    myslot = sm.bslot[wp][lane];
+    sm.grp[wp][lane] = my;
+    sm.gslot[wp][lane] = myslot;
+    if (FP64) sm.g64[wp][lane] = reinterpret_cast<const P4*>(xs64)[myslot];
+  }
+  __syncwarp();
+  const float c = w.R32 + my.w;
+  const float c2 = c * c;
+  const float c2_in = c2 / w.band, c2_out = c2 * w.band;
+  int qn = 0;
+  for (int q = 0; q < Q; ++q) {
+    float4 qq = sm.qrel[q];
+    float dx = my.x - qq.x, dy = my.y - qq.y, dz = my.z - qq.z;
+    float d2 = dx * dx + dy * dy + dz * dz;
+    bool hit;
+    if (FP64) {
+      hit = valid && d2 < c2_in;
+      if (valid && d2 >= c2_in && d2 <= c2_out) {  // inside the band: exact FP64 predicate
+        P4 pj = sm.g64[wp][lane];
+        double ddx = __dsub_rn(pj.x, sm.xq[wp][q][0]);
+        double ddy = __dsub_rn(pj.y, sm.xq[wp][q][1]);
+        double ddz = __dsub_rn(pj.z, sm.xq[wp][q][2]);
+        double dd2 =
+            __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
+        double cc = __dadd_rn(w.R, pj.w);
+        hit = dd2 < __dmul_rn(cc, cc);
+      }
+    } else {
+      hit = valid && d2 < c2;
+    }
+    unsigned mask = __ballot_sync(FULL, hit);
+    if (hit) sm.queue[wp][qn + __popc(mask & w.lt_mask)] = (lane << 6) | q;
+    qn += __popc(mask);
+    if (qn >= 32) {
+      __syncwarp();
+      qcm_flush<K, FP64>(sm, w, 32, perm);
+      int rest = qn - 32;
+      int tmp = lane < rest ? sm.queue[wp][32 + lane] : 0;
+      __syncwarp();
+      if (lane < rest) sm.queue[wp][lane] = tmp;
+      qn = rest;
+    }
+    __syncwarp();
+  }
+  if (qn > 0) qcm_flush<K, FP64>(sm, w, qn, perm);
+}
+
+template <int K, bool FP64>
+__global__ void __launch_bounds__(kQcmWarps * 32, 6)
 k_qcm(MeshDev m, QcmParams P, BinDev b, const int32_t* __restrict__ bin_start,
       const int32_t* __restrict__ perm, const double* __restrict__ xs64,
       const float* __restrict__ xs32, const DevStatus* __restrict__ st,
@@ -107,162 +243,70 @@ k_qcm(MeshDev m, QcmParams P, BinDev b, const int32_t* __restrict__ bin_start,
   constexpr int NQ = K + 1;
   constexpr int Q = NQ * NQ * NQ;
   __shared__ QcmSmem<K, FP64> sm;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // per-lane quadrature offsets are read with lane-varying indices: keep them
-  // in shared memory (the kernel-parameter bank would serialise them)
-  for (int t = threadIdx.x; t < Q * 3; t += blockDim.x) sm.qrel[t / 3][t % 3] = P.qrel[t / 3][t % 3];
-  __syncthreads();
-  const int64_t e = blockIdx.x * (int64_t)kQcmWarps + warp;
-  if (e >= m.E) return;  // whole warp leaves together
   const unsigned FULL = 0xffffffffu;
-  const unsigned lt_mask = (1u << lane) - 1u;
+  QcmWarp w;
+  w.warp = threadIdx.x >> 5;
+  w.lane = threadIdx.x & 31;
+  w.lt_mask = (1u << w.lane) - 1u;
+  w.R = P.R;
+  w.R32 = P.R32;
+  w.band = 1.0f + P.delta;
+  w.want_ids = nb_idsum != nullptr;
+  const int lane = w.lane, wp = w.warp;
+  for (int t = threadIdx.x; t < Q; t += blockDim.x)
+    sm.qrel[t] = make_float4(P.qrel[t][0], P.qrel[t][1], P.qrel[t][2], 0.f);
+  __syncthreads();
+  const int64_t e = blockIdx.x * (int64_t)kQcmWarps + wp;
+  if (e >= m.E) return;  // whole warp leaves together
   const int ex = (int)(e % m.ne[0]);
   const int ey = (int)((e / m.ne[0]) % m.ne[1]);
   const int ez = (int)(e / ((int64_t)m.ne[0] * m.ne[1]));
 
-  // element centre relative to the mesh origin, float-float
-  float c_hi[3], c_lo[3];
-  c_hi[0] = ff_two_prod_sum((float)ex + 0.5f, P.hx_hi, P.hx_lo, &c_lo[0]);
-  c_hi[1] = ff_two_prod_sum((float)ey + 0.5f, P.hy_hi, P.hy_lo, &c_lo[1]);
-  c_hi[2] = ff_two_prod_sum((float)ez + 0.5f, P.hz_hi, P.hz_lo, &c_lo[2]);
-  const float hh[3] = {0.5f * P.hx, 0.5f * P.hy, 0.5f * P.hz};
-
-  // FP64 Gauss point coordinates, exactly as the definition rounds them
-  if (FP64) {
-    for (int q = lane; q < Q; q += 32) {
+  for (int q = lane; q < Q; q += 32) {
+    sm.acc[wp][q] = 0.f;
+    sm.cmp[wp][q] = 0.f;
+    sm.cnt[wp][q] = 0;
+    sm.ids[wp][q] = 0;
+    if (FP64) {
+      sm.acc64[wp][q] = 0.0;
       int qx = q % NQ, qy = (q / NQ) % NQ, qz = q / (NQ * NQ);
-      sm.xq[warp][q][0] = __dadd_rn(m.x0[0], __dmul_rn(m.h[0], __dadd_rn((double)ex, P.g[qx])));
-      sm.xq[warp][q][1] = __dadd_rn(m.x0[1], __dmul_rn(m.h[1], __dadd_rn((double)ey, P.g[qy])));
-      sm.xq[warp][q][2] = __dadd_rn(m.x0[2], __dmul_rn(m.h[2], __dadd_rn((double)ez, P.g[qz])));
+      // FP64 Gauss point coordinates, rounded exactly as the definition
+      sm.xq[wp][q][0] = __dadd_rn(m.x0[0], __dmul_rn(m.h[0], __dadd_rn((double)ex, P.g[qx])));
+      sm.xq[wp][q][1] = __dadd_rn(m.x0[1], __dmul_rn(m.h[1], __dadd_rn((double)ey, P.g[qy])));
+      sm.xq[wp][q][2] = __dadd_rn(m.x0[2], __dmul_rn(m.h[2], __dadd_rn((double)ez, P.g[qz])));
     }
   }
-
+  // element centre relative to the mesh origin, float-float
+  float chx, clx, chy, cly, chz, clz;
+  chx = ff_two_prod_sum((float)ex + 0.5f, P.hx_hi, P.hx_lo, &clx);
+  chy = ff_two_prod_sum((float)ey + 0.5f, P.hy_hi, P.hy_lo, &cly);
+  chz = ff_two_prod_sum((float)ez + 0.5f, P.hz_hi, P.hz_lo, &clz);
+  const float hhx = 0.5f * P.hx, hhy = 0.5f * P.hy, hhz = 0.5f * P.hz;
   const double rmax = __longlong_as_double((long long)st->rmax_bits);
   const float cut = (float)(P.R + rmax) * (1.0f + 1e-5f);
-  const float R32 = P.R32;
-  const float band = 1.0f + P.delta;
-
   // bin range per axis (conservative)
-  int blo[3], bhi[3];
-  for (int a = 0; a < 3; ++a) {
-    float lo = (c_hi[a] - hh[a] - cut) * P.inv_be[a];
-    float hi = (c_hi[a] + hh[a] + cut) * P.inv_be[a];
-    int l = (int)floorf(lo - 1e-3f), h = (int)floorf(hi + 1e-3f);
-    blo[a] = l < 0 ? 0 : (l > b.nb[a] - 1 ? b.nb[a] - 1 : l);
-    bhi[a] = h < 0 ? 0 : (h > b.nb[a] - 1 ? b.nb[a] - 1 : h);
+  int bx0, bx1, by0, by1, bz0, bz1;
+  {
+    int l = (int)floorf((chx - hhx - cut) * P.inv_be[0] - 1e-3f);
+    int h = (int)floorf((chx + hhx + cut) * P.inv_be[0] + 1e-3f);
+    bx0 = min(max(l, 0), b.nb[0] - 1);
+    bx1 = min(max(h, 0), b.nb[0] - 1);
+    l = (int)floorf((chy - hhy - cut) * P.inv_be[1] - 1e-3f);
+    h = (int)floorf((chy + hhy + cut) * P.inv_be[1] + 1e-3f);
+    by0 = min(max(l, 0), b.nb[1] - 1);
+    by1 = min(max(h, 0), b.nb[1] - 1);
+    l = (int)floorf((chz - hhz - cut) * P.inv_be[2] - 1e-3f);
+    h = (int)floorf((chz + hhz + cut) * P.inv_be[2] + 1e-3f);
+    bz0 = min(max(l, 0), b.nb[2] - 1);
+    bz1 = min(max(h, 0), b.nb[2] - 1);
   }
+  __syncwarp();
 
-  // per-lane accumulators: quadrature points q0 = lane, q1 = lane + 32
-  double acc64_0 = 0.0, acc64_1 = 0.0;
-  float acc0 = 0.f, cmp0 = 0.f, acc1 = 0.f, cmp1 = 0.f;
-  int cnt0 = 0, cnt1 = 0;
-  long long ids0 = 0, ids1 = 0;
-  const bool want_ids = nb_idsum != nullptr;
-  int qn = 0;  // queue fill (warp-uniform)
-
-  float4* cand = sm.cand[warp];
-  int32_t* cslot = sm.cslot[warp];
-  int32_t* queue = sm.queue[warp];
-
-  // evaluate the first cnt queued pairs and hand the volumes to their owners
-  auto flush = [&](int cnt) {
-    double v64 = 0.0;
-    float v32 = 0.f;
-    int q = 0;
-    long long pid = 0;
-    if (lane < cnt) {
-      int pk = queue[lane];
-      q = pk & 63;
-      int j = pk >> 6;
-      if (FP64) {
-        P4 pj = reinterpret_cast<const P4*>(xs64)[cslot[j]];
-        double dx = __dsub_rn(pj.x, sm.xq[warp][q][0]);
-        double dy = __dsub_rn(pj.y, sm.xq[warp][q][1]);
-        double dz = __dsub_rn(pj.z, sm.xq[warp][q][2]);
-        double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-        v64 = lens64(P.R, pj.w, d2);
-      } else {
-        float4 cj = cand[j];
-        float dx = cj.x - sm.qrel[q][0], dy = cj.y - sm.qrel[q][1], dz = cj.z - sm.qrel[q][2];
-        v32 = lens32(R32, cj.w, dx * dx + dy * dy + dz * dz);
-      }
-      if (want_ids) pid = perm[cslot[j]];
-    }
-    for (int t = 0; t < cnt; ++t) {
-      int qt = __shfl_sync(FULL, q, t);
-      long long it = want_ids ? __shfl_sync(FULL, pid, t) : 0;
-      if (FP64) {
-        double vt = __shfl_sync(FULL, v64, t);
-        if (qt == lane) { acc64_0 += vt; ++cnt0; ids0 += it; }
-        if (Q > 32 && qt == lane + 32) { acc64_1 += vt; ++cnt1; ids1 += it; }
-      } else {
-        float vt = __shfl_sync(FULL, v32, t);
-        if (qt == lane) { neumaier(acc0, cmp0, vt); ++cnt0; ids0 += it; }
-        if (Q > 32 && qt == lane + 32) { neumaier(acc1, cmp1, vt); ++cnt1; ids1 += it; }
-      }
-    }
-    __syncwarp();
-  };
-
-  // test all (q, candidate) pairs of the staged chunk
-  auto process_chunk = [&](int nc) {
-    const int total = nc * Q;
-    for (int base = 0; base < total; base += 32) {
-      int idx = base + lane;
-      bool hit = false;
-      int j = 0, q = 0;
-      if (idx < total) {
-        j = idx / Q;
-        q = idx - j * Q;
-        float4 cj = cand[j];
-        float dx = cj.x - sm.qrel[q][0], dy = cj.y - sm.qrel[q][1], dz = cj.z - sm.qrel[q][2];
-        float d2 = dx * dx + dy * dy + dz * dz;
-        float c = R32 + cj.w;
-        float c2 = c * c;
-        if (FP64) {
-          if (d2 * band < c2) {
-            hit = true;
-          } else if (d2 > c2 * band) {
-            hit = false;
-          } else {  // inside the band: exact FP64 predicate
-            P4 pj = reinterpret_cast<const P4*>(xs64)[cslot[j]];
-            double ddx = __dsub_rn(pj.x, sm.xq[warp][q][0]);
-            double ddy = __dsub_rn(pj.y, sm.xq[warp][q][1]);
-            double ddz = __dsub_rn(pj.z, sm.xq[warp][q][2]);
-            double dd2 =
-                __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
-            double cc = __dadd_rn(P.R, pj.w);
-            hit = dd2 < __dmul_rn(cc, cc);
-          }
-        } else {
-          hit = d2 < c2;
-        }
-      }
-      unsigned mask = __ballot_sync(FULL, hit);
-      if (hit) queue[qn + __popc(mask & lt_mask)] = (j << 6) | q;
-      qn += __popc(mask);
-      __syncwarp();
-      if (qn >= 32) {
-        flush(32);
-        int rest = qn - 32;
-        int tmp = lane < rest ? queue[32 + lane] : 0;
-        __syncwarp();
-        if (lane < rest) queue[lane] = tmp;
-        __syncwarp();
-        qn = rest;
-      }
-    }
-    if (qn > 0) {
-      flush(qn);
-      qn = 0;
-    }
-  };
-
-  int nc = 0;
-  for (int bz = blo[2]; bz <= bhi[2]; ++bz) {
-    for (int by = blo[1]; by <= bhi[1]; ++by) {
+  int nb = 0;  // buffered culled candidates (warp-uniform)
+  for (int bz = bz0; bz <= bz1; ++bz) {
+    for (int by = by0; by <= by1; ++by) {
       int64_t row = (int64_t)b.nb[0] * (by + (int64_t)b.nb[1] * bz);
-      int s0 = bin_start[row + blo[0]], s1 = bin_start[row + bhi[0] + 1];
+      int s0 = bin_start[row + bx0], s1 = bin_start[row + bx1 + 1];
       for (int sb = s0; sb < s1; sb += 32) {
         int s = sb + lane;
         bool keep = false;
@@ -270,58 +314,59 @@ k_qcm(MeshDev m, QcmParams P, BinDev b, const int32_t* __restrict__ bin_start,
         if (s < s1) {
           const float4* p = reinterpret_cast<const float4*>(xs32) + 2 * (int64_t)s;
           float4 hi = p[0], lo = p[1];
-          rel.x = (hi.x - c_hi[0]) + (lo.x - c_lo[0]);
-          rel.y = (hi.y - c_hi[1]) + (lo.y - c_lo[1]);
-          rel.z = (hi.z - c_hi[2]) + (lo.z - c_lo[2]);
+          rel.x = (hi.x - chx) + (lo.x - clx);
+          rel.y = (hi.y - chy) + (lo.y - cly);
+          rel.z = (hi.z - chz) + (lo.z - clz);
           rel.w = hi.w;
-          float ox = fmaxf(fabsf(rel.x) - hh[0], 0.f);
-          float oy = fmaxf(fabsf(rel.y) - hh[1], 0.f);
-          float oz = fmaxf(fabsf(rel.z) - hh[2], 0.f);
-          float c = (R32 + rel.w) * band;
-          keep = ox * ox + oy * oy + oz * oz < c * c * band;
+          float ox = fmaxf(fabsf(rel.x) - hhx, 0.f);
+          float oy = fmaxf(fabsf(rel.y) - hhy, 0.f);
+          float oz = fmaxf(fabsf(rel.z) - hhz, 0.f);
+          float c = (w.R32 + rel.w) * w.band;
+          keep = ox * ox + oy * oy + oz * oz < c * c * w.band;
         }
         unsigned mask = __ballot_sync(FULL, keep);
         if (keep) {
-          int pos = nc + __popc(mask & lt_mask);
-          cand[pos] = rel;
-          cslot[pos] = s;
+          int pos = nb + __popc(mask & w.lt_mask);
+          sm.buf[wp][pos] = rel;
+          sm.bslot[wp][pos] = s;
         }
-        nc += __popc(mask);
+        nb += __popc(mask);
         __syncwarp();
-        if (nc > kQcmChunk - 32) {
-          process_chunk(nc);
-          nc = 0;
+        if (nb >= 32) {
+          qcm_group<K, FP64>(sm, w, 32, xs64, perm);
+          int rest = nb - 32;
+          float4 tb = make_float4(0.f, 0.f, 0.f, 0.f);
+          int ts = 0;
+          if (lane < rest) {
+            tb = sm.buf[wp][32 + lane];
+            ts = sm.bslot[wp][32 + lane];
+          }
+          __syncwarp();
+          if (lane < rest) {
+            sm.buf[wp][lane] = tb;
+            sm.bslot[wp][lane] = ts;
+          }
+          __syncwarp();
+          nb = rest;
         }
       }
     }
   }
-  if (nc > 0) process_chunk(nc);
+  if (nb > 0) qcm_group<K, FP64>(sm, w, nb, xs64, perm);
+  __syncwarp();
 
   // outputs
   const int64_t o = e * Q;
-  if (lane < Q) {
-    double eps;
+  for (int q = lane; q < Q; q += 32) {
     if (FP64) {
-      eps = 1.0 - acc64_0 * P.inv_vr;
-      if (eps64) eps64[o + lane] = eps;
+      if (eps64) eps64[o + q] = 1.0 - sm.acc64[wp][q] * P.inv_vr;
     } else {
-      float v = 1.0f - (acc0 + cmp0) * P.inv_vr32;
-      if (eps32) eps32[o + lane] = v;
-      if (eps64) eps64[o + lane] = (double)v;
+      float v = 1.0f - (sm.acc[wp][q] + sm.cmp[wp][q]) * P.inv_vr32;
+      if (eps32) eps32[o + q] = v;
+      if (eps64) eps64[o + q] = (double)v;
     }
-    if (nb_count) nb_count[o + lane] = cnt0;
-    if (nb_idsum) nb_idsum[o + lane] = ids0;
-  }
-  if (Q > 32 && lane + 32 < Q) {
-    if (FP64) {
-      if (eps64) eps64[o + lane + 32] = 1.0 - acc64_1 * P.inv_vr;
-    } else {
-      float v = 1.0f - (acc1 + cmp1) * P.inv_vr32;
-      if (eps32) eps32[o + lane + 32] = v;
-      if (eps64) eps64[o + lane + 32] = (double)v;
-    }
-    if (nb_count) nb_count[o + lane + 32] = cnt1;
-    if (nb_idsum) nb_idsum[o + lane + 32] = ids1;
+    if (nb_count) nb_count[o + q] = sm.cnt[wp][q];
+    if (nb_idsum) nb_idsum[o + q] = sm.ids[wp][q];
   }
 }
 
