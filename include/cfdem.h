@@ -94,7 +94,7 @@ typedef struct {
      * launches */
     double stage_ms[8];
     int64_t stage_calls[8];
-    int32_t timer_overflow;       /* 1 if more than 4096 pairs per stage were asked */
+    int32_t timer_overflow;       /* 1 if more than 1024 pairs per stage were asked */
     int64_t kernel_launches;      /* kernels launched by the library since set_timing */
     int32_t precond;              /* preconditioner in use: 0 Jacobi, 1 FDM */
 } cfdem_stats;

@@ -23,12 +23,16 @@ static std::atomic<long long> g_launches{0};
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
-void Timer::begin(int s, cudaStream_t st) {
-  if (!on) return;
-  if (!ev[s]) {
+void Timer::create() {
+  for (int s = 0; s < kStages; ++s) {
+    if (ev[s]) continue;
     ev[s] = new cudaEvent_t[2 * kCap];
     for (int i = 0; i < 2 * kCap; ++i) cudaEventCreate(&ev[s][i]);
   }
+}
+
+void Timer::begin(int s, cudaStream_t st) {
+  if (!on || !ev[s]) return;
   if (count[s] >= kCap) {
     overflow = true;
     return;
@@ -751,6 +755,7 @@ cfdem_status cfdem_set_timing(cfdem_t c, int enable) {
     c->timer.calls[s] = 0;
   }
   c->timer.overflow = false;
+  if (enable) c->timer.create();
   c->timer.on = enable != 0;
   c->launches_at_reset = launches_total();
   return CFDEM_OK;

@@ -8,8 +8,17 @@
 //   A^-1 = (Vz(x)Vy(x)Vx) D^-1 (Vz(x)Vy(x)Vx)^T,
 //   D = cM + cKx lam_x + cKy lam_y + cKz lam_z   (one value per node).
 // Applied in FP32 it is the inverse up to single-precision rounding, so the
-// conjugate gradients it preconditions converge in a few iterations.  The six
-// 1D transforms are plain dense GEMMs (cuBLAS SGEMM, FP32 math, no TF32).
+// conjugate gradients it preconditions converge in a few iterations.
+//
+// Two device forms:
+//  * slab form (default): only x and y are diagonalised.  For a mode (i, j)
+//    the z operator is the banded SPD matrix s_ij Mz + cKz Kz with s_ij = cM +
+//    cKx lam_x,i + cKy lam_y,j, factorised A = L D L^T on the host.  One
+//    kernel transforms each z-slab with Vx, Vy^T in shared memory, one solves
+//    the banded systems along z (one lane per mode), one transforms back:
+//    about 4 (nx + ny) + 6 k flops per node instead of 4 (nx + ny + nz).
+//  * dense form (slabs too large for shared memory): the six 1D transforms as
+//    plain dense GEMMs (cuBLAS SGEMM, FP32 math, no TF32).
 //
 // Host side: the 1D eigenproblems are solved once per mesh/parameter set:
 // Cholesky M = L L^T, C = L^-1 K L^-T, symmetric eigen-decomposition of C by
@@ -236,10 +245,178 @@ cublasStatus_t gemm_rm(cublasHandle_t h, int M, int N, int K, const float* A, lo
                                    sA, &zero, C, N, sC, batch);
 }
 
+// C[M x N] = A[M x K] B[K x N], all row-major in shared memory, 256
+// threads as a 16 x 16 grid, each owning a strided 5 x 5 set of outputs
+// (M, N <= 80 per pass; larger sizes loop over output tiles)
+__device__ __forceinline__ void smem_gemm(const float* A, int lda, const float* B, int ldb,
+                                          float* C, int ldc, int M, int N, int K) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (int m0 = 0; m0 < M; m0 += 80)
+    for (int n0 = 0; n0 < N; n0 += 80) {
+      float acc[5][5];
+#pragma unroll
+      for (int a = 0; a < 5; ++a)
+#pragma unroll
+        for (int b = 0; b < 5; ++b) acc[a][b] = 0.f;
+      for (int k = 0; k < K; ++k) {
+        float av[5], bv[5];
+#pragma unroll
+        for (int a = 0; a < 5; ++a) {
+          int r = m0 + ty + 16 * a;
+          av[a] = r < M ? A[r * lda + k] : 0.f;
+        }
+#pragma unroll
+        for (int b = 0; b < 5; ++b) {
+          int c = n0 + tx + 16 * b;
+          bv[b] = c < N ? B[k * ldb + c] : 0.f;
+        }
+#pragma unroll
+        for (int a = 0; a < 5; ++a)
+#pragma unroll
+          for (int b = 0; b < 5; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+      }
+#pragma unroll
+      for (int a = 0; a < 5; ++a)
+#pragma unroll
+        for (int b = 0; b < 5; ++b) {
+          int r = m0 + ty + 16 * a, c = n0 + tx + 16 * b;
+          if (r < M && c < N) C[r * ldc + c] = acc[a][b];
+        }
+    }
+}
+
+// forward (inverse = 0): out_z = Vy^T (in_z Vx); inverse (inverse = 1): out_z =
+// Vy (in_z Vx^T), for every z-slab; 256 threads per block, one slab per block
+__global__ void __launch_bounds__(256)
+k_fdm_slab(int nx, int ny, int nz, const float* __restrict__ Bx, const float* __restrict__ Ay,
+           const float* __restrict__ in, float* __restrict__ out, const int* __restrict__ done) {
+  if (done && *(volatile const int*)done) return;
+  extern __shared__ __align__(16) float fsm[];
+  const int plane = nx * ny;
+  float* X = fsm;                  // [ny][nx]
+  float* T = X + plane;            // [ny][nx]
+  float* MB = T + plane;           // [nx][nx]  right factor of the x transform
+  float* MA = MB + nx * nx;        // [ny][ny]  left factor of the y transform
+  for (int t = threadIdx.x; t < nx * nx; t += blockDim.x) MB[t] = Bx[t];
+  for (int t = threadIdx.x; t < ny * ny; t += blockDim.x) MA[t] = Ay[t];
+  for (int z = blockIdx.x; z < nz; z += gridDim.x) {
+    const float* src = in + (int64_t)z * plane;
+    for (int t = threadIdx.x; t < plane; t += blockDim.x) X[t] = src[t];
+    __syncthreads();
+    smem_gemm(X, nx, MB, nx, T, nx, ny, nx, nx);      // T = X Bx
+    __syncthreads();
+    smem_gemm(MA, ny, T, nx, X, nx, ny, nx, ny);      // X = Ay T
+    __syncthreads();
+    float* dst = out + (int64_t)z * plane;
+    for (int t = threadIdx.x; t < plane; t += blockDim.x) dst[t] = X[t];
+    __syncthreads();
+  }
+}
+
+// banded solves along z: for every mode m (x-y index of the transformed
+// slab) solve L D L^T w = t with the host factors; fac[z][0..k-1][mode] =
+// L(z, z-1-c), fac[z][k][mode] = 1 / D(z).  One lane per mode; the lines of
+// 32 modes and their factors are staged in shared memory.
+template <int K>
+__global__ void __launch_bounds__(256)
+k_fdm_zsolve(int nmodes, int nz, const float* __restrict__ fac, float* __restrict__ v,
+             const int* __restrict__ done) {
+  if (done && *(volatile const int*)done) return;
+  extern __shared__ __align__(16) float zsm[];
+  float* line = zsm;                  // [nz][32]
+  float* f = line + nz * 32;          // [nz][K+1][32]
+  const int m0 = blockIdx.x * 32;
+  const int lane = threadIdx.x & 31;
+  for (int t = threadIdx.x; t < nz * 32; t += blockDim.x) {
+    int z = t >> 5, l = t & 31, mode = m0 + l;
+    line[t] = mode < nmodes ? v[(int64_t)z * nmodes + mode] : 0.f;
+  }
+  for (int t = threadIdx.x; t < nz * (K + 1) * 32; t += blockDim.x) {
+    int l = t & 31, zc = t >> 5, mode = m0 + l;
+    f[t] = mode < nmodes ? fac[(int64_t)zc * nmodes + mode] : 0.f;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float w[K];  // last K solved values (forward)
+#pragma unroll
+    for (int c = 0; c < K; ++c) w[c] = 0.f;
+    for (int z = 0; z < nz; ++z) {  // L u = t
+      float u = line[z * 32 + lane];
+#pragma unroll
+      for (int c = 0; c < K; ++c) u -= f[(z * (K + 1) + c) * 32 + lane] * w[c];
+#pragma unroll
+      for (int c = K - 1; c > 0; --c) w[c] = w[c - 1];
+      w[0] = u;
+      line[z * 32 + lane] = u;
+    }
+#pragma unroll
+    for (int c = 0; c < K; ++c) w[c] = 0.f;
+    for (int z = nz - 1; z >= 0; --z) {  // L^T y = u / D
+      float y = line[z * 32 + lane] * f[(z * (K + 1) + K) * 32 + lane];
+#pragma unroll
+      for (int c = 0; c < K; ++c) {
+        int zz = z + 1 + c;
+        if (zz < nz) y -= f[(zz * (K + 1) + c) * 32 + lane] * w[c];
+      }
+#pragma unroll
+      for (int c = K - 1; c > 0; --c) w[c] = w[c - 1];
+      w[0] = y;
+      line[z * 32 + lane] = y;
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nz * 32; t += blockDim.x) {
+    int z = t >> 5, l = t & 31, mode = m0 + l;
+    if (mode < nmodes) v[(int64_t)z * nmodes + mode] = line[t];
+  }
+}
+
+// host LDL^T factors of s Mz + cKz Kz (bandwidth k) for every mode
+void band_ldlt_factors(int nz, int k, const std::vector<double>& Mz,
+                       const std::vector<double>& Kz, double cKz,
+                       const std::vector<double>& s_modes, std::vector<float>& fac) {
+  int nm = (int)s_modes.size();
+  fac.assign((size_t)nz * (k + 1) * nm, 0.f);
+  std::vector<double> L((size_t)nz * (k + 1)), D(nz);
+  for (int m = 0; m < nm; ++m) {
+    double s = s_modes[m];
+    auto A = [&](int i, int j) {
+      return s * Mz[(size_t)i * nz + j] + cKz * Kz[(size_t)i * nz + j];
+    };
+    for (int i = 0; i < nz; ++i) {
+      // L(i, i-1-c) for c = k-1 .. 0 (farther first), then D(i)
+      for (int c = k - 1; c >= 0; --c) {
+        int j = i - 1 - c;
+        double val = 0.0;
+        if (j >= 0) {
+          val = A(i, j);
+          for (int p = (i - k > 0 ? i - k : 0); p < j; ++p)
+            val -= L[(size_t)i * (k + 1) + (i - 1 - p)] * L[(size_t)j * (k + 1) + (j - 1 - p)] * D[p];
+          val /= D[j];
+        }
+        L[(size_t)i * (k + 1) + c] = val;
+      }
+      double d = A(i, i);
+      for (int p = (i - k > 0 ? i - k : 0); p < i; ++p) {
+        double l = L[(size_t)i * (k + 1) + (i - 1 - p)];
+        d -= l * l * D[p];
+      }
+      D[i] = d;
+      for (int c = 0; c < k; ++c)
+        fac[((size_t)i * (k + 1) + c) * nm + m] = (float)L[(size_t)i * (k + 1) + c];
+      fac[((size_t)i * (k + 1) + k) * nm + m] = (float)(1.0 / d);
+    }
+  }
+}
+
 }  // namespace
 
 struct FdmPlan {
   int n[3] = {0, 0, 0};
+  int k = 1;
+  bool slab = false;          // slab form (x, y diagonalised, banded z solves)
+  float* fac = nullptr;       // slab form: LDL^T factors [nz][k+1][nx*ny]
+  size_t slab_smem = 0, z_smem = 0;
   float* V[3] = {nullptr, nullptr, nullptr};   // V_a row-major
   float* VT[3] = {nullptr, nullptr, nullptr};  // V_a^T row-major
   float* dinv = nullptr;                       // 1 / D per node
@@ -255,6 +432,7 @@ void fdm_destroy(FdmPlan* p) {
   }
   if (p->dinv) cudaFree(p->dinv);
   if (p->tmp) cudaFree(p->tmp);
+  if (p->fac) cudaFree(p->fac);
   if (p->blas) cublasDestroy(p->blas);
   delete p;
 }
@@ -269,11 +447,17 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4],
       return cudaSuccess;
     }
   FdmPlan* p = new FdmPlan();
+  p->k = m.k;
+  for (int a = 0; a < 3; ++a) p->n[a] = m.nn[a];
+  const int nx = m.nn[0], ny = m.nn[1], nz = m.nn[2];
+  p->slab_smem = (2 * (size_t)nx * ny + (size_t)nx * nx + (size_t)ny * ny) * sizeof(float);
+  p->z_smem = (size_t)nz * 32 * (m.k + 2) * sizeof(float);
+  p->slab = p->slab_smem <= 200 * 1024 && p->z_smem <= 200 * 1024;
   std::vector<double> lam[3];
   cudaError_t e = cudaSuccess;
-  for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
+  const int naxes = p->slab ? 2 : 3;
+  for (int a = 0; a < naxes && e == cudaSuccess; ++a) {
     int n = m.nn[a];
-    p->n[a] = n;
     std::vector<double> M, K, V;
     assemble_1d(m.ne[a], m.k, t.Mh, M);
     assemble_1d(m.ne[a], m.k, t.Kh, K);
@@ -295,29 +479,58 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4],
       break;
     e = cudaMemcpy(p->VT[a], vt32.data(), vt32.size() * 4, cudaMemcpyHostToDevice);
   }
-  double* dl[3] = {nullptr, nullptr, nullptr};
-  for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
-    if ((e = cudaMalloc(&dl[a], lam[a].size() * 8)) != cudaSuccess) break;
-    e = cudaMemcpy(dl[a], lam[a].data(), lam[a].size() * 8, cudaMemcpyHostToDevice);
-  }
   int64_t nn = m.n_nodes;
-  if (e == cudaSuccess) e = cudaMalloc(&p->dinv, nn * 4);
   if (e == cudaSuccess) e = cudaMalloc(&p->tmp, nn * 4);
-  if (e == cudaSuccess) {
-    k_fdm_dinv<<<(unsigned)((nn + 255) / 256), 256>>>(m.nn[0], m.nn[1], m.nn[2], dl[0], dl[1],
-                                                       dl[2], coef[0], coef[1], coef[2],
-                                                       coef[3], p->dinv);
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess && p->slab) {
+    // banded LDL^T factors of s Mz + cKz Kz for every (x, y) mode
+    std::vector<double> Mz, Kz;
+    assemble_1d(m.ne[2], m.k, t.Mh, Mz);
+    assemble_1d(m.ne[2], m.k, t.Kh, Kz);
+    std::vector<double> smodes((size_t)nx * ny);
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i)
+        smodes[i + (size_t)nx * j] = coef[0] + coef[1] * lam[0][i] + coef[2] * lam[1][j];
+    std::vector<float> fac;
+    band_ldlt_factors(nz, m.k, Mz, Kz, coef[3], smodes, fac);
+    if ((e = cudaMalloc(&p->fac, fac.size() * 4)) == cudaSuccess)
+      e = cudaMemcpy(p->fac, fac.data(), fac.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_fdm_slab, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)p->slab_smem);
+    if (e == cudaSuccess) {
+      if (m.k == 1)
+        e = cudaFuncSetAttribute(k_fdm_zsolve<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)p->z_smem);
+      else if (m.k == 2)
+        e = cudaFuncSetAttribute(k_fdm_zsolve<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)p->z_smem);
+      else
+        e = cudaFuncSetAttribute(k_fdm_zsolve<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)p->z_smem);
+    }
+  } else if (e == cudaSuccess) {
+    double* dl[3] = {nullptr, nullptr, nullptr};
+    for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
+      if ((e = cudaMalloc(&dl[a], lam[a].size() * 8)) != cudaSuccess) break;
+      e = cudaMemcpy(dl[a], lam[a].data(), lam[a].size() * 8, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&p->dinv, nn * 4);
+    if (e == cudaSuccess) {
+      k_fdm_dinv<<<(unsigned)((nn + 255) / 256), 256>>>(nx, ny, nz, dl[0], dl[1], dl[2],
+                                                         coef[0], coef[1], coef[2], coef[3],
+                                                         p->dinv);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
+    for (int a = 0; a < 3; ++a)
+      if (dl[a]) cudaFree(dl[a]);
+    if (e == cudaSuccess && cublasCreate(&p->blas) != CUBLAS_STATUS_SUCCESS) {
+      *why = "cublasCreate failed";
+      fdm_destroy(p);
+      return cudaSuccess;
+    }
+    if (e == cudaSuccess) cublasSetMathMode(p->blas, CUBLAS_PEDANTIC_MATH);
   }
-  for (int a = 0; a < 3; ++a)
-    if (dl[a]) cudaFree(dl[a]);
-  if (e == cudaSuccess && cublasCreate(&p->blas) != CUBLAS_STATUS_SUCCESS) {
-    *why = "cublasCreate failed";
-    fdm_destroy(p);
-    return cudaSuccess;
-  }
-  if (e == cudaSuccess) cublasSetMathMode(p->blas, CUBLAS_PEDANTIC_MATH);
   if (e != cudaSuccess) {
     fdm_destroy(p);
     return e;
@@ -326,10 +539,27 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4],
   return cudaSuccess;
 }
 
-// z = A^-1 r (FP32), r is preserved.  Uses p->tmp.
-cudaError_t fdm_apply(FdmPlan* p, const float* r, float* z, cudaStream_t s) {
-  cublasSetStream(p->blas, s);
+// z = A^-1 r (FP32), r is preserved.  Uses p->tmp.  The slab-form kernels
+// return at once when *done is set (a converged CG), so iterations can be
+// queued without host round trips.
+cudaError_t fdm_apply(FdmPlan* p, const float* r, float* z, const int* done, cudaStream_t s) {
   int nx = p->n[0], ny = p->n[1], nz = p->n[2];
+  if (p->slab) {
+    int nblk = nz < 304 ? nz : 304;
+    k_fdm_slab<<<nblk, 256, p->slab_smem, s>>>(nx, ny, nz, p->V[0], p->VT[1], r, p->tmp, done);
+    int nm = nx * ny;
+    unsigned zb = (unsigned)((nm + 31) / 32);
+    if (p->k == 1)
+      k_fdm_zsolve<1><<<zb, 256, p->z_smem, s>>>(nm, nz, p->fac, p->tmp, done);
+    else if (p->k == 2)
+      k_fdm_zsolve<2><<<zb, 256, p->z_smem, s>>>(nm, nz, p->fac, p->tmp, done);
+    else
+      k_fdm_zsolve<3><<<zb, 256, p->z_smem, s>>>(nm, nz, p->fac, p->tmp, done);
+    k_fdm_slab<<<nblk, 256, p->slab_smem, s>>>(nx, ny, nz, p->VT[0], p->V[1], p->tmp, z, done);
+    count_launches(3);
+    return cudaGetLastError();
+  }
+  cublasSetStream(p->blas, s);
   long long plane = (long long)nx * ny;
   float* t = p->tmp;
   cublasStatus_t st;

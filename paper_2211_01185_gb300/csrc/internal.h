@@ -89,7 +89,7 @@ enum Stage {
 };
 
 struct Timer {
-  static constexpr int kCap = 4096;
+  static constexpr int kCap = 1024;
   bool on = false;
   cudaEvent_t* ev[kStages] = {};  // 2 * kCap events per stage, created on first use
   int count[kStages] = {};
@@ -100,6 +100,7 @@ struct Timer {
   void end(int s, cudaStream_t st);
   void collect();
   void release();
+  void create();  // allocate the events (outside any timed region)
 };
 
 // process-wide count of kernel launches made by the library
@@ -143,7 +144,7 @@ cudaError_t launch_apply64(const MeshDev& m, const double* bands, const double* 
 struct FdmPlan;
 cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4],
                        FdmPlan** out, const char** why);
-cudaError_t fdm_apply(FdmPlan* p, const float* r, float* z, cudaStream_t s);
+cudaError_t fdm_apply(FdmPlan* p, const float* r, float* z, const int* done, cudaStream_t s);
 void fdm_destroy(FdmPlan* p);
 
 struct CgWork {

@@ -805,7 +805,7 @@ static cudaError_t cg_solve_fdm(const MeshDev& m, const T* bands, const double* 
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // z = P^-1 r
   float* zout = conv ? zf : reinterpret_cast<float*>(z);
-  if ((e = fdm_apply(fdm, rin, zout, s)) != cudaSuccess) return e;
+  if ((e = fdm_apply(fdm, rin, zout, nullptr, s)) != cudaSuccess) return e;
   k_cg_dot_fdm<T><<<vb, 256, 0, s>>>(n, r, conv ? zf : nullptr, z, z, partials, sc, 1, 1);
   count_launches(1);
   T* pc = p0;
@@ -816,36 +816,42 @@ static cudaError_t cg_solve_fdm(const MeshDev& m, const T* bands, const double* 
   if ((e = cudaMemcpyAsync(&hs, sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return e;
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-  int it = 0;
-  while (!hs.done && it < maxit) {
-    int first = it == 0;
-    if (tm) tm->begin(op_stage, s);
-    if ((e = cg_apply_t<T>(m, bands, coef, zc, pc, pn, Ap, partials, sc, first, s)) !=
-        cudaSuccess)
-      return e;
-    if (tm) tm->end(op_stage, s);
-    k_cg_update_fdm<T, TX_><<<vb, 256, 0, s>>>(n, x, r, pn, Ap, conv ? rf : nullptr, partials,
-                                               sc, maxit);
-    count_launches(1);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    ++it;
+  // iterations are queued in chunks: every kernel of an iteration (operator,
+  // update, FDM transforms and solves, dot) returns at once on the device flag
+  // `done`, so only one host round trip per chunk is needed
+  const int chunk = sizeof(T) == 8 ? 4 : 2;
+  int launched = 0;
+  while (!hs.done && launched < maxit) {
+    int todo = maxit - launched < chunk ? maxit - launched : chunk;
+    for (int c = 0; c < todo; ++c) {
+      int first = launched + c == 0;
+      if (tm) tm->begin(op_stage, s);
+      if ((e = cg_apply_t<T>(m, bands, coef, zc, pc, pn, Ap, partials, sc, first, s)) !=
+          cudaSuccess)
+        return e;
+      if (tm) tm->end(op_stage, s);
+      k_cg_update_fdm<T, TX_><<<vb, 256, 0, s>>>(n, x, r, pn, Ap, conv ? rf : nullptr,
+                                                 partials, sc, maxit);
+      count_launches(1);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      // z_new = P^-1 r, beta (skipped on the device once converged)
+      float* zo_f = conv ? zf : reinterpret_cast<float*>(zo);
+      if ((e = fdm_apply(fdm, rin, zo_f, &sc->done, s)) != cudaSuccess) return e;
+      k_cg_dot_fdm<T><<<vb, 256, 0, s>>>(n, r, conv ? zf : nullptr, zc, zo, partials, sc, 0, 0);
+      count_launches(1);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      T* t = zc;
+      zc = zo;
+      zo = t;
+      t = pc;
+      pc = pn;
+      pn = t;
+    }
+    launched += todo;
     if ((e = cudaMemcpyAsync(&hs, sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s)) !=
         cudaSuccess)
       return e;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-    if (hs.done) break;
-    // z_new = P^-1 r, beta
-    float* zo_f = conv ? zf : reinterpret_cast<float*>(zo);
-    if ((e = fdm_apply(fdm, rin, zo_f, s)) != cudaSuccess) return e;
-    k_cg_dot_fdm<T><<<vb, 256, 0, s>>>(n, r, conv ? zf : nullptr, zc, zo, partials, sc, 0, 0);
-    count_launches(1);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    T* t = zc;
-    zc = zo;
-    zo = t;
-    t = pc;
-    pc = pn;
-    pn = t;
   }
   *iters = hs.it;
   double bb = hs.bb > 0 ? hs.bb : 1.0;
