@@ -245,81 +245,107 @@ cublasStatus_t gemm_rm(cublasHandle_t h, int M, int N, int K, const float* A, lo
                                    sA, &zero, C, N, sC, batch);
 }
 
-// C[M x N] = A[M x K] B[K x N], all row-major in shared memory, 256
-// threads as a 16 x 16 grid, each owning a strided 5 x 5 set of outputs
-// (M, N <= 80 per pass; larger sizes loop over output tiles)
+// C[M x N] = A[M x K] B[K x N], row-major in shared memory.  The block is a
+// tg x tg grid of threads (tg = ceil(max(M, N) / 5)), each owning the
+// strided 5 x 5 outputs (ty + tg a, tx + tg b), so a 65-node slab runs on
+// 13 x 13 threads with no idle outputs.
 __device__ __forceinline__ void smem_gemm(const float* A, int lda, const float* B, int ldb,
-                                          float* C, int ldc, int M, int N, int K) {
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  for (int m0 = 0; m0 < M; m0 += 80)
-    for (int n0 = 0; n0 < N; n0 += 80) {
-      float acc[5][5];
+                                          float* C, int ldc, int M, int N, int K, int tg) {
+  const int tid = threadIdx.x;
+  if (tid >= tg * tg) return;
+  const int tx = tid % tg, ty = tid / tg;
+  float acc[5][5];
 #pragma unroll
-      for (int a = 0; a < 5; ++a)
+  for (int a = 0; a < 5; ++a)
 #pragma unroll
-        for (int b = 0; b < 5; ++b) acc[a][b] = 0.f;
-      for (int k = 0; k < K; ++k) {
-        float av[5], bv[5];
+    for (int b = 0; b < 5; ++b) acc[a][b] = 0.f;
+  int ra[5], cb[5];
 #pragma unroll
-        for (int a = 0; a < 5; ++a) {
-          int r = m0 + ty + 16 * a;
-          av[a] = r < M ? A[r * lda + k] : 0.f;
-        }
+  for (int a = 0; a < 5; ++a) {
+    ra[a] = min(ty + tg * a, M - 1);
+    cb[a] = min(tx + tg * a, N - 1);
+  }
+#pragma unroll 4
+  for (int k = 0; k < K; ++k) {
+    float av[5], bv[5];
 #pragma unroll
-        for (int b = 0; b < 5; ++b) {
-          int c = n0 + tx + 16 * b;
-          bv[b] = c < N ? B[k * ldb + c] : 0.f;
-        }
+    for (int a = 0; a < 5; ++a) av[a] = A[ra[a] * lda + k];
 #pragma unroll
-        for (int a = 0; a < 5; ++a)
+    for (int b = 0; b < 5; ++b) bv[b] = B[k * ldb + cb[b]];
 #pragma unroll
-          for (int b = 0; b < 5; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
-      }
+    for (int a = 0; a < 5; ++a)
 #pragma unroll
-      for (int a = 0; a < 5; ++a)
+      for (int b = 0; b < 5; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+  }
 #pragma unroll
-        for (int b = 0; b < 5; ++b) {
-          int r = m0 + ty + 16 * a, c = n0 + tx + 16 * b;
-          if (r < M && c < N) C[r * ldc + c] = acc[a][b];
-        }
+  for (int a = 0; a < 5; ++a)
+#pragma unroll
+    for (int b = 0; b < 5; ++b) {
+      int r = ty + tg * a, c = tx + tg * b;
+      if (r < M && c < N) C[r * ldc + c] = acc[a][b];
     }
 }
 
-// forward (inverse = 0): out_z = Vy^T (in_z Vx); inverse (inverse = 1): out_z =
-// Vy (in_z Vx^T), for every z-slab; 256 threads per block, one slab per block
-__global__ void __launch_bounds__(256)
-k_fdm_slab(int nx, int ny, int nz, const float* __restrict__ Bx, const float* __restrict__ Ay,
-           const float* __restrict__ in, float* __restrict__ out, const int* __restrict__ done) {
+// copy n floats global -> shared, 16-byte vectors when both are aligned
+__device__ __forceinline__ void stage(float* dst, const float* __restrict__ src, int n) {
+  if ((((uintptr_t)src | (uintptr_t)dst) & 15) == 0) {
+    int n4 = n >> 2;
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll 4
+    for (int t = threadIdx.x; t < n4; t += blockDim.x) d4[t] = s4[t];
+    for (int t = (n4 << 2) + threadIdx.x; t < n; t += blockDim.x) dst[t] = src[t];
+  } else {
+#pragma unroll 4
+    for (int t = threadIdx.x; t < n; t += blockDim.x) dst[t] = src[t];
+  }
+}
+
+// forward: out_z = Vy^T (in_z Vx); inverse: out_z = Vy (in_z Vx^T), one z-slab
+// per block iteration; the two factors stay in shared memory
+__global__ void k_fdm_slab(int nx, int ny, int nz, int tg, const float* __restrict__ Bx,
+                           const float* __restrict__ Ay, const float* __restrict__ in,
+                           int in_stride, float* __restrict__ out, int out_stride,
+                           const int* __restrict__ done) {
   if (done && *(volatile const int*)done) return;
   extern __shared__ __align__(16) float fsm[];
   const int plane = nx * ny;
-  float* X = fsm;                  // [ny][nx]
-  float* T = X + plane;            // [ny][nx]
-  float* MB = T + plane;           // [nx][nx]  right factor of the x transform
-  float* MA = MB + nx * nx;        // [ny][ny]  left factor of the y transform
-  for (int t = threadIdx.x; t < nx * nx; t += blockDim.x) MB[t] = Bx[t];
-  for (int t = threadIdx.x; t < ny * ny; t += blockDim.x) MA[t] = Ay[t];
+  const int p4 = (plane + 3) & ~3;  // keep every array 16-byte aligned
+  float* X = fsm;                   // [ny][nx]
+  float* T = X + p4;                // [ny][nx]
+  float* MB = T + p4;               // [nx][nx]
+  float* MA = MB + ((nx * nx + 3) & ~3);  // [ny][ny]
+  stage(MB, Bx, nx * nx);
+  stage(MA, Ay, ny * ny);
   for (int z = blockIdx.x; z < nz; z += gridDim.x) {
-    const float* src = in + (int64_t)z * plane;
-    for (int t = threadIdx.x; t < plane; t += blockDim.x) X[t] = src[t];
+    stage(X, in + (int64_t)z * in_stride, plane);
     __syncthreads();
-    smem_gemm(X, nx, MB, nx, T, nx, ny, nx, nx);      // T = X Bx
+    smem_gemm(X, nx, MB, nx, T, nx, ny, nx, nx, tg);      // T = X Bx
     __syncthreads();
-    smem_gemm(MA, ny, T, nx, X, nx, ny, nx, ny);      // X = Ay T
+    smem_gemm(MA, ny, T, nx, X, nx, ny, nx, ny, tg);      // X = Ay T
     __syncthreads();
-    float* dst = out + (int64_t)z * plane;
-    for (int t = threadIdx.x; t < plane; t += blockDim.x) dst[t] = X[t];
+    float* dst = out + (int64_t)z * out_stride;
+    if (((uintptr_t)dst & 15) == 0) {
+      int n4 = plane >> 2;
+      float4* d4 = reinterpret_cast<float4*>(dst);
+      const float4* x4 = reinterpret_cast<const float4*>(X);
+      for (int t = threadIdx.x; t < n4; t += blockDim.x) d4[t] = x4[t];
+      for (int t = (n4 << 2) + threadIdx.x; t < plane; t += blockDim.x) dst[t] = X[t];
+    } else {
+      for (int t = threadIdx.x; t < plane; t += blockDim.x) dst[t] = X[t];
+    }
     __syncthreads();
   }
 }
 
 // banded solves along z: for every mode m (x-y index of the transformed
-// slab) solve L D L^T w = t with the host factors; fac[z][0..k-1][mode] =
-// L(z, z-1-c), fac[z][k][mode] = 1 / D(z).  One lane per mode; the lines of
-// 32 modes and their factors are staged in shared memory.
+// slab) solve L D L^T w = t with the host factors; fac[z][c][mode] = L(z,
+// z-1-c) for c < K, fac[z][K][mode] = 1 / D(z).  One lane per mode; 32
+// modes per block; lines and factors staged in shared memory by 8 warps with
+// 16-byte loads, the recurrences run by warp 0.
 template <int K>
 __global__ void __launch_bounds__(256)
-k_fdm_zsolve(int nmodes, int nz, const float* __restrict__ fac, float* __restrict__ v,
+k_fdm_zsolve(int nmodes, int ms, int nz, const float* __restrict__ fac, float* __restrict__ v,
              const int* __restrict__ done) {
   if (done && *(volatile const int*)done) return;
   extern __shared__ __align__(16) float zsm[];
@@ -327,19 +353,41 @@ k_fdm_zsolve(int nmodes, int nz, const float* __restrict__ fac, float* __restric
   float* f = line + nz * 32;          // [nz][K+1][32]
   const int m0 = blockIdx.x * 32;
   const int lane = threadIdx.x & 31;
-  for (int t = threadIdx.x; t < nz * 32; t += blockDim.x) {
-    int z = t >> 5, l = t & 31, mode = m0 + l;
-    line[t] = mode < nmodes ? v[(int64_t)z * nmodes + mode] : 0.f;
-  }
-  for (int t = threadIdx.x; t < nz * (K + 1) * 32; t += blockDim.x) {
-    int l = t & 31, zc = t >> 5, mode = m0 + l;
-    f[t] = mode < nmodes ? fac[(int64_t)zc * nmodes + mode] : 0.f;
+  // rows have stride ms (a multiple of 4 floats): whole 32-mode rows move as
+  // 8 float4
+  const bool full = m0 + 32 <= nmodes;
+  if (full) {
+    // rows of 32 floats = 8 float4 per row
+#pragma unroll 4
+    for (int t = threadIdx.x; t < nz * 8; t += blockDim.x) {
+      int z = t >> 3, q = t & 7;
+      reinterpret_cast<float4*>(line)[t] =
+          *reinterpret_cast<const float4*>(v + (int64_t)z * ms + m0 + 4 * q);
+    }
+#pragma unroll 4
+    for (int t = threadIdx.x; t < nz * (K + 1) * 8; t += blockDim.x) {
+      int zc = t >> 3, q = t & 7;
+      reinterpret_cast<float4*>(f)[t] =
+          *reinterpret_cast<const float4*>(fac + (int64_t)zc * ms + m0 + 4 * q);
+    }
+  } else {
+#pragma unroll 4
+    for (int t = threadIdx.x; t < nz * 32; t += blockDim.x) {
+      int z = t >> 5, l = t & 31, mode = m0 + l;
+      line[t] = mode < nmodes ? v[(int64_t)z * ms + mode] : 0.f;
+    }
+#pragma unroll 4
+    for (int t = threadIdx.x; t < nz * (K + 1) * 32; t += blockDim.x) {
+      int l = t & 31, zc = t >> 5, mode = m0 + l;
+      f[t] = mode < nmodes ? fac[(int64_t)zc * ms + mode] : 0.f;
+    }
   }
   __syncthreads();
   if (threadIdx.x < 32) {
-    float w[K];  // last K solved values (forward)
+    float w[K];  // last K solved values
 #pragma unroll
     for (int c = 0; c < K; ++c) w[c] = 0.f;
+#pragma unroll 4
     for (int z = 0; z < nz; ++z) {  // L u = t
       float u = line[z * 32 + lane];
 #pragma unroll
@@ -351,12 +399,14 @@ k_fdm_zsolve(int nmodes, int nz, const float* __restrict__ fac, float* __restric
     }
 #pragma unroll
     for (int c = 0; c < K; ++c) w[c] = 0.f;
+#pragma unroll 4
     for (int z = nz - 1; z >= 0; --z) {  // L^T y = u / D
       float y = line[z * 32 + lane] * f[(z * (K + 1) + K) * 32 + lane];
 #pragma unroll
       for (int c = 0; c < K; ++c) {
         int zz = z + 1 + c;
-        if (zz < nz) y -= f[(zz * (K + 1) + c) * 32 + lane] * w[c];
+        float lv = zz < nz ? f[(zz * (K + 1) + c) * 32 + lane] : 0.f;
+        y -= lv * w[c];
       }
 #pragma unroll
       for (int c = K - 1; c > 0; --c) w[c] = w[c - 1];
@@ -365,18 +415,27 @@ k_fdm_zsolve(int nmodes, int nz, const float* __restrict__ fac, float* __restric
     }
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < nz * 32; t += blockDim.x) {
-    int z = t >> 5, l = t & 31, mode = m0 + l;
-    if (mode < nmodes) v[(int64_t)z * nmodes + mode] = line[t];
+  if (full) {
+#pragma unroll 4
+    for (int t = threadIdx.x; t < nz * 8; t += blockDim.x) {
+      int z = t >> 3, q = t & 7;
+      *reinterpret_cast<float4*>(v + (int64_t)z * ms + m0 + 4 * q) =
+          reinterpret_cast<const float4*>(line)[t];
+    }
+  } else {
+    for (int t = threadIdx.x; t < nz * 32; t += blockDim.x) {
+      int z = t >> 5, l = t & 31, mode = m0 + l;
+      if (mode < nmodes) v[(int64_t)z * ms + mode] = line[t];
+    }
   }
 }
 
 // host LDL^T factors of s Mz + cKz Kz (bandwidth k) for every mode
 void band_ldlt_factors(int nz, int k, const std::vector<double>& Mz,
                        const std::vector<double>& Kz, double cKz,
-                       const std::vector<double>& s_modes, std::vector<float>& fac) {
+                       const std::vector<double>& s_modes, int stride, std::vector<float>& fac) {
   int nm = (int)s_modes.size();
-  fac.assign((size_t)nz * (k + 1) * nm, 0.f);
+  fac.assign((size_t)nz * (k + 1) * stride, 0.f);
   std::vector<double> L((size_t)nz * (k + 1)), D(nz);
   for (int m = 0; m < nm; ++m) {
     double s = s_modes[m];
@@ -403,8 +462,8 @@ void band_ldlt_factors(int nz, int k, const std::vector<double>& Mz,
       }
       D[i] = d;
       for (int c = 0; c < k; ++c)
-        fac[((size_t)i * (k + 1) + c) * nm + m] = (float)L[(size_t)i * (k + 1) + c];
-      fac[((size_t)i * (k + 1) + k) * nm + m] = (float)(1.0 / d);
+        fac[((size_t)i * (k + 1) + c) * stride + m] = (float)L[(size_t)i * (k + 1) + c];
+      fac[((size_t)i * (k + 1) + k) * stride + m] = (float)(1.0 / d);
     }
   }
 }
@@ -417,6 +476,8 @@ struct FdmPlan {
   bool slab = false;          // slab form (x, y diagonalised, banded z solves)
   float* fac = nullptr;       // slab form: LDL^T factors [nz][k+1][nx*ny]
   size_t slab_smem = 0, z_smem = 0;
+  int tg = 16, slab_threads = 256;
+  int ms = 0;                 // slab form: padded plane stride of tmp and fac
   float* V[3] = {nullptr, nullptr, nullptr};   // V_a row-major
   float* VT[3] = {nullptr, nullptr, nullptr};  // V_a^T row-major
   float* dinv = nullptr;                       // 1 / D per node
@@ -450,7 +511,12 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4],
   p->k = m.k;
   for (int a = 0; a < 3; ++a) p->n[a] = m.nn[a];
   const int nx = m.nn[0], ny = m.nn[1], nz = m.nn[2];
-  p->slab_smem = (2 * (size_t)nx * ny + (size_t)nx * nx + (size_t)ny * ny) * sizeof(float);
+  auto r4 = [](size_t v) { return (v + 3) & ~(size_t)3; };
+  p->slab_smem = (2 * r4((size_t)nx * ny) + r4((size_t)nx * nx) + r4((size_t)ny * ny)) * sizeof(float);
+  int mx = nx > ny ? nx : ny;
+  p->tg = (mx + 4) / 5;
+  p->slab_threads = ((p->tg * p->tg + 31) / 32) * 32;
+  if (p->tg > 32) p->slab_smem = (size_t)1 << 30;   // beyond the thread budget: dense form
   p->z_smem = (size_t)nz * 32 * (m.k + 2) * sizeof(float);
   p->slab = p->slab_smem <= 200 * 1024 && p->z_smem <= 200 * 1024;
   std::vector<double> lam[3];
@@ -480,7 +546,8 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4],
     e = cudaMemcpy(p->VT[a], vt32.data(), vt32.size() * 4, cudaMemcpyHostToDevice);
   }
   int64_t nn = m.n_nodes;
-  if (e == cudaSuccess) e = cudaMalloc(&p->tmp, nn * 4);
+  p->ms = (nx * ny + 3) & ~3;
+  if (e == cudaSuccess) e = cudaMalloc(&p->tmp, (size_t)nz * p->ms * 4 + nn * 4);
   if (e == cudaSuccess && p->slab) {
     // banded LDL^T factors of s Mz + cKz Kz for every (x, y) mode
     std::vector<double> Mz, Kz;
@@ -491,7 +558,7 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4],
       for (int i = 0; i < nx; ++i)
         smodes[i + (size_t)nx * j] = coef[0] + coef[1] * lam[0][i] + coef[2] * lam[1][j];
     std::vector<float> fac;
-    band_ldlt_factors(nz, m.k, Mz, Kz, coef[3], smodes, fac);
+    band_ldlt_factors(nz, m.k, Mz, Kz, coef[3], smodes, p->ms, fac);
     if ((e = cudaMalloc(&p->fac, fac.size() * 4)) == cudaSuccess)
       e = cudaMemcpy(p->fac, fac.data(), fac.size() * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -546,16 +613,18 @@ cudaError_t fdm_apply(FdmPlan* p, const float* r, float* z, const int* done, cud
   int nx = p->n[0], ny = p->n[1], nz = p->n[2];
   if (p->slab) {
     int nblk = nz < 304 ? nz : 304;
-    k_fdm_slab<<<nblk, 256, p->slab_smem, s>>>(nx, ny, nz, p->V[0], p->VT[1], r, p->tmp, done);
     int nm = nx * ny;
+    k_fdm_slab<<<nblk, p->slab_threads, p->slab_smem, s>>>(nx, ny, nz, p->tg, p->V[0], p->VT[1],
+                                                            r, nm, p->tmp, p->ms, done);
     unsigned zb = (unsigned)((nm + 31) / 32);
     if (p->k == 1)
-      k_fdm_zsolve<1><<<zb, 256, p->z_smem, s>>>(nm, nz, p->fac, p->tmp, done);
+      k_fdm_zsolve<1><<<zb, 256, p->z_smem, s>>>(nm, p->ms, nz, p->fac, p->tmp, done);
     else if (p->k == 2)
-      k_fdm_zsolve<2><<<zb, 256, p->z_smem, s>>>(nm, nz, p->fac, p->tmp, done);
+      k_fdm_zsolve<2><<<zb, 256, p->z_smem, s>>>(nm, p->ms, nz, p->fac, p->tmp, done);
     else
-      k_fdm_zsolve<3><<<zb, 256, p->z_smem, s>>>(nm, nz, p->fac, p->tmp, done);
-    k_fdm_slab<<<nblk, 256, p->slab_smem, s>>>(nx, ny, nz, p->VT[0], p->V[1], p->tmp, z, done);
+      k_fdm_zsolve<3><<<zb, 256, p->z_smem, s>>>(nm, p->ms, nz, p->fac, p->tmp, done);
+    k_fdm_slab<<<nblk, p->slab_threads, p->slab_smem, s>>>(nx, ny, nz, p->tg, p->VT[0], p->V[1],
+                                                            p->tmp, p->ms, z, nm, done);
     count_launches(3);
     return cudaGetLastError();
   }

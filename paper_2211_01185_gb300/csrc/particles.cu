@@ -88,20 +88,41 @@ __global__ void k_bin_count(MeshDev m, BinDev b, int64_t n, const double* __rest
                            int32_t* __restrict__ slot, int32_t* __restrict__ count,
                            DevStatus* st) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double p[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
-  if (!(in_box(p[0], m.x0[0], m.L[0]) && in_box(p[1], m.x0[1], m.L[1]) &&
-        in_box(p[2], m.x0[2], m.L[2])))
-    report_bad(st, i);
-  int bx = bin_axis(p[0], m.x0[0], b.be[0], b.nb[0]);
-  int by = bin_axis(p[1], m.x0[1], b.be[1], b.nb[1]);
-  int bz = bin_axis(p[2], m.x0[2], b.be[2], b.nb[2]);
-  int32_t id = bx + b.nb[0] * (by + b.nb[1] * bz);
-  bin_of[i] = id;
-  slot[i] = atomicAdd(&count[id], 1);
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  bool valid = i < n;
+  int32_t id = -1;
+  double ri = 0.0;
+  if (valid) {
+    double p[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+    if (!(in_box(p[0], m.x0[0], m.L[0]) && in_box(p[1], m.x0[1], m.L[1]) &&
+          in_box(p[2], m.x0[2], m.L[2])))
+      report_bad(st, i);
+    int bx = bin_axis(p[0], m.x0[0], b.be[0], b.nb[0]);
+    int by = bin_axis(p[1], m.x0[1], b.be[1], b.nb[1]);
+    int bz = bin_axis(p[2], m.x0[2], b.be[2], b.nb[2]);
+    id = bx + b.nb[0] * (by + b.nb[1] * bz);
+    bin_of[i] = id;
+    if (r) ri = r[i];
+  }
+  // warp-aggregated counting: one atomic per distinct bin of the warp; the
+  // slot order inside a bin is fixed afterwards by k_sort_bins
+  unsigned peers = __match_any_sync(FULL, id);
+  int leader = __ffs(peers) - 1;
+  int rank = __popc(peers & ((1u << lane) - 1u));
+  int base = 0;
+  if (valid && lane == leader) base = atomicAdd(&count[id], __popc(peers));
+  base = __shfl_sync(FULL, base, leader);
+  if (valid) slot[i] = base + rank;
+  // largest radius: one atomic per warp
   if (r) {
-    double ri = r[i];
-    if (ri >= 0.0) atomicMax(&st->rmax_bits, (unsigned long long)__double_as_longlong(ri));
+    unsigned long long bits = valid && ri >= 0.0 ? (unsigned long long)__double_as_longlong(ri) : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      unsigned long long ob = __shfl_xor_sync(FULL, bits, o);
+      bits = ob > bits ? ob : bits;
+    }
+    if (lane == 0 && bits) atomicMax(&st->rmax_bits, bits);
   }
 }
 
