@@ -82,6 +82,7 @@ struct cfdem_ctx {
   DevStatus* st = nullptr;
   double* bands64 = nullptr;
   float* bands32 = nullptr;
+  float* bandsdf = nullptr;
   // particle arena
   int64_t cap_n = 0;
   int32_t *bin_of = nullptr, *slot = nullptr, *perm = nullptr;
@@ -291,7 +292,8 @@ cfdem_status resolve(cfdem_t c) {
     edge *= 1.5;
   }
   DeviceGuard g(c->device);
-  CK(upload_bands(m, c->tab, L2, &c->bands64, &c->bands32), "upload_bands");
+  CK(upload_bands(m, c->tab, L2, &c->bands64, &c->bands32, &c->bandsdf), "upload_bands");
+  c->cg.bands_df = reinterpret_cast<const df64*>(c->bandsdf);
   if (c->fdm) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     fdm_destroy(c->fdm);
@@ -331,7 +333,8 @@ void free_mesh_arena(cfdem_t c) {
   void* ps[] = {c->eps64, c->eps32, c->b, c->S, c->vol, c->cg.r, c->cg.z, c->cg.p0,
                 c->cg.p1, c->cg.Ap, c->cg.dinv, c->cg.xcor, c->cg.r32, c->cg.z32,
                 c->cg.q0, c->cg.q1, c->cg.Aq, c->cg.dinv32, c->cg.d32, c->cg.partials,
-                c->cg.sc, c->cg.zn, c->cg.zn32, c->cg.rin32};
+                c->cg.sc, c->cg.zn, c->cg.zn32, c->cg.rin32, c->cg.x_df, c->cg.r_df,
+                c->cg.b_df, c->cg.Ap_df};
   for (void* p : ps)
     if (p) cudaFree(p);
   c->eps64 = nullptr;
@@ -340,8 +343,10 @@ void free_mesh_arena(cfdem_t c) {
   c->S = nullptr;
   c->vol = nullptr;
   FdmPlan* keep = c->cg.fdm;
+  const df64* kb = c->cg.bands_df;
   c->cg = CgWork{};
   c->cg.fdm = keep;
+  c->cg.bands_df = kb;
 }
 
 cfdem_status alloc_mesh_arena(cfdem_t c) {
@@ -369,6 +374,20 @@ cfdem_status alloc_mesh_arena(cfdem_t c) {
   CK(grow(&w.zn, nn), "cg");
   CK(grow(&w.zn32, nn), "cg");
   CK(grow(&w.rin32, nn), "cg");
+  {
+    float* t = nullptr;
+    CK(grow(&t, 2 * nn), "cg");
+    w.x_df = reinterpret_cast<df64*>(t);
+    t = nullptr;
+    CK(grow(&t, 2 * nn), "cg");
+    w.r_df = reinterpret_cast<df64*>(t);
+    t = nullptr;
+    CK(grow(&t, 2 * nn), "cg");
+    w.b_df = reinterpret_cast<df64*>(t);
+    t = nullptr;
+    CK(grow(&t, 2 * nn), "cg");
+    w.Ap_df = reinterpret_cast<df64*>(t);
+  }
   w.nblocks = cg_blocks(m);
   CK(grow(&w.partials, 4 * (size_t)w.nblocks), "cg");
   CK(grow(&w.sc, 1), "cg");
@@ -455,7 +474,7 @@ cfdem_status cfdem_destroy(cfdem_t c) {
   if (c->fdm) fdm_destroy(c->fdm);
   c->fdm = nullptr;
   c->timer.release();
-  void* ps[] = {c->st, c->bands64, c->bands32, c->bin_of, c->slot, c->perm, c->xs64,
+  void* ps[] = {c->st, c->bands64, c->bands32, c->bandsdf, c->bin_of, c->slot, c->perm, c->xs64,
                 c->xs32, c->bin_count, c->bin_start, c->scan_tmp};
   for (void* p : ps)
     if (p) cudaFree(p);

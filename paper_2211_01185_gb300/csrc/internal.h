@@ -138,7 +138,7 @@ cudaError_t launch_pcm(const MeshDev& m, int64_t n, const double* x, const doubl
 cudaError_t launch_rhs(const MeshDev& m, const Tables& t, const double* eps_q64,
                        const float* eps_q32, double* b, cudaStream_t s);
 cudaError_t upload_bands(const MeshDev& m, const Tables& t, double L2, double** bands64,
-                         float** bands32);
+                         float** bands32, float** bands_df);
 cudaError_t launch_apply64(const MeshDev& m, const double* bands, const double* coef,
                            const double* x, double* y, cudaStream_t s);
 struct FdmPlan;
@@ -153,6 +153,12 @@ struct CgWork {
   // FP32 vectors (mixed inner solve, FDM conversions)
   float *r32, *z32, *q0, *q1, *Aq, *dinv32, *d32, *zn32, *rin32;
   FdmPlan* fdm;       // fast-diagonalisation preconditioner, or null (Jacobi)
+  // double-float vectors of the mixed solve (pairs of floats, hi first)
+  struct df64* x_df;
+  struct df64* r_df;
+  struct df64* b_df;
+  struct df64* Ap_df;
+  const struct df64* bands_df;  // operator bands as df64 pairs
   double* partials;   // per-block partial sums
   CgScalars* sc;      // device scalars
   int nblocks;
