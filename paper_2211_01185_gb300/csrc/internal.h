@@ -71,6 +71,7 @@ struct CgScalars {
   int done;         // 1 once converged (kernels then return at once)
   unsigned int ticket;  // last-block counter
   int pad;
+  float alpha_hi, alpha_lo;  // double-float split of alpha (mixed solve)
 };
 
 // Optional per-stage CUDA-event timers of a context (off by default).  A
@@ -158,6 +159,8 @@ struct CgWork {
   struct df64* r_df;
   struct df64* b_df;
   struct df64* Ap_df;
+  struct df64* p0_df;
+  struct df64* p1_df;
   const struct df64* bands_df;  // operator bands as df64 pairs
   double* partials;   // per-block partial sums
   CgScalars* sc;      // device scalars

@@ -31,6 +31,25 @@ __device__ __forceinline__ int elem_axis(double x, double x0, double h, int N, d
   return i;
 }
 
+// element index and reference coordinate from a multiplication by 1/h; the
+// IEEE division of the definition is redone only when the product lies
+// within 1e-9 of an element face, where the two could round to different
+// sides.  xi is then within a few ulps of the divided value.
+__device__ __forceinline__ int elem_axis_fast(double x, double x0, double h, double inv_h, int N,
+                                              double* xi) {
+  double t = (x - x0) * inv_h;
+  double f = floor(t);
+  double fr = t - f;
+  if (fr < 1e-9 || fr > 1.0 - 1e-9) {
+    t = __ddiv_rn(__dsub_rn(x, x0), h);
+    f = floor(t);
+  }
+  int i = (int)f;
+  i = i < 0 ? 0 : (i > N - 1 ? N - 1 : i);
+  *xi = t - (double)i;
+  return i;
+}
+
 __device__ __forceinline__ int bin_axis(double x, double x0, double be, int nb) {
   double t = __ddiv_rn(__dsub_rn(x, x0), be);
   double f = floor(t);
@@ -344,6 +363,7 @@ struct Closure<float> {
 
 struct ForceParams {
   double rho, mu, g[3], eps_floor;
+  double inv_h[3];
   int drag_model, beta_over_eps, vans_model;
 };
 
@@ -368,7 +388,8 @@ k_forces(MeshDev m, Tables tb, ForceParams fp, int64_t n, const double* __restri
   }
   int ie[3];
   double xid[3];
-  for (int a = 0; a < 3; ++a) ie[a] = elem_axis(p[a], m.x0[a], m.h[a], m.ne[a], &xid[a]);
+  for (int a = 0; a < 3; ++a)
+    ie[a] = elem_axis_fast(p[a], m.x0[a], m.h[a], fp.inv_h[a], m.ne[a], &xid[a]);
   T xi[3] = {(T)xid[0], (T)xid[1], (T)xid[2]};
 
   // u_f and eps at the particle: Q_k interpolation.  The velocity is
@@ -379,8 +400,7 @@ k_forces(MeshDev m, Tables tb, ForceParams fp, int64_t n, const double* __restri
   lagrange<K, double>(tb.z, tb.lw, xid[0], lxd, (double*)nullptr);
   lagrange<K, double>(tb.z, tb.lw, xid[1], lyd, (double*)nullptr);
   lagrange<K, double>(tb.z, tb.lw, xid[2], lzd, (double*)nullptr);
-  double ufd0 = 0, ufd1 = 0, ufd2 = 0;
-  T eps = 0;
+  double ufd0 = 0, ufd1 = 0, ufd2 = 0, epsd = 0;
   int64_t nx = m.nn[0], nxy = (int64_t)m.nn[0] * m.nn[1];
   int64_t base = (int64_t)ie[0] * K + nx * ((int64_t)ie[1] * K) + nxy * ((int64_t)ie[2] * K);
 #pragma unroll
@@ -395,7 +415,7 @@ k_forces(MeshDev m, Tables tb, ForceParams fp, int64_t n, const double* __restri
         ufd0 += phi * __ldg(u_nodal + 3 * nd);
         ufd1 += phi * __ldg(u_nodal + 3 * nd + 1);
         ufd2 += phi * __ldg(u_nodal + 3 * nd + 2);
-        eps += (T)phi * (T)__ldg(eps_nodal + nd);
+        epsd += phi * __ldg(eps_nodal + nd);
       }
     }
   }
@@ -425,9 +445,9 @@ k_forces(MeshDev m, Tables tb, ForceParams fp, int64_t n, const double* __restri
     for (int b = 0; b <= KP; ++b) {
 #pragma unroll
       for (int a = 0; a <= KP; ++a) {
-        gp0 += dpx[a] * py[b] * pz[c] * (T)(pv[c][b][a] - pv[c][b][0]);
-        gp1 += px[a] * dpy[b] * pz[c] * (T)(pv[c][b][a] - pv[c][0][a]);
-        gp2 += px[a] * py[b] * dpz[c] * (T)(pv[c][b][a] - pv[0][b][a]);
+        if (a > 0) gp0 += dpx[a] * py[b] * pz[c] * (T)(pv[c][b][a] - pv[c][b][0]);
+        if (b > 0) gp1 += px[a] * dpy[b] * pz[c] * (T)(pv[c][b][a] - pv[c][0][a]);
+        if (c > 0) gp2 += px[a] * py[b] * dpz[c] * (T)(pv[c][b][a] - pv[0][b][a]);
       }
     }
   }
@@ -440,6 +460,7 @@ k_forces(MeshDev m, Tables tb, ForceParams fp, int64_t n, const double* __restri
   T U0 = (T)(ufd0 - u_p[3 * i]), U1 = (T)(ufd1 - u_p[3 * i + 1]),
     U2 = (T)(ufd2 - u_p[3 * i + 2]);
   T speed = t_sqrt<T>(U0 * U0 + U1 * U1 + U2 * U2);
+  T eps = (T)epsd;
   T epsc = eps < (T)fp.eps_floor ? (T)fp.eps_floor : eps;
   epsc = epsc > (T)1 ? (T)1 : epsc;
   T fd0 = 0, fd1 = 0, fd2 = 0;
@@ -515,6 +536,7 @@ cudaError_t launch_forces(const MeshDev& m, const Tables& t, int precision, doub
   fp.drag_model = drag_model;
   fp.beta_over_eps = beta_over_eps;
   fp.vans_model = vans_model;
+  for (int a = 0; a < 3; ++a) fp.inv_h[a] = 1.0 / m.h[a];
 #define CFDEM_FORCES(K, KP)                                                                  \
   if (m.k == K && m.kp == KP) {                                                              \
     if (precision == 0)                                                                      \

@@ -280,34 +280,52 @@ struct LoadDirF32 {
     return df64(v);
   }
 };
+// CG direction in double-float from the FP32 preconditioned residual:
+// p = z + beta p_old (first iteration: p = z)
+struct LoadDirDf {
+  const float* z;
+  const df64* p_old;
+  df64* p_new;
+  df64 beta;
+  bool first;
+  __device__ __forceinline__ df64 operator()(int64_t g, bool own) const {
+    df64 v = first ? df64(z[g]) : df64(z[g]) + beta * p_old[g];
+    if (own) p_new[g] = v;
+    return v;
+  }
+};
+
 // y[g] = acc; dot += x_eff * acc (FP64 accumulation)
 template <typename T>
 struct EpiStore {
+  using acc_t = T;
   T* y;
-  __device__ __forceinline__ double operator()(int64_t g, T acc, T xe) const {
+  __device__ __forceinline__ T operator()(int64_t g, T acc, T xe) const {
     y[g] = acc;
-    return (double)(xe * acc);
+    return xe * acc;
   }
 };
 // df64 image of an FP32 direction: store, dot with the high part
 struct EpiStoreDf {
+  using acc_t = float;
   df64* y;
-  __device__ __forceinline__ double operator()(int64_t g, df64 acc, df64 xe) const {
+  __device__ __forceinline__ float operator()(int64_t g, df64 acc, df64 xe) const {
     y[g] = acc;
-    return (double)(xe.hi * acc.hi);
+    return xe.hi * acc.hi;
   }
 };
 // residual r = b - A x in df64; r32 = high part (input of the FP32
 // preconditioner); returns r.r from the high parts
 struct EpiResidualDf {
+  using acc_t = float;
   const df64* b;
   df64* r;
   float* r32;
-  __device__ __forceinline__ double operator()(int64_t g, df64 acc, df64) const {
+  __device__ __forceinline__ float operator()(int64_t g, df64 acc, df64) const {
     df64 v = b[g] - acc;
     r[g] = v;
     r32[g] = v.hi;
-    return (double)(v.hi * v.hi);
+    return v.hi * v.hi;
   }
 };
 
@@ -352,12 +370,12 @@ __device__ __forceinline__ double apply_tile(const MeshDev& m, const T* __restri
   // a tile whose input (halo included) is zero has a zero image: skip the
   // passes (a cold start of the projection begins with x = 0)
   if (!__syncthreads_or(nonzero)) {
-    double dot = 0.0;
+    typename Epi::acc_t dot = 0;
     for (int t = threadIdx.x; t < TX * TY * TZ; t += blockDim.x) {
       int gx = x0 + t % TX, gy = y0 + (t / TX) % TY, gz = z0 + t / (TX * TY);
       if (gx < nx && gy < ny && gz < nz) dot += ep(gx + (int64_t)nx * gy + sxy * gz, T(0), T(0));
     }
-    return dot;
+    return (double)dot;
   }
   // z pass
   for (int t = threadIdx.x; t < TL::NT; t += blockDim.x) {
@@ -396,8 +414,9 @@ __device__ __forceinline__ double apply_tile(const MeshDev& m, const T* __restri
     V[t] = cf.cKx * s1;
   }
   __syncthreads();
-  // x pass + output
-  double dot = 0.0;
+  // x pass + output (per-thread partial in the epilogue's type, one
+  // conversion per thread)
+  typename Epi::acc_t dot = 0;
   for (int t = threadIdx.x; t < TX * TY * TZ; t += blockDim.x) {
     int lx = t % TX, ly = (t / TX) % TY, lz = t / (TX * TY);
     int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
@@ -411,7 +430,7 @@ __device__ __forceinline__ double apply_tile(const MeshDev& m, const T* __restri
     T xe = X[(lz + H) * TL::YW * TL::XW + (ly + H) * TL::XW + lx + H];
     dot += ep(gx + (int64_t)nx * gy + sxy * gz, acc, xe);
   }
-  return dot;
+  return (double)dot;
 }
 
 __device__ __forceinline__ double block_sum(double v, double* red) {
@@ -500,7 +519,7 @@ k_cg_update(int64_t n, TX_* __restrict__ xv, T* __restrict__ r, T* __restrict__ 
   if (((volatile CgScalars*)sc)->done) return;
   __shared__ double red[32];
   T alpha = (T)sc->alpha;
-  double rz = 0.0, rr = 0.0;
+  T rz = 0, rr = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     xv[i] += (TX_)(alpha * p[i]);
@@ -508,11 +527,11 @@ k_cg_update(int64_t n, TX_* __restrict__ xv, T* __restrict__ r, T* __restrict__ 
     T zi = ri * dinv[i];
     r[i] = ri;
     z[i] = zi;
-    rz += (double)(ri * zi);
-    rr += (double)(ri * ri);
+    rz += ri * zi;
+    rr += ri * ri;
   }
-  double s1 = block_sum(rz, red);
-  double s2 = block_sum(rr, red);
+  double s1 = block_sum((double)rz, red);
+  double s2 = block_sum((double)rr, red);
   double vals[2] = {s1, s2};
   double out[2];
   if (last_block_reduce(partials, 2, vals, &sc->ticket, out, red) && threadIdx.x == 0) {
@@ -531,20 +550,21 @@ k_cg_start(int64_t n, const TB* __restrict__ b, const T* __restrict__ Ax, T* __r
            T* __restrict__ z, const T* __restrict__ dinv, double* partials, CgScalars* sc,
            double rtol) {
   __shared__ double red[32];
-  double rz = 0.0, rr = 0.0, bb = 0.0;
+  T rz = 0, rr = 0, bb = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    T ri = (T)b[i] - Ax[i];
+    T bi = (T)b[i];
+    T ri = bi - Ax[i];
     T zi = ri * dinv[i];
     r[i] = ri;
     z[i] = zi;
-    rz += (double)(ri * zi);
-    rr += (double)(ri * ri);
-    bb += (double)b[i] * (double)b[i];
+    rz += ri * zi;
+    rr += ri * ri;
+    bb += bi * bi;
   }
-  double s1 = block_sum(rz, red);
-  double s2 = block_sum(rr, red);
-  double s3 = block_sum(bb, red);
+  double s1 = block_sum((double)rz, red);
+  double s2 = block_sum((double)rr, red);
+  double s3 = block_sum((double)bb, red);
   double vals[3] = {s1, s2, s3};
   double out[3];
   if (last_block_reduce(partials, 3, vals, &sc->ticket, out, red) && threadIdx.x == 0) {
@@ -570,16 +590,16 @@ k_cg_update_fdm(int64_t n, TX_* __restrict__ xv, T* __restrict__ r, const T* __r
   if (((volatile CgScalars*)sc)->done) return;
   __shared__ double red[32];
   T alpha = (T)sc->alpha;
-  double rr = 0.0;
+  T rr = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     xv[i] += (TX_)(alpha * p[i]);
     T ri = r[i] - alpha * Ap[i];
     r[i] = ri;
     if (rf) rf[i] = (float)ri;
-    rr += (double)(ri * ri);
+    rr += ri * ri;
   }
-  double s = block_sum(rr, red);
+  double s = block_sum((double)rr, red);
   double vals[1] = {s};
   double out[1];
   if (last_block_reduce(partials, 1, vals, &sc->ticket, out, red) && threadIdx.x == 0) {
@@ -599,17 +619,19 @@ k_cg_dot_fdm(int64_t n, const T* __restrict__ r, const float* __restrict__ zf,
              CgScalars* sc, int first, int ignore_done) {
   if (!ignore_done && ((volatile CgScalars*)sc)->done) return;
   __shared__ double red[32];
-  double rz = 0.0, rzo = 0.0;
+  // per-thread sums in T (a few terms each), one conversion per thread: FP64
+  // arithmetic per element would run on the slow FP64 pipe
+  T rz = 0, rzo = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     T zi = zf ? (T)zf[i] : z_new[i];
     if (zf) z_new[i] = zi;
     T ri = r[i];
-    rz += (double)(ri * zi);
-    if (!first) rzo += (double)(ri * z_old[i]);
+    rz += ri * zi;
+    if (!first) rzo += ri * z_old[i];
   }
-  double s1 = block_sum(rz, red);
-  double s2 = block_sum(rzo, red);
+  double s1 = block_sum((double)rz, red);
+  double s2 = block_sum((double)rzo, red);
   double vals[2] = {s1, s2};
   double out[2];
   if (last_block_reduce(partials, 2, vals, &sc->ticket, out, red) && threadIdx.x == 0) {
@@ -625,17 +647,18 @@ k_cg_start_fdm(int64_t n, const TB* __restrict__ b, const T* __restrict__ Ax,
                T* __restrict__ r, float* __restrict__ rf, double* partials, CgScalars* sc,
                double rtol) {
   __shared__ double red[32];
-  double rr = 0.0, bb = 0.0;
+  T rr = 0, bb = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    T ri = (T)b[i] - Ax[i];
+    T bi = (T)b[i];
+    T ri = bi - Ax[i];
     r[i] = ri;
     if (rf) rf[i] = (float)ri;
-    rr += (double)(ri * ri);
-    bb += (double)b[i] * (double)b[i];
+    rr += ri * ri;
+    bb += bi * bi;
   }
-  double s1 = block_sum(rr, red);
-  double s2 = block_sum(bb, red);
+  double s1 = block_sum((double)rr, red);
+  double s2 = block_sum((double)bb, red);
   double vals[2] = {s1, s2};
   double out[2];
   if (last_block_reduce(partials, 2, vals, &sc->ticket, out, red) && threadIdx.x == 0) {
@@ -650,20 +673,22 @@ k_cg_start_fdm(int64_t n, const TB* __restrict__ b, const T* __restrict__ Ax,
 }
 
 // --- mixed path: outer CG in double-float, FP32 directions and FDM --------
-// out = df64(in); with partials: b . b of in (FP64) into sc->bb
+// b, x (FP64) -> df64 copies in one pass; b . b from the high parts (FP32
+// products, one conversion per thread) into sc->bb
 __global__ void __launch_bounds__(256)
-k_split_df(int64_t n, const double* __restrict__ in, df64* __restrict__ out, double* partials,
+k_split_df(int64_t n, const double* __restrict__ b, df64* __restrict__ b_df,
+           const double* __restrict__ x, df64* __restrict__ x_df, double* partials,
            CgScalars* sc) {
   __shared__ double red[32];
-  double bb = 0.0;
+  float bb = 0.f;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    double v = in[i];
-    out[i] = df_from_double(v);
-    bb += v * v;
+    df64 v = df_from_double(b[i]);
+    b_df[i] = v;
+    bb = fmaf(v.hi, v.hi, bb);
+    x_df[i] = df_from_double(x[i]);
   }
-  if (!partials) return;
-  double s = block_sum(bb, red);
+  double s = block_sum((double)bb, red);
   double vals[1] = {s};
   double o[1];
   if (last_block_reduce(partials, 1, vals, &sc->ticket, o, red) && threadIdx.x == 0) sc->bb = o[0];
@@ -701,17 +726,17 @@ k_residual_df(MeshDev m, const df64* __restrict__ bands, Coefs<df64> cf,
   }
 }
 
-// p = z + beta p_old (FP32) ; Ap = A p in df64 ; alpha = rz / (p . Ap)
+// p = z + beta p_old (df64) ; Ap = A p in df64 ; alpha = rz / (p . Ap)
 template <int K>
 __global__ void __launch_bounds__(kApplyThreads)
 k_cg_apply_df(MeshDev m, const df64* __restrict__ bands, Coefs<df64> cf,
-              const float* __restrict__ z, const float* __restrict__ p_old,
-              float* __restrict__ p_new, df64* __restrict__ Ap, double* partials, CgScalars* sc,
+              const float* __restrict__ z, const df64* __restrict__ p_old,
+              df64* __restrict__ p_new, df64* __restrict__ Ap, double* partials, CgScalars* sc,
               int first) {
   if (((volatile CgScalars*)sc)->done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double red[32];
-  LoadDirF32 ld{z, p_old, p_new, first ? 0.f : (float)sc->beta, first != 0};
+  LoadDirDf ld{z, p_old, p_new, first ? df64(0.f) : df_from_double(sc->beta), first != 0};
   EpiStoreDf ep{Ap};
   double d = apply_tile<K, df64>(m, bands, cf, ld, ep, reinterpret_cast<df64*>(smraw));
   double s = block_sum(d, red);
@@ -720,21 +745,23 @@ k_cg_apply_df(MeshDev m, const df64* __restrict__ bands, Coefs<df64> cf,
   if (last_block_reduce(partials, 1, vals, &sc->ticket, out, red) && threadIdx.x == 0) {
     sc->pAp = out[0];
     sc->alpha = sc->rz / out[0];
+    sc->alpha_hi = (float)sc->alpha;
+    sc->alpha_lo = (float)(sc->alpha - (double)sc->alpha_hi);
   }
 }
 
 // x += alpha p ; r -= alpha Ap (df64) ; r32 = hi(r) ; r . r ; convergence
 __global__ void __launch_bounds__(256)
-k_cg_update_df(int64_t n, df64* __restrict__ x, df64* __restrict__ r, const float* __restrict__ p,
+k_cg_update_df(int64_t n, df64* __restrict__ x, df64* __restrict__ r, const df64* __restrict__ p,
                const df64* __restrict__ Ap, float* __restrict__ r32, double* partials,
                CgScalars* sc, int maxit) {
   if (((volatile CgScalars*)sc)->done) return;
   __shared__ double red[32];
-  const df64 alpha = df_from_double(sc->alpha);
+  const df64 alpha(sc->alpha_hi, sc->alpha_lo);
   float rr = 0.f;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    x[i] = x[i] + alpha * df64(p[i]);
+    x[i] = x[i] + alpha * p[i];
     df64 v = r[i] - alpha * Ap[i];
     r[i] = v;
     r32[i] = v.hi;
@@ -1105,18 +1132,17 @@ static cudaError_t cg_solve_df(const MeshDev& m, const df64* bands, const double
   const size_t sm = apply_smem<K, df64>();
   Timer* tm = w.timer;
   if ((e = cudaMemsetAsync(w.sc, 0, sizeof(CgScalars), s)) != cudaSuccess) return e;
-  k_split_df<<<vb, 256, 0, s>>>(n, b, w.b_df, w.partials, w.sc);
-  k_split_df<<<vb, 256, 0, s>>>(n, x, w.x_df, nullptr, w.sc);
+  k_split_df<<<vb, 256, 0, s>>>(n, b, w.b_df, x, w.x_df, w.partials, w.sc);
   if (tm) tm->begin(kStageOp32, s);
   k_residual_df<K><<<g, kApplyThreads, sm, s>>>(m, bands, cf, w.x_df, w.b_df, w.r_df, w.r32,
                                                 w.partials, w.sc, rtol);
   if (tm) tm->end(kStageOp32, s);
-  count_launches(3);
+  count_launches(2);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   float* zc = w.z32;
   float* zo = w.zn32;
-  float* pc = w.q0;
-  float* pn = w.q1;
+  df64* pc = w.p0_df;
+  df64* pn = w.p1_df;
   if ((e = fdm_apply(w.fdm, w.r32, zc, nullptr, s)) != cudaSuccess) return e;
   k_cg_dot_fdm<float><<<vb, 256, 0, s>>>(n, w.r32, nullptr, zc, zc, w.partials, w.sc, 1, 1);
   count_launches(1);
@@ -1145,9 +1171,9 @@ static cudaError_t cg_solve_df(const MeshDev& m, const df64* bands, const double
       float* t = zc;
       zc = zo;
       zo = t;
-      t = pc;
+      df64* tp = pc;
       pc = pn;
-      pn = t;
+      pn = tp;
     }
     launched += todo;
     if ((e = cudaMemcpyAsync(&hs, w.sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s)) !=
