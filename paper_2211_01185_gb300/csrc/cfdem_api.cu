@@ -511,6 +511,7 @@ cfdem_status cfdem_set_mesh(cfdem_t c, const double origin[3], const double exte
   m.Ve = m.h[0] * m.h[1] * m.h[2];
   if (m.E * m.Q > ((int64_t)1 << 31) || m.n_nodes > ((int64_t)1 << 31))
     return fail(c, CFDEM_EINVAL, "mesh too large");
+  m.shape = pick_shape(m);
   DeviceGuard g(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   free_mesh_arena(c);

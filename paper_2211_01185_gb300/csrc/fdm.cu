@@ -245,178 +245,236 @@ cublasStatus_t gemm_rm(cublasHandle_t h, int M, int N, int K, const float* A, lo
                                    sA, &zero, C, N, sC, batch);
 }
 
-// C[M x N] = A[M x K] B[K x N], row-major in shared memory.  The block is a
-// tg x tg grid of threads (tg = ceil(max(M, N) / 5)), each owning the
-// strided 5 x 5 outputs (ty + tg a, tx + tg b), so a 65-node slab runs on
-// 13 x 13 threads with no idle outputs.
-__device__ __forceinline__ void smem_gemm(const float* A, int lda, const float* B, int ldb,
-                                          float* C, int ldc, int M, int N, int K, int tg) {
+// C[M x N] = A[M x K] B[K x N] in shared memory with A stored transposed
+// (AT[K][lda]) and B row-major (B[K][ldb]); lda, ldb multiples of 4 floats.
+// Each thread owns an 8 x 8 block of C, so one k step is two 128-bit loads of
+// A, two of B and 64 FMAs.  Threads form a gm x gn grid (gm = ceil(M/8),
+// gn = ceil(N/8)); rows and columns past M, N read padding and are not
+// stored.
+__device__ __forceinline__ void smem_gemm8(const float* AT, int lda, const float* B, int ldb,
+                                           float* C, int ldc, int M, int N, int K) {
+  const int gn = (N + 7) >> 3, gm = (M + 7) >> 3;
   const int tid = threadIdx.x;
-  if (tid >= tg * tg) return;
-  const int tx = tid % tg, ty = tid / tg;
-  float acc[5][5];
+  if (tid >= gm * gn) return;
+  const int r0 = (tid / gn) * 8, c0 = (tid % gn) * 8;
+  float acc[8][8];
 #pragma unroll
-  for (int a = 0; a < 5; ++a)
+  for (int a = 0; a < 8; ++a)
 #pragma unroll
-    for (int b = 0; b < 5; ++b) acc[a][b] = 0.f;
-  int ra[5], cb[5];
-#pragma unroll
-  for (int a = 0; a < 5; ++a) {
-    ra[a] = min(ty + tg * a, M - 1);
-    cb[a] = min(tx + tg * a, N - 1);
-  }
-#pragma unroll 4
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+#pragma unroll 2
   for (int k = 0; k < K; ++k) {
-    float av[5], bv[5];
+    const float4* ap = reinterpret_cast<const float4*>(AT + k * lda + r0);
+    const float4* bp = reinterpret_cast<const float4*>(B + k * ldb + c0);
+    float4 a0 = ap[0], a1 = ap[1], b0 = bp[0], b1 = bp[1];
+    float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-    for (int a = 0; a < 5; ++a) av[a] = A[ra[a] * lda + k];
+    for (int a = 0; a < 8; ++a)
 #pragma unroll
-    for (int b = 0; b < 5; ++b) bv[b] = B[k * ldb + cb[b]];
-#pragma unroll
-    for (int a = 0; a < 5; ++a)
-#pragma unroll
-      for (int b = 0; b < 5; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+      for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
   }
 #pragma unroll
-  for (int a = 0; a < 5; ++a)
+  for (int a = 0; a < 8; ++a)
 #pragma unroll
-    for (int b = 0; b < 5; ++b) {
-      int r = ty + tg * a, c = tx + tg * b;
+    for (int b = 0; b < 8; ++b) {
+      int r = r0 + a, c = c0 + b;
       if (r < M && c < N) C[r * ldc + c] = acc[a][b];
     }
 }
 
-// copy n floats global -> shared, 16-byte vectors when both are aligned
-__device__ __forceinline__ void stage(float* dst, const float* __restrict__ src, int n) {
-  if ((((uintptr_t)src | (uintptr_t)dst) & 15) == 0) {
-    int n4 = n >> 2;
-    const float4* s4 = reinterpret_cast<const float4*>(src);
-    float4* d4 = reinterpret_cast<float4*>(dst);
-#pragma unroll 4
-    for (int t = threadIdx.x; t < n4; t += blockDim.x) d4[t] = s4[t];
-    for (int t = (n4 << 2) + threadIdx.x; t < n; t += blockDim.x) dst[t] = src[t];
-  } else {
-#pragma unroll 4
-    for (int t = threadIdx.x; t < n; t += blockDim.x) dst[t] = src[t];
-  }
+// asynchronous global -> shared copies (no register round trip, every copy of
+// a thread in flight at once); completion by cp.async.wait_all
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
-// forward: out_z = Vy^T (in_z Vx); inverse: out_z = Vy (in_z Vx^T), one z-slab
-// per block iteration; the two factors stay in shared memory
-__global__ void k_fdm_slab(int nx, int ny, int nz, int tg, const float* __restrict__ Bx,
-                           const float* __restrict__ Ay, const float* __restrict__ in,
+// padded row length of the slab-form transform matrices and tiles: a
+// multiple of 8 for the 8 x 8 register tiles, plus 4 against bank conflicts
+__host__ __device__ __forceinline__ int slab_pad(int n) { return ((n + 7) & ~7) + 4; }
+
+// forward: out_z = Vy^T (in_z Vx); inverse: out_z = Vy (in_z Vx^T), for every
+// z-slab.  Bx is the right factor of the x transform ([nx][slab_pad(nx)]),
+// AyT the transpose of the left factor of the y transform ([ny][slab_pad(ny)]),
+// both zero-padded row-major in global memory and copied to shared memory as
+// they are.  The slab is staged transposed (x major) as the A operand of the
+// first product.
+__global__ void k_fdm_slab(int nx, int ny, int nz, const float* __restrict__ Bx,
+                           const float* __restrict__ AyT, const float* __restrict__ in,
                            int in_stride, float* __restrict__ out, int out_stride,
                            const int* __restrict__ done) {
   if (done && *(volatile const int*)done) return;
   extern __shared__ __align__(16) float fsm[];
+  const int px = slab_pad(nx), py = slab_pad(ny);
   const int plane = nx * ny;
-  const int p4 = (plane + 3) & ~3;  // keep every array 16-byte aligned
-  float* X = fsm;                   // [ny][nx]
-  float* T = X + p4;                // [ny][nx]
-  float* MB = T + p4;               // [nx][nx]
-  float* MA = MB + ((nx * nx + 3) & ~3);  // [ny][ny]
-  stage(MB, Bx, nx * nx);
-  stage(MA, Ay, ny * ny);
+  const int big = nx * py > ny * px ? nx * py : ny * px;
+  float* XT = fsm;                 // [nx][py]   slab, transposed
+  float* Y = XT;                   // [ny][px]   result (reuses the slab's space)
+  float* T = XT + big;             // [ny][px]   after the x transform
+  float* MB = T + ny * px;         // [nx][px]
+  float* MA = MB + nx * px;        // [ny][py]   (AyT)
+  for (int t = threadIdx.x; t < (nx * px) >> 2; t += blockDim.x)
+    cp_async16(MB + 4 * t, Bx + 4 * t);
+  for (int t = threadIdx.x; t < (ny * py) >> 2; t += blockDim.x)
+    cp_async16(MA + 4 * t, AyT + 4 * t);
   for (int z = blockIdx.x; z < nz; z += gridDim.x) {
-    stage(X, in + (int64_t)z * in_stride, plane);
+    const float* src = in + (int64_t)z * in_stride;
+    for (int t = threadIdx.x; t < plane; t += blockDim.x) {
+      int y = t / nx, x = t - y * nx;
+      cp_async4(XT + x * py + y, src + t);
+    }
+    cp_async_wait_all();
     __syncthreads();
-    smem_gemm(X, nx, MB, nx, T, nx, ny, nx, nx, tg);      // T = X Bx
+    // rows y >= ny of XT are never written: they feed only outputs that are
+    // not stored
+    smem_gemm8(XT, py, MB, px, T, px, ny, nx, nx);      // T[y][x'] = sum_x X[y][x] Bx[x][x']
     __syncthreads();
-    smem_gemm(MA, ny, T, nx, X, nx, ny, nx, ny, tg);      // X = Ay T
+    smem_gemm8(MA, py, T, px, Y, px, ny, nx, ny);       // Y[y'][x] = sum_y AyT[y][y'] T[y][x]
     __syncthreads();
     float* dst = out + (int64_t)z * out_stride;
-    if (((uintptr_t)dst & 15) == 0) {
-      int n4 = plane >> 2;
-      float4* d4 = reinterpret_cast<float4*>(dst);
-      const float4* x4 = reinterpret_cast<const float4*>(X);
-      for (int t = threadIdx.x; t < n4; t += blockDim.x) d4[t] = x4[t];
-      for (int t = (n4 << 2) + threadIdx.x; t < plane; t += blockDim.x) dst[t] = X[t];
-    } else {
-      for (int t = threadIdx.x; t < plane; t += blockDim.x) dst[t] = X[t];
+    for (int t = threadIdx.x; t < plane; t += blockDim.x) {
+      int y = t / nx, x = t - y * nx;
+      dst[t] = Y[y * px + x];
     }
     __syncthreads();
   }
 }
 
-// banded solves along z: for every mode m (x-y index of the transformed
-// slab) solve L D L^T w = t with the host factors; fac[z][c][mode] = L(z,
-// z-1-c) for c < K, fac[z][K][mode] = 1 / D(z).  One lane per mode; 32
-// modes per block; lines and factors staged in shared memory by 8 warps with
-// 16-byte loads, the recurrences run by warp 0.
+// banded solves along z: for every mode m (x-y index of the transformed slab)
+// solve L D L^T w = t with the host factors; fac[z][c][mode] = L(z, z-1-c)
+// for c < K, fac[z][K][mode] = 1 / D(z) (mode stride ms, a multiple of 4).
+// One lane per mode, 32 modes per block.  The block's lines and factors are
+// copied to shared memory by all its threads with asynchronous copies; warp 0
+// runs the two recurrences, reading U steps ahead into registers so that the
+// shared-memory latency stays off the dependency chain.
 template <int K>
 __global__ void __launch_bounds__(256)
 k_fdm_zsolve(int nmodes, int ms, int nz, const float* __restrict__ fac, float* __restrict__ v,
              const int* __restrict__ done) {
   if (done && *(volatile const int*)done) return;
+  constexpr int U = 4;
   extern __shared__ __align__(16) float zsm[];
   float* line = zsm;                  // [nz][32]
   float* f = line + nz * 32;          // [nz][K+1][32]
   const int m0 = blockIdx.x * 32;
   const int lane = threadIdx.x & 31;
-  // rows have stride ms (a multiple of 4 floats): whole 32-mode rows move as
-  // 8 float4
   const bool full = m0 + 32 <= nmodes;
   if (full) {
-    // rows of 32 floats = 8 float4 per row
-#pragma unroll 4
     for (int t = threadIdx.x; t < nz * 8; t += blockDim.x) {
       int z = t >> 3, q = t & 7;
-      reinterpret_cast<float4*>(line)[t] =
-          *reinterpret_cast<const float4*>(v + (int64_t)z * ms + m0 + 4 * q);
+      cp_async16(line + 4 * t, v + (int64_t)z * ms + m0 + 4 * q);
     }
-#pragma unroll 4
     for (int t = threadIdx.x; t < nz * (K + 1) * 8; t += blockDim.x) {
       int zc = t >> 3, q = t & 7;
-      reinterpret_cast<float4*>(f)[t] =
-          *reinterpret_cast<const float4*>(fac + (int64_t)zc * ms + m0 + 4 * q);
+      cp_async16(f + 4 * t, fac + (int64_t)zc * ms + m0 + 4 * q);
     }
   } else {
-#pragma unroll 4
     for (int t = threadIdx.x; t < nz * 32; t += blockDim.x) {
       int z = t >> 5, l = t & 31, mode = m0 + l;
-      line[t] = mode < nmodes ? v[(int64_t)z * ms + mode] : 0.f;
+      if (mode < nmodes) cp_async4(line + t, v + (int64_t)z * ms + mode);
+      else line[t] = 0.f;
     }
-#pragma unroll 4
     for (int t = threadIdx.x; t < nz * (K + 1) * 32; t += blockDim.x) {
-      int l = t & 31, zc = t >> 5, mode = m0 + l;
-      f[t] = mode < nmodes ? fac[(int64_t)zc * ms + mode] : 0.f;
+      int zc = t >> 5, l = t & 31, mode = m0 + l;
+      if (mode < nmodes) cp_async4(f + t, fac + (int64_t)zc * ms + mode);
+      else f[t] = (zc % (K + 1)) == K ? 1.f : 0.f;
     }
   }
+  cp_async_wait_all();
   __syncthreads();
   if (threadIdx.x < 32) {
-    float w[K];  // last K solved values
+    // L u = t, forwards
+    float w[K];
 #pragma unroll
     for (int c = 0; c < K; ++c) w[c] = 0.f;
-#pragma unroll 4
-    for (int z = 0; z < nz; ++z) {  // L u = t
-      float u = line[z * 32 + lane];
+    float tn[U], ln[U][K];
 #pragma unroll
-      for (int c = 0; c < K; ++c) u -= f[(z * (K + 1) + c) * 32 + lane] * w[c];
+    for (int j = 0; j < U; ++j) {
+      int z = j < nz ? j : nz - 1;
+      tn[j] = line[z * 32 + lane];
 #pragma unroll
-      for (int c = K - 1; c > 0; --c) w[c] = w[c - 1];
-      w[0] = u;
-      line[z * 32 + lane] = u;
+      for (int c = 0; c < K; ++c) ln[j][c] = f[(z * (K + 1) + c) * 32 + lane];
     }
+    for (int z0 = 0; z0 < nz; z0 += U) {
+      float tc[U], lc[U][K];
 #pragma unroll
-    for (int c = 0; c < K; ++c) w[c] = 0.f;
-#pragma unroll 4
-    for (int z = nz - 1; z >= 0; --z) {  // L^T y = u / D
-      float y = line[z * 32 + lane] * f[(z * (K + 1) + K) * 32 + lane];
+      for (int j = 0; j < U; ++j) {
+        tc[j] = tn[j];
 #pragma unroll
-      for (int c = 0; c < K; ++c) {
-        int zz = z + 1 + c;
-        float lv = zz < nz ? f[(zz * (K + 1) + c) * 32 + lane] : 0.f;
-        y -= lv * w[c];
+        for (int c = 0; c < K; ++c) lc[j][c] = ln[j][c];
       }
 #pragma unroll
-      for (int c = K - 1; c > 0; --c) w[c] = w[c - 1];
-      w[0] = y;
-      line[z * 32 + lane] = y;
+      for (int j = 0; j < U; ++j) {  // next U steps, clamped at the last row
+        int z = z0 + U + j < nz ? z0 + U + j : nz - 1;
+        tn[j] = line[z * 32 + lane];
+#pragma unroll
+        for (int c = 0; c < K; ++c) ln[j][c] = f[(z * (K + 1) + c) * 32 + lane];
+      }
+#pragma unroll
+      for (int j = 0; j < U; ++j) {
+        if (z0 + j < nz) {
+          float u = tc[j];
+#pragma unroll
+          for (int c = 0; c < K; ++c) u -= lc[j][c] * w[c];
+#pragma unroll
+          for (int c = K - 1; c > 0; --c) w[c] = w[c - 1];
+          w[0] = u;
+          line[(z0 + j) * 32 + lane] = u;
+        }
+      }
+    }
+    // L^T y = D^-1 u, backwards: y(z) = u(z)/D(z) - sum_c L(z+1+c, z) y(z+1+c)
+#pragma unroll
+    for (int c = 0; c < K; ++c) w[c] = 0.f;
+    // step z needs u(z), 1/D(z) and L(z+1+c, z) = fac[z+1+c][c] (0 past the end)
+    auto fetch = [&](int z, float& uo, float& dio, float* lo) {
+      int zs = z < 0 ? 0 : z;
+      uo = line[zs * 32 + lane];
+      dio = f[(zs * (K + 1) + K) * 32 + lane];
+#pragma unroll
+      for (int c = 0; c < K; ++c) {
+        int zz = zs + 1 + c;
+        lo[c] = zz < nz ? f[(zz * (K + 1) + c) * 32 + lane] : 0.f;
+      }
+    };
+    float un[U], dn[U], bn[U][K];
+#pragma unroll
+    for (int j = 0; j < U; ++j) fetch(nz - 1 - j, un[j], dn[j], bn[j]);
+    for (int z0 = nz - 1; z0 >= 0; z0 -= U) {
+      float uc[U], dc[U], bc[U][K];
+#pragma unroll
+      for (int j = 0; j < U; ++j) {
+        uc[j] = un[j];
+        dc[j] = dn[j];
+#pragma unroll
+        for (int c = 0; c < K; ++c) bc[j][c] = bn[j][c];
+      }
+#pragma unroll
+      for (int j = 0; j < U; ++j) fetch(z0 - U - j, un[j], dn[j], bn[j]);
+#pragma unroll
+      for (int j = 0; j < U; ++j) {
+        if (z0 - j >= 0) {
+          float y = uc[j] * dc[j];
+#pragma unroll
+          for (int c = 0; c < K; ++c) y -= bc[j][c] * w[c];
+#pragma unroll
+          for (int c = K - 1; c > 0; --c) w[c] = w[c - 1];
+          w[0] = y;
+          line[(z0 - j) * 32 + lane] = y;
+        }
+      }
     }
   }
   __syncthreads();
   if (full) {
-#pragma unroll 4
     for (int t = threadIdx.x; t < nz * 8; t += blockDim.x) {
       int z = t >> 3, q = t & 7;
       *reinterpret_cast<float4*>(v + (int64_t)z * ms + m0 + 4 * q) =
@@ -430,39 +488,39 @@ k_fdm_zsolve(int nmodes, int ms, int nz, const float* __restrict__ fac, float* _
   }
 }
 
-// host LDL^T factors of s Mz + cKz Kz (bandwidth k) for every mode
+// host LDL^T factors of s Mz + cKz Kz (band rows of half-width k) for every
+// mode, in FP64, stored in FP32 as fac[z][c][mode] = L(z, z-1-c) (c < k) and
+// fac[z][k][mode] = 1 / D(z), mode stride `stride`
 void band_ldlt_factors(int nz, int k, const std::vector<double>& Mz,
                        const std::vector<double>& Kz, double cKz,
                        const std::vector<double>& s_modes, int stride, std::vector<float>& fac) {
-  int nm = (int)s_modes.size();
+  const int nm = (int)s_modes.size();
   fac.assign((size_t)nz * (k + 1) * stride, 0.f);
-  std::vector<double> L((size_t)nz * (k + 1)), D(nz);
+  std::vector<double> L((size_t)nz * k), D(nz);
+  auto lw = [&](int i, int j) {  // L(i, j) for i - k <= j < i
+    return L[(size_t)i * k + (i - 1 - j)];
+  };
   for (int m = 0; m < nm; ++m) {
-    double s = s_modes[m];
+    const double s = s_modes[m];
     auto A = [&](int i, int j) {
       return s * Mz[(size_t)i * nz + j] + cKz * Kz[(size_t)i * nz + j];
     };
     for (int i = 0; i < nz; ++i) {
-      // L(i, i-1-c) for c = k-1 .. 0 (farther first), then D(i)
-      for (int c = k - 1; c >= 0; --c) {
+      for (int c = k - 1; c >= 0; --c) {  // L(i, i-1-c), farther columns first
         int j = i - 1 - c;
         double val = 0.0;
         if (j >= 0) {
           val = A(i, j);
-          for (int p = (i - k > 0 ? i - k : 0); p < j; ++p)
-            val -= L[(size_t)i * (k + 1) + (i - 1 - p)] * L[(size_t)j * (k + 1) + (j - 1 - p)] * D[p];
+          for (int p = (i - k > 0 ? i - k : 0); p < j; ++p) val -= lw(i, p) * lw(j, p) * D[p];
           val /= D[j];
         }
-        L[(size_t)i * (k + 1) + c] = val;
+        L[(size_t)i * k + c] = val;
       }
       double d = A(i, i);
-      for (int p = (i - k > 0 ? i - k : 0); p < i; ++p) {
-        double l = L[(size_t)i * (k + 1) + (i - 1 - p)];
-        d -= l * l * D[p];
-      }
+      for (int p = (i - k > 0 ? i - k : 0); p < i; ++p) d -= lw(i, p) * lw(i, p) * D[p];
       D[i] = d;
       for (int c = 0; c < k; ++c)
-        fac[((size_t)i * (k + 1) + c) * stride + m] = (float)L[(size_t)i * (k + 1) + c];
+        fac[((size_t)i * (k + 1) + c) * stride + m] = (float)L[(size_t)i * k + c];
       fac[((size_t)i * (k + 1) + k) * stride + m] = (float)(1.0 / d);
     }
   }
@@ -474,13 +532,15 @@ struct FdmPlan {
   int n[3] = {0, 0, 0};
   int k = 1;
   bool slab = false;          // slab form (x, y diagonalised, banded z solves)
-  float* fac = nullptr;       // slab form: LDL^T factors [nz][k+1][nx*ny]
+  float* fac = nullptr;       // slab form: LDL^T factors [nz][k+1][ms]
   size_t slab_smem = 0, z_smem = 0;
-  int tg = 16, slab_threads = 256;
+  int slab_threads = 256;
   int ms = 0;                 // slab form: padded plane stride of tmp and fac
-  float* V[3] = {nullptr, nullptr, nullptr};   // V_a row-major
-  float* VT[3] = {nullptr, nullptr, nullptr};  // V_a^T row-major
-  float* dinv = nullptr;                       // 1 / D per node
+  // V_a and V_a^T row-major; in the slab form (axes x, y only) with rows
+  // zero-padded to slab_pad(n_a)
+  float* V[3] = {nullptr, nullptr, nullptr};
+  float* VT[3] = {nullptr, nullptr, nullptr};
+  float* dinv = nullptr;                       // dense form: 1 / D per node
   float* tmp = nullptr;                        // work vector
   cublasHandle_t blas = nullptr;
 };
@@ -498,8 +558,8 @@ void fdm_destroy(FdmPlan* p) {
   delete p;
 }
 
-cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4],
-                       FdmPlan** out, const char** why) {
+cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4], FdmPlan** out,
+                       const char** why) {
   *out = nullptr;
   *why = nullptr;
   for (int a = 0; a < 3; ++a)
@@ -511,19 +571,21 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4],
   p->k = m.k;
   for (int a = 0; a < 3; ++a) p->n[a] = m.nn[a];
   const int nx = m.nn[0], ny = m.nn[1], nz = m.nn[2];
-  auto r4 = [](size_t v) { return (v + 3) & ~(size_t)3; };
-  p->slab_smem = (2 * r4((size_t)nx * ny) + r4((size_t)nx * nx) + r4((size_t)ny * ny)) * sizeof(float);
-  int mx = nx > ny ? nx : ny;
-  p->tg = (mx + 4) / 5;
-  p->slab_threads = ((p->tg * p->tg + 31) / 32) * 32;
-  if (p->tg > 32) p->slab_smem = (size_t)1 << 30;   // beyond the thread budget: dense form
+  {
+    size_t px = slab_pad(nx), py = slab_pad(ny);
+    size_t big = nx * py > ny * px ? nx * py : ny * px;
+    p->slab_smem = (big + ny * px + nx * px + ny * py) * sizeof(float);
+    p->slab_threads = ((((nx + 7) / 8) * ((ny + 7) / 8) + 31) / 32) * 32;
+    if (p->slab_threads > 1024) p->slab_smem = (size_t)1 << 30;  // dense form instead
+  }
   p->z_smem = (size_t)nz * 32 * (m.k + 2) * sizeof(float);
-  p->slab = p->slab_smem <= 200 * 1024 && p->z_smem <= 200 * 1024;
+  p->slab = p->slab_smem <= 220 * 1024 && p->z_smem <= 220 * 1024;
   std::vector<double> lam[3];
   cudaError_t e = cudaSuccess;
   const int naxes = p->slab ? 2 : 3;
   for (int a = 0; a < naxes && e == cudaSuccess; ++a) {
-    int n = m.nn[a];
+    const int n = m.nn[a];
+    const int ld = p->slab ? slab_pad(n) : n;
     std::vector<double> M, K, V;
     assemble_1d(m.ne[a], m.k, t.Mh, M);
     assemble_1d(m.ne[a], m.k, t.Kh, K);
@@ -532,11 +594,11 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4],
       fdm_destroy(p);
       return cudaSuccess;
     }
-    std::vector<float> v32(n * (size_t)n), vt32(n * (size_t)n);
+    std::vector<float> v32(n * (size_t)ld, 0.f), vt32(n * (size_t)ld, 0.f);
     for (int i = 0; i < n; ++i)
       for (int j = 0; j < n; ++j) {
-        v32[i * (size_t)n + j] = (float)V[i * (size_t)n + j];
-        vt32[j * (size_t)n + i] = (float)V[i * (size_t)n + j];
+        v32[i * (size_t)ld + j] = (float)V[i * (size_t)n + j];
+        vt32[j * (size_t)ld + i] = (float)V[i * (size_t)n + j];
       }
     if ((e = cudaMalloc(&p->V[a], v32.size() * 4)) != cudaSuccess) break;
     if ((e = cudaMalloc(&p->VT[a], v32.size() * 4)) != cudaSuccess) break;
@@ -549,7 +611,8 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4],
   p->ms = (nx * ny + 3) & ~3;
   if (e == cudaSuccess) e = cudaMalloc(&p->tmp, (size_t)nz * p->ms * 4 + nn * 4);
   if (e == cudaSuccess && p->slab) {
-    // banded LDL^T factors of s Mz + cKz Kz for every (x, y) mode
+    // banded LDL^T factors of s_m Mz + cKz Kz for every (x, y) mode m, with
+    // s_m = cM + cKx lam_x + cKy lam_y
     std::vector<double> Mz, Kz;
     assemble_1d(m.ne[2], m.k, t.Mh, Mz);
     assemble_1d(m.ne[2], m.k, t.Kh, Kz);
@@ -614,8 +677,8 @@ cudaError_t fdm_apply(FdmPlan* p, const float* r, float* z, const int* done, cud
   if (p->slab) {
     int nblk = nz < 304 ? nz : 304;
     int nm = nx * ny;
-    k_fdm_slab<<<nblk, p->slab_threads, p->slab_smem, s>>>(nx, ny, nz, p->tg, p->V[0], p->VT[1],
-                                                            r, nm, p->tmp, p->ms, done);
+    k_fdm_slab<<<nblk, p->slab_threads, p->slab_smem, s>>>(nx, ny, nz, p->V[0], p->V[1], r, nm,
+                                                            p->tmp, p->ms, done);
     unsigned zb = (unsigned)((nm + 31) / 32);
     if (p->k == 1)
       k_fdm_zsolve<1><<<zb, 256, p->z_smem, s>>>(nm, p->ms, nz, p->fac, p->tmp, done);
@@ -623,8 +686,8 @@ cudaError_t fdm_apply(FdmPlan* p, const float* r, float* z, const int* done, cud
       k_fdm_zsolve<2><<<zb, 256, p->z_smem, s>>>(nm, p->ms, nz, p->fac, p->tmp, done);
     else
       k_fdm_zsolve<3><<<zb, 256, p->z_smem, s>>>(nm, p->ms, nz, p->fac, p->tmp, done);
-    k_fdm_slab<<<nblk, p->slab_threads, p->slab_smem, s>>>(nx, ny, nz, p->tg, p->VT[0], p->V[1],
-                                                            p->tmp, p->ms, z, nm, done);
+    k_fdm_slab<<<nblk, p->slab_threads, p->slab_smem, s>>>(nx, ny, nz, p->VT[0], p->VT[1], p->tmp,
+                                                            p->ms, z, nm, done);
     count_launches(3);
     return cudaGetLastError();
   }

@@ -30,6 +30,7 @@ struct MeshDev {
   int64_t n_nodes;   // Q_k nodes
   int64_t n_pnodes;  // Q_kp nodes
   double Ve;         // element volume hx hy hz
+  int shape;         // tile shape of the projection operator (pick_shape)
 };
 
 // 1D reference tables on [0,1] (degree <= 3).  Built on the host from
@@ -143,8 +144,8 @@ cudaError_t upload_bands(const MeshDev& m, const Tables& t, double L2, double** 
 cudaError_t launch_apply64(const MeshDev& m, const double* bands, const double* coef,
                            const double* x, double* y, cudaStream_t s);
 struct FdmPlan;
-cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4],
-                       FdmPlan** out, const char** why);
+cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4], FdmPlan** out,
+                       const char** why);
 cudaError_t fdm_apply(FdmPlan* p, const float* r, float* z, const int* done, cudaStream_t s);
 void fdm_destroy(FdmPlan* p);
 
@@ -168,6 +169,7 @@ struct CgWork {
   Timer* timer;       // may be null
 };
 int cg_blocks(const MeshDev& m);
+int pick_shape(const MeshDev& m);
 cudaError_t run_cg64(const MeshDev& m, const double* bands, const double* coef,
                      const double* b, double* x, double rtol, int maxit, CgWork& w,
                      cudaStream_t s, int* iters_host, double* relres_host, int* converged);

@@ -29,6 +29,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -186,11 +187,23 @@ cudaError_t upload_bands(const MeshDev& m, const Tables& t, double /*L2*/, doubl
 // ---------------------------------------------------------------------------
 // operator
 
-constexpr int TX = 16, TY = 8, TZ = 8;
+// Node tiles of the operator: X x Y x Z owned nodes plus a halo of k.  The
+// shape is picked per mesh (pick_shape) to waste the fewest nodes on partial
+// tiles; e.g. 22 x 13 tiles cover a 65 x 65 node plane with 1.5 % waste
+// where 16 x 8 tiles waste 27 %.
+template <int X_, int Y_, int Z_>
+struct Shape {
+  static constexpr int X = X_, Y = Y_, Z = Z_;
+};
+using Shape0 = Shape<16, 8, 8>;
+using Shape1 = Shape<22, 13, 4>;
+using Shape2 = Shape<25, 15, 4>;
+constexpr int kShapes = 3;
 constexpr int kApplyThreads = 256;
 
-template <int K>
+template <int K, class S>
 struct Tile {
+  static constexpr int TX = S::X, TY = S::Y, TZ = S::Z;
   static constexpr int H = K;
   static constexpr int XW = TX + 2 * H, YW = TY + 2 * H, ZW = TZ + 2 * H;
   static constexpr int NX = ZW * YW * XW;     // input with halo
@@ -333,11 +346,12 @@ struct EpiResidualDf {
 // file).  ld(g, own) gives the input value at node g; ep(g, acc, x_eff)
 // consumes the result of an owned node and returns its share of a dot
 // product.
-template <int K, typename T, class Load, class Epi>
+template <int K, class S, typename T, class Load, class Epi>
 __device__ __forceinline__ double apply_tile(const MeshDev& m, const T* __restrict__ bands,
                                              const Coefs<T>& cf, const Load& ld, const Epi& ep,
                                              T* sm) {
-  using TL = Tile<K>;
+  using TL = Tile<K, S>;
+  constexpr int TX = TL::TX, TY = TL::TY, TZ = TL::TZ;
   constexpr int H = K, W = 2 * K + 1;
   const int nx = m.nn[0], ny = m.nn[1], nz = m.nn[2];
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
@@ -477,19 +491,19 @@ __device__ bool last_block_reduce(double* partials, int nvals, const double* val
   return true;
 }
 
-template <int K, typename T>
+template <int K, class S, typename T>
 __global__ void __launch_bounds__(kApplyThreads)
 k_apply(MeshDev m, const T* __restrict__ bands, Coefs<T> cf, const T* __restrict__ x,
         T* __restrict__ y) {
   extern __shared__ __align__(16) unsigned char smraw[];
   LoadPlain<T> ld{x};
   EpiStore<T> ep{y};
-  apply_tile<K, T>(m, bands, cf, ld, ep, reinterpret_cast<T*>(smraw));
+  apply_tile<K, S, T>(m, bands, cf, ld, ep, reinterpret_cast<T*>(smraw));
 }
 
 // CG step 1: p = z + beta p_old (fused into the load) ; Ap = A p ; alpha =
 // rz / (p . Ap)
-template <int K, typename T>
+template <int K, class S, typename T>
 __global__ void __launch_bounds__(kApplyThreads)
 k_cg_apply(MeshDev m, const T* __restrict__ bands, Coefs<T> cf, const T* __restrict__ z,
            const T* __restrict__ p_old, T* __restrict__ p_new, T* __restrict__ Ap,
@@ -500,7 +514,7 @@ k_cg_apply(MeshDev m, const T* __restrict__ bands, Coefs<T> cf, const T* __restr
   T beta = first ? (T)0 : (T)sc->beta;
   LoadDir<T> ld{z, p_old, p_new, beta, first != 0};
   EpiStore<T> ep{Ap};
-  double d = apply_tile<K, T>(m, bands, cf, ld, ep, reinterpret_cast<T*>(smraw));
+  double d = apply_tile<K, S, T>(m, bands, cf, ld, ep, reinterpret_cast<T*>(smraw));
   double s = block_sum(d, red);
   double vals[1] = {s};
   double out[1];
@@ -611,12 +625,16 @@ k_cg_update_fdm(int64_t n, TX_* __restrict__ xv, T* __restrict__ r, const T* __r
 
 // after z_new = P^-1 r: z_new (from the FP32 FDM output zf) ; rz_new = r . z_new ;
 // Polak-Ribiere beta = (rz_new - r . z_old) / rz_old (robust to the rounding
-// of the FP32 preconditioner) ; first: plain rz
+// of the FP32 preconditioner) ; first: plain rz.  With fletcher_reeves the
+// plain beta = rz_new / rz_old is used: when the dots are formed from FP32
+// products, r . z_old (zero in exact arithmetic, large terms) carries an
+// error of order 1e-7 |r||z_old|, which is comparable to rz_new itself once
+// the residual has dropped by 1e-6 and would spoil the Polak-Ribiere beta
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_cg_dot_fdm(int64_t n, const T* __restrict__ r, const float* __restrict__ zf,
              const T* __restrict__ z_old, T* __restrict__ z_new, double* partials,
-             CgScalars* sc, int first, int ignore_done) {
+             CgScalars* sc, int first, int ignore_done, int fletcher_reeves = 0) {
   if (!ignore_done && ((volatile CgScalars*)sc)->done) return;
   __shared__ double red[32];
   // per-thread sums in T (a few terms each), one conversion per thread: FP64
@@ -628,7 +646,7 @@ k_cg_dot_fdm(int64_t n, const T* __restrict__ r, const float* __restrict__ zf,
     if (zf) z_new[i] = zi;
     T ri = r[i];
     rz += ri * zi;
-    if (!first) rzo += ri * z_old[i];
+    if (!first && !fletcher_reeves) rzo += ri * z_old[i];
   }
   double s1 = block_sum((double)rz, red);
   double s2 = block_sum((double)rzo, red);
@@ -703,7 +721,7 @@ __global__ void k_join_df(int64_t n, const df64* __restrict__ in, double* __rest
 }
 
 // r = b - A x (df64), r32 = hi(r), r . r ; tolerance and convergence flag
-template <int K>
+template <int K, class S>
 __global__ void __launch_bounds__(kApplyThreads)
 k_residual_df(MeshDev m, const df64* __restrict__ bands, Coefs<df64> cf,
               const df64* __restrict__ x, const df64* __restrict__ b, df64* __restrict__ r,
@@ -712,7 +730,7 @@ k_residual_df(MeshDev m, const df64* __restrict__ bands, Coefs<df64> cf,
   __shared__ double red[32];
   LoadPlain<df64> ld{x};
   EpiResidualDf ep{b, r, r32};
-  double d = apply_tile<K, df64>(m, bands, cf, ld, ep, reinterpret_cast<df64*>(smraw));
+  double d = apply_tile<K, S, df64>(m, bands, cf, ld, ep, reinterpret_cast<df64*>(smraw));
   double s = block_sum(d, red);
   double vals[1] = {s};
   double out[1];
@@ -727,7 +745,7 @@ k_residual_df(MeshDev m, const df64* __restrict__ bands, Coefs<df64> cf,
 }
 
 // p = z + beta p_old (df64) ; Ap = A p in df64 ; alpha = rz / (p . Ap)
-template <int K>
+template <int K, class S>
 __global__ void __launch_bounds__(kApplyThreads)
 k_cg_apply_df(MeshDev m, const df64* __restrict__ bands, Coefs<df64> cf,
               const float* __restrict__ z, const df64* __restrict__ p_old,
@@ -738,7 +756,7 @@ k_cg_apply_df(MeshDev m, const df64* __restrict__ bands, Coefs<df64> cf,
   __shared__ double red[32];
   LoadDirDf ld{z, p_old, p_new, first ? df64(0.f) : df_from_double(sc->beta), first != 0};
   EpiStoreDf ep{Ap};
-  double d = apply_tile<K, df64>(m, bands, cf, ld, ep, reinterpret_cast<df64*>(smraw));
+  double d = apply_tile<K, S, df64>(m, bands, cf, ld, ep, reinterpret_cast<df64*>(smraw));
   double s = block_sum(d, red);
   double vals[1] = {s};
   double out[1];
@@ -840,19 +858,68 @@ __global__ void k_add_scaled(int64_t n, double* __restrict__ x, const float* __r
 // ---------------------------------------------------------------------------
 // host side
 
-template <int K, typename T>
+template <int K, class S, typename T>
 static size_t apply_smem() {
-  using TL = Tile<K>;
+  using TL = Tile<K, S>;
   return ((size_t)TL::NX + 2 * (size_t)TL::NT + 2 * (size_t)TL::NU) * sizeof(T);
 }
 
+template <class S>
+static dim3 apply_grid_s(const MeshDev& m) {
+  return dim3((m.nn[0] + S::X - 1) / S::X, (m.nn[1] + S::Y - 1) / S::Y,
+              (m.nn[2] + S::Z - 1) / S::Z);
+}
+
+// call f(Shape) with the mesh's tile shape
+template <class F>
+static auto with_shape(const MeshDev& m, F&& f) {
+  if (m.shape == 1) return f(Shape1{});
+  if (m.shape == 2) return f(Shape2{});
+  return f(Shape0{});
+}
+
+// call f(integral_constant<int, k>)
+template <class F>
+static auto with_k(const MeshDev& m, F&& f) {
+  if (m.k == 1) return f(std::integral_constant<int, 1>{});
+  if (m.k == 2) return f(std::integral_constant<int, 2>{});
+  return f(std::integral_constant<int, 3>{});
+}
+
 static dim3 apply_grid(const MeshDev& m) {
-  return dim3((m.nn[0] + TX - 1) / TX, (m.nn[1] + TY - 1) / TY, (m.nn[2] + TZ - 1) / TZ);
+  return with_shape(m, [&](auto s) { return apply_grid_s<decltype(s)>(m); });
+}
+
+// work of one tile in 1D taps: z pass on the haloed x-y columns, y pass on
+// the x-haloed rows, x pass on the owned nodes
+template <int K, class S>
+static double tile_cost(const MeshDev& m) {
+  using TL = Tile<K, S>;
+  dim3 g = apply_grid_s<S>(m);
+  double per = 2.0 * TL::TZ * TL::YW * TL::XW + 3.0 * TL::TZ * TL::TY * TL::XW +
+               2.0 * TL::TZ * TL::TY * TL::TX;
+  return per * g.x * g.y * g.z;
+}
+
+int pick_shape(const MeshDev& m) {
+  return with_k(m, [&](auto kc) {
+    constexpr int K = decltype(kc)::value;
+    double c[kShapes] = {tile_cost<K, Shape0>(m), tile_cost<K, Shape1>(m), tile_cost<K, Shape2>(m)};
+    size_t sm[kShapes] = {apply_smem<K, Shape0, double>(), apply_smem<K, Shape1, double>(),
+                          apply_smem<K, Shape2, double>()};
+    int best = 0;
+    for (int i = 1; i < kShapes; ++i)
+      if (sm[i] <= 200 * 1024 && c[i] < 0.97 * c[best]) best = i;
+    return best;
+  });
 }
 
 int cg_blocks(const MeshDev& m) {
-  dim3 g = apply_grid(m);
-  int na = (int)(g.x * g.y * g.z);
+  int na = 0;
+  dim3 g0 = apply_grid_s<Shape0>(m), g1 = apply_grid_s<Shape1>(m), g2 = apply_grid_s<Shape2>(m);
+  na = (int)(g0.x * g0.y * g0.z);
+  na = na > (int)(g1.x * g1.y * g1.z) ? na : (int)(g1.x * g1.y * g1.z);
+  na = na > (int)(g2.x * g2.y * g2.z) ? na : (int)(g2.x * g2.y * g2.z);
   return na > 1216 ? na : 1216;
 }
 
@@ -866,15 +933,15 @@ static Coefs<T> make_coefs(const double* c) {
   return cf;
 }
 
-template <int K, typename T>
+template <int K, class S, typename T>
 static cudaError_t set_smem() {
   static bool done = false;
   if (done) return cudaSuccess;
-  size_t sm = apply_smem<K, T>();
-  cudaError_t e = cudaFuncSetAttribute(k_apply<K, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sm);
+  size_t sm = apply_smem<K, S, T>();
+  cudaError_t e = cudaFuncSetAttribute(k_apply<K, S, T>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_cg_apply<K, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(k_cg_apply<K, S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sm);
   if (e == cudaSuccess) done = true;
   return e;
@@ -883,44 +950,38 @@ static cudaError_t set_smem() {
 template <typename T>
 static cudaError_t apply_t(const MeshDev& m, const T* bands, const double* coef, const T* x,
                            T* y, cudaStream_t s) {
-  dim3 g = apply_grid(m);
   Coefs<T> cf = make_coefs<T>(coef);
-  cudaError_t e;
-#define CFDEM_APPLY(KK)                                                                    \
-  if (m.k == KK) {                                                                         \
-    if ((e = set_smem<KK, T>()) != cudaSuccess) return e;                                  \
-    k_apply<KK, T><<<g, kApplyThreads, apply_smem<KK, T>(), s>>>(m, bands, cf, x, y);      \
-    count_launches(1);                                                                     \
-    return cudaGetLastError();                                                             \
-  }
-  CFDEM_APPLY(1)
-  CFDEM_APPLY(2)
-  CFDEM_APPLY(3)
-#undef CFDEM_APPLY
-  return cudaErrorInvalidValue;
+  return with_k(m, [&](auto kc) {
+    constexpr int K = decltype(kc)::value;
+    return with_shape(m, [&](auto sh) {
+      using S = decltype(sh);
+      cudaError_t e = set_smem<K, S, T>();
+      if (e != cudaSuccess) return e;
+      k_apply<K, S, T><<<apply_grid_s<S>(m), kApplyThreads, apply_smem<K, S, T>(), s>>>(
+          m, bands, cf, x, y);
+      count_launches(1);
+      return cudaGetLastError();
+    });
+  });
 }
 
 template <typename T>
 static cudaError_t cg_apply_t(const MeshDev& m, const T* bands, const double* coef, const T* z,
                               const T* p_old, T* p_new, T* Ap, double* partials, CgScalars* sc,
                               int first, cudaStream_t s) {
-  dim3 g = apply_grid(m);
   Coefs<T> cf = make_coefs<T>(coef);
-  cudaError_t e;
-#define CFDEM_CGA(KK)                                                                       \
-  if (m.k == KK) {                                                                          \
-    if ((e = set_smem<KK, T>()) != cudaSuccess) return e;                                   \
-    k_cg_apply<KK, T><<<g, kApplyThreads, apply_smem<KK, T>(), s>>>(m, bands, cf, z, p_old, \
-                                                                    p_new, Ap, partials, sc,\
-                                                                    first);                 \
-    count_launches(1);                                                                      \
-    return cudaGetLastError();                                                              \
-  }
-  CFDEM_CGA(1)
-  CFDEM_CGA(2)
-  CFDEM_CGA(3)
-#undef CFDEM_CGA
-  return cudaErrorInvalidValue;
+  return with_k(m, [&](auto kc) {
+    constexpr int K = decltype(kc)::value;
+    return with_shape(m, [&](auto sh) {
+      using S = decltype(sh);
+      cudaError_t e = set_smem<K, S, T>();
+      if (e != cudaSuccess) return e;
+      k_cg_apply<K, S, T><<<apply_grid_s<S>(m), kApplyThreads, apply_smem<K, S, T>(), s>>>(
+          m, bands, cf, z, p_old, p_new, Ap, partials, sc, first);
+      count_launches(1);
+      return cudaGetLastError();
+    });
+  });
 }
 
 cudaError_t launch_apply64(const MeshDev& m, const double* bands, const double* coef,
@@ -1089,14 +1150,15 @@ static cudaError_t cg_solve_fdm(const MeshDev& m, const T* bands, const double* 
   return cudaSuccess;
 }
 
-template <int K>
+template <int K, class S>
 static cudaError_t set_smem_df() {
   static bool done = false;
   if (done) return cudaSuccess;
-  int sm = (int)apply_smem<K, df64>();
-  cudaError_t e = cudaFuncSetAttribute(k_residual_df<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  int sm = (int)apply_smem<K, S, df64>();
+  cudaError_t e =
+      cudaFuncSetAttribute(k_residual_df<K, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_cg_apply_df<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    e = cudaFuncSetAttribute(k_cg_apply_df<K, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e == cudaSuccess) done = true;
   return e;
 }
@@ -1119,7 +1181,7 @@ static Coefs<df64> split_coefs(const double* c) {
 // FP32 -- Krylov-accelerated mixed-precision iterative refinement: the FP32
 // preconditioner is the inner solver, the df64 residual keeps the outer
 // accuracy at ~1e-14 without the FP64 pipes.
-template <int K>
+template <int K, class S>
 static cudaError_t cg_solve_df(const MeshDev& m, const df64* bands, const double* coef,
                                const double* b, double* x, double rtol, int maxit, CgWork& w,
                                cudaStream_t s, int* iters, double* relres) {
@@ -1127,14 +1189,14 @@ static cudaError_t cg_solve_df(const MeshDev& m, const df64* bands, const double
   int64_t n = m.n_nodes;
   int vb = vec_blocks(n);
   Coefs<df64> cf = split_coefs(coef);
-  if ((e = set_smem_df<K>()) != cudaSuccess) return e;
-  const dim3 g = apply_grid(m);
-  const size_t sm = apply_smem<K, df64>();
+  if ((e = set_smem_df<K, S>()) != cudaSuccess) return e;
+  const dim3 g = apply_grid_s<S>(m);
+  const size_t sm = apply_smem<K, S, df64>();
   Timer* tm = w.timer;
   if ((e = cudaMemsetAsync(w.sc, 0, sizeof(CgScalars), s)) != cudaSuccess) return e;
   k_split_df<<<vb, 256, 0, s>>>(n, b, w.b_df, x, w.x_df, w.partials, w.sc);
   if (tm) tm->begin(kStageOp32, s);
-  k_residual_df<K><<<g, kApplyThreads, sm, s>>>(m, bands, cf, w.x_df, w.b_df, w.r_df, w.r32,
+  k_residual_df<K, S><<<g, kApplyThreads, sm, s>>>(m, bands, cf, w.x_df, w.b_df, w.r_df, w.r32,
                                                 w.partials, w.sc, rtol);
   if (tm) tm->end(kStageOp32, s);
   count_launches(2);
@@ -1157,7 +1219,7 @@ static cudaError_t cg_solve_df(const MeshDev& m, const df64* bands, const double
     for (int c = 0; c < todo; ++c) {
       int first = launched + c == 0;
       if (tm) tm->begin(kStageOp32, s);
-      k_cg_apply_df<K><<<g, kApplyThreads, sm, s>>>(m, bands, cf, zc, pc, pn, w.Ap_df,
+      k_cg_apply_df<K, S><<<g, kApplyThreads, sm, s>>>(m, bands, cf, zc, pc, pn, w.Ap_df,
                                                     w.partials, w.sc, first);
       if (tm) tm->end(kStageOp32, s);
       k_cg_update_df<<<vb, 256, 0, s>>>(n, w.x_df, w.r_df, pn, w.Ap_df, w.r32, w.partials, w.sc,
@@ -1165,7 +1227,8 @@ static cudaError_t cg_solve_df(const MeshDev& m, const df64* bands, const double
       count_launches(2);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       if ((e = fdm_apply(w.fdm, w.r32, zo, &w.sc->done, s)) != cudaSuccess) return e;
-      k_cg_dot_fdm<float><<<vb, 256, 0, s>>>(n, w.r32, nullptr, zc, zo, w.partials, w.sc, 0, 0);
+      k_cg_dot_fdm<float><<<vb, 256, 0, s>>>(n, w.r32, nullptr, zc, zo, w.partials, w.sc, 0, 0,
+                                             1);
       count_launches(1);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       float* t = zc;
@@ -1223,9 +1286,13 @@ cudaError_t run_cg_mixed(const MeshDev& m, const double* bands64, const float* b
   if (w.fdm && w.bands_df) {
     int it = 0;
     double rel = 0.0;
-    if (m.k == 1) e = cg_solve_df<1>(m, w.bands_df, coef, b, x, rtol, maxit, w, s, &it, &rel);
-    else if (m.k == 2) e = cg_solve_df<2>(m, w.bands_df, coef, b, x, rtol, maxit, w, s, &it, &rel);
-    else e = cg_solve_df<3>(m, w.bands_df, coef, b, x, rtol, maxit, w, s, &it, &rel);
+    e = with_k(m, [&](auto kc) {
+      constexpr int K = decltype(kc)::value;
+      return with_shape(m, [&](auto sh) {
+        return cg_solve_df<K, decltype(sh)>(m, w.bands_df, coef, b, x, rtol, maxit, w, s, &it,
+                                             &rel);
+      });
+    });
     if (e != cudaSuccess) return e;
     *iters_host = it;
     *outer_host = it;
