@@ -203,6 +203,36 @@ cfdem_status cfdem_synchronize(cfdem_t ctx);
 /* Synchronize, then copy the counters into *out. */
 cfdem_status cfdem_get_stats(cfdem_t ctx, cfdem_stats *out);
 
+/* Largest element count accepted by cfdem_pcm_void_fraction_static. */
+#define CFDEM_PCM_STATIC_MAX_ELEMS 524288
+
+/* Particle-centroid void fraction that allocates nothing.  The paper has no
+ * counterpart: this is a service to callers that cannot allocate device
+ * memory -- solvers that hand all of the GPU's memory to their own pool, and
+ * loops that must not take the device-wide synchronisation a cudaMalloc may
+ * cause.
+ * It needs no context: mesh as in cfdem_set_mesh (host arrays), particles
+ * x_dev[n][3], r_dev[n] and the output eps_q_dev[E][Q] on the current device,
+ * work ordered on `stream` (a cudaStream_t, NULL = legacy default).  The
+ * result equals cfdem_void_fraction with scheme = 1 (eps_e = (V_e - sum of
+ * V_p,i of the particles centred in e) / V_e on every Gauss point of e).
+ *   - The per-element scratch is one fixed device array of
+ *     CFDEM_PCM_STATIC_MAX_ELEMS doubles (4 MiB) compiled into the library
+ *     and kept by every GPU that loads it until the process exits; meshes
+ *     with more elements return CFDEM_EINVAL.
+ *   - The first call on a device looks the array's address up (no
+ *     allocation); make that first call before any stream capture.
+ *   - All calls share the array: each call clears it on its stream before
+ *     use, but calls that overlap on the GPU (on different streams, or from
+ *     several threads) race on it and must be serialised by the caller.
+ *   - Particles outside the mesh are left out and not reported.
+ * Returns CFDEM_EINVAL on bad arguments or too many elements, CFDEM_ECUDA if
+ * a CUDA call fails, else CFDEM_OK without synchronising. */
+cfdem_status cfdem_pcm_void_fraction_static(const double origin[3], const double extent[3],
+                                            const int n_el[3], int degree, int64_t n,
+                                            const double *x_dev, const double *r_dev,
+                                            double *eps_q_dev, void *stream);
+
 /* Turn the per-stage CUDA-event timers on (1) or off (0) and reset them and
  * the launch counter.  Synchronizes the stream.  Timers record an event pair
  * per stage and per operator launch; they do not change results. */

@@ -93,6 +93,8 @@ def lib():
     L.cfdem_synchronize.argtypes = [vp]
     L.cfdem_get_stats.argtypes = [vp, C.POINTER(cfdem_stats)]
     L.cfdem_set_timing.argtypes = [vp, cint]
+    L.cfdem_pcm_void_fraction_static.argtypes = [d3, d3, C.POINTER(cint), cint, i64, vp, vp, vp,
+                                                 vp]
     L.cfdem_last_error.argtypes = [vp]
     L.cfdem_last_error.restype = C.c_char_p
     _lib = L
@@ -208,6 +210,19 @@ def cfdem_get_stats(h):
     s = cfdem_stats()
     _check(h, lib().cfdem_get_stats(h, C.byref(s)))
     return s
+
+
+PCM_STATIC_MAX_ELEMS = 524288
+
+
+def cfdem_pcm_void_fraction_static(origin, extent, n_el, degree, n, x, r, eps_q, stream=None):
+    """Particle-centroid void fraction without any device allocation (see
+    include/cfdem.h); returns the status code."""
+    o = (C.c_double * 3)(*[float(v) for v in origin])
+    e = (C.c_double * 3)(*[float(v) for v in extent])
+    ne = (C.c_int * 3)(*[int(v) for v in n_el])
+    return lib().cfdem_pcm_void_fraction_static(o, e, ne, int(degree), int(n), _ptr(x), _ptr(r),
+                                                _ptr(eps_q), C.c_void_p(stream or 0))
 
 
 def cfdem_set_timing(h, enable):
