@@ -64,10 +64,23 @@ class Clocks:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + q,
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
+
+    def wait_first(self, timeout=3.0):
+        """Block until nvidia-smi has written its first sample (so that the
+        samples cover the timed region that follows)."""
+        t0 = time.time()
+        while self.p is not None and time.time() - t0 < timeout:
+            self.f.flush()
+            try:
+                if os.path.getsize(self.f.name) > 0:
+                    return
+            except OSError:
+                return
+            time.sleep(0.02)
 
     def stop(self):
         if self.p is None:
@@ -153,6 +166,194 @@ def run_reference(args):
     return 0
 
 
+def run_batch(args):
+    """The ensemble of 64 independent beds (Q1-Q3, 8-32 elements per axis, z up
+    to 64, N log-uniform in [5e3, 2e5]): one cfdem_batch_coupling_step per step
+    (one CUDA-graph replay after the first), against the same 64 beds stepped
+    one after another through cfdem_coupling_step on one stream."""
+    import torch
+    from paper_2211_01185_gb300 import build as B
+    from paper_2211_01185_gb300 import cfdem as cf
+    from paper_2211_01185_gb300 import synth
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.build()
+    beds = synth.make_batch_workload(64)
+    prec = 0 if args.precision == "fp64" else 1
+    for b in beds:
+        b["params"] = dict(b["params"], precision=prec, cg_rtol=1e-13 if prec == 0 else 1e-12,
+                           max_radius=float(b["r"].max()))
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    t = lambda a: torch.as_tensor(a, dtype=torch.float64).to(dev).contiguous()  # noqa: E731
+    bufs = []
+    with torch.cuda.stream(stream):
+        for b in beds:
+            n = b["x"].shape[0]
+            ne = int(np.prod(b["n_el"]))
+            nn = b["u_nodal"].shape[0]
+            bufs.append(dict(n=n, x=t(b["x"]), r=t(b["r"]), u_p=t(b["u_p"]), u=t(b["u_nodal"]),
+                             p=t(b["p_nodal"]),
+                             eps=torch.zeros(nn, dtype=torch.float64, device=dev),
+                             f=torch.empty((n, 3), dtype=torch.float64, device=dev),
+                             fd=torch.empty((n, 3), dtype=torch.float64, device=dev),
+                             Fe=torch.empty((ne, 3), dtype=torch.float64, device=dev)))
+    n_tot = sum(bb["n"] for bb in bufs)
+    ios = [cf.bed_io(bb["n"], bb["x"], bb["r"], bb["u_p"], bb["u"], bb["p"], bb["eps"], bb["f"],
+                     bb["fd"], bb["Fe"]) for bb in bufs]
+    bh = cf.cfdem_batch_create(len(beds), local, stream.cuda_stream)
+    for i, b in enumerate(beds):
+        h = cf.cfdem_batch_bed(bh, i)
+        cf.cfdem_set_mesh(h, b["origin"], b["extent"], b["n_el"], b["k"])
+        cf.cfdem_set_params(h, cf.make_params(**b["params"]))
+    solo = [cf.Context(b["origin"], b["extent"], b["n_el"], b["k"], b["params"], device=local,
+                       stream=stream.cuda_stream) for b in beds]
+
+    def zero_eps():
+        for bb in bufs:
+            bb["eps"].zero_()   # cold start of every projection
+
+    def step_batch():
+        zero_eps()
+        st = cf.cfdem_batch_coupling_step(bh, ios)
+        if st != cf.OK:
+            raise RuntimeError("batch step failed: %d" % st)
+
+    def step_solo():
+        zero_eps()
+        for c, bb in zip(solo, bufs):
+            cf.cfdem_coupling_step(c.h, bb["n"], bb["x"], bb["r"], bb["u_p"], bb["u"], bb["p"],
+                                   bb["eps"], bb["f"], bb["fd"], bb["Fe"])
+
+    def timed(fn, k):
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize(dev)
+            clk = Clocks(local)
+            clk.wait_first()
+            ev = []
+            for _ in range(k):
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                e = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                e.record(stream)
+                ev.append((a, e))
+            torch.cuda.synchronize(dev)
+            clocks = clk.stop()
+        return float(np.mean([a.elapsed_time(e) for a, e in ev])), clocks
+
+    ms_b, clk_b = timed(step_batch, args.steps)
+    st, bad = cf.cfdem_batch_synchronize(bh)
+    replayed = cf.cfdem_batch_last_replayed(bh)
+    its = [cf.cfdem_get_stats(cf.cfdem_batch_bed(bh, i)).cg_iterations for i in range(len(beds))]
+    ms_s, clk_s = timed(step_solo, max(3, args.steps // 4))
+    for c in solo:
+        cf.cfdem_synchronize(c.h)
+    res = {"metric": METRIC, "value": n_tot / (ms_b * 1e-3), "unit": "particle updates/s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64" if prec == 1 else "f64", "data": "synthetic",
+           "config": {"workload": "batch64: 64 beds Q1-Q3, N log-uniform [5e3, 2e5]",
+                      "beds": len(beds), "particles": n_tot,
+                      "nodes": int(sum(b["u_nodal"].shape[0] for b in beds)),
+                      "precision": "mixed" if prec == 1 else "fp64", "cold_start": True,
+                      "l2": "256 MiB buffer written between timed steps",
+                      "parallelism": "single GPU, beds as parallel graph branches"},
+           "graph_replayed": replayed, "batch_status": st,
+           "cg_iterations": {"min": min(its), "max": max(its)},
+           "solo_sequential": {"value": n_tot / (ms_s * 1e-3), "ms_per_step": ms_s,
+                               "speedup_of_batch": ms_s / ms_b},
+           "clocks": clk_b, "clocks_solo": clk_s}
+    print(json.dumps(res), flush=True)
+    cf.cfdem_batch_destroy(bh)
+    for c in solo:
+        c.close()
+    return 0
+
+
+def run_adjoint(args):
+    """The sensitivity workload (24x24x96 Q2, 200,000 spheres, annulus and jet):
+    one step = the forward coupling step and the adjoint of J = sum_i e_z .
+    f_D,i + ||eps_h||_M (dJ/dx and dJ/du), FP64 and mixed."""
+    import torch
+    from paper_2211_01185_gb300 import build as B
+    from paper_2211_01185_gb300 import cfdem as cf
+    from paper_2211_01185_gb300 import synth
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.build()
+    w = synth.make_adjoint_workload()
+    n = w["x"].shape[0]
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    t = lambda a: torch.as_tensor(a, dtype=torch.float64).to(dev).contiguous()  # noqa: E731
+    out = {}
+    with torch.cuda.stream(stream):
+        x, r, up, un, pn = t(w["x"]), t(w["r"]), t(w["u_p"]), t(w["u_nodal"]), t(w["p_nodal"])
+        nn = un.shape[0]
+        E = int(np.prod(w["n_el"]))
+        z = lambda *s: torch.zeros(s, dtype=torch.float64, device=dev)  # noqa: E731
+        eps, f, fd, Fe = z(nn), z(n, 3), z(n, 3), z(E, 3)
+        g_fd = z(n, 3)
+        g_fd[:, 2] = 1.0
+        Me, dJdx, dJdu = z(nn), z(n, 3), z(nn, 3)
+    for prec in (0, 1):
+        prm = dict(w["params"], precision=prec, cg_rtol=1e-13 if prec == 0 else 1e-12,
+                   max_radius=float(w["r"].max()))
+        ctx = cf.Context(w["origin"], w["extent"], w["n_el"], w["k"], prm, device=local,
+                         stream=stream.cuda_stream)
+
+        def step():
+            eps.zero_()
+            cf.cfdem_coupling_step(ctx.h, n, x, r, up, un, pn, eps, f, fd, Fe)
+            cf.cfdem_mass_apply(ctx.h, eps, Me)
+            g_eps = Me / torch.sqrt(torch.dot(eps, Me))
+            cf.cfdem_adjoint(ctx.h, n, x, r, up, un, pn, eps, None, g_fd, g_eps, dJdx, dJdu)
+
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                step()
+            cf.cfdem_synchronize(ctx.h)
+            torch.cuda.synchronize(dev)
+            clk = Clocks(local)
+            clk.wait_first()
+            ev = []
+            for _ in range(args.steps):
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                step()
+                b.record(stream)
+                ev.append((a, b))
+            torch.cuda.synchronize(dev)
+            clocks = clk.stop()
+            cf.cfdem_synchronize(ctx.h)
+            st = ctx.stats()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        out[prec] = {"ms_per_step": ms, "value": n / (ms * 1e-3), "adjoint_cg_iterations":
+                     st.cg_iterations, "clocks": clocks,
+                     "dJdx_norm": float(torch.linalg.norm(dJdx).item()),
+                     "dJdu_norm": float(torch.linalg.norm(dJdu).item())}
+        ctx.close()
+    res = {"metric": "particle gradient evaluations/s (forward step + adjoint)",
+           "value": out[1]["value"], "unit": "particle updates/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": out[1]["ms_per_step"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64", "data": "synthetic",
+           "config": {"workload": w["name"], "mesh": "Q2 24x24x96", "particles": n,
+                      "nodes": int(nn), "loss": "sum_i e_z.f_D,i + ||eps_h||_M",
+                      "l2": "256 MiB buffer written between timed steps"},
+           "mixed": out[1], "fp64": out[0]}
+    print(json.dumps(res), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -163,10 +364,17 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"],
                     help="paths to time (profiling runs use one)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch64", "adjoint5"],
+                    help="batch64: the 64-bed ensemble, graph replay against 64 solo runs; "
+                         "adjoint5: forward step + adjoint of J = sum e_z.f_D + ||eps_h||_M")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch64":
+        return run_batch(args)
+    if args.workload == "adjoint5":
+        return run_adjoint(args)
 
     import torch
     from paper_2211_01185_gb300 import build as B
@@ -226,6 +434,7 @@ def main():
                 dist.barrier()
             torch.cuda.synchronize(dev)
             clk = Clocks(local)
+            clk.wait_first()
             for _ in range(k):
                 flush.zero_()                     # evict L2 (256 MiB > 129 MB) between steps
                 a = torch.cuda.Event(enable_timing=True)

@@ -164,10 +164,19 @@ cfdem_status cfdem_project_rhs(cfdem_t ctx, const double *eps_q_dev, double *b_d
 cfdem_status cfdem_apply(cfdem_t ctx, const double *x_dev, double *y_dev);
 
 /* Steps a4-a5 -- smoothed L2 projection: solves (M + L^2 K) eps_h = b by
- * preconditioned CG (FP64) or FP32 CG inside FP64 iterative refinement
- * (mixed); preconditioner Jacobi or fast diagonalisation (cg_precond).  eps_q_dev: NULL = the context's last void fraction.
- * eps_nodal_dev[n_nodes]: start vector on entry, solution on exit.  The
- * iteration count and relative residual go to cfdem_get_stats. */
+ * preconditioned CG.  FP64: CG in FP64.  Mixed: CG with double-float (FP32
+ * pair) iterate, residual and operator and the FP32 preconditioner as inner
+ * solver, or, without the fast-diagonalisation preconditioner, FP32 CG
+ * inside FP64 iterative refinement.  Preconditioner: Jacobi or fast
+ * diagonalisation (cg_precond).  eps_q_dev: NULL = the context's last void
+ * fraction.  eps_nodal_dev[n_nodes]: start vector on entry, solution on exit.
+ * The iteration count and relative residual go to cfdem_get_stats.
+ * While the context's stream is being captured into a CUDA graph the CG
+ * loop becomes a conditional (while) node of that graph that iterates on the
+ * device until convergence or cg_maxit; the statistics of a replay are read
+ * by the next cfdem_synchronize / cfdem_get_stats.  Capture requires the
+ * stage timers off and, for the mixed path, the fast-diagonalisation
+ * preconditioner (else CFDEM_ESTATE). */
 cfdem_status cfdem_project(cfdem_t ctx, const double *eps_q_dev, double *eps_nodal_dev);
 
 /* Steps a6-a7 -- particle forces and fluid source.  Per particle i: u_f,
@@ -194,6 +203,85 @@ cfdem_status cfdem_coupling_step(cfdem_t ctx, int64_t n, const double *x_dev,
                                  const double *u_nodal_dev, const double *p_nodal_dev,
                                  double *eps_nodal_dev, double *f_dev, double *f_drag_dev,
                                  double *F_elem_dev, double *F_q_dev);
+
+/* Adjoint of the coupling step (no counterpart in the paper: the
+ * derivative of a loss J of the step's outputs with respect to its inputs,
+ * for sensitivity studies and gradient-based calibration).  Given the
+ * gradients of J with respect to the forces f (g_f_dev[n][3]), the drag
+ * forces f_D (g_fdrag_dev[n][3]) and the projected void fraction eps_h
+ * (g_eps_dev[n_nodes]) -- each NULL if J does not depend on it -- and the
+ * forward step's inputs with its eps_nodal_dev (eps_h of that step), writes
+ * dJ/dx (dJdx_dev[n][3]) and, if not NULL, dJ/du_nodal (dJdu_dev
+ * [n_nodes][3]), by reverse-mode differentiation through the force closures
+ * (forward-mode duals for their 3 x 4 Jacobian), the interpolations, the
+ * projection (one more CG solve with the same operator, which is symmetric)
+ * and the quadrature-centred void fraction (dV_lens/dd = -pi a^2, a the
+ * radius of the circle where particle and averaging sphere meet).  The
+ * particle-centroid void fraction is piecewise constant in x and adds
+ * nothing; the fluid source is not an output of this derivative.  Precision
+ * follows the context (mixed: closure Jacobian in FP32).  The CG statistics
+ * of the adjoint solve replace those of the forward solve in
+ * cfdem_get_stats. */
+cfdem_status cfdem_adjoint(cfdem_t ctx, int64_t n, const double *x_dev, const double *r_dev,
+                           const double *u_p_dev, const double *u_nodal_dev,
+                           const double *p_nodal_dev, const double *eps_nodal_dev,
+                           const double *g_f_dev, const double *g_fdrag_dev,
+                           const double *g_eps_dev, double *dJdx_dev, double *dJdu_dev);
+
+/* y = M x with M the consistent mass matrix of the nodal Q_k space (the
+ * operator of cfdem_apply without the smoothing term), e.g. for the
+ * gradient M eps_h / ||eps_h||_M of the L2 norm ||eps_h||_M. */
+cfdem_status cfdem_mass_apply(cfdem_t ctx, const double *x_dev, double *y_dev);
+
+/* ---- Batched ensemble of independent beds ------------------------------
+ * An array of beds, each with its own mesh, degree, parameters and
+ * particles, advanced by one coupling step each in one call (the many small
+ * problems of a parameter study or an ensemble, which one at a time leave
+ * most of the GPU idle).  The batch owns one context per bed, each with its
+ * own stream.  The first step, and any step whose bed inputs, meshes or
+ * parameters differ from the previous one, runs every bed eagerly (forked
+ * from and joined to the batch's stream) and then captures the whole
+ * ensemble -- binning, QCM, projection with device-driven CG loops, forces
+ * and sources of all beds as parallel branches -- into one CUDA graph; later
+ * identical steps replay it with a single launch.  Results equal those of
+ * cfdem_coupling_step on each bed alone up to the order of the atomic
+ * additions inside the right-hand side and the fluid source (rounding). */
+typedef struct cfdem_batch *cfdem_batch_t;
+
+/* Per-bed arguments of cfdem_batch_coupling_step: those of
+ * cfdem_coupling_step (device pointers on the batch's device). */
+typedef struct {
+    int64_t n;
+    const double *x, *r, *u_p, *u_nodal, *p_nodal;
+    double *eps_nodal, *f, *f_drag, *F_elem, *F_q;
+} cfdem_bed_io;
+
+/* Create a batch of n_beds (1 .. 4096) empty beds on `device`; `stream`
+ * (a cudaStream_t, NULL = legacy default) orders the batch against the
+ * caller's work. */
+cfdem_status cfdem_batch_create(cfdem_batch_t *out, int device, void *stream, int n_beds);
+/* Synchronise and release the batch, its graph and its bed contexts. */
+cfdem_status cfdem_batch_destroy(cfdem_batch_t b);
+/* The context of bed i, owned by the batch: give it a mesh and parameters
+ * with cfdem_set_mesh / cfdem_set_params, read its statistics with
+ * cfdem_get_stats after cfdem_batch_synchronize.  NULL if i is out of range.
+ * A bed whose step cannot be captured (stage timers on, or a mixed solve
+ * without the fast-diagonalisation preconditioner) keeps the whole batch
+ * eager. */
+cfdem_t cfdem_batch_bed(cfdem_batch_t b, int i);
+/* 1 (default): capture and replay graphs; 0: always run the beds eagerly. */
+cfdem_status cfdem_batch_set_graph(cfdem_batch_t b, int enable);
+/* One coupling step of every bed; io[n_beds] (host array).  Returns without
+ * synchronising; CFDEM_EINVAL for a bad argument, or the first failing
+ * bed's status (cfdem_last_error of that bed tells why). */
+cfdem_status cfdem_batch_coupling_step(cfdem_batch_t b, const cfdem_bed_io *io);
+/* Wait for the batch; then as cfdem_synchronize on every bed.  Returns the
+ * first bed's error (its index in *first_failed_bed, else -1), or CFDEM_OK. */
+cfdem_status cfdem_batch_synchronize(cfdem_batch_t b, int *first_failed_bed);
+/* 1 if the last step was a graph replay, 0 if it ran eagerly. */
+int cfdem_batch_last_replayed(cfdem_batch_t b);
+/* Text of the batch's last failure (empty if none); owned by the batch. */
+const char *cfdem_batch_last_error(cfdem_batch_t b);
 
 /* Wait for the context's stream and return the first device-side error of
  * the calls since the last synchronize (CFDEM_OUT_OF_DOMAIN,

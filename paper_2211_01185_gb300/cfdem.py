@@ -47,6 +47,13 @@ class cfdem_stats(C.Structure):
                 ("stage_calls", C.c_int64 * 8), ("timer_overflow", C.c_int32),
                 ("kernel_launches", C.c_int64), ("precond", C.c_int32)]
 
+class cfdem_bed_io(C.Structure):
+    _fields_ = [("n", C.c_int64), ("x", C.c_void_p), ("r", C.c_void_p), ("u_p", C.c_void_p),
+                ("u_nodal", C.c_void_p), ("p_nodal", C.c_void_p), ("eps_nodal", C.c_void_p),
+                ("f", C.c_void_p), ("f_drag", C.c_void_p), ("F_elem", C.c_void_p),
+                ("F_q", C.c_void_p)]
+
+
 STAGES = ("bin", "void_fraction", "rhs", "solve", "forces", "fluid_source", "op32", "op64")
 
 
@@ -95,6 +102,18 @@ def lib():
     L.cfdem_set_timing.argtypes = [vp, cint]
     L.cfdem_pcm_void_fraction_static.argtypes = [d3, d3, C.POINTER(cint), cint, i64, vp, vp, vp,
                                                  vp]
+    L.cfdem_adjoint.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.cfdem_mass_apply.argtypes = [vp, vp, vp]
+    L.cfdem_batch_create.argtypes = [C.POINTER(vp), cint, vp, cint]
+    L.cfdem_batch_destroy.argtypes = [vp]
+    L.cfdem_batch_bed.argtypes = [vp, cint]
+    L.cfdem_batch_bed.restype = vp
+    L.cfdem_batch_set_graph.argtypes = [vp, cint]
+    L.cfdem_batch_coupling_step.argtypes = [vp, C.POINTER(cfdem_bed_io)]
+    L.cfdem_batch_synchronize.argtypes = [vp, C.POINTER(cint)]
+    L.cfdem_batch_last_replayed.argtypes = [vp]
+    L.cfdem_batch_last_error.argtypes = [vp]
+    L.cfdem_batch_last_error.restype = C.c_char_p
     L.cfdem_last_error.argtypes = [vp]
     L.cfdem_last_error.restype = C.c_char_p
     _lib = L
@@ -223,6 +242,69 @@ def cfdem_pcm_void_fraction_static(origin, extent, n_el, degree, n, x, r, eps_q,
     ne = (C.c_int * 3)(*[int(v) for v in n_el])
     return lib().cfdem_pcm_void_fraction_static(o, e, ne, int(degree), int(n), _ptr(x), _ptr(r),
                                                 _ptr(eps_q), C.c_void_p(stream or 0))
+
+
+def cfdem_adjoint(h, n, x, r, u_p, u_nodal, p_nodal, eps_nodal, g_f, g_fdrag, g_eps, dJdx,
+                  dJdu=None):
+    return _check(h, lib().cfdem_adjoint(h, int(n), _ptr(x), _ptr(r), _ptr(u_p), _ptr(u_nodal),
+                                         _ptr(p_nodal), _ptr(eps_nodal), _ptr(g_f),
+                                         _ptr(g_fdrag), _ptr(g_eps), _ptr(dJdx), _ptr(dJdu)))
+
+
+def cfdem_mass_apply(h, x, y):
+    return _check(h, lib().cfdem_mass_apply(h, _ptr(x), _ptr(y)))
+
+
+def cfdem_batch_create(n_beds, device=0, stream=None):
+    h = C.c_void_p()
+    st = lib().cfdem_batch_create(C.byref(h), int(device), C.c_void_p(stream or 0), int(n_beds))
+    if st != OK:
+        raise CfdemError(st, "cfdem_batch_create failed")
+    return h
+
+
+def cfdem_batch_destroy(b):
+    return lib().cfdem_batch_destroy(b)
+
+
+def cfdem_batch_bed(b, i):
+    """The context handle of bed i (owned by the batch)."""
+    v = lib().cfdem_batch_bed(b, int(i))
+    if not v:
+        raise CfdemError(EINVAL, "bed index out of range")
+    return C.c_void_p(v)
+
+
+def cfdem_batch_set_graph(b, enable):
+    return lib().cfdem_batch_set_graph(b, int(bool(enable)))
+
+
+def bed_io(n, x, r, u_p, u_nodal, p_nodal, eps_nodal, f, f_drag=None, F_elem=None, F_q=None):
+    """One cfdem_bed_io record (device tensors or addresses)."""
+    return cfdem_bed_io(int(n), _ptr(x), _ptr(r), _ptr(u_p), _ptr(u_nodal), _ptr(p_nodal),
+                        _ptr(eps_nodal), _ptr(f), _ptr(f_drag), _ptr(F_elem), _ptr(F_q))
+
+
+def cfdem_batch_coupling_step(b, ios):
+    """One coupling step of every bed; ios: sequence of cfdem_bed_io (one per
+    bed).  Returns the status code."""
+    arr = (cfdem_bed_io * len(ios))(*ios)
+    return lib().cfdem_batch_coupling_step(b, arr)
+
+
+def cfdem_batch_synchronize(b):
+    """Returns (status, first failing bed or -1)."""
+    bad = C.c_int(-1)
+    st = lib().cfdem_batch_synchronize(b, C.byref(bad))
+    return st, bad.value
+
+
+def cfdem_batch_last_replayed(b):
+    return lib().cfdem_batch_last_replayed(b)
+
+
+def cfdem_batch_last_error(b):
+    return lib().cfdem_batch_last_error(b).decode()
 
 
 def cfdem_set_timing(h, enable):

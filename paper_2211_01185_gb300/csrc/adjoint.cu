@@ -1,0 +1,465 @@
+// adjoint.cu -- gradients of a loss of the coupling step's outputs with
+// respect to the particle positions x and the nodal fluid velocities u.
+//
+// The coupling step maps (x, u) to the forces f (and their drag part f_D)
+// and to the projected void fraction eps_h.  Given the gradients of a loss J
+// with respect to those outputs (g_f, g_fD per particle, g_eps per node),
+// reverse-mode differentiation through the steps of the method gives:
+//
+//  forces (Sec. 2.3.2): f_D depends on the slip U = u_f(x) - u_p and on the
+//    clamped void fraction eps_c(x) at the particle; f_gradp = -V_p grad
+//    p(x).  With a_U = (df_D/dU)^T (g_f + g_fD) and a_eps = (df_D/deps_c)^T
+//    (g_f + g_fD) (zero where the clamp is active):
+//      dJ/du_j    += phi_j(x) a_U                      (scatter to nodes)
+//      dJ/deps_h,j += phi_j(x) a_eps                   (scatter to nodes)
+//      dJ/dx      += (grad u_f)^T a_U + a_eps grad eps - V_p H_p g_f
+//    with H_p the Hessian of the interpolated pressure.  The 3 x 4 Jacobian
+//    of f_D is taken by forward differentiation of the closure on dual
+//    numbers carrying four derivatives.
+//  projection: eps_h = A^-1 b(eps_q) with A = M + L^2 K symmetric, so the
+//    adjoint is lambda = A^-1 dJ/deps_h and dJ/deps_q = w_q |J_e| lambda_h(x_q)
+//    (the transpose of the right-hand side's quadrature).
+//  quadrature-centred void fraction: eps_q = 1 - sum_i V(R, r_i, d_iq) / V_R
+//    with d_iq = |x_i - x_q|.  The lens volume decreases at the rate of the
+//    area of the circle in which the two spheres meet, dV/dd = -pi a^2 with
+//    a^2 = (4 d^2 R^2 - (d^2 - r^2 + R^2)^2) / (4 d^2) for |R - r| < d <
+//    R + r (zero outside: full containment or no contact), so
+//      dJ/dx_i += sum_q dJ/deps_q (pi a^2 / V_R) (x_i - x_q) / d_iq.
+//    One thread per particle gathers over the Gauss points within R + r_i,
+//    in a fixed order, so this part needs no atomics.
+// The particle-centroid scheme is piecewise constant in x: it adds nothing.
+#include <cstdint>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace cfdem {
+namespace {
+
+// ---------------------------------------------------------------- duals
+
+template <typename T>
+struct D4 {  // value and derivatives along (U_0, U_1, U_2, eps_c)
+  T v, d[4];
+};
+
+template <typename T>
+__device__ __forceinline__ D4<T> dc(T v) {
+  D4<T> r;
+  r.v = v;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) r.d[j] = (T)0;
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ D4<T> dv(T v, int j) {
+  D4<T> r = dc<T>(v);
+  r.d[j] = (T)1;
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ D4<T> operator+(D4<T> a, D4<T> b) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) a.d[j] += b.d[j];
+  a.v += b.v;
+  return a;
+}
+template <typename T>
+__device__ __forceinline__ D4<T> operator-(D4<T> a, D4<T> b) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) a.d[j] -= b.d[j];
+  a.v -= b.v;
+  return a;
+}
+template <typename T>
+__device__ __forceinline__ D4<T> operator*(D4<T> a, D4<T> b) {
+  D4<T> r;
+  r.v = a.v * b.v;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) r.d[j] = a.d[j] * b.v + a.v * b.d[j];
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ D4<T> operator*(T s, D4<T> a) {
+  a.v *= s;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) a.d[j] *= s;
+  return a;
+}
+template <typename T>
+__device__ __forceinline__ D4<T> operator/(D4<T> a, D4<T> b) {
+  D4<T> r;
+  r.v = a.v / b.v;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) r.d[j] = (a.d[j] - r.v * b.d[j]) / b.v;
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ D4<T> d_sqrt(D4<T> a) {
+  D4<T> r;
+  r.v = t_sqrt<T>(a.v);
+  T k = r.v > (T)0 ? (T)0.5 / r.v : (T)0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) r.d[j] = k * a.d[j];
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ D4<T> d_exp(D4<T> a) {
+  D4<T> r;
+  r.v = Closure<T>::exp_(a.v);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) r.d[j] = r.v * a.d[j];
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ D4<T> d_log(D4<T> a, T scale) {  // scale * ln(a) derivative
+  D4<T> r;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) r.d[j] = scale * a.d[j] / a.v;
+  r.v = (T)0;
+  return r;
+}
+
+// the drag closure of the forward kernel on dual numbers: fd[c] = coef U_c
+template <typename T>
+__device__ __forceinline__ void drag_dual(const ForceParams& fp, T rp, T U0v, T U1v, T U2v,
+                                          T epscv, bool clamped, D4<T> fd[3]) {
+  D4<T> U[3] = {dv<T>(U0v, 0), dv<T>(U1v, 1), dv<T>(U2v, 2)};
+  D4<T> ec = clamped ? dc<T>(epscv) : dv<T>(epscv, 3);
+  D4<T> speed = d_sqrt<T>(U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
+  if (!(speed.v > (T)0)) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) fd[c] = dc<T>((T)0);
+    return;
+  }
+  const T rho = (T)fp.rho, mu = (T)fp.mu, dp = (T)2 * rp;
+  D4<T> a = (T)0.63 * d_sqrt<T>(speed) + (T)4.8 * d_sqrt<T>(dc<T>(mu) / (rho * dp * ec));
+  D4<T> cds = a * a;
+  if (fp.drag_model == 0) {
+    D4<T> Re = (rho * dp / mu) * (ec * speed);
+    if (!(Re.v > Closure<T>::tiny())) Re = dc<T>(Closure<T>::tiny());
+    D4<T> l10 = d_log<T>(Re, (T)0.43429448190325176);  // derivative of log10
+    l10.v = Closure<T>::log10_(Re.v);
+    D4<T> tt = dc<T>((T)1.5) - l10;
+    D4<T> chi = dc<T>((T)3.7) - (T)0.65 * d_exp<T>((T)(-0.5) * (tt * tt));
+    D4<T> ln = d_log<T>(ec, (T)1);
+    ln.v = Closure<T>::logn(ec.v);
+    cds = cds * d_exp<T>((dc<T>((T)2) - chi) * ln);
+  }
+  D4<T> coef = ((T)0.5 * rho * (T)kPi * rp * rp) * cds;
+  if (fp.beta_over_eps) coef = coef / ec;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) fd[c] = coef * U[c];
+}
+
+// Lagrange basis, first and second derivatives at t (FP64)
+template <int D>
+__device__ __forceinline__ void lagrange2(const double* zz, const double* lw, double t, double* l,
+                                          double* dl, double* ddl) {
+#pragma unroll
+  for (int a = 0; a <= D; ++a) {
+    double v = 1.0, d1 = 0.0, d2 = 0.0;
+#pragma unroll
+    for (int b = 0; b <= D; ++b) {
+      if (b == a) continue;
+      double db = t - zz[b];
+      d2 = d2 * db + 2.0 * d1;
+      d1 = d1 * db + v;
+      v = v * db;
+    }
+    l[a] = v * lw[a];
+    dl[a] = d1 * lw[a];
+    ddl[a] = d2 * lw[a];
+  }
+}
+
+// ------------------------------------------------------------ kernels
+
+// Per particle: the force part of the adjoint.  Writes dJ/dx (direct part),
+// adds phi_j a_U to dJ/du_j and phi_j a_eps to geps_j.
+template <int K, int KP, typename T>
+__global__ void __launch_bounds__(128)
+k_adj_forces(MeshDev m, Tables tb, ForceParams fp, int64_t n, const double* __restrict__ x,
+             const double* __restrict__ r, const double* __restrict__ u_p,
+             const double* __restrict__ u_nodal, const double* __restrict__ p_nodal,
+             const double* __restrict__ eps_nodal, const double* __restrict__ gf,
+             const double* __restrict__ gfd, double* __restrict__ dJdx, double* __restrict__ dJdu,
+             double* __restrict__ geps, DevStatus* st) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double p[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+  if (!(in_box(p[0], m.x0[0], m.L[0]) && in_box(p[1], m.x0[1], m.L[1]) &&
+        in_box(p[2], m.x0[2], m.L[2]))) {
+    report_bad(st, i);
+    dJdx[3 * i] = dJdx[3 * i + 1] = dJdx[3 * i + 2] = 0.0;
+    return;
+  }
+  int ie[3];
+  double xid[3];
+  for (int a = 0; a < 3; ++a)
+    ie[a] = elem_axis_fast(p[a], m.x0[a], m.h[a], fp.inv_h[a], m.ne[a], &xid[a]);
+  const double ih[3] = {fp.inv_h[0], fp.inv_h[1], fp.inv_h[2]};
+
+  // u_f, eps and their gradients (Q_k, FP64)
+  double lx[K + 1], ly[K + 1], lz[K + 1], dlx[K + 1], dly[K + 1], dlz[K + 1];
+  lagrange<K, double>(tb.z, tb.lw, xid[0], lx, dlx);
+  lagrange<K, double>(tb.z, tb.lw, xid[1], ly, dly);
+  lagrange<K, double>(tb.z, tb.lw, xid[2], lz, dlz);
+  int64_t nx = m.nn[0], nxy = (int64_t)m.nn[0] * m.nn[1];
+  int64_t base = (int64_t)ie[0] * K + nx * ((int64_t)ie[1] * K) + nxy * ((int64_t)ie[2] * K);
+  double uf[3] = {0, 0, 0}, gu[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  double eps = 0, ge[3] = {0, 0, 0};
+#pragma unroll
+  for (int c = 0; c <= K; ++c)
+#pragma unroll
+    for (int b = 0; b <= K; ++b)
+#pragma unroll
+      for (int a = 0; a <= K; ++a) {
+        double phi = lx[a] * ly[b] * lz[c];
+        double dphi[3] = {dlx[a] * ly[b] * lz[c] * ih[0], lx[a] * dly[b] * lz[c] * ih[1],
+                          lx[a] * ly[b] * dlz[c] * ih[2]};
+        int64_t nd = base + a + nx * b + nxy * c;
+        double e = __ldg(eps_nodal + nd);
+        eps += phi * e;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) ge[k] += dphi[k] * e;
+#pragma unroll
+        for (int comp = 0; comp < 3; ++comp) {
+          double u = __ldg(u_nodal + 3 * nd + comp);
+          uf[comp] += phi * u;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) gu[comp][k] += dphi[k] * u;
+        }
+      }
+
+  // Hessian of the interpolated pressure (Q_kp, FP64)
+  double px[KP + 1], py[KP + 1], pz[KP + 1], dpx[KP + 1], dpy[KP + 1], dpz[KP + 1];
+  double ddpx[KP + 1], ddpy[KP + 1], ddpz[KP + 1];
+  lagrange2<KP>(tb.zp, tb.lwp, xid[0], px, dpx, ddpx);
+  lagrange2<KP>(tb.zp, tb.lwp, xid[1], py, dpy, ddpy);
+  lagrange2<KP>(tb.zp, tb.lwp, xid[2], pz, dpz, ddpz);
+  int64_t pnx = m.np[0], pnxy = (int64_t)m.np[0] * m.np[1];
+  int64_t pbase =
+      (int64_t)ie[0] * KP + pnx * ((int64_t)ie[1] * KP) + pnxy * ((int64_t)ie[2] * KP);
+  double H[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+  for (int c = 0; c <= KP; ++c)
+#pragma unroll
+    for (int b = 0; b <= KP; ++b)
+#pragma unroll
+      for (int a = 0; a <= KP; ++a) {
+        double pv = __ldg(p_nodal + pbase + a + pnx * b + pnxy * c);
+        H[0][0] += ddpx[a] * py[b] * pz[c] * pv;
+        H[1][1] += px[a] * ddpy[b] * pz[c] * pv;
+        H[2][2] += px[a] * py[b] * ddpz[c] * pv;
+        H[0][1] += dpx[a] * dpy[b] * pz[c] * pv;
+        H[0][2] += dpx[a] * py[b] * dpz[c] * pv;
+        H[1][2] += px[a] * dpy[b] * dpz[c] * pv;
+      }
+  H[0][0] *= ih[0] * ih[0];
+  H[1][1] *= ih[1] * ih[1];
+  H[2][2] *= ih[2] * ih[2];
+  H[0][1] *= ih[0] * ih[1];
+  H[0][2] *= ih[0] * ih[2];
+  H[1][2] *= ih[1] * ih[2];
+  H[1][0] = H[0][1];
+  H[2][0] = H[0][2];
+  H[2][1] = H[1][2];
+
+  // closure Jacobian
+  T rp = (T)r[i];
+  T U0 = (T)(uf[0] - u_p[3 * i]), U1 = (T)(uf[1] - u_p[3 * i + 1]),
+    U2 = (T)(uf[2] - u_p[3 * i + 2]);
+  T ev = (T)eps;
+  bool clamped = ev < (T)fp.eps_floor || ev > (T)1;
+  T epsc = ev < (T)fp.eps_floor ? (T)fp.eps_floor : (ev > (T)1 ? (T)1 : ev);
+  D4<T> fd[3];
+  drag_dual<T>(fp, rp, U0, U1, U2, epsc, clamped, fd);
+  double g_f[3] = {0, 0, 0}, g_d[3];
+  if (gf)
+    for (int c = 0; c < 3; ++c) g_f[c] = gf[3 * i + c];
+  for (int c = 0; c < 3; ++c) g_d[c] = g_f[c] + (gfd ? gfd[3 * i + c] : 0.0);
+  double aU[3], aE = 0.0;
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+    aU[j] = g_d[0] * (double)fd[0].d[j] + g_d[1] * (double)fd[1].d[j] +
+            g_d[2] * (double)fd[2].d[j];
+  aE = g_d[0] * (double)fd[0].d[3] + g_d[1] * (double)fd[1].d[3] + g_d[2] * (double)fd[2].d[3];
+
+  // direct gradient with respect to x_i
+  const double Vp = 4.0 / 3.0 * kPi * r[i] * r[i] * r[i];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double g = aE * ge[k];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) g += aU[c] * gu[c][k] - Vp * g_f[c] * H[c][k];
+    dJdx[3 * i + k] = g;
+  }
+  // scatter to the nodes
+#pragma unroll
+  for (int c = 0; c <= K; ++c)
+#pragma unroll
+    for (int b = 0; b <= K; ++b)
+#pragma unroll
+      for (int a = 0; a <= K; ++a) {
+        double phi = lx[a] * ly[b] * lz[c];
+        int64_t nd = base + a + nx * b + nxy * c;
+        if (aE != 0.0) atomicAdd(geps + nd, phi * aE);
+        if (dJdu)
+#pragma unroll
+          for (int comp = 0; comp < 3; ++comp) atomicAdd(dJdu + 3 * nd + comp, phi * aU[comp]);
+      }
+}
+
+// g_q = w_q |J_e| lambda_h(x_q) for every Gauss point: the transpose of the
+// right-hand side's quadrature.  One thread per (element, Gauss point).
+template <int K>
+__global__ void __launch_bounds__(256)
+k_adj_interp_q(MeshDev m, Tables tb, const double* __restrict__ lam, double* __restrict__ gq) {
+  constexpr int NQ = K + 1, Q = NQ * NQ * NQ;
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= m.E * Q) return;
+  int64_t e = t / Q;
+  int q = (int)(t - e * Q);
+  int qx = q % NQ, qy = (q / NQ) % NQ, qz = q / (NQ * NQ);
+  int ex = (int)(e % m.ne[0]), ey = (int)((e / m.ne[0]) % m.ne[1]),
+      ez = (int)(e / ((int64_t)m.ne[0] * m.ne[1]));
+  int64_t nx = m.nn[0], nxy = (int64_t)m.nn[0] * m.nn[1];
+  int64_t base = (int64_t)ex * K + nx * ((int64_t)ey * K) + nxy * ((int64_t)ez * K);
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c <= K; ++c)
+#pragma unroll
+    for (int b = 0; b <= K; ++b) {
+      double wyz = tb.Bw[b][qy] * tb.Bw[c][qz];
+#pragma unroll
+      for (int a = 0; a <= K; ++a)
+        s += tb.Bw[a][qx] * wyz * __ldg(lam + base + a + nx * b + nxy * c);
+    }
+  gq[t] = s * m.Ve;
+}
+
+// Per particle: sum over the Gauss points q within R + r_i of
+// g_q (pi a^2 / V_R) (x_i - x_q) / d, added to dJ/dx_i.
+template <int K>
+__global__ void __launch_bounds__(128)
+k_adj_qcm(MeshDev m, Tables tb, double R, int64_t n, const double* __restrict__ x,
+          const double* __restrict__ r, const double* __restrict__ gq, double* __restrict__ dJdx) {
+  constexpr int NQ = K + 1, Q = NQ * NQ * NQ;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double p[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+  if (!(in_box(p[0], m.x0[0], m.L[0]) && in_box(p[1], m.x0[1], m.L[1]) &&
+        in_box(p[2], m.x0[2], m.L[2])))
+    return;
+  const double ri = r[i];
+  const double cut = R + ri, cut2 = cut * cut;
+  const double dm = R - ri, dm2 = dm * dm;
+  const double coef = kPi / (4.0 / 3.0 * kPi * R * R * R);
+  const double R2r2 = R * R - ri * ri;
+  int lo[3], hi[3];
+  for (int a = 0; a < 3; ++a) {
+    double tl = (p[a] - cut - m.x0[a]) / m.h[a], th = (p[a] + cut - m.x0[a]) / m.h[a];
+    lo[a] = (int)floor(tl);
+    hi[a] = (int)floor(th);
+    lo[a] = lo[a] < 0 ? 0 : (lo[a] > m.ne[a] - 1 ? m.ne[a] - 1 : lo[a]);
+    hi[a] = hi[a] < 0 ? 0 : (hi[a] > m.ne[a] - 1 ? m.ne[a] - 1 : hi[a]);
+  }
+  double g0 = 0, g1 = 0, g2 = 0;
+  for (int ez = lo[2]; ez <= hi[2]; ++ez)
+    for (int ey = lo[1]; ey <= hi[1]; ++ey)
+      for (int ex = lo[0]; ex <= hi[0]; ++ex) {
+        int64_t e = ex + (int64_t)m.ne[0] * (ey + (int64_t)m.ne[1] * ez);
+        const double* g = gq + e * Q;
+#pragma unroll
+        for (int qz = 0; qz < NQ; ++qz) {
+          double dz = p[2] - (m.x0[2] + m.h[2] * ((double)ez + tb.g[qz]));
+#pragma unroll
+          for (int qy = 0; qy < NQ; ++qy) {
+            double dy = p[1] - (m.x0[1] + m.h[1] * ((double)ey + tb.g[qy]));
+#pragma unroll
+            for (int qx = 0; qx < NQ; ++qx) {
+              double dx = p[0] - (m.x0[0] + m.h[0] * ((double)ex + tb.g[qx]));
+              double d2 = dx * dx + dy * dy + dz * dz;
+              if (d2 >= cut2 || d2 <= dm2) continue;  // no contact, or full containment
+              double w = d2 + R2r2;
+              double a2 = (4.0 * d2 * R * R - w * w) / (4.0 * d2);
+              double s = __ldg(g + qx + NQ * (qy + NQ * qz)) * coef * a2 * rsqrt(d2);
+              g0 += s * dx;
+              g1 += s * dy;
+              g2 += s * dz;
+            }
+          }
+        }
+      }
+  dJdx[3 * i] += g0;
+  dJdx[3 * i + 1] += g1;
+  dJdx[3 * i + 2] += g2;
+}
+
+}  // namespace
+
+cudaError_t launch_adj_forces(const MeshDev& m, const Tables& t, int precision, double rho,
+                              double mu, int drag_model, int beta_over_eps, double eps_floor,
+                              int64_t n, const double* x, const double* r, const double* u_p,
+                              const double* u_nodal, const double* p_nodal,
+                              const double* eps_nodal, const double* gf, const double* gfd,
+                              double* dJdx, double* dJdu, double* geps, DevStatus* st,
+                              cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  ForceParams fp{};
+  fp.rho = rho;
+  fp.mu = mu;
+  fp.eps_floor = eps_floor;
+  fp.drag_model = drag_model;
+  fp.beta_over_eps = beta_over_eps;
+  for (int a = 0; a < 3; ++a) fp.inv_h[a] = 1.0 / m.h[a];
+  const int bs = 128;
+  const unsigned nb = (unsigned)((n + bs - 1) / bs);
+#define CFDEM_ADJ(K, KP)                                                                    \
+  if (m.k == K && m.kp == KP) {                                                             \
+    if (precision == 0)                                                                     \
+      k_adj_forces<K, KP, double><<<nb, bs, 0, s>>>(m, t, fp, n, x, r, u_p, u_nodal,        \
+                                                    p_nodal, eps_nodal, gf, gfd, dJdx, dJdu, \
+                                                    geps, st);                              \
+    else                                                                                    \
+      k_adj_forces<K, KP, float><<<nb, bs, 0, s>>>(m, t, fp, n, x, r, u_p, u_nodal,         \
+                                                   p_nodal, eps_nodal, gf, gfd, dJdx, dJdu,  \
+                                                   geps, st);                               \
+    count_launches(1);                                                                      \
+    return cudaGetLastError();                                                              \
+  }
+  CFDEM_ADJ(1, 1)
+  CFDEM_ADJ(2, 1)
+  CFDEM_ADJ(2, 2)
+  CFDEM_ADJ(3, 1)
+  CFDEM_ADJ(3, 2)
+  CFDEM_ADJ(3, 3)
+  CFDEM_ADJ(1, 2)
+  CFDEM_ADJ(1, 3)
+  CFDEM_ADJ(2, 3)
+#undef CFDEM_ADJ
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_adj_qcm(const MeshDev& m, const Tables& t, double R, const double* lam,
+                           double* gq, int64_t n, const double* x, const double* r,
+                           double* dJdx, cudaStream_t s) {
+  const int64_t nq = m.E * m.Q;
+  const unsigned gb = (unsigned)((nq + 255) / 256);
+  const unsigned pb = (unsigned)((n + 127) / 128);
+  if (m.k == 1) {
+    k_adj_interp_q<1><<<gb, 256, 0, s>>>(m, t, lam, gq);
+    if (n > 0) k_adj_qcm<1><<<pb, 128, 0, s>>>(m, t, R, n, x, r, gq, dJdx);
+  } else if (m.k == 2) {
+    k_adj_interp_q<2><<<gb, 256, 0, s>>>(m, t, lam, gq);
+    if (n > 0) k_adj_qcm<2><<<pb, 128, 0, s>>>(m, t, R, n, x, r, gq, dJdx);
+  } else {
+    k_adj_interp_q<3><<<gb, 256, 0, s>>>(m, t, lam, gq);
+    if (n > 0) k_adj_qcm<3><<<pb, 128, 0, s>>>(m, t, R, n, x, r, gq, dJdx);
+  }
+  count_launches(n > 0 ? 2 : 1);
+  return cudaGetLastError();
+}
+
+}  // namespace cfdem

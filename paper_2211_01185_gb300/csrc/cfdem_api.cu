@@ -13,6 +13,7 @@
 
 #include "../../include/cfdem.h"
 #include "internal.h"
+#include "context.h"
 
 using namespace cfdem;
 
@@ -67,47 +68,6 @@ void Timer::release() {
 }
 
 }  // namespace cfdem
-
-struct cfdem_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  bool have_mesh = false;
-  MeshDev mesh{};
-  Tables tab{};
-  BinDev bins{};
-  cfdem_params prm{};
-  double R = 0.0;  // resolved averaging radius
-  double coef[4] = {0, 0, 0, 0};
-  // device memory
-  DevStatus* st = nullptr;
-  double* bands64 = nullptr;
-  float* bands32 = nullptr;
-  float* bandsdf = nullptr;
-  // particle arena
-  int64_t cap_n = 0;
-  int32_t *bin_of = nullptr, *slot = nullptr, *perm = nullptr;
-  double* xs64 = nullptr;
-  float* xs32 = nullptr;
-  int64_t cap_bins = 0;
-  int32_t *bin_count = nullptr, *bin_start = nullptr, *scan_tmp = nullptr;
-  // mesh arena
-  double* eps64 = nullptr;     // internal eps_q (FP64 path)
-  float* eps32 = nullptr;      // internal eps_q (mixed path)
-  double* b = nullptr;
-  double* S = nullptr;         // per-element source accumulator [E][3]
-  double* vol = nullptr;       // per-element particle volume (PCM)
-  CgWork cg{};
-  FdmPlan* fdm = nullptr;
-  const char* fdm_note = "";
-  int eps_state = 0;           // 0 none, 1 eps64 valid, 2 eps32 valid
-  // host-side record
-  int last_iters = 0, last_outer = 0, last_converged = 1;
-  double last_relres = 0.0;
-  int pending_not_converged = 0;
-  Timer timer;
-  long long launches_at_reset = 0;
-  std::string err;
-};
 
 namespace {
 
@@ -334,7 +294,8 @@ void free_mesh_arena(cfdem_t c) {
                 c->cg.p1, c->cg.Ap, c->cg.dinv, c->cg.xcor, c->cg.r32, c->cg.z32,
                 c->cg.q0, c->cg.q1, c->cg.Aq, c->cg.dinv32, c->cg.d32, c->cg.partials,
                 c->cg.sc, c->cg.zn, c->cg.zn32, c->cg.rin32, c->cg.x_df, c->cg.r_df,
-                c->cg.b_df, c->cg.Ap_df, c->cg.p0_df, c->cg.p1_df};
+                c->cg.b_df, c->cg.Ap_df, c->cg.p0_df, c->cg.p1_df, c->adj_geps,
+                c->adj_lam, c->adj_gq};
   for (void* p : ps)
     if (p) cudaFree(p);
   c->eps64 = nullptr;
@@ -342,6 +303,7 @@ void free_mesh_arena(cfdem_t c) {
   c->b = nullptr;
   c->S = nullptr;
   c->vol = nullptr;
+  c->adj_geps = c->adj_lam = c->adj_gq = nullptr;
   FdmPlan* keep = c->cg.fdm;
   const df64* kb = c->cg.bands_df;
   c->cg = CgWork{};
@@ -400,6 +362,23 @@ cfdem_status alloc_mesh_arena(cfdem_t c) {
   return CFDEM_OK;
 }
 
+// statistics of a solve that ran inside a graph, from the device scalars
+// (the stream has been synchronised)
+cudaError_t read_pending_stats(cfdem_t c) {
+  if (!c->stats_pending || !c->cg.sc) return cudaSuccess;
+  CgScalars hs;
+  cudaError_t e = cudaMemcpy(&hs, c->cg.sc, sizeof hs, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return e;
+  double bb = hs.bb > 0 ? hs.bb : 1.0;
+  c->last_iters = hs.it;
+  c->last_outer = c->prm.precision == 1 ? hs.it : 0;
+  c->last_relres = std::sqrt(hs.rr / bb);
+  c->last_converged = c->last_relres <= c->prm.cg_rtol;
+  if (!c->last_converged) c->pending_not_converged = 1;
+  c->stats_pending = false;
+  return cudaSuccess;
+}
+
 cfdem_status need_mesh(cfdem_t c) {
   if (!c) return CFDEM_EINVAL;
   if (!c->have_mesh) return fail(c, CFDEM_ESTATE, "cfdem_set_mesh has not been called");
@@ -416,6 +395,44 @@ cfdem_status do_bin(cfdem_t c, int64_t n, const double* x, const double* r) {
                 c->perm, c->scan_tmp, c->xs64, c->xs32, c->st, c->stream),
      "bin");
   c->timer.end(kStageBin, c->stream);
+  return CFDEM_OK;
+}
+
+// (M + L^2 K) x = b by the context's CG (x: start vector in, solution out).
+// Inside a stream capture the CG iterates on the device (a conditional node
+// of the graph) and its statistics are read at the next synchronise.
+cfdem_status solve(cfdem_t c, const double* b, double* x, const char* what) {
+  int it = 0, outer = 0, conv = 0;
+  double rel = 0.0;
+  cudaError_t e;
+  const bool captured = stream_capturing(c->stream);
+  if (captured && c->timer.on)
+    return fail(c, CFDEM_ESTATE, "stage timers must be off while the stream is captured");
+  c->cg.loop = captured ? c->loop_stream : nullptr;
+  c->cg.timer = c->timer.on ? &c->timer : nullptr;
+  c->timer.begin(kStageSolve, c->stream);
+  if (c->prm.precision == 1)
+    e = run_cg_mixed(c->mesh, c->bands64, c->bands32, c->coef, b, x, c->prm.cg_rtol,
+                     c->prm.cg_maxit, c->cg, c->stream, &it, &outer, &rel, &conv);
+  else
+    e = run_cg64(c->mesh, c->bands64, c->coef, b, x, c->prm.cg_rtol, c->prm.cg_maxit, c->cg,
+                 c->stream, &it, &rel, &conv);
+  c->cg.loop = nullptr;
+  if (e == cudaErrorNotSupported && captured)
+    return fail(c, CFDEM_ESTATE,
+                "a captured mixed-precision solve needs the fast-diagonalisation preconditioner");
+  if (e != cudaSuccess) return cuda_fail(c, e, what);
+  c->timer.end(kStageSolve, c->stream);
+  if (captured) {
+    c->stats_pending = true;
+    return CFDEM_OK;
+  }
+  c->stats_pending = false;
+  c->last_iters = it;
+  c->last_outer = outer;
+  c->last_relres = rel;
+  c->last_converged = conv;
+  if (!conv) c->pending_not_converged = 1;
   return CFDEM_OK;
 }
 
@@ -462,7 +479,8 @@ cfdem_status cfdem_create(cfdem_t* out, int device, void* stream) {
   }
   DevStatus init{};
   init.first_bad = ~0ull;
-  if (cudaMemcpy(c->st, &init, sizeof init, cudaMemcpyHostToDevice) != cudaSuccess) {
+  if (cudaMemcpy(c->st, &init, sizeof init, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->loop_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaFree(c->st);
     delete c;
     return CFDEM_ECUDA;
@@ -484,6 +502,7 @@ cfdem_status cfdem_destroy(cfdem_t c) {
                 c->xs32, c->bin_count, c->bin_start, c->scan_tmp};
   for (void* p : ps)
     if (p) cudaFree(p);
+  if (c->loop_stream) cudaStreamDestroy(c->loop_stream);
   delete c;
   return CFDEM_OK;
 }
@@ -512,6 +531,7 @@ cfdem_status cfdem_set_mesh(cfdem_t c, const double origin[3], const double exte
   if (m.E * m.Q > ((int64_t)1 << 31) || m.n_nodes > ((int64_t)1 << 31))
     return fail(c, CFDEM_EINVAL, "mesh too large");
   m.shape = pick_shape(m);
+  ++c->gen;
   DeviceGuard g(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   free_mesh_arena(c);
@@ -544,6 +564,7 @@ cfdem_status cfdem_set_params(cfdem_t c, const cfdem_params* p) {
   if (p->cg_precond < 0 || p->cg_precond > 1)
     return fail(c, CFDEM_EINVAL, "cg_precond must be 0 (Jacobi) or 1 (FDM)");
   c->prm = *p;
+  ++c->gen;
   return resolve(c);
 }
 
@@ -658,25 +679,7 @@ cfdem_status cfdem_project(cfdem_t c, const double* eps_q, double* eps_nodal) {
   s = cfdem_project_rhs(c, eps_q, c->b);
   if (s != CFDEM_OK) return s;
   DeviceGuard g(c->device);
-  int it = 0, outer = 0, conv = 0;
-  double rel = 0.0;
-  cudaError_t e;
-  c->cg.timer = c->timer.on ? &c->timer : nullptr;
-  c->timer.begin(kStageSolve, c->stream);
-  if (c->prm.precision == 1)
-    e = run_cg_mixed(c->mesh, c->bands64, c->bands32, c->coef, c->b, eps_nodal,
-                     c->prm.cg_rtol, c->prm.cg_maxit, c->cg, c->stream, &it, &outer, &rel, &conv);
-  else
-    e = run_cg64(c->mesh, c->bands64, c->coef, c->b, eps_nodal, c->prm.cg_rtol,
-                 c->prm.cg_maxit, c->cg, c->stream, &it, &rel, &conv);
-  if (e != cudaSuccess) return cuda_fail(c, e, "project");
-  c->timer.end(kStageSolve, c->stream);
-  c->last_iters = it;
-  c->last_outer = outer;
-  c->last_relres = rel;
-  c->last_converged = conv;
-  if (!conv) c->pending_not_converged = 1;
-  return CFDEM_OK;
+  return solve(c, c->b, eps_nodal, "project");
 }
 
 cfdem_status cfdem_forces(cfdem_t c, int64_t n, const double* x, const double* r,
@@ -717,11 +720,61 @@ cfdem_status cfdem_coupling_step(cfdem_t c, int64_t n, const double* x, const do
   return cfdem_forces(c, n, x, r, u_p, u_nodal, p_nodal, eps_nodal, f, f_drag, F_elem, F_q);
 }
 
+cfdem_status cfdem_mass_apply(cfdem_t c, const double* x, double* y) {
+  cfdem_status s = need_mesh(c);
+  if (s != CFDEM_OK) return s;
+  if (!x || !y) return fail(c, CFDEM_EINVAL, "null vector");
+  DeviceGuard g(c->device);
+  const double mass_only[4] = {c->coef[0], 0.0, 0.0, 0.0};
+  CK(launch_apply64(c->mesh, c->bands64, mass_only, x, y, c->stream), "mass apply");
+  return CFDEM_OK;
+}
+
+cfdem_status cfdem_adjoint(cfdem_t c, int64_t n, const double* x, const double* r,
+                           const double* u_p, const double* u_nodal, const double* p_nodal,
+                           const double* eps_nodal, const double* g_f, const double* g_fdrag,
+                           const double* g_eps, double* dJ_dx, double* dJ_du) {
+  cfdem_status s = need_mesh(c);
+  if (s != CFDEM_OK) return s;
+  if (n < 0 || n >= ((int64_t)1 << 31) || (n > 0 && (!x || !r || !u_p || !dJ_dx)) ||
+      !u_nodal || !p_nodal || !eps_nodal)
+    return fail(c, CFDEM_EINVAL, "null input");
+  DeviceGuard g(c->device);
+  const MeshDev& m = c->mesh;
+  if (!c->adj_geps) {  // the mesh arena is released (and these reset) by every set_mesh
+    CK(grow(&c->adj_geps, m.n_nodes), "adjoint arena");
+    CK(grow(&c->adj_lam, m.n_nodes), "adjoint arena");
+    CK(grow(&c->adj_gq, m.E * m.Q), "adjoint arena");
+  }
+  if (g_eps)
+    CK(cudaMemcpyAsync(c->adj_geps, g_eps, sizeof(double) * m.n_nodes, cudaMemcpyDeviceToDevice,
+                       c->stream),
+       "adjoint");
+  else
+    CK(cudaMemsetAsync(c->adj_geps, 0, sizeof(double) * m.n_nodes, c->stream), "adjoint");
+  if (dJ_du) CK(cudaMemsetAsync(dJ_du, 0, sizeof(double) * 3 * m.n_nodes, c->stream), "adjoint");
+  CK(launch_adj_forces(m, c->tab, c->prm.precision, c->prm.rho_f, c->prm.mu_f,
+                       c->prm.drag_model, c->prm.beta_over_eps, c->prm.eps_floor, n, x, r, u_p,
+                       u_nodal, p_nodal, eps_nodal, g_f, g_fdrag, dJ_dx, dJ_du, c->adj_geps,
+                       c->st, c->stream),
+     "adjoint forces");
+  if (c->prm.scheme == 0) {
+    // lambda = A^-1 dJ/deps_h (A symmetric), then through the QCM
+    CK(cudaMemsetAsync(c->adj_lam, 0, sizeof(double) * m.n_nodes, c->stream), "adjoint");
+    s = solve(c, c->adj_geps, c->adj_lam, "adjoint solve");
+    if (s != CFDEM_OK) return s;
+    CK(launch_adj_qcm(m, c->tab, c->R, c->adj_lam, c->adj_gq, n, x, r, dJ_dx, c->stream),
+       "adjoint void fraction");
+  }
+  return CFDEM_OK;
+}
+
 cfdem_status cfdem_synchronize(cfdem_t c) {
   if (!c) return CFDEM_EINVAL;
   DeviceGuard g(c->device);
   cudaError_t e = c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(c, e, "synchronize");
+  CK(read_pending_stats(c), "status");
   DevStatus h;
   CK(cudaMemcpy(&h, c->st, sizeof h, cudaMemcpyDeviceToHost), "status");
   cfdem_status s = CFDEM_OK;
@@ -743,6 +796,7 @@ cfdem_status cfdem_get_stats(cfdem_t c, cfdem_stats* out) {
   DeviceGuard g(c->device);
   cudaError_t e = c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(c, e, "get_stats");
+  CK(read_pending_stats(c), "status");
   DevStatus h;
   CK(cudaMemcpy(&h, c->st, sizeof h, cudaMemcpyDeviceToHost), "status");
   out->first_bad_particle = h.first_bad == ~0ull ? -1 : (int64_t)h.first_bad;
@@ -783,6 +837,7 @@ cfdem_status cfdem_set_timing(cfdem_t c, int enable) {
   c->timer.overflow = false;
   if (enable) c->timer.create();
   c->timer.on = enable != 0;
+  ++c->gen;
   c->launches_at_reset = launches_total();
   return CFDEM_OK;
 }

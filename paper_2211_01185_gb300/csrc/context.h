@@ -1,0 +1,66 @@
+// context.h -- the library context behind the opaque cfdem_t handle (shared
+// by the single-bed entry points and the batched ensemble).
+#pragma once
+#include <string>
+
+#include "../../include/cfdem.h"
+#include "internal.h"
+
+using cfdem::BinDev;
+using cfdem::CgWork;
+using cfdem::DevStatus;
+using cfdem::FdmPlan;
+using cfdem::MeshDev;
+using cfdem::Tables;
+using cfdem::Timer;
+
+struct cfdem_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool have_mesh = false;
+  MeshDev mesh{};
+  Tables tab{};
+  BinDev bins{};
+  cfdem_params prm{};
+  double R = 0.0;  // resolved averaging radius
+  double coef[4] = {0, 0, 0, 0};
+  // device memory
+  DevStatus* st = nullptr;
+  double* bands64 = nullptr;
+  float* bands32 = nullptr;
+  float* bandsdf = nullptr;
+  // particle arena
+  int64_t cap_n = 0;
+  int32_t *bin_of = nullptr, *slot = nullptr, *perm = nullptr;
+  double* xs64 = nullptr;
+  float* xs32 = nullptr;
+  int64_t cap_bins = 0;
+  int32_t *bin_count = nullptr, *bin_start = nullptr, *scan_tmp = nullptr;
+  // mesh arena
+  double* eps64 = nullptr;     // internal eps_q (FP64 path)
+  float* eps32 = nullptr;      // internal eps_q (mixed path)
+  double* b = nullptr;
+  double* S = nullptr;         // per-element source accumulator [E][3]
+  double* vol = nullptr;       // per-element particle volume (PCM)
+  // adjoint arena (grown by the first cfdem_adjoint)
+  double* adj_geps = nullptr;  // dJ/deps_h [n_nodes]
+  double* adj_lam = nullptr;   // lambda = A^-1 dJ/deps_h [n_nodes]
+  double* adj_gq = nullptr;    // dJ/deps_q [E][Q]
+  CgWork cg{};
+  FdmPlan* fdm = nullptr;
+  const char* fdm_note = "";
+  int eps_state = 0;           // 0 none, 1 eps64 valid, 2 eps32 valid
+  // host-side record
+  int last_iters = 0, last_outer = 0, last_converged = 1;
+  double last_relres = 0.0;
+  int pending_not_converged = 0;
+  // set when the last solve ran inside a captured graph: its iteration count
+  // and residual are read from the device scalars at the next synchronising
+  // call
+  bool stats_pending = false;
+  cudaStream_t loop_stream = nullptr;  // capture stream of device-driven CG loops
+  unsigned gen = 0;                    // bumped by every change of mesh, parameters or timing
+  Timer timer;
+  long long launches_at_reset = 0;
+  std::string err;
+};

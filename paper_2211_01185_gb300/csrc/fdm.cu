@@ -624,20 +624,27 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4], 
     band_ldlt_factors(nz, m.k, Mz, Kz, coef[3], smodes, p->ms, fac);
     if ((e = cudaMalloc(&p->fac, fac.size() * 4)) == cudaSuccess)
       e = cudaMemcpy(p->fac, fac.data(), fac.size() * 4, cudaMemcpyHostToDevice);
+    // the dynamic shared-memory limit is a property of the kernel, shared by
+    // every plan (context) of the process: raise it to the device's opt-in
+    // maximum rather than to this plan's size, which a later plan with
+    // smaller slabs would otherwise lower below what this one launches with
+    int dev = 0, optin = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_fdm_slab, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)p->slab_smem);
-    if (e == cudaSuccess) {
-      if (m.k == 1)
-        e = cudaFuncSetAttribute(k_fdm_zsolve<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)p->z_smem);
-      else if (m.k == 2)
-        e = cudaFuncSetAttribute(k_fdm_zsolve<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)p->z_smem);
-      else
-        e = cudaFuncSetAttribute(k_fdm_zsolve<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)p->z_smem);
-    }
+      e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess && ((size_t)optin < p->slab_smem || (size_t)optin < p->z_smem))
+      e = cudaErrorInvalidValue;
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_fdm_slab, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_fdm_zsolve<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               optin);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_fdm_zsolve<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               optin);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_fdm_zsolve<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               optin);
   } else if (e == cudaSuccess) {
     double* dl[3] = {nullptr, nullptr, nullptr};
     for (int a = 0; a < 3 && e == cudaSuccess; ++a) {

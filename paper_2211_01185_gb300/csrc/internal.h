@@ -71,7 +71,7 @@ struct CgScalars {
   int it;           // iterations done
   int done;         // 1 once converged (kernels then return at once)
   unsigned int ticket;  // last-block counter
-  int pad;
+  int loops;       // bodies of a device-driven CG loop run so far
   float alpha_hi, alpha_lo;  // double-float split of alpha (mixed solve)
 };
 
@@ -143,6 +143,16 @@ cudaError_t upload_bands(const MeshDev& m, const Tables& t, double L2, double** 
                          float** bands32, float** bands_df);
 cudaError_t launch_apply64(const MeshDev& m, const double* bands, const double* coef,
                            const double* x, double* y, cudaStream_t s);
+cudaError_t launch_adj_forces(const MeshDev& m, const Tables& t, int precision, double rho,
+                              double mu, int drag_model, int beta_over_eps, double eps_floor,
+                              int64_t n, const double* x, const double* r, const double* u_p,
+                              const double* u_nodal, const double* p_nodal,
+                              const double* eps_nodal, const double* gf, const double* gfd,
+                              double* dJdx, double* dJdu, double* geps, DevStatus* st,
+                              cudaStream_t s);
+cudaError_t launch_adj_qcm(const MeshDev& m, const Tables& t, double R, const double* lam,
+                           double* gq, int64_t n, const double* x, const double* r,
+                           double* dJdx, cudaStream_t s);
 struct FdmPlan;
 cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4], FdmPlan** out,
                        const char** why);
@@ -167,7 +177,12 @@ struct CgWork {
   CgScalars* sc;      // device scalars
   int nblocks;
   Timer* timer;       // may be null
+  // non-null while the solve is being captured into a CUDA graph: the stream
+  // on which the body of the device-driven CG loop is captured
+  cudaStream_t loop;
 };
+// true when s is a stream under active capture
+bool stream_capturing(cudaStream_t s);
 int cg_blocks(const MeshDev& m);
 int pick_shape(const MeshDev& m);
 cudaError_t run_cg64(const MeshDev& m, const double* bands, const double* coef,

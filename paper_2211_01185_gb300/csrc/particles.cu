@@ -6,61 +6,9 @@
 #include <cstdint>
 
 #include "internal.h"
+#include "device_common.cuh"
 
 namespace cfdem {
-
-// ----------------------------------------------------------------------------
-// exact location arithmetic (no contraction into FMA: same rounding as the
-// plain IEEE definition)
-
-__device__ __forceinline__ bool in_box(double x, double x0, double L) {
-  double slack = __dmul_rn(1e-12, L);
-  double lo = __dsub_rn(x0, slack);
-  double hi = __dadd_rn(__dadd_rn(x0, L), slack);
-  return x >= lo && x <= hi;  // false for NaN
-}
-
-// element index along one axis and the reference coordinate; caller checked
-// in_box so t is finite
-__device__ __forceinline__ int elem_axis(double x, double x0, double h, int N, double* xi) {
-  double t = __ddiv_rn(__dsub_rn(x, x0), h);
-  double f = floor(t);
-  int i = (int)f;
-  i = i < 0 ? 0 : (i > N - 1 ? N - 1 : i);
-  *xi = __dsub_rn(t, (double)i);
-  return i;
-}
-
-// element index and reference coordinate from a multiplication by 1/h; the
-// IEEE division of the definition is redone only when the product lies
-// within 1e-9 of an element face, where the two could round to different
-// sides.  xi is then within a few ulps of the divided value.
-__device__ __forceinline__ int elem_axis_fast(double x, double x0, double h, double inv_h, int N,
-                                              double* xi) {
-  double t = (x - x0) * inv_h;
-  double f = floor(t);
-  double fr = t - f;
-  if (fr < 1e-9 || fr > 1.0 - 1e-9) {
-    t = __ddiv_rn(__dsub_rn(x, x0), h);
-    f = floor(t);
-  }
-  int i = (int)f;
-  i = i < 0 ? 0 : (i > N - 1 ? N - 1 : i);
-  *xi = t - (double)i;
-  return i;
-}
-
-__device__ __forceinline__ int bin_axis(double x, double x0, double be, int nb) {
-  double t = __ddiv_rn(__dsub_rn(x, x0), be);
-  double f = floor(t);
-  if (!(f >= 0.0)) return 0;
-  if (f > (double)(nb - 1)) return nb - 1;
-  return (int)f;
-}
-
-__device__ __forceinline__ void report_bad(DevStatus* st, int64_t i) {
-  atomicMin(&st->first_bad, (unsigned long long)i);
-}
 
 // ----------------------------------------------------------------------------
 // a1: locate
@@ -309,63 +257,6 @@ cudaError_t launch_bin(const MeshDev& m, const BinDev& b, int64_t n, const doubl
 
 // ----------------------------------------------------------------------------
 // a6: forces
-
-template <typename T>
-__device__ __forceinline__ T t_sqrt(T v);
-template <>
-__device__ __forceinline__ double t_sqrt<double>(double v) { return sqrt(v); }
-template <>
-__device__ __forceinline__ float t_sqrt<float>(float v) { return sqrtf(v); }
-
-// Lagrange basis of degree D on nodes z and its derivative at t; lw[a] =
-// 1 / prod_{b != a} (z_a - z_b) comes from the host so that no division is
-// done here
-template <int D, typename T>
-__device__ __forceinline__ void lagrange(const double* zz, const double* lw, T t, T* l, T* dl) {
-  T d[D + 1];
-#pragma unroll
-  for (int a = 0; a <= D; ++a) d[a] = t - (T)zz[a];
-#pragma unroll
-  for (int a = 0; a <= D; ++a) {
-    T v = (T)1, dv = (T)0;
-#pragma unroll
-    for (int b = 0; b <= D; ++b) {
-      if (b == a) continue;
-      dv = dv * d[b] + v;
-      v = v * d[b];
-    }
-    l[a] = v * (T)lw[a];
-    if (dl) dl[a] = dv * (T)lw[a];
-  }
-}
-
-template <typename T>
-struct Closure {
-  static __device__ __forceinline__ T log10_(T v);
-  static __device__ __forceinline__ T exp_(T v);
-  static __device__ __forceinline__ T logn(T v);
-  static __device__ __forceinline__ T tiny();
-};
-template <>
-struct Closure<double> {
-  static __device__ __forceinline__ double log10_(double v) { return log10(v); }
-  static __device__ __forceinline__ double exp_(double v) { return exp(v); }
-  static __device__ __forceinline__ double logn(double v) { return log(v); }
-  static __device__ __forceinline__ double tiny() { return 1e-300; }
-};
-template <>
-struct Closure<float> {
-  static __device__ __forceinline__ float log10_(float v) { return log10f(v); }
-  static __device__ __forceinline__ float exp_(float v) { return expf(v); }
-  static __device__ __forceinline__ float logn(float v) { return logf(v); }
-  static __device__ __forceinline__ float tiny() { return 1e-37f; }
-};
-
-struct ForceParams {
-  double rho, mu, g[3], eps_floor;
-  double inv_h[3];
-  int drag_model, beta_over_eps, vans_model;
-};
 
 template <int K, int KP, typename T>
 __global__ void __launch_bounds__(128)

@@ -1011,6 +1011,70 @@ static int vec_blocks(int64_t n) {
   return (int)(b < 1216 ? (b < 1 ? 1 : b) : 1216);
 }
 
+// ---------------------------------------------------------------------------
+// Device-driven iteration inside a stream capture.  When the stream is being
+// captured into a CUDA graph, the CG loops below do not read the device flag
+// `done` on the host between chunks; instead they add a conditional WHILE
+// node to the graph under construction.  Its body -- captured on a second
+// stream `ls` -- holds two CG iterations and ends with k_loop_cond, which sets
+// the node's condition from `done`, so the graph iterates on the device until
+// the CG has converged or reached its iteration cap.  (Two iterations, so that
+// the ping-pong buffers are back in their roles at the end of the body; the
+// first iteration, with beta = 0, is queued before the node.)
+
+// one thread: continue while the CG is not done, and never beyond
+// max_bodies bodies whatever the kernels of the body did (sc->loops is
+// cleared with the other scalars at the start of every solve)
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, CgScalars* sc, int max_bodies) {
+  volatile CgScalars* v = sc;
+  int n = v->loops + 1;
+  v->loops = n;
+  cudaGraphSetConditional(h, (!v->done && n < max_bodies) ? 1u : 0u);
+}
+
+static cudaError_t loop_open(cudaStream_t s, cudaStream_t ls, cudaGraphConditionalHandle* h) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureUnmatched;
+  if ((e = cudaGraphConditionalHandleCreate(h, g, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
+    return e;
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = *h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  if ((e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &np)) != cudaSuccess) return e;
+  if ((e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1,
+                                               cudaStreamSetCaptureDependencies)) != cudaSuccess)
+    return e;
+  return cudaStreamBeginCaptureToGraph(ls, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                       cudaStreamCaptureModeRelaxed);
+}
+
+static cudaError_t loop_close(cudaStream_t ls, cudaGraphConditionalHandle h, CgScalars* sc,
+                              int maxit, cudaError_t body_status) {
+  if (body_status == cudaSuccess) {
+    // maxit iterations = the peeled one + (maxit - 1) / 2 bodies of two
+    k_loop_cond<<<1, 1, 0, ls>>>(h, sc, maxit / 2 + 2);
+    count_launches(1);
+    body_status = cudaGetLastError();
+  }
+  cudaGraph_t body = nullptr;
+  cudaError_t e = cudaStreamEndCapture(ls, &body);
+  return body_status != cudaSuccess ? body_status : e;
+}
+
+bool stream_capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (!s || cudaStreamIsCapturing(s, &cs) != cudaSuccess) return false;
+  return cs == cudaStreamCaptureStatusActive;
+}
+
 // one CG solve of A x = b in precision T from the start vector x (in T, or
 // FP64 for the outer vector when TX_ = double); iterations run in chunks
 // between host checks of the device flag
@@ -1019,7 +1083,7 @@ static cudaError_t cg_solve(const MeshDev& m, const T* bands, const double* coef
                             TX_* x, const T* x_as_T, double rtol, int maxit, T* r, T* z,
                             T* p0, T* p1, T* Ap, const T* dinv, double* partials,
                             CgScalars* sc, cudaStream_t s, int* iters, double* relres,
-                            Timer* tm) {
+                            Timer* tm, cudaStream_t ls) {
   cudaError_t e;
   int64_t n = m.n_nodes;
   int vb = vec_blocks(n);
@@ -1033,25 +1097,39 @@ static cudaError_t cg_solve(const MeshDev& m, const T* bands, const double* coef
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   T* pc = p0;
   T* pn = p1;
+  auto iter = [&](int first, cudaStream_t st) -> cudaError_t {
+    cudaError_t ee;
+    if (tm) tm->begin(op_stage, st);
+    if ((ee = cg_apply_t<T>(m, bands, coef, z, pc, pn, Ap, partials, sc, first, st)) !=
+        cudaSuccess)
+      return ee;
+    if (tm) tm->end(op_stage, st);
+    k_cg_update<T, TX_><<<vb, 256, 0, st>>>(n, x, r, z, pn, Ap, dinv, partials, sc, maxit);
+    count_launches(1);
+    if ((ee = cudaGetLastError()) != cudaSuccess) return ee;
+    T* t = pc;
+    pc = pn;
+    pn = t;
+    return cudaSuccess;
+  };
+  if (ls) {  // device-driven loop inside a stream capture
+    if ((e = iter(1, s)) != cudaSuccess) return e;
+    cudaGraphConditionalHandle h;
+    if ((e = loop_open(s, ls, &h)) != cudaSuccess) return e;
+    e = iter(0, ls);
+    if (e == cudaSuccess) e = iter(0, ls);
+    if ((e = loop_close(ls, h, sc, maxit, e)) != cudaSuccess) return e;
+    *iters = -1;
+    *relres = -1.0;
+    return cudaSuccess;
+  }
   int launched = 0;
   CgScalars hs;
   const int chunk = 16;
   while (launched < maxit) {
     int todo = maxit - launched < chunk ? maxit - launched : chunk;
-    for (int it = 0; it < todo; ++it) {
-      int first = launched + it == 0;
-      if (tm) tm->begin(op_stage, s);
-      if ((e = cg_apply_t<T>(m, bands, coef, z, pc, pn, Ap, partials, sc, first, s)) !=
-          cudaSuccess)
-        return e;
-      if (tm) tm->end(op_stage, s);
-      k_cg_update<T, TX_><<<vb, 256, 0, s>>>(n, x, r, z, pn, Ap, dinv, partials, sc, maxit);
-      count_launches(1);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-      T* t = pc;
-      pc = pn;
-      pn = t;
-    }
+    for (int it = 0; it < todo; ++it)
+      if ((e = iter(launched + it == 0, s)) != cudaSuccess) return e;
     launched += todo;
     if ((e = cudaMemcpyAsync(&hs, sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s)) !=
         cudaSuccess)
@@ -1077,7 +1155,7 @@ static cudaError_t cg_solve_fdm(const MeshDev& m, const T* bands, const double* 
                                 T* r, T* z, T* zn, T* p0, T* p1, T* Ap, float* rf, float* zf,
                                 FdmPlan* fdm, double* partials, CgScalars* sc,
                                 cudaStream_t s, int* iters, double* relres, Timer* tm,
-                                bool x_is_zero) {
+                                bool x_is_zero, cudaStream_t ls) {
   cudaError_t e;
   int64_t n = m.n_nodes;
   int vb = vec_blocks(n);
@@ -1103,6 +1181,42 @@ static cudaError_t cg_solve_fdm(const MeshDev& m, const T* bands, const double* 
   T* pn = p1;
   T* zc = z;   // current preconditioned residual
   T* zo = zn;  // spare buffer
+  auto iter = [&](int first, cudaStream_t st) -> cudaError_t {
+    cudaError_t ee;
+    if (tm) tm->begin(op_stage, st);
+    if ((ee = cg_apply_t<T>(m, bands, coef, zc, pc, pn, Ap, partials, sc, first, st)) !=
+        cudaSuccess)
+      return ee;
+    if (tm) tm->end(op_stage, st);
+    k_cg_update_fdm<T, TX_><<<vb, 256, 0, st>>>(n, x, r, pn, Ap, conv ? rf : nullptr, partials,
+                                                sc, maxit);
+    count_launches(1);
+    if ((ee = cudaGetLastError()) != cudaSuccess) return ee;
+    // z_new = P^-1 r, beta (skipped on the device once converged)
+    float* zo_f = conv ? zf : reinterpret_cast<float*>(zo);
+    if ((ee = fdm_apply(fdm, rin, zo_f, &sc->done, st)) != cudaSuccess) return ee;
+    k_cg_dot_fdm<T><<<vb, 256, 0, st>>>(n, r, conv ? zf : nullptr, zc, zo, partials, sc, 0, 0);
+    count_launches(1);
+    if ((ee = cudaGetLastError()) != cudaSuccess) return ee;
+    T* t = zc;
+    zc = zo;
+    zo = t;
+    t = pc;
+    pc = pn;
+    pn = t;
+    return cudaSuccess;
+  };
+  if (ls) {  // device-driven loop inside a stream capture
+    if ((e = iter(1, s)) != cudaSuccess) return e;
+    cudaGraphConditionalHandle h;
+    if ((e = loop_open(s, ls, &h)) != cudaSuccess) return e;
+    e = iter(0, ls);
+    if (e == cudaSuccess) e = iter(0, ls);
+    if ((e = loop_close(ls, h, sc, maxit, e)) != cudaSuccess) return e;
+    *iters = -1;
+    *relres = -1.0;
+    return cudaSuccess;
+  }
   CgScalars hs;
   if ((e = cudaMemcpyAsync(&hs, sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return e;
@@ -1114,30 +1228,8 @@ static cudaError_t cg_solve_fdm(const MeshDev& m, const T* bands, const double* 
   int launched = 0;
   while (!hs.done && launched < maxit) {
     int todo = maxit - launched < chunk ? maxit - launched : chunk;
-    for (int c = 0; c < todo; ++c) {
-      int first = launched + c == 0;
-      if (tm) tm->begin(op_stage, s);
-      if ((e = cg_apply_t<T>(m, bands, coef, zc, pc, pn, Ap, partials, sc, first, s)) !=
-          cudaSuccess)
-        return e;
-      if (tm) tm->end(op_stage, s);
-      k_cg_update_fdm<T, TX_><<<vb, 256, 0, s>>>(n, x, r, pn, Ap, conv ? rf : nullptr,
-                                                 partials, sc, maxit);
-      count_launches(1);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-      // z_new = P^-1 r, beta (skipped on the device once converged)
-      float* zo_f = conv ? zf : reinterpret_cast<float*>(zo);
-      if ((e = fdm_apply(fdm, rin, zo_f, &sc->done, s)) != cudaSuccess) return e;
-      k_cg_dot_fdm<T><<<vb, 256, 0, s>>>(n, r, conv ? zf : nullptr, zc, zo, partials, sc, 0, 0);
-      count_launches(1);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-      T* t = zc;
-      zc = zo;
-      zo = t;
-      t = pc;
-      pc = pn;
-      pn = t;
-    }
+    for (int c = 0; c < todo; ++c)
+      if ((e = iter(launched + c == 0, s)) != cudaSuccess) return e;
     launched += todo;
     if ((e = cudaMemcpyAsync(&hs, sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s)) !=
         cudaSuccess)
@@ -1208,6 +1300,42 @@ static cudaError_t cg_solve_df(const MeshDev& m, const df64* bands, const double
   if ((e = fdm_apply(w.fdm, w.r32, zc, nullptr, s)) != cudaSuccess) return e;
   k_cg_dot_fdm<float><<<vb, 256, 0, s>>>(n, w.r32, nullptr, zc, zc, w.partials, w.sc, 1, 1);
   count_launches(1);
+  auto iter = [&](int first, cudaStream_t st) -> cudaError_t {
+    cudaError_t ee;
+    if (tm) tm->begin(kStageOp32, st);
+    k_cg_apply_df<K, S><<<g, kApplyThreads, sm, st>>>(m, bands, cf, zc, pc, pn, w.Ap_df,
+                                                     w.partials, w.sc, first);
+    if (tm) tm->end(kStageOp32, st);
+    k_cg_update_df<<<vb, 256, 0, st>>>(n, w.x_df, w.r_df, pn, w.Ap_df, w.r32, w.partials, w.sc,
+                                      maxit);
+    count_launches(2);
+    if ((ee = cudaGetLastError()) != cudaSuccess) return ee;
+    if ((ee = fdm_apply(w.fdm, w.r32, zo, &w.sc->done, st)) != cudaSuccess) return ee;
+    k_cg_dot_fdm<float><<<vb, 256, 0, st>>>(n, w.r32, nullptr, zc, zo, w.partials, w.sc, 0, 0, 1);
+    count_launches(1);
+    if ((ee = cudaGetLastError()) != cudaSuccess) return ee;
+    float* t = zc;
+    zc = zo;
+    zo = t;
+    df64* tp = pc;
+    pc = pn;
+    pn = tp;
+    return cudaSuccess;
+  };
+  if (w.loop) {  // device-driven loop inside a stream capture
+    if ((e = iter(1, s)) != cudaSuccess) return e;
+    cudaGraphConditionalHandle h;
+    if ((e = loop_open(s, w.loop, &h)) != cudaSuccess) return e;
+    e = iter(0, w.loop);
+    if (e == cudaSuccess) e = iter(0, w.loop);
+    if ((e = loop_close(w.loop, h, w.sc, maxit, e)) != cudaSuccess) return e;
+    k_join_df<<<vb, 256, 0, s>>>(n, w.x_df, x);
+    count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    *iters = -1;
+    *relres = -1.0;
+    return cudaSuccess;
+  }
   CgScalars hs;
   if ((e = cudaMemcpyAsync(&hs, w.sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return e;
@@ -1216,28 +1344,8 @@ static cudaError_t cg_solve_df(const MeshDev& m, const df64* bands, const double
   int launched = 0;
   while (!hs.done && launched < maxit) {
     int todo = maxit - launched < chunk ? maxit - launched : chunk;
-    for (int c = 0; c < todo; ++c) {
-      int first = launched + c == 0;
-      if (tm) tm->begin(kStageOp32, s);
-      k_cg_apply_df<K, S><<<g, kApplyThreads, sm, s>>>(m, bands, cf, zc, pc, pn, w.Ap_df,
-                                                    w.partials, w.sc, first);
-      if (tm) tm->end(kStageOp32, s);
-      k_cg_update_df<<<vb, 256, 0, s>>>(n, w.x_df, w.r_df, pn, w.Ap_df, w.r32, w.partials, w.sc,
-                                       maxit);
-      count_launches(2);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-      if ((e = fdm_apply(w.fdm, w.r32, zo, &w.sc->done, s)) != cudaSuccess) return e;
-      k_cg_dot_fdm<float><<<vb, 256, 0, s>>>(n, w.r32, nullptr, zc, zo, w.partials, w.sc, 0, 0,
-                                             1);
-      count_launches(1);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-      float* t = zc;
-      zc = zo;
-      zo = t;
-      df64* tp = pc;
-      pc = pn;
-      pn = tp;
-    }
+    for (int c = 0; c < todo; ++c)
+      if ((e = iter(launched + c == 0, s)) != cudaSuccess) return e;
     launched += todo;
     if ((e = cudaMemcpyAsync(&hs, w.sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s)) !=
         cudaSuccess)
@@ -1262,7 +1370,7 @@ cudaError_t run_cg64(const MeshDev& m, const double* bands, const double* coef,
     e = cg_solve_fdm<double, double, double>(m, bands, coef, b, x, x, rtol, maxit, w.r, w.z,
                                              w.zn, w.p0, w.p1, w.Ap, w.r32, w.z32, w.fdm,
                                              w.partials, w.sc, s, iters_host, relres_host,
-                                             w.timer, false);
+                                             w.timer, false, w.loop);
     if (e != cudaSuccess) return e;
     *converged = *relres_host <= rtol;
     return cudaSuccess;
@@ -1270,7 +1378,7 @@ cudaError_t run_cg64(const MeshDev& m, const double* bands, const double* coef,
   if ((e = make_dinv<double>(m, bands, coef, w.dinv, s)) != cudaSuccess) return e;
   e = cg_solve<double, double, double>(m, bands, coef, b, x, x, rtol, maxit, w.r, w.z, w.p0,
                                        w.p1, w.Ap, w.dinv, w.partials, w.sc, s, iters_host,
-                                       relres_host, w.timer);
+                                       relres_host, w.timer, w.loop);
   if (e != cudaSuccess) return e;
   *converged = *relres_host <= rtol;
   return cudaSuccess;
@@ -1300,6 +1408,9 @@ cudaError_t run_cg_mixed(const MeshDev& m, const double* bands64, const float* b
     *converged = rel <= rtol;
     return cudaSuccess;
   }
+  // the refinement loop below decides on the host: it cannot run inside a
+  // stream capture (the graph form of the mixed solve needs the FDM path)
+  if (w.loop) return cudaErrorNotSupported;
   if (!w.fdm && (e = make_dinv<float>(m, bands64, coef, w.dinv32, s)) != cudaSuccess) return e;
   int total_it = 0, outer = 0;
   double relres = 1.0;
@@ -1333,11 +1444,12 @@ cudaError_t run_cg_mixed(const MeshDev& m, const double* bands64, const float* b
       e = cg_solve_fdm<float, float, float>(m, bands32, coef, w.rin32, w.d32, w.d32, inner_rtol,
                                             maxit - total_it, w.r32, w.z32, w.zn32, w.q0, w.q1,
                                             w.Aq, nullptr, nullptr, w.fdm, w.partials, w.sc, s,
-                                            &it, &rr, w.timer, true);
+                                            &it, &rr, w.timer, true, nullptr);
     else
       e = cg_solve<float, float, float>(m, bands32, coef, w.rin32, w.d32, w.d32, inner_rtol,
                                         maxit - total_it, w.r32, w.z32, w.q0, w.q1, w.Aq,
-                                        w.dinv32, w.partials, w.sc, s, &it, &rr, w.timer);
+                                        w.dinv32, w.partials, w.sc, s, &it, &rr, w.timer,
+                                        nullptr);
     if (e != cudaSuccess) return e;
     total_it += it;
     k_add_scaled<<<vb, 256, 0, s>>>(n, x, w.d32, rn);

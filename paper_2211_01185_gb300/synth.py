@@ -220,6 +220,113 @@ def make_workload(name: str, seed: int | None = None) -> dict:
                 p_nodal=p, params=params)
 
 
+def make_batch_workload(n_beds: int = 64, seed: int | None = None, n_range=(5_000, 200_000),
+                        nxy=(8, 32), nz=(8, 64)) -> list:
+    """The ensemble of independent beds: per bed, elements per axis drawn from
+    nxy (x, y) and nz (z), degree k uniform in {1, 2, 3}, N log-uniform in
+    n_range, one diameter d ~ U[1, 3] mm, cubic elements of edge h chosen so
+    that N V_p = 0.3 of the box volume, particles on a jittered FCC lattice
+    at solid fraction 0.55 from the floor up, averaging radius at least the
+    particle radius, inflow u_z ~ U[0.5, 2] m/s with 5 % noise."""
+    rng = np.random.default_rng(SEED0 + 4 if seed is None else seed)
+    beds = []
+    for b in range(n_beds):
+        ne = (int(rng.integers(nxy[0], nxy[1] + 1)), int(rng.integers(nxy[0], nxy[1] + 1)),
+              int(rng.integers(nz[0], nz[1] + 1)))
+        k = int(rng.integers(1, 4))
+        n = int(round(math.exp(rng.uniform(math.log(n_range[0]), math.log(n_range[1])))))
+        d = float(rng.uniform(1e-3, 3e-3))
+        vp = math.pi * d ** 3 / 6.0
+        h = (n * vp / (0.3 * ne[0] * ne[1] * ne[2])) ** (1.0 / 3.0)
+        spec = dict(index=4, origin=(0.0, 0.0, 0.0),
+                    extent=(ne[0] * h, ne[1] * h, ne[2] * h), n_el=ne, k=k, n=n, d=(d, d),
+                    phi=0.55, packing="fcc", bed_frac=0.55, field="noise",
+                    u_mean=float(rng.uniform(0.5, 2.0)))
+        x, r = make_particles(spec, rng)
+        u, p, u_p = make_fields(spec, rng, n)
+        params = gas_params(d, k)
+        r_default = (3.0 * h ** 3 / (4.0 * math.pi)) ** (1.0 / 3.0)
+        if r_default < 0.5 * d:
+            params["qcm_radius"] = 0.5 * d
+        beds.append(dict(name="bed%02d" % b, origin=spec["origin"], extent=spec["extent"],
+                         n_el=ne, k=k, x=x, r=r, u_p=u_p, u_nodal=u, p_nodal=p, params=params))
+    return beds
+
+
+def make_adjoint_workload(seed: int | None = None) -> dict:
+    """The sensitivity workload: a 0.096 x 0.096 x 0.384 m box of 24 x 24 x 96
+    Q2 elements (h = 4 mm, averaging radius 2.481 mm), 200,000 spheres of
+    d = 2 mm from the floor up -- an annulus at solid fraction 0.5 on a
+    jittered FCC lattice (its top a little above half height) and a central
+    column of radius 0.15 L_x, lower half, at 0.05 by random sequential
+    addition -- under a jet u_z = 0.2 + 1.8 (1 - tanh((rho - 0.15
+    L_x) / (0.02 L_x))) / 2 m/s (rho the distance from the axis).  The loss
+    of this workload is J = sum_i e_z . f_D,i + ||eps_h||_M."""
+    rng = np.random.default_rng(SEED0 + 5 if seed is None else seed)
+    n_el, k, d = (24, 24, 96), 2, 2e-3
+    h = 4e-3
+    extent = (n_el[0] * h, n_el[1] * h, n_el[2] * h)
+    Lx = extent[0]
+    rc = 0.15 * Lx
+    cx = cy = 0.5 * Lx
+    top = 0.5 * extent[2]
+    r0 = 0.5 * d
+    # annulus: FCC at 0.5, sites whose sphere stays outside the column
+    a_nn = d * (0.74048 / 0.5) ** (1.0 / 3.0)
+    a = a_nn * math.sqrt(2.0)
+    ncx = int(math.floor(extent[0] / a))
+    ncz = int(math.floor(extent[2] / a))
+    basis = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]]) + 0.25
+    iz, iy, ix = np.meshgrid(np.arange(ncz), np.arange(ncx), np.arange(ncx), indexing="ij")
+    cells = np.stack([ix.ravel(), iy.ravel(), iz.ravel()], axis=1).astype(np.float64)
+    sites = (cells[:, None, :] + basis[None, :, :]).reshape(-1, 3) * a
+    rad = np.hypot(sites[:, 0] - cx, sites[:, 1] - cy)
+    sites = sites[rad >= rc + r0]
+    vcol = math.pi * rc * rc * top
+    ncol = int(round(0.05 * vcol / (math.pi * d ** 3 / 6.0)))
+    # the lowest annulus sites up to N = 200,000 in all (the lattice, cut by
+    # the walls, holds a little less than that below half height)
+    sites = sites[np.lexsort((sites[:, 0], sites[:, 1], sites[:, 2]))][:200_000 - ncol]
+    jit = 0.5 * (a_nn - d)
+    u = rng.normal(size=sites.shape)
+    u /= np.linalg.norm(u, axis=1)[:, None]
+    xa = sites + u * (jit * rng.random(sites.shape[0]) ** (1.0 / 3.0))[:, None]
+    # column: random sequential addition at 0.05
+    cand = []
+    lo = np.array([cx - rc + r0, cy - rc + r0, r0])
+    hi = np.array([cx + rc - r0, cy + rc - r0, top - r0])
+    pts = np.zeros((0, 3))
+    while pts.shape[0] < ncol:
+        c = lo + (hi - lo) * rng.random((4 * ncol, 3))
+        c = c[np.hypot(c[:, 0] - cx, c[:, 1] - cy) <= rc - r0]
+        for q in c:
+            if pts.shape[0] >= ncol:
+                break
+            if pts.shape[0] == 0 or np.min(np.sum((pts - q) ** 2, axis=1)) >= d * d:
+                pts = np.vstack([pts, q])
+        cand.append(c.shape[0])
+    x = np.ascontiguousarray(np.vstack([xa, pts]))
+    n = x.shape[0]
+    r = np.full(n, r0)
+    spec = dict(index=5, origin=(0.0, 0.0, 0.0), extent=extent, n_el=n_el, k=k, n=n, d=(d, d),
+                phi=0.5, packing="fcc", bed_frac=0.5, field="noise", u_mean=0.0)
+    ax, ay, az = node_axes(np.zeros(3), np.asarray(extent), n_el, k)
+    Z, Y, X = np.meshgrid(az, ay, ax, indexing="ij")
+    rho = np.hypot(X.ravel() - cx, Y.ravel() - cy)
+    un = np.zeros((X.size, 3))
+    un[:, 2] = 0.2 + 1.8 * 0.5 * (1.0 - np.tanh((rho - rc) / (0.02 * Lx)))
+    kp = max(1, k - 1)
+    px, py, pz = node_axes(np.zeros(3), np.asarray(extent), n_el, kp)
+    PZ, PY, PX = np.meshgrid(pz, py, px, indexing="ij")
+    p = 0.5 * (RHO_P - 1.2) * 9.81 * (extent[2] - PZ.ravel())
+    u_p = 0.1 * rng.random((n, 3)) - 0.05
+    params = gas_params(d, k)
+    del spec, cand
+    return dict(name="adjoint_24x24x96_200k", origin=(0.0, 0.0, 0.0), extent=extent, n_el=n_el,
+                k=k, x=x, r=r, u_p=u_p, u_nodal=np.ascontiguousarray(un), p_nodal=p,
+                params=params)
+
+
 def make_random_case(seed: int, n_el=(3, 4, 5), k=2, n=150, extent=(0.03, 0.04, 0.05),
                      d=(2e-3, 6e-3), origin=(0.0, 0.0, 0.0), overlap_ok=True) -> dict:
     """Small uneven case for parity tests: uniform random centres over the

@@ -1,0 +1,159 @@
+"""Batched ensemble of independent beds (cfdem_batch_*), replayed as one
+CUDA graph whose CG loops iterate on the device.
+
+Every bed of a batch step must give what cfdem_coupling_step gives on that
+bed alone (up to the order of the atomic additions of the right-hand side
+and the fluid source), on the eager first step and on graph replays; a
+replay must read the current contents of the captured buffers; a bed that
+cannot be captured keeps the batch eager; and a replayed FP64 bed must match
+the oracle within the FP64 bound."""
+import numpy as np
+import pytest
+
+from _parity import dev, host, rel_err
+from oracle import oracle as O
+from paper_2211_01185_gb300 import cfdem as cf
+from paper_2211_01185_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+SAME = 1e-9  # batch vs solo: both converge to rtol 1e-12 from the same data
+
+
+def _beds():
+    beds = synth.make_batch_workload(6, seed=77, n_range=(400, 2500), nxy=(4, 8), nz=(4, 10))
+    for i, b in enumerate(beds):
+        b["params"] = dict(b["params"], precision=i % 2, cg_rtol=1e-12)
+    # one FP64 bed with the Jacobi preconditioner (a longer device-driven loop)
+    beds[2]["params"] = dict(beds[2]["params"], precision=0, cg_precond=0)
+    return beds
+
+
+def _buffers(b):
+    import torch
+    n = b["x"].shape[0]
+    ne = int(np.prod(b["n_el"]))
+    nn = int(np.prod([b["n_el"][a] * b["k"] + 1 for a in range(3)]))
+    z = lambda *s: torch.zeros(s, dtype=torch.float64, device="cuda:0")
+    return dict(x=dev(b["x"]), r=dev(b["r"]), u_p=dev(b["u_p"]), u=dev(b["u_nodal"]),
+                p=dev(b["p_nodal"]), eps=z(nn), f=z(n, 3), fd=z(n, 3), Fe=z(ne, 3), n=n)
+
+
+def _io(t):
+    return cf.bed_io(t["n"], t["x"], t["r"], t["u_p"], t["u"], t["p"], t["eps"], t["f"],
+                     t["fd"], t["Fe"])
+
+
+def _solo(b, t):
+    """cfdem_coupling_step on the bed alone, cold start; host copies."""
+    import torch
+    out = {k: torch.zeros_like(t[k]) for k in ("eps", "f", "fd", "Fe")}
+    with cf.Context(b["origin"], b["extent"], b["n_el"], b["k"], b["params"]) as ctx:
+        cf.cfdem_coupling_step(ctx.h, t["n"], t["x"], t["r"], t["u_p"], t["u"], t["p"],
+                               out["eps"], out["f"], out["fd"], out["Fe"])
+        cf.cfdem_synchronize(ctx.h)
+    return {k: host(v) for k, v in out.items()}
+
+
+def _make_batch(beds):
+    import torch
+    bh = cf.cfdem_batch_create(len(beds), 0, torch.cuda.current_stream().cuda_stream)
+    for i, b in enumerate(beds):
+        h = cf.cfdem_batch_bed(bh, i)
+        cf.cfdem_set_mesh(h, b["origin"], b["extent"], b["n_el"], b["k"])
+        cf.cfdem_set_params(h, cf.make_params(**b["params"]))
+    return bh
+
+
+def _step(bh, bufs):
+    for t in bufs:
+        t["eps"].zero_()  # cold start, as the solo reference
+    st = cf.cfdem_batch_coupling_step(bh, [_io(t) for t in bufs])
+    assert st == cf.OK, cf.cfdem_batch_last_error(bh)
+    st, bad = cf.cfdem_batch_synchronize(bh)
+    assert st == cf.OK and bad == -1
+    return cf.cfdem_batch_last_replayed(bh)
+
+
+def _check(bufs, refs):
+    for t, ref in zip(bufs, refs):
+        for k in ("eps", "f", "fd", "Fe"):
+            assert rel_err(host(t[k]), ref[k]) <= SAME, k
+
+
+def test_batch_matches_solo_eager_and_replayed():
+    beds = _beds()
+    bufs = [_buffers(b) for b in beds]
+    refs = [_solo(b, t) for b, t in zip(beds, bufs)]
+    bh = _make_batch(beds)
+    try:
+        replayed = []
+        for _ in range(3):
+            replayed.append(_step(bh, bufs))
+            _check(bufs, refs)
+        assert replayed == [0, 1, 1]
+        for i, b in enumerate(beds):
+            s = cf.cfdem_get_stats(cf.cfdem_batch_bed(bh, i))
+            assert s.converged == 1 and s.cg_iterations >= 1
+            if b["params"].get("cg_precond", 1) == 1:
+                assert s.cg_iterations <= 8
+    finally:
+        cf.cfdem_batch_destroy(bh)
+
+
+def test_replay_reads_current_buffer_contents():
+    beds = _beds()[:3]
+    bufs = [_buffers(b) for b in beds]
+    bh = _make_batch(beds)
+    try:
+        assert _step(bh, bufs) == 0
+        rng = np.random.default_rng(5)
+        for b, t in zip(beds, bufs):  # move the particles and change the flow in place
+            ext = np.asarray(b["extent"])
+            x = np.clip(b["x"] + 0.05 * b["r"][:, None] * rng.standard_normal(b["x"].shape),
+                        0.0, ext)
+            b["x"] = x
+            b["u_nodal"] = b["u_nodal"] * 1.3
+            t["x"].copy_(dev(x))
+            t["u"].copy_(dev(b["u_nodal"]))
+        refs = [_solo(b, t) for b, t in zip(beds, bufs)]
+        assert _step(bh, bufs) == 1
+        _check(bufs, refs)
+    finally:
+        cf.cfdem_batch_destroy(bh)
+
+
+def test_uncapturable_bed_keeps_the_batch_eager():
+    beds = _beds()[:2]
+    beds[1]["params"] = dict(beds[1]["params"], precision=1, cg_precond=0)
+    bufs = [_buffers(b) for b in beds]
+    refs = [_solo(b, t) for b, t in zip(beds, bufs)]
+    bh = _make_batch(beds)
+    try:
+        assert [_step(bh, bufs) for _ in range(2)] == [0, 0]
+        _check(bufs, refs)
+    finally:
+        cf.cfdem_batch_destroy(bh)
+
+
+def test_replayed_fp64_bed_matches_oracle():
+    case = synth.make_random_case(321, n_el=(5, 4, 6), k=2, n=300, extent=(0.05, 0.04, 0.06))
+    prm = dict(case["params"], precision=0)
+    bed = dict(origin=case["origin"], extent=case["extent"], n_el=case["n_el"], k=case["k"],
+               x=case["x"], r=case["r"], u_p=case["u_p"], u_nodal=case["u_nodal"],
+               p_nodal=case["p_nodal"], params=prm)
+    bufs = [_buffers(bed)]
+    bh = _make_batch([bed])
+    try:
+        _step(bh, bufs)
+        assert _step(bh, bufs) == 1
+    finally:
+        cf.cfdem_batch_destroy(bh)
+    m = O.Mesh(case["origin"], case["extent"], case["n_el"], case["k"])
+    ref = O.coupling_step(m, prm, case["x"], case["r"], case["u_p"], case["u_nodal"],
+                          case["p_nodal"])
+    t = bufs[0]
+    assert rel_err(host(t["eps"]), ref["eps_h"]) <= 1e-10
+    assert rel_err(host(t["f"]), ref["f"]) <= 1e-10
+    assert rel_err(host(t["fd"]), ref["f_drag"]) <= 1e-10
+    assert rel_err(host(t["Fe"]), ref["F_e"]) <= 1e-10

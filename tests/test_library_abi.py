@@ -44,6 +44,9 @@ int main(void) {
   P(cfdem_stats, cg_iterations); P(cfdem_stats, cg_relres); P(cfdem_stats, nb);
   P(cfdem_stats, bin_edge); P(cfdem_stats, qcm_radius); P(cfdem_stats, n_pnodes);
   P(cfdem_stats, stage_ms); P(cfdem_stats, kernel_launches); P(cfdem_stats, precond);
+  printf("cfdem_bed_io %zu\n", sizeof(cfdem_bed_io));
+  P(cfdem_bed_io, n); P(cfdem_bed_io, x); P(cfdem_bed_io, p_nodal); P(cfdem_bed_io, eps_nodal);
+  P(cfdem_bed_io, F_q);
   return 0;
 }
 '''
@@ -57,6 +60,7 @@ int main(void) {
     import ctypes as C
     assert int(got["cfdem_params"]) == C.sizeof(cf.cfdem_params)
     assert int(got["cfdem_stats"]) == C.sizeof(cf.cfdem_stats)
+    assert int(got["cfdem_bed_io"]) == C.sizeof(cf.cfdem_bed_io)
     for key, val in got.items():
         if "." in key:
             s, f = key.split(".")
