@@ -1,0 +1,66 @@
+// df64.cuh -- double-float arithmetic: a value carried as an unevaluated sum
+// of two FP32 numbers (hi + lo, |lo| <= ulp(hi) / 2), about 48 significant
+// bits, on the FP32 pipes.  Addition by Knuth's two-sum, multiplication by
+// the FMA-based exact product (Dekker 1971; Shewchuk 1997), square root and
+// reciprocal by one Newton step from the FP32 estimate.
+#pragma once
+
+namespace cfdem {
+
+struct df64 {
+  float hi, lo;
+  __host__ __device__ __forceinline__ df64() {}
+  __host__ __device__ __forceinline__ df64(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ __forceinline__ df64(int v) : hi((float)v), lo(0.f) {}
+  __host__ __device__ __forceinline__ df64(float v) : hi(v), lo(0.f) {}
+};
+__device__ __forceinline__ df64 df_renorm(float s, float e) {
+  float hi = s + e;
+  return df64(hi, e - (hi - s));
+}
+__device__ __forceinline__ df64 operator+(df64 a, df64 b) {
+  float s = a.hi + b.hi;
+  float bb = s - a.hi;
+  float e = (a.hi - (s - bb)) + (b.hi - bb);
+  e += a.lo + b.lo;
+  return df_renorm(s, e);
+}
+__device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
+__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
+__device__ __forceinline__ df64 operator*(df64 a, df64 b) {
+  float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return df_renorm(p, e);
+}
+__device__ __forceinline__ df64& operator+=(df64& a, df64 b) {
+  a = a + b;
+  return a;
+}
+__device__ __forceinline__ bool operator!=(df64 a, df64 b) { return a.hi != b.hi || a.lo != b.lo; }
+__device__ __forceinline__ df64 df_from_double(double v) {
+  float h = (float)v;
+  return df64(h, (float)(v - (double)h));
+}
+
+__device__ __forceinline__ bool df_le(df64 a, df64 b) {
+  return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo);
+}
+// sqrt(a) for a > 0: x0 = a.hi rsqrt(a.hi), then x0 + (a - x0^2) / (2 x0)
+__device__ __forceinline__ df64 df_sqrt(df64 a) {
+  float y = rsqrtf(a.hi);
+  float x0 = a.hi * y;
+  float p = x0 * x0;
+  float e = fmaf(x0, x0, -p);
+  df64 r = a - df64(p, e);
+  return df_renorm(x0, r.hi * (0.5f * y));
+}
+// 1/b: y0 = 1/b.hi, then y0 + y0 (1 - b y0)
+__device__ __forceinline__ df64 df_recip(df64 b) {
+  float y0 = 1.0f / b.hi;
+  df64 r = df64(1.0f) - b * df64(y0);
+  return df_renorm(y0, y0 * r.hi);
+}
+
+}  // namespace cfdem

@@ -230,7 +230,7 @@ __global__ void k_gather_sorted(MeshDev m, int64_t n, const int32_t* __restrict_
   }
   float4* o = reinterpret_cast<float4*>(xs32) + 2 * s;
   o[0] = make_float4(hi[0], hi[1], hi[2], (float)ri);
-  o[1] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+  o[1] = make_float4(lo[0], lo[1], lo[2], (float)(ri - (double)(float)ri));
 }
 
 cudaError_t launch_bin(const MeshDev& m, const BinDev& b, int64_t n, const double* x,

@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "df64.cuh"
 
 namespace cfdem {
 
@@ -221,43 +222,6 @@ struct Coefs {
 // two-product (Dekker 1971; Knuth, TAOCP vol. 2).  They give the mixed path
 // residuals accurate to ~1e-14 on the FP32 pipes, which on this part have 61
 // times the FP64 throughput.
-struct df64 {
-  float hi, lo;
-  __host__ __device__ __forceinline__ df64() {}
-  __host__ __device__ __forceinline__ df64(float h, float l) : hi(h), lo(l) {}
-  __host__ __device__ __forceinline__ df64(int v) : hi((float)v), lo(0.f) {}
-  __host__ __device__ __forceinline__ df64(float v) : hi(v), lo(0.f) {}
-};
-__device__ __forceinline__ df64 df_renorm(float s, float e) {
-  float hi = s + e;
-  return df64(hi, e - (hi - s));
-}
-__device__ __forceinline__ df64 operator+(df64 a, df64 b) {
-  float s = a.hi + b.hi;
-  float bb = s - a.hi;
-  float e = (a.hi - (s - bb)) + (b.hi - bb);
-  e += a.lo + b.lo;
-  return df_renorm(s, e);
-}
-__device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
-__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
-__device__ __forceinline__ df64 operator*(df64 a, df64 b) {
-  float p = a.hi * b.hi;
-  float e = fmaf(a.hi, b.hi, -p);
-  e = fmaf(a.hi, b.lo, e);
-  e = fmaf(a.lo, b.hi, e);
-  return df_renorm(p, e);
-}
-__device__ __forceinline__ df64& operator+=(df64& a, df64 b) {
-  a = a + b;
-  return a;
-}
-__device__ __forceinline__ bool operator!=(df64 a, df64 b) { return a.hi != b.hi || a.lo != b.lo; }
-__device__ __forceinline__ df64 df_from_double(double v) {
-  float h = (float)v;
-  return df64(h, (float)(v - (double)h));
-}
-
 // --- load and epilogue policies of the tile operator -----------------------
 // Plain: x_eff = x[g]
 template <typename T>

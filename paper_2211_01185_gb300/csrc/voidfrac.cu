@@ -28,11 +28,11 @@
 #include <cstdint>
 
 #include "internal.h"
+#include "df64.cuh"
 
 namespace cfdem {
 
 constexpr int kQcmWarps = 4;      // warps (elements) per block
-constexpr int kQcmChunk = 128;    // staged candidates per warp
 
 struct QcmParams {
   double R;            // averaging radius
@@ -44,7 +44,13 @@ struct QcmParams {
   float hx_hi, hx_lo, hy_hi, hy_lo, hz_hi, hz_lo;  // float-float element size
   float inv_be[3];     // 1 / bin edge
   float qrel[64][3];   // Gauss point minus element centre, FP32
+  float g1[3][4];      // per axis: 1D Gauss point minus element centre, FP32
   double g[4];         // Gauss points on [0,1]
+  // double-float constants of the FP64 path's lens volumes
+  float g_hi[4], g_lo[4];  // Gauss points on [0,1]
+  float R_hi, R_lo;        // averaging radius
+  float c43_hi, c43_lo;    // 4 pi / 3
+  float c12_hi, c12_lo;    // pi / 12
 };
 
 __device__ __forceinline__ float ff_two_prod_sum(float a, float b_hi, float b_lo, float* lo) {
@@ -55,27 +61,17 @@ __device__ __forceinline__ float ff_two_prod_sum(float a, float b_hi, float b_lo
   return p;
 }
 
-__device__ __forceinline__ double lens64(double R, double r, double d2) {
-  // intersection volume of spheres of radii R, r at squared distance d2 < (R+r)^2:
-  // pi s^2 (d^2 + 2 d (R+r) - 3 (R-r)^2) / (12 d), s = R + r - d, written with
-  // y = 1/d from one reciprocal square root (d = d2 y) to spare the FP64
-  // square root and division
-  double dm = R - r;
-  double mn = R < r ? R : r;
-  if (d2 <= dm * dm) return (4.0 / 3.0 * kPi) * mn * mn * mn;
-  double y = rsqrt(d2);
-  double d = d2 * y;
-  double s = (R + r) - d;
-  return (kPi / 12.0) * s * s * (d + 2.0 * (R + r) - 3.0 * dm * dm * y);
-}
-
 __device__ __forceinline__ float lens32(float R, float r, float d2) {
+  // d and 1/d from one reciprocal square root (no square root, no division)
   float dm = R - r;
-  float mn = fminf(R, r);
-  float d = sqrtf(d2);
-  if (d <= fabsf(dm)) return (float)(4.0 / 3.0 * kPi) * mn * mn * mn;
+  if (d2 <= dm * dm) {
+    float mn = fminf(R, r);
+    return (float)(4.0 / 3.0 * kPi) * mn * mn * mn;
+  }
+  float y = rsqrtf(d2);
+  float d = d2 * y;
   float s = (R + r) - d;
-  return (float)kPi * s * s * (d2 + 2.0f * d * (R + r) - 3.0f * dm * dm) / (12.0f * d);
+  return (float)(kPi / 12.0) * s * s * (d2 + 2.0f * d * (R + r) - 3.0f * dm * dm) * y;
 }
 
 // Neumaier compensated accumulation
@@ -96,48 +92,78 @@ struct QcmSmem {
   int32_t bslot[kQcmWarps][64];            // their sorted slots
   float4 grp[kQcmWarps][32];               // the group under test (one per lane)
   int32_t gslot[kQcmWarps][32];
-  int32_t queue[kQcmWarps][64];            // hits (lane of the group << 6) | q, q-sorted
+  // hits (lane of the group << 6) | q, q-sorted: room for the hits of one
+  // layer of Gauss points ((K+1)^2 points x 32 lanes) on top of < 32 pending
+  static constexpr int QCAP = 32 * (K + 1) * (K + 1) + 32;
+  int32_t queue[kQcmWarps][QCAP];
   float acc[kQcmWarps][Q], cmp[kQcmWarps][Q];       // mixed: Neumaier sums
-  double acc64[kQcmWarps][FP64 ? Q : 1];            // FP64 sums
+  df64 accdf[kQcmWarps][FP64 ? Q : 1];              // FP64 path: double-float sums
   int32_t cnt[kQcmWarps][Q];
   long long ids[kQcmWarps][Q];
   double xq[kQcmWarps][FP64 ? Q : 1][3];            // FP64 Gauss points
   P4 g64[kQcmWarps][FP64 ? 32 : 1];                 // FP64 positions of the group
+  // FP64 path: the group's positions relative to the mesh origin and radii
+  // as double-float (hi and lo parts), and the Gauss points of the element
+  // per axis (x0-relative, hi and lo)
+  float4 ghi[kQcmWarps][FP64 ? 32 : 1], glo[kQcmWarps][FP64 ? 32 : 1];
+  float xqf[kQcmWarps][FP64 ? 3 : 1][4][2];
 };
+
+// lens volume of the FP64 path in double-float arithmetic (relative error
+// ~1e-13 on the FP32 pipes): the full smaller sphere for d <= |R - r|, else
+// pi (R + r - d)^2 (d^2 + 2 d (R + r) - 3 (R - r)^2) / (12 d)
+// (c43 = 4 pi / 3 and c12 = pi / 12 as double-float, split on the host)
+__device__ __forceinline__ df64 lens_df(df64 R, df64 r, df64 D, df64 c43, df64 c12) {
+  df64 dm = R - r;
+  df64 dm2 = dm * dm;
+  if (df_le(D, dm2)) {
+    df64 mn = df_le(R, r) ? R : r;
+    return c43 * (mn * mn * mn);
+  }
+  df64 d = df_sqrt(D);
+  df64 S = R + r;
+  df64 sdist = S - d;
+  df64 num = D + df64(2.0f) * d * S - df64(3.0f) * dm2;
+  return c12 * sdist * sdist * num * df_recip(d);
+}
 
 struct QcmWarp {
   int warp, lane;
   unsigned lt_mask;
   double R;
   float R32, band;
-  bool want_ids;
+  float R_hi, R_lo;
+  df64 c43, c12;
+  bool want_counts, want_ids;
 };
 
 // Evaluate the first cnt queued hits (q-sorted) and add each quadrature
 // point's share with one segmented warp scan; the last lane of a segment
 // updates that point's sum, so every sum is accumulated in a fixed order.
 template <int K, bool FP64>
-__device__ __forceinline__ void qcm_flush(QcmSmem<K, FP64>& sm, const QcmWarp& w, int cnt,
-                                          const int32_t* __restrict__ perm) {
+__device__ __forceinline__ void qcm_flush(QcmSmem<K, FP64>& sm, const QcmWarp& w, int base,
+                                          int cnt, const int32_t* __restrict__ perm) {
   const unsigned FULL = 0xffffffffu;
   const int lane = w.lane, wp = w.warp;
   int q = -1 - lane;  // distinct sentinels for idle lanes
-  double v64 = 0.0;
+  df64 vdf(0.f, 0.f);
   float v32 = 0.f;
   long long id = 0;
   int one = 0;
   if (lane < cnt) {
-    int pk = sm.queue[wp][lane];
+    int pk = sm.queue[wp][base + lane];
     q = pk & 63;
     int j = pk >> 6;
     one = 1;
     if (FP64) {
-      P4 pj = sm.g64[wp][j];
-      double dx = __dsub_rn(pj.x, sm.xq[wp][q][0]);
-      double dy = __dsub_rn(pj.y, sm.xq[wp][q][1]);
-      double dz = __dsub_rn(pj.z, sm.xq[wp][q][2]);
-      double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-      v64 = lens64(w.R, pj.w, d2);
+      constexpr int NQ = K + 1;
+      const int qx = q % NQ, qy = (q / NQ) % NQ, qz = q / (NQ * NQ);
+      float4 H = sm.ghi[wp][j], L = sm.glo[wp][j];
+      df64 dx = df64(H.x, L.x) - df64(sm.xqf[wp][0][qx][0], sm.xqf[wp][0][qx][1]);
+      df64 dy = df64(H.y, L.y) - df64(sm.xqf[wp][1][qy][0], sm.xqf[wp][1][qy][1]);
+      df64 dz = df64(H.z, L.z) - df64(sm.xqf[wp][2][qz][0], sm.xqf[wp][2][qz][1]);
+      df64 D = dx * dx + dy * dy + dz * dz;
+      vdf = lens_df(df64(w.R_hi, w.R_lo), df64(H.w, L.w), D, w.c43, w.c12);
     } else {
       float4 cj = sm.grp[wp][j];
       float4 qq = sm.qrel[q];
@@ -146,39 +172,56 @@ __device__ __forceinline__ void qcm_flush(QcmSmem<K, FP64>& sm, const QcmWarp& w
     }
     if (w.want_ids) id = perm[sm.gslot[wp][j]];
   }
+  if (w.want_counts) {
 #pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    int qu = __shfl_up_sync(FULL, q, off);
-    int nu = __shfl_up_sync(FULL, one, off);
-    double vu64 = FP64 ? __shfl_up_sync(FULL, v64, off) : 0.0;
-    float vu32 = FP64 ? 0.f : __shfl_up_sync(FULL, v32, off);
-    long long iu = w.want_ids ? __shfl_up_sync(FULL, id, off) : 0;
-    if (lane >= off && qu == q) {
-      one += nu;
-      if (FP64) v64 += vu64; else v32 += vu32;
-      id += iu;
+    for (int off = 1; off < 32; off <<= 1) {
+      int qu = __shfl_up_sync(FULL, q, off);
+      int nu = __shfl_up_sync(FULL, one, off);
+      df64 vu(FP64 ? __shfl_up_sync(FULL, vdf.hi, off) : 0.f,
+              FP64 ? __shfl_up_sync(FULL, vdf.lo, off) : 0.f);
+      float vu32 = FP64 ? 0.f : __shfl_up_sync(FULL, v32, off);
+      long long iu = w.want_ids ? __shfl_up_sync(FULL, id, off) : 0;
+      if (lane >= off && qu == q) {
+        one += nu;
+        if (FP64) vdf = vdf + vu; else v32 += vu32;
+        id += iu;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      int qu = __shfl_up_sync(FULL, q, off);
+      df64 vu(FP64 ? __shfl_up_sync(FULL, vdf.hi, off) : 0.f,
+              FP64 ? __shfl_up_sync(FULL, vdf.lo, off) : 0.f);
+      float vu32 = FP64 ? 0.f : __shfl_up_sync(FULL, v32, off);
+      if (lane >= off && qu == q) {
+        if (FP64) vdf = vdf + vu; else v32 += vu32;
+      }
     }
   }
   int qn = __shfl_down_sync(FULL, q, 1);
   bool last = lane < cnt && (lane == cnt - 1 || qn != q);
   if (last) {
     if (FP64) {
-      sm.acc64[wp][q] += v64;
+      sm.accdf[wp][q] += vdf;
     } else {
       neumaier(sm.acc[wp][q], sm.cmp[wp][q], v32);
     }
-    sm.cnt[wp][q] += one;
-    sm.ids[wp][q] += id;
+    if (w.want_counts) {
+      sm.cnt[wp][q] += one;
+      sm.ids[wp][q] += id;
+    }
   }
   __syncwarp();
 }
 
 // test the cnt (<= 32) buffered candidates against every quadrature point
 template <int K, bool FP64>
-__device__ __forceinline__ void qcm_group(QcmSmem<K, FP64>& sm, const QcmWarp& w, int cnt,
+__device__ __forceinline__ void qcm_group(QcmSmem<K, FP64>& sm, const QcmWarp& w,
+                                          const QcmParams& P, int cnt,
                                           const double* __restrict__ xs64,
+                                          const float* __restrict__ xs32,
                                           const int32_t* __restrict__ perm) {
-  constexpr int Q = QcmSmem<K, FP64>::Q;
   const unsigned FULL = 0xffffffffu;
   const int lane = w.lane, wp = w.warp;
   const bool valid = lane < cnt;
@@ -189,48 +232,76 @@ __device__ __forceinline__ void qcm_group(QcmSmem<K, FP64>& sm, const QcmWarp& w
     myslot = sm.bslot[wp][lane];
     sm.grp[wp][lane] = my;
     sm.gslot[wp][lane] = myslot;
-    if (FP64) sm.g64[wp][lane] = reinterpret_cast<const P4*>(xs64)[myslot];
+    if (FP64) {
+      sm.g64[wp][lane] = reinterpret_cast<const P4*>(xs64)[myslot];
+      const float4* ff = reinterpret_cast<const float4*>(xs32) + 2 * (int64_t)myslot;
+      sm.ghi[wp][lane] = ff[0];
+      sm.glo[wp][lane] = ff[1];
+    }
   }
   __syncwarp();
   const float c = w.R32 + my.w;
   const float c2 = c * c;
   const float c2_in = c2 / w.band, c2_out = c2 * w.band;
+  // squared distance to Gauss point (a, b, c) = sx[a] + (sy[b] + sz[c]):
+  // per-axis squares once per candidate, two additions per point
+  float sx[K + 1], sy[K + 1];
+#pragma unroll
+  for (int a = 0; a <= K; ++a) {
+    float dx = my.x - P.g1[0][a];
+    float dy = my.y - P.g1[1][a];
+    sx[a] = dx * dx;
+    sy[a] = dy * dy;
+  }
   int qn = 0;
-  for (int q = 0; q < Q; ++q) {
-    float4 qq = sm.qrel[q];
-    float dx = my.x - qq.x, dy = my.y - qq.y, dz = my.z - qq.z;
-    float d2 = dx * dx + dy * dy + dz * dz;
-    bool hit;
-    if (FP64) {
-      hit = valid && d2 < c2_in;
-      if (valid && d2 >= c2_in && d2 <= c2_out) {  // inside the band: exact FP64 predicate
-        P4 pj = sm.g64[wp][lane];
-        double ddx = __dsub_rn(pj.x, sm.xq[wp][q][0]);
-        double ddy = __dsub_rn(pj.y, sm.xq[wp][q][1]);
-        double ddz = __dsub_rn(pj.z, sm.xq[wp][q][2]);
-        double dd2 =
-            __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
-        double cc = __dadd_rn(w.R, pj.w);
-        hit = dd2 < __dmul_rn(cc, cc);
+  for (int cz = 0; cz <= K; ++cz) {
+    // the z offset of Gauss layer cz, from shared memory (a runtime index into
+    // the kernel parameters would move them to local memory)
+    float dz = my.z - sm.qrel[cz * (K + 1) * (K + 1)].z;
+    float sz = dz * dz;
+#pragma unroll
+    for (int b = 0; b <= K; ++b) {
+      float syz = sy[b] + sz;
+#pragma unroll
+      for (int a = 0; a <= K; ++a) {
+        const int q = a + (K + 1) * (b + (K + 1) * cz);
+        float d2 = sx[a] + syz;
+        bool hit;
+        if (FP64) {
+          hit = valid && d2 < c2_in;
+          if (valid && d2 >= c2_in && d2 <= c2_out) {  // inside the band: exact FP64 predicate
+            P4 pj = sm.g64[wp][lane];
+            double ddx = __dsub_rn(pj.x, sm.xq[wp][q][0]);
+            double ddy = __dsub_rn(pj.y, sm.xq[wp][q][1]);
+            double ddz = __dsub_rn(pj.z, sm.xq[wp][q][2]);
+            double dd2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)),
+                                   __dmul_rn(ddz, ddz));
+            double cc = __dadd_rn(w.R, pj.w);
+            hit = dd2 < __dmul_rn(cc, cc);
+          }
+        } else {
+          hit = valid && d2 < c2;
+        }
+        unsigned mask = __ballot_sync(FULL, hit);
+        if (hit) sm.queue[wp][qn + __popc(mask & w.lt_mask)] = (lane << 6) | q;
+        qn += __popc(mask);
       }
-    } else {
-      hit = valid && d2 < c2;
     }
-    unsigned mask = __ballot_sync(FULL, hit);
-    if (hit) sm.queue[wp][qn + __popc(mask & w.lt_mask)] = (lane << 6) | q;
-    qn += __popc(mask);
+    // evaluate the full batches of 32 hits queued by this layer (one copy of
+    // the flush, outside the unrolled tests), keep the rest at the front
     if (qn >= 32) {
       __syncwarp();
-      qcm_flush<K, FP64>(sm, w, 32, perm);
-      int rest = qn - 32;
-      int tmp = lane < rest ? sm.queue[wp][32 + lane] : 0;
+      int base = 0;
+      for (; qn - base >= 32; base += 32) qcm_flush<K, FP64>(sm, w, base, 32, perm);
+      int rest = qn - base;
+      int tmp = lane < rest ? sm.queue[wp][base + lane] : 0;
       __syncwarp();
       if (lane < rest) sm.queue[wp][lane] = tmp;
       qn = rest;
     }
-    __syncwarp();
   }
-  if (qn > 0) qcm_flush<K, FP64>(sm, w, qn, perm);
+  __syncwarp();
+  if (qn > 0) qcm_flush<K, FP64>(sm, w, 0, qn, perm);
 }
 
 template <int K, bool FP64>
@@ -251,7 +322,12 @@ k_qcm(MeshDev m, QcmParams P, BinDev b, const int32_t* __restrict__ bin_start,
   w.R = P.R;
   w.R32 = P.R32;
   w.band = 1.0f + P.delta;
+  w.R_hi = P.R_hi;
+  w.R_lo = P.R_lo;
+  w.c43 = df64(P.c43_hi, P.c43_lo);
+  w.c12 = df64(P.c12_hi, P.c12_lo);
   w.want_ids = nb_idsum != nullptr;
+  w.want_counts = nb_count != nullptr || nb_idsum != nullptr;
   const int lane = w.lane, wp = w.warp;
   for (int t = threadIdx.x; t < Q; t += blockDim.x)
     sm.qrel[t] = make_float4(P.qrel[t][0], P.qrel[t][1], P.qrel[t][2], 0.f);
@@ -268,13 +344,27 @@ k_qcm(MeshDev m, QcmParams P, BinDev b, const int32_t* __restrict__ bin_start,
     sm.cnt[wp][q] = 0;
     sm.ids[wp][q] = 0;
     if (FP64) {
-      sm.acc64[wp][q] = 0.0;
+      sm.accdf[wp][q] = df64(0.f, 0.f);
       int qx = q % NQ, qy = (q / NQ) % NQ, qz = q / (NQ * NQ);
       // FP64 Gauss point coordinates, rounded exactly as the definition
       sm.xq[wp][q][0] = __dadd_rn(m.x0[0], __dmul_rn(m.h[0], __dadd_rn((double)ex, P.g[qx])));
       sm.xq[wp][q][1] = __dadd_rn(m.x0[1], __dmul_rn(m.h[1], __dadd_rn((double)ey, P.g[qy])));
       sm.xq[wp][q][2] = __dadd_rn(m.x0[2], __dmul_rn(m.h[2], __dadd_rn((double)ez, P.g[qz])));
     }
+  }
+  if (FP64 && lane == 0) {
+    // Gauss points relative to the origin as double-float, h (e + g), per axis
+    const int eax[3] = {ex, ey, ez};
+    const float hh[3] = {P.hx_hi, P.hy_hi, P.hz_hi}, hl[3] = {P.hx_lo, P.hy_lo, P.hz_lo};
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax)
+#pragma unroll
+      for (int a = 0; a <= K; ++a) {
+        df64 t = df64((float)eax[ax]) + df64(P.g_hi[a], P.g_lo[a]);
+        df64 G = df64(hh[ax], hl[ax]) * t;
+        sm.xqf[wp][FP64 ? ax : 0][a][0] = G.hi;
+        sm.xqf[wp][FP64 ? ax : 0][a][1] = G.lo;
+      }
   }
   // element centre relative to the mesh origin, float-float
   float chx, clx, chy, cly, chz, clz;
@@ -333,7 +423,7 @@ k_qcm(MeshDev m, QcmParams P, BinDev b, const int32_t* __restrict__ bin_start,
         nb += __popc(mask);
         __syncwarp();
         if (nb >= 32) {
-          qcm_group<K, FP64>(sm, w, 32, xs64, perm);
+          qcm_group<K, FP64>(sm, w, P, 32, xs64, xs32, perm);
           int rest = nb - 32;
           float4 tb = make_float4(0.f, 0.f, 0.f, 0.f);
           int ts = 0;
@@ -352,14 +442,15 @@ k_qcm(MeshDev m, QcmParams P, BinDev b, const int32_t* __restrict__ bin_start,
       }
     }
   }
-  if (nb > 0) qcm_group<K, FP64>(sm, w, nb, xs64, perm);
+  if (nb > 0) qcm_group<K, FP64>(sm, w, P, nb, xs64, xs32, perm);
   __syncwarp();
 
   // outputs
   const int64_t o = e * Q;
   for (int q = lane; q < Q; q += 32) {
     if (FP64) {
-      if (eps64) eps64[o + q] = 1.0 - sm.acc64[wp][q] * P.inv_vr;
+      df64 a = sm.accdf[wp][q];
+      if (eps64) eps64[o + q] = 1.0 - ((double)a.hi + (double)a.lo) * P.inv_vr;
     } else {
       float v = 1.0f - (sm.acc[wp][q] + sm.cmp[wp][q]) * P.inv_vr32;
       if (eps32) eps32[o + q] = v;
@@ -400,7 +491,15 @@ cudaError_t launch_qcm(const MeshDev& m, const Tables& t, const BinDev& b, int p
     P.qrel[q][1] = (float)(m.h[1] * (t.g[qy] - 0.5));
     P.qrel[q][2] = (float)(m.h[2] * (t.g[qz] - 0.5));
   }
-  for (int a = 0; a < 4; ++a) P.g[a] = t.g[a];
+  split_ff(R, &P.R_hi, &P.R_lo);
+  split_ff(4.0 / 3.0 * kPi, &P.c43_hi, &P.c43_lo);
+  split_ff(kPi / 12.0, &P.c12_hi, &P.c12_lo);
+  for (int a = 0; a < 4; ++a) {
+    P.g[a] = t.g[a];
+    split_ff(t.g[a], &P.g_hi[a], &P.g_lo[a]);
+    for (int ax = 0; ax < 3; ++ax)
+      P.g1[ax][a] = a < nq ? (float)(m.h[ax] * (t.g[a] - 0.5)) : 0.f;
+  }
   // band of the FP32 predicate: above the worst FP32 error of the squared
   // distance, about 2^-22 * 10 * (D / R)^2 relative, with D the largest
   // coordinate offset of a kept candidate (half diagonal + cutoff + bin)
