@@ -168,8 +168,9 @@ def run_reference(args):
 
 def _element_candidates(w):
     """(element, particle) pairs whose particle centre lies within R + r of the
-    element box: the candidates of element-level culling; times the Gauss
-    points per element, the (point, particle) tests the QCM has to make."""
+    box spanned by the element's Gauss points: the candidates of element-level
+    culling; times the Gauss points per element, the (point, particle) tests
+    the QCM has to make."""
     x = np.asarray(w["x"])
     r = np.asarray(w["r"])
     o = np.asarray(w["origin"], dtype=np.float64)
@@ -178,6 +179,8 @@ def _element_candidates(w):
     R = w["params"].get("qcm_radius", 0.0) or (3.0 * np.prod(h) / (4.0 * np.pi)) ** (1.0 / 3.0)
     cut = R + r
     m = int(np.ceil((R + r.max()) / h.min()))
+    g = np.polynomial.legendre.leggauss(w["k"] + 1)[0]
+    half = h * (0.5 * (g.max() + 1.0) - 0.5)   # Gauss box half extent
     base = np.clip(np.floor((x - o) / h).astype(np.int64), 0, ne - 1)
     total = 0
     rng = range(-m, m + 1)
@@ -187,7 +190,7 @@ def _element_candidates(w):
                 e = base + np.array([dx, dy, dz])
                 ok = np.all((e >= 0) & (e < ne), axis=1)
                 c = o + (e + 0.5) * h
-                gap = np.maximum(np.abs(x - c) - 0.5 * h, 0.0)
+                gap = np.maximum(np.abs(x - c) - half, 0.0)
                 total += int(np.count_nonzero(ok & (np.sum(gap * gap, axis=1) < cut * cut)))
     return float(total)
 

@@ -312,36 +312,72 @@ k_adj_forces(MeshDev m, Tables tb, ForceParams fp, int64_t n, const double* __re
 }
 
 // g_q = w_q |J_e| lambda_h(x_q) for every Gauss point: the transpose of the
-// right-hand side's quadrature.  One thread per (element, Gauss point).
+// right-hand side's quadrature, sum-factorised (three contractions of
+// (k+1)^4 per element instead of (k+1)^6).  One thread per element.
 template <int K>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128)
 k_adj_interp_q(MeshDev m, Tables tb, const double* __restrict__ lam, double* __restrict__ gq) {
-  constexpr int NQ = K + 1, Q = NQ * NQ * NQ;
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= m.E * Q) return;
-  int64_t e = t / Q;
-  int q = (int)(t - e * Q);
-  int qx = q % NQ, qy = (q / NQ) % NQ, qz = q / (NQ * NQ);
+  constexpr int N = K + 1, Q = N * N * N;
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m.E) return;
   int ex = (int)(e % m.ne[0]), ey = (int)((e / m.ne[0]) % m.ne[1]),
       ez = (int)(e / ((int64_t)m.ne[0] * m.ne[1]));
   int64_t nx = m.nn[0], nxy = (int64_t)m.nn[0] * m.nn[1];
   int64_t base = (int64_t)ex * K + nx * ((int64_t)ey * K) + nxy * ((int64_t)ez * K);
-  double s = 0.0;
+  double u[N][N][N], v[N][N][N];
 #pragma unroll
-  for (int c = 0; c <= K; ++c)
+  for (int c = 0; c < N; ++c)
 #pragma unroll
-    for (int b = 0; b <= K; ++b) {
-      double wyz = tb.Bw[b][qy] * tb.Bw[c][qz];
+    for (int b = 0; b < N; ++b)
 #pragma unroll
-      for (int a = 0; a <= K; ++a)
-        s += tb.Bw[a][qx] * wyz * __ldg(lam + base + a + nx * b + nxy * c);
-    }
-  gq[t] = s * m.Ve;
+      for (int a = 0; a < N; ++a) u[c][b][a] = __ldg(lam + base + a + nx * b + nxy * c);
+  // x: v[c][b][qx] = sum_a Bw[a][qx] u[c][b][a]
+#pragma unroll
+  for (int c = 0; c < N; ++c)
+#pragma unroll
+    for (int b = 0; b < N; ++b)
+#pragma unroll
+      for (int q = 0; q < N; ++q) {
+        double t = 0.0;
+#pragma unroll
+        for (int a = 0; a < N; ++a) t += tb.Bw[a][q] * u[c][b][a];
+        v[c][b][q] = t;
+      }
+  // y: u[c][qy][qx] = sum_b Bw[b][qy] v[c][b][qx]
+#pragma unroll
+  for (int c = 0; c < N; ++c)
+#pragma unroll
+    for (int q = 0; q < N; ++q)
+#pragma unroll
+      for (int qx = 0; qx < N; ++qx) {
+        double t = 0.0;
+#pragma unroll
+        for (int b = 0; b < N; ++b) t += tb.Bw[b][q] * v[c][b][qx];
+        u[c][q][qx] = t;
+      }
+  // z: g[qz][qy][qx] = |J| sum_c Bw[c][qz] u[c][qy][qx]
+  double* g = gq + e * Q;
+#pragma unroll
+  for (int q = 0; q < N; ++q)
+#pragma unroll
+    for (int qy = 0; qy < N; ++qy)
+#pragma unroll
+      for (int qx = 0; qx < N; ++qx) {
+        double t = 0.0;
+#pragma unroll
+        for (int c = 0; c < N; ++c) t += tb.Bw[c][q] * u[c][qy][qx];
+        g[qx + N * (qy + N * q)] = t * m.Ve;
+      }
 }
 
 // Per particle: sum over the Gauss points q within R + r_i of
-// g_q (pi a^2 / V_R) (x_i - x_q) / d, added to dJ/dx_i.
-template <int K>
+// g_q (pi a^2 / V_R) (x_i - x_q) / d, added to dJ/dx_i.  The distance to
+// every Gauss point in reach is first tested in FP32 (positions relative to
+// the first element in reach, per-axis squares, a margin of 1e-4 on the
+// squared cutoff); only the pairs that pass are evaluated, in T, from FP64
+// differences.  The derivative vanishes at the cutoff, so the margin only
+// adds terms that are zero or nearly so.
+template <int K, typename T>
 __global__ void __launch_bounds__(128)
 k_adj_qcm(MeshDev m, Tables tb, double R, int64_t n, const double* __restrict__ x,
           const double* __restrict__ r, const double* __restrict__ gq, double* __restrict__ dJdx) {
@@ -355,46 +391,66 @@ k_adj_qcm(MeshDev m, Tables tb, double R, int64_t n, const double* __restrict__ 
   const double ri = r[i];
   const double cut = R + ri, cut2 = cut * cut;
   const double dm = R - ri, dm2 = dm * dm;
-  const double coef = kPi / (4.0 / 3.0 * kPi * R * R * R);
-  const double R2r2 = R * R - ri * ri;
+  const float pre2 = (float)(cut2 * (1.0 + 1e-4));
+  const T coef = (T)(kPi / (4.0 / 3.0 * kPi * R * R * R));
+  const T R2r2 = (T)(R * R - ri * ri), RR4 = (T)(4.0 * R * R);
   int lo[3], hi[3];
+  float rel0[3], hf[3], gf[3][NQ];
   for (int a = 0; a < 3; ++a) {
     double tl = (p[a] - cut - m.x0[a]) / m.h[a], th = (p[a] + cut - m.x0[a]) / m.h[a];
     lo[a] = (int)floor(tl);
     hi[a] = (int)floor(th);
     lo[a] = lo[a] < 0 ? 0 : (lo[a] > m.ne[a] - 1 ? m.ne[a] - 1 : lo[a]);
     hi[a] = hi[a] < 0 ? 0 : (hi[a] > m.ne[a] - 1 ? m.ne[a] - 1 : hi[a]);
+    // particle relative to the first element in reach (FP32 for the filter)
+    rel0[a] = (float)(p[a] - (m.x0[a] + m.h[a] * (double)lo[a]));
+    hf[a] = (float)m.h[a];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) gf[a][q] = (float)(m.h[a] * tb.g[q]);
   }
-  double g0 = 0, g1 = 0, g2 = 0;
-  for (int ez = lo[2]; ez <= hi[2]; ++ez)
-    for (int ey = lo[1]; ey <= hi[1]; ++ey)
+  T g0 = 0, g1 = 0, g2 = 0;
+  for (int ez = lo[2]; ez <= hi[2]; ++ez) {
+    const float rz = rel0[2] - hf[2] * (float)(ez - lo[2]);
+    for (int ey = lo[1]; ey <= hi[1]; ++ey) {
+      const float ry = rel0[1] - hf[1] * (float)(ey - lo[1]);
       for (int ex = lo[0]; ex <= hi[0]; ++ex) {
-        int64_t e = ex + (int64_t)m.ne[0] * (ey + (int64_t)m.ne[1] * ez);
-        const double* g = gq + e * Q;
+        const float rx = rel0[0] - hf[0] * (float)(ex - lo[0]);
+        const int64_t e = ex + (int64_t)m.ne[0] * (ey + (int64_t)m.ne[1] * ez);
+        float sx[NQ], sy[NQ], sz[NQ];
 #pragma unroll
-        for (int qz = 0; qz < NQ; ++qz) {
-          double dz = p[2] - (m.x0[2] + m.h[2] * ((double)ez + tb.g[qz]));
+        for (int q = 0; q < NQ; ++q) {
+          float u = rx - gf[0][q], v = ry - gf[1][q], w = rz - gf[2][q];
+          sx[q] = u * u;
+          sy[q] = v * v;
+          sz[q] = w * w;
+        }
 #pragma unroll
-          for (int qy = 0; qy < NQ; ++qy) {
-            double dy = p[1] - (m.x0[1] + m.h[1] * ((double)ey + tb.g[qy]));
+        for (int qz = 0; qz < NQ; ++qz)
+#pragma unroll
+          for (int qy = 0; qy < NQ; ++qy)
 #pragma unroll
             for (int qx = 0; qx < NQ; ++qx) {
+              if (sx[qx] + sy[qy] + sz[qz] >= pre2) continue;
               double dx = p[0] - (m.x0[0] + m.h[0] * ((double)ex + tb.g[qx]));
+              double dy = p[1] - (m.x0[1] + m.h[1] * ((double)ey + tb.g[qy]));
+              double dz = p[2] - (m.x0[2] + m.h[2] * ((double)ez + tb.g[qz]));
               double d2 = dx * dx + dy * dy + dz * dz;
               if (d2 >= cut2 || d2 <= dm2) continue;  // no contact, or full containment
-              double w = d2 + R2r2;
-              double a2 = (4.0 * d2 * R * R - w * w) / (4.0 * d2);
-              double s = __ldg(g + qx + NQ * (qy + NQ * qz)) * coef * a2 * rsqrt(d2);
-              g0 += s * dx;
-              g1 += s * dy;
-              g2 += s * dz;
+              T d2t = (T)d2;
+              T w = d2t + R2r2;
+              T a2 = (RR4 * d2t - w * w) / ((T)4 * d2t);
+              T s = (T)__ldg(gq + e * Q + qx + NQ * (qy + NQ * qz)) * coef * a2 /
+                    t_sqrt<T>(d2t);
+              g0 += s * (T)dx;
+              g1 += s * (T)dy;
+              g2 += s * (T)dz;
             }
-          }
-        }
       }
-  dJdx[3 * i] += g0;
-  dJdx[3 * i + 1] += g1;
-  dJdx[3 * i + 2] += g2;
+    }
+  }
+  dJdx[3 * i] += (double)g0;
+  dJdx[3 * i + 1] += (double)g1;
+  dJdx[3 * i + 2] += (double)g2;
 }
 
 }  // namespace
@@ -442,24 +498,28 @@ cudaError_t launch_adj_forces(const MeshDev& m, const Tables& t, int precision, 
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_adj_qcm(const MeshDev& m, const Tables& t, double R, const double* lam,
-                           double* gq, int64_t n, const double* x, const double* r,
-                           double* dJdx, cudaStream_t s) {
-  const int64_t nq = m.E * m.Q;
-  const unsigned gb = (unsigned)((nq + 255) / 256);
+cudaError_t launch_adj_qcm(const MeshDev& m, const Tables& t, int precision, double R,
+                           const double* lam, double* gq, int64_t n, const double* x,
+                           const double* r, double* dJdx, cudaStream_t s) {
+  const unsigned eb = (unsigned)((m.E + 127) / 128);
   const unsigned pb = (unsigned)((n + 127) / 128);
-  if (m.k == 1) {
-    k_adj_interp_q<1><<<gb, 256, 0, s>>>(m, t, lam, gq);
-    if (n > 0) k_adj_qcm<1><<<pb, 128, 0, s>>>(m, t, R, n, x, r, gq, dJdx);
-  } else if (m.k == 2) {
-    k_adj_interp_q<2><<<gb, 256, 0, s>>>(m, t, lam, gq);
-    if (n > 0) k_adj_qcm<2><<<pb, 128, 0, s>>>(m, t, R, n, x, r, gq, dJdx);
-  } else {
-    k_adj_interp_q<3><<<gb, 256, 0, s>>>(m, t, lam, gq);
-    if (n > 0) k_adj_qcm<3><<<pb, 128, 0, s>>>(m, t, R, n, x, r, gq, dJdx);
+#define CFDEM_ADJQ(KK)                                                                \
+  if (m.k == KK) {                                                                    \
+    k_adj_interp_q<KK><<<eb, 128, 0, s>>>(m, t, lam, gq);                             \
+    if (n > 0) {                                                                      \
+      if (precision == 0)                                                             \
+        k_adj_qcm<KK, double><<<pb, 128, 0, s>>>(m, t, R, n, x, r, gq, dJdx);         \
+      else                                                                            \
+        k_adj_qcm<KK, float><<<pb, 128, 0, s>>>(m, t, R, n, x, r, gq, dJdx);          \
+    }                                                                                 \
+    count_launches(n > 0 ? 2 : 1);                                                    \
+    return cudaGetLastError();                                                        \
   }
-  count_launches(n > 0 ? 2 : 1);
-  return cudaGetLastError();
+  CFDEM_ADJQ(1)
+  CFDEM_ADJQ(2)
+  CFDEM_ADJQ(3)
+#undef CFDEM_ADJQ
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace cfdem

@@ -763,7 +763,8 @@ cfdem_status cfdem_adjoint(cfdem_t c, int64_t n, const double* x, const double* 
     CK(cudaMemsetAsync(c->adj_lam, 0, sizeof(double) * m.n_nodes, c->stream), "adjoint");
     s = solve(c, c->adj_geps, c->adj_lam, "adjoint solve");
     if (s != CFDEM_OK) return s;
-    CK(launch_adj_qcm(m, c->tab, c->R, c->adj_lam, c->adj_gq, n, x, r, dJ_dx, c->stream),
+    CK(launch_adj_qcm(m, c->tab, c->prm.precision, c->R, c->adj_lam, c->adj_gq, n, x, r,
+                      dJ_dx, c->stream),
        "adjoint void fraction");
   }
   return CFDEM_OK;

@@ -150,9 +150,9 @@ cudaError_t launch_adj_forces(const MeshDev& m, const Tables& t, int precision, 
                               const double* eps_nodal, const double* gf, const double* gfd,
                               double* dJdx, double* dJdu, double* geps, DevStatus* st,
                               cudaStream_t s);
-cudaError_t launch_adj_qcm(const MeshDev& m, const Tables& t, double R, const double* lam,
-                           double* gq, int64_t n, const double* x, const double* r,
-                           double* dJdx, cudaStream_t s);
+cudaError_t launch_adj_qcm(const MeshDev& m, const Tables& t, int precision, double R,
+                           const double* lam, double* gq, int64_t n, const double* x,
+                           const double* r, double* dJdx, cudaStream_t s);
 struct FdmPlan;
 cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4], FdmPlan** out,
                        const char** why);

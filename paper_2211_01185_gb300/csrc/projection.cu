@@ -217,11 +217,42 @@ struct Coefs {
   T cM, cKx, cKy, cKz;
 };
 
+// Sum of products b_k x_k for the banded passes of the tile operator.  In
+// FP32/FP64 a plain FMA chain; in double-float a compensated sum: the high
+// products are added with Knuth's two-sum and every error term (the product
+// errors, the cross products b.hi x.lo + b.lo x.hi, the two-sum errors) is
+// gathered in one FP32 correction, renormalised once at the end -- about 10
+// FP32 operations per term instead of a full double-float multiply and add.
+template <typename T>
+struct Acc {
+  T v;
+  __device__ __forceinline__ void zero() { v = (T)0; }
+  __device__ __forceinline__ void add(T b, T x) { v += b * x; }
+  __device__ __forceinline__ T get() const { return v; }
+};
+
 // Double-float ("df64") numbers: an unevaluated sum hi + lo of two floats
 // carrying about 48 significant bits, with error-free two-sum and FMA-based
 // two-product (Dekker 1971; Knuth, TAOCP vol. 2).  They give the mixed path
 // residuals accurate to ~1e-14 on the FP32 pipes, which on this part have 61
 // times the FP64 throughput.
+template <>
+struct Acc<df64> {
+  float s, c;
+  __device__ __forceinline__ void zero() { s = c = 0.f; }
+  __device__ __forceinline__ void add(df64 b, df64 x) {
+    float p = b.hi * x.hi;
+    float e = fmaf(b.hi, x.hi, -p);
+    e = fmaf(b.hi, x.lo, e);
+    e = fmaf(b.lo, x.hi, e);
+    float t = s + p;
+    float bb = t - s;
+    c += ((s - (t - bb)) + (p - bb)) + e;
+    s = t;
+  }
+  __device__ __forceinline__ df64 get() const { return df_renorm(s, c); }
+};
+
 // --- load and epilogue policies of the tile operator -----------------------
 // Plain: x_eff = x[g]
 template <typename T>
@@ -359,35 +390,41 @@ __device__ __forceinline__ double apply_tile(const MeshDev& m, const T* __restri
   for (int t = threadIdx.x; t < TL::NT; t += blockDim.x) {
     int lx = t % TL::XW, ly = (t / TL::XW) % TL::YW, lz = t / (TL::XW * TL::YW);
     int gz = z0 + lz;
-    T a1 = 0, a2 = 0;
+    Acc<T> a1, a2;
+    a1.zero();
+    a2.zero();
     if (gz < nz) {
 #pragma unroll
       for (int w = 0; w < W; ++w) {
         T xv = X[(lz + w) * TL::YW * TL::XW + ly * TL::XW + lx];
-        a1 += bMz[(size_t)gz * W + w] * xv;
-        a2 += bKz[(size_t)gz * W + w] * xv;
+        a1.add(bMz[(size_t)gz * W + w], xv);
+        a2.add(bKz[(size_t)gz * W + w], xv);
       }
     }
-    T1[t] = a1;
-    T2[t] = a2;
+    T1[t] = a1.get();
+    T2[t] = a2.get();
   }
   __syncthreads();
   // y pass
   for (int t = threadIdx.x; t < TL::NU; t += blockDim.x) {
     int lx = t % TL::XW, ly = (t / TL::XW) % TY, lz = t / (TL::XW * TY);
     int gy = y0 + ly;
-    T s1 = 0, s2 = 0, s3 = 0;
+    Acc<T> a1, a2, a3;
+    a1.zero();
+    a2.zero();
+    a3.zero();
     if (gy < ny) {
 #pragma unroll
       for (int w = 0; w < W; ++w) {
         int src = lz * TL::YW * TL::XW + (ly + w) * TL::XW + lx;
         T mv = bMy[(size_t)gy * W + w], kv = bKy[(size_t)gy * W + w];
         T t1 = T1[src];
-        s1 += mv * t1;
-        s2 += kv * t1;
-        s3 += mv * T2[src];
+        a1.add(mv, t1);
+        a2.add(kv, t1);
+        a3.add(mv, T2[src]);
       }
     }
+    T s1 = a1.get(), s2 = a2.get(), s3 = a3.get();
     U[t] = cf.cM * s1 + cf.cKy * s2 + cf.cKz * s3;
     V[t] = cf.cKx * s1;
   }
@@ -399,12 +436,15 @@ __device__ __forceinline__ double apply_tile(const MeshDev& m, const T* __restri
     int lx = t % TX, ly = (t / TX) % TY, lz = t / (TX * TY);
     int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
     if (gx >= nx || gy >= ny || gz >= nz) continue;
-    T acc = 0;
+    Acc<T> ax;
+    ax.zero();
 #pragma unroll
     for (int w = 0; w < W; ++w) {
       int src = lz * TY * TL::XW + ly * TL::XW + lx + w;
-      acc += bMx[(size_t)gx * W + w] * U[src] + bKx[(size_t)gx * W + w] * V[src];
+      ax.add(bMx[(size_t)gx * W + w], U[src]);
+      ax.add(bKx[(size_t)gx * W + w], V[src]);
     }
+    T acc = ax.get();
     T xe = X[(lz + H) * TL::YW * TL::XW + (ly + H) * TL::XW + lx + H];
     dot += ep(gx + (int64_t)nx * gy + sxy * gz, acc, xe);
   }

@@ -45,6 +45,7 @@ struct QcmParams {
   float inv_be[3];     // 1 / bin edge
   float qrel[64][3];   // Gauss point minus element centre, FP32
   float g1[3][4];      // per axis: 1D Gauss point minus element centre, FP32
+  float gbox[3];       // half extent of the Gauss points' box per axis (a little above)
   double g[4];         // Gauss points on [0,1]
   // double-float constants of the FP64 path's lens volumes
   float g_hi[4], g_lo[4];  // Gauss points on [0,1]
@@ -254,45 +255,54 @@ __device__ __forceinline__ void qcm_group(QcmSmem<K, FP64>& sm, const QcmWarp& w
     sy[a] = dy * dy;
   }
   int qn = 0;
-  for (int cz = 0; cz <= K; ++cz) {
-    // the z offset of Gauss layer cz, from shared memory (a runtime index into
-    // the kernel parameters would move them to local memory)
-    float dz = my.z - sm.qrel[cz * (K + 1) * (K + 1)].z;
-    float sz = dz * dz;
+  // layers cz = 0..K of Gauss points, then one more pass that only drains
+  for (int cz = 0; cz <= K + 1; ++cz) {
+    if (cz <= K) {
+      // the z offset of Gauss layer cz, from shared memory (a runtime index into
+      // the kernel parameters would move them to local memory)
+      float dz = my.z - sm.qrel[cz * (K + 1) * (K + 1)].z;
+      float sz = dz * dz;
 #pragma unroll
-    for (int b = 0; b <= K; ++b) {
-      float syz = sy[b] + sz;
+      for (int b = 0; b <= K; ++b) {
+        float syz = sy[b] + sz;
 #pragma unroll
-      for (int a = 0; a <= K; ++a) {
-        const int q = a + (K + 1) * (b + (K + 1) * cz);
-        float d2 = sx[a] + syz;
-        bool hit;
-        if (FP64) {
-          hit = valid && d2 < c2_in;
-          if (valid && d2 >= c2_in && d2 <= c2_out) {  // inside the band: exact FP64 predicate
-            P4 pj = sm.g64[wp][lane];
-            double ddx = __dsub_rn(pj.x, sm.xq[wp][q][0]);
-            double ddy = __dsub_rn(pj.y, sm.xq[wp][q][1]);
-            double ddz = __dsub_rn(pj.z, sm.xq[wp][q][2]);
-            double dd2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)),
-                                   __dmul_rn(ddz, ddz));
-            double cc = __dadd_rn(w.R, pj.w);
-            hit = dd2 < __dmul_rn(cc, cc);
+        for (int a = 0; a <= K; ++a) {
+          const int q = a + (K + 1) * (b + (K + 1) * cz);
+          float d2 = sx[a] + syz;
+          bool hit;
+          if (FP64) {
+            hit = valid && d2 < c2_in;
+            if (valid && d2 >= c2_in && d2 <= c2_out) {  // inside the band: exact FP64 predicate
+              P4 pj = sm.g64[wp][lane];
+              double ddx = __dsub_rn(pj.x, sm.xq[wp][q][0]);
+              double ddy = __dsub_rn(pj.y, sm.xq[wp][q][1]);
+              double ddz = __dsub_rn(pj.z, sm.xq[wp][q][2]);
+              double dd2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)),
+                                     __dmul_rn(ddz, ddz));
+              double cc = __dadd_rn(w.R, pj.w);
+              hit = dd2 < __dmul_rn(cc, cc);
+            }
+          } else {
+            hit = valid && d2 < c2;
           }
-        } else {
-          hit = valid && d2 < c2;
+          unsigned mask = __ballot_sync(FULL, hit);
+          if (hit) sm.queue[wp][qn + __popc(mask & w.lt_mask)] = (lane << 6) | q;
+          qn += __popc(mask);
         }
-        unsigned mask = __ballot_sync(FULL, hit);
-        if (hit) sm.queue[wp][qn + __popc(mask & w.lt_mask)] = (lane << 6) | q;
-        qn += __popc(mask);
       }
     }
-    // evaluate the full batches of 32 hits queued by this layer (one copy of
-    // the flush, outside the unrolled tests), keep the rest at the front
-    if (qn >= 32) {
+    // evaluate the full batches of 32 hits queued so far (after the last
+    // layer: all of them) -- the only call of the flush -- and keep the rest
+    // at the front of the queue
+    const bool last = cz == K + 1;
+    if (qn >= 32 || (last && qn > 0)) {
       __syncwarp();
       int base = 0;
-      for (; qn - base >= 32; base += 32) qcm_flush<K, FP64>(sm, w, base, 32, perm);
+      while (qn - base >= 32 || (last && qn > base)) {
+        const int c = qn - base < 32 ? qn - base : 32;
+        qcm_flush<K, FP64>(sm, w, base, c, perm);
+        base += c;
+      }
       int rest = qn - base;
       int tmp = lane < rest ? sm.queue[wp][base + lane] : 0;
       __syncwarp();
@@ -301,7 +311,6 @@ __device__ __forceinline__ void qcm_group(QcmSmem<K, FP64>& sm, const QcmWarp& w
     }
   }
   __syncwarp();
-  if (qn > 0) qcm_flush<K, FP64>(sm, w, 0, qn, perm);
 }
 
 template <int K, bool FP64>
@@ -371,7 +380,9 @@ k_qcm(MeshDev m, QcmParams P, BinDev b, const int32_t* __restrict__ bin_start,
   chx = ff_two_prod_sum((float)ex + 0.5f, P.hx_hi, P.hx_lo, &clx);
   chy = ff_two_prod_sum((float)ey + 0.5f, P.hy_hi, P.hy_lo, &cly);
   chz = ff_two_prod_sum((float)ez + 0.5f, P.hz_hi, P.hz_lo, &clz);
-  const float hhx = 0.5f * P.hx, hhy = 0.5f * P.hy, hhz = 0.5f * P.hz;
+  // half extents of the box spanned by the element's Gauss points (every
+  // neighbour of a Gauss point lies within R + r of it)
+  const float hhx = P.gbox[0], hhy = P.gbox[1], hhz = P.gbox[2];
   const double rmax = __longlong_as_double((long long)st->rmax_bits);
   const float cut = (float)(P.R + rmax) * (1.0f + 1e-5f);
   // bin range per axis (conservative)
@@ -392,57 +403,75 @@ k_qcm(MeshDev m, QcmParams P, BinDev b, const int32_t* __restrict__ bin_start,
   }
   __syncwarp();
 
+  // Stream the candidates bin row by bin row into the buffer; test each full
+  // group of 32 (and the last, partial one).  Written as one loop so that the
+  // group -- and the flush inside it -- has a single call site in the code.
   int nb = 0;  // buffered culled candidates (warp-uniform)
-  for (int bz = bz0; bz <= bz1; ++bz) {
-    for (int by = by0; by <= by1; ++by) {
-      int64_t row = (int64_t)b.nb[0] * (by + (int64_t)b.nb[1] * bz);
-      int s0 = bin_start[row + bx0], s1 = bin_start[row + bx1 + 1];
-      for (int sb = s0; sb < s1; sb += 32) {
-        int s = sb + lane;
-        bool keep = false;
-        float4 rel = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (s < s1) {
-          const float4* p = reinterpret_cast<const float4*>(xs32) + 2 * (int64_t)s;
-          float4 hi = p[0], lo = p[1];
-          rel.x = (hi.x - chx) + (lo.x - clx);
-          rel.y = (hi.y - chy) + (lo.y - cly);
-          rel.z = (hi.z - chz) + (lo.z - clz);
-          rel.w = hi.w;
-          float ox = fmaxf(fabsf(rel.x) - hhx, 0.f);
-          float oy = fmaxf(fabsf(rel.y) - hhy, 0.f);
-          float oz = fmaxf(fabsf(rel.z) - hhz, 0.f);
-          float c = (w.R32 + rel.w) * w.band;
-          keep = ox * ox + oy * oy + oz * oz < c * c * w.band;
-        }
-        unsigned mask = __ballot_sync(FULL, keep);
-        if (keep) {
-          int pos = nb + __popc(mask & w.lt_mask);
-          sm.buf[wp][pos] = rel;
-          sm.bslot[wp][pos] = s;
-        }
-        nb += __popc(mask);
-        __syncwarp();
-        if (nb >= 32) {
-          qcm_group<K, FP64>(sm, w, P, 32, xs64, xs32, perm);
-          int rest = nb - 32;
-          float4 tb = make_float4(0.f, 0.f, 0.f, 0.f);
-          int ts = 0;
-          if (lane < rest) {
-            tb = sm.buf[wp][32 + lane];
-            ts = sm.bslot[wp][32 + lane];
-          }
-          __syncwarp();
-          if (lane < rest) {
-            sm.buf[wp][lane] = tb;
-            sm.bslot[wp][lane] = ts;
-          }
-          __syncwarp();
-          nb = rest;
-        }
-      }
-    }
+  const int nrx = by1 - by0 + 1, nrows = nrx * (bz1 - bz0 + 1);
+  int rowi = 0, sb = 0, s1 = 0;
+  bool more = nrows > 0;
+  if (more) {
+    int64_t row = (int64_t)b.nb[0] * (by0 + (int64_t)b.nb[1] * bz0);
+    sb = bin_start[row + bx0];
+    s1 = bin_start[row + bx1 + 1];
   }
-  if (nb > 0) qcm_group<K, FP64>(sm, w, P, nb, xs64, xs32, perm);
+  for (;;) {
+    while (more && nb < 32) {
+      if (sb >= s1) {  // next bin row
+        if (++rowi >= nrows) {
+          more = false;
+          break;
+        }
+        int by = by0 + rowi % nrx, bz = bz0 + rowi / nrx;
+        int64_t row = (int64_t)b.nb[0] * (by + (int64_t)b.nb[1] * bz);
+        sb = bin_start[row + bx0];
+        s1 = bin_start[row + bx1 + 1];
+        continue;
+      }
+      int s = sb + lane;
+      bool keep = false;
+      float4 rel = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (s < s1) {
+        const float4* p = reinterpret_cast<const float4*>(xs32) + 2 * (int64_t)s;
+        float4 hi = p[0], lo = p[1];
+        rel.x = (hi.x - chx) + (lo.x - clx);
+        rel.y = (hi.y - chy) + (lo.y - cly);
+        rel.z = (hi.z - chz) + (lo.z - clz);
+        rel.w = hi.w;
+        float ox = fmaxf(fabsf(rel.x) - hhx, 0.f);
+        float oy = fmaxf(fabsf(rel.y) - hhy, 0.f);
+        float oz = fmaxf(fabsf(rel.z) - hhz, 0.f);
+        float c = (w.R32 + rel.w) * w.band;
+        keep = ox * ox + oy * oy + oz * oz < c * c * w.band;
+      }
+      unsigned mask = __ballot_sync(FULL, keep);
+      if (keep) {
+        int pos = nb + __popc(mask & w.lt_mask);
+        sm.buf[wp][pos] = rel;
+        sm.bslot[wp][pos] = s;
+      }
+      nb += __popc(mask);
+      sb += 32;
+    }
+    if (nb == 0) break;
+    __syncwarp();
+    const int cnt = nb < 32 ? nb : 32;
+    qcm_group<K, FP64>(sm, w, P, cnt, xs64, xs32, perm);
+    int rest = nb - cnt;
+    float4 tb = make_float4(0.f, 0.f, 0.f, 0.f);
+    int ts = 0;
+    if (lane < rest) {
+      tb = sm.buf[wp][32 + lane];
+      ts = sm.bslot[wp][32 + lane];
+    }
+    __syncwarp();
+    if (lane < rest) {
+      sm.buf[wp][lane] = tb;
+      sm.bslot[wp][lane] = ts;
+    }
+    __syncwarp();
+    nb = rest;
+  }
   __syncwarp();
 
   // outputs
@@ -491,6 +520,8 @@ cudaError_t launch_qcm(const MeshDev& m, const Tables& t, const BinDev& b, int p
     P.qrel[q][1] = (float)(m.h[1] * (t.g[qy] - 0.5));
     P.qrel[q][2] = (float)(m.h[2] * (t.g[qz] - 0.5));
   }
+  for (int ax = 0; ax < 3; ++ax)  // rounded up: culling stays conservative
+    P.gbox[ax] = (float)(m.h[ax] * (t.g[nq - 1] - 0.5) * (1.0 + 1e-6));
   split_ff(R, &P.R_hi, &P.R_lo);
   split_ff(4.0 / 3.0 * kPi, &P.c43_hi, &P.c43_lo);
   split_ff(kPi / 12.0, &P.c12_hi, &P.c12_lo);

@@ -157,3 +157,49 @@ def test_replayed_fp64_bed_matches_oracle():
     assert rel_err(host(t["f"]), ref["f"]) <= 1e-10
     assert rel_err(host(t["fd"]), ref["f_drag"]) <= 1e-10
     assert rel_err(host(t["Fe"]), ref["F_e"]) <= 1e-10
+
+
+def test_replayed_loop_stops_at_the_iteration_cap():
+    """A bed whose CG is capped at 3 iterations: the device-driven loop of the
+    replayed graph must end there and the batch must report the bed as not
+    converged, with the other bed unaffected."""
+    beds = _beds()[:2]
+    beds[1]["params"] = dict(beds[1]["params"], precision=0, cg_precond=0, cg_maxit=3)
+    bufs = [_buffers(b) for b in beds]
+    bh = _make_batch(beds)
+    try:
+        for replay in (0, 1, 1):
+            for t in bufs:
+                t["eps"].zero_()
+            assert cf.cfdem_batch_coupling_step(bh, [_io(t) for t in bufs]) == cf.OK
+            st, bad = cf.cfdem_batch_synchronize(bh)
+            assert cf.cfdem_batch_last_replayed(bh) == replay
+            assert st == cf.NOT_CONVERGED and bad == 1
+            s1 = cf.cfdem_get_stats(cf.cfdem_batch_bed(bh, 1))
+            assert s1.converged == 0 and s1.cg_iterations == 3
+            s0 = cf.cfdem_get_stats(cf.cfdem_batch_bed(bh, 0))
+            assert s0.converged == 1
+    finally:
+        cf.cfdem_batch_destroy(bh)
+
+
+def test_empty_bed_in_a_batch():
+    """A bed with no particles steps (eps = 1, no forces) inside a replayed graph."""
+    import torch
+    beds = _beds()[:2]
+    b = beds[1]
+    b["x"] = b["x"][:0]
+    b["r"] = b["r"][:0]
+    b["u_p"] = b["u_p"][:0]
+    bufs = [_buffers(bb) for bb in beds]
+    bh = _make_batch(beds)
+    try:
+        assert [_step(bh, bufs) for _ in range(2)] == [0, 1]
+        eps = host(bufs[1]["eps"])
+        # mixed path: the right-hand side is summed in FP32 (the mixed bound
+        # is 1e-5); FP64 path: to the CG tolerance
+        tol = 1e-6 if b["params"].get("precision", 0) == 1 else 1e-10
+        assert np.abs(eps - 1.0).max() <= tol
+        assert torch.count_nonzero(bufs[1]["Fe"]).item() == 0
+    finally:
+        cf.cfdem_batch_destroy(bh)
