@@ -166,6 +166,19 @@ def run_reference(args):
     return 0
 
 
+def _step_bytes(n, n_nodes, E, Q, iters, ms, hbm_gbs):
+    """Algorithmic HBM bytes of one mixed coupling step and their rate: per
+    particle x, r, u_p read, element/bin/slot and the sorted copies written
+    and read back, forces and drag forces written (~180 B); the void fraction
+    at the Gauss points written and read once (4 B each in FP32); the nodal
+    right-hand side, velocity (24 B), void fraction and pressure read or
+    written once (~48 B per node); per CG iteration about ten passes over
+    double-float nodal vectors (8 B each: 80 B per node)."""
+    b = 180.0 * n + 8.0 * E * Q + 48.0 * n_nodes + 80.0 * max(iters, 1) * n_nodes
+    gbs = b / (ms * 1e-3) / 1e9
+    return {"bytes": b, "achieved_gbs": gbs, "peak_gbs": hbm_gbs, "frac": gbs / hbm_gbs}
+
+
 def _element_candidates(w):
     """(element, particle) pairs whose particle centre lies within R + r of the
     box spanned by the element's Gauss points: the candidates of element-level
@@ -533,7 +546,9 @@ def main():
     replayed = cf.cfdem_batch_last_replayed(bh)
     gst, _ = cf.cfdem_batch_synchronize(bh)
     st_g = cf.cfdem_get_stats(bed)
-    ms_g = float(np.mean([a.elapsed_time(b) for a, b in evg]))
+    ms_all_g = [a.elapsed_time(b) for a, b in evg]
+    ms_g = float(np.mean(ms_all_g))
+    ms_g_median = float(np.median(ms_all_g))
     if dist is not None:
         tt = torch.tensor([ms_g], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -590,10 +605,17 @@ def main():
     #   operator: 7 banded 1D applies x (2k+1) taps x 2 flops + 5 = flops per node
     #   QCM: per neighbour pair 8 flops (distance) + 20 flops (lens volume)
     op_flops_node = 7 * (2 * k + 1) * 2 + 5
+    # the op32 stage holds the double-float residual and the CG operator
+    # launches (the last chunk's are no-ops once the CG has converged): per
+    # launch, the productive ones only
+    it_mx = max(1, st_mx.cg_iterations)
+    calls["op32"] = it_mx + 1
+    stages_k = dict(stages)
+    stages_k["op32"] = stages["op32"] * it_mx / (it_mx + 1)   # the operator launches alone
     candidates = {
-        "op64": ("alu", op_flops_node * n_nodes, FP64_TFLOPS, "k_apply<double> (FP64 residual)"),
-        "op32": ("hbm", 16.0 * n_nodes, peaks.get("hbm_gbs", 6800.0) / 1e3,
-                 "k_cg_apply<float> (FP32 CG operator)"),
+        "op32": ("alu", op_flops_node * n_nodes, FP64_TFLOPS,
+                 "k_cg_apply_df (double-float CG operator: 48-bit arithmetic on the FP32 "
+                 "pipes, stated against the FP64 peak)"),
         "void_fraction": ("alu", None, FP32_TFLOPS, "k_qcm<2,false> (FP32 QCM)"),
         "forces": ("hbm", 180.0 * n, peaks.get("hbm_gbs", 6800.0) / 1e3, "k_forces<2,1,float>"),
     }
@@ -606,7 +628,7 @@ def main():
     tested = float(w["k"] + 1) ** 3 * _element_candidates(w)
     candidates["void_fraction"] = ("alu", 8.0 * tested + 20.0 * pairs, FP32_TFLOPS,
                                    "k_qcm<2,false> (FP32 QCM)")
-    dom = max(candidates, key=lambda s: stages[s])
+    dom = max(candidates, key=lambda s: stages_k[s])
     bound, work, peak, kname = candidates[dom]
     per_launch_ms = stages[dom] / max(calls[dom], 1.0)
     if bound == "alu":
@@ -619,7 +641,13 @@ def main():
             "unit": unit, "frac": achieved / peak_v, "traffic": None,
             "peak_source": ("measured FMA loop (profiles/alu_peaks_gb300.md)" if bound == "alu"
                             else "%s MEASURED_PEAKS.json hbm_gbs" % peak_kind),
-            "launches_per_step": calls[dom], "ms_per_launch": per_launch_ms}
+            "launches_per_step": calls[dom], "ms_per_launch": per_launch_ms,
+            "others": {c: {"kernel": candidates[c][3], "ms_per_step": stages_k[c],
+                           "frac": ((candidates[c][1] / (stages[c] / max(calls[c], 1.0) * 1e-3)
+                                     / (1e12 if candidates[c][0] == "alu" else 1e9))
+                                    / (candidates[c][2] if candidates[c][0] == "alu"
+                                       else peaks.get("hbm_gbs", 6800.0)))}
+                       for c in candidates if c != dom}}
 
     value = world * n / (ms_g * 1e-3)
     res = {"metric": METRIC, "value": value, "unit": "particle updates/s", "n_gpus": world,
@@ -632,6 +660,9 @@ def main():
                       "cg_rtol": 1e-12, "cold_start": True,
                       "launch": "one CUDA-graph replay per step (cfdem_batch_coupling_step)",
                       "parallelism": "replicas" if world > 1 else "single GPU"},
+           "ms_per_step_median": ms_g_median,
+           "step_hbm": _step_bytes(n, n_nodes, E, Q, st_g.cg_iterations, ms_g,
+                                   peaks.get("hbm_gbs", 6800.0)),
            "graph": {"replayed": replayed, "status": gst, "cg_iterations": st_g.cg_iterations,
                      "cg_relres": st_g.cg_relres, "err_vs_eager": err_graph},
            "eager": {"value": world * n / (ms_mx * 1e-3), "ms_per_step": ms_mx,

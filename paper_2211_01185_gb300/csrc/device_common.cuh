@@ -49,9 +49,19 @@ __device__ __forceinline__ int elem_axis_fast(double x, double x0, double h, dou
   return i;
 }
 
-__device__ __forceinline__ int bin_axis(double x, double x0, double be, int nb) {
-  double t = __ddiv_rn(__dsub_rn(x, x0), be);
+
+// bin index along one axis, floor((x - x0) / be) clamped to [0, nb-1], from a
+// multiplication by 1/be; the IEEE division of the definition is redone only
+// within 1e-9 of a bin face, where the two could round to different sides
+__device__ __forceinline__ int bin_axis_fast(double x, double x0, double be, double inv_be,
+                                             int nb) {
+  double t = (x - x0) * inv_be;
   double f = floor(t);
+  double fr = t - f;
+  if (fr < 1e-9 || fr > 1.0 - 1e-9) {
+    t = __ddiv_rn(__dsub_rn(x, x0), be);
+    f = floor(t);
+  }
   if (!(f >= 0.0)) return 0;
   if (f > (double)(nb - 1)) return nb - 1;
   return (int)f;

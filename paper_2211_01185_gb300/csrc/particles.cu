@@ -54,6 +54,7 @@ __global__ void k_bin_count(MeshDev m, BinDev b, int64_t n, const double* __rest
                            const double* __restrict__ r, int32_t* __restrict__ bin_of,
                            int32_t* __restrict__ slot, int32_t* __restrict__ count,
                            DevStatus* st) {
+  const double inv_be[3] = {1.0 / b.be[0], 1.0 / b.be[1], 1.0 / b.be[2]};
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -65,15 +66,15 @@ __global__ void k_bin_count(MeshDev m, BinDev b, int64_t n, const double* __rest
     if (!(in_box(p[0], m.x0[0], m.L[0]) && in_box(p[1], m.x0[1], m.L[1]) &&
           in_box(p[2], m.x0[2], m.L[2])))
       report_bad(st, i);
-    int bx = bin_axis(p[0], m.x0[0], b.be[0], b.nb[0]);
-    int by = bin_axis(p[1], m.x0[1], b.be[1], b.nb[1]);
-    int bz = bin_axis(p[2], m.x0[2], b.be[2], b.nb[2]);
+    int bx = bin_axis_fast(p[0], m.x0[0], b.be[0], inv_be[0], b.nb[0]);
+    int by = bin_axis_fast(p[1], m.x0[1], b.be[1], inv_be[1], b.nb[1]);
+    int bz = bin_axis_fast(p[2], m.x0[2], b.be[2], inv_be[2], b.nb[2]);
     id = bx + b.nb[0] * (by + b.nb[1] * bz);
     bin_of[i] = id;
     if (r) ri = r[i];
   }
   // warp-aggregated counting: one atomic per distinct bin of the warp; the
-  // slot order inside a bin is fixed afterwards by k_sort_bins
+  // slot order inside a bin is fixed afterwards by k_rank_bins
   unsigned peers = __match_any_sync(FULL, id);
   int leader = __ffs(peers) - 1;
   int rank = __popc(peers & ((1u << lane) - 1u));
@@ -81,15 +82,28 @@ __global__ void k_bin_count(MeshDev m, BinDev b, int64_t n, const double* __rest
   if (valid && lane == leader) base = atomicAdd(&count[id], __popc(peers));
   base = __shfl_sync(FULL, base, leader);
   if (valid) slot[i] = base + rank;
-  // largest radius: one atomic per warp
+  // largest radius: reduced over the warp, then the block, one atomic per
+  // block (the bits of a non-negative double order like the value)
   if (r) {
+    __shared__ unsigned long long wmax[32];
     unsigned long long bits = valid && ri >= 0.0 ? (unsigned long long)__double_as_longlong(ri) : 0ull;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       unsigned long long ob = __shfl_xor_sync(FULL, bits, o);
       bits = ob > bits ? ob : bits;
     }
-    if (lane == 0 && bits) atomicMax(&st->rmax_bits, bits);
+    const int wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) wmax[wid] = bits;
+    __syncthreads();
+    if (wid == 0) {
+      bits = lane < nw ? wmax[lane] : 0ull;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long ob = __shfl_xor_sync(FULL, bits, o);
+        bits = ob > bits ? ob : bits;
+      }
+      if (lane == 0 && bits) atomicMax(&st->rmax_bits, bits);
+    }
   }
 }
 
@@ -188,26 +202,25 @@ __global__ void k_scatter(int64_t n, const int32_t* __restrict__ bin_of,
 }
 
 // restore ascending particle id inside every bin (the atomic slots above
-// arrive in any order): insertion sort of each bin's segment
-__global__ void k_sort_bins(int64_t nbins, const int32_t* __restrict__ start,
-                            int32_t* __restrict__ perm) {
-  int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (b >= nbins) return;
+// arrive in any order): a particle's place is the number of particles of its
+// bin with a smaller index (one thread per particle; the bins are
+// small, and the work of a bin is spread over its particles)
+__global__ void k_rank_bins(int64_t n, const int32_t* __restrict__ bin_of,
+                            const int32_t* __restrict__ start,
+                            const int32_t* __restrict__ unsorted, int32_t* __restrict__ perm) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  int32_t i = unsorted[t];
+  int32_t b = bin_of[i];
   int32_t s0 = start[b], s1 = start[b + 1];
-  for (int32_t i = s0 + 1; i < s1; ++i) {
-    int32_t v = perm[i];
-    int32_t j = i - 1;
-    while (j >= s0 && perm[j] > v) {
-      perm[j + 1] = perm[j];
-      --j;
-    }
-    perm[j + 1] = v;
-  }
+  int32_t rank = 0;
+  for (int32_t j = s0; j < s1; ++j) rank += unsorted[j] < i;
+  perm[s0 + rank] = i;
 }
 
 // sorted copies: xs64[s] = (x, y, z, r); xs32[s] = float-float split of the
-// position relative to the mesh origin, hi part in [0..2], radius in [3],
-// lo part in [4..6]
+// position relative to the mesh origin and of the radius, hi parts in
+// [0..3], lo parts in [4..7]
 __global__ void k_gather_sorted(MeshDev m, int64_t n, const int32_t* __restrict__ perm,
                                 const double* __restrict__ x, const double* __restrict__ r,
                                 double* __restrict__ xs64, float* __restrict__ xs32) {
@@ -247,8 +260,11 @@ cudaError_t launch_bin(const MeshDev& m, const BinDev& b, int64_t n, const doubl
   k_scan_sums<<<1, kScanThreads, 0, s>>>(scan_tmp, ntiles);
   k_scan_final<<<ntiles, kScanThreads, 0, s>>>(bin_count, b.nbins, scan_tmp, bin_start);
   if (n > 0) {
-    k_scatter<<<gp, bs, 0, s>>>(n, bin_of, slot, bin_start, perm);
-    k_sort_bins<<<(unsigned)((b.nbins + bs - 1) / bs), bs, 0, s>>>(b.nbins, bin_start, perm);
+    // the float-float copy written last by k_gather_sorted holds the
+    // unsorted permutation in the meantime (8 floats per particle of room)
+    int32_t* unsorted = reinterpret_cast<int32_t*>(xs32);
+    k_scatter<<<gp, bs, 0, s>>>(n, bin_of, slot, bin_start, unsorted);
+    k_rank_bins<<<gp, bs, 0, s>>>(n, bin_of, bin_start, unsorted, perm);
     k_gather_sorted<<<gp, bs, 0, s>>>(m, n, perm, x, r, xs64, xs32);
   }
   count_launches(n > 0 ? 7 : 3);

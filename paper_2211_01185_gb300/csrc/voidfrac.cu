@@ -403,41 +403,66 @@ k_qcm(MeshDev m, QcmParams P, BinDev b, const int32_t* __restrict__ bin_start,
   }
   __syncwarp();
 
-  // Stream the candidates bin row by bin row into the buffer; test each full
-  // group of 32 (and the last, partial one).  Written as one loop so that the
-  // group -- and the flush inside it -- has a single call site in the code.
+  // Stream the candidates into the buffer; test each full group of 32 (and
+  // the last, partial one).  The bin rows (by, bz) in reach, each spanning
+  // bins bx0..bx1, are handled 32 at a time: every lane loads one row's
+  // bounds, a warp scan concatenates the rows, and each chunk of 32
+  // candidates spans rows (a lane finds its row by binary search over the
+  // scanned offsets).  Written as one loop so that the group -- and the flush
+  // inside it -- has a single call site in the code.
   int nb = 0;  // buffered culled candidates (warp-uniform)
   const int nrx = by1 - by0 + 1, nrows = nrx * (bz1 - bz0 + 1);
-  int rowi = 0, sb = 0, s1 = 0;
-  bool more = nrows > 0;
-  if (more) {
-    int64_t row = (int64_t)b.nb[0] * (by0 + (int64_t)b.nb[1] * bz0);
-    sb = bin_start[row + bx0];
-    s1 = bin_start[row + bx1 + 1];
-  }
+  int rb = -32, base = 0, total = 0;  // row batch, chunk start, candidates in the batch
+  int my_s0 = 0, my_excl = 0;         // this lane's row: first slot, offset in the batch
+  bool more = true;
   for (;;) {
     while (more && nb < 32) {
-      if (sb >= s1) {  // next bin row
-        if (++rowi >= nrows) {
+      if (base >= total) {  // next batch of rows
+        rb += 32;
+        if (rb >= nrows) {
           more = false;
           break;
         }
-        int by = by0 + rowi % nrx, bz = bz0 + rowi / nrx;
-        int64_t row = (int64_t)b.nb[0] * (by + (int64_t)b.nb[1] * bz);
-        sb = bin_start[row + bx0];
-        s1 = bin_start[row + bx1 + 1];
+        const int ri = rb + lane;
+        int cntr = 0;
+        my_s0 = 0;
+        if (ri < nrows) {
+          int by = by0 + ri % nrx, bz = bz0 + ri / nrx;
+          int64_t row = (int64_t)b.nb[0] * (by + (int64_t)b.nb[1] * bz);
+          my_s0 = bin_start[row + bx0];
+          cntr = bin_start[row + bx1 + 1] - my_s0;
+        }
+        int incl = cntr;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          int v = __shfl_up_sync(FULL, incl, o);
+          if (lane >= o) incl += v;
+        }
+        total = __shfl_sync(FULL, incl, 31);
+        my_excl = incl - cntr;
+        base = 0;
         continue;
       }
-      int s = sb + lane;
+      const int kk = base + lane;
+      // the row holding candidate kk: the last one whose offset is <= kk
+      int lo = 0, hi = 31;
+#pragma unroll
+      for (int st = 0; st < 5; ++st) {
+        int mid = (lo + hi + 1) >> 1;
+        int em = __shfl_sync(FULL, my_excl, mid);
+        if (em <= kk) lo = mid;
+        else hi = mid - 1;
+      }
+      const int s = __shfl_sync(FULL, my_s0, lo) + (kk - __shfl_sync(FULL, my_excl, lo));
       bool keep = false;
       float4 rel = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (s < s1) {
+      if (kk < total) {
         const float4* p = reinterpret_cast<const float4*>(xs32) + 2 * (int64_t)s;
-        float4 hi = p[0], lo = p[1];
-        rel.x = (hi.x - chx) + (lo.x - clx);
-        rel.y = (hi.y - chy) + (lo.y - cly);
-        rel.z = (hi.z - chz) + (lo.z - clz);
-        rel.w = hi.w;
+        float4 hi4 = p[0], lo4 = p[1];
+        rel.x = (hi4.x - chx) + (lo4.x - clx);
+        rel.y = (hi4.y - chy) + (lo4.y - cly);
+        rel.z = (hi4.z - chz) + (lo4.z - clz);
+        rel.w = hi4.w;
         float ox = fmaxf(fabsf(rel.x) - hhx, 0.f);
         float oy = fmaxf(fabsf(rel.y) - hhy, 0.f);
         float oz = fmaxf(fabsf(rel.z) - hhz, 0.f);
@@ -451,7 +476,7 @@ k_qcm(MeshDev m, QcmParams P, BinDev b, const int32_t* __restrict__ bin_start,
         sm.bslot[wp][pos] = s;
       }
       nb += __popc(mask);
-      sb += 32;
+      base += 32;
     }
     if (nb == 0) break;
     __syncwarp();
