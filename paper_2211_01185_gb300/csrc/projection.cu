@@ -210,6 +210,12 @@ struct Tile {
   static constexpr int NX = ZW * YW * XW;     // input with halo
   static constexpr int NT = TZ * YW * XW;     // after the z pass (each of t1, t2)
   static constexpr int NU = TZ * TY * XW;     // after the y pass (each of U, V)
+  static constexpr int NO = TZ * TY * TX;     // owned nodes (their input, for the epilogue)
+  // U, V reuse the input's space once the z pass has read it, when they fit
+  static constexpr bool UV_IN_X = 2 * NU <= NX;
+  // values in shared memory: with U, V over the input, the owned nodes' input
+  // is kept aside for the epilogue; otherwise the epilogue reads it in place
+  static constexpr int NSM = NX + 2 * NT + (UV_IN_X ? NO : 2 * NU);
 };
 
 template <typename T>
@@ -354,8 +360,9 @@ __device__ __forceinline__ double apply_tile(const MeshDev& m, const T* __restri
   T* X = sm;                 // [ZW][YW][XW]
   T* T1 = sm + TL::NX;       // [TZ][YW][XW]
   T* T2 = T1 + TL::NT;
-  T* U = T2 + TL::NT;        // [TZ][TY][XW]
+  T* U = TL::UV_IN_X ? X : T2 + TL::NT;   // [TZ][TY][XW], over X once the z pass is done
   T* V = U + TL::NU;
+  T* XE = T2 + TL::NT;       // [TZ][TY][TX] input at the owned nodes (when U, V are over X)
   const T* bMx = bands;
   const T* bKx = bMx + (size_t)nx * W;
   const T* bMy = bKx + (size_t)nx * W;
@@ -403,6 +410,8 @@ __device__ __forceinline__ double apply_tile(const MeshDev& m, const T* __restri
     }
     T1[t] = a1.get();
     T2[t] = a2.get();
+    if (TL::UV_IN_X && ly >= H && ly < H + TY && lx >= H && lx < H + TX)
+      XE[(lz * TY + (ly - H)) * TX + (lx - H)] = X[(lz + H) * TL::YW * TL::XW + ly * TL::XW + lx];
   }
   __syncthreads();
   // y pass
@@ -445,7 +454,8 @@ __device__ __forceinline__ double apply_tile(const MeshDev& m, const T* __restri
       ax.add(bKx[(size_t)gx * W + w], V[src]);
     }
     T acc = ax.get();
-    T xe = X[(lz + H) * TL::YW * TL::XW + (ly + H) * TL::XW + lx + H];
+    T xe = TL::UV_IN_X ? XE[(lz * TY + ly) * TX + lx]
+                       : X[(lz + H) * TL::YW * TL::XW + (ly + H) * TL::XW + lx + H];
     dot += ep(gx + (int64_t)nx * gy + sxy * gz, acc, xe);
   }
   return (double)dot;
@@ -865,7 +875,7 @@ __global__ void k_add_scaled(int64_t n, double* __restrict__ x, const float* __r
 template <int K, class S, typename T>
 static size_t apply_smem() {
   using TL = Tile<K, S>;
-  return ((size_t)TL::NX + 2 * (size_t)TL::NT + 2 * (size_t)TL::NU) * sizeof(T);
+  return (size_t)TL::NSM * sizeof(T);
 }
 
 template <class S>
