@@ -166,6 +166,23 @@ def run_reference(args):
     return 0
 
 
+def _max_over_ranks(x, dist, device):
+    """The largest value of x over the ranks (x itself without a process
+    group): a replica run is timed by its slowest rank."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_value(n_per_rank, world, ms):
+    """Whole-job throughput: every rank advances its own replica of n
+    particles in (at most) ms milliseconds."""
+    return world * n_per_rank / (ms * 1e-3)
+
+
 def _step_bytes(n, n_nodes, E, Q, iters, ms, hbm_gbs):
     """Algorithmic HBM bytes of one mixed coupling step and their rate: per
     particle x, r, u_p read, element/bin/slot and the sorted copies written
@@ -490,11 +507,7 @@ def main():
             st = ctxs[p].stats()
             cf.cfdem_synchronize(ctxs[p].h)
         ms = [a.elapsed_time(b) for a, b in ev]
-        tot = float(np.sum(ms))
-        if dist is not None:
-            tt = torch.tensor([tot], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            tot = float(tt.item())
+        tot = _max_over_ranks(float(np.sum(ms)), dist, dev)
         return tot / k, st, clocks
 
     k64 = max(3, args.steps // 2)
@@ -547,12 +560,8 @@ def main():
     gst, _ = cf.cfdem_batch_synchronize(bh)
     st_g = cf.cfdem_get_stats(bed)
     ms_all_g = [a.elapsed_time(b) for a, b in evg]
-    ms_g = float(np.mean(ms_all_g))
-    ms_g_median = float(np.median(ms_all_g))
-    if dist is not None:
-        tt = torch.tensor([ms_g], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_g = float(tt.item())
+    ms_g = _max_over_ranks(float(np.mean(ms_all_g)), dist, dev)
+    ms_g_median = _max_over_ranks(float(np.median(ms_all_g)), dist, dev)
     if args.precision == "mixed":
         print(json.dumps({"mixed_ms_per_step": ms_mx, "stages_ms": {
             nm: st_mx.stage_ms[i] / args.steps for i, nm in enumerate(cf.STAGES)}}), flush=True)
@@ -649,7 +658,7 @@ def main():
                                        else peaks.get("hbm_gbs", 6800.0)))}
                        for c in candidates if c != dom}}
 
-    value = world * n / (ms_g * 1e-3)
+    value = _job_value(n, world, ms_g)
     res = {"metric": METRIC, "value": value, "unit": "particle updates/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_g,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

@@ -353,14 +353,14 @@ __global__ void k_fdm_slab(int nx, int ny, int nz, const float* __restrict__ Bx,
 // for c < K, fac[z][K][mode] = 1 / D(z) (mode stride ms, a multiple of 4).
 // One lane per mode, 32 modes per block.  The block's lines and factors are
 // copied to shared memory by all its threads with asynchronous copies; warp 0
-// runs the two recurrences, reading U steps ahead into registers so that the
-// shared-memory latency stays off the dependency chain.
+// runs the two recurrences, reading U = 8 steps ahead into registers so that
+// the shared-memory latency stays off the dependency chain.
 template <int K>
 __global__ void __launch_bounds__(256)
 k_fdm_zsolve(int nmodes, int ms, int nz, const float* __restrict__ fac, float* __restrict__ v,
              const int* __restrict__ done) {
   if (done && *(volatile const int*)done) return;
-  constexpr int U = 4;
+  constexpr int U = 8;
   extern __shared__ __align__(16) float zsm[];
   float* line = zsm;                  // [nz][32]
   float* f = line + nz * 32;          // [nz][K+1][32]
@@ -421,9 +421,10 @@ k_fdm_zsolve(int nmodes, int ms, int nz, const float* __restrict__ fac, float* _
 #pragma unroll
       for (int j = 0; j < U; ++j) {
         if (z0 + j < nz) {
+          // older terms first: only the newest product is on the dependency chain
           float u = tc[j];
 #pragma unroll
-          for (int c = 0; c < K; ++c) u -= lc[j][c] * w[c];
+          for (int c = K - 1; c >= 0; --c) u -= lc[j][c] * w[c];
 #pragma unroll
           for (int c = K - 1; c > 0; --c) w[c] = w[c - 1];
           w[0] = u;
@@ -464,7 +465,7 @@ k_fdm_zsolve(int nmodes, int ms, int nz, const float* __restrict__ fac, float* _
         if (z0 - j >= 0) {
           float y = uc[j] * dc[j];
 #pragma unroll
-          for (int c = 0; c < K; ++c) y -= bc[j][c] * w[c];
+          for (int c = K - 1; c >= 0; --c) y -= bc[j][c] * w[c];
 #pragma unroll
           for (int c = K - 1; c > 0; --c) w[c] = w[c - 1];
           w[0] = y;
