@@ -62,7 +62,9 @@ typedef struct {
     int scheme;            /* 0 = QCM (quadrature-centred), 1 = PCM */
     double qcm_radius;     /* averaging-sphere radius R; 0 => (3 V_e / 4 pi)^(1/3) */
     double l2_smoothing;   /* L^2 [m^2]; 0 => plain L2 (mass) projection */
-    int drag_model;        /* 0 = Di Felice, 1 = Dallavalle */
+    int drag_model;        /* closure of Sec. 2.3.2: 0 = Di Felice, 1 = Dallavalle,
+                              2 = Rong, 3 = Koch-Hill, 4 = Gidaspow (Ergun below
+                              eps 0.8, Wen-Yu above), 5 = Beetstra */
     int vans_model;        /* 0 = model A (F_pf from drag), 1 = model B (drag + grad p) */
     int beta_over_eps;     /* 1 => beta_B = beta_A / eps (Eq. beta) */
     int precision;         /* 0 = FP64, 1 = mixed (FP32 work, FP64 refinement) */
@@ -74,6 +76,11 @@ typedef struct {
     double bin_edge;       /* bin edge [m]; 0 => R + max_radius */
     int cg_precond;        /* 0 = Jacobi, 1 = fast diagonalisation (exact inverse of the
                               Kronecker-sum operator, applied in FP32; default) */
+    int shear_force;       /* 1 => add the shear force -V_p div tau (Sec. 2.3.2,
+                              undisturbed-flow forces; tau the deviatoric stress of
+                              Eq. (stress), second derivatives of the Q_k velocity
+                              at the particle) to f, and for model B to the fluid
+                              source; default 0 */
 } cfdem_params;
 
 /* Counters of the last calls on a context. */
@@ -245,7 +252,8 @@ cfdem_status cfdem_mass_apply(cfdem_t ctx, const double *x_dev, double *y_dev);
  * and sources of all beds as parallel branches -- into one CUDA graph; later
  * identical steps replay it with a single launch.  Results equal those of
  * cfdem_coupling_step on each bed alone up to the order of the atomic
- * additions inside the right-hand side and the fluid source (rounding). */
+ * additions inside the fluid source and the PCM element volumes
+ * (rounding); the void fraction and the forces are identical. */
 typedef struct cfdem_batch *cfdem_batch_t;
 
 /* Per-bed arguments of cfdem_batch_coupling_step: those of

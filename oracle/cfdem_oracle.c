@@ -25,9 +25,11 @@
  *   or_rhs / or_apply  smoothed L2 projection (M + L^2 K) eps_h = b, the
  *   or_cg              reading of the "void fraction smoothing factor L^2"
  *                      (Tables setup1, setup2, setup4)
- *   or_drag_*          Eqs. (drag) .. Di Felice, Dallavalle, Re_p (Sec. 2.3.2)
+ *   or_drag_*          Eq. (drag) and the closures of Sec. 2.3.2: Di Felice,
+ *                      Dallavalle, Rong, Koch-Hill, Gidaspow, Beetstra, Re_p
  *   or_forces          drag + buoyancy + pressure gradient per particle,
  *                      f_fp,i of Eqs. (fb)/(fa) without the shear term
+ *   or_shear_force     the shear term -V_p div tau, Eq. (stress)
  *   or_fluid_source    F_pf of Eqs. (fb)/(fa), with the minus sign that
  *                      Newton's third law requires (Sec. 2.3.2)
  * Parity is pinned by the tests: closed forms, limits, brute force,
@@ -121,6 +123,37 @@ static void lagrange(int k, const double *z, double t, double *l, double *dl)
         l[a] = v;
         if (dl) dl[a] = dv;
     }
+}
+
+/* Second derivatives of the Lagrange basis from the definition
+ *   l_a(t) = prod_{m != a} (t - z_m) / (z_a - z_m),
+ * differentiated twice: l_a''(t) = sum over ordered pairs b != c (both != a)
+ * of 1/((z_a - z_b)(z_a - z_c)) prod_{m != a, b, c} (t - z_m)/(z_a - z_m). */
+static void lagrange_dd(int k, const double *z, double t, double *ddl)
+{
+    for (int a = 0; a <= k; ++a) {
+        double s = 0.0;
+        for (int b = 0; b <= k; ++b) {
+            if (b == a) continue;
+            for (int c = 0; c <= k; ++c) {
+                if (c == a || c == b) continue;
+                double p = 1.0 / ((z[a] - z[b]) * (z[a] - z[c]));
+                for (int m = 0; m <= k; ++m) {
+                    if (m == a || m == b || m == c) continue;
+                    p *= (t - z[m]) / (z[a] - z[m]);
+                }
+                s += p;
+            }
+        }
+        ddl[a] = s;
+    }
+}
+
+void or_lagrange_dd(int k, double t, double *ddl)
+{
+    double z[8];
+    or_gll_nodes(k, z);
+    lagrange_dd(k, z, t, ddl);
 }
 
 void or_lagrange(int k, double t, double *l, double *dl)
@@ -629,22 +662,101 @@ double or_difelice_chi(double Re)
     return 3.7 - 0.65 * exp(-(t * t) / 2.0);
 }
 
-/* Drag force on one particle of radius rp with slip U = u_f - u_p:
- * F_D = 1/2 rho C_D pi rp^2 |U| U, C_D Dallavalle (model 1) or Di Felice
- * (model 0, Dallavalle times eps^(2 - chi)); divided by eps when
- * beta_over_eps (beta_B = beta_A / eps). */
+/* Rong et al. exponent 2.65 (eps + 1) - (5.3 - 3.5 eps) eps^2
+ * exp(-(1.5 - log10 Re)^2 / 2); C_D is Dallavalle times eps^(2 - it). */
+double or_rong_exponent(double eps, double Re)
+{
+    double re = Re > 1e-300 ? Re : 1e-300;
+    double t = 1.5 - log10(re);
+    return 2.65 * (eps + 1.0) - (5.3 - 3.5 * eps) * eps * eps * exp(-(t * t) / 2.0);
+}
+
+/* Koch-Hill F_0(eps_p): the dilute rational form below eps_p = 0.4, with
+ * eps_p ln eps_p taken as its limit 0 at eps_p = 0; 10 eps_p / eps_f^3 from
+ * 0.4 up. */
+double or_koch_hill_f0(double eps_p)
+{
+    double eps_f = 1.0 - eps_p;
+    if (eps_p >= 0.4) return 10.0 * eps_p / (eps_f * eps_f * eps_f);
+    double plogp = eps_p > 0.0 ? eps_p * log(eps_p) : 0.0;
+    double num = 1.0 + 3.0 * sqrt(eps_p / 2.0) + 135.0 / 64.0 * plogp + 16.14 * eps_p;
+    double den = 1.0 + 0.681 * eps_p - 8.48 * eps_p * eps_p + 8.14 * eps_p * eps_p * eps_p;
+    return num / den;
+}
+
+/* Koch-Hill F_3(eps_p) = 0.0673 + 0.212 eps_p + 0.0232 / eps_f^5 */
+double or_koch_hill_f3(double eps_p)
+{
+    double eps_f = 1.0 - eps_p;
+    return 0.0673 + 0.212 * eps_p + 0.0232 / pow(eps_f, 5.0);
+}
+
+/* Beetstra normalised drag F_i(eps_f, Re) with the bracket read as one
+ * fraction:
+ *   10 eps_p / eps_f^2 + eps_f^2 (1 + 1.5 sqrt(eps_p))
+ *   + 0.413 Re / (24 eps_f^2) (1/eps_f + 3 eps_p eps_f + 8.4 Re^-0.343)
+ *                            / (1 + 10^(3 eps_p) Re^(-(1 + 4 eps_p)/2)). */
+double or_beetstra_f(double eps_f, double Re)
+{
+    double eps_p = 1.0 - eps_f;
+    double a = 10.0 * eps_p / (eps_f * eps_f) + eps_f * eps_f * (1.0 + 1.5 * sqrt(eps_p));
+    if (Re <= 0.0) return a;
+    double num = 1.0 / eps_f + 3.0 * eps_p * eps_f + 8.4 * pow(Re, -0.343);
+    double den = 1.0 + pow(10.0, 3.0 * eps_p) * pow(Re, -(1.0 + 4.0 * eps_p) / 2.0);
+    return a + 0.413 * Re / (24.0 * eps_f * eps_f) * num / den;
+}
+
+/* Drag coefficient of the Schiller-Naumann law used by Gidaspow above
+ * eps_f = 0.8: 24/Re (1 + 0.15 Re^0.687) below Re = 1000, 0.44 above. */
+double or_schiller_naumann_cd(double Re)
+{
+    return Re < 1000.0 ? 24.0 / Re * (1.0 + 0.15 * pow(Re, 0.687)) : 0.44;
+}
+
+/* Drag force on one particle of radius rp with slip U = u_f - u_p, eps the
+ * (clamped) fluid fraction, Re = rho eps |U| d / mu (Sec. 2.3.2):
+ *   0 Di Felice  1/2 rho C_D pi rp^2 |U| U, C_D Dallavalle x eps^(2 - chi)
+ *   1 Dallavalle 1/2 rho C_D pi rp^2 |U| U, C_D = (0.63 + 4.8/sqrt(Re))^2
+ *   2 Rong       as Di Felice with the Rong exponent
+ *   3 Koch-Hill  beta U, beta = 18 mu eps^2 eps_p / d^2 (F_0 + F_3 Re / 2) V_p / eps_p,
+ *                evaluated with eps_p cancelled (finite at eps_p = 0)
+ *   4 Gidaspow   the printed beta is per unit volume of the mixture; one
+ *                particle takes the share V_p / eps_p of it, so the force
+ *                is beta V_p / eps_p U, again with eps_p cancelled: Ergun
+ *                below eps = 0.8 (|U| for the printed vector), Wen-Yu with
+ *                the Schiller-Naumann C_D from 0.8 up
+ *   5 Beetstra   3 pi mu d eps F_i U (the slip U for the printed u_f)
+ * divided by eps when beta_over_eps (beta_B = beta_A / eps). */
 void or_drag_force(int model, int beta_over_eps, double rho, double mu, double eps,
                    const double *U, double rp, double *fd)
 {
     double speed = sqrt(U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
     if (speed == 0.0) { fd[0] = fd[1] = fd[2] = 0.0; return; }
     double dp = 2.0 * rp;
-    double cds = or_cd_times_speed_dallavalle(rho, mu, eps, speed, dp);
-    if (model == 0) {
-        double Re = or_reynolds(rho, mu, eps, speed, dp);
-        cds = cds * pow(eps, 2.0 - or_difelice_chi(Re));
+    double Re = or_reynolds(rho, mu, eps, speed, dp);
+    double Vp = 4.0 / 3.0 * OR_PI * rp * rp * rp;
+    double eps_p = 1.0 - eps;
+    double coef;
+    if (model <= 2) {
+        double cds = or_cd_times_speed_dallavalle(rho, mu, eps, speed, dp);
+        if (model == 0) cds = cds * pow(eps, 2.0 - or_difelice_chi(Re));
+        if (model == 2) cds = cds * pow(eps, 2.0 - or_rong_exponent(eps, Re));
+        coef = 0.5 * rho * cds * OR_PI * rp * rp;
+    } else if (model == 3) {
+        coef = 18.0 * mu * eps * eps / (dp * dp) *
+               (or_koch_hill_f0(eps_p) + 0.5 * or_koch_hill_f3(eps_p) * Re) * Vp;
+    } else if (model == 4) {
+        double beta_over_epsp;   /* beta / eps_p */
+        if (eps < 0.8) {
+            beta_over_epsp = 150.0 * eps_p * mu / (eps * dp * dp) + 1.75 * rho * speed / dp;
+        } else {
+            double cd = or_schiller_naumann_cd(Re);
+            beta_over_epsp = 0.75 * cd * eps * speed * rho / dp * pow(eps, -2.65);
+        }
+        coef = beta_over_epsp * Vp;
+    } else {
+        coef = 3.0 * OR_PI * mu * dp * eps * or_beetstra_f(eps, Re);
     }
-    double coef = 0.5 * rho * cds * OR_PI * rp * rp;
     if (beta_over_eps) coef = coef / eps;
     for (int a = 0; a < 3; ++a) fd[a] = coef * U[a];
 }
@@ -728,12 +840,78 @@ int64_t or_forces(const double *origin, const double *extent, const int *n_el, i
     return bad;
 }
 
+/* Shear force on each particle, F_div_tau = -V_p div tau (Sec. 2.3.2,
+ * undisturbed-flow forces), with the deviatoric stress of Eq. (stress),
+ * tau = mu (grad u + grad u^T) - 2/3 mu (div u) I, whose divergence is
+ *   (div tau)_a = mu sum_b d_b d_b u_a + mu/3 d_a (sum_b d_b u_b),
+ * all second derivatives taken of the Q_k interpolant of u at x_i (the
+ * element's tensor Lagrange basis, chain rule 1/h per axis).  f_shear[n][3].
+ * Returns the first particle outside the mesh, or -1 (its force is 0). */
+int64_t or_shear_force(const double *origin, const double *extent, const int *n_el, int k,
+                       double mu, int64_t n, const double *x, const double *r,
+                       const double *u_nodal, double *f_shear)
+{
+    omesh m = make_mesh(origin, extent, n_el, k);
+    double z[8];
+    or_gll_nodes(k, z);
+    int64_t bad = -1;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        int ie[3];
+        double xi[3];
+        int ok = 1;
+        for (int a = 0; a < 3; ++a)
+            ok &= locate_axis(x[3 * i + a], m.x0[a], m.L[a], m.h[a], m.ne[a], &ie[a], &xi[a]);
+        if (!ok) {
+#pragma omp critical
+            { if (bad < 0 || i < bad) bad = i; }
+            for (int a = 0; a < 3; ++a) f_shear[3 * i + a] = 0.0;
+            continue;
+        }
+        double l[3][8], dl[3][8], ddl[3][8];
+        for (int a = 0; a < 3; ++a) {
+            lagrange(k, z, xi[a], l[a], dl[a]);
+            lagrange_dd(k, z, xi[a], ddl[a]);
+        }
+        /* H[c][p][q] = d_p d_q u_c at x_i */
+        double H[3][3][3];
+        memset(H, 0, sizeof(H));
+        for (int cz = 0; cz <= k; ++cz)
+        for (int cy = 0; cy <= k; ++cy)
+        for (int cx = 0; cx <= k; ++cx) {
+            int64_t nd = gnode(&m, k, ie[0], ie[1], ie[2], cx, cy, cz);
+            int idx[3] = {cx, cy, cz};
+            for (int p = 0; p < 3; ++p)
+                for (int q = 0; q < 3; ++q) {
+                    /* d_p d_q of phi = prod_axis (derivative order along axis) */
+                    double w = 1.0;
+                    for (int a = 0; a < 3; ++a) {
+                        int order = (a == p) + (a == q);
+                        double v = order == 0 ? l[a][idx[a]]
+                                 : order == 1 ? dl[a][idx[a]] : ddl[a][idx[a]];
+                        for (int o = 0; o < order; ++o) v /= m.h[a];
+                        w *= v;
+                    }
+                    for (int c = 0; c < 3; ++c) H[c][p][q] += w * u_nodal[3 * nd + c];
+                }
+        }
+        double Vp = 4.0 / 3.0 * OR_PI * r[i] * r[i] * r[i];
+        for (int a = 0; a < 3; ++a) {
+            double lap = H[a][0][0] + H[a][1][1] + H[a][2][2];
+            double graddiv = H[0][a][0] + H[1][a][1] + H[2][a][2];
+            f_shear[3 * i + a] = -Vp * (mu * lap + mu / 3.0 * graddiv);
+        }
+    }
+    return bad;
+}
+
 /* Fluid source per element, Eqs. (fa)/(fb): F_pf,e = -(1/V_e) sum_{i in e} S_i
- * with S_i = f_D,i (model A, vans_model 0) or f_D,i + f_gradp,i (model B).
+ * with S_i = f_D,i (model A, vans_model 0) or f_D,i + f_gradp,i (+ f_shear,i
+ * when given) (model B).
  * F_e[E][3]; the same value holds at every quadrature point of e. */
 int64_t or_fluid_source(const double *origin, const double *extent, const int *n_el, int k,
                         int vans_model, int64_t n, const double *x, const double *f_drag,
-                        const double *f_gradp, double *F_e)
+                        const double *f_gradp, const double *f_shear, double *F_e)
 {
     omesh m = make_mesh(origin, extent, n_el, k);
     int64_t E = n_elem(&m);
@@ -746,6 +924,7 @@ int64_t or_fluid_source(const double *origin, const double *extent, const int *n
         for (int a = 0; a < 3; ++a) {
             double s = f_drag[3 * i + a];
             if (vans_model == 1) s += f_gradp[3 * i + a];
+            if (vans_model == 1 && f_shear) s += f_shear[3 * i + a];
             S[3 * (int64_t)elem[i] + a] += s;
         }
     }

@@ -10,7 +10,7 @@ dual numbers: every quantity carries its value and its derivative along one
 fixed direction (dx, du) of the inputs, and every elementary operation
 propagates both by the chain rule.  Nothing here uses a closed-form
 derivative of a model formula: the lens volume, the Lagrange basis, the
-closures (Dallavalle, Di Felice) and the norms are differentiated by running
+drag closures and the norms are differentiated by running
 their defining expressions on dual numbers.
 
 The pipeline follows the oracle step by step (oracle.py):
@@ -166,6 +166,26 @@ def lagrange_basis(z, xi):
     return phi, dphi
 
 
+def lagrange_dd(z, xi):
+    """d^2 phi_a / d xi^2 (dual) from the product formula differentiated
+    twice: a sum over ordered pairs b != c of the other nodes."""
+    k = len(z) - 1
+    out = []
+    for a in range(k + 1):
+        s = Dual(np.zeros_like(xi.v))
+        for b in range(k + 1):
+            for c in range(k + 1):
+                if b == a or c == a or b == c:
+                    continue
+                term = Dual(np.full_like(xi.v, 1.0 / ((z[a] - z[b]) * (z[a] - z[c]))))
+                for m in range(k + 1):
+                    if m not in (a, b, c):
+                        term = term * ((xi - z[m]) / (z[a] - z[m]))
+                s = s + term
+        out.append(s)
+    return out
+
+
 def qcm_dual(mesh: O.Mesh, R, x: Dual, r):
     """eps_q[E*Q] (dual) by brute force over all pairs."""
     qp = O.quadrature_points(mesh).reshape(-1, 3)
@@ -194,6 +214,50 @@ def _gnode(mesh, deg, ie, a, b, c):
     nx = int(mesh.n_el[0]) * deg + 1
     ny = int(mesh.n_el[1]) * deg + 1
     return (ie[0] * deg + a) + nx * ((ie[1] * deg + b) + ny * (ie[2] * deg + c))
+
+
+def drag_coef(model, rho, mu, epsc: Dual, speed: Dual, r):
+    """f_D = coef U for the closures of Sec. 2.3.2 (model numbers as in the
+    C oracle's or_drag_force), with Re = rho eps |U| d / mu.  Written from
+    the printed formulas (C_D = 24/Re (...), 10^(3 eps_p) Re^-s, ...);
+    branches are chosen on values, both sides evaluated on safe inputs."""
+    dp = 2.0 * r
+    Re = rho * epsc * speed * dp / mu
+    Vp = 4.0 / 3.0 * PI * r ** 3
+    ep = 1.0 - epsc
+    if model <= 2:
+        a_ = 0.63 * sqrt(speed) + 4.8 * sqrt(mu / (rho * epsc * dp))
+        cds = a_ * a_
+        re = where(Re.v > 1e-300, Re, 1e-300)
+        t = 1.5 - log10(re)
+        g = exp(-(t * t) / 2.0)
+        if model == 0:
+            cds = cds * power(epsc, 2.0 - (3.7 - 0.65 * g))
+        elif model == 2:
+            cds = cds * power(epsc, 2.0 - (2.65 * (epsc + 1.0) - (5.3 - 3.5 * epsc) * epsc * epsc * g))
+        return 0.5 * rho * cds * PI * r * r
+    if model == 3:  # Koch-Hill, eps_p cancelled between beta and V_p / eps_p
+        eps_s = where(ep.v > 0, ep, 1.0)
+        plogp = where(ep.v > 0, eps_s * log(eps_s), 0.0)
+        f0_dilute = (1.0 + 3.0 * sqrt(ep / 2.0) + 135.0 / 64.0 * plogp + 16.14 * ep) / \
+            (1.0 + 0.681 * ep - 8.48 * ep * ep + 8.14 * ep * ep * ep)
+        f0_dense = 10.0 * ep / (epsc * epsc * epsc)
+        F0 = where(ep.v >= 0.4, f0_dense, f0_dilute)
+        F3 = 0.0673 + 0.212 * ep + 0.0232 / power(epsc, 5.0)
+        return 18.0 * mu * epsc * epsc / (dp * dp) * (F0 + 0.5 * F3 * Re) * Vp
+    if model == 4:  # Gidaspow: beta V_p / eps_p with eps_p cancelled
+        dense = 150.0 * ep * mu / (epsc * dp * dp) + 1.75 * rho * speed / dp
+        re = where(Re.v > 0, Re, 1.0)
+        cd = where(Re.v < 1000.0, 24.0 / re * (1.0 + 0.15 * power(re, 0.687)), 0.44)
+        dilute = 0.75 * cd * epsc * speed * rho / dp * power(epsc, -2.65)
+        return where(epsc.v < 0.8, dense, dilute) * Vp
+    # Beetstra, the slip velocity for the printed u_f
+    a_ = 10.0 * ep / (epsc * epsc) + epsc * epsc * (1.0 + 1.5 * sqrt(ep))
+    re = where(Re.v > 0, Re, 1.0)
+    num = 1.0 / epsc + 3.0 * ep * epsc + 8.4 * power(re, -0.343)
+    den = 1.0 + power(Dual(10.0), 3.0 * ep) * power(re, -(1.0 + 4.0 * ep) / 2.0)
+    F = a_ + where(Re.v > 0, 0.413 * Re / (24.0 * epsc * epsc) * num / den, 0.0)
+    return 3.0 * PI * mu * dp * epsc * F
 
 
 def forces_dual(mesh: O.Mesh, params: dict, x: Dual, r, u_p, u_nodal: Dual, p_nodal,
@@ -239,16 +303,8 @@ def forces_dual(mesh: O.Mesh, params: dict, x: Dual, r, u_p, u_nodal: Dual, p_no
     epsc = clamp(eps, floor, 1.0)
     U = [uf[c] - u_p[:, c] for c in range(3)]
     speed = sqrt(U[0] * U[0] + U[1] * U[1] + U[2] * U[2])
-    dp = 2.0 * r
-    a_ = 0.63 * sqrt(speed) + 4.8 * sqrt(mu / (rho * epsc * dp))
-    cds = a_ * a_
-    if model == 0:
-        Re = rho * epsc * speed * dp / mu
-        Re = where(Re.v > 1e-300, Re, 1e-300)
-        t = 1.5 - log10(Re)
-        chi = 3.7 - 0.65 * exp(-(t * t) / 2.0)
-        cds = cds * power(epsc, 2.0 - chi)
-    coef = 0.5 * rho * cds * PI * r * r
+    with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
+        coef = drag_coef(model, rho, mu, epsc, speed, r)
     if boe:
         coef = coef / epsc
     moving = speed.v > 0
@@ -258,7 +314,41 @@ def forces_dual(mesh: O.Mesh, params: dict, x: Dual, r, u_p, u_nodal: Dual, p_no
     f = [fd[c] + (-rho * Vp * grav[c]) + fg[c] for c in range(3)]
     stack = lambda parts: Dual(np.stack([p.v for p in parts], axis=1),  # noqa: E731
                                np.stack([p.t for p in parts], axis=1))
-    return {"f": stack(f), "f_drag": stack(fd), "f_gradp": stack(fg), "eps_p": eps}
+    out = {"f_drag": stack(fd), "f_gradp": stack(fg), "eps_p": eps}
+    if params.get("shear_force", 0):
+        # -V_p div tau, tau = mu (grad u + grad u^T) - 2/3 mu (div u) I:
+        # (div tau)_a = mu lap u_a + mu/3 d_a div u, second derivatives of the
+        # Q_k interpolant (chain rule 1/h per axis)
+        D1 = [lagrange_basis(z, xi[a])[1] for a in range(3)]
+        D2 = [lagrange_dd(z, xi[a]) for a in range(3)]
+        H = [[[Dual(np.zeros(n)) for _ in range(3)] for _ in range(3)] for _ in range(3)]
+        for c in range(k + 1):
+            for b in range(k + 1):
+                for a in range(k + 1):
+                    nd = _gnode(mesh, k, ie, a, b, c)
+                    idx = (a, b, c)
+                    for p in range(3):
+                        for q in range(p, 3):
+                            w = 1.0
+                            for ax in range(3):
+                                order = (ax == p) + (ax == q)
+                                basis = (L, D1, D2)[order][ax][idx[ax]]
+                                w = basis * w if order == 0 else basis / mesh.h[ax] ** order * w
+                            for comp in range(3):
+                                H[comp][p][q] = H[comp][p][q] + w * u_nodal[nd, comp]
+        for comp in range(3):
+            for p in range(3):
+                for q in range(p):
+                    H[comp][p][q] = H[comp][q][p]
+        fs = []
+        for a in range(3):
+            lap = H[a][0][0] + H[a][1][1] + H[a][2][2]
+            graddiv = H[0][a][0] + H[1][a][1] + H[2][a][2]
+            fs.append(-Vp * (mu * lap + (mu / 3.0) * graddiv))
+        f = [f[c] + fs[c] for c in range(3)]
+        out["f_shear"] = stack(fs)
+    out["f"] = stack(f)
+    return out
 
 
 def coupling_jvp(mesh: O.Mesh, params: dict, x, r, u_p, u_nodal, p_nodal, dx=None, du=None):

@@ -68,6 +68,9 @@ def lib():
             L.or_gauss_rule.argtypes = [cint, dp, dp]
             L.or_gll_nodes.argtypes = [cint, dp]
             L.or_lagrange.argtypes = [cint, dbl, dp, dp]
+            L.or_lagrange_dd.argtypes = [cint, dbl, dp]
+            L.or_shear_force.argtypes = [dp, dp, ip, cint, dbl, i64, dp, dp, dp, dp]
+            L.or_shear_force.restype = i64
             L.or_locate.argtypes = [dp, dp, ip, cint, i64, dp, ip, dp]
             L.or_locate.restype = i64
             L.or_bin.argtypes = [dp, dp, ip, i64, dp, ip, ip, ip]
@@ -92,7 +95,7 @@ def lib():
             L.or_forces.argtypes = [dp, dp, ip, cint, cint, dbl, dbl, dp, cint, cint, dbl, i64,
                                     dp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
             L.or_forces.restype = i64
-            L.or_fluid_source.argtypes = [dp, dp, ip, cint, cint, i64, dp, dp, dp, dp]
+            L.or_fluid_source.argtypes = [dp, dp, ip, cint, cint, i64, dp, dp, dp, dp, dp]
             L.or_fluid_source.restype = i64
             L.or_num_threads.restype = cint
             L.or_set_num_threads.argtypes = [cint]
@@ -179,6 +182,12 @@ def lagrange(k, t):
     lib().or_lagrange(k, float(t), l.ctypes.data_as(C.POINTER(C.c_double)),
                       dl.ctypes.data_as(C.POINTER(C.c_double)))
     return l, dl
+
+
+def lagrange_dd(k, t):
+    ddl = np.zeros(k + 1)
+    lib().or_lagrange_dd(k, float(t), ddl.ctypes.data_as(C.POINTER(C.c_double)))
+    return ddl
 
 
 # ---------------------------------------------------------------- locate / bin
@@ -485,15 +494,35 @@ def forces(mesh: Mesh, params: dict, x, r, u_p, u_nodal, p_nodal, eps_nodal):
                           float(params.get("eps_floor", 0.05)), n, px, pr, pup, pun, ppn, pen,
                           f.ctypes.data_as(dp), fd.ctypes.data_as(dp), fg.ctypes.data_as(dp),
                           ep.ctypes.data_as(dp))
-    return {"f": f, "f_drag": fd, "f_gradp": fg, "eps_p": ep, "bad": int(bad)}
+    out = {"f": f, "f_drag": fd, "f_gradp": fg, "eps_p": ep, "bad": int(bad)}
+    if params.get("shear_force", 0):
+        fs, _ = shear_force(mesh, float(params["mu_f"]), x, r, u_nodal)
+        out["f"] = f + fs
+        out["f_shear"] = fs
+    return out
 
 
-def fluid_source(mesh: Mesh, vans_model, x, f_drag, f_gradp):
+def shear_force(mesh: Mesh, mu, x, r, u_nodal):
+    """-V_p div tau per particle (deviatoric stress of Eq. (stress))."""
+    x, px = _d(x)
+    r, pr = _d(r)
+    un, pun = _d(u_nodal)
+    f = np.zeros((x.shape[0], 3))
+    bad = lib().or_shear_force(*mesh.args(), float(mu), x.shape[0], px, pr, pun,
+                               f.ctypes.data_as(C.POINTER(C.c_double)))
+    return f, int(bad)
+
+
+def fluid_source(mesh: Mesh, vans_model, x, f_drag, f_gradp, f_shear=None):
     x, px = _d(x)
     fd, pfd = _d(f_drag)
     fg, pfg = _d(f_gradp)
+    if f_shear is not None:
+        fs, pfs = _d(f_shear)
+    else:
+        pfs = None
     F = np.zeros((mesh.n_elem, 3))
-    bad = lib().or_fluid_source(*mesh.args(), int(vans_model), x.shape[0], px, pfd, pfg,
+    bad = lib().or_fluid_source(*mesh.args(), int(vans_model), x.shape[0], px, pfd, pfg, pfs,
                                 F.ctypes.data_as(C.POINTER(C.c_double)))
     return F, int(bad)
 
@@ -510,7 +539,8 @@ def coupling_step(mesh: Mesh, params: dict, x, r, u_p, u_nodal, p_nodal, eps0=No
     L2 = float(params.get("l2_smoothing", 0.0))
     eps_h, it, res = cg(mesh, L2, b, x0=eps0, rtol=float(params.get("oracle_rtol", 1e-14)))
     fo = forces(mesh, params, x, r, u_p, u_nodal, p_nodal, eps_h)
-    F, _ = fluid_source(mesh, int(params.get("vans_model", 0)), x, fo["f_drag"], fo["f_gradp"])
+    F, _ = fluid_source(mesh, int(params.get("vans_model", 0)), x, fo["f_drag"], fo["f_gradp"],
+                        fo.get("f_shear"))
     return {"eps_q": eps_q, "b": b, "eps_h": eps_h, "cg_iters": it, "cg_relres": res,
             **fo, "F_e": F}
 

@@ -13,7 +13,10 @@
 //      dJ/du_j    += phi_j(x) a_U                      (scatter to nodes)
 //      dJ/deps_h,j += phi_j(x) a_eps                   (scatter to nodes)
 //      dJ/dx      += (grad u_f)^T a_U + a_eps grad eps - V_p H_p g_f
-//    with H_p the Hessian of the interpolated pressure.  The 3 x 4 Jacobian
+//    with H_p the Hessian of the interpolated pressure.  The optional shear
+//    force -V_p mu (lap u + grad div u / 3) is linear in the nodal velocities
+//    (its weights, second derivatives of the basis, go to dJ/du) and adds
+//    third derivatives of the interpolant to dJ/dx.  The 3 x 4 Jacobian
 //    of f_D is taken by forward differentiation of the closure on dual
 //    numbers carrying four derivatives.
 //  projection: eps_h = A^-1 b(eps_q) with A = M + L^2 K symmetric, so the
@@ -31,146 +34,29 @@
 #include <cstdint>
 
 #include "device_common.cuh"
+#include "drag.cuh"
 #include "internal.h"
 
 namespace cfdem {
 namespace {
 
-// ---------------------------------------------------------------- duals
-
-template <typename T>
-struct D4 {  // value and derivatives along (U_0, U_1, U_2, eps_c)
-  T v, d[4];
-};
-
-template <typename T>
-__device__ __forceinline__ D4<T> dc(T v) {
-  D4<T> r;
-  r.v = v;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) r.d[j] = (T)0;
-  return r;
-}
-template <typename T>
-__device__ __forceinline__ D4<T> dv(T v, int j) {
-  D4<T> r = dc<T>(v);
-  r.d[j] = (T)1;
-  return r;
-}
-template <typename T>
-__device__ __forceinline__ D4<T> operator+(D4<T> a, D4<T> b) {
-#pragma unroll
-  for (int j = 0; j < 4; ++j) a.d[j] += b.d[j];
-  a.v += b.v;
-  return a;
-}
-template <typename T>
-__device__ __forceinline__ D4<T> operator-(D4<T> a, D4<T> b) {
-#pragma unroll
-  for (int j = 0; j < 4; ++j) a.d[j] -= b.d[j];
-  a.v -= b.v;
-  return a;
-}
-template <typename T>
-__device__ __forceinline__ D4<T> operator*(D4<T> a, D4<T> b) {
-  D4<T> r;
-  r.v = a.v * b.v;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) r.d[j] = a.d[j] * b.v + a.v * b.d[j];
-  return r;
-}
-template <typename T>
-__device__ __forceinline__ D4<T> operator*(T s, D4<T> a) {
-  a.v *= s;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) a.d[j] *= s;
-  return a;
-}
-template <typename T>
-__device__ __forceinline__ D4<T> operator/(D4<T> a, D4<T> b) {
-  D4<T> r;
-  r.v = a.v / b.v;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) r.d[j] = (a.d[j] - r.v * b.d[j]) / b.v;
-  return r;
-}
-template <typename T>
-__device__ __forceinline__ D4<T> d_sqrt(D4<T> a) {
-  D4<T> r;
-  r.v = t_sqrt<T>(a.v);
-  T k = r.v > (T)0 ? (T)0.5 / r.v : (T)0;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) r.d[j] = k * a.d[j];
-  return r;
-}
-template <typename T>
-__device__ __forceinline__ D4<T> d_exp(D4<T> a) {
-  D4<T> r;
-  r.v = Closure<T>::exp_(a.v);
-#pragma unroll
-  for (int j = 0; j < 4; ++j) r.d[j] = r.v * a.d[j];
-  return r;
-}
-template <typename T>
-__device__ __forceinline__ D4<T> d_log(D4<T> a, T scale) {  // scale * ln(a) derivative
-  D4<T> r;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) r.d[j] = scale * a.d[j] / a.v;
-  r.v = (T)0;
-  return r;
-}
-
-// the drag closure of the forward kernel on dual numbers: fd[c] = coef U_c
+// the drag closure of the forward kernel on dual numbers: fd[c] = coef U_c,
+// derivatives along (U_0, U_1, U_2, eps_c); eps_c is a constant where the
+// clamp is active
 template <typename T>
 __device__ __forceinline__ void drag_dual(const ForceParams& fp, T rp, T U0v, T U1v, T U2v,
                                           T epscv, bool clamped, D4<T> fd[3]) {
   D4<T> U[3] = {dv<T>(U0v, 0), dv<T>(U1v, 1), dv<T>(U2v, 2)};
   D4<T> ec = clamped ? dc<T>(epscv) : dv<T>(epscv, 3);
-  D4<T> speed = d_sqrt<T>(U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
+  D4<T> speed = nsqrt(U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
   if (!(speed.v > (T)0)) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) fd[c] = dc<T>((T)0);
     return;
   }
-  const T rho = (T)fp.rho, mu = (T)fp.mu, dp = (T)2 * rp;
-  D4<T> a = (T)0.63 * d_sqrt<T>(speed) + (T)4.8 * d_sqrt<T>(dc<T>(mu) / (rho * dp * ec));
-  D4<T> cds = a * a;
-  if (fp.drag_model == 0) {
-    D4<T> Re = (rho * dp / mu) * (ec * speed);
-    if (!(Re.v > Closure<T>::tiny())) Re = dc<T>(Closure<T>::tiny());
-    D4<T> l10 = d_log<T>(Re, (T)0.43429448190325176);  // derivative of log10
-    l10.v = Closure<T>::log10_(Re.v);
-    D4<T> tt = dc<T>((T)1.5) - l10;
-    D4<T> chi = dc<T>((T)3.7) - (T)0.65 * d_exp<T>((T)(-0.5) * (tt * tt));
-    D4<T> ln = d_log<T>(ec, (T)1);
-    ln.v = Closure<T>::logn(ec.v);
-    cds = cds * d_exp<T>((dc<T>((T)2) - chi) * ln);
-  }
-  D4<T> coef = ((T)0.5 * rho * (T)kPi * rp * rp) * cds;
-  if (fp.beta_over_eps) coef = coef / ec;
+  const D4<T> coef = drag_coef<D4<T>, T>(fp, speed, ec, rp);
 #pragma unroll
   for (int c = 0; c < 3; ++c) fd[c] = coef * U[c];
-}
-
-// Lagrange basis, first and second derivatives at t (FP64)
-template <int D>
-__device__ __forceinline__ void lagrange2(const double* zz, const double* lw, double t, double* l,
-                                          double* dl, double* ddl) {
-#pragma unroll
-  for (int a = 0; a <= D; ++a) {
-    double v = 1.0, d1 = 0.0, d2 = 0.0;
-#pragma unroll
-    for (int b = 0; b <= D; ++b) {
-      if (b == a) continue;
-      double db = t - zz[b];
-      d2 = d2 * db + 2.0 * d1;
-      d1 = d1 * db + v;
-      v = v * db;
-    }
-    l[a] = v * lw[a];
-    dl[a] = d1 * lw[a];
-    ddl[a] = d2 * lw[a];
-  }
 }
 
 // ------------------------------------------------------------ kernels
@@ -235,9 +121,9 @@ k_adj_forces(MeshDev m, Tables tb, ForceParams fp, int64_t n, const double* __re
   // Hessian of the interpolated pressure (Q_kp, FP64)
   double px[KP + 1], py[KP + 1], pz[KP + 1], dpx[KP + 1], dpy[KP + 1], dpz[KP + 1];
   double ddpx[KP + 1], ddpy[KP + 1], ddpz[KP + 1];
-  lagrange2<KP>(tb.zp, tb.lwp, xid[0], px, dpx, ddpx);
-  lagrange2<KP>(tb.zp, tb.lwp, xid[1], py, dpy, ddpy);
-  lagrange2<KP>(tb.zp, tb.lwp, xid[2], pz, dpz, ddpz);
+  lagrange_d3<KP, double>(tb.zp, tb.lwp, xid[0], px, dpx, ddpx, (double*)nullptr);
+  lagrange_d3<KP, double>(tb.zp, tb.lwp, xid[1], py, dpy, ddpy, (double*)nullptr);
+  lagrange_d3<KP, double>(tb.zp, tb.lwp, xid[2], pz, dpz, ddpz, (double*)nullptr);
   int64_t pnx = m.np[0], pnxy = (int64_t)m.np[0] * m.np[1];
   int64_t pbase =
       (int64_t)ie[0] * KP + pnx * ((int64_t)ie[1] * KP) + pnxy * ((int64_t)ie[2] * KP);
@@ -288,9 +174,55 @@ k_adj_forces(MeshDev m, Tables tb, ForceParams fp, int64_t n, const double* __re
 
   // direct gradient with respect to x_i
   const double Vp = 4.0 / 3.0 * kPi * r[i] * r[i] * r[i];
+  // shear force f_s,a = c0 (lap u_a + d_a div u / 3), c0 = -V_p mu: linear in
+  // the nodal velocities; its x-derivative takes third derivatives of the basis
+  const bool shear = fp.shear && gf;
+  const double c0 = -Vp * fp.mu;
+  double sb[3][K + 1], s1[3][K + 1], s2[3][K + 1], s3[3][K + 1];
+  double gs[3] = {0, 0, 0};
+  if (shear) {
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax)
+      lagrange_d3<K, double>(tb.z, tb.lw, xid[ax], sb[ax], s1[ax], s2[ax], s3[ax]);
+#pragma unroll
+    for (int c = 0; c <= K; ++c)
+#pragma unroll
+      for (int b = 0; b <= K; ++b)
+#pragma unroll
+        for (int a = 0; a <= K; ++a) {
+          const int id[3] = {a, b, c};
+          // D3(p, q, w): d_p d_q d_w of the node's basis function
+          auto D3 = [&](int pp, int qq, int ww) {
+            double v = 1.0;
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) {
+              const int o = (pp == ax) + (qq == ax) + (ww == ax);
+              const double bv = o == 0 ? sb[ax][id[ax]]
+                              : o == 1 ? s1[ax][id[ax]] * ih[ax]
+                              : o == 2 ? s2[ax][id[ax]] * ih[ax] * ih[ax]
+                                       : s3[ax][id[ax]] * ih[ax] * ih[ax] * ih[ax];
+              v *= bv;
+            }
+            return v;
+          };
+          const int64_t nd = base + a + nx * b + nxy * c;
+          const double u[3] = {__ldg(u_nodal + 3 * nd), __ldg(u_nodal + 3 * nd + 1),
+                               __ldg(u_nodal + 3 * nd + 2)};
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const double lapk = D3(k, 0, 0) + D3(k, 1, 1) + D3(k, 2, 2);
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+              const double m3 = g_f[0] * D3(k, 0, cc) + g_f[1] * D3(k, 1, cc) +
+                                g_f[2] * D3(k, 2, cc);
+              gs[k] += u[cc] * (g_f[cc] * lapk + m3 / 3.0);
+            }
+          }
+        }
+  }
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    double g = aE * ge[k];
+    double g = aE * ge[k] + c0 * gs[k];
 #pragma unroll
     for (int c = 0; c < 3; ++c) g += aU[c] * gu[c][k] - Vp * g_f[c] * H[c][k];
     dJdx[3 * i + k] = g;
@@ -305,9 +237,33 @@ k_adj_forces(MeshDev m, Tables tb, ForceParams fp, int64_t n, const double* __re
         double phi = lx[a] * ly[b] * lz[c];
         int64_t nd = base + a + nx * b + nxy * c;
         if (aE != 0.0) atomicAdd(geps + nd, phi * aE);
-        if (dJdu)
+        if (dJdu) {
+          double add[3] = {phi * aU[0], phi * aU[1], phi * aU[2]};
+          if (shear) {  // c0 (g_c lap phi + sum_a g_a d_a d_c phi / 3)
+            const int id[3] = {a, b, c};
+            double D2[3][3];
 #pragma unroll
-          for (int comp = 0; comp < 3; ++comp) atomicAdd(dJdu + 3 * nd + comp, phi * aU[comp]);
+            for (int pp = 0; pp < 3; ++pp)
+#pragma unroll
+              for (int qq = 0; qq < 3; ++qq) {
+                double v = 1.0;
+#pragma unroll
+                for (int ax = 0; ax < 3; ++ax) {
+                  const int o = (pp == ax) + (qq == ax);
+                  v *= o == 0 ? sb[ax][id[ax]]
+                     : o == 1 ? s1[ax][id[ax]] * ih[ax] : s2[ax][id[ax]] * ih[ax] * ih[ax];
+                }
+                D2[pp][qq] = v;
+              }
+            const double lap = D2[0][0] + D2[1][1] + D2[2][2];
+#pragma unroll
+            for (int comp = 0; comp < 3; ++comp)
+              add[comp] += c0 * (g_f[comp] * lap + (g_f[0] * D2[0][comp] + g_f[1] * D2[1][comp] +
+                                                    g_f[2] * D2[2][comp]) / 3.0);
+          }
+#pragma unroll
+          for (int comp = 0; comp < 3; ++comp) atomicAdd(dJdu + 3 * nd + comp, add[comp]);
+        }
       }
 }
 
@@ -455,21 +411,13 @@ k_adj_qcm(MeshDev m, Tables tb, double R, int64_t n, const double* __restrict__ 
 
 }  // namespace
 
-cudaError_t launch_adj_forces(const MeshDev& m, const Tables& t, int precision, double rho,
-                              double mu, int drag_model, int beta_over_eps, double eps_floor,
-                              int64_t n, const double* x, const double* r, const double* u_p,
-                              const double* u_nodal, const double* p_nodal,
+cudaError_t launch_adj_forces(const MeshDev& m, const Tables& t, int precision,
+                              const ForceParams& fp, int64_t n, const double* x, const double* r,
+                              const double* u_p, const double* u_nodal, const double* p_nodal,
                               const double* eps_nodal, const double* gf, const double* gfd,
                               double* dJdx, double* dJdu, double* geps, DevStatus* st,
                               cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  ForceParams fp{};
-  fp.rho = rho;
-  fp.mu = mu;
-  fp.eps_floor = eps_floor;
-  fp.drag_model = drag_model;
-  fp.beta_over_eps = beta_over_eps;
-  for (int a = 0; a < 3; ++a) fp.inv_h[a] = 1.0 / m.h[a];
   const int bs = 128;
   const unsigned nb = (unsigned)((n + bs - 1) / bs);
 #define CFDEM_ADJ(K, KP)                                                                    \

@@ -101,6 +101,23 @@ cfdem_status cuda_fail(cfdem_t c, cudaError_t e, const char* where) {
   return fail(c, CFDEM_ECUDA, "%s: %s", where, cudaGetErrorString(e));
 }
 
+// the force kernels' parameters from the context's parameters and mesh
+ForceParams force_params(const cfdem_ctx* c) {
+  ForceParams fp{};
+  fp.rho = c->prm.rho_f;
+  fp.mu = c->prm.mu_f;
+  for (int a = 0; a < 3; ++a) {
+    fp.g[a] = c->prm.g[a];
+    fp.inv_h[a] = 1.0 / c->mesh.h[a];
+  }
+  fp.eps_floor = c->prm.eps_floor;
+  fp.drag_model = c->prm.drag_model;
+  fp.beta_over_eps = c->prm.beta_over_eps;
+  fp.vans_model = c->prm.vans_model;
+  fp.shear = c->prm.shear_force;
+  return fp;
+}
+
 #define CK(expr, where)                                  \
   do {                                                   \
     cudaError_t e_ = (expr);                             \
@@ -295,7 +312,7 @@ void free_mesh_arena(cfdem_t c) {
                 c->cg.q0, c->cg.q1, c->cg.Aq, c->cg.dinv32, c->cg.d32, c->cg.partials,
                 c->cg.sc, c->cg.zn, c->cg.zn32, c->cg.rin32, c->cg.x_df, c->cg.r_df,
                 c->cg.b_df, c->cg.Ap_df, c->cg.p0_df, c->cg.p1_df, c->adj_geps,
-                c->adj_lam, c->adj_gq};
+                c->adj_lam, c->adj_gq, c->rhs_local};
   for (void* p : ps)
     if (p) cudaFree(p);
   c->eps64 = nullptr;
@@ -304,6 +321,7 @@ void free_mesh_arena(cfdem_t c) {
   c->S = nullptr;
   c->vol = nullptr;
   c->adj_geps = c->adj_lam = c->adj_gq = nullptr;
+  c->rhs_local = nullptr;
   FdmPlan* keep = c->cg.fdm;
   const df64* kb = c->cg.bands_df;
   c->cg = CgWork{};
@@ -319,6 +337,7 @@ cfdem_status alloc_mesh_arena(cfdem_t c) {
   CK(grow(&c->b, nn), "mesh arena");
   CK(grow(&c->S, 3 * m.E), "mesh arena");
   CK(grow(&c->vol, m.E), "mesh arena");
+  CK(grow(&c->rhs_local, m.E * (int64_t)(m.k + 1) * (m.k + 1) * (m.k + 1)), "mesh arena");
   CgWork& w = c->cg;
   CK(grow(&w.r, nn), "cg");
   CK(grow(&w.z, nn), "cg");
@@ -460,6 +479,7 @@ void cfdem_params_default(cfdem_params* p) {
   p->cg_maxit = 2000;
   p->eps_floor = 0.05;
   p->cg_precond = 1;
+  p->shear_force = 0;
 }
 
 cfdem_status cfdem_create(cfdem_t* out, int device, void* stream) {
@@ -551,8 +571,10 @@ cfdem_status cfdem_set_params(cfdem_t c, const cfdem_params* p) {
       !is_finite_d(p->g[2]))
     return fail(c, CFDEM_EINVAL, "rho_f, mu_f must be > 0 and g finite");
   if (p->scheme < 0 || p->scheme > 1) return fail(c, CFDEM_EINVAL, "scheme must be 0 or 1");
-  if (p->drag_model < 0 || p->drag_model > 1)
-    return fail(c, CFDEM_EINVAL, "drag_model must be 0 (Di Felice) or 1 (Dallavalle)");
+  if (p->drag_model < 0 || p->drag_model > 5)
+    return fail(c, CFDEM_EINVAL,
+                "drag_model must be 0 (Di Felice), 1 (Dallavalle), 2 (Rong), 3 (Koch-Hill), "
+                "4 (Gidaspow) or 5 (Beetstra)");
   if (p->vans_model < 0 || p->vans_model > 1) return fail(c, CFDEM_EINVAL, "vans_model 0|1");
   if (p->precision < 0 || p->precision > 1) return fail(c, CFDEM_EINVAL, "precision 0|1");
   if (!(p->qcm_radius >= 0) || !(p->l2_smoothing >= 0) || !(p->cg_rtol > 0) ||
@@ -563,6 +585,8 @@ cfdem_status cfdem_set_params(cfdem_t c, const cfdem_params* p) {
     return fail(c, CFDEM_EINVAL, "pressure_degree must be 0..3");
   if (p->cg_precond < 0 || p->cg_precond > 1)
     return fail(c, CFDEM_EINVAL, "cg_precond must be 0 (Jacobi) or 1 (FDM)");
+  if (p->shear_force < 0 || p->shear_force > 1)
+    return fail(c, CFDEM_EINVAL, "shear_force must be 0 or 1");
   c->prm = *p;
   ++c->gen;
   return resolve(c);
@@ -653,10 +677,10 @@ cfdem_status cfdem_project_rhs(cfdem_t c, const double* eps_q, double* b) {
   if (!eps_q && c->eps_state == 0) return fail(c, CFDEM_ESTATE, "no void fraction computed yet");
   c->timer.begin(kStageRhs, c->stream);
   if (eps_q) {
-    CK(launch_rhs(c->mesh, c->tab, eps_q, nullptr, b, c->stream), "rhs");
+    CK(launch_rhs(c->mesh, c->tab, eps_q, nullptr, c->rhs_local, b, c->stream), "rhs");
   } else {
-    CK(launch_rhs(c->mesh, c->tab, c->eps64, c->eps_state == 2 ? c->eps32 : nullptr, b,
-                  c->stream),
+    CK(launch_rhs(c->mesh, c->tab, c->eps64, c->eps_state == 2 ? c->eps32 : nullptr,
+                  c->rhs_local, b, c->stream),
        "rhs");
   }
   c->timer.end(kStageRhs, c->stream);
@@ -695,10 +719,8 @@ cfdem_status cfdem_forces(cfdem_t c, int64_t n, const double* x, const double* r
   bool want_src = F_elem || F_q;
   if (want_src) CK(cudaMemsetAsync(c->S, 0, sizeof(double) * 3 * m.E, c->stream), "forces");
   c->timer.begin(kStageForces, c->stream);
-  CK(launch_forces(m, c->tab, c->prm.precision, c->prm.rho_f, c->prm.mu_f, c->prm.g,
-                   c->prm.drag_model, c->prm.beta_over_eps, c->prm.eps_floor,
-                   c->prm.vans_model, n, x, r, u_p, u_nodal, p_nodal, eps_nodal, f, f_drag,
-                   want_src ? c->S : nullptr, c->st, c->stream),
+  CK(launch_forces(m, c->tab, c->prm.precision, force_params(c), n, x, r, u_p, u_nodal,
+                   p_nodal, eps_nodal, f, f_drag, want_src ? c->S : nullptr, c->st, c->stream),
      "forces");
   c->timer.end(kStageForces, c->stream);
   if (want_src) {
@@ -753,10 +775,9 @@ cfdem_status cfdem_adjoint(cfdem_t c, int64_t n, const double* x, const double* 
   else
     CK(cudaMemsetAsync(c->adj_geps, 0, sizeof(double) * m.n_nodes, c->stream), "adjoint");
   if (dJ_du) CK(cudaMemsetAsync(dJ_du, 0, sizeof(double) * 3 * m.n_nodes, c->stream), "adjoint");
-  CK(launch_adj_forces(m, c->tab, c->prm.precision, c->prm.rho_f, c->prm.mu_f,
-                       c->prm.drag_model, c->prm.beta_over_eps, c->prm.eps_floor, n, x, r, u_p,
-                       u_nodal, p_nodal, eps_nodal, g_f, g_fdrag, dJ_dx, dJ_du, c->adj_geps,
-                       c->st, c->stream),
+  CK(launch_adj_forces(m, c->tab, c->prm.precision, force_params(c), n, x, r, u_p, u_nodal,
+                       p_nodal, eps_nodal, g_f, g_fdrag, dJ_dx, dJ_du, c->adj_geps, c->st,
+                       c->stream),
      "adjoint forces");
   if (c->prm.scheme == 0) {
     // lambda = A^-1 dJ/deps_h (A symmetric), then through the QCM

@@ -42,6 +42,7 @@ struct cfdem_ctx {
   double* b = nullptr;
   double* S = nullptr;         // per-element source accumulator [E][3]
   double* vol = nullptr;       // per-element particle volume (PCM)
+  double* rhs_local = nullptr; // per-element right-hand-side contributions [(k+1)^3][E]
   // adjoint arena (grown by the first cfdem_adjoint)
   double* adj_geps = nullptr;  // dJ/deps_h [n_nodes]
   double* adj_lam = nullptr;   // lambda = A^-1 dJ/deps_h [n_nodes]

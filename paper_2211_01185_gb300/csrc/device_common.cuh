@@ -100,6 +100,33 @@ __device__ __forceinline__ void lagrange(const double* zz, const double* lw, T t
   }
 }
 
+// Lagrange basis with its first, second and (if d3 is given) third
+// derivatives at t: the product prod_{b != a} (t - z_b) differentiated by
+// the Leibniz rule, scaled by the barycentric weight lw[a].
+template <int D, typename T>
+__device__ __forceinline__ void lagrange_d3(const double* zz, const double* lw, T t, T* l, T* d1,
+                                            T* d2, T* d3) {
+  T d[D + 1];
+#pragma unroll
+  for (int a = 0; a <= D; ++a) d[a] = t - (T)zz[a];
+#pragma unroll
+  for (int a = 0; a <= D; ++a) {
+    T v = (T)1, v1 = (T)0, v2 = (T)0, v3 = (T)0;
+#pragma unroll
+    for (int b = 0; b <= D; ++b) {
+      if (b == a) continue;
+      v3 = v3 * d[b] + (T)3 * v2;
+      v2 = v2 * d[b] + (T)2 * v1;
+      v1 = v1 * d[b] + v;
+      v = v * d[b];
+    }
+    l[a] = v * (T)lw[a];
+    d1[a] = v1 * (T)lw[a];
+    d2[a] = v2 * (T)lw[a];
+    if (d3) d3[a] = v3 * (T)lw[a];
+  }
+}
+
 template <typename T>
 struct Closure {
   static __device__ __forceinline__ T log10_(T v);
@@ -122,10 +149,5 @@ struct Closure<float> {
   static __device__ __forceinline__ float tiny() { return 1e-37f; }
 };
 
-struct ForceParams {
-  double rho, mu, g[3], eps_floor;
-  double inv_h[3];
-  int drag_model, beta_over_eps, vans_model;
-};
 
 }  // namespace cfdem

@@ -109,6 +109,15 @@ struct Timer {
 void count_launches(int n);
 long long launches_total();
 
+// Parameters of the per-particle force kernels (from cfdem_params and the
+// mesh): fluid density and viscosity, gravity, closure floor, 1/h per axis,
+// drag closure, beta_B = beta_A / eps flag, VANS model, shear force flag.
+struct ForceParams {
+  double rho, mu, g[3], eps_floor;
+  double inv_h[3];
+  int drag_model, beta_over_eps, vans_model, shear;
+};
+
 // ---------------------------------------------------------------- launchers
 // particles.cu
 cudaError_t launch_locate(const MeshDev& m, int64_t n, const double* x, int32_t* elem,
@@ -117,12 +126,11 @@ cudaError_t launch_bin(const MeshDev& m, const BinDev& b, int64_t n, const doubl
                        const double* r, int32_t* bin_of, int32_t* slot, int32_t* bin_count,
                        int32_t* bin_start, int32_t* perm, int32_t* scan_tmp, double* xs64,
                        float* xs32, DevStatus* st, cudaStream_t s);
-cudaError_t launch_forces(const MeshDev& m, const Tables& t, int precision, double rho,
-                          double mu, const double g[3], int drag_model, int beta_over_eps,
-                          double eps_floor, int vans_model, int64_t n, const double* x,
-                          const double* r, const double* u_p, const double* u_nodal,
-                          const double* p_nodal, const double* eps_nodal, double* f,
-                          double* f_drag, double* S_elem, DevStatus* st, cudaStream_t s);
+cudaError_t launch_forces(const MeshDev& m, const Tables& t, int precision, const ForceParams& fp,
+                          int64_t n, const double* x, const double* r, const double* u_p,
+                          const double* u_nodal, const double* p_nodal,
+                          const double* eps_nodal, double* f, double* f_drag, double* S_elem,
+                          DevStatus* st, cudaStream_t s);
 cudaError_t launch_fluid_source(const MeshDev& m, const double* S_elem, double* F_elem,
                                 double* F_q, cudaStream_t s);
 
@@ -137,15 +145,16 @@ cudaError_t launch_pcm(const MeshDev& m, int64_t n, const double* x, const doubl
                        cudaStream_t s);
 
 // projection.cu
+// local: scratch of (k+1)^3 E doubles (per-element contributions)
 cudaError_t launch_rhs(const MeshDev& m, const Tables& t, const double* eps_q64,
-                       const float* eps_q32, double* b, cudaStream_t s);
+                       const float* eps_q32, double* local, double* b, cudaStream_t s);
 cudaError_t upload_bands(const MeshDev& m, const Tables& t, double L2, double** bands64,
                          float** bands32, float** bands_df);
 cudaError_t launch_apply64(const MeshDev& m, const double* bands, const double* coef,
                            const double* x, double* y, cudaStream_t s);
-cudaError_t launch_adj_forces(const MeshDev& m, const Tables& t, int precision, double rho,
-                              double mu, int drag_model, int beta_over_eps, double eps_floor,
-                              int64_t n, const double* x, const double* r, const double* u_p,
+cudaError_t launch_adj_forces(const MeshDev& m, const Tables& t, int precision,
+                              const ForceParams& fp, int64_t n, const double* x, const double* r,
+                              const double* u_p,
                               const double* u_nodal, const double* p_nodal,
                               const double* eps_nodal, const double* gf, const double* gfd,
                               double* dJdx, double* dJdu, double* geps, DevStatus* st,

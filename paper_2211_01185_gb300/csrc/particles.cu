@@ -7,6 +7,7 @@
 
 #include "internal.h"
 #include "device_common.cuh"
+#include "drag.cuh"
 
 namespace cfdem {
 
@@ -274,6 +275,56 @@ cudaError_t launch_bin(const MeshDev& m, const BinDev& b, int64_t n, const doubl
 // ----------------------------------------------------------------------------
 // a6: forces
 
+// Shear force -V_p div tau at local coordinates xi of the element whose first
+// velocity node is `base` (Sec. 2.3.2), tau the deviatoric stress of Eq.
+// (stress): (div tau)_a = mu (lap u_a + d_a (div u) / 3), second derivatives
+// of the Q_k interpolant with the chain rule 1/h per axis.  Nodal values are
+// taken relative to the element's first node (in FP64) so that the FP32 path
+// does not carry the mean velocity through the cancelling weights.
+template <int K, typename T>
+__device__ __forceinline__ void shear_force(const Tables& tb, const ForceParams& fp,
+                                            const double* __restrict__ u_nodal, int64_t base,
+                                            int64_t nx, int64_t nxy, const T xi[3], T Vp,
+                                            T fs[3]) {
+  T l[3][K + 1], d1[3][K + 1], d2[3][K + 1];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax)
+    lagrange_d3<K, T>(tb.z, tb.lw, xi[ax], l[ax], d1[ax], d2[ax], (T*)nullptr);
+  const T ih0 = (T)fp.inv_h[0], ih1 = (T)fp.inv_h[1], ih2 = (T)fp.inv_h[2];
+  const T sxx = ih0 * ih0, syy = ih1 * ih1, szz = ih2 * ih2;
+  const T sxy = ih0 * ih1, sxz = ih0 * ih2, syz = ih1 * ih2;
+  T H[3][6];  // per component: xx, yy, zz, xy, xz, yz
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int q = 0; q < 6; ++q) H[c][q] = (T)0;
+  const double u00 = __ldg(u_nodal + 3 * base), u01 = __ldg(u_nodal + 3 * base + 1),
+               u02 = __ldg(u_nodal + 3 * base + 2);
+#pragma unroll
+  for (int c = 0; c <= K; ++c)
+#pragma unroll
+    for (int b = 0; b <= K; ++b)
+#pragma unroll
+      for (int a = 0; a <= K; ++a) {
+        const int64_t nd = base + a + nx * b + nxy * c;
+        const T du[3] = {(T)(__ldg(u_nodal + 3 * nd) - u00), (T)(__ldg(u_nodal + 3 * nd + 1) - u01),
+                         (T)(__ldg(u_nodal + 3 * nd + 2) - u02)};
+        const T w[6] = {d2[0][a] * l[1][b] * l[2][c] * sxx, l[0][a] * d2[1][b] * l[2][c] * syy,
+                        l[0][a] * l[1][b] * d2[2][c] * szz, d1[0][a] * d1[1][b] * l[2][c] * sxy,
+                        d1[0][a] * l[1][b] * d1[2][c] * sxz, l[0][a] * d1[1][b] * d1[2][c] * syz};
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc)
+#pragma unroll
+          for (int q = 0; q < 6; ++q) H[cc][q] += w[q] * du[cc];
+      }
+  const T mu = (T)fp.mu, mu3 = (T)(fp.mu / 3.0);
+  const T gd[3] = {H[0][0] + H[1][3] + H[2][4], H[0][3] + H[1][1] + H[2][5],
+                   H[0][4] + H[1][5] + H[2][2]};  // d_a div u
+#pragma unroll
+  for (int cc = 0; cc < 3; ++cc)
+    fs[cc] = -Vp * (mu * (H[cc][0] + H[cc][1] + H[cc][2]) + mu3 * gd[cc]);
+}
+
 template <int K, int KP, typename T>
 __global__ void __launch_bounds__(128)
 k_forces(MeshDev m, Tables tb, ForceParams fp, int64_t n, const double* __restrict__ x,
@@ -372,25 +423,20 @@ k_forces(MeshDev m, Tables tb, ForceParams fp, int64_t n, const double* __restri
   epsc = epsc > (T)1 ? (T)1 : epsc;
   T fd0 = 0, fd1 = 0, fd2 = 0;
   if (speed > (T)0) {
-    T rho = (T)fp.rho, mu = (T)fp.mu;
-    T dp = (T)2 * rp;
-    T a = (T)0.63 * t_sqrt<T>(speed) + (T)4.8 * t_sqrt<T>(mu / (rho * epsc * dp));
-    T cds = a * a;
-    if (fp.drag_model == 0) {
-      T Re = rho * epsc * speed * dp / mu;
-      T re = Re > Closure<T>::tiny() ? Re : Closure<T>::tiny();
-      T tt = (T)1.5 - Closure<T>::log10_(re);
-      T chi = (T)3.7 - (T)0.65 * Closure<T>::exp_(-(tt * tt) / (T)2);
-      cds = cds * Closure<T>::exp_(((T)2 - chi) * Closure<T>::logn(epsc));
-    }
-    T coef = (T)0.5 * rho * cds * (T)kPi * rp * rp;
-    if (fp.beta_over_eps) coef = coef / epsc;
+    const T coef = drag_coef<T, T>(fp, speed, epsc, rp);
     fd0 = coef * U0;
     fd1 = coef * U1;
     fd2 = coef * U2;
   }
   T Vp = (T)(4.0 / 3.0 * kPi) * rp * rp * rp;
   T fg0 = -Vp * gp0, fg1 = -Vp * gp1, fg2 = -Vp * gp2;
+  if (fp.shear) {  // the shear force joins the pressure term: f and model B's source
+    T fs[3];
+    shear_force<K, T>(tb, fp, u_nodal, base, nx, nxy, xi, Vp, fs);
+    fg0 += fs[0];
+    fg1 += fs[1];
+    fg2 += fs[2];
+  }
   T rv = (T)fp.rho * Vp;
   f[3 * i] = (double)(fd0 + (-rv * (T)fp.g[0]) + fg0);
   f[3 * i + 1] = (double)(fd1 + (-rv * (T)fp.g[1]) + fg1);
@@ -426,24 +472,12 @@ static void launch_forces_t(const MeshDev& m, const Tables& t, const ForceParams
   count_launches(1);
 }
 
-cudaError_t launch_forces(const MeshDev& m, const Tables& t, int precision, double rho,
-                          double mu, const double g[3], int drag_model, int beta_over_eps,
-                          double eps_floor, int vans_model, int64_t n, const double* x,
-                          const double* r, const double* u_p, const double* u_nodal,
-                          const double* p_nodal, const double* eps_nodal, double* f,
-                          double* f_drag, double* S_elem, DevStatus* st, cudaStream_t s) {
+cudaError_t launch_forces(const MeshDev& m, const Tables& t, int precision, const ForceParams& fp,
+                          int64_t n, const double* x, const double* r, const double* u_p,
+                          const double* u_nodal, const double* p_nodal,
+                          const double* eps_nodal, double* f, double* f_drag, double* S_elem,
+                          DevStatus* st, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  ForceParams fp;
-  fp.rho = rho;
-  fp.mu = mu;
-  fp.g[0] = g[0];
-  fp.g[1] = g[1];
-  fp.g[2] = g[2];
-  fp.eps_floor = eps_floor;
-  fp.drag_model = drag_model;
-  fp.beta_over_eps = beta_over_eps;
-  fp.vans_model = vans_model;
-  for (int a = 0; a < 3; ++a) fp.inv_h[a] = 1.0 / m.h[a];
 #define CFDEM_FORCES(K, KP)                                                                  \
   if (m.k == K && m.kp == KP) {                                                              \
     if (precision == 0)                                                                      \

@@ -26,6 +26,7 @@
 // last block to finish, so dot products are deterministic, and every kernel
 // returns at once after convergence.  The mixed path runs the same CG in FP32
 // on the correction equation inside FP64 iterative refinement.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -40,24 +41,31 @@ namespace cfdem {
 // ---------------------------------------------------------------------------
 // right-hand side
 
+// elements (threads) per block of k_rhs: the staged quadrature values fit 40 KB
 template <int K, typename T>
 constexpr int rhs_block() {
   return ((K + 1) * (K + 1) * (K + 1) * (int)sizeof(T) * 128 <= 40 * 1024) ? 128 : 64;
 }
 
+// Per element: its contribution to the right-hand side at each of its
+// (k+1)^3 nodes, |J| sum_q phi_j(x_q) w_q eps_q, sum-factorised into three
+// 1D contractions (x, then y, then z), one thread per element, in the path's
+// precision T.  Written to local[j][e] (no atomics; k_rhs_gather adds the
+// slots up per global node), element index fastest so that the stores of a
+// warp coalesce.
 template <int K, typename T>
 __global__ void __launch_bounds__(128)
-k_rhs(MeshDev m, Tables tb, const T* __restrict__ eps_q, double* __restrict__ b) {
+k_rhs(MeshDev m, Tables tb, const T* __restrict__ eps_q, T* __restrict__ local) {
   constexpr int NQ = K + 1;
   constexpr int Q = NQ * NQ * NQ;
   constexpr int NB = (Q * (int)sizeof(T) * 128 <= 40 * 1024) ? 128 : 64;
   __shared__ T sh[NB * Q];
-  int64_t e0 = blockIdx.x * (int64_t)NB;
-  int64_t tot = m.E - e0 < NB ? (m.E - e0) * Q : (int64_t)NB * Q;
+  const int64_t E = m.E, e0 = blockIdx.x * (int64_t)NB;
+  const int64_t tot = E - e0 < NB ? (E - e0) * Q : (int64_t)NB * Q;
   for (int64_t t = threadIdx.x; t < tot; t += blockDim.x) sh[t] = eps_q[e0 * Q + t];
   __syncthreads();
-  int64_t e = e0 + threadIdx.x;
-  if (e >= m.E) return;
+  const int64_t e = e0 + threadIdx.x;
+  if (e >= E) return;
   T B[NQ][NQ];  // B[a][q] = l_a(g_q) w_q
 #pragma unroll
   for (int a = 0; a < NQ; ++a)
@@ -88,12 +96,7 @@ k_rhs(MeshDev m, Tables tb, const T* __restrict__ eps_q, double* __restrict__ b)
         for (int qy = 0; qy < NQ; ++qy) s += B[bb][qy] * t1[qz][qy][a];
         t2[qz][bb][a] = s;
       }
-  int ex = (int)(e % m.ne[0]);
-  int ey = (int)((e / m.ne[0]) % m.ne[1]);
-  int ez = (int)(e / ((int64_t)m.ne[0] * m.ne[1]));
-  int64_t nx = m.nn[0], nxy = (int64_t)m.nn[0] * m.nn[1];
-  int64_t base = (int64_t)ex * K + nx * ((int64_t)ey * K) + nxy * ((int64_t)ez * K);
-  double detJ = m.Ve;
+  const T detJ = (T)m.Ve;
 #pragma unroll
   for (int c = 0; c < NQ; ++c)
 #pragma unroll
@@ -103,25 +106,80 @@ k_rhs(MeshDev m, Tables tb, const T* __restrict__ eps_q, double* __restrict__ b)
         T s = 0;
 #pragma unroll
         for (int qz = 0; qz < NQ; ++qz) s += B[c][qz] * t2[qz][bb][a];
-        atomicAdd(b + base + a + nx * bb + nxy * c, (double)s * detJ);
+        local[(a + NQ * (bb + NQ * c)) * E + e] = s * detJ;
       }
 }
 
+// b_j = sum of the element contributions to node j, added in a fixed order
+// (elements ascending) in the path's precision T and stored in FP64.  One
+// thread per element writes the nodes the element owns: local indices
+// 0..k-1 along each axis, and k on the last element of an axis.  A node with
+// local index 0 along an axis also takes the contribution of the element
+// before it on that axis (local index k there), so a node sums one to eight
+// slots.  Grid: x along a row of elements (element index fastest, so that
+// for every slot neighbouring threads read neighbouring words of local[j][.]),
+// y over e_y, z over e_z (both strided when the mesh exceeds the grid).
+template <int K, typename T>
+__global__ void __launch_bounds__(32)
+k_rhs_gather(MeshDev m, const T* __restrict__ local, double* __restrict__ b) {
+  constexpr int NQ = K + 1;
+  const int ex = blockIdx.x * 32 + threadIdx.x;
+  const int nex = m.ne[0], ney = m.ne[1], nez = m.ne[2];
+  if (ex >= nex) return;
+  const int64_t E = m.E, sy = nex, sz = (int64_t)nex * ney;
+  const int64_t nx = m.nn[0], nxy = (int64_t)m.nn[0] * m.nn[1];
+  const bool lastx = ex == nex - 1, px = ex > 0;
+  for (int ez = blockIdx.z; ez < nez; ez += gridDim.z) {
+    const bool lastz = ez == nez - 1, pz = ez > 0;
+    for (int ey = blockIdx.y; ey < ney; ey += gridDim.y) {
+      const bool lasty = ey == ney - 1, py = ey > 0;
+      const int64_t e = ex + sy * ey + sz * ez;
+      const T* pe = local + e;
+      double* be = b + (int64_t)ex * K + nx * ((int64_t)ey * K) + nxy * ((int64_t)ez * K);
+#pragma unroll
+      for (int c = 0; c < NQ; ++c) {
+        if (c == K && !lastz) continue;
+#pragma unroll
+        for (int bb = 0; bb < NQ; ++bb) {
+          if (bb == K && !lasty) continue;
+#pragma unroll
+          for (int a = 0; a < NQ; ++a) {
+            if (a == K && !lastx) continue;
+            T s = 0;
+#pragma unroll
+            for (int q = 7; q >= 0; --q) {  // (dz, dy, dx) = bits of q: elements ascending
+              const int dx = q & 1, dy = (q >> 1) & 1, dz = q >> 2;
+              if ((dx && !(a == 0 && px)) || (dy && !(bb == 0 && py)) || (dz && !(c == 0 && pz)))
+                continue;
+              const int jj = (a + K * dx) + NQ * ((bb + K * dy) + NQ * (c + K * dz));
+              s += __ldg(pe + jj * E - (dx + sy * dy + sz * dz));
+            }
+            be[a + nx * bb + nxy * c] = (double)s;
+          }
+        }
+      }
+    }
+  }
+}
+
 cudaError_t launch_rhs(const MeshDev& m, const Tables& t, const double* eps_q64,
-                       const float* eps_q32, double* b, cudaStream_t s) {
-  cudaError_t err = cudaMemsetAsync(b, 0, sizeof(double) * m.n_nodes, s);
-  if (err != cudaSuccess) return err;
-#define CFDEM_RHS(KK)                                                                  \
-  if (m.k == KK) {                                                                     \
-    if (eps_q32) {                                                                     \
-      constexpr int nb = rhs_block<KK, float>();                                       \
-      k_rhs<KK, float><<<(unsigned)((m.E + nb - 1) / nb), nb, 0, s>>>(m, t, eps_q32, b); \
-    } else {                                                                           \
-      constexpr int nb = rhs_block<KK, double>();                                      \
-      k_rhs<KK, double><<<(unsigned)((m.E + nb - 1) / nb), nb, 0, s>>>(m, t, eps_q64, b); \
-    }                                                                                  \
-    count_launches(1);                                                                 \
-    return cudaGetLastError();                                                         \
+                       const float* eps_q32, double* local, double* b, cudaStream_t s) {
+  const dim3 g((unsigned)((m.ne[0] + 31) / 32), (unsigned)std::min(m.ne[1], 65535),
+               (unsigned)std::min(m.ne[2], 65535));
+#define CFDEM_RHS(KK)                                                                       \
+  if (m.k == KK) {                                                                          \
+    if (eps_q32) {                                                                          \
+      constexpr int nb = rhs_block<KK, float>();                                            \
+      float* lf = reinterpret_cast<float*>(local);                                          \
+      k_rhs<KK, float><<<(unsigned)((m.E + nb - 1) / nb), nb, 0, s>>>(m, t, eps_q32, lf);   \
+      k_rhs_gather<KK, float><<<g, 32, 0, s>>>(m, lf, b);                                   \
+    } else {                                                                                \
+      constexpr int nb = rhs_block<KK, double>();                                           \
+      k_rhs<KK, double><<<(unsigned)((m.E + nb - 1) / nb), nb, 0, s>>>(m, t, eps_q64, local); \
+      k_rhs_gather<KK, double><<<g, 32, 0, s>>>(m, local, b);                               \
+    }                                                                                       \
+    count_launches(2);                                                                      \
+    return cudaGetLastError();                                                              \
   }
   CFDEM_RHS(1)
   CFDEM_RHS(2)

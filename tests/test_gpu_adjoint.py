@@ -64,7 +64,8 @@ def _directional(m, prm, c, dx, du, g_f, g_fd, g_eps):
     return s
 
 
-@pytest.mark.parametrize("k,precision,drag", [(1, 0, 0), (2, 0, 0), (3, 0, 1), (2, 1, 0)])
+@pytest.mark.parametrize("k,precision,drag", [(1, 0, 0), (2, 0, 0), (3, 0, 1), (2, 1, 0),
+                                               (2, 0, 2), (1, 0, 3), (2, 0, 4), (2, 1, 5)])
 def test_adjoint_matches_oracle_directional_derivatives(k, precision, drag):
     c = _case(600 + k, k)
     m = O.Mesh(c["origin"], c["extent"], c["n_el"], c["k"])
@@ -91,6 +92,33 @@ def test_adjoint_matches_oracle_directional_derivatives(k, precision, drag):
         got = float(np.sum(dJdu * du))
         scale = np.linalg.norm(dJdu) * np.linalg.norm(du)
         assert abs(got - want) <= TOL[precision] * scale
+
+
+@pytest.mark.parametrize("k,precision", [(1, 0), (2, 0), (3, 0), (2, 1)])
+def test_adjoint_with_shear_force(k, precision):
+    """The shear force in a viscous liquid with a rough velocity field: its
+    weights reach dJ/du, its third derivatives dJ/dx."""
+    c = _case(700 + k, k)
+    rng = np.random.default_rng(3 + k)
+    c["u_nodal"] = c["u_nodal"] * (1.0 + 0.3 * rng.standard_normal(c["u_nodal"].shape))
+    m = O.Mesh(c["origin"], c["extent"], c["n_el"], c["k"])
+    prm = dict(c["params"], precision=precision, shear_force=1, mu_f=1e-3,
+               cg_rtol=1e-13 if precision == 0 else 1e-12)
+    n = c["x"].shape[0]
+    g_f = rng.standard_normal((n, 3))
+    dJdx, dJdu, _ = _gpu(c, prm, g_f, None, None)
+    ref = np.zeros((n, 3))
+    for i in range(n):
+        for a in range(3):
+            dx = np.zeros((n, 3))
+            dx[i, a] = 1.0
+            ref[i, a] = _directional(m, prm, c, dx, None, g_f, None, None)
+    assert rel_err(dJdx, ref) <= TOL[precision]
+    for t in range(3):
+        du = rng.standard_normal(c["u_nodal"].shape)
+        want = _directional(m, prm, c, None, du, g_f, None, None)
+        got = float(np.sum(dJdu * du))
+        assert abs(got - want) <= TOL[precision] * np.linalg.norm(dJdu) * np.linalg.norm(du)
 
 
 def test_mass_apply_matches_oracle():

@@ -182,10 +182,13 @@ def test_rhs_and_operator(c):
     with _ctx(case) as ctx:
         b = _zeros(m.n_nodes())
         y = _zeros(m.n_nodes())
+        b2 = _zeros(m.n_nodes())
         cf.cfdem_project_rhs(ctx.h, dev(eps_q), b)
+        cf.cfdem_project_rhs(ctx.h, dev(eps_q), b2)
         cf.cfdem_apply(ctx.h, dev(xv), y)
         cf.cfdem_synchronize(ctx.h)
     assert rel_err(host(b), O.rhs(m, eps_q)) <= 1e-12
+    assert np.array_equal(host(b), host(b2))  # no atomics: reproducible bit for bit
     assert np.max(np.abs(host(y) - O.apply(m, L2, xv))) <= 1e-12 * np.max(np.abs(O.apply(m, L2, xv)))
 
 
@@ -212,7 +215,8 @@ def test_projection(c, precision, precond):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("drag,vans,boe", [(0, 0, 0), (1, 1, 0), (0, 1, 1)])
+@pytest.mark.parametrize("drag,vans,boe", [(0, 0, 0), (1, 1, 0), (0, 1, 1), (2, 0, 0),
+                                            (3, 1, 0), (4, 0, 1), (5, 1, 1), (4, 1, 0)])
 @pytest.mark.parametrize("c", CASES)
 def test_forces(c, drag, vans, boe, precision):
     case = _case(*c)
@@ -339,3 +343,37 @@ def test_full_size_q2_bed(bed, precision, precond):
     assert rel_err(host(f), fo["f"]) <= tol
     assert rel_err(host(fd), fo["f_drag"]) <= tol
     assert rel_err(host(Fe), F_ref) <= tol
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("vans", [0, 1])
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_forces_with_shear(k, vans, precision):
+    """Shear force -V_p div tau (second derivatives of the Q_k velocity) in a
+    viscous liquid with a rough velocity field, where it is not negligible:
+    f and the fluid source against the oracle, and the shear part alone
+    (f with it minus f without it) against the oracle's shear force."""
+    case = _case(*[c for c in CASES if c[2] == k][0])
+    m = _mesh(case)
+    rng = np.random.default_rng(30 + k)
+    u = case["u_nodal"] * (1.0 + 0.3 * rng.standard_normal(case["u_nodal"].shape))
+    eps_n = 0.3 + 0.7 * rng.random(m.n_nodes())
+    prm = dict(case["params"], mu_f=1e-3, vans_model=vans, precision=precision)
+    n = case["x"].shape[0]
+    out = {}
+    for shear in (0, 1):
+        with _ctx(case, **dict(prm, shear_force=shear)) as ctx:
+            f, fd, Fe = _zeros(n, 3), _zeros(n, 3), _zeros(m.n_elem, 3)
+            cf.cfdem_forces(ctx.h, n, dev(case["x"]), dev(case["r"]), dev(case["u_p"]), dev(u),
+                            dev(case["p_nodal"]), dev(eps_n), f, fd, Fe, None)
+            cf.cfdem_synchronize(ctx.h)
+            out[shear] = (host(f), host(fd), host(Fe))
+    ref = O.forces(m, dict(prm, shear_force=1), case["x"], case["r"], case["u_p"], u,
+                   case["p_nodal"], eps_n)
+    F_ref, _ = O.fluid_source(m, vans, case["x"], ref["f_drag"], ref["f_gradp"], ref["f_shear"])
+    tol = TOL[precision]
+    assert rel_err(out[1][0], ref["f"]) <= tol
+    assert rel_err(out[1][2], F_ref) <= tol
+    assert np.array_equal(out[1][1], out[0][1])          # the drag does not change
+    fs = out[1][0] - out[0][0]
+    assert rel_err(fs, ref["f_shear"]) <= (1e-9 if precision == 0 else 2e-4)

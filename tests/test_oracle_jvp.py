@@ -144,3 +144,46 @@ def test_loss_derivative_matches_central_difference():
     t = 1e-6
     fd = (loss(t) - loss(-t)) / (2 * t)
     assert dJ == pytest.approx(fd, rel=1e-6)
+
+
+@pytest.mark.parametrize("drag", [2, 3, 4, 5])
+def test_other_closures_primal_and_tangents(drag):
+    """Rong, Koch-Hill, Gidaspow, Beetstra: the dual primal is the C oracle's
+    step and the tangents its central differences (the seeded void
+    fractions stay clear of the Gidaspow and Koch-Hill branch points)."""
+    c = _case(40 + drag, k=2, rough_p=True)
+    m = _mesh(c)
+    prm = dict(c["params"], drag_model=drag, beta_over_eps=drag % 2)
+    ref = O.coupling_step(m, prm, c["x"], c["r"], c["u_p"], c["u_nodal"], c["p_nodal"])
+    rng = np.random.default_rng(5)
+    dx = rng.standard_normal(c["x"].shape) * c["r"][:, None]
+    du = rng.standard_normal(c["u_nodal"].shape)
+    out = J.coupling_jvp(m, prm, c["x"], c["r"], c["u_p"], c["u_nodal"], c["p_nodal"], dx, du)
+    for key in ("f", "f_drag"):
+        scale = np.abs(ref[key]).max()
+        assert np.abs(out[key].v - ref[key]).max() <= 1e-11 * scale, key
+    fd = _fd(m, prm, c, dx, du, 1e-6)
+    for key in ("f", "f_drag"):
+        assert _rel(out[key].t, fd[key]) <= 2e-6, key
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_shear_force_primal_and_tangents(k):
+    """The shear force (second derivatives of the Q_k velocity at the
+    particle): dual primal = C oracle, tangents = central differences."""
+    c = _case(50 + k, k=k, rough_p=True)
+    m = _mesh(c)
+    rng = np.random.default_rng(6)
+    c["u_nodal"] = c["u_nodal"] * (1.0 + 0.3 * rng.standard_normal(c["u_nodal"].shape))
+    prm = dict(c["params"], shear_force=1, mu_f=1e-3)
+    ref = O.coupling_step(m, prm, c["x"], c["r"], c["u_p"], c["u_nodal"], c["p_nodal"])
+    dx = rng.standard_normal(c["x"].shape) * c["r"][:, None]
+    du = rng.standard_normal(c["u_nodal"].shape)
+    out = J.coupling_jvp(m, prm, c["x"], c["r"], c["u_p"], c["u_nodal"], c["p_nodal"], dx, du)
+    assert np.abs(out["f_shear"].v - ref["f_shear"]).max() <= 1e-11 * np.abs(ref["f_shear"]).max()
+    fd = _fd(m, prm, c, dx, du, 1e-6)
+    sh = lambda o: o["f_shear"]  # noqa: E731
+    p, q = (O.coupling_step(m, dict(prm, oracle_rtol=1e-15), c["x"] + s * dx, c["r"], c["u_p"],
+                            c["u_nodal"] + s * du, c["p_nodal"]) for s in (1e-6, -1e-6))
+    assert _rel(out["f_shear"].t, (sh(p) - sh(q)) / 2e-6) <= 2e-6
+    assert _rel(out["f"].t, fd["f"]) <= 2e-6
