@@ -81,6 +81,13 @@ typedef struct {
                               Eq. (stress), second derivatives of the Q_k velocity
                               at the particle) to f, and for model B to the fluid
                               source; default 0 */
+    int fluid_drag;        /* drag on the fluid side: 0 = explicit, F_pf,e = -(1/V_e)
+                              sum_{i in e} f_D,i per element (Eqs. fa/fb); 1 = the
+                              fluid-side form of Sec. 2.3.2, F_pf(x_q) = -beta_e
+                              (u_f(x_q) - u_p,avg,e) with beta_e = (1/V_e) sum_i beta_i
+                              and u_p,avg,e the plain mean particle velocity in e
+                              (F_q then varies over the element; F_elem is its Gauss
+                              average; see cfdem_fluid_drag_coefficients); default 0 */
 } cfdem_params;
 
 /* Counters of the last calls on a context. */
@@ -189,18 +196,31 @@ cfdem_status cfdem_project(cfdem_t ctx, const double *eps_q_dev, double *eps_nod
 /* Steps a6-a7 -- particle forces and fluid source.  Per particle i: u_f,
  * eps (Q_k) and grad p (Q_kp) interpolated at x_i; eps_c clamped to
  * [eps_floor, 1] for the closures; Re_p = rho_f eps_c |u_f - u_p| d_p /
- * mu_f; f_D = 1/2 rho_f C_D pi r^2 |U| U (Dallavalle, or Di Felice's
- * C_D eps_c^(2 - chi)), divided by eps_c if beta_over_eps; f_B = -rho_f V_p
- * g; f_gradp = -V_p grad p; f = f_D + f_B + f_gradp.  Fluid source per
- * element F_e = -(1/V_e) sum_{i in e} S_i with S_i = f_D (model A) or f_D +
- * f_gradp (model B).  Outputs (device): f_dev[n][3] required; f_drag_dev
- * [n][3], F_elem_dev[E][3] and F_q_dev[E][Q][3] (F_e at every quadrature
- * point) optional. */
+ * mu_f; f_D = beta_i (u_f - u_p) with the closure of drag_model (Sec.
+ * 2.3.2), divided by eps_c if beta_over_eps; f_B = -rho_f V_p g; f_gradp =
+ * -V_p grad p; f_shear = -V_p div tau if shear_force; f = f_D + f_B +
+ * f_gradp (+ f_shear).  Fluid source per element F_e = -(1/V_e) sum_{i in
+ * e} S_i with S_i = f_D (model A) or f_D + f_gradp (+ f_shear) (model B);
+ * with fluid_drag = 1 the drag part is -beta_e (u_f(x_q) - u_p,avg,e) at
+ * each quadrature point instead.  Outputs (device): f_dev[n][3] required;
+ * f_drag_dev [n][3], F_elem_dev[E][3] and F_q_dev[E][Q][3] (the source at
+ * every quadrature point) optional. */
 cfdem_status cfdem_forces(cfdem_t ctx, int64_t n, const double *x_dev, const double *r_dev,
                           const double *u_p_dev, const double *u_nodal_dev,
                           const double *p_nodal_dev, const double *eps_nodal_dev,
                           double *f_dev, double *f_drag_dev, double *F_elem_dev,
                           double *F_q_dev);
+
+/* The per-element coefficients of the fluid-side drag (fluid_drag = 1,
+ * Sec. 2.3.2) from the last cfdem_forces / cfdem_coupling_step on this
+ * context: beta_e[E] = (1/V_e) sum_{i in e} beta_i, beta_i the drag
+ * coefficient of particle i (f_D,i = beta_i (u_f(x_i) - u_p,i)), and
+ * up_avg[E][3] the mean velocity of the particles in e (0 in an empty
+ * element), for a fluid solver that treats -beta_e (u_f - u_p,avg) in its
+ * own (implicit) assembly.  Device pointers; either may be NULL.  Stream
+ * ordered.  CFDEM_ESTATE if no forces call with fluid_drag = 1 ran since the
+ * mesh was set. */
+cfdem_status cfdem_fluid_drag_coefficients(cfdem_t ctx, double *beta_e, double *up_avg);
 
 /* Steps a1-a7 in one call: void fraction, projection (eps_nodal_dev is the
  * start vector and receives eps_h), forces and fluid source.  Outputs as in

@@ -32,6 +32,9 @@
  *   or_shear_force     the shear term -V_p div tau, Eq. (stress)
  *   or_fluid_source    F_pf of Eqs. (fb)/(fa), with the minus sign that
  *                      Newton's third law requires (Sec. 2.3.2)
+ *   or_fluid_source_semi  the same with the fluid-side drag of Sec. 2.3.2
+ *                      (fluid velocity at the quadrature point, cell-mean
+ *                      particle velocity)
  * Parity is pinned by the tests: closed forms, limits, brute force,
  * conservation laws and the worked numbers the paper prints.
  */
@@ -930,6 +933,108 @@ int64_t or_fluid_source(const double *origin, const double *extent, const int *n
     }
     for (int64_t e = 0; e < 3 * E; ++e) F_e[e] = -S[e] / Ve;
     free(S);
+    free(elem);
+    return bad;
+}
+
+/* Fluid source with the fluid-side drag of Sec. 2.3.2 (the single-particle
+ * drag written with the fluid velocity at the quadrature point and the mean
+ * particle velocity of the cell):
+ *   F_pf(x_q) = -beta_e (u_f(x_q) - u_p,avg,e) - (1/V_e) sum_{i in e} T_i,
+ * beta_e = (1/V_e) sum_{i in e} beta_i, beta_i the particle's drag
+ * coefficient (f_D,i = beta_i (u_f(x_i) - u_p,i)), u_p,avg,e the plain mean
+ * of the particle velocities in e, T_i = 0 (model A) or f_gradp,i (+
+ * f_shear,i when given) (model B).  beta_i is recovered from f_D,i and the
+ * slip at the particle (Q_k interpolation of u at x_i).  An element without
+ * particles has beta_e = 0.  F_q[E][Q][3] with q = qx + nq (qy + nq qz);
+ * F_e[E][3] is the Gauss average of F_q (the element mean of F_pf). */
+int64_t or_fluid_source_semi(const double *origin, const double *extent, const int *n_el,
+                             int k, int vans_model, int64_t n, const double *x,
+                             const double *u_p, const double *u_nodal, const double *f_drag,
+                             const double *f_gradp, const double *f_shear, double *F_q,
+                             double *F_e)
+{
+    omesh m = make_mesh(origin, extent, n_el, k);
+    int64_t E = n_elem(&m);
+    int nq = k + 1, Q = nq * nq * nq;
+    double Ve = m.h[0] * m.h[1] * m.h[2];
+    double z[8], g[8], w[8];
+    or_gll_nodes(k, z);
+    or_gauss_rule(nq, g, w);
+    int32_t *elem = (int32_t *)malloc(sizeof(int32_t) * (n > 0 ? n : 1));
+    double *xi = (double *)malloc(sizeof(double) * 3 * (n > 0 ? n : 1));
+    int64_t bad = or_locate(origin, extent, n_el, k, n, x, elem, xi);
+    double *B = (double *)calloc(E, sizeof(double));
+    double *U = (double *)calloc(3 * E, sizeof(double));
+    double *T = (double *)calloc(3 * E, sizeof(double));
+    double *cnt = (double *)calloc(E, sizeof(double));
+    for (int64_t i = 0; i < n; ++i) {
+        if (elem[i] < 0) continue;
+        int64_t e = elem[i];
+        int ie[3] = {(int)(e % m.ne[0]), (int)((e / m.ne[0]) % m.ne[1]),
+                     (int)(e / ((int64_t)m.ne[0] * m.ne[1]))};
+        double lx[8], ly[8], lz[8];
+        lagrange(k, z, xi[3 * i], lx, NULL);
+        lagrange(k, z, xi[3 * i + 1], ly, NULL);
+        lagrange(k, z, xi[3 * i + 2], lz, NULL);
+        double uf[3] = {0.0, 0.0, 0.0};
+        for (int c = 0; c <= k; ++c)
+        for (int b = 0; b <= k; ++b)
+        for (int a = 0; a <= k; ++a) {
+            int64_t nd = gnode(&m, k, ie[0], ie[1], ie[2], a, b, c);
+            for (int d = 0; d < 3; ++d) uf[d] += lx[a] * ly[b] * lz[c] * u_nodal[3 * nd + d];
+        }
+        double slip[3], num = 0.0, den = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            slip[d] = uf[d] - u_p[3 * i + d];
+            num += f_drag[3 * i + d] * slip[d];
+            den += slip[d] * slip[d];
+        }
+        B[e] += den > 0.0 ? num / den : 0.0;
+        cnt[e] += 1.0;
+        for (int d = 0; d < 3; ++d) {
+            U[3 * e + d] += u_p[3 * i + d];
+            double t = 0.0;
+            if (vans_model == 1) t += f_gradp[3 * i + d];
+            if (vans_model == 1 && f_shear) t += f_shear[3 * i + d];
+            T[3 * e + d] += t;
+        }
+    }
+    for (int64_t e = 0; e < E; ++e) {
+        int ie[3] = {(int)(e % m.ne[0]), (int)((e / m.ne[0]) % m.ne[1]),
+                     (int)(e / ((int64_t)m.ne[0] * m.ne[1]))};
+        double beta = B[e] / Ve, upa[3] = {0.0, 0.0, 0.0};
+        if (cnt[e] > 0.0)
+            for (int d = 0; d < 3; ++d) upa[d] = U[3 * e + d] / cnt[e];
+        double mean[3] = {0.0, 0.0, 0.0};
+        for (int qz = 0; qz < nq; ++qz)
+        for (int qy = 0; qy < nq; ++qy)
+        for (int qx = 0; qx < nq; ++qx) {
+            double lx[8], ly[8], lz[8];
+            lagrange(k, z, g[qx], lx, NULL);
+            lagrange(k, z, g[qy], ly, NULL);
+            lagrange(k, z, g[qz], lz, NULL);
+            double uf[3] = {0.0, 0.0, 0.0};
+            for (int c = 0; c <= k; ++c)
+            for (int b = 0; b <= k; ++b)
+            for (int a = 0; a <= k; ++a) {
+                int64_t nd = gnode(&m, k, ie[0], ie[1], ie[2], a, b, c);
+                for (int d = 0; d < 3; ++d) uf[d] += lx[a] * ly[b] * lz[c] * u_nodal[3 * nd + d];
+            }
+            int q = qx + nq * (qy + nq * qz);
+            for (int d = 0; d < 3; ++d) {
+                double F = -beta * (uf[d] - upa[d]) - T[3 * e + d] / Ve;
+                F_q[(e * Q + q) * 3 + d] = F;
+                mean[d] += w[qx] * w[qy] * w[qz] * F;
+            }
+        }
+        for (int d = 0; d < 3; ++d) F_e[3 * e + d] = mean[d];
+    }
+    free(cnt);
+    free(T);
+    free(U);
+    free(B);
+    free(xi);
     free(elem);
     return bad;
 }

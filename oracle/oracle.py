@@ -96,6 +96,9 @@ def lib():
                                     dp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
             L.or_forces.restype = i64
             L.or_fluid_source.argtypes = [dp, dp, ip, cint, cint, i64, dp, dp, dp, dp, dp]
+            L.or_fluid_source_semi.argtypes = [dp, dp, ip, cint, cint, i64, dp, dp, dp, dp, dp,
+                                               dp, dp, dp]
+            L.or_fluid_source_semi.restype = i64
             L.or_fluid_source.restype = i64
             L.or_num_threads.restype = cint
             L.or_set_num_threads.argtypes = [cint]
@@ -527,6 +530,26 @@ def fluid_source(mesh: Mesh, vans_model, x, f_drag, f_gradp, f_shear=None):
     return F, int(bad)
 
 
+def fluid_source_semi(mesh: Mesh, vans_model, x, u_p, u_nodal, f_drag, f_gradp, f_shear=None):
+    """Fluid source with the fluid-side drag -beta_e (u_f(x_q) - u_p,avg,e):
+    (F_q [E][Q][3], F_e [E][3] the element mean, first out-of-domain index)."""
+    x, px = _d(x)
+    up, pup = _d(u_p)
+    un, pun = _d(u_nodal)
+    fd, pfd = _d(f_drag)
+    fg, pfg = _d(f_gradp)
+    if f_shear is not None:
+        fs, pfs = _d(f_shear)
+    else:
+        pfs = None
+    Fq = np.zeros((mesh.n_elem, mesh.Q, 3))
+    Fe = np.zeros((mesh.n_elem, 3))
+    dp = C.POINTER(C.c_double)
+    bad = lib().or_fluid_source_semi(*mesh.args(), int(vans_model), x.shape[0], px, pup, pun,
+                                     pfd, pfg, pfs, Fq.ctypes.data_as(dp), Fe.ctypes.data_as(dp))
+    return Fq, Fe, int(bad)
+
+
 def coupling_step(mesh: Mesh, params: dict, x, r, u_p, u_nodal, p_nodal, eps0=None):
     """The whole coupling step in FP64: void fraction (QCM or PCM), smoothed
     projection (Jacobi-PCG), forces and fluid source."""
@@ -539,10 +562,14 @@ def coupling_step(mesh: Mesh, params: dict, x, r, u_p, u_nodal, p_nodal, eps0=No
     L2 = float(params.get("l2_smoothing", 0.0))
     eps_h, it, res = cg(mesh, L2, b, x0=eps0, rtol=float(params.get("oracle_rtol", 1e-14)))
     fo = forces(mesh, params, x, r, u_p, u_nodal, p_nodal, eps_h)
-    F, _ = fluid_source(mesh, int(params.get("vans_model", 0)), x, fo["f_drag"], fo["f_gradp"],
-                        fo.get("f_shear"))
-    return {"eps_q": eps_q, "b": b, "eps_h": eps_h, "cg_iters": it, "cg_relres": res,
-            **fo, "F_e": F}
+    vans = int(params.get("vans_model", 0))
+    out = {"eps_q": eps_q, "b": b, "eps_h": eps_h, "cg_iters": it, "cg_relres": res, **fo}
+    if params.get("fluid_drag", 0):
+        out["F_q"], out["F_e"], _ = fluid_source_semi(mesh, vans, x, u_p, u_nodal, fo["f_drag"],
+                                                       fo["f_gradp"], fo.get("f_shear"))
+    else:
+        out["F_e"], _ = fluid_source(mesh, vans, x, fo["f_drag"], fo["f_gradp"], fo.get("f_shear"))
+    return out
 
 
 def num_threads():

@@ -35,7 +35,7 @@ class cfdem_params(C.Structure):
                 ("precision", C.c_int), ("cg_rtol", C.c_double), ("cg_maxit", C.c_int),
                 ("eps_floor", C.c_double), ("pressure_degree", C.c_int),
                 ("max_radius", C.c_double), ("bin_edge", C.c_double),
-                ("cg_precond", C.c_int), ("shear_force", C.c_int)]
+                ("cg_precond", C.c_int), ("shear_force", C.c_int), ("fluid_drag", C.c_int)]
 
 
 class cfdem_stats(C.Structure):
@@ -96,6 +96,7 @@ def lib():
     L.cfdem_apply.argtypes = [vp, vp, vp]
     L.cfdem_project.argtypes = [vp, vp, vp]
     L.cfdem_forces.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.cfdem_fluid_drag_coefficients.argtypes = [vp, vp, vp]
     L.cfdem_coupling_step.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.cfdem_synchronize.argtypes = [vp]
     L.cfdem_get_stats.argtypes = [vp, C.POINTER(cfdem_stats)]
@@ -209,6 +210,10 @@ def cfdem_forces(h, n, x, r, u_p, u_nodal, p_nodal, eps_nodal, f, f_drag=None, F
     return _check(h, lib().cfdem_forces(h, int(n), _ptr(x), _ptr(r), _ptr(u_p), _ptr(u_nodal),
                                         _ptr(p_nodal), _ptr(eps_nodal), _ptr(f), _ptr(f_drag),
                                         _ptr(F_elem), _ptr(F_q)))
+
+
+def cfdem_fluid_drag_coefficients(h, beta_e=None, up_avg=None):
+    return _check(h, lib().cfdem_fluid_drag_coefficients(h, _ptr(beta_e), _ptr(up_avg)))
 
 
 def cfdem_coupling_step(h, n, x, r, u_p, u_nodal, p_nodal, eps_nodal, f, f_drag=None,

@@ -115,7 +115,13 @@ ForceParams force_params(const cfdem_ctx* c) {
   fp.beta_over_eps = c->prm.beta_over_eps;
   fp.vans_model = c->prm.vans_model;
   fp.shear = c->prm.shear_force;
+  fp.fluid_drag = c->prm.fluid_drag;
   return fp;
+}
+
+SemiAcc semi_acc(const cfdem_ctx* c) {
+  const int64_t E = c->mesh.E;
+  return SemiAcc{c->semi, c->semi + E, c->semi + 4 * E};
 }
 
 #define CK(expr, where)                                  \
@@ -312,7 +318,7 @@ void free_mesh_arena(cfdem_t c) {
                 c->cg.q0, c->cg.q1, c->cg.Aq, c->cg.dinv32, c->cg.d32, c->cg.partials,
                 c->cg.sc, c->cg.zn, c->cg.zn32, c->cg.rin32, c->cg.x_df, c->cg.r_df,
                 c->cg.b_df, c->cg.Ap_df, c->cg.p0_df, c->cg.p1_df, c->adj_geps,
-                c->adj_lam, c->adj_gq, c->rhs_local};
+                c->adj_lam, c->adj_gq, c->rhs_local, c->semi};
   for (void* p : ps)
     if (p) cudaFree(p);
   c->eps64 = nullptr;
@@ -322,6 +328,8 @@ void free_mesh_arena(cfdem_t c) {
   c->vol = nullptr;
   c->adj_geps = c->adj_lam = c->adj_gq = nullptr;
   c->rhs_local = nullptr;
+  c->semi = nullptr;
+  c->semi_valid = 0;
   FdmPlan* keep = c->cg.fdm;
   const df64* kb = c->cg.bands_df;
   c->cg = CgWork{};
@@ -338,6 +346,8 @@ cfdem_status alloc_mesh_arena(cfdem_t c) {
   CK(grow(&c->S, 3 * m.E), "mesh arena");
   CK(grow(&c->vol, m.E), "mesh arena");
   CK(grow(&c->rhs_local, m.E * (int64_t)(m.k + 1) * (m.k + 1) * (m.k + 1)), "mesh arena");
+  CK(grow(&c->semi, 5 * m.E), "mesh arena");
+  c->semi_valid = 0;
   CgWork& w = c->cg;
   CK(grow(&w.r, nn), "cg");
   CK(grow(&w.z, nn), "cg");
@@ -480,6 +490,7 @@ void cfdem_params_default(cfdem_params* p) {
   p->eps_floor = 0.05;
   p->cg_precond = 1;
   p->shear_force = 0;
+  p->fluid_drag = 0;
 }
 
 cfdem_status cfdem_create(cfdem_t* out, int device, void* stream) {
@@ -587,6 +598,8 @@ cfdem_status cfdem_set_params(cfdem_t c, const cfdem_params* p) {
     return fail(c, CFDEM_EINVAL, "cg_precond must be 0 (Jacobi) or 1 (FDM)");
   if (p->shear_force < 0 || p->shear_force > 1)
     return fail(c, CFDEM_EINVAL, "shear_force must be 0 or 1");
+  if (p->fluid_drag < 0 || p->fluid_drag > 1)
+    return fail(c, CFDEM_EINVAL, "fluid_drag must be 0 (explicit) or 1 (fluid-side form)");
   c->prm = *p;
   ++c->gen;
   return resolve(c);
@@ -716,18 +729,39 @@ cfdem_status cfdem_forces(cfdem_t c, int64_t n, const double* x, const double* r
     return fail(c, CFDEM_EINVAL, "null input");
   DeviceGuard g(c->device);
   const MeshDev& m = c->mesh;
-  bool want_src = F_elem || F_q;
+  const bool semi = c->prm.fluid_drag == 1;
+  const bool want_src = F_elem || F_q || semi;
   if (want_src) CK(cudaMemsetAsync(c->S, 0, sizeof(double) * 3 * m.E, c->stream), "forces");
+  if (semi) CK(cudaMemsetAsync(c->semi, 0, sizeof(double) * 5 * m.E, c->stream), "forces");
   c->timer.begin(kStageForces, c->stream);
   CK(launch_forces(m, c->tab, c->prm.precision, force_params(c), n, x, r, u_p, u_nodal,
-                   p_nodal, eps_nodal, f, f_drag, want_src ? c->S : nullptr, c->st, c->stream),
+                   p_nodal, eps_nodal, f, f_drag, want_src ? c->S : nullptr, semi_acc(c), c->st,
+                   c->stream),
      "forces");
   c->timer.end(kStageForces, c->stream);
-  if (want_src) {
+  if (F_elem || F_q) {
     c->timer.begin(kStageSource, c->stream);
-    CK(launch_fluid_source(m, c->S, F_elem, F_q, c->stream), "fluid source");
+    if (semi)
+      CK(launch_fluid_source_semi(m, c->tab, c->prm.precision, c->S, semi_acc(c), u_nodal,
+                                  F_elem, F_q, c->stream),
+         "fluid source");
+    else
+      CK(launch_fluid_source(m, c->S, F_elem, F_q, c->stream), "fluid source");
     c->timer.end(kStageSource, c->stream);
   }
+  c->semi_valid = semi ? 1 : 0;
+  return CFDEM_OK;
+}
+
+cfdem_status cfdem_fluid_drag_coefficients(cfdem_t c, double* beta_e, double* up_avg) {
+  cfdem_status s = need_mesh(c);
+  if (s != CFDEM_OK) return s;
+  if (!c->semi_valid)
+    return fail(c, CFDEM_ESTATE, "no forces call with fluid_drag = 1 since the mesh was set");
+  if (!beta_e && !up_avg) return CFDEM_OK;
+  DeviceGuard g(c->device);
+  CK(launch_drag_coefficients(c->mesh, semi_acc(c), beta_e, up_avg, c->stream),
+     "drag coefficients");
   return CFDEM_OK;
 }
 

@@ -43,6 +43,8 @@ struct cfdem_ctx {
   double* S = nullptr;         // per-element source accumulator [E][3]
   double* vol = nullptr;       // per-element particle volume (PCM)
   double* rhs_local = nullptr; // per-element right-hand-side contributions [(k+1)^3][E]
+  double* semi = nullptr;      // fluid-side drag sums: B [E], U [3E], N [E]
+  int semi_valid = 0;          // 1 once a forces call with fluid_drag = 1 filled them
   // adjoint arena (grown by the first cfdem_adjoint)
   double* adj_geps = nullptr;  // dJ/deps_h [n_nodes]
   double* adj_lam = nullptr;   // lambda = A^-1 dJ/deps_h [n_nodes]

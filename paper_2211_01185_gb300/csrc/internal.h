@@ -115,7 +115,13 @@ long long launches_total();
 struct ForceParams {
   double rho, mu, g[3], eps_floor;
   double inv_h[3];
-  int drag_model, beta_over_eps, vans_model, shear;
+  int drag_model, beta_over_eps, vans_model, shear, fluid_drag;
+};
+
+// Per-element accumulators of the fluid-side drag (fluid_drag = 1): sum of
+// the particles' drag coefficients, of their velocities [3], and their count.
+struct SemiAcc {
+  double *B, *U, *N;
 };
 
 // ---------------------------------------------------------------- launchers
@@ -126,13 +132,19 @@ cudaError_t launch_bin(const MeshDev& m, const BinDev& b, int64_t n, const doubl
                        const double* r, int32_t* bin_of, int32_t* slot, int32_t* bin_count,
                        int32_t* bin_start, int32_t* perm, int32_t* scan_tmp, double* xs64,
                        float* xs32, DevStatus* st, cudaStream_t s);
+// S_elem (and acc when fp.fluid_drag) accumulate per element; both may be null
 cudaError_t launch_forces(const MeshDev& m, const Tables& t, int precision, const ForceParams& fp,
                           int64_t n, const double* x, const double* r, const double* u_p,
                           const double* u_nodal, const double* p_nodal,
                           const double* eps_nodal, double* f, double* f_drag, double* S_elem,
-                          DevStatus* st, cudaStream_t s);
+                          SemiAcc acc, DevStatus* st, cudaStream_t s);
 cudaError_t launch_fluid_source(const MeshDev& m, const double* S_elem, double* F_elem,
                                 double* F_q, cudaStream_t s);
+cudaError_t launch_fluid_source_semi(const MeshDev& m, const Tables& t, int precision,
+                                     const double* S_elem, SemiAcc acc, const double* u_nodal,
+                                     double* F_elem, double* F_q, cudaStream_t s);
+cudaError_t launch_drag_coefficients(const MeshDev& m, SemiAcc acc, double* beta_e,
+                                     double* up_avg, cudaStream_t s);
 
 // voidfrac.cu
 cudaError_t launch_qcm(const MeshDev& m, const Tables& t, const BinDev& b, int precision,

@@ -331,7 +331,8 @@ k_forces(MeshDev m, Tables tb, ForceParams fp, int64_t n, const double* __restri
          const double* __restrict__ r, const double* __restrict__ u_p,
          const double* __restrict__ u_nodal, const double* __restrict__ p_nodal,
          const double* __restrict__ eps_nodal, double* __restrict__ f,
-         double* __restrict__ f_drag, double* __restrict__ S_elem, DevStatus* st) {
+         double* __restrict__ f_drag, double* __restrict__ S_elem, SemiAcc acc,
+         DevStatus* st) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   double p[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
@@ -421,9 +422,9 @@ k_forces(MeshDev m, Tables tb, ForceParams fp, int64_t n, const double* __restri
   T eps = (T)epsd;
   T epsc = eps < (T)fp.eps_floor ? (T)fp.eps_floor : eps;
   epsc = epsc > (T)1 ? (T)1 : epsc;
-  T fd0 = 0, fd1 = 0, fd2 = 0;
+  T fd0 = 0, fd1 = 0, fd2 = 0, coef = 0;
   if (speed > (T)0) {
-    const T coef = drag_coef<T, T>(fp, speed, epsc, rp);
+    coef = drag_coef<T, T>(fp, speed, epsc, rp);
     fd0 = coef * U0;
     fd1 = coef * U1;
     fd2 = coef * U2;
@@ -449,6 +450,14 @@ k_forces(MeshDev m, Tables tb, ForceParams fp, int64_t n, const double* __restri
   if (S_elem) {
     int64_t e = ie[0] + (int64_t)m.ne[0] * (ie[1] + (int64_t)m.ne[1] * ie[2]);
     T s0 = fd0, s1 = fd1, s2 = fd2;
+    if (fp.fluid_drag) {  // the drag goes to the fluid through beta_e and the mean u_p
+      s0 = s1 = s2 = (T)0;
+      atomicAdd(acc.B + e, (double)coef);
+      atomicAdd(acc.U + 3 * e, u_p[3 * i]);
+      atomicAdd(acc.U + 3 * e + 1, u_p[3 * i + 1]);
+      atomicAdd(acc.U + 3 * e + 2, u_p[3 * i + 2]);
+      atomicAdd(acc.N + e, 1.0);
+    }
     if (fp.vans_model == 1) {
       s0 += fg0;
       s1 += fg1;
@@ -465,10 +474,10 @@ static void launch_forces_t(const MeshDev& m, const Tables& t, const ForceParams
                             int64_t n, const double* x, const double* r, const double* u_p,
                             const double* u_nodal, const double* p_nodal,
                             const double* eps_nodal, double* f, double* f_drag, double* S,
-                            DevStatus* st, cudaStream_t s) {
+                            SemiAcc acc, DevStatus* st, cudaStream_t s) {
   int bs = 128;
   k_forces<K, KP, T><<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(
-      m, t, fp, n, x, r, u_p, u_nodal, p_nodal, eps_nodal, f, f_drag, S, st);
+      m, t, fp, n, x, r, u_p, u_nodal, p_nodal, eps_nodal, f, f_drag, S, acc, st);
   count_launches(1);
 }
 
@@ -476,16 +485,16 @@ cudaError_t launch_forces(const MeshDev& m, const Tables& t, int precision, cons
                           int64_t n, const double* x, const double* r, const double* u_p,
                           const double* u_nodal, const double* p_nodal,
                           const double* eps_nodal, double* f, double* f_drag, double* S_elem,
-                          DevStatus* st, cudaStream_t s) {
+                          SemiAcc acc, DevStatus* st, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
 #define CFDEM_FORCES(K, KP)                                                                  \
   if (m.k == K && m.kp == KP) {                                                              \
     if (precision == 0)                                                                      \
       launch_forces_t<K, KP, double>(m, t, fp, n, x, r, u_p, u_nodal, p_nodal, eps_nodal, f, \
-                                     f_drag, S_elem, st, s);                                 \
+                                     f_drag, S_elem, acc, st, s);                            \
     else                                                                                     \
       launch_forces_t<K, KP, float>(m, t, fp, n, x, r, u_p, u_nodal, p_nodal, eps_nodal, f,  \
-                                    f_drag, S_elem, st, s);                                  \
+                                    f_drag, S_elem, acc, st, s);                             \
     return cudaGetLastError();                                                               \
   }
   CFDEM_FORCES(1, 1)
@@ -548,6 +557,138 @@ cudaError_t launch_fluid_source(const MeshDev& m, const double* S_elem, double* 
                                                                     F_q);
   }
   count_launches((F_elem ? 1 : 0) + (F_q ? 1 : 0));
+  return cudaGetLastError();
+}
+
+// Fluid source with the fluid-side drag (Sec. 2.3.2: the drag written with
+// the fluid velocity at the quadrature point and the cell-mean particle
+// velocity), one thread per element:
+//   F_q = -beta_e (u_f(x_q) - u_p,avg) - S_e / V_e,  beta_e = B_e / V_e,
+// u_f at the Gauss points by sum-factorised interpolation of the nodal
+// velocity relative to u_p,avg (so that FP32 does not carry the mean),
+// S_e the model-B pressure (and shear) part.  F_e is the Gauss average.
+template <int K, typename T>
+__global__ void __launch_bounds__(128)
+k_fluid_source_semi(MeshDev m, Tables tb, const double* __restrict__ S, SemiAcc acc,
+                    const double* __restrict__ u_nodal, double* __restrict__ F_e,
+                    double* __restrict__ F_q) {
+  constexpr int NQ = K + 1, Q = NQ * NQ * NQ;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m.E) return;
+  const double inv_ve = 1.0 / m.Ve;
+  const double cnt = acc.N[e];
+  const double beta = acc.B[e] * inv_ve;
+  double upa[3] = {0.0, 0.0, 0.0};
+  if (cnt > 0.0)
+    for (int d = 0; d < 3; ++d) upa[d] = acc.U[3 * e + d] / cnt;
+  const int ex = (int)(e % m.ne[0]);
+  const int ey = (int)((e / m.ne[0]) % m.ne[1]);
+  const int ez = (int)(e / ((int64_t)m.ne[0] * m.ne[1]));
+  const int64_t nx = m.nn[0], nxy = (int64_t)m.nn[0] * m.nn[1];
+  const int64_t base = (int64_t)ex * K + nx * ((int64_t)ey * K) + nxy * ((int64_t)ez * K);
+  T L[NQ][NQ];  // L[q][a] = l_a(g_q)
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    T l[NQ];
+    lagrange<K, T>(tb.z, tb.lw, (T)tb.g[q], l, (T*)nullptr);
+#pragma unroll
+    for (int a = 0; a < NQ; ++a) L[q][a] = l[a];
+  }
+  const T bt = (T)beta;
+  double mean[3] = {0.0, 0.0, 0.0};
+#pragma unroll 1
+  for (int d = 0; d < 3; ++d) {
+    T v[NQ][NQ][NQ];  // [c][b][a]: u_j - u_p,avg
+#pragma unroll
+    for (int c = 0; c < NQ; ++c)
+#pragma unroll
+      for (int b = 0; b < NQ; ++b)
+#pragma unroll
+        for (int a = 0; a < NQ; ++a)
+          v[c][b][a] = (T)(__ldg(u_nodal + 3 * (base + a + nx * b + nxy * c) + d) - upa[d]);
+    T t1[NQ][NQ][NQ];  // [c][b][qx]
+#pragma unroll
+    for (int c = 0; c < NQ; ++c)
+#pragma unroll
+      for (int b = 0; b < NQ; ++b)
+#pragma unroll
+        for (int qx = 0; qx < NQ; ++qx) {
+          T s = 0;
+#pragma unroll
+          for (int a = 0; a < NQ; ++a) s += L[qx][a] * v[c][b][a];
+          t1[c][b][qx] = s;
+        }
+    T t2[NQ][NQ][NQ];  // [c][qy][qx]
+#pragma unroll
+    for (int c = 0; c < NQ; ++c)
+#pragma unroll
+      for (int qy = 0; qy < NQ; ++qy)
+#pragma unroll
+        for (int qx = 0; qx < NQ; ++qx) {
+          T s = 0;
+#pragma unroll
+          for (int b = 0; b < NQ; ++b) s += L[qy][b] * t1[c][b][qx];
+          t2[c][qy][qx] = s;
+        }
+    const double sv = -S[3 * e + d] * inv_ve;
+#pragma unroll
+    for (int qz = 0; qz < NQ; ++qz)
+#pragma unroll
+      for (int qy = 0; qy < NQ; ++qy)
+#pragma unroll
+        for (int qx = 0; qx < NQ; ++qx) {
+          T s = 0;
+#pragma unroll
+          for (int c = 0; c < NQ; ++c) s += L[qz][c] * t2[c][qy][qx];
+          const double F = (double)(-bt * s) + sv;
+          const int q = qx + NQ * (qy + NQ * qz);
+          if (F_q) F_q[(e * Q + q) * 3 + d] = F;
+          mean[d] += tb.w[qx] * tb.w[qy] * tb.w[qz] * F;
+        }
+  }
+  if (F_e)
+    for (int d = 0; d < 3; ++d) F_e[3 * e + d] = mean[d];
+}
+
+cudaError_t launch_fluid_source_semi(const MeshDev& m, const Tables& t, int precision,
+                                     const double* S_elem, SemiAcc acc, const double* u_nodal,
+                                     double* F_elem, double* F_q, cudaStream_t s) {
+  if (!F_elem && !F_q) return cudaSuccess;
+  const unsigned nb = (unsigned)((m.E + 127) / 128);
+#define CFDEM_SEMI(KK)                                                                      \
+  if (m.k == KK) {                                                                          \
+    if (precision == 0)                                                                     \
+      k_fluid_source_semi<KK, double><<<nb, 128, 0, s>>>(m, t, S_elem, acc, u_nodal, F_elem, \
+                                                         F_q);                              \
+    else                                                                                    \
+      k_fluid_source_semi<KK, float><<<nb, 128, 0, s>>>(m, t, S_elem, acc, u_nodal, F_elem,  \
+                                                        F_q);                               \
+    count_launches(1);                                                                      \
+    return cudaGetLastError();                                                              \
+  }
+  CFDEM_SEMI(1)
+  CFDEM_SEMI(2)
+  CFDEM_SEMI(3)
+#undef CFDEM_SEMI
+  return cudaErrorInvalidValue;
+}
+
+// beta_e = B_e / V_e and u_p,avg,e = U_e / N_e (0 for an empty element)
+__global__ void k_drag_coefficients(int64_t E, double inv_ve, SemiAcc acc,
+                                    double* __restrict__ beta_e, double* __restrict__ up_avg) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const double cnt = acc.N[e];
+  if (beta_e) beta_e[e] = acc.B[e] * inv_ve;
+  if (up_avg)
+    for (int d = 0; d < 3; ++d) up_avg[3 * e + d] = cnt > 0.0 ? acc.U[3 * e + d] / cnt : 0.0;
+}
+
+cudaError_t launch_drag_coefficients(const MeshDev& m, SemiAcc acc, double* beta_e,
+                                     double* up_avg, cudaStream_t s) {
+  k_drag_coefficients<<<(unsigned)((m.E + 255) / 256), 256, 0, s>>>(m.E, 1.0 / m.Ve, acc,
+                                                                    beta_e, up_avg);
+  count_launches(1);
   return cudaGetLastError();
 }
 
