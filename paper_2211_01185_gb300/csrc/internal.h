@@ -73,6 +73,7 @@ struct CgScalars {
   unsigned int ticket;  // last-block counter
   int loops;       // bodies of a device-driven CG loop run so far
   float alpha_hi, alpha_lo;  // double-float split of alpha (mixed solve)
+  int xnz;          // 1 if the start vector has a nonzero entry (else A x0 = 0 is skipped)
 };
 
 // Optional per-stage CUDA-event timers of a context (off by default).  A

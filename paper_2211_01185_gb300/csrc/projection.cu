@@ -566,7 +566,10 @@ __device__ bool last_block_reduce(double* partials, int nvals, const double* val
 template <int K, class S, typename T>
 __global__ void __launch_bounds__(kApplyThreads)
 k_apply(MeshDev m, const T* __restrict__ bands, Coefs<T> cf, const T* __restrict__ x,
-        T* __restrict__ y) {
+        T* __restrict__ y, const int* __restrict__ xnz) {
+  // a zero start vector (flag cleared by k_flag_nonzero): A x = 0, the
+  // consumer reads the flag instead of y
+  if (xnz && !*(volatile const int*)xnz) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   LoadPlain<T> ld{x};
   EpiStore<T> ep{y};
@@ -731,17 +734,30 @@ k_cg_dot_fdm(int64_t n, const T* __restrict__ r, const float* __restrict__ zf,
 }
 
 // start: r = b - Ax ; rf = (float) r ; rr, bb, tolerance
+// *flag = 1 if x has an entry other than zero (flag cleared beforehand)
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_flag_nonzero(int64_t n, const T* __restrict__ x, int* flag) {
+  int nz = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    nz |= x[i] != (T)0;
+  if (__syncthreads_or(nz) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
 template <typename T, typename TB>
 __global__ void __launch_bounds__(256)
 k_cg_start_fdm(int64_t n, const TB* __restrict__ b, const T* __restrict__ Ax,
                T* __restrict__ r, float* __restrict__ rf, double* partials, CgScalars* sc,
-               double rtol) {
+               double rtol, int use_flag) {
   __shared__ double red[32];
   T rr = 0, bb = 0;
+  // with use_flag, A x was skipped for a zero start vector (sc->xnz == 0)
+  const bool ax = !use_flag || ((volatile CgScalars*)sc)->xnz;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     T bi = (T)b[i];
-    T ri = bi - Ax[i];
+    T ri = ax ? bi - Ax[i] : bi;
     r[i] = ri;
     if (rf) rf[i] = (float)ri;
     rr += ri * ri;
@@ -771,13 +787,16 @@ k_split_df(int64_t n, const double* __restrict__ b, df64* __restrict__ b_df,
            CgScalars* sc) {
   __shared__ double red[32];
   float bb = 0.f;
+  int nz = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     df64 v = df_from_double(b[i]);
     b_df[i] = v;
     bb = fmaf(v.hi, v.hi, bb);
     x_df[i] = df_from_double(x[i]);
+    nz |= x[i] != 0.0;
   }
+  if (__syncthreads_or(nz) && threadIdx.x == 0) atomicOr(&sc->xnz, 1);
   double s = block_sum((double)bb, red);
   double vals[1] = {s};
   double o[1];
@@ -800,9 +819,23 @@ k_residual_df(MeshDev m, const df64* __restrict__ bands, Coefs<df64> cf,
               float* __restrict__ r32, double* partials, CgScalars* sc, double rtol) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double red[32];
-  LoadPlain<df64> ld{x};
-  EpiResidualDf ep{b, r, r32};
-  double d = apply_tile<K, S, df64>(m, bands, cf, ld, ep, reinterpret_cast<df64*>(smraw));
+  double d;
+  if (((volatile CgScalars*)sc)->xnz) {
+    LoadPlain<df64> ld{x};
+    EpiResidualDf ep{b, r, r32};
+    d = apply_tile<K, S, df64>(m, bands, cf, ld, ep, reinterpret_cast<df64*>(smraw));
+  } else {  // zero start vector (flag from k_split_df): r = b, no operator
+    float acc = 0.f;
+    const int64_t n = m.n_nodes;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      const df64 v = b[i];
+      r[i] = v;
+      r32[i] = v.hi;
+      acc = fmaf(v.hi, v.hi, acc);
+    }
+    d = (double)acc;
+  }
   double s = block_sum(d, red);
   double vals[1] = {s};
   double out[1];
@@ -1021,7 +1054,7 @@ static cudaError_t set_smem() {
 
 template <typename T>
 static cudaError_t apply_t(const MeshDev& m, const T* bands, const double* coef, const T* x,
-                           T* y, cudaStream_t s) {
+                           T* y, cudaStream_t s, const int* xnz = nullptr) {
   Coefs<T> cf = make_coefs<T>(coef);
   return with_k(m, [&](auto kc) {
     constexpr int K = decltype(kc)::value;
@@ -1030,7 +1063,7 @@ static cudaError_t apply_t(const MeshDev& m, const T* bands, const double* coef,
       cudaError_t e = set_smem<K, S, T>();
       if (e != cudaSuccess) return e;
       k_apply<K, S, T><<<apply_grid_s<S>(m), kApplyThreads, apply_smem<K, S, T>(), s>>>(
-          m, bands, cf, x, y);
+          m, bands, cf, x, y, xnz);
       count_launches(1);
       return cudaGetLastError();
     });
@@ -1237,11 +1270,15 @@ static cudaError_t cg_solve_fdm(const MeshDev& m, const T* bands, const double* 
   if (x_is_zero) {
     if ((e = cudaMemsetAsync(Ap, 0, sizeof(T) * n, s)) != cudaSuccess) return e;
   } else {
+    // the operator is skipped on the device when x0 has no nonzero entry
+    k_flag_nonzero<TX_><<<vb, 256, 0, s>>>(n, x, &sc->xnz);
+    count_launches(1);
     if (tm) tm->begin(op_stage, s);
-    if ((e = apply_t<T>(m, bands, coef, x_as_T, Ap, s)) != cudaSuccess) return e;
+    if ((e = apply_t<T>(m, bands, coef, x_as_T, Ap, s, &sc->xnz)) != cudaSuccess) return e;
     if (tm) tm->end(op_stage, s);
   }
-  k_cg_start_fdm<T, TB><<<vb, 256, 0, s>>>(n, b, Ap, r, conv ? rf : nullptr, partials, sc, rtol);
+  k_cg_start_fdm<T, TB><<<vb, 256, 0, s>>>(n, b, Ap, r, conv ? rf : nullptr, partials, sc, rtol,
+                                          x_is_zero ? 0 : 1);
   count_launches(1);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // z = P^-1 r

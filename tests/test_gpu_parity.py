@@ -195,14 +195,23 @@ def test_rhs_and_operator(c):
 @pytest.mark.parametrize("precond", [0, 1])
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("c", CASES[:4])
-def test_projection(c, precision, precond):
+@pytest.mark.parametrize("start", ["zero", "one_entry", "dense"])
+def test_projection(c, precision, precond, start):
+    """Cold and warm starts: a zero start vector skips the operator in the
+    initial residual (r0 = b), one nonzero entry anywhere or a dense start
+    vector takes the full residual."""
     case = _case(*c)
     m = _mesh(case)
     rng = np.random.default_rng(c[0] + 1)
     eps_q = 0.3 + 0.7 * rng.random((m.n_elem, m.Q))
     L2 = case["params"]["l2_smoothing"]
+    x0 = np.zeros(m.n_nodes())
+    if start == "one_entry":
+        x0[rng.integers(m.n_nodes())] = 0.7
+    elif start == "dense":
+        x0[:] = 0.5 + 0.1 * rng.standard_normal(m.n_nodes())
     with _ctx(case, precision=precision, cg_rtol=1e-13, cg_precond=precond) as ctx:
-        x = _zeros(m.n_nodes())
+        x = dev(x0)
         cf.cfdem_project(ctx.h, dev(eps_q), x)
         cf.cfdem_synchronize(ctx.h)
         st = ctx.stats()
