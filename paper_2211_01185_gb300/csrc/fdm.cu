@@ -247,37 +247,50 @@ cublasStatus_t gemm_rm(cublasHandle_t h, int M, int N, int K, const float* A, lo
 
 // C[M x N] = A[M x K] B[K x N] in shared memory with A stored transposed
 // (AT[K][lda]) and B row-major (B[K][ldb]); lda, ldb multiples of 4 floats.
-// Each thread owns an 8 x 8 block of C, so one k step is two 128-bit loads of
-// A, two of B and 64 FMAs.  Threads form a gm x gn grid (gm = ceil(M/8),
-// gn = ceil(N/8)); rows and columns past M, N read padding and are not
-// stored.
-__device__ __forceinline__ void smem_gemm8(const float* AT, int lda, const float* B, int ldb,
-                                           float* C, int ldc, int M, int N, int K) {
-  const int gn = (N + 7) >> 3, gm = (M + 7) >> 3;
+// Each thread owns a TR x TC block of C (TR, TC = 4 or 8), so one k step is
+// TR/4 + TC/4 128-bit loads and TR TC FMAs.  Threads form a gm x gn grid
+// (gm = ceil(M/TR), gn = ceil(N/TC)); rows and columns past M, N read
+// padding and are not stored.
+template <int TR, int TC>
+__device__ __forceinline__ void smem_gemm(const float* AT, int lda, const float* B, int ldb,
+                                          float* C, int ldc, int M, int N, int K) {
+  const int gn = (N + TC - 1) / TC, gm = (M + TR - 1) / TR;
   const int tid = threadIdx.x;
   if (tid >= gm * gn) return;
-  const int r0 = (tid / gn) * 8, c0 = (tid % gn) * 8;
-  float acc[8][8];
+  const int r0 = (tid / gn) * TR, c0 = (tid % gn) * TC;
+  float acc[TR][TC];
 #pragma unroll
-  for (int a = 0; a < 8; ++a)
+  for (int a = 0; a < TR; ++a)
 #pragma unroll
-    for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+    for (int b = 0; b < TC; ++b) acc[a][b] = 0.f;
 #pragma unroll 2
   for (int k = 0; k < K; ++k) {
-    const float4* ap = reinterpret_cast<const float4*>(AT + k * lda + r0);
-    const float4* bp = reinterpret_cast<const float4*>(B + k * ldb + c0);
-    float4 a0 = ap[0], a1 = ap[1], b0 = bp[0], b1 = bp[1];
-    float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-    float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+    float av[TR], bv[TC];
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
+    for (int q = 0; q < TR / 4; ++q) {
+      const float4 v = reinterpret_cast<const float4*>(AT + k * lda + r0)[q];
+      av[4 * q] = v.x;
+      av[4 * q + 1] = v.y;
+      av[4 * q + 2] = v.z;
+      av[4 * q + 3] = v.w;
+    }
 #pragma unroll
-      for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+    for (int q = 0; q < TC / 4; ++q) {
+      const float4 v = reinterpret_cast<const float4*>(B + k * ldb + c0)[q];
+      bv[4 * q] = v.x;
+      bv[4 * q + 1] = v.y;
+      bv[4 * q + 2] = v.z;
+      bv[4 * q + 3] = v.w;
+    }
+#pragma unroll
+    for (int a = 0; a < TR; ++a)
+#pragma unroll
+      for (int b = 0; b < TC; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
   }
 #pragma unroll
-  for (int a = 0; a < 8; ++a)
+  for (int a = 0; a < TR; ++a)
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
+    for (int b = 0; b < TC; ++b) {
       int r = r0 + a, c = c0 + b;
       if (r < M && c < N) C[r * ldc + c] = acc[a][b];
     }
@@ -307,6 +320,7 @@ __host__ __device__ __forceinline__ int slab_pad(int n) { return ((n + 7) & ~7) 
 // both zero-padded row-major in global memory and copied to shared memory as
 // they are.  The slab is staged transposed (x major) as the A operand of the
 // first product.
+template <int TILE>
 __global__ void k_fdm_slab(int nx, int ny, int nz, const float* __restrict__ Bx,
                            const float* __restrict__ AyT, const float* __restrict__ in,
                            int in_stride, float* __restrict__ out, int out_stride,
@@ -335,9 +349,9 @@ __global__ void k_fdm_slab(int nx, int ny, int nz, const float* __restrict__ Bx,
     __syncthreads();
     // rows y >= ny of XT are never written: they feed only outputs that are
     // not stored
-    smem_gemm8(XT, py, MB, px, T, px, ny, nx, nx);      // T[y][x'] = sum_x X[y][x] Bx[x][x']
+    smem_gemm<TILE, TILE>(XT, py, MB, px, T, px, ny, nx, nx);  // T[y][x'] = sum_x X[y][x] Bx[x][x']
     __syncthreads();
-    smem_gemm8(MA, py, T, px, Y, px, ny, nx, ny);       // Y[y'][x] = sum_y AyT[y][y'] T[y][x]
+    smem_gemm<TILE, TILE>(MA, py, T, px, Y, px, ny, nx, ny);   // Y[y'][x] = sum_y AyT[y][y'] T[y][x]
     __syncthreads();
     float* dst = out + (int64_t)z * out_stride;
     for (int t = threadIdx.x; t < plane; t += blockDim.x) {
@@ -536,6 +550,7 @@ struct FdmPlan {
   float* fac = nullptr;       // slab form: LDL^T factors [nz][k+1][ms]
   size_t slab_smem = 0, z_smem = 0;
   int slab_threads = 256;
+  int slab_tile = 8;          // register tile of the slab transforms (4 or 8)
   int ms = 0;                 // slab form: padded plane stride of tmp and fac
   // V_a and V_a^T row-major; in the slab form (axes x, y only) with rows
   // zero-padded to slab_pad(n_a)
@@ -576,7 +591,10 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4], 
     size_t px = slab_pad(nx), py = slab_pad(ny);
     size_t big = nx * py > ny * px ? nx * py : ny * px;
     p->slab_smem = (big + ny * px + nx * px + ny * py) * sizeof(float);
-    p->slab_threads = ((((nx + 7) / 8) * ((ny + 7) / 8) + 31) / 32) * 32;
+    // 4 x 4 register tiles (more warps per slab) where the thread count allows
+    p->slab_tile = ((nx + 3) / 4) * ((ny + 3) / 4) <= 1024 ? 4 : 8;
+    const int tl = p->slab_tile;
+    p->slab_threads = ((((nx + tl - 1) / tl) * ((ny + tl - 1) / tl) + 31) / 32) * 32;
     if (p->slab_threads > 1024) p->slab_smem = (size_t)1 << 30;  // dense form instead
   }
   p->z_smem = (size_t)nz * 32 * (m.k + 2) * sizeof(float);
@@ -636,7 +654,9 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4], 
     if (e == cudaSuccess && ((size_t)optin < p->slab_smem || (size_t)optin < p->z_smem))
       e = cudaErrorInvalidValue;
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_fdm_slab, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+      e = cudaFuncSetAttribute(k_fdm_slab<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_fdm_slab<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_fdm_zsolve<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                optin);
@@ -685,8 +705,16 @@ cudaError_t fdm_apply(FdmPlan* p, const float* r, float* z, const int* done, cud
   if (p->slab) {
     int nblk = nz < 304 ? nz : 304;
     int nm = nx * ny;
-    k_fdm_slab<<<nblk, p->slab_threads, p->slab_smem, s>>>(nx, ny, nz, p->V[0], p->V[1], r, nm,
-                                                            p->tmp, p->ms, done);
+    auto slab = [&](const float* Bx, const float* AyT, const float* in, int is, float* out,
+                    int os) {
+      if (p->slab_tile == 4)
+        k_fdm_slab<4><<<nblk, p->slab_threads, p->slab_smem, s>>>(nx, ny, nz, Bx, AyT, in, is,
+                                                                   out, os, done);
+      else
+        k_fdm_slab<8><<<nblk, p->slab_threads, p->slab_smem, s>>>(nx, ny, nz, Bx, AyT, in, is,
+                                                                   out, os, done);
+    };
+    slab(p->V[0], p->V[1], r, nm, p->tmp, p->ms);
     unsigned zb = (unsigned)((nm + 31) / 32);
     if (p->k == 1)
       k_fdm_zsolve<1><<<zb, 256, p->z_smem, s>>>(nm, p->ms, nz, p->fac, p->tmp, done);
@@ -694,8 +722,7 @@ cudaError_t fdm_apply(FdmPlan* p, const float* r, float* z, const int* done, cud
       k_fdm_zsolve<2><<<zb, 256, p->z_smem, s>>>(nm, p->ms, nz, p->fac, p->tmp, done);
     else
       k_fdm_zsolve<3><<<zb, 256, p->z_smem, s>>>(nm, p->ms, nz, p->fac, p->tmp, done);
-    k_fdm_slab<<<nblk, p->slab_threads, p->slab_smem, s>>>(nx, ny, nz, p->VT[0], p->VT[1], p->tmp,
-                                                            p->ms, z, nm, done);
+    slab(p->VT[0], p->VT[1], p->tmp, p->ms, z, nm);
     count_launches(3);
     return cudaGetLastError();
   }

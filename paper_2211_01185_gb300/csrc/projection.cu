@@ -733,7 +733,6 @@ k_cg_dot_fdm(int64_t n, const T* __restrict__ r, const float* __restrict__ zf,
   }
 }
 
-// start: r = b - Ax ; rf = (float) r ; rr, bb, tolerance
 // *flag = 1 if x has an entry other than zero (flag cleared beforehand)
 template <typename T>
 __global__ void __launch_bounds__(256)
@@ -745,6 +744,7 @@ k_flag_nonzero(int64_t n, const T* __restrict__ x, int* flag) {
   if (__syncthreads_or(nz) && threadIdx.x == 0) atomicOr(flag, 1);
 }
 
+// start: r = b - Ax ; rf = (float) r ; rr, bb, tolerance
 template <typename T, typename TB>
 __global__ void __launch_bounds__(256)
 k_cg_start_fdm(int64_t n, const TB* __restrict__ b, const T* __restrict__ Ax,
@@ -825,10 +825,13 @@ k_residual_df(MeshDev m, const df64* __restrict__ bands, Coefs<df64> cf,
     EpiResidualDf ep{b, r, r32};
     d = apply_tile<K, S, df64>(m, bands, cf, ld, ep, reinterpret_cast<df64*>(smraw));
   } else {  // zero start vector (flag from k_split_df): r = b, no operator
+    // the tile grid is three-dimensional: stride over the flattened grid
     float acc = 0.f;
     const int64_t n = m.n_nodes;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t blk =
+        blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
+    const int64_t nthr = (int64_t)gridDim.x * gridDim.y * gridDim.z * blockDim.x;
+    for (int64_t i = blk * blockDim.x + threadIdx.x; i < n; i += nthr) {
       const df64 v = b[i];
       r[i] = v;
       r32[i] = v.hi;
