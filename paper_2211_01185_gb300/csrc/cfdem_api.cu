@@ -268,6 +268,7 @@ cfdem_status resolve(cfdem_t c) {
       int nb = f < 1.0 ? 1 : (f > 1e6 ? 1000000 : (int)f);
       c->bins.nb[a] = nb;
       c->bins.be[a] = m.L[a] / nb;
+      c->bins.inv_be[a] = 1.0 / c->bins.be[a];
       tot *= nb;
     }
     c->bins.nbins = tot;

@@ -26,6 +26,7 @@
 // Wilkinson shifts (Golub & Van Loan, Sec. 8.3), V = L^-T Q.
 #include <cublas_v2.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -365,21 +366,33 @@ __global__ void k_fdm_slab(int nx, int ny, int nz, const float* __restrict__ Bx,
 // banded solves along z: for every mode m (x-y index of the transformed slab)
 // solve L D L^T w = t with the host factors; fac[z][c][mode] = L(z, z-1-c)
 // for c < K, fac[z][K][mode] = 1 / D(z) (mode stride ms, a multiple of 4).
-// One lane per mode, 32 modes per block.  The block's lines and factors are
-// copied to shared memory by all its threads with asynchronous copies; warp 0
-// runs the two recurrences, reading U = 8 steps ahead into registers so that
-// the shared-memory latency stays off the dependency chain.
+// One lane per mode, 32 modes per block; the block's lines and factors are
+// copied to shared memory by all its threads with asynchronous copies.
+//
+// Both recurrences (forward L u = t, backward L^T y = D^-1 u) are split
+// into kZSeg segments of z, one warp each.  A recurrence of order K is
+// linear in its K-value carried state, so a segment maps its incoming state
+// c_in to its outgoing state as c_out = p + T c_in, with p the result from a
+// zero incoming state and T (K x K per mode and segment) fixed by the
+// factors alone, tabulated on the host (tr).  Pass 1: every warp runs its
+// segment from a zero state and keeps p; warp 0 chains the states through
+// the segments with T; pass 2: every warp reruns its segment from its true
+// incoming state and writes the result.  2 x nz / kZSeg dependent steps per
+// warp instead of nz, with all warps of the block busy.
+constexpr int kZSeg = 8;
+
 template <int K>
-__global__ void __launch_bounds__(256)
-k_fdm_zsolve(int nmodes, int ms, int nz, const float* __restrict__ fac, float* __restrict__ v,
-             const int* __restrict__ done) {
+__global__ void __launch_bounds__(32 * kZSeg)
+k_fdm_zsolve(int nmodes, int ms, int nz, const float* __restrict__ fac,
+             const float* __restrict__ tr, float* __restrict__ v, const int* __restrict__ done) {
   if (done && *(volatile const int*)done) return;
-  constexpr int U = 8;
   extern __shared__ __align__(16) float zsm[];
-  float* line = zsm;                  // [nz][32]
-  float* f = line + nz * 32;          // [nz][K+1][32]
+  float* line = zsm;                          // [nz][32]
+  float* f = line + nz * 32;                  // [nz][K+1][32]
+  float* car = f + nz * (K + 1) * 32;         // [kZSeg][K][32]  segment results from zero
+  float* cin = car + kZSeg * K * 32;          // [kZSeg][K][32]  true incoming states
   const int m0 = blockIdx.x * 32;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
   const bool full = m0 + 32 <= nmodes;
   if (full) {
     for (int t = threadIdx.x; t < nz * 8; t += blockDim.x) {
@@ -404,90 +417,107 @@ k_fdm_zsolve(int nmodes, int ms, int nz, const float* __restrict__ fac, float* _
   }
   cp_async_wait_all();
   __syncthreads();
-  if (threadIdx.x < 32) {
-    // L u = t, forwards
-    float w[K];
+  const int zs = seg * nz / kZSeg, ze = (seg + 1) * nz / kZSeg;
+  const int mode = m0 + lane;
+  // transfer matrix entry T[dir][s][i][j] of this lane's mode (0 past the end)
+  auto T = [&](int dir, int s, int i, int j) {
+    return mode < nmodes ? __ldg(tr + ((int64_t)((dir * kZSeg + s) * K + i) * K + j) * ms + mode)
+                         : 0.f;
+  };
+  // forward step at z: u = t(z) - sum_c L(z, z-1-c) w[c]; w[0] newest
+  auto fwd = [&](float* w, bool store) {
+#pragma unroll 4
+    for (int z = zs; z < ze; ++z) {
+      float u = line[z * 32 + lane];
 #pragma unroll
-    for (int c = 0; c < K; ++c) w[c] = 0.f;
-    float tn[U], ln[U][K];
+      for (int c = K - 1; c >= 0; --c) u -= f[(z * (K + 1) + c) * 32 + lane] * w[c];
 #pragma unroll
-    for (int j = 0; j < U; ++j) {
-      int z = j < nz ? j : nz - 1;
-      tn[j] = line[z * 32 + lane];
-#pragma unroll
-      for (int c = 0; c < K; ++c) ln[j][c] = f[(z * (K + 1) + c) * 32 + lane];
+      for (int c = K - 1; c > 0; --c) w[c] = w[c - 1];
+      w[0] = u;
+      if (store) line[z * 32 + lane] = u;
     }
-    for (int z0 = 0; z0 < nz; z0 += U) {
-      float tc[U], lc[U][K];
+  };
+  // backward step at z: y = u(z) / D(z) - sum_c L(z+1+c, z) v[c]; v[0] newest
+  auto bwd = [&](float* w, bool store) {
+#pragma unroll 4
+    for (int z = ze - 1; z >= zs; --z) {
+      float y = line[z * 32 + lane] * f[(z * (K + 1) + K) * 32 + lane];
 #pragma unroll
-      for (int j = 0; j < U; ++j) {
-        tc[j] = tn[j];
-#pragma unroll
-        for (int c = 0; c < K; ++c) lc[j][c] = ln[j][c];
+      for (int c = K - 1; c >= 0; --c) {
+        const int zz = z + 1 + c;
+        const float l = zz < nz ? f[(zz * (K + 1) + c) * 32 + lane] : 0.f;
+        y -= l * w[c];
       }
 #pragma unroll
-      for (int j = 0; j < U; ++j) {  // next U steps, clamped at the last row
-        int z = z0 + U + j < nz ? z0 + U + j : nz - 1;
-        tn[j] = line[z * 32 + lane];
-#pragma unroll
-        for (int c = 0; c < K; ++c) ln[j][c] = f[(z * (K + 1) + c) * 32 + lane];
-      }
-#pragma unroll
-      for (int j = 0; j < U; ++j) {
-        if (z0 + j < nz) {
-          // older terms first: only the newest product is on the dependency chain
-          float u = tc[j];
-#pragma unroll
-          for (int c = K - 1; c >= 0; --c) u -= lc[j][c] * w[c];
-#pragma unroll
-          for (int c = K - 1; c > 0; --c) w[c] = w[c - 1];
-          w[0] = u;
-          line[(z0 + j) * 32 + lane] = u;
-        }
-      }
+      for (int c = K - 1; c > 0; --c) w[c] = w[c - 1];
+      w[0] = y;
+      if (store) line[z * 32 + lane] = y;
     }
-    // L^T y = D^-1 u, backwards: y(z) = u(z)/D(z) - sum_c L(z+1+c, z) y(z+1+c)
+  };
+  float w[K];
+  // ---- forward
 #pragma unroll
-    for (int c = 0; c < K; ++c) w[c] = 0.f;
-    // step z needs u(z), 1/D(z) and L(z+1+c, z) = fac[z+1+c][c] (0 past the end)
-    auto fetch = [&](int z, float& uo, float& dio, float* lo) {
-      int zs = z < 0 ? 0 : z;
-      uo = line[zs * 32 + lane];
-      dio = f[(zs * (K + 1) + K) * 32 + lane];
+  for (int c = 0; c < K; ++c) w[c] = 0.f;
+  fwd(w, false);
 #pragma unroll
-      for (int c = 0; c < K; ++c) {
-        int zz = zs + 1 + c;
-        lo[c] = zz < nz ? f[(zz * (K + 1) + c) * 32 + lane] : 0.f;
+  for (int c = 0; c < K; ++c) car[(seg * K + c) * 32 + lane] = w[c];
+  __syncthreads();
+  if (seg == 0) {
+    float st[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) st[c] = 0.f;
+    for (int s = 0; s < kZSeg; ++s) {
+#pragma unroll
+      for (int c = 0; c < K; ++c) cin[(s * K + c) * 32 + lane] = st[c];
+      if (s + 1 == kZSeg) break;
+      float nx[K];
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        float a = car[(s * K + i) * 32 + lane];
+#pragma unroll
+        for (int j = 0; j < K; ++j) a += T(0, s, i, j) * st[j];
+        nx[i] = a;
       }
-    };
-    float un[U], dn[U], bn[U][K];
 #pragma unroll
-    for (int j = 0; j < U; ++j) fetch(nz - 1 - j, un[j], dn[j], bn[j]);
-    for (int z0 = nz - 1; z0 >= 0; z0 -= U) {
-      float uc[U], dc[U], bc[U][K];
-#pragma unroll
-      for (int j = 0; j < U; ++j) {
-        uc[j] = un[j];
-        dc[j] = dn[j];
-#pragma unroll
-        for (int c = 0; c < K; ++c) bc[j][c] = bn[j][c];
-      }
-#pragma unroll
-      for (int j = 0; j < U; ++j) fetch(z0 - U - j, un[j], dn[j], bn[j]);
-#pragma unroll
-      for (int j = 0; j < U; ++j) {
-        if (z0 - j >= 0) {
-          float y = uc[j] * dc[j];
-#pragma unroll
-          for (int c = K - 1; c >= 0; --c) y -= bc[j][c] * w[c];
-#pragma unroll
-          for (int c = K - 1; c > 0; --c) w[c] = w[c - 1];
-          w[0] = y;
-          line[(z0 - j) * 32 + lane] = y;
-        }
-      }
+      for (int c = 0; c < K; ++c) st[c] = nx[c];
     }
   }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < K; ++c) w[c] = cin[(seg * K + c) * 32 + lane];
+  fwd(w, true);
+  __syncthreads();
+  // ---- backward
+#pragma unroll
+  for (int c = 0; c < K; ++c) w[c] = 0.f;
+  bwd(w, false);
+#pragma unroll
+  for (int c = 0; c < K; ++c) car[(seg * K + c) * 32 + lane] = w[c];
+  __syncthreads();
+  if (seg == 0) {
+    float st[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) st[c] = 0.f;
+    for (int s = kZSeg - 1; s >= 0; --s) {
+#pragma unroll
+      for (int c = 0; c < K; ++c) cin[(s * K + c) * 32 + lane] = st[c];
+      if (s == 0) break;
+      float nx[K];
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        float a = car[(s * K + i) * 32 + lane];
+#pragma unroll
+        for (int j = 0; j < K; ++j) a += T(1, s, i, j) * st[j];
+        nx[i] = a;
+      }
+#pragma unroll
+      for (int c = 0; c < K; ++c) st[c] = nx[c];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < K; ++c) w[c] = cin[(seg * K + c) * 32 + lane];
+  bwd(w, true);
   __syncthreads();
   if (full) {
     for (int t = threadIdx.x; t < nz * 8; t += blockDim.x) {
@@ -497,10 +527,52 @@ k_fdm_zsolve(int nmodes, int ms, int nz, const float* __restrict__ fac, float* _
     }
   } else {
     for (int t = threadIdx.x; t < nz * 32; t += blockDim.x) {
-      int z = t >> 5, l = t & 31, mode = m0 + l;
-      if (mode < nmodes) v[(int64_t)z * ms + mode] = line[t];
+      int z = t >> 5, l = t & 31, md = m0 + l;
+      if (md < nmodes) v[(int64_t)z * ms + md] = line[t];
     }
   }
+}
+
+// Segment transfer matrices of the two z recurrences (see k_fdm_zsolve),
+// from the FP32 factors the device uses: tr[dir][s][i][j][mode] is entry
+// (i, j) of the map from a segment's incoming K-value state to its outgoing
+// state with zero right-hand side (dir 0 forward, 1 backward).
+void zsolve_transfers(int nz, int k, const std::vector<float>& fac, int stride, int nm,
+                      std::vector<float>& tr) {
+  tr.assign((size_t)2 * kZSeg * k * k * stride, 0.f);
+  auto F = [&](int z, int c, int m) { return (double)fac[((size_t)z * (k + 1) + c) * stride + m]; };
+  std::vector<double> w(k), nw(k);
+  for (int m = 0; m < nm; ++m)
+    for (int s = 0; s < kZSeg; ++s) {
+      const int zs = s * nz / kZSeg, ze = (s + 1) * nz / kZSeg;
+      for (int j = 0; j < k; ++j) {
+        // forward
+        std::fill(w.begin(), w.end(), 0.0);
+        w[j] = 1.0;
+        for (int z = zs; z < ze; ++z) {
+          double u = 0.0;
+          for (int c = 0; c < k; ++c) u -= F(z, c, m) * w[c];
+          for (int c = k - 1; c > 0; --c) w[c] = w[c - 1];
+          w[0] = u;
+        }
+        for (int i = 0; i < k; ++i)
+          tr[((size_t)((0 * kZSeg + s) * k + i) * k + j) * stride + m] = (float)w[i];
+        // backward
+        std::fill(w.begin(), w.end(), 0.0);
+        w[j] = 1.0;
+        for (int z = ze - 1; z >= zs; --z) {
+          double y = 0.0;
+          for (int c = 0; c < k; ++c) {
+            const int zz = z + 1 + c;
+            if (zz < nz) y -= F(zz, c, m) * w[c];
+          }
+          for (int c = k - 1; c > 0; --c) w[c] = w[c - 1];
+          w[0] = y;
+        }
+        for (int i = 0; i < k; ++i)
+          tr[((size_t)((1 * kZSeg + s) * k + i) * k + j) * stride + m] = (float)w[i];
+      }
+    }
 }
 
 // host LDL^T factors of s Mz + cKz Kz (band rows of half-width k) for every
@@ -548,6 +620,7 @@ struct FdmPlan {
   int k = 1;
   bool slab = false;          // slab form (x, y diagonalised, banded z solves)
   float* fac = nullptr;       // slab form: LDL^T factors [nz][k+1][ms]
+  float* tr = nullptr;        // slab form: z-segment transfer matrices [2][kZSeg][k][k][ms]
   size_t slab_smem = 0, z_smem = 0;
   int slab_threads = 256;
   int slab_tile = 8;          // register tile of the slab transforms (4 or 8)
@@ -570,6 +643,7 @@ void fdm_destroy(FdmPlan* p) {
   if (p->dinv) cudaFree(p->dinv);
   if (p->tmp) cudaFree(p->tmp);
   if (p->fac) cudaFree(p->fac);
+  if (p->tr) cudaFree(p->tr);
   if (p->blas) cublasDestroy(p->blas);
   delete p;
 }
@@ -597,7 +671,7 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4], 
     p->slab_threads = ((((nx + tl - 1) / tl) * ((ny + tl - 1) / tl) + 31) / 32) * 32;
     if (p->slab_threads > 1024) p->slab_smem = (size_t)1 << 30;  // dense form instead
   }
-  p->z_smem = (size_t)nz * 32 * (m.k + 2) * sizeof(float);
+  p->z_smem = ((size_t)nz * 32 * (m.k + 2) + (size_t)2 * kZSeg * m.k * 32) * sizeof(float);
   p->slab = p->slab_smem <= 220 * 1024 && p->z_smem <= 220 * 1024;
   std::vector<double> lam[3];
   cudaError_t e = cudaSuccess;
@@ -643,6 +717,10 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4], 
     band_ldlt_factors(nz, m.k, Mz, Kz, coef[3], smodes, p->ms, fac);
     if ((e = cudaMalloc(&p->fac, fac.size() * 4)) == cudaSuccess)
       e = cudaMemcpy(p->fac, fac.data(), fac.size() * 4, cudaMemcpyHostToDevice);
+    std::vector<float> tr;
+    zsolve_transfers(nz, m.k, fac, p->ms, nx * ny, tr);
+    if (e == cudaSuccess && (e = cudaMalloc(&p->tr, tr.size() * 4)) == cudaSuccess)
+      e = cudaMemcpy(p->tr, tr.data(), tr.size() * 4, cudaMemcpyHostToDevice);
     // the dynamic shared-memory limit is a property of the kernel, shared by
     // every plan (context) of the process: raise it to the device's opt-in
     // maximum rather than to this plan's size, which a later plan with
@@ -717,11 +795,14 @@ cudaError_t fdm_apply(FdmPlan* p, const float* r, float* z, const int* done, cud
     slab(p->V[0], p->V[1], r, nm, p->tmp, p->ms);
     unsigned zb = (unsigned)((nm + 31) / 32);
     if (p->k == 1)
-      k_fdm_zsolve<1><<<zb, 256, p->z_smem, s>>>(nm, p->ms, nz, p->fac, p->tmp, done);
+      k_fdm_zsolve<1><<<zb, 32 * kZSeg, p->z_smem, s>>>(nm, p->ms, nz, p->fac, p->tr, p->tmp,
+                                                           done);
     else if (p->k == 2)
-      k_fdm_zsolve<2><<<zb, 256, p->z_smem, s>>>(nm, p->ms, nz, p->fac, p->tmp, done);
+      k_fdm_zsolve<2><<<zb, 32 * kZSeg, p->z_smem, s>>>(nm, p->ms, nz, p->fac, p->tr, p->tmp,
+                                                           done);
     else
-      k_fdm_zsolve<3><<<zb, 256, p->z_smem, s>>>(nm, p->ms, nz, p->fac, p->tmp, done);
+      k_fdm_zsolve<3><<<zb, 32 * kZSeg, p->z_smem, s>>>(nm, p->ms, nz, p->fac, p->tr, p->tmp,
+                                                           done);
     slab(p->VT[0], p->VT[1], p->tmp, p->ms, z, nm);
     count_launches(3);
     return cudaGetLastError();

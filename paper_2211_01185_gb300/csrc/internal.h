@@ -49,6 +49,7 @@ struct Tables {
 struct BinDev {
   int nb[3];
   double be[3];      // bin edge per axis, L / nb
+  double inv_be[3];  // 1 / be (IEEE division on the host, as on the device)
   int64_t nbins;
 };
 

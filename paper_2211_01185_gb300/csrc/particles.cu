@@ -55,7 +55,7 @@ __global__ void k_bin_count(MeshDev m, BinDev b, int64_t n, const double* __rest
                            const double* __restrict__ r, int32_t* __restrict__ bin_of,
                            int32_t* __restrict__ slot, int32_t* __restrict__ count,
                            DevStatus* st) {
-  const double inv_be[3] = {1.0 / b.be[0], 1.0 / b.be[1], 1.0 / b.be[2]};
+  const double* inv_be = b.inv_be;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
