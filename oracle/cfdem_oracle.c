@@ -21,6 +21,8 @@
  *   or_qcm             Eq. (void_fraction) evaluated with averaging spheres
  *                      centred at the quadrature points (quadrature-centred
  *                      reading of the deferred void-fraction scheme)
+ *   or_qcm_weights     per-particle scaling of the QCM sum that conserves
+ *                      the particle volume on the mesh (walls included)
  *   or_pcm             Eq. (void_fraction), particle-centroid method
  *   or_rhs / or_apply  smoothed L2 projection (M + L^2 K) eps_h = b, the
  *   or_cg              reading of the "void fraction smoothing factor L^2"
@@ -319,7 +321,7 @@ static int cmp_i32(const void *a, const void *b)
  * force when brute != 0).  Optional outputs: neighbour count and id sum per
  * quadrature point. */
 void or_qcm(const double *origin, const double *extent, const int *n_el, int k, double R,
-            int64_t n, const double *x, const double *r, int brute,
+            int64_t n, const double *x, const double *r, const double *cw, int brute,
             double *eps_q, int32_t *nb_count, int64_t *nb_idsum)
 {
     omesh m = make_mesh(origin, extent, n_el, k);
@@ -398,7 +400,8 @@ void or_qcm(const double *origin, const double *extent, const int *n_el, int k, 
                     int32_t i = list[j];
                     double dx = x[3 * i] - xq, dy = x[3 * i + 1] - yq, dz = x[3 * i + 2] - zq;
                     double d = sqrt(dx * dx + dy * dy + dz * dz);
-                    vs += or_lens_volume(R, r[i], d);
+                    double v = or_lens_volume(R, r[i], d);
+                    vs += cw ? cw[i] * v : v;
                     ids += i;
                 }
                 eps_q[e * Q + q] = 1.0 - vs / VR;
@@ -411,6 +414,54 @@ void or_qcm(const double *origin, const double *extent, const int *n_el, int k, 
     free(cell_of);
     free(cstart);
     free(cperm);
+}
+
+/* Weights of the volume-conserving quadrature-centred void fraction: the
+ * volume a particle deposits on the mesh through the QCM sum is
+ *   S_i = sum_e sum_q w_q |J_e| V(R, r_i, |x_i - x_q|) / V_R
+ * (every Gauss point of every element, w_q the unit-cube Gauss weights, |J_e|
+ * = V_e), which differs from V_p,i by the quadrature error and, near a wall,
+ * by the part of the averaging spheres outside the mesh.  Scaling the
+ * particle's lens volumes by c_i = V_p,i / S_i makes sum_q w_q |J| (1 - eps_q)
+ * equal sum_i V_p,i.  A particle that reaches no Gauss point keeps c_i = 1.
+ * Elements are visited when their box meets the cube of half-width R + r_i
+ * around x_i; the Gauss points of the others are farther than R + r_i. */
+void or_qcm_weights(const double *origin, const double *extent, const int *n_el, int k,
+                    double R, int64_t n, const double *x, const double *r, double *cw)
+{
+    omesh m = make_mesh(origin, extent, n_el, k);
+    int nq = k + 1;
+    double g[8], w[8];
+    or_gauss_rule(nq, g, w);
+    double VR = 4.0 / 3.0 * OR_PI * R * R * R;
+    double Ve = m.h[0] * m.h[1] * m.h[2];
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double cut = R + r[i];
+        int lo[3], hi[3];
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = (int)floor((x[3 * i + a] - cut - m.x0[a]) / m.h[a]);
+            hi[a] = (int)floor((x[3 * i + a] + cut - m.x0[a]) / m.h[a]);
+            if (lo[a] < 0) lo[a] = 0;
+            if (hi[a] > m.ne[a] - 1) hi[a] = m.ne[a] - 1;
+        }
+        double S = 0.0;
+        for (int ez = lo[2]; ez <= hi[2]; ++ez)
+        for (int ey = lo[1]; ey <= hi[1]; ++ey)
+        for (int ex = lo[0]; ex <= hi[0]; ++ex)
+            for (int qz = 0; qz < nq; ++qz)
+            for (int qy = 0; qy < nq; ++qy)
+            for (int qx = 0; qx < nq; ++qx) {
+                double dx = x[3 * i] - qp_coord(m.x0[0], m.h[0], ex, g[qx]);
+                double dy = x[3 * i + 1] - qp_coord(m.x0[1], m.h[1], ey, g[qy]);
+                double dz = x[3 * i + 2] - qp_coord(m.x0[2], m.h[2], ez, g[qz]);
+                double d2 = dx * dx + dy * dy + dz * dz;
+                if (!(d2 < cut * cut)) continue;
+                S += w[qx] * w[qy] * w[qz] * Ve * or_lens_volume(R, r[i], sqrt(d2)) / VR;
+            }
+        double Vp = 4.0 / 3.0 * OR_PI * r[i] * r[i] * r[i];
+        cw[i] = S > 0.0 ? Vp / S : 1.0;
+    }
 }
 
 /* Particle-centroid void fraction, Eq. (void_fraction): eps_e = (V_e -

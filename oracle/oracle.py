@@ -76,7 +76,8 @@ def lib():
             L.or_bin.argtypes = [dp, dp, ip, i64, dp, ip, ip, ip]
             L.or_lens_volume.argtypes = [dbl, dbl, dbl]
             L.or_lens_volume.restype = dbl
-            L.or_qcm.argtypes = [dp, dp, ip, cint, dbl, i64, dp, dp, cint, dp, ip, lp]
+            L.or_qcm.argtypes = [dp, dp, ip, cint, dbl, i64, dp, dp, dp, cint, dp, ip, lp]
+            L.or_qcm_weights.argtypes = [dp, dp, ip, cint, dbl, i64, dp, dp, dp]
             L.or_pcm.argtypes = [dp, dp, ip, cint, i64, dp, dp, dp]
             L.or_pcm.restype = i64
             L.or_element_matrix.argtypes = [cint, dp, dp, dp]
@@ -234,9 +235,20 @@ def default_qcm_radius(mesh: Mesh):
     return (3.0 * mesh.elem_volume / (4.0 * PI)) ** (1.0 / 3.0)
 
 
-def qcm(mesh: Mesh, R, x, r, brute=False, want_lists=False):
+def qcm_weights(mesh: Mesh, R, x, r):
+    """Per-particle scaling c_i = V_p,i / S_i of the volume-conserving QCM."""
+    x, px = _d(x)
+    r, pr = _d(r)
+    c = np.zeros(x.shape[0])
+    lib().or_qcm_weights(*mesh.args(), float(R), x.shape[0], px, pr,
+                         c.ctypes.data_as(C.POINTER(C.c_double)))
+    return c
+
+
+def qcm(mesh: Mesh, R, x, r, brute=False, want_lists=False, conserve=False):
     """Quadrature-centred void fraction eps_q[E][Q]; also neighbour counts
-    and id sums per quadrature point."""
+    and id sums per quadrature point.  conserve: lens volumes scaled per
+    particle by qcm_weights."""
     x, px = _d(x)
     r, pr = _d(r)
     n = x.shape[0]
@@ -244,7 +256,9 @@ def qcm(mesh: Mesh, R, x, r, brute=False, want_lists=False):
     eps = np.zeros(E * Q)
     cnt = np.zeros(E * Q, dtype=np.int32)
     ids = np.zeros(E * Q, dtype=np.int64)
-    lib().or_qcm(*mesh.args(), float(R), n, px, pr, int(bool(brute)),
+    cw = qcm_weights(mesh, R, x, r) if conserve else None
+    pcw = None if cw is None else cw.ctypes.data_as(C.POINTER(C.c_double))
+    lib().or_qcm(*mesh.args(), float(R), n, px, pr, pcw, int(bool(brute)),
                  eps.ctypes.data_as(C.POINTER(C.c_double)),
                  cnt.ctypes.data_as(C.POINTER(C.c_int32)),
                  ids.ctypes.data_as(C.POINTER(C.c_int64)))
@@ -555,7 +569,7 @@ def coupling_step(mesh: Mesh, params: dict, x, r, u_p, u_nodal, p_nodal, eps0=No
     projection (Jacobi-PCG), forces and fluid source."""
     R = params.get("qcm_radius", 0.0) or default_qcm_radius(mesh)
     if params.get("scheme", 0) == 0:
-        eps_q, _, _ = qcm(mesh, R, x, r)
+        eps_q, _, _ = qcm(mesh, R, x, r, conserve=bool(params.get("qcm_conserve", 0)))
     else:
         eps_q, _ = pcm(mesh, x, r)
     b = rhs(mesh, eps_q)

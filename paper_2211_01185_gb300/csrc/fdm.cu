@@ -370,18 +370,17 @@ __global__ void k_fdm_slab(int nx, int ny, int nz, const float* __restrict__ Bx,
 // copied to shared memory by all its threads with asynchronous copies.
 //
 // Both recurrences (forward L u = t, backward L^T y = D^-1 u) are split
-// into kZSeg segments of z, one warp each.  A recurrence of order K is
+// into kZSeg (8 or 16) segments of z, one warp each.  A recurrence of order K is
 // linear in its K-value carried state, so a segment maps its incoming state
 // c_in to its outgoing state as c_out = p + T c_in, with p the result from a
 // zero incoming state and T (K x K per mode and segment) fixed by the
-// factors alone, tabulated on the host (tr).  Pass 1: every warp runs its
-// segment from a zero state and keeps p; warp 0 chains the states through
-// the segments with T; pass 2: every warp reruns its segment from its true
-// incoming state and writes the result.  2 x nz / kZSeg dependent steps per
-// warp instead of nz, with all warps of the block busy.
-constexpr int kZSeg = 8;
+// factors alone, tabulated on the host (tr) and staged with the lines.
+// Pass 1: every warp runs its segment from a zero state and keeps p; warp 0
+// chains the states through the segments with T; pass 2: every warp reruns
+// its segment from its true incoming state and writes the result.
+// 2 x nz / kZSeg dependent steps per warp instead of nz, all warps busy.
 
-template <int K>
+template <int K, int kZSeg>
 __global__ void __launch_bounds__(32 * kZSeg)
 k_fdm_zsolve(int nmodes, int ms, int nz, const float* __restrict__ fac,
              const float* __restrict__ tr, float* __restrict__ v, const int* __restrict__ done) {
@@ -391,6 +390,7 @@ k_fdm_zsolve(int nmodes, int ms, int nz, const float* __restrict__ fac,
   float* f = line + nz * 32;                  // [nz][K+1][32]
   float* car = f + nz * (K + 1) * 32;         // [kZSeg][K][32]  segment results from zero
   float* cin = car + kZSeg * K * 32;          // [kZSeg][K][32]  true incoming states
+  float* tm = cin + kZSeg * K * 32;           // [2][kZSeg][K][K][32] transfer matrices
   const int m0 = blockIdx.x * 32;
   const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
   const bool full = m0 + 32 <= nmodes;
@@ -415,14 +415,17 @@ k_fdm_zsolve(int nmodes, int ms, int nz, const float* __restrict__ fac,
       else f[t] = (zc % (K + 1)) == K ? 1.f : 0.f;
     }
   }
+  for (int t = threadIdx.x; t < 2 * kZSeg * K * K * 32; t += blockDim.x) {
+    const int row = t >> 5, l = t & 31, md = m0 + l;
+    if (md < nmodes) cp_async4(tm + t, tr + (int64_t)row * ms + md);
+    else tm[t] = 0.f;
+  }
   cp_async_wait_all();
   __syncthreads();
   const int zs = seg * nz / kZSeg, ze = (seg + 1) * nz / kZSeg;
-  const int mode = m0 + lane;
-  // transfer matrix entry T[dir][s][i][j] of this lane's mode (0 past the end)
+  // transfer matrix entry T[dir][s][i][j] of this lane's mode
   auto T = [&](int dir, int s, int i, int j) {
-    return mode < nmodes ? __ldg(tr + ((int64_t)((dir * kZSeg + s) * K + i) * K + j) * ms + mode)
-                         : 0.f;
+    return tm[(((dir * kZSeg + s) * K + i) * K + j) * 32 + lane];
   };
   // forward step at z: u = t(z) - sum_c L(z, z-1-c) w[c]; w[0] newest
   auto fwd = [&](float* w, bool store) {
@@ -537,8 +540,8 @@ k_fdm_zsolve(int nmodes, int ms, int nz, const float* __restrict__ fac,
 // from the FP32 factors the device uses: tr[dir][s][i][j][mode] is entry
 // (i, j) of the map from a segment's incoming K-value state to its outgoing
 // state with zero right-hand side (dir 0 forward, 1 backward).
-void zsolve_transfers(int nz, int k, const std::vector<float>& fac, int stride, int nm,
-                      std::vector<float>& tr) {
+void zsolve_transfers(int nz, int k, int kZSeg, const std::vector<float>& fac, int stride,
+                      int nm, std::vector<float>& tr) {
   tr.assign((size_t)2 * kZSeg * k * k * stride, 0.f);
   auto F = [&](int z, int c, int m) { return (double)fac[((size_t)z * (k + 1) + c) * stride + m]; };
   std::vector<double> w(k), nw(k);
@@ -620,7 +623,8 @@ struct FdmPlan {
   int k = 1;
   bool slab = false;          // slab form (x, y diagonalised, banded z solves)
   float* fac = nullptr;       // slab form: LDL^T factors [nz][k+1][ms]
-  float* tr = nullptr;        // slab form: z-segment transfer matrices [2][kZSeg][k][k][ms]
+  float* tr = nullptr;        // slab form: z-segment transfer matrices [2][zseg][k][k][ms]
+  int zseg = 8;               // slab form: z-segments of the banded solves (8 or 16)
   size_t slab_smem = 0, z_smem = 0;
   int slab_threads = 256;
   int slab_tile = 8;          // register tile of the slab transforms (4 or 8)
@@ -671,7 +675,14 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4], 
     p->slab_threads = ((((nx + tl - 1) / tl) * ((ny + tl - 1) / tl) + 31) / 32) * 32;
     if (p->slab_threads > 1024) p->slab_smem = (size_t)1 << 30;  // dense form instead
   }
-  p->z_smem = ((size_t)nz * 32 * (m.k + 2) + (size_t)2 * kZSeg * m.k * 32) * sizeof(float);
+  // 16 z-segments where the lines, factors, states and transfer matrices fit
+  // in shared memory, else 8
+  auto zsmem = [&](int seg) {
+    return ((size_t)nz * 32 * (m.k + 2) + (size_t)2 * seg * m.k * 32 +
+            (size_t)2 * seg * m.k * m.k * 32) * sizeof(float);
+  };
+  p->zseg = zsmem(16) <= 220 * 1024 ? 16 : 8;
+  p->z_smem = zsmem(p->zseg);
   p->slab = p->slab_smem <= 220 * 1024 && p->z_smem <= 220 * 1024;
   std::vector<double> lam[3];
   cudaError_t e = cudaSuccess;
@@ -718,7 +729,7 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4], 
     if ((e = cudaMalloc(&p->fac, fac.size() * 4)) == cudaSuccess)
       e = cudaMemcpy(p->fac, fac.data(), fac.size() * 4, cudaMemcpyHostToDevice);
     std::vector<float> tr;
-    zsolve_transfers(nz, m.k, fac, p->ms, nx * ny, tr);
+    zsolve_transfers(nz, m.k, p->zseg, fac, p->ms, nx * ny, tr);
     if (e == cudaSuccess && (e = cudaMalloc(&p->tr, tr.size() * 4)) == cudaSuccess)
       e = cudaMemcpy(p->tr, tr.data(), tr.size() * 4, cudaMemcpyHostToDevice);
     // the dynamic shared-memory limit is a property of the kernel, shared by
@@ -736,13 +747,22 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4], 
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_fdm_slab<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_fdm_zsolve<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(k_fdm_zsolve<1, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                optin);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_fdm_zsolve<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(k_fdm_zsolve<1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                optin);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_fdm_zsolve<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(k_fdm_zsolve<2, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               optin);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_fdm_zsolve<2, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               optin);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_fdm_zsolve<3, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               optin);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_fdm_zsolve<3, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                optin);
   } else if (e == cudaSuccess) {
     double* dl[3] = {nullptr, nullptr, nullptr};
@@ -794,15 +814,18 @@ cudaError_t fdm_apply(FdmPlan* p, const float* r, float* z, const int* done, cud
     };
     slab(p->V[0], p->V[1], r, nm, p->tmp, p->ms);
     unsigned zb = (unsigned)((nm + 31) / 32);
-    if (p->k == 1)
-      k_fdm_zsolve<1><<<zb, 32 * kZSeg, p->z_smem, s>>>(nm, p->ms, nz, p->fac, p->tr, p->tmp,
-                                                           done);
-    else if (p->k == 2)
-      k_fdm_zsolve<2><<<zb, 32 * kZSeg, p->z_smem, s>>>(nm, p->ms, nz, p->fac, p->tr, p->tmp,
-                                                           done);
-    else
-      k_fdm_zsolve<3><<<zb, 32 * kZSeg, p->z_smem, s>>>(nm, p->ms, nz, p->fac, p->tr, p->tmp,
-                                                           done);
+#define CFDEM_ZS(KK, SS)                                                                   \
+  k_fdm_zsolve<KK, SS><<<zb, 32 * SS, p->z_smem, s>>>(nm, p->ms, nz, p->fac, p->tr, p->tmp, done)
+    if (p->zseg == 16) {
+      if (p->k == 1) CFDEM_ZS(1, 16);
+      else if (p->k == 2) CFDEM_ZS(2, 16);
+      else CFDEM_ZS(3, 16);
+    } else {
+      if (p->k == 1) CFDEM_ZS(1, 8);
+      else if (p->k == 2) CFDEM_ZS(2, 8);
+      else CFDEM_ZS(3, 8);
+    }
+#undef CFDEM_ZS
     slab(p->VT[0], p->VT[1], p->tmp, p->ms, z, nm);
     count_launches(3);
     return cudaGetLastError();
