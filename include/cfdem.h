@@ -88,6 +88,12 @@ typedef struct {
                               and u_p,avg,e the plain mean particle velocity in e
                               (F_q then varies over the element; F_elem is its Gauss
                               average; see cfdem_fluid_drag_coefficients); default 0 */
+    int qcm_conserve;      /* 1 => volume-conserving QCM: each particle's lens volumes
+                              are scaled by c_i = V_p,i / S_i, S_i = sum_q w_q |J|
+                              V(R, r_i, d_iq) / V_R the volume the plain sum puts on the
+                              mesh, so that sum_q w_q |J| (1 - eps_q) = sum_i V_p,i also
+                              where averaging spheres cross the walls; not supported by
+                              cfdem_adjoint (CFDEM_EINVAL); default 0 */
 } cfdem_params;
 
 /* Counters of the last calls on a context. */

@@ -35,7 +35,7 @@ class cfdem_params(C.Structure):
                 ("precision", C.c_int), ("cg_rtol", C.c_double), ("cg_maxit", C.c_int),
                 ("eps_floor", C.c_double), ("pressure_degree", C.c_int),
                 ("max_radius", C.c_double), ("bin_edge", C.c_double),
-                ("cg_precond", C.c_int), ("shear_force", C.c_int), ("fluid_drag", C.c_int)]
+                ("cg_precond", C.c_int), ("shear_force", C.c_int), ("fluid_drag", C.c_int), ("qcm_conserve", C.c_int)]
 
 
 class cfdem_stats(C.Structure):

@@ -309,6 +309,7 @@ cfdem_status ensure_particles(cfdem_t c, int64_t n) {
   CK(grow(&c->perm, cap), "particle arena");
   CK(grow(&c->xs64, 4 * cap), "particle arena");
   CK(grow(&c->xs32, 8 * cap), "particle arena");
+  CK(grow(&c->qcm_w, 2 * cap), "particle arena");
   c->cap_n = cap;
   return CFDEM_OK;
 }
@@ -492,6 +493,7 @@ void cfdem_params_default(cfdem_params* p) {
   p->cg_precond = 1;
   p->shear_force = 0;
   p->fluid_drag = 0;
+  p->qcm_conserve = 0;
 }
 
 cfdem_status cfdem_create(cfdem_t* out, int device, void* stream) {
@@ -531,7 +533,7 @@ cfdem_status cfdem_destroy(cfdem_t c) {
   c->fdm = nullptr;
   c->timer.release();
   void* ps[] = {c->st, c->bands64, c->bands32, c->bandsdf, c->bin_of, c->slot, c->perm, c->xs64,
-                c->xs32, c->bin_count, c->bin_start, c->scan_tmp};
+                c->xs32, c->qcm_w, c->bin_count, c->bin_start, c->scan_tmp};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (c->loop_stream) cudaStreamDestroy(c->loop_stream);
@@ -601,6 +603,8 @@ cfdem_status cfdem_set_params(cfdem_t c, const cfdem_params* p) {
     return fail(c, CFDEM_EINVAL, "shear_force must be 0 or 1");
   if (p->fluid_drag < 0 || p->fluid_drag > 1)
     return fail(c, CFDEM_EINVAL, "fluid_drag must be 0 (explicit) or 1 (fluid-side form)");
+  if (p->qcm_conserve < 0 || p->qcm_conserve > 1)
+    return fail(c, CFDEM_EINVAL, "qcm_conserve must be 0 or 1");
   c->prm = *p;
   ++c->gen;
   return resolve(c);
@@ -666,8 +670,10 @@ cfdem_status cfdem_void_fraction(cfdem_t c, int64_t n, const double* x, const do
     s = do_bin(c, n, x, r);
     if (s != CFDEM_OK) return s;
     c->timer.begin(kStageVoid, c->stream);
+    const bool conserve = c->prm.qcm_conserve == 1;
     CK(launch_qcm(m, c->tab, c->bins, mixed ? 1 : 0, c->R, c->bin_start, c->perm, c->xs64,
-                  c->xs32, c->st, out64, out32, nb_count, nb_idsum, c->stream),
+                  c->xs32, c->st, out64, out32, nb_count, nb_idsum, c->stream,
+                  conserve ? reinterpret_cast<float2*>(c->qcm_w) : nullptr, conserve ? n : 0),
        "qcm");
     c->timer.end(kStageVoid, c->stream);
   }
@@ -796,6 +802,9 @@ cfdem_status cfdem_adjoint(cfdem_t c, int64_t n, const double* x, const double* 
   if (n < 0 || n >= ((int64_t)1 << 31) || (n > 0 && (!x || !r || !u_p || !dJ_dx)) ||
       !u_nodal || !p_nodal || !eps_nodal)
     return fail(c, CFDEM_EINVAL, "null input");
+  if (c->prm.scheme == 0 && c->prm.qcm_conserve)
+    return fail(c, CFDEM_EINVAL,
+                "the adjoint does not differentiate the volume-conserving QCM weights");
   DeviceGuard g(c->device);
   const MeshDev& m = c->mesh;
   if (!c->adj_geps) {  // the mesh arena is released (and these reset) by every set_mesh

@@ -34,6 +34,7 @@ struct cfdem_ctx {
   int32_t *bin_of = nullptr, *slot = nullptr, *perm = nullptr;
   double* xs64 = nullptr;
   float* xs32 = nullptr;
+  float* qcm_w = nullptr;      // volume-conserving QCM weights per sorted particle [2 n]
   int64_t cap_bins = 0;
   int32_t *bin_count = nullptr, *bin_start = nullptr, *scan_tmp = nullptr;
   // mesh arena

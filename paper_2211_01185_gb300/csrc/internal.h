@@ -149,11 +149,14 @@ cudaError_t launch_drag_coefficients(const MeshDev& m, SemiAcc acc, double* beta
                                      double* up_avg, cudaStream_t s);
 
 // voidfrac.cu
+// cw (optional): scratch of n float pairs; when given, the volume-conserving
+// weights of the n sorted particles are computed into it first and scale
+// every particle's lens volumes
 cudaError_t launch_qcm(const MeshDev& m, const Tables& t, const BinDev& b, int precision,
                        double R, const int32_t* bin_start, const int32_t* perm,
                        const double* xs64, const float* xs32, const DevStatus* st,
                        double* eps_q64, float* eps_q32, int32_t* nb_count, int64_t* nb_idsum,
-                       cudaStream_t s);
+                       cudaStream_t s, float2* cw = nullptr, int64_t n = 0);
 cudaError_t launch_pcm(const MeshDev& m, int64_t n, const double* x, const double* r,
                        double* vol_elem, double* eps_q64, float* eps_q32, DevStatus* st,
                        cudaStream_t s);

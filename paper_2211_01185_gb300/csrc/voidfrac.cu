@@ -52,6 +52,9 @@ struct QcmParams {
   float R_hi, R_lo;        // averaging radius
   float c43_hi, c43_lo;    // 4 pi / 3
   float c12_hi, c12_lo;    // pi / 12
+  const float2* cw;        // volume-conserving weights per sorted particle (hi, lo), or null
+  float w3[64], w3_lo[64]; // unit-cube Gauss weights w_qx w_qy w_qz (float pair)
+  float vr_ve_hi, vr_ve_lo, vr_ve32;  // V_R / V_e
 };
 
 __device__ __forceinline__ float ff_two_prod_sum(float a, float b_hi, float b_lo, float* lo) {
@@ -136,6 +139,7 @@ struct QcmWarp {
   float R_hi, R_lo;
   df64 c43, c12;
   bool want_counts, want_ids;
+  const float2* cw;  // per sorted particle scale of its lens volumes, or null
 };
 
 // Evaluate the first cnt queued hits (q-sorted) and add each quadrature
@@ -170,6 +174,11 @@ __device__ __forceinline__ void qcm_flush(QcmSmem<K, FP64>& sm, const QcmWarp& w
       float4 qq = sm.qrel[q];
       float dx = cj.x - qq.x, dy = cj.y - qq.y, dz = cj.z - qq.z;
       v32 = lens32(w.R32, cj.w, dx * dx + dy * dy + dz * dz);
+    }
+    if (w.cw) {  // volume-conserving QCM: the particle's lens volumes scaled by c
+      const float2 c = __ldg(w.cw + sm.gslot[wp][j]);
+      if (FP64) vdf = vdf * df64(c.x, c.y);
+      else v32 *= c.x;
     }
     if (w.want_ids) id = perm[sm.gslot[wp][j]];
   }
@@ -337,6 +346,7 @@ k_qcm(MeshDev m, QcmParams P, BinDev b, const int32_t* __restrict__ bin_start,
   w.c12 = df64(P.c12_hi, P.c12_lo);
   w.want_ids = nb_idsum != nullptr;
   w.want_counts = nb_count != nullptr || nb_idsum != nullptr;
+  w.cw = P.cw;
   const int lane = w.lane, wp = w.warp;
   for (int t = threadIdx.x; t < Q; t += blockDim.x)
     sm.qrel[t] = make_float4(P.qrel[t][0], P.qrel[t][1], P.qrel[t][2], 0.f);
@@ -520,12 +530,113 @@ static void split_ff(double v, float* hi, float* lo) {
   *lo = (float)(v - (double)*hi);
 }
 
+// Volume-conserving QCM weights, one thread per sorted particle s:
+//   c_s = V_p / S_s,  S_s = sum over the Gauss points within R + r of
+//   w_q V_e V(R, r, |x_s - x_q|) / V_R
+// (w_q the unit-cube Gauss weights), 1 where S_s = 0.  Distances are taken
+// relative to the corner of the particle's own element, so that FP32 keeps
+// digits of millimetre-scale offsets in a large box.  FP32 path: FP32
+// throughout.  FP64 path: an FP32 prefilter with a margin, then the kept
+// pairs' squared distances, lens volumes and the sum in double-float; c is
+// stored as a float pair (hi, lo).
+template <int K, bool FP64>
+__global__ void __launch_bounds__(128)
+k_qcm_weights(MeshDev m, QcmParams P, int64_t n, const double* __restrict__ xs64,
+              float2* __restrict__ cw) {
+  constexpr int NQ = K + 1;
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const P4 pt = reinterpret_cast<const P4*>(xs64)[s];
+  const double pc[3] = {pt.x, pt.y, pt.z};
+  const double r = pt.w;
+  const float hf[3] = {P.hx, P.hy, P.hz};
+  const df64 hdf[3] = {df64(P.hx_hi, P.hx_lo), df64(P.hy_hi, P.hy_lo), df64(P.hz_hi, P.hz_lo)};
+  // particle relative to the corner of its element, FP64 then split
+  int ie[3], lo[3], hi[3];
+  float xe[3];
+  df64 xedf[3];
+  const float cut = (float)(P.R + r);
+  for (int a = 0; a < 3; ++a) {
+    const double rel = pc[a] - m.x0[a];
+    int e = (int)floor(rel / m.h[a]);
+    e = e < 0 ? 0 : (e > m.ne[a] - 1 ? m.ne[a] - 1 : e);
+    ie[a] = e;
+    const double off = rel - m.h[a] * (double)e;
+    xe[a] = (float)off;
+    xedf[a] = df_from_double(off);
+    const float cu = cut / hf[a];
+    int l = (int)floorf(xe[a] / hf[a] - cu - 1e-3f), h = (int)floorf(xe[a] / hf[a] + cu + 1e-3f);
+    lo[a] = ie[a] + l < 0 ? -ie[a] : l;
+    hi[a] = ie[a] + h > m.ne[a] - 1 ? m.ne[a] - 1 - ie[a] : h;
+  }
+  const float cut2 = cut * cut * (FP64 ? 1.0001f : 1.0f);
+  const float R32 = P.R32, r32 = (float)r;
+  float S32 = 0.f;
+  df64 Sdf(0.f, 0.f);
+  const df64 Rdf(P.R_hi, P.R_lo), rdf = df_from_double(r);
+  const df64 c43(P.c43_hi, P.c43_lo), c12(P.c12_hi, P.c12_lo);
+  for (int dz = lo[2]; dz <= hi[2]; ++dz)
+    for (int qz = 0; qz < NQ; ++qz) {
+      const float Zr = hf[2] * ((float)dz + (float)P.g[qz]);
+      const float fz = xe[2] - Zr;
+      for (int dy = lo[1]; dy <= hi[1]; ++dy)
+        for (int qy = 0; qy < NQ; ++qy) {
+          const float Yr = hf[1] * ((float)dy + (float)P.g[qy]);
+          const float fy = xe[1] - Yr;
+          const float dyz = fy * fy + fz * fz;
+          if (!(dyz < cut2)) continue;
+          for (int dx = lo[0]; dx <= hi[0]; ++dx)
+#pragma unroll
+            for (int qx = 0; qx < NQ; ++qx) {
+              const float Xr = hf[0] * ((float)dx + (float)P.g[qx]);
+              const float fx = xe[0] - Xr;
+              const float d2 = fx * fx + dyz;
+              if (!(d2 < cut2)) continue;
+              const float wq = P.w3[qx + NQ * (qy + NQ * qz)];
+              if (FP64) {
+                // offsets from the element corner in double-float: h (d + g)
+                const df64 X = hdf[0] * (df64((float)dx) + df64(P.g_hi[qx], P.g_lo[qx]));
+                const df64 Y = hdf[1] * (df64((float)dy) + df64(P.g_hi[qy], P.g_lo[qy]));
+                const df64 Z = hdf[2] * (df64((float)dz) + df64(P.g_hi[qz], P.g_lo[qz]));
+                const df64 ddx = xedf[0] - X, ddy = xedf[1] - Y, ddz = xedf[2] - Z;
+                const df64 D = ddx * ddx + ddy * ddy + ddz * ddz;
+                const df64 Rc = Rdf + rdf;
+                if (!df_le(D, Rc * Rc) || (D.hi == (Rc * Rc).hi && D.lo == (Rc * Rc).lo)) continue;
+                Sdf += df64(wq, P.w3_lo[qx + NQ * (qy + NQ * qz)]) * lens_df(Rdf, rdf, D, c43, c12);
+              } else {
+                S32 += wq * lens32(R32, r32, d2);
+              }
+            }
+        }
+    }
+  // S = V_e / V_R * sum w_q V ; c = V_p / S = (4/3 pi r^3) V_R / (V_e sum)
+  float2 out;
+  if (FP64) {
+    if (Sdf.hi > 0.f) {
+      const df64 vp = c43 * (rdf * rdf * rdf);
+      const df64 c = vp * df64(P.vr_ve_hi, P.vr_ve_lo) * df_recip(Sdf);
+      out = make_float2(c.hi, c.lo);
+    } else {
+      out = make_float2(1.f, 0.f);
+    }
+  } else {
+    if (S32 > 0.f) {
+      const float vp = (float)(4.0 / 3.0 * kPi) * r32 * r32 * r32;
+      out = make_float2(vp * P.vr_ve32 / S32, 0.f);
+    } else {
+      out = make_float2(1.f, 0.f);
+    }
+  }
+  cw[s] = out;
+}
+
 cudaError_t launch_qcm(const MeshDev& m, const Tables& t, const BinDev& b, int precision,
                        double R, const int32_t* bin_start, const int32_t* perm,
                        const double* xs64, const float* xs32, const DevStatus* st,
                        double* eps_q64, float* eps_q32, int32_t* nb_count, int64_t* nb_idsum,
-                       cudaStream_t s) {
+                       cudaStream_t s, float2* cw, int64_t n) {
   QcmParams P;
+  P.cw = nullptr;
   P.R = R;
   P.R32 = (float)R;
   P.inv_vr = 1.0 / (4.0 / 3.0 * kPi * R * R * R);
@@ -569,6 +680,30 @@ cudaError_t launch_qcm(const MeshDev& m, const Tables& t, const BinDev& b, int p
   if (delta < 1.0 / 4096.0) delta = 1.0 / 4096.0;
   if (delta > 0.25) delta = 0.25;
   P.delta = (float)delta;
+  for (int q = 0; q < 64; ++q) {
+    int qx = q % nq, qy = (q / nq) % nq, qz = q / (nq * nq);
+    double wq = q < nq * nq * nq ? t.w[qx] * t.w[qy] * t.w[qz] : 0.0;
+    split_ff(wq, &P.w3[q], &P.w3_lo[q]);
+  }
+  const double vr_ve = 4.0 / 3.0 * kPi * R * R * R / m.Ve;
+  split_ff(vr_ve, &P.vr_ve_hi, &P.vr_ve_lo);
+  P.vr_ve32 = (float)vr_ve;
+  if (cw && n > 0) {  // volume-conserving weights first, then the scaled sums
+    const unsigned nb = (unsigned)((n + 127) / 128);
+#define CFDEM_QW(KK)                                                                \
+    if (m.k == KK) {                                                                \
+      if (precision == 0)                                                           \
+        k_qcm_weights<KK, true><<<nb, 128, 0, s>>>(m, P, n, xs64, cw);             \
+      else                                                                          \
+        k_qcm_weights<KK, false><<<nb, 128, 0, s>>>(m, P, n, xs64, cw);            \
+    }
+    CFDEM_QW(1)
+    CFDEM_QW(2)
+    CFDEM_QW(3)
+#undef CFDEM_QW
+    count_launches(1);
+    P.cw = cw;
+  }
   dim3 grid((unsigned)((m.E + kQcmWarps - 1) / kQcmWarps));
   dim3 block(kQcmWarps * 32);
   bool fp64 = precision == 0;

@@ -447,3 +447,44 @@ def test_fluid_side_drag(c, vans, precision):
         occ = cnt > 0
         beta_ref = -np.sum(Fe_ref[occ] * d[occ], axis=1) / np.sum(d[occ] * d[occ], axis=1)
         assert rel_err(b[occ], beta_ref) <= tol
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("c", CASES)
+def test_qcm_volume_conserving(c, precision):
+    """qcm_conserve = 1: every particle's lens volumes scaled by V_p / S; the
+    void fraction matches the oracle's, neighbour sets are unchanged, and the
+    solid volume on the mesh equals the particles' volume (walls included)."""
+    import math
+    import torch
+    case = _case(*c)
+    m = _mesh(case)
+    n = case["x"].shape[0]
+    R = O.default_qcm_radius(m)
+    with _ctx(case, precision=precision, qcm_radius=R, qcm_conserve=1) as ctx:
+        eps = _zeros(m.n_elem, m.Q)
+        cnt = _zeros(m.n_elem, m.Q, dtype=torch.int32)
+        cf.cfdem_void_fraction(ctx.h, n, dev(case["x"]), dev(case["r"]), eps, cnt, None)
+        cf.cfdem_synchronize(ctx.h)
+    e_ref, c_ref, _ = O.qcm(m, R, case["x"], case["r"], conserve=True)
+    assert rel_err_eps(host(eps), e_ref, precision) <= TOL[precision]
+    if precision == 0:
+        assert np.array_equal(host(cnt), c_ref)
+    _, w = O.gauss_rule(m.nq)
+    w3 = np.einsum("i,j,k->kji", w, w, w).reshape(-1)
+    solid = float(np.sum((1.0 - host(eps)) * w3[None, :]) * np.prod(m.h))
+    vp = float(np.sum(4.0 / 3.0 * math.pi * case["r"] ** 3))
+    assert solid == pytest.approx(vp, rel=1e-10 if precision == 0 else 1e-5)
+
+
+def test_adjoint_rejects_volume_conserving_qcm():
+    case = _case(*CASES[1])
+    m = _mesh(case)
+    n = case["x"].shape[0]
+    with _ctx(case, qcm_conserve=1) as ctx:
+        z = lambda *s: _zeros(*s)  # noqa: E731
+        st = cf.lib().cfdem_adjoint(ctx.h, n, cf._ptr(dev(case["x"])), cf._ptr(dev(case["r"])),
+                                    cf._ptr(dev(case["u_p"])), cf._ptr(dev(case["u_nodal"])),
+                                    cf._ptr(dev(case["p_nodal"])), cf._ptr(z(m.n_nodes())),
+                                    None, None, None, cf._ptr(z(n, 3)), None)
+        assert st == cf.EINVAL

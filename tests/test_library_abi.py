@@ -40,7 +40,7 @@ int main(void) {
   P(cfdem_params, qcm_radius); P(cfdem_params, l2_smoothing); P(cfdem_params, drag_model);
   P(cfdem_params, precision); P(cfdem_params, cg_rtol); P(cfdem_params, cg_maxit);
   P(cfdem_params, eps_floor); P(cfdem_params, pressure_degree); P(cfdem_params, max_radius);
-  P(cfdem_params, bin_edge); P(cfdem_params, cg_precond); P(cfdem_params, shear_force); P(cfdem_params, fluid_drag);
+  P(cfdem_params, bin_edge); P(cfdem_params, cg_precond); P(cfdem_params, shear_force); P(cfdem_params, fluid_drag); P(cfdem_params, qcm_conserve);
   P(cfdem_stats, cg_iterations); P(cfdem_stats, cg_relres); P(cfdem_stats, nb);
   P(cfdem_stats, bin_edge); P(cfdem_stats, qcm_radius); P(cfdem_stats, n_pnodes);
   P(cfdem_stats, stage_ms); P(cfdem_stats, kernel_launches); P(cfdem_stats, precond);
