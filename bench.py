@@ -413,6 +413,109 @@ def run_adjoint(args):
     return 0
 
 
+def run_dem(args):
+    """The particle side of the coupling on the bench bed (100,000 spheres,
+    d ~ U[2,3] mm, packed with small overlaps in the lower 40 % of the
+    0.1 x 0.1 x 0.4 m box): one step = one CFD step's worth of DEM, 10
+    Velocity Verlet sub-steps of 5 us with the contact model of Table
+    (viscoelastic), FP64, with the coupling step's forces held as f_fp; also
+    timed: the coupled step (mixed coupling step replayed as a graph, then
+    the 10 DEM sub-steps on its forces)."""
+    import torch
+    from paper_2211_01185_gb300 import build as B
+    from paper_2211_01185_gb300 import cfdem as cf
+    from paper_2211_01185_gb300 import synth
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.build()
+    w = synth.make_workload(WORKLOAD)
+    n = w["x"].shape[0]
+    nsub, dt = 10, 5e-6
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    t = lambda a: torch.as_tensor(a, dtype=torch.float64).to(dev).contiguous()  # noqa: E731
+    lo = np.asarray(w["origin"], dtype=np.float64)
+    hi = lo + np.asarray(w["extent"], dtype=np.float64)
+    dprm = dict(rho_p=2500.0, youngs=1e7, poisson=0.3, restitution=0.9, friction=0.3,
+                rolling_friction=0.01, wall_youngs=1e7, wall_poisson=0.3,
+                wall_restitution=0.9, wall_friction=0.3, wall_rolling_friction=0.01,
+                g=(0.0, 0.0, -9.81), lo=tuple(lo), hi=tuple(hi),
+                max_radius=float(w["r"].max()), capacity=24)
+    with torch.cuda.stream(stream):
+        x0, r, up, un, pn = t(w["x"]), t(w["r"]), t(w["u_p"]), t(w["u_nodal"]), t(w["p_nodal"])
+        x, v, om = x0.clone(), up.clone(), torch.zeros_like(up)
+        nn = un.shape[0]
+        E = int(np.prod(w["n_el"]))
+        eps = torch.zeros(nn, dtype=torch.float64, device=dev)
+        f = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+        fd, Fe = torch.zeros_like(f), torch.zeros((E, 3), dtype=torch.float64, device=dev)
+    prm = dict(w["params"], precision=1, max_radius=float(w["r"].max()), cg_rtol=1e-12)
+    bh = cf.cfdem_batch_create(1, local, stream.cuda_stream)
+    bed = cf.cfdem_batch_bed(bh, 0)
+    cf.cfdem_set_mesh(bed, w["origin"], w["extent"], w["n_el"], w["k"])
+    cf.cfdem_set_params(bed, cf.make_params(**prm))
+    dem = cf.Dem(dprm, device=local, stream=stream.cuda_stream)
+
+    def coupling():
+        eps.zero_()
+        io = cf.bed_io(n, x, r, v, un, pn, eps, f, fd, Fe)
+        assert cf.cfdem_batch_coupling_step(bh, [io]) == cf.OK
+
+    def timed(fn, k):
+        ev = []
+        clk = Clocks(local)
+        clk.wait_first()
+        for _ in range(k):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            ev.append((a, b))
+        torch.cuda.synchronize(dev)
+        return float(np.mean([a.elapsed_time(b) for a, b in ev])), clk.stop()
+
+    with torch.cuda.stream(stream):
+        coupling()                                  # forces of the packed bed
+        cf.cfdem_batch_synchronize(bh)
+        for _ in range(args.warmup):
+            dem.step(x, v, om, r, f, dt, nsub)
+        torch.cuda.synchronize(dev)
+        ms_dem, clocks = timed(lambda: dem.step(x, v, om, r, f, dt, nsub), args.steps)
+        st_dem = dem.synchronize()
+
+        def coupled():
+            coupling()
+            dem.step(x, v, om, r, f, dt, nsub)
+
+        for _ in range(args.warmup):
+            coupled()
+        torch.cuda.synchronize(dev)
+        ms_cpl, clocks_cpl = timed(coupled, args.steps)
+        st_b = cf.cfdem_batch_synchronize(bh)
+        st_dem2 = dem.synchronize()
+        drift = float(torch.linalg.norm(x - x0, dim=1).max().item())
+    dem.close()
+    cf.cfdem_batch_destroy(bh)
+    res = {"metric": "DEM particle sub-steps/s (visco-elastic contacts, Velocity Verlet)",
+           "value": n * nsub / (ms_dem * 1e-3), "unit": "particle sub-steps/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_dem,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": "dem_" + WORKLOAD, "particles": n, "substeps_per_step": nsub,
+                      "dt_dem": dt, "contact_capacity": 24,
+                      "l2": "256 MiB buffer written between timed steps"},
+           "status": {"dem": int(st_dem), "dem_coupled": int(st_dem2), "batch": list(st_b)},
+           "coupled_step": {"ms_per_step": ms_cpl, "value": n / (ms_cpl * 1e-3),
+                            "unit": "particle CFD steps/s (coupling + 10 DEM sub-steps)",
+                            "clocks": clocks_cpl},
+           "max_displacement_m": drift, "clocks": clocks}
+    print(json.dumps(res), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -423,9 +526,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"],
                     help="paths to time (profiling runs use one)")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch64", "adjoint5"],
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "batch64", "adjoint5", "dem"],
                     help="batch64: the 64-bed ensemble, graph replay against 64 solo runs; "
-                         "adjoint5: forward step + adjoint of J = sum e_z.f_D + ||eps_h||_M")
+                         "adjoint5: forward step + adjoint of J = sum e_z.f_D + ||eps_h||_M; "
+                         "dem: 10 DEM sub-steps per step on the bench bed, and the coupled step")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -434,6 +539,8 @@ def main():
         return run_batch(args)
     if args.workload == "adjoint5":
         return run_adjoint(args)
+    if args.workload == "dem":
+        return run_dem(args)
 
     import torch
     from paper_2211_01185_gb300 import build as B

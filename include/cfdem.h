@@ -51,7 +51,8 @@ typedef enum {
     CFDEM_NOT_CONVERGED = -3,   /* CG stopped at cg_maxit; last iterate kept */
     CFDEM_ENOMEM = -4,          /* device allocation failed */
     CFDEM_ECUDA = -5,           /* a CUDA runtime call failed */
-    CFDEM_ESTATE = -6           /* call needs set_mesh / a previous stage */
+    CFDEM_ESTATE = -6,          /* call needs set_mesh / a previous stage */
+    CFDEM_ECAPACITY = -7        /* a fixed per-particle capacity was exceeded */
 } cfdem_status;
 
 /* Physical and numerical parameters.  cfdem_params_default fills them. */
@@ -365,6 +366,75 @@ const char *cfdem_last_error(cfdem_t ctx);
 
 /* Library version string. */
 const char *cfdem_version(void);
+
+/* ------------------------------------------------------------------ DEM */
+
+/* The particle side of the coupling (Sec. 2.2): Newton's laws for
+ * translation and rotation, Eqs. (newton_law) and (angular_momentum),
+ *   m dv/dt = sum_j f_ij + sum_w f_wi + m g + f_fp,  I dw/dt = sum_j (M^t + M^r),
+ * I = 2/5 m r^2, with soft-sphere contacts of the non-linear visco-elastic
+ * model of Table (viscoelastic): k_n = 4/3 Y_e sqrt(R_e d_n), eta_n =
+ * -2 sqrt(5/6) beta sqrt(S_n m_e), k_t = 8 G_e sqrt(R_e d_n), eta_t =
+ * -2 sqrt(5/6) beta sqrt(S_t m_e), beta = ln e / sqrt(ln^2 e + pi^2), the
+ * effective mass, radius and moduli of the table, f^n = -k_n d_n n -
+ * eta_n v_rn, f^t = -k_t d_t - eta_t v_rt; Velocity Verlet integration
+ * (Sec. 2.2), sub-cycled with the fluid force f_fp held (the DEM frequency
+ * f_coupling of Sec. 2.3).  Readings: the tangential displacement d_t is
+ * kept per contact, turned onto the current tangent plane and advanced by
+ * v_rt dt; the Coulomb limit mu_s |f^n| caps f^t (and resets d_t to match);
+ * rolling resistance is the constant-torque form -mu_r R_e |f^n| w_rel /
+ * |w_rel|; the six faces of the box [lo, hi] are walls of infinite mass and
+ * radius; forces at step n+1 use positions x(n+1) and half-step velocities. */
+typedef struct cfdem_dem *cfdem_dem_t;
+
+typedef struct {
+    double rho_p;                 /* particle density [kg/m^3] */
+    double youngs, poisson;       /* particle Young's modulus [Pa], Poisson ratio */
+    double restitution;           /* particle-particle coefficient of restitution e, (0, 1] */
+    double friction;              /* sliding friction mu_s */
+    double rolling_friction;      /* rolling friction mu_r */
+    double wall_youngs, wall_poisson, wall_restitution, wall_friction, wall_rolling_friction;
+    double g[3];                  /* gravity [m/s^2] */
+    double lo[3], hi[3];          /* the walls: faces of the box [lo, hi] */
+    double max_radius;            /* the largest particle radius (cell size 2 max_radius) */
+    int capacity;                 /* contacts kept per particle, 1..64 (default 24) */
+} cfdem_dem_params;
+
+/* Glass-like defaults (rho 2500, Y 1e7, nu 0.3, e 0.9, mu_s 0.3, mu_r 0,
+ * walls alike), g = (0, 0, -9.81), capacity 24; the box and max_radius
+ * are left 0 and must be set. */
+void cfdem_dem_params_default(cfdem_dem_params *p);
+
+/* A DEM state on CUDA device `device`, work ordered on `stream`. */
+cfdem_status cfdem_dem_create(cfdem_dem_t *out, int device, void *stream);
+cfdem_status cfdem_dem_destroy(cfdem_dem_t dem);
+
+/* Set (or change) the parameters; CFDEM_EINVAL for a bad value.  The
+ * carried accelerations are recomputed at the next step. */
+cfdem_status cfdem_dem_set_params(cfdem_dem_t dem, const cfdem_dem_params *p);
+
+/* Forget the contact history and the carried accelerations. */
+cfdem_status cfdem_dem_reset(cfdem_dem_t dem);
+
+/* nsub Velocity Verlet sub-steps of length dt, in place: x_dev, v_dev, w_dev
+ * [n][3] (positions, velocities, angular velocities, device, FP64), radii
+ * r_dev[n], fluid force f_ext_dev[n][3] held over the sub-steps (NULL =
+ * none).  The contact history (tangential displacements per particle pair
+ * and per wall) and the last accelerations carry over to the next call
+ * while n stays the same and particle i stays particle i; a different n
+ * starts afresh.  Stream ordered; a particle with more than `capacity`
+ * contacts (its extra contacts are dropped) or a radius above max_radius
+ * is reported by the next cfdem_dem_synchronize. */
+cfdem_status cfdem_dem_step(cfdem_dem_t dem, int64_t n, double *x_dev, double *v_dev,
+                            double *w_dev, const double *r_dev, const double *f_ext_dev,
+                            double dt, int nsub);
+
+/* Wait for the stream; CFDEM_ECAPACITY or CFDEM_EINVAL (radius above
+ * max_radius) if a step since the last call met one (the flag is cleared). */
+cfdem_status cfdem_dem_synchronize(cfdem_dem_t dem);
+
+/* Text of the last error on this DEM state. */
+const char *cfdem_dem_last_error(cfdem_dem_t dem);
 
 #ifdef __cplusplus
 }

@@ -23,9 +23,20 @@ NOT_CONVERGED = -3
 ENOMEM = -4
 ECUDA = -5
 ESTATE = -6
+ECAPACITY = -7
 STATUS_NAMES = {0: "CFDEM_OK", -1: "CFDEM_EINVAL", -2: "CFDEM_OUT_OF_DOMAIN",
                 -3: "CFDEM_NOT_CONVERGED", -4: "CFDEM_ENOMEM", -5: "CFDEM_ECUDA",
-                -6: "CFDEM_ESTATE"}
+                -6: "CFDEM_ESTATE", -7: "CFDEM_ECAPACITY"}
+
+
+class cfdem_dem_params(C.Structure):
+    _fields_ = [("rho_p", C.c_double), ("youngs", C.c_double), ("poisson", C.c_double),
+                ("restitution", C.c_double), ("friction", C.c_double),
+                ("rolling_friction", C.c_double), ("wall_youngs", C.c_double),
+                ("wall_poisson", C.c_double), ("wall_restitution", C.c_double),
+                ("wall_friction", C.c_double), ("wall_rolling_friction", C.c_double),
+                ("g", C.c_double * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("max_radius", C.c_double), ("capacity", C.c_int)]
 
 
 class cfdem_params(C.Structure):
@@ -97,6 +108,16 @@ def lib():
     L.cfdem_project.argtypes = [vp, vp, vp]
     L.cfdem_forces.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.cfdem_fluid_drag_coefficients.argtypes = [vp, vp, vp]
+    L.cfdem_dem_params_default.argtypes = [C.POINTER(cfdem_dem_params)]
+    L.cfdem_dem_params_default.restype = None
+    L.cfdem_dem_create.argtypes = [C.POINTER(vp), C.c_int, vp]
+    L.cfdem_dem_destroy.argtypes = [vp]
+    L.cfdem_dem_set_params.argtypes = [vp, C.POINTER(cfdem_dem_params)]
+    L.cfdem_dem_reset.argtypes = [vp]
+    L.cfdem_dem_step.argtypes = [vp, i64, vp, vp, vp, vp, vp, C.c_double, C.c_int]
+    L.cfdem_dem_synchronize.argtypes = [vp]
+    L.cfdem_dem_last_error.argtypes = [vp]
+    L.cfdem_dem_last_error.restype = C.c_char_p
     L.cfdem_coupling_step.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.cfdem_synchronize.argtypes = [vp]
     L.cfdem_get_stats.argtypes = [vp, C.POINTER(cfdem_stats)]
@@ -371,3 +392,70 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------ DEM
+
+def _dcheck(h, st):
+    if st != OK:
+        raise CfdemError(st, lib().cfdem_dem_last_error(h).decode())
+    return st
+
+
+def dem_params(**kw):
+    """cfdem_dem_params from keyword arguments on top of the library defaults."""
+    p = cfdem_dem_params()
+    lib().cfdem_dem_params_default(C.byref(p))
+    for k, v in kw.items():
+        if k in ("g", "lo", "hi"):
+            arr = getattr(p, k)
+            for a in range(3):
+                arr[a] = float(v[a])
+        else:
+            setattr(p, k, v)
+    return p
+
+
+class Dem:
+    """Owns one DEM state; tensors are torch CUDA tensors (FP64)."""
+
+    def __init__(self, params=None, device=0, stream=None):
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream(device).cuda_stream
+        h = C.c_void_p()
+        st = lib().cfdem_dem_create(C.byref(h), int(device), C.c_void_p(stream))
+        if st != OK:
+            raise CfdemError(st, "cfdem_dem_create failed")
+        self.h = h
+        if params is not None:
+            self.set_params(params)
+
+    def set_params(self, params):
+        p = params if isinstance(params, cfdem_dem_params) else dem_params(**params)
+        _dcheck(self.h, lib().cfdem_dem_set_params(self.h, C.byref(p)))
+
+    def reset(self):
+        _dcheck(self.h, lib().cfdem_dem_reset(self.h))
+
+    def step(self, x, v, w, r, f_ext, dt, nsub):
+        n = x.shape[0]
+        return _dcheck(self.h, lib().cfdem_dem_step(self.h, int(n), _ptr(x), _ptr(v), _ptr(w),
+                                                    _ptr(r), _ptr(f_ext), float(dt), int(nsub)))
+
+    def synchronize(self):
+        return lib().cfdem_dem_synchronize(self.h)
+
+    def last_error(self):
+        return lib().cfdem_dem_last_error(self.h).decode()
+
+    def close(self):
+        if self.h:
+            lib().cfdem_dem_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,591 @@
+// dem.cu -- the DEM step of the particles (Sec. 2.2): Newton's laws for
+// translation and rotation (Eqs. newton_law, angular_momentum), soft-sphere
+// contacts with the non-linear visco-elastic model of Table (viscoelastic)
+// and Velocity Verlet integration, sub-cycled inside one CFD step with the
+// fluid force f_fp held (Sec. 2.3, f_coupling = dt_CFD / dt_DEM).
+//
+// Contact model per pair (unit normal n from i to its partner, overlap
+// d_n = r_i + r_j - |x_j - x_i|):
+//   k_n = 4/3 Y_e sqrt(R_e d_n), k_t = 8 G_e sqrt(R_e d_n),
+//   eta_n = -2 sqrt(5/6) beta sqrt(S_n m_e), eta_t = -2 sqrt(5/6) beta sqrt(S_t m_e),
+//   S_n = 2 Y_e sqrt(R_e d_n), S_t = 8 G_e sqrt(R_e d_n), beta = ln e / sqrt(ln^2 e + pi^2),
+//   f^n = -k_n d_n n - eta_n v_rn, f^t = -k_t d_t - eta_t v_rt,
+// with the effective mass, radius and moduli of the table.  The contact
+// point of i lies at r_i n; its velocity relative to the partner is
+// v_i - v_j + (r_i w_i + r_j w_j) x n.  The tangential displacement d_t is
+// carried per contact, turned onto the current tangent plane and advanced
+// by v_rt dt; a Coulomb limit mu_s |f^n| caps f^t (d_t reset to match);
+// rolling resistance M^r = -mu_r R_e |f^n| w_rel/|w_rel|; M^t = r_i n x f^t.
+// The box faces are walls of infinite mass and radius.
+//
+// GPU layout.  One thread per particle.  A cell list (edge >= 2 r_max) is
+// rebuilt by counting sort every sub-step; each particle gathers its
+// overlapping partners from the 27 cells around it into a list sorted by
+// partner index (capacity C per particle), merges it with its previous list
+// to carry d_t, and sums its contacts in that order, then the six walls,
+// gravity and the fluid force -- so the forces do not depend on the order
+// in which the cell list was filled, and no atomics touch a force.  Each
+// particle keeps its own copy of a pair's d_t (the partner's is its
+// negative), so i and j never write the same word.  All FP64.
+#include <cmath>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include "cfdem.h"
+#include "internal.h"
+
+namespace cfdem {
+namespace {
+
+constexpr int kDemMaxCap = 64;
+
+struct DemDev {
+  double rho, Y, nu, e, mus, mur;       // particles
+  double Yw, nuw, ew, musw, murw;       // walls
+  double g[3], lo[3], hi[3];
+  double rmax;
+  int nc[3];                            // cells per axis
+  double inv_ce[3];                     // 1 / cell edge
+  int cap;                              // contacts per particle
+};
+
+__device__ __forceinline__ void d_cross(const double* a, const double* b, double* c) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+__device__ __forceinline__ double d_dot(const double* a, const double* b) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+// one contact's force (added to F) and torque (added to T) on particle i,
+// advancing the carried tangential displacement th in place
+__device__ void dem_contact(const double* n, double dn, const double* vrel, const double* wrel,
+                            double ri, double me, double Re, double Ye, double Ge, double e,
+                            double mus, double mur, double dt, double* th, double* F, double* T) {
+  const double vn = d_dot(vrel, n);
+  double vrn[3], vrt[3];
+  for (int a = 0; a < 3; ++a) {
+    vrn[a] = vn * n[a];
+    vrt[a] = vrel[a] - vrn[a];
+  }
+  const double sq = sqrt(Re * dn);
+  const double kn = 4.0 / 3.0 * Ye * sq;
+  const double kt = 8.0 * Ge * sq;
+  const double Sn = 2.0 * Ye * sq;
+  const double St = 8.0 * Ge * sq;
+  const double le = log(e);
+  const double beta = le / sqrt(le * le + kPi * kPi);
+  const double c56 = -2.0 * sqrt(5.0 / 6.0) * beta;
+  const double etan = c56 * sqrt(Sn * me);
+  const double etat = c56 * sqrt(St * me);
+  const double hn = d_dot(th, n);
+  for (int a = 0; a < 3; ++a) th[a] = th[a] - hn * n[a] + vrt[a] * dt;
+  double fn[3], ft[3];
+  for (int a = 0; a < 3; ++a) {
+    fn[a] = -(kn * dn) * n[a] - etan * vrn[a];
+    ft[a] = -kt * th[a] - etat * vrt[a];
+  }
+  const double fnm = sqrt(d_dot(fn, fn));
+  const double ftm = sqrt(d_dot(ft, ft));
+  if (ftm > mus * fnm) {
+    const double s = mus * fnm / ftm;
+    for (int a = 0; a < 3; ++a) {
+      ft[a] = ft[a] * s;
+      th[a] = -(ft[a] + etat * vrt[a]) / kt;
+    }
+  }
+  const double arm[3] = {ri * n[0], ri * n[1], ri * n[2]};
+  double mt[3];
+  d_cross(arm, ft, mt);
+  const double wm = sqrt(d_dot(wrel, wrel));
+  for (int a = 0; a < 3; ++a) {
+    F[a] += fn[a] + ft[a];
+    T[a] += mt[a];
+    if (wm > 0.0) T[a] += -mur * Re * fnm * wrel[a] / wm;
+  }
+}
+
+__device__ __forceinline__ int cell_axis(double x, double lo, double inv_ce, int nc) {
+  int c = (int)floor((x - lo) * inv_ce);
+  return c < 0 ? 0 : (c > nc - 1 ? nc - 1 : c);
+}
+
+// first half kick and drift
+__global__ void k_dem_kick_drift(int64_t n, double dt, double* __restrict__ x,
+                                 double* __restrict__ v, double* __restrict__ w,
+                                 const double* __restrict__ acc,
+                                 const double* __restrict__ alpha) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= 3 * n) return;
+  v[t] += 0.5 * dt * acc[t];
+  w[t] += 0.5 * dt * alpha[t];
+  x[t] += dt * v[t];
+}
+
+// second half kick
+__global__ void k_dem_kick(int64_t n, double dt, double* __restrict__ v, double* __restrict__ w,
+                           const double* __restrict__ acc, const double* __restrict__ alpha) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= 3 * n) return;
+  v[t] += 0.5 * dt * acc[t];
+  w[t] += 0.5 * dt * alpha[t];
+}
+
+// cell of every particle and its slot in the cell (counting sort, pass 1);
+// a radius above the stated maximum raises the flag
+__global__ void k_dem_cell_count(int64_t n, DemDev p, const double* __restrict__ x,
+                                 const double* __restrict__ r, int32_t* __restrict__ cell_of,
+                                 int32_t* __restrict__ slot, int32_t* __restrict__ count,
+                                 int* __restrict__ flags) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int cx = cell_axis(x[3 * i], p.lo[0], p.inv_ce[0], p.nc[0]);
+  const int cy = cell_axis(x[3 * i + 1], p.lo[1], p.inv_ce[1], p.nc[1]);
+  const int cz = cell_axis(x[3 * i + 2], p.lo[2], p.inv_ce[2], p.nc[2]);
+  const int c = cx + p.nc[0] * (cy + p.nc[1] * cz);
+  cell_of[i] = c;
+  slot[i] = atomicAdd(count + c, 1);
+  if (!(r[i] <= p.rmax)) atomicOr(flags, 2);
+}
+
+// exclusive scan of count[0..nc) into start[0..nc], one block: each thread
+// sums a contiguous chunk, the chunk sums are scanned in shared memory
+__global__ void __launch_bounds__(1024)
+k_dem_scan(int ncells, const int32_t* __restrict__ count, int32_t* __restrict__ start) {
+  __shared__ int32_t part[1024];
+  const int t = threadIdx.x;
+  const int chunk = (ncells + 1023) / 1024;
+  const int b = t * chunk, e = b + chunk < ncells ? b + chunk : ncells;
+  int32_t s = 0;
+  for (int c = b; c < e; ++c) s += count[c];
+  part[t] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    int32_t v = t >= off ? part[t - off] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  int32_t run = t > 0 ? part[t - 1] : 0;
+  for (int c = b; c < e; ++c) {
+    start[c] = run;
+    run += count[c];
+  }
+  if (t == 1023) start[ncells] = part[1023];
+}
+
+__global__ void k_dem_cell_scatter(int64_t n, const int32_t* __restrict__ cell_of,
+                                   const int32_t* __restrict__ slot,
+                                   const int32_t* __restrict__ start, int32_t* __restrict__ perm) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  perm[start[cell_of[i]] + slot[i]] = (int32_t)i;
+}
+
+// forces and torques on every particle; tangential displacements advance by
+// dt (0 for the first evaluation of a fresh state)
+__global__ void __launch_bounds__(128)
+k_dem_forces(int64_t n, DemDev p, double dt, const double* __restrict__ x,
+             const double* __restrict__ v, const double* __restrict__ w,
+             const double* __restrict__ r, const double* __restrict__ f_ext,
+             const int32_t* __restrict__ start, const int32_t* __restrict__ perm,
+             const int32_t* __restrict__ hj_old, const double* __restrict__ ht_old,
+             int32_t* __restrict__ hj_new, double* __restrict__ ht_new, double* __restrict__ wh,
+             double* __restrict__ acc, double* __restrict__ alpha, int* __restrict__ flags) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int C = p.cap;
+  const double xi[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+  const double ri = r[i];
+  // partners, sorted by index (insertion into a list of at most C)
+  int32_t cand[kDemMaxCap];
+  int nc = 0;
+  const int cx = cell_axis(xi[0], p.lo[0], p.inv_ce[0], p.nc[0]);
+  const int cy = cell_axis(xi[1], p.lo[1], p.inv_ce[1], p.nc[1]);
+  const int cz = cell_axis(xi[2], p.lo[2], p.inv_ce[2], p.nc[2]);
+  for (int dz = -1; dz <= 1; ++dz) {
+    const int z = cz + dz;
+    if (z < 0 || z >= p.nc[2]) continue;
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int y = cy + dy;
+      if (y < 0 || y >= p.nc[1]) continue;
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int xx = cx + dx;
+        if (xx < 0 || xx >= p.nc[0]) continue;
+        const int c = xx + p.nc[0] * (y + p.nc[1] * z);
+        for (int s = start[c]; s < start[c + 1]; ++s) {
+          const int32_t j = perm[s];
+          if (j == i) continue;
+          const double d[3] = {x[3 * j] - xi[0], x[3 * j + 1] - xi[1], x[3 * j + 2] - xi[2]};
+          const double dist = sqrt(d_dot(d, d));
+          if (!(dist < ri + r[j] && dist > 0.0)) continue;
+          if (nc == C) {
+            atomicOr(flags, 1);
+            continue;
+          }
+          int q = nc++;
+          while (q > 0 && cand[q - 1] > j) {
+            cand[q] = cand[q - 1];
+            --q;
+          }
+          cand[q] = j;
+        }
+      }
+    }
+  }
+  const double mi = p.rho * (4.0 / 3.0 * kPi) * ri * ri * ri;
+  const double Ii = 0.4 * mi * ri * ri;
+  double F[3] = {0.0, 0.0, 0.0}, T[3] = {0.0, 0.0, 0.0};
+  const double Ye = 1.0 / ((1.0 - p.nu * p.nu) / p.Y + (1.0 - p.nu * p.nu) / p.Y);
+  const double Ge = 1.0 / (2.0 * (2.0 - p.nu) * (1.0 + p.nu) / p.Y +
+                           2.0 * (2.0 - p.nu) * (1.0 + p.nu) / p.Y);
+  int o = 0;  // cursor in the previous (sorted) list
+  for (int c = 0; c < nc; ++c) {
+    const int32_t j = cand[c];
+    const double d[3] = {x[3 * j] - xi[0], x[3 * j + 1] - xi[1], x[3 * j + 2] - xi[2]};
+    const double dist = sqrt(d_dot(d, d));
+    const double nrm[3] = {d[0] / dist, d[1] / dist, d[2] / dist};
+    const double rj = r[j];
+    const double dn = ri + rj - dist;
+    const double mj = p.rho * (4.0 / 3.0 * kPi) * rj * rj * rj;
+    const double me = 1.0 / (1.0 / mi + 1.0 / mj);
+    const double Re = 1.0 / (1.0 / ri + 1.0 / rj);
+    const double ws[3] = {ri * w[3 * i] + rj * w[3 * j], ri * w[3 * i + 1] + rj * w[3 * j + 1],
+                          ri * w[3 * i + 2] + rj * w[3 * j + 2]};
+    double wxn[3];
+    d_cross(ws, nrm, wxn);
+    double vrel[3], wrel[3];
+    for (int a = 0; a < 3; ++a) {
+      vrel[a] = v[3 * i + a] - v[3 * j + a] + wxn[a];
+      wrel[a] = w[3 * i + a] - w[3 * j + a];
+    }
+    double th[3] = {0.0, 0.0, 0.0};
+    while (o < C && hj_old[i * C + o] >= 0 && hj_old[i * C + o] < j) ++o;
+    if (o < C && hj_old[i * C + o] == j)
+      for (int a = 0; a < 3; ++a) th[a] = ht_old[(i * C + o) * 3 + a];
+    dem_contact(nrm, dn, vrel, wrel, ri, me, Re, Ye, Ge, p.e, p.mus, p.mur, dt, th, F, T);
+    hj_new[i * C + c] = j;
+    for (int a = 0; a < 3; ++a) ht_new[(i * C + c) * 3 + a] = th[a];
+  }
+  for (int c = nc; c < C; ++c) hj_new[i * C + c] = -1;
+  // walls x-, x+, y-, y+, z-, z+
+  const double Yew = 1.0 / ((1.0 - p.nu * p.nu) / p.Y + (1.0 - p.nuw * p.nuw) / p.Yw);
+  const double Gew = 1.0 / (2.0 * (2.0 - p.nu) * (1.0 + p.nu) / p.Y +
+                            2.0 * (2.0 - p.nuw) * (1.0 + p.nuw) / p.Yw);
+  for (int wl = 0; wl < 6; ++wl) {
+    const int ax = wl / 2;
+    double nrm[3] = {0.0, 0.0, 0.0};
+    double dn;
+    if (wl % 2 == 0) {
+      nrm[ax] = -1.0;
+      dn = ri - (xi[ax] - p.lo[ax]);
+    } else {
+      nrm[ax] = 1.0;
+      dn = ri - (p.hi[ax] - xi[ax]);
+    }
+    double* th = wh + (i * 6 + wl) * 3;
+    if (!(dn > 0.0)) {
+      th[0] = th[1] = th[2] = 0.0;
+      continue;
+    }
+    const double rw[3] = {ri * w[3 * i], ri * w[3 * i + 1], ri * w[3 * i + 2]};
+    double wxn[3];
+    d_cross(rw, nrm, wxn);
+    const double vrel[3] = {v[3 * i] + wxn[0], v[3 * i + 1] + wxn[1], v[3 * i + 2] + wxn[2]};
+    const double wrel[3] = {w[3 * i], w[3 * i + 1], w[3 * i + 2]};
+    double t3[3] = {th[0], th[1], th[2]};
+    dem_contact(nrm, dn, vrel, wrel, ri, mi, ri, Yew, Gew, p.ew, p.musw, p.murw, dt, t3, F, T);
+    th[0] = t3[0];
+    th[1] = t3[1];
+    th[2] = t3[2];
+  }
+  for (int a = 0; a < 3; ++a) {
+    const double fa = F[a] + mi * p.g[a] + (f_ext ? f_ext[3 * i + a] : 0.0);
+    acc[3 * i + a] = fa / mi;
+    alpha[3 * i + a] = T[a] / Ii;
+  }
+}
+
+}  // namespace
+}  // namespace cfdem
+
+using namespace cfdem;
+
+struct cfdem_dem {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cfdem_dem_params prm{};
+  bool have_prm = false;
+  DemDev dd{};
+  int64_t n = -1;        // particle count the state belongs to
+  int have_acc = 0;
+  int cur = 0;           // which history buffer holds the last lists
+  int64_t cap_n = 0, cap_cells = 0, cap_h = 0;
+  double *acc = nullptr, *alpha = nullptr, *ht[2] = {nullptr, nullptr}, *wh = nullptr;
+  int32_t *hj[2] = {nullptr, nullptr};
+  int32_t *cell_of = nullptr, *slot = nullptr, *perm = nullptr, *count = nullptr,
+          *start = nullptr;
+  int* flags = nullptr;
+  std::string err;
+};
+
+namespace {
+
+cfdem_status dfail(cfdem_dem_t d, cfdem_status s, const char* fmt, ...) {
+  if (d) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    d->err = buf;
+  }
+  return s;
+}
+
+cfdem_status dcuda(cfdem_dem_t d, cudaError_t e, const char* where) {
+  if (e == cudaErrorMemoryAllocation)
+    return dfail(d, CFDEM_ENOMEM, "%s: out of device memory", where);
+  return dfail(d, CFDEM_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define DCK(expr, where)                                  \
+  do {                                                    \
+    cudaError_t e_ = (expr);                              \
+    if (e_ != cudaSuccess) return dcuda(d, e_, where);    \
+  } while (0)
+
+struct DevGuard {
+  int prev = -1;
+  explicit DevGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DevGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+void cfdem_dem_params_default(cfdem_dem_params* p) {
+  if (!p) return;
+  *p = cfdem_dem_params{};
+  p->rho_p = 2500.0;
+  p->youngs = 1e7;
+  p->poisson = 0.3;
+  p->restitution = 0.9;
+  p->friction = 0.3;
+  p->rolling_friction = 0.0;
+  p->wall_youngs = 1e7;
+  p->wall_poisson = 0.3;
+  p->wall_restitution = 0.9;
+  p->wall_friction = 0.3;
+  p->wall_rolling_friction = 0.0;
+  p->g[2] = -9.81;
+  p->capacity = 24;
+}
+
+cfdem_status cfdem_dem_create(cfdem_dem_t* out, int device, void* stream) {
+  if (!out) return CFDEM_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+    return CFDEM_ECUDA;
+  cfdem_dem* d = new cfdem_dem();
+  d->device = device;
+  d->stream = reinterpret_cast<cudaStream_t>(stream);
+  DevGuard g(device);
+  if (cudaMalloc(&d->flags, sizeof(int)) != cudaSuccess) {
+    delete d;
+    return CFDEM_ENOMEM;
+  }
+  if (cudaMemset(d->flags, 0, sizeof(int)) != cudaSuccess) {
+    cudaFree(d->flags);
+    delete d;
+    return CFDEM_ECUDA;
+  }
+  *out = d;
+  return CFDEM_OK;
+}
+
+cfdem_status cfdem_dem_destroy(cfdem_dem_t d) {
+  if (!d) return CFDEM_OK;
+  DevGuard g(d->device);
+  if (d->stream) cudaStreamSynchronize(d->stream);
+  else cudaDeviceSynchronize();
+  void* ps[] = {d->acc, d->alpha, d->ht[0], d->ht[1], d->wh, d->hj[0], d->hj[1], d->cell_of,
+                d->slot, d->perm, d->count, d->start, d->flags};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  delete d;
+  return CFDEM_OK;
+}
+
+cfdem_status cfdem_dem_set_params(cfdem_dem_t d, const cfdem_dem_params* p) {
+  if (!d || !p) return dfail(d, CFDEM_EINVAL, "null argument");
+  const double vals[] = {p->rho_p, p->youngs, p->wall_youngs, p->max_radius};
+  for (double v : vals)
+    if (!(v > 0.0) || !std::isfinite(v))
+      return dfail(d, CFDEM_EINVAL, "rho_p, youngs, wall_youngs and max_radius must be > 0");
+  if (!(p->poisson > -1.0 && p->poisson < 0.5) || !(p->wall_poisson > -1.0 && p->wall_poisson < 0.5))
+    return dfail(d, CFDEM_EINVAL, "Poisson ratios must lie in (-1, 0.5)");
+  if (!(p->restitution > 0.0 && p->restitution <= 1.0) ||
+      !(p->wall_restitution > 0.0 && p->wall_restitution <= 1.0))
+    return dfail(d, CFDEM_EINVAL, "coefficients of restitution must lie in (0, 1]");
+  if (!(p->friction >= 0.0) || !(p->wall_friction >= 0.0) || !(p->rolling_friction >= 0.0) ||
+      !(p->wall_rolling_friction >= 0.0))
+    return dfail(d, CFDEM_EINVAL, "friction coefficients must be >= 0");
+  if (p->capacity < 1 || p->capacity > kDemMaxCap)
+    return dfail(d, CFDEM_EINVAL, "capacity must be 1..%d", kDemMaxCap);
+  for (int a = 0; a < 3; ++a)
+    if (!(p->hi[a] > p->lo[a]) || !std::isfinite(p->lo[a]) || !std::isfinite(p->hi[a]))
+      return dfail(d, CFDEM_EINVAL, "box: hi must exceed lo on every axis");
+  DemDev& q = d->dd;
+  q.rho = p->rho_p;
+  q.Y = p->youngs;
+  q.nu = p->poisson;
+  q.e = p->restitution;
+  q.mus = p->friction;
+  q.mur = p->rolling_friction;
+  q.Yw = p->wall_youngs;
+  q.nuw = p->wall_poisson;
+  q.ew = p->wall_restitution;
+  q.musw = p->wall_friction;
+  q.murw = p->wall_rolling_friction;
+  q.rmax = p->max_radius;
+  int64_t tot = 1;
+  for (int a = 0; a < 3; ++a) {
+    q.g[a] = p->g[a];
+    q.lo[a] = p->lo[a];
+    q.hi[a] = p->hi[a];
+    double f = std::floor((p->hi[a] - p->lo[a]) / (2.0 * p->max_radius));
+    int nc = f < 1.0 ? 1 : (f > 4096.0 ? 4096 : (int)f);
+    q.nc[a] = nc;
+    q.inv_ce[a] = nc / (p->hi[a] - p->lo[a]);
+    tot *= nc;
+  }
+  if (tot > ((int64_t)1 << 28)) return dfail(d, CFDEM_EINVAL, "too many cells");
+  q.cap = p->capacity;
+  const bool resize = !d->have_prm || d->prm.capacity != p->capacity;
+  d->prm = *p;
+  d->have_prm = true;
+  if (resize) d->n = -1;  // history layout changes with the capacity
+  d->have_acc = 0;        // accelerations depend on the parameters
+  return CFDEM_OK;
+}
+
+cfdem_status cfdem_dem_reset(cfdem_dem_t d) {
+  if (!d) return CFDEM_EINVAL;
+  d->n = -1;
+  d->have_acc = 0;
+  return CFDEM_OK;
+}
+
+cfdem_status cfdem_dem_step(cfdem_dem_t d, int64_t n, double* x, double* v, double* w,
+                            const double* r, const double* f_ext, double dt, int nsub) {
+  if (!d) return CFDEM_EINVAL;
+  if (!d->have_prm) return dfail(d, CFDEM_ESTATE, "cfdem_dem_set_params first");
+  if (n < 0 || n >= ((int64_t)1 << 31) || (n > 0 && (!x || !v || !w || !r)))
+    return dfail(d, CFDEM_EINVAL, "null input or bad count");
+  if (!(dt > 0.0) || nsub < 0) return dfail(d, CFDEM_EINVAL, "dt must be > 0, nsub >= 0");
+  if (n == 0 || nsub == 0) return CFDEM_OK;
+  DevGuard g(d->device);
+  cudaStream_t s = d->stream;
+  const int C = d->prm.capacity;
+  const int64_t ncells = (int64_t)d->dd.nc[0] * d->dd.nc[1] * d->dd.nc[2];
+  if (n != d->n) {  // a new particle set: fresh state
+    if (n > d->cap_n || (int64_t)n * C > d->cap_h) {
+      void* old[] = {d->acc, d->alpha, d->wh, d->cell_of, d->slot, d->perm,
+                     d->hj[0], d->hj[1], d->ht[0], d->ht[1]};
+      for (void* q : old)
+        if (q) cudaFree(q);
+      d->acc = d->alpha = d->wh = d->ht[0] = d->ht[1] = nullptr;
+      d->cell_of = d->slot = d->perm = d->hj[0] = d->hj[1] = nullptr;
+      d->cap_n = d->cap_h = 0;
+      const int64_t cap = n + n / 4 + 256;
+      DCK(cudaMalloc(&d->acc, sizeof(double) * 3 * cap), "dem arena");
+      DCK(cudaMalloc(&d->alpha, sizeof(double) * 3 * cap), "dem arena");
+      DCK(cudaMalloc(&d->wh, sizeof(double) * 18 * cap), "dem arena");
+      DCK(cudaMalloc(&d->cell_of, sizeof(int32_t) * cap), "dem arena");
+      DCK(cudaMalloc(&d->slot, sizeof(int32_t) * cap), "dem arena");
+      DCK(cudaMalloc(&d->perm, sizeof(int32_t) * cap), "dem arena");
+      DCK(cudaMalloc(&d->hj[0], sizeof(int32_t) * cap * C), "dem arena");
+      DCK(cudaMalloc(&d->hj[1], sizeof(int32_t) * cap * C), "dem arena");
+      DCK(cudaMalloc(&d->ht[0], sizeof(double) * 3 * cap * C), "dem arena");
+      DCK(cudaMalloc(&d->ht[1], sizeof(double) * 3 * cap * C), "dem arena");
+      d->cap_n = cap;
+      d->cap_h = cap * C;
+    }
+    DCK(cudaMemsetAsync(d->hj[0], 0xff, sizeof(int32_t) * n * C, s), "dem reset");
+    DCK(cudaMemsetAsync(d->wh, 0, sizeof(double) * 18 * n, s), "dem reset");
+    d->cur = 0;
+    d->n = n;
+    d->have_acc = 0;
+  }
+  if (ncells + 1 > d->cap_cells) {
+    if (d->count) cudaFree(d->count);
+    if (d->start) cudaFree(d->start);
+    d->count = d->start = nullptr;
+    d->cap_cells = 0;
+    DCK(cudaMalloc(&d->count, sizeof(int32_t) * ncells), "dem cells");
+    DCK(cudaMalloc(&d->start, sizeof(int32_t) * (ncells + 1)), "dem cells");
+    d->cap_cells = ncells + 1;
+  }
+  const unsigned nb = (unsigned)((n + 127) / 128), nb3 = (unsigned)((3 * n + 255) / 256);
+  auto forces = [&](double hdt) -> cudaError_t {
+    cudaError_t e = cudaMemsetAsync(d->count, 0, sizeof(int32_t) * ncells, s);
+    if (e != cudaSuccess) return e;
+    k_dem_cell_count<<<nb, 128, 0, s>>>(n, d->dd, x, r, d->cell_of, d->slot, d->count,
+                                        d->flags);
+    k_dem_scan<<<1, 1024, 0, s>>>((int)ncells, d->count, d->start);
+    k_dem_cell_scatter<<<nb, 128, 0, s>>>(n, d->cell_of, d->slot, d->start, d->perm);
+    const int o = d->cur, nw = 1 - d->cur;
+    k_dem_forces<<<nb, 128, 0, s>>>(n, d->dd, hdt, x, v, w, r, f_ext, d->start, d->perm,
+                                    d->hj[o], d->ht[o], d->hj[nw], d->ht[nw], d->wh, d->acc,
+                                    d->alpha, d->flags);
+    count_launches(4);
+    d->cur = nw;
+    return cudaGetLastError();
+  };
+  if (!d->have_acc) {
+    DCK(forces(0.0), "dem forces");
+    d->have_acc = 1;
+  }
+  for (int it = 0; it < nsub; ++it) {
+    k_dem_kick_drift<<<nb3, 256, 0, s>>>(n, dt, x, v, w, d->acc, d->alpha);
+    count_launches(1);
+    DCK(cudaGetLastError(), "dem drift");
+    DCK(forces(dt), "dem forces");
+    k_dem_kick<<<nb3, 256, 0, s>>>(n, dt, v, w, d->acc, d->alpha);
+    count_launches(1);
+    DCK(cudaGetLastError(), "dem kick");
+  }
+  return CFDEM_OK;
+}
+
+cfdem_status cfdem_dem_synchronize(cfdem_dem_t d) {
+  if (!d) return CFDEM_EINVAL;
+  DevGuard g(d->device);
+  int h = 0;
+  DCK(cudaMemcpyAsync(&h, d->flags, sizeof(int), cudaMemcpyDeviceToHost, d->stream),
+      "dem status");
+  DCK(cudaStreamSynchronize(d->stream), "dem synchronize");
+  if (h) {
+    DCK(cudaMemsetAsync(d->flags, 0, sizeof(int), d->stream), "dem status");
+    DCK(cudaStreamSynchronize(d->stream), "dem synchronize");
+    if (h & 2) return dfail(d, CFDEM_EINVAL, "a particle radius exceeds max_radius");
+    return dfail(d, CFDEM_ECAPACITY, "a particle had more contacts than the capacity");
+  }
+  return CFDEM_OK;
+}
+
+const char* cfdem_dem_last_error(cfdem_dem_t d) { return d ? d->err.c_str() : "null handle"; }
+
+}  // extern "C"

@@ -1,0 +1,94 @@
+"""The DEM step on the GPU (cfdem_dem_*) against the FP64 oracle of
+oracle/dem_oracle.c: a packed, slightly compressed bed in a box with walls,
+spinning and moving particles and a held fluid force; exactness of free
+fall; the contact memory carried from call to call; bit-for-bit
+reproducibility; and the capacity and radius checks."""
+import math
+
+import numpy as np
+import pytest
+
+from _parity import dev, host, rel_err
+from oracle import dem as D
+from paper_2211_01185_gb300 import cfdem as cf
+from paper_2211_01185_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _bed(seed=5, n=400, box=(0.02, 0.02, 0.03)):
+    rng = np.random.default_rng(seed)
+    lo = np.zeros(3)
+    hi = np.asarray(box)
+    r = rng.uniform(0.8e-3, 1.2e-3, n)
+    x = synth.rsa(rng, n, 0.0, lo + 1.2e-3, hi - 1.2e-3, radii=r * 0.97)   # small overlaps
+    v = 0.05 * rng.standard_normal((n, 3))
+    w = 20.0 * rng.standard_normal((n, 3))
+    fe = 1e-6 * rng.standard_normal((n, 3))
+    p = D.glass_params(lo, hi, restitution=0.7, wall_restitution=0.8, friction=0.4,
+                       wall_friction=0.3, rolling_friction=0.02, wall_rolling_friction=0.01)
+    return x, v, w, r, fe, p
+
+
+def _gpu_params(p, r):
+    kw = {k: p[k] for k in D.PARAM_KEYS}
+    return dict(kw, g=p["g"], lo=p["lo"], hi=p["hi"], max_radius=float(r.max()), capacity=24)
+
+
+def _run_gpu(x, v, w, r, fe, p, dt, chunks):
+    tx, tv, tw = dev(x), dev(v), dev(w)
+    with cf.Dem(_gpu_params(p, r)) as dm:
+        for k in chunks:
+            dm.step(tx, tv, tw, dev(r), dev(fe), dt, k)
+        assert dm.synchronize() == cf.OK, dm.last_error()
+    return host(tx), host(tv), host(tw)
+
+
+def test_matches_oracle():
+    x, v, w, r, fe, p = _bed()
+    ref = D.State(x, v, w, r)
+    dt, k = 2e-6, 60
+    assert ref.step(p, dt, k, f_ext=fe) == 0
+    gx, gv, gw = _run_gpu(x, v, w, r, fe, p, dt, [k])
+    assert rel_err(gx - x, ref.x - x) <= 1e-9
+    assert rel_err(gv, ref.v) <= 1e-9
+    assert rel_err(gw, ref.w) <= 1e-9
+    assert np.abs(ref.v - v).max() > 1e-3        # the contacts did act
+
+
+def test_history_carries_over_calls_and_is_reproducible():
+    x, v, w, r, fe, p = _bed(seed=6)
+    a = _run_gpu(x, v, w, r, fe, p, 2e-6, [40])
+    b = _run_gpu(x, v, w, r, fe, p, 2e-6, [15, 25])
+    c = _run_gpu(x, v, w, r, fe, p, 2e-6, [40])
+    for u, t in zip(a, b):
+        assert np.array_equal(u, t)
+    for u, t in zip(a, c):
+        assert np.array_equal(u, t)
+
+
+def test_free_fall_is_exact():
+    p = D.glass_params((0, 0, 0), (0.02, 0.02, 0.02))
+    x = np.array([[0.01, 0.01, 0.015]])
+    v = np.array([[0.01, -0.02, 0.3]])
+    gx, gv, _ = _run_gpu(x, v, np.zeros((1, 3)), np.array([1e-3]), np.zeros((1, 3)), p, 1e-5,
+                         [200])
+    t = 2e-3
+    want = np.array([0.01 + 0.01 * t, 0.01 - 0.02 * t, 0.015 + 0.3 * t - 0.5 * 9.81 * t * t])
+    assert np.allclose(gx[0], want, rtol=0, atol=1e-15)
+    assert np.allclose(gv[0], [0.01, -0.02, 0.3 - 9.81 * t], rtol=0, atol=1e-14)
+
+
+def test_capacity_and_radius_checks():
+    x, v, w, r, fe, p = _bed(seed=7, n=60)
+    prm = _gpu_params(p, r)
+    tx, tv, tw = dev(x), dev(v), dev(w)
+    with cf.Dem(dict(prm, capacity=1)) as dm:
+        x2 = x.copy()
+        x2[1] = x2[0] + [1.5e-3, 0, 0]
+        x2[2] = x2[0] - [1.5e-3, 0, 0]                # particle 0 touches two
+        dm.step(dev(x2), tv, tw, dev(r), None, 1e-7, 1)
+        assert dm.synchronize() == cf.ECAPACITY
+    with cf.Dem(dict(prm, max_radius=0.5 * float(r.max()))) as dm:
+        dm.step(tx, tv, tw, dev(r), None, 1e-7, 1)
+        assert dm.synchronize() == cf.EINVAL

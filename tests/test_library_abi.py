@@ -47,6 +47,10 @@ int main(void) {
   printf("cfdem_bed_io %zu\n", sizeof(cfdem_bed_io));
   P(cfdem_bed_io, n); P(cfdem_bed_io, x); P(cfdem_bed_io, p_nodal); P(cfdem_bed_io, eps_nodal);
   P(cfdem_bed_io, F_q);
+  printf("cfdem_dem_params %zu\n", sizeof(cfdem_dem_params));
+  P(cfdem_dem_params, rolling_friction); P(cfdem_dem_params, wall_rolling_friction);
+  P(cfdem_dem_params, g); P(cfdem_dem_params, hi); P(cfdem_dem_params, max_radius);
+  P(cfdem_dem_params, capacity);
   return 0;
 }
 '''
@@ -61,6 +65,7 @@ int main(void) {
     assert int(got["cfdem_params"]) == C.sizeof(cf.cfdem_params)
     assert int(got["cfdem_stats"]) == C.sizeof(cf.cfdem_stats)
     assert int(got["cfdem_bed_io"]) == C.sizeof(cf.cfdem_bed_io)
+    assert int(got["cfdem_dem_params"]) == C.sizeof(cf.cfdem_dem_params)
     for key, val in got.items():
         if "." in key:
             s, f = key.split(".")
