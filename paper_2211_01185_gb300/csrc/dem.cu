@@ -49,6 +49,10 @@ struct DemDev {
   int nc[3];                            // cells per axis
   double inv_ce[3];                     // 1 / cell edge
   int cap;                              // contacts per particle
+  // host-computed constants: -2 sqrt(5/6) beta(e) for particle pairs and
+  // walls, effective Young's and shear moduli of particle-particle and
+  // particle-wall contacts
+  double c56, c56w, Ye, Ge, Yew, Gew;
 };
 
 __device__ __forceinline__ void d_cross(const double* a, const double* b, double* c) {
@@ -63,7 +67,7 @@ __device__ __forceinline__ double d_dot(const double* a, const double* b) {
 // one contact's force (added to F) and torque (added to T) on particle i,
 // advancing the carried tangential displacement th in place
 __device__ void dem_contact(const double* n, double dn, const double* vrel, const double* wrel,
-                            double ri, double me, double Re, double Ye, double Ge, double e,
+                            double ri, double me, double Re, double Ye, double Ge, double c56,
                             double mus, double mur, double dt, double* th, double* F, double* T) {
   const double vn = d_dot(vrel, n);
   double vrn[3], vrt[3];
@@ -76,9 +80,6 @@ __device__ void dem_contact(const double* n, double dn, const double* vrel, cons
   const double kt = 8.0 * Ge * sq;
   const double Sn = 2.0 * Ye * sq;
   const double St = 8.0 * Ge * sq;
-  const double le = log(e);
-  const double beta = le / sqrt(le * le + kPi * kPi);
-  const double c56 = -2.0 * sqrt(5.0 / 6.0) * beta;
   const double etan = c56 * sqrt(Sn * me);
   const double etat = c56 * sqrt(St * me);
   const double hn = d_dot(th, n);
@@ -151,30 +152,80 @@ __global__ void k_dem_cell_count(int64_t n, DemDev p, const double* __restrict__
   if (!(r[i] <= p.rmax)) atomicOr(flags, 2);
 }
 
-// exclusive scan of count[0..nc) into start[0..nc], one block: each thread
-// sums a contiguous chunk, the chunk sums are scanned in shared memory
-__global__ void __launch_bounds__(1024)
-k_dem_scan(int ncells, const int32_t* __restrict__ count, int32_t* __restrict__ start) {
-  __shared__ int32_t part[1024];
-  const int t = threadIdx.x;
-  const int chunk = (ncells + 1023) / 1024;
-  const int b = t * chunk, e = b + chunk < ncells ? b + chunk : ncells;
-  int32_t s = 0;
-  for (int c = b; c < e; ++c) s += count[c];
-  part[t] = s;
+// exclusive scan of count[0..nc) into start[0..nc]: tiles of 1024 cells
+// (256 threads x 4) are summed, the tile sums scanned by one block, then
+// every tile scans itself from its offset
+constexpr int kScanTile = 1024;
+
+__device__ __forceinline__ int32_t block_excl_scan256(int32_t v, int32_t* sh, int32_t* total) {
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  int32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[wid] = x;
   __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {
-    int32_t v = t >= off ? part[t - off] : 0;
-    __syncthreads();
-    part[t] += v;
-    __syncthreads();
+  if (wid == 0) {
+    int32_t wsum = lane < 8 ? sh[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, wsum, o);
+      if (lane >= o) wsum += y;
+    }
+    if (lane < 8) sh[8 + lane] = wsum;
   }
-  int32_t run = t > 0 ? part[t - 1] : 0;
-  for (int c = b; c < e; ++c) {
-    start[c] = run;
-    run += count[c];
+  __syncthreads();
+  const int32_t before = wid > 0 ? sh[8 + wid - 1] : 0;
+  *total = sh[15];
+  __syncthreads();
+  return before + x - v;
+}
+
+__global__ void __launch_bounds__(256)
+k_dem_scan_tiles(int ncells, const int32_t* __restrict__ count, int32_t* __restrict__ tsum) {
+  __shared__ int32_t sh[16];
+  const int base = blockIdx.x * kScanTile + threadIdx.x * 4;
+  int32_t v = 0;
+  for (int q = 0; q < 4; ++q) v += base + q < ncells ? count[base + q] : 0;
+  int32_t tot;
+  block_excl_scan256(v, sh, &tot);
+  if (threadIdx.x == 0) tsum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(256)
+k_dem_scan_sums(int ntiles, int32_t* __restrict__ tsum) {  // in place, exclusive; tsum[ntiles] = total
+  __shared__ int32_t sh[16];
+  int32_t run = 0;
+  for (int b0 = 0; b0 < ntiles; b0 += 256) {
+    const int b = b0 + threadIdx.x;
+    const int32_t v = b < ntiles ? tsum[b] : 0;
+    int32_t tot;
+    const int32_t ex = block_excl_scan256(v, sh, &tot);
+    if (b < ntiles) tsum[b] = run + ex;
+    run += tot;
   }
-  if (t == 1023) start[ncells] = part[1023];
+  if (threadIdx.x == 0) tsum[ntiles] = run;
+}
+
+__global__ void __launch_bounds__(256)
+k_dem_scan_final(int ncells, const int32_t* __restrict__ count,
+                 const int32_t* __restrict__ tsum, int32_t* __restrict__ start) {
+  __shared__ int32_t sh[16];
+  const int base = blockIdx.x * kScanTile + threadIdx.x * 4;
+  int32_t c[4], v = 0;
+  for (int q = 0; q < 4; ++q) {
+    c[q] = base + q < ncells ? count[base + q] : 0;
+    v += c[q];
+  }
+  int32_t tot;
+  int32_t run = tsum[blockIdx.x] + block_excl_scan256(v, sh, &tot);
+  for (int q = 0; q < 4; ++q) {
+    if (base + q < ncells) start[base + q] = run;
+    run += c[q];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) start[ncells] = tsum[gridDim.x];
 }
 
 __global__ void k_dem_cell_scatter(int64_t n, const int32_t* __restrict__ cell_of,
@@ -220,8 +271,11 @@ k_dem_forces(int64_t n, DemDev p, double dt, const double* __restrict__ x,
           const int32_t j = perm[s];
           if (j == i) continue;
           const double d[3] = {x[3 * j] - xi[0], x[3 * j + 1] - xi[1], x[3 * j + 2] - xi[2]};
-          const double dist = sqrt(d_dot(d, d));
-          if (!(dist < ri + r[j] && dist > 0.0)) continue;
+          const double d2 = d_dot(d, d);
+          const double rs = ri + r[j];
+          if (!(d2 < rs * rs)) continue;
+          const double dist = sqrt(d2);        // the oracle's test, decided on the root
+          if (!(dist < rs && dist > 0.0)) continue;
           if (nc == C) {
             atomicOr(flags, 1);
             continue;
@@ -239,9 +293,6 @@ k_dem_forces(int64_t n, DemDev p, double dt, const double* __restrict__ x,
   const double mi = p.rho * (4.0 / 3.0 * kPi) * ri * ri * ri;
   const double Ii = 0.4 * mi * ri * ri;
   double F[3] = {0.0, 0.0, 0.0}, T[3] = {0.0, 0.0, 0.0};
-  const double Ye = 1.0 / ((1.0 - p.nu * p.nu) / p.Y + (1.0 - p.nu * p.nu) / p.Y);
-  const double Ge = 1.0 / (2.0 * (2.0 - p.nu) * (1.0 + p.nu) / p.Y +
-                           2.0 * (2.0 - p.nu) * (1.0 + p.nu) / p.Y);
   int o = 0;  // cursor in the previous (sorted) list
   for (int c = 0; c < nc; ++c) {
     const int32_t j = cand[c];
@@ -266,15 +317,12 @@ k_dem_forces(int64_t n, DemDev p, double dt, const double* __restrict__ x,
     while (o < C && hj_old[i * C + o] >= 0 && hj_old[i * C + o] < j) ++o;
     if (o < C && hj_old[i * C + o] == j)
       for (int a = 0; a < 3; ++a) th[a] = ht_old[(i * C + o) * 3 + a];
-    dem_contact(nrm, dn, vrel, wrel, ri, me, Re, Ye, Ge, p.e, p.mus, p.mur, dt, th, F, T);
+    dem_contact(nrm, dn, vrel, wrel, ri, me, Re, p.Ye, p.Ge, p.c56, p.mus, p.mur, dt, th, F, T);
     hj_new[i * C + c] = j;
     for (int a = 0; a < 3; ++a) ht_new[(i * C + c) * 3 + a] = th[a];
   }
   for (int c = nc; c < C; ++c) hj_new[i * C + c] = -1;
   // walls x-, x+, y-, y+, z-, z+
-  const double Yew = 1.0 / ((1.0 - p.nu * p.nu) / p.Y + (1.0 - p.nuw * p.nuw) / p.Yw);
-  const double Gew = 1.0 / (2.0 * (2.0 - p.nu) * (1.0 + p.nu) / p.Y +
-                            2.0 * (2.0 - p.nuw) * (1.0 + p.nuw) / p.Yw);
   for (int wl = 0; wl < 6; ++wl) {
     const int ax = wl / 2;
     double nrm[3] = {0.0, 0.0, 0.0};
@@ -297,7 +345,8 @@ k_dem_forces(int64_t n, DemDev p, double dt, const double* __restrict__ x,
     const double vrel[3] = {v[3 * i] + wxn[0], v[3 * i + 1] + wxn[1], v[3 * i + 2] + wxn[2]};
     const double wrel[3] = {w[3 * i], w[3 * i + 1], w[3 * i + 2]};
     double t3[3] = {th[0], th[1], th[2]};
-    dem_contact(nrm, dn, vrel, wrel, ri, mi, ri, Yew, Gew, p.ew, p.musw, p.murw, dt, t3, F, T);
+    dem_contact(nrm, dn, vrel, wrel, ri, mi, ri, p.Yew, p.Gew, p.c56w, p.musw, p.murw, dt, t3, F,
+                T);
     th[0] = t3[0];
     th[1] = t3[1];
     th[2] = t3[2];
@@ -327,7 +376,7 @@ struct cfdem_dem {
   double *acc = nullptr, *alpha = nullptr, *ht[2] = {nullptr, nullptr}, *wh = nullptr;
   int32_t *hj[2] = {nullptr, nullptr};
   int32_t *cell_of = nullptr, *slot = nullptr, *perm = nullptr, *count = nullptr,
-          *start = nullptr;
+          *start = nullptr, *tsum = nullptr;
   int* flags = nullptr;
   std::string err;
 };
@@ -421,7 +470,7 @@ cfdem_status cfdem_dem_destroy(cfdem_dem_t d) {
   if (d->stream) cudaStreamSynchronize(d->stream);
   else cudaDeviceSynchronize();
   void* ps[] = {d->acc, d->alpha, d->ht[0], d->ht[1], d->wh, d->hj[0], d->hj[1], d->cell_of,
-                d->slot, d->perm, d->count, d->start, d->flags};
+                d->slot, d->perm, d->count, d->start, d->tsum, d->flags};
   for (void* p : ps)
     if (p) cudaFree(p);
   delete d;
@@ -460,6 +509,18 @@ cfdem_status cfdem_dem_set_params(cfdem_dem_t d, const cfdem_dem_params* p) {
   q.musw = p->wall_friction;
   q.murw = p->wall_rolling_friction;
   q.rmax = p->max_radius;
+  auto c56 = [](double e) {
+    const double le = std::log(e);
+    return -2.0 * std::sqrt(5.0 / 6.0) * (le / std::sqrt(le * le + kPi * kPi));
+  };
+  q.c56 = c56(p->restitution);
+  q.c56w = c56(p->wall_restitution);
+  const double nu = p->poisson, nuw = p->wall_poisson;
+  q.Ye = 1.0 / ((1.0 - nu * nu) / p->youngs + (1.0 - nu * nu) / p->youngs);
+  q.Ge = 1.0 / (2.0 * (2.0 - nu) * (1.0 + nu) / p->youngs + 2.0 * (2.0 - nu) * (1.0 + nu) / p->youngs);
+  q.Yew = 1.0 / ((1.0 - nu * nu) / p->youngs + (1.0 - nuw * nuw) / p->wall_youngs);
+  q.Gew = 1.0 / (2.0 * (2.0 - nu) * (1.0 + nu) / p->youngs +
+                 2.0 * (2.0 - nuw) * (1.0 + nuw) / p->wall_youngs);
   int64_t tot = 1;
   for (int a = 0; a < 3; ++a) {
     q.g[a] = p->g[a];
@@ -532,10 +593,12 @@ cfdem_status cfdem_dem_step(cfdem_dem_t d, int64_t n, double* x, double* v, doub
   if (ncells + 1 > d->cap_cells) {
     if (d->count) cudaFree(d->count);
     if (d->start) cudaFree(d->start);
-    d->count = d->start = nullptr;
+    if (d->tsum) cudaFree(d->tsum);
+    d->count = d->start = d->tsum = nullptr;
     d->cap_cells = 0;
     DCK(cudaMalloc(&d->count, sizeof(int32_t) * ncells), "dem cells");
     DCK(cudaMalloc(&d->start, sizeof(int32_t) * (ncells + 1)), "dem cells");
+    DCK(cudaMalloc(&d->tsum, sizeof(int32_t) * (ncells / kScanTile + 2)), "dem cells");
     d->cap_cells = ncells + 1;
   }
   const unsigned nb = (unsigned)((n + 127) / 128), nb3 = (unsigned)((3 * n + 255) / 256);
@@ -544,13 +607,16 @@ cfdem_status cfdem_dem_step(cfdem_dem_t d, int64_t n, double* x, double* v, doub
     if (e != cudaSuccess) return e;
     k_dem_cell_count<<<nb, 128, 0, s>>>(n, d->dd, x, r, d->cell_of, d->slot, d->count,
                                         d->flags);
-    k_dem_scan<<<1, 1024, 0, s>>>((int)ncells, d->count, d->start);
+    const int ntiles = (int)((ncells + kScanTile - 1) / kScanTile);
+    k_dem_scan_tiles<<<ntiles, 256, 0, s>>>((int)ncells, d->count, d->tsum);
+    k_dem_scan_sums<<<1, 256, 0, s>>>(ntiles, d->tsum);
+    k_dem_scan_final<<<ntiles, 256, 0, s>>>((int)ncells, d->count, d->tsum, d->start);
     k_dem_cell_scatter<<<nb, 128, 0, s>>>(n, d->cell_of, d->slot, d->start, d->perm);
     const int o = d->cur, nw = 1 - d->cur;
     k_dem_forces<<<nb, 128, 0, s>>>(n, d->dd, hdt, x, v, w, r, f_ext, d->start, d->perm,
                                     d->hj[o], d->ht[o], d->hj[nw], d->ht[nw], d->wh, d->acc,
                                     d->alpha, d->flags);
-    count_launches(4);
+    count_launches(6);
     d->cur = nw;
     return cudaGetLastError();
   };
