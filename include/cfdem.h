@@ -398,6 +398,9 @@ typedef struct {
     double lo[3], hi[3];          /* the walls: faces of the box [lo, hi] */
     double max_radius;            /* the largest particle radius (cell size 2 max_radius) */
     int capacity;                 /* contacts kept per particle, 1..64 (default 24) */
+    int precision;                /* 0 = FP64 (default); 1 = mixed: FP64 positions,
+                                     velocities, partner search and the difference of
+                                     squares behind each overlap, FP32 contact forces */
 } cfdem_dem_params;
 
 /* Glass-like defaults (rho 2500, Y 1e7, nu 0.3, e 0.9, mu_s 0.3, mu_r 0,

@@ -36,7 +36,7 @@ class cfdem_dem_params(C.Structure):
                 ("wall_poisson", C.c_double), ("wall_restitution", C.c_double),
                 ("wall_friction", C.c_double), ("wall_rolling_friction", C.c_double),
                 ("g", C.c_double * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
-                ("max_radius", C.c_double), ("capacity", C.c_int)]
+                ("max_radius", C.c_double), ("capacity", C.c_int), ("precision", C.c_int)]
 
 
 class cfdem_params(C.Structure):

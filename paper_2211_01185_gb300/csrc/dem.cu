@@ -33,7 +33,10 @@
 #include <cstdio>
 #include <string>
 
+#include <type_traits>
+
 #include "cfdem.h"
+#include "device_common.cuh"
 #include "internal.h"
 
 namespace cfdem {
@@ -55,57 +58,54 @@ struct DemDev {
   double c56, c56w, Ye, Ge, Yew, Gew;
 };
 
-__device__ __forceinline__ void d_cross(const double* a, const double* b, double* c) {
-  c[0] = a[1] * b[2] - a[2] * b[1];
-  c[1] = a[2] * b[0] - a[0] * b[2];
-  c[2] = a[0] * b[1] - a[1] * b[0];
-}
 __device__ __forceinline__ double d_dot(const double* a, const double* b) {
   return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
 }
 
 // one contact's force (added to F) and torque (added to T) on particle i,
-// advancing the carried tangential displacement th in place
-__device__ void dem_contact(const double* n, double dn, const double* vrel, const double* wrel,
-                            double ri, double me, double Re, double Ye, double Ge, double c56,
-                            double mus, double mur, double dt, double* th, double* F, double* T) {
-  const double vn = d_dot(vrel, n);
-  double vrn[3], vrt[3];
+// advancing the carried tangential displacement th in place; T = double
+// (FP64 path) or float (mixed path: the overlap arrives from an FP64
+// difference, the rest of the contact in FP32)
+template <typename R>
+__device__ void dem_contact(const R* n, R dn, const R* vrel, const R* wrel, R ri, R me, R Re,
+                            R Ye, R Ge, R c56, R mus, R mur, R dt, R* th, R* F, R* Tq) {
+  const R vn = n[0] * vrel[0] + n[1] * vrel[1] + n[2] * vrel[2];
+  R vrn[3], vrt[3];
   for (int a = 0; a < 3; ++a) {
     vrn[a] = vn * n[a];
     vrt[a] = vrel[a] - vrn[a];
   }
-  const double sq = sqrt(Re * dn);
-  const double kn = 4.0 / 3.0 * Ye * sq;
-  const double kt = 8.0 * Ge * sq;
-  const double Sn = 2.0 * Ye * sq;
-  const double St = 8.0 * Ge * sq;
-  const double etan = c56 * sqrt(Sn * me);
-  const double etat = c56 * sqrt(St * me);
-  const double hn = d_dot(th, n);
+  const R sq = t_sqrt<R>(Re * dn);
+  const R kn = (R)(4.0 / 3.0) * Ye * sq;
+  const R kt = (R)8 * Ge * sq;
+  const R Sn = (R)2 * Ye * sq;
+  const R St = (R)8 * Ge * sq;
+  const R etan = c56 * t_sqrt<R>(Sn * me);
+  const R etat = c56 * t_sqrt<R>(St * me);
+  const R hn = th[0] * n[0] + th[1] * n[1] + th[2] * n[2];
   for (int a = 0; a < 3; ++a) th[a] = th[a] - hn * n[a] + vrt[a] * dt;
-  double fn[3], ft[3];
+  R fn[3], ft[3];
   for (int a = 0; a < 3; ++a) {
     fn[a] = -(kn * dn) * n[a] - etan * vrn[a];
     ft[a] = -kt * th[a] - etat * vrt[a];
   }
-  const double fnm = sqrt(d_dot(fn, fn));
-  const double ftm = sqrt(d_dot(ft, ft));
+  const R fnm = t_sqrt<R>(fn[0] * fn[0] + fn[1] * fn[1] + fn[2] * fn[2]);
+  const R ftm = t_sqrt<R>(ft[0] * ft[0] + ft[1] * ft[1] + ft[2] * ft[2]);
   if (ftm > mus * fnm) {
-    const double s = mus * fnm / ftm;
+    const R sc = mus * fnm / ftm;
     for (int a = 0; a < 3; ++a) {
-      ft[a] = ft[a] * s;
+      ft[a] = ft[a] * sc;
       th[a] = -(ft[a] + etat * vrt[a]) / kt;
     }
   }
-  const double arm[3] = {ri * n[0], ri * n[1], ri * n[2]};
-  double mt[3];
-  d_cross(arm, ft, mt);
-  const double wm = sqrt(d_dot(wrel, wrel));
+  // (r_i n) x f^t
+  const R mt[3] = {ri * (n[1] * ft[2] - n[2] * ft[1]), ri * (n[2] * ft[0] - n[0] * ft[2]),
+                   ri * (n[0] * ft[1] - n[1] * ft[0])};
+  const R wm = t_sqrt<R>(wrel[0] * wrel[0] + wrel[1] * wrel[1] + wrel[2] * wrel[2]);
   for (int a = 0; a < 3; ++a) {
     F[a] += fn[a] + ft[a];
-    T[a] += mt[a];
-    if (wm > 0.0) T[a] += -mur * Re * fnm * wrel[a] / wm;
+    Tq[a] += mt[a];
+    if (wm > (R)0) Tq[a] += -mur * Re * fnm * wrel[a] / wm;
   }
 }
 
@@ -237,7 +237,11 @@ __global__ void k_dem_cell_scatter(int64_t n, const int32_t* __restrict__ cell_o
 }
 
 // forces and torques on every particle; tangential displacements advance by
-// dt (0 for the first evaluation of a fresh state)
+// dt (0 for the first evaluation of a fresh state).  Partner search in
+// FP64; the contact arithmetic in R (double, or float on the mixed path,
+// where the overlap is (rs^2 - d^2) / (rs + d) with the difference of squares
+// in FP64, so the small overlap keeps its digits).
+template <typename R>
 __global__ void __launch_bounds__(128)
 k_dem_forces(int64_t n, DemDev p, double dt, const double* __restrict__ x,
              const double* __restrict__ v, const double* __restrict__ w,
@@ -274,8 +278,12 @@ k_dem_forces(int64_t n, DemDev p, double dt, const double* __restrict__ x,
           const double d2 = d_dot(d, d);
           const double rs = ri + r[j];
           if (!(d2 < rs * rs)) continue;
-          const double dist = sqrt(d2);        // the oracle's test, decided on the root
-          if (!(dist < rs && dist > 0.0)) continue;
+          if (std::is_same<R, double>::value) {  // the oracle's test, decided on the root
+            const double dist = sqrt(d2);
+            if (!(dist < rs && dist > 0.0)) continue;
+          } else if (!(d2 > 0.0)) {
+            continue;
+          }
           if (nc == C) {
             atomicOr(flags, 1);
             continue;
@@ -292,69 +300,81 @@ k_dem_forces(int64_t n, DemDev p, double dt, const double* __restrict__ x,
   }
   const double mi = p.rho * (4.0 / 3.0 * kPi) * ri * ri * ri;
   const double Ii = 0.4 * mi * ri * ri;
-  double F[3] = {0.0, 0.0, 0.0}, T[3] = {0.0, 0.0, 0.0};
+  const R rir = (R)ri, mir = (R)mi;
+  R F[3] = {0, 0, 0}, Tq[3] = {0, 0, 0};
+  const R wi[3] = {(R)w[3 * i], (R)w[3 * i + 1], (R)w[3 * i + 2]};
   int o = 0;  // cursor in the previous (sorted) list
   for (int c = 0; c < nc; ++c) {
     const int32_t j = cand[c];
     const double d[3] = {x[3 * j] - xi[0], x[3 * j + 1] - xi[1], x[3 * j + 2] - xi[2]};
-    const double dist = sqrt(d_dot(d, d));
-    const double nrm[3] = {d[0] / dist, d[1] / dist, d[2] / dist};
-    const double rj = r[j];
-    const double dn = ri + rj - dist;
-    const double mj = p.rho * (4.0 / 3.0 * kPi) * rj * rj * rj;
-    const double me = 1.0 / (1.0 / mi + 1.0 / mj);
-    const double Re = 1.0 / (1.0 / ri + 1.0 / rj);
-    const double ws[3] = {ri * w[3 * i] + rj * w[3 * j], ri * w[3 * i + 1] + rj * w[3 * j + 1],
-                          ri * w[3 * i + 2] + rj * w[3 * j + 2]};
-    double wxn[3];
-    d_cross(ws, nrm, wxn);
-    double vrel[3], wrel[3];
-    for (int a = 0; a < 3; ++a) {
-      vrel[a] = v[3 * i + a] - v[3 * j + a] + wxn[a];
-      wrel[a] = w[3 * i + a] - w[3 * j + a];
+    const double rjd = r[j];
+    R nrm[3], dn;
+    if (std::is_same<R, double>::value) {
+      const double dist = sqrt(d_dot(d, d));
+      for (int a = 0; a < 3; ++a) nrm[a] = (R)(d[a] / dist);
+      dn = (R)(ri + rjd - dist);
+    } else {
+      const double d2 = d_dot(d, d), rs = ri + rjd;
+      const R dist = t_sqrt<R>((R)d2);
+      const R inv = (R)1 / dist;
+      for (int a = 0; a < 3; ++a) nrm[a] = (R)d[a] * inv;
+      dn = (R)(rs * rs - d2) / ((R)rs + dist);
     }
-    double th[3] = {0.0, 0.0, 0.0};
+    const R rj = (R)rjd;
+    const R mj = (R)(p.rho * (4.0 / 3.0 * kPi)) * rj * rj * rj;
+    const R me = (R)1 / ((R)1 / mir + (R)1 / mj);
+    const R Re = (R)1 / ((R)1 / rir + (R)1 / rj);
+    const R wj[3] = {(R)w[3 * j], (R)w[3 * j + 1], (R)w[3 * j + 2]};
+    const R ws[3] = {rir * wi[0] + rj * wj[0], rir * wi[1] + rj * wj[1], rir * wi[2] + rj * wj[2]};
+    const R wxn[3] = {ws[1] * nrm[2] - ws[2] * nrm[1], ws[2] * nrm[0] - ws[0] * nrm[2],
+                      ws[0] * nrm[1] - ws[1] * nrm[0]};
+    R vrel[3], wrel[3];
+    for (int a = 0; a < 3; ++a) {
+      vrel[a] = (R)(v[3 * i + a] - v[3 * j + a]) + wxn[a];
+      wrel[a] = wi[a] - wj[a];
+    }
+    R th[3] = {0, 0, 0};
     while (o < C && hj_old[i * C + o] >= 0 && hj_old[i * C + o] < j) ++o;
     if (o < C && hj_old[i * C + o] == j)
-      for (int a = 0; a < 3; ++a) th[a] = ht_old[(i * C + o) * 3 + a];
-    dem_contact(nrm, dn, vrel, wrel, ri, me, Re, p.Ye, p.Ge, p.c56, p.mus, p.mur, dt, th, F, T);
+      for (int a = 0; a < 3; ++a) th[a] = (R)ht_old[(i * C + o) * 3 + a];
+    dem_contact<R>(nrm, dn, vrel, wrel, rir, me, Re, (R)p.Ye, (R)p.Ge, (R)p.c56, (R)p.mus,
+                   (R)p.mur, (R)dt, th, F, Tq);
     hj_new[i * C + c] = j;
-    for (int a = 0; a < 3; ++a) ht_new[(i * C + c) * 3 + a] = th[a];
+    for (int a = 0; a < 3; ++a) ht_new[(i * C + c) * 3 + a] = (double)th[a];
   }
   for (int c = nc; c < C; ++c) hj_new[i * C + c] = -1;
   // walls x-, x+, y-, y+, z-, z+
   for (int wl = 0; wl < 6; ++wl) {
     const int ax = wl / 2;
-    double nrm[3] = {0.0, 0.0, 0.0};
-    double dn;
+    R nrm[3] = {0, 0, 0};
+    double dnd;
     if (wl % 2 == 0) {
-      nrm[ax] = -1.0;
-      dn = ri - (xi[ax] - p.lo[ax]);
+      nrm[ax] = (R)-1;
+      dnd = ri - (xi[ax] - p.lo[ax]);
     } else {
-      nrm[ax] = 1.0;
-      dn = ri - (p.hi[ax] - xi[ax]);
+      nrm[ax] = (R)1;
+      dnd = ri - (p.hi[ax] - xi[ax]);
     }
     double* th = wh + (i * 6 + wl) * 3;
-    if (!(dn > 0.0)) {
+    if (!(dnd > 0.0)) {
       th[0] = th[1] = th[2] = 0.0;
       continue;
     }
-    const double rw[3] = {ri * w[3 * i], ri * w[3 * i + 1], ri * w[3 * i + 2]};
-    double wxn[3];
-    d_cross(rw, nrm, wxn);
-    const double vrel[3] = {v[3 * i] + wxn[0], v[3 * i + 1] + wxn[1], v[3 * i + 2] + wxn[2]};
-    const double wrel[3] = {w[3 * i], w[3 * i + 1], w[3 * i + 2]};
-    double t3[3] = {th[0], th[1], th[2]};
-    dem_contact(nrm, dn, vrel, wrel, ri, mi, ri, p.Yew, p.Gew, p.c56w, p.musw, p.murw, dt, t3, F,
-                T);
+    const R rw[3] = {rir * wi[0], rir * wi[1], rir * wi[2]};
+    const R wxn[3] = {rw[1] * nrm[2] - rw[2] * nrm[1], rw[2] * nrm[0] - rw[0] * nrm[2],
+                      rw[0] * nrm[1] - rw[1] * nrm[0]};
+    const R vrel[3] = {(R)v[3 * i] + wxn[0], (R)v[3 * i + 1] + wxn[1], (R)v[3 * i + 2] + wxn[2]};
+    R t3[3] = {(R)th[0], (R)th[1], (R)th[2]};
+    dem_contact<R>(nrm, (R)dnd, vrel, wi, rir, mir, rir, (R)p.Yew, (R)p.Gew, (R)p.c56w,
+                   (R)p.musw, (R)p.murw, (R)dt, t3, F, Tq);
     th[0] = t3[0];
     th[1] = t3[1];
     th[2] = t3[2];
   }
   for (int a = 0; a < 3; ++a) {
-    const double fa = F[a] + mi * p.g[a] + (f_ext ? f_ext[3 * i + a] : 0.0);
+    const double fa = (double)F[a] + mi * p.g[a] + (f_ext ? f_ext[3 * i + a] : 0.0);
     acc[3 * i + a] = fa / mi;
-    alpha[3 * i + a] = T[a] / Ii;
+    alpha[3 * i + a] = (double)Tq[a] / Ii;
   }
 }
 
@@ -491,6 +511,8 @@ cfdem_status cfdem_dem_set_params(cfdem_dem_t d, const cfdem_dem_params* p) {
   if (!(p->friction >= 0.0) || !(p->wall_friction >= 0.0) || !(p->rolling_friction >= 0.0) ||
       !(p->wall_rolling_friction >= 0.0))
     return dfail(d, CFDEM_EINVAL, "friction coefficients must be >= 0");
+  if (p->precision < 0 || p->precision > 1)
+    return dfail(d, CFDEM_EINVAL, "precision must be 0 (FP64) or 1 (mixed)");
   if (p->capacity < 1 || p->capacity > kDemMaxCap)
     return dfail(d, CFDEM_EINVAL, "capacity must be 1..%d", kDemMaxCap);
   for (int a = 0; a < 3; ++a)
@@ -613,9 +635,14 @@ cfdem_status cfdem_dem_step(cfdem_dem_t d, int64_t n, double* x, double* v, doub
     k_dem_scan_final<<<ntiles, 256, 0, s>>>((int)ncells, d->count, d->tsum, d->start);
     k_dem_cell_scatter<<<nb, 128, 0, s>>>(n, d->cell_of, d->slot, d->start, d->perm);
     const int o = d->cur, nw = 1 - d->cur;
-    k_dem_forces<<<nb, 128, 0, s>>>(n, d->dd, hdt, x, v, w, r, f_ext, d->start, d->perm,
-                                    d->hj[o], d->ht[o], d->hj[nw], d->ht[nw], d->wh, d->acc,
-                                    d->alpha, d->flags);
+    if (d->prm.precision == 1)
+      k_dem_forces<float><<<nb, 128, 0, s>>>(n, d->dd, hdt, x, v, w, r, f_ext, d->start,
+                                             d->perm, d->hj[o], d->ht[o], d->hj[nw], d->ht[nw],
+                                             d->wh, d->acc, d->alpha, d->flags);
+    else
+      k_dem_forces<double><<<nb, 128, 0, s>>>(n, d->dd, hdt, x, v, w, r, f_ext, d->start,
+                                              d->perm, d->hj[o], d->ht[o], d->hj[nw], d->ht[nw],
+                                              d->wh, d->acc, d->alpha, d->flags);
     count_launches(6);
     d->cur = nw;
     return cudaGetLastError();

@@ -50,7 +50,7 @@ int main(void) {
   printf("cfdem_dem_params %zu\n", sizeof(cfdem_dem_params));
   P(cfdem_dem_params, rolling_friction); P(cfdem_dem_params, wall_rolling_friction);
   P(cfdem_dem_params, g); P(cfdem_dem_params, hi); P(cfdem_dem_params, max_radius);
-  P(cfdem_dem_params, capacity);
+  P(cfdem_dem_params, capacity); P(cfdem_dem_params, precision);
   return 0;
 }
 '''
