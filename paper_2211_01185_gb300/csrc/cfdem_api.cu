@@ -310,7 +310,6 @@ cfdem_status ensure_particles(cfdem_t c, int64_t n) {
   CK(grow(&c->xs64, 4 * cap), "particle arena");
   CK(grow(&c->xs32, 8 * cap), "particle arena");
   CK(grow(&c->qcm_w, 2 * cap), "particle arena");
-  CK(grow(&c->fpre, 6 * cap), "particle arena");
   c->cap_n = cap;
   return CFDEM_OK;
 }
@@ -515,14 +514,7 @@ cfdem_status cfdem_create(cfdem_t* out, int device, void* stream) {
   DevStatus init{};
   init.first_bad = ~0ull;
   if (cudaMemcpy(c->st, &init, sizeof init, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&c->loop_stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
-    if (c->loop_stream) cudaStreamDestroy(c->loop_stream);
-    if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
-    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-    if (c->ev_join) cudaEventDestroy(c->ev_join);
+      cudaStreamCreateWithFlags(&c->loop_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaFree(c->st);
     delete c;
     return CFDEM_ECUDA;
@@ -541,16 +533,10 @@ cfdem_status cfdem_destroy(cfdem_t c) {
   c->fdm = nullptr;
   c->timer.release();
   void* ps[] = {c->st, c->bands64, c->bands32, c->bandsdf, c->bin_of, c->slot, c->perm, c->xs64,
-                c->xs32, c->qcm_w, c->fpre, c->bin_count, c->bin_start, c->scan_tmp};
+                c->xs32, c->qcm_w, c->bin_count, c->bin_start, c->scan_tmp};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (c->loop_stream) cudaStreamDestroy(c->loop_stream);
-  if (c->aux_stream) {
-    cudaStreamSynchronize(c->aux_stream);
-    cudaStreamDestroy(c->aux_stream);
-  }
-  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-  if (c->ev_join) cudaEventDestroy(c->ev_join);
   delete c;
   return CFDEM_OK;
 }
@@ -740,28 +726,10 @@ cfdem_status cfdem_project(cfdem_t c, const double* eps_q, double* eps_nodal) {
   return solve(c, c->b, eps_nodal, "project");
 }
 
-namespace {
-// forces and fluid source; mode 0 whole, 2 = the part after the void
-// fraction, with the slip and pressure force already in c->fpre (mode 1 of
-// launch_forces, launched by the coupling step on its side stream)
-cfdem_status forces_impl(cfdem_t c, int64_t n, const double* x, const double* r,
-                         const double* u_p, const double* u_nodal, const double* p_nodal,
-                         const double* eps_nodal, double* f, double* f_drag, double* F_elem,
-                         double* F_q, int mode);
-}  // namespace
-
 cfdem_status cfdem_forces(cfdem_t c, int64_t n, const double* x, const double* r,
                           const double* u_p, const double* u_nodal, const double* p_nodal,
                           const double* eps_nodal, double* f, double* f_drag, double* F_elem,
                           double* F_q) {
-  return forces_impl(c, n, x, r, u_p, u_nodal, p_nodal, eps_nodal, f, f_drag, F_elem, F_q, 0);
-}
-
-namespace {
-cfdem_status forces_impl(cfdem_t c, int64_t n, const double* x, const double* r,
-                         const double* u_p, const double* u_nodal, const double* p_nodal,
-                         const double* eps_nodal, double* f, double* f_drag, double* F_elem,
-                         double* F_q, int mode) {
   cfdem_status s = need_mesh(c);
   if (s != CFDEM_OK) return s;
   if (n < 0 || (n > 0 && (!x || !r || !u_p || !f)) || !u_nodal || !p_nodal || !eps_nodal)
@@ -775,7 +743,7 @@ cfdem_status forces_impl(cfdem_t c, int64_t n, const double* x, const double* r,
   c->timer.begin(kStageForces, c->stream);
   CK(launch_forces(m, c->tab, c->prm.precision, force_params(c), n, x, r, u_p, u_nodal,
                    p_nodal, eps_nodal, f, f_drag, want_src ? c->S : nullptr, semi_acc(c), c->st,
-                   c->stream, mode, c->fpre),
+                   c->stream),
      "forces");
   c->timer.end(kStageForces, c->stream);
   if (F_elem || F_q) {
@@ -791,7 +759,6 @@ cfdem_status forces_impl(cfdem_t c, int64_t n, const double* x, const double* r,
   c->semi_valid = semi ? 1 : 0;
   return CFDEM_OK;
 }
-}  // namespace
 
 cfdem_status cfdem_fluid_drag_coefficients(cfdem_t c, double* beta_e, double* up_avg) {
   cfdem_status s = need_mesh(c);
@@ -809,36 +776,11 @@ cfdem_status cfdem_coupling_step(cfdem_t c, int64_t n, const double* x, const do
                                  const double* u_p, const double* u_nodal,
                                  const double* p_nodal, double* eps_nodal, double* f,
                                  double* f_drag, double* F_elem, double* F_q) {
-  // The part of the forces that does not need the void fraction (FP64
-  // interpolation of the slip, the pressure force) runs on a side stream
-  // alongside the void fraction and the projection, which leave the FP64
-  // pipe idle; with the stage timers on, the stages run one after another.
-  const bool overlap = !c->timer.on && n > 0 && c->mesh.E > 0 && u_nodal && p_nodal && x && r &&
-                       u_p && f && n < ((int64_t)1 << 31);
-  if (overlap) {
-    cfdem_status s0 = need_mesh(c);
-    if (s0 != CFDEM_OK) return s0;
-    DeviceGuard g(c->device);
-    s0 = ensure_particles(c, n);
-    if (s0 != CFDEM_OK) return s0;
-    CK(cudaEventRecord(c->ev_fork, c->stream), "fork");
-    CK(cudaStreamWaitEvent(c->aux_stream, c->ev_fork, 0), "fork");
-    CK(launch_forces(c->mesh, c->tab, c->prm.precision, force_params(c), n, x, r, u_p, u_nodal,
-                     p_nodal, nullptr, nullptr, nullptr, nullptr, semi_acc(c), c->st,
-                     c->aux_stream, 1, c->fpre),
-       "forces");
-    CK(cudaEventRecord(c->ev_join, c->aux_stream), "join");
-  }
   cfdem_status s = cfdem_void_fraction(c, n, x, r, nullptr, nullptr, nullptr);
-  if (s == CFDEM_OK) s = cfdem_project(c, nullptr, eps_nodal);
-  if (overlap) {
-    // join even on failure, so that no capture is left with an open branch
-    DeviceGuard g(c->device);
-    CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0), "join");
-  }
   if (s != CFDEM_OK) return s;
-  return forces_impl(c, n, x, r, u_p, u_nodal, p_nodal, eps_nodal, f, f_drag, F_elem, F_q,
-                     overlap ? 2 : 0);
+  s = cfdem_project(c, nullptr, eps_nodal);
+  if (s != CFDEM_OK) return s;
+  return cfdem_forces(c, n, x, r, u_p, u_nodal, p_nodal, eps_nodal, f, f_drag, F_elem, F_q);
 }
 
 cfdem_status cfdem_mass_apply(cfdem_t c, const double* x, double* y) {

@@ -63,9 +63,6 @@ struct cfdem_ctx {
   // call
   bool stats_pending = false;
   cudaStream_t loop_stream = nullptr;  // capture stream of device-driven CG loops
-  cudaStream_t aux_stream = nullptr;   // side stream of the coupling step (FP64 force part)
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  double* fpre = nullptr;              // per particle: slip and pressure force [6 n]
   unsigned gen = 0;                    // bumped by every change of mesh, parameters or timing
   Timer timer;
   long long launches_at_reset = 0;

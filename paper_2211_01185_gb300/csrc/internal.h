@@ -134,15 +134,12 @@ cudaError_t launch_bin(const MeshDev& m, const BinDev& b, int64_t n, const doubl
                        const double* r, int32_t* bin_of, int32_t* slot, int32_t* bin_count,
                        int32_t* bin_start, int32_t* perm, int32_t* scan_tmp, double* xs64,
                        float* xs32, DevStatus* st, cudaStream_t s);
-// S_elem (and acc when fp.fluid_drag) accumulate per element; both may be null.
-// mode 0: whole evaluation; 1: slip and pressure force only, into pre[6 n];
-// 2: the rest, reading pre (eps_nodal is read only in modes 0 and 2)
+// S_elem (and acc when fp.fluid_drag) accumulate per element; both may be null
 cudaError_t launch_forces(const MeshDev& m, const Tables& t, int precision, const ForceParams& fp,
                           int64_t n, const double* x, const double* r, const double* u_p,
                           const double* u_nodal, const double* p_nodal,
                           const double* eps_nodal, double* f, double* f_drag, double* S_elem,
-                          SemiAcc acc, DevStatus* st, cudaStream_t s, int mode = 0,
-                          double* pre = nullptr);
+                          SemiAcc acc, DevStatus* st, cudaStream_t s);
 cudaError_t launch_fluid_source(const MeshDev& m, const double* S_elem, double* F_elem,
                                 double* F_q, cudaStream_t s);
 cudaError_t launch_fluid_source_semi(const MeshDev& m, const Tables& t, int precision,

@@ -325,32 +325,24 @@ __device__ __forceinline__ void shear_force(const Tables& tb, const ForceParams&
     fs[cc] = -Vp * (mu * (H[cc][0] + H[cc][1] + H[cc][2]) + mu3 * gd[cc]);
 }
 
-// MODE 0: the whole force evaluation.  MODE 1 (pre): the part that does not
-// need the void fraction -- slip u_f - u_p and pressure (and shear) force --
-// written to pre[6 i ..]; the coupling step runs it on a second stream while
-// the void fraction and the projection occupy the FP32 pipes, since its
-// FP64 interpolation uses the FP64 pipe the other two leave idle.  MODE 2
-// (post): eps at the particle, the closures and the outputs, with the slip
-// and pressure force read from pre.
-template <int K, int KP, typename T, int MODE>
+template <int K, int KP, typename T>
 __global__ void __launch_bounds__(128)
 k_forces(MeshDev m, Tables tb, ForceParams fp, int64_t n, const double* __restrict__ x,
          const double* __restrict__ r, const double* __restrict__ u_p,
          const double* __restrict__ u_nodal, const double* __restrict__ p_nodal,
          const double* __restrict__ eps_nodal, double* __restrict__ f,
          double* __restrict__ f_drag, double* __restrict__ S_elem, SemiAcc acc,
-         DevStatus* st, double* __restrict__ pre) {
+         DevStatus* st) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   double p[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
   if (!(in_box(p[0], m.x0[0], m.L[0]) && in_box(p[1], m.x0[1], m.L[1]) &&
         in_box(p[2], m.x0[2], m.L[2]))) {
-    if (MODE != 2) report_bad(st, i);
-    if (MODE != 1)
-      for (int a = 0; a < 3; ++a) {
-        f[3 * i + a] = 0.0;
-        if (f_drag) f_drag[3 * i + a] = 0.0;
-      }
+    report_bad(st, i);
+    for (int a = 0; a < 3; ++a) {
+      f[3 * i + a] = 0.0;
+      if (f_drag) f_drag[3 * i + a] = 0.0;
+    }
     return;
   }
   int ie[3];
@@ -379,12 +371,10 @@ k_forces(MeshDev m, Tables tb, ForceParams fp, int64_t n, const double* __restri
       for (int a = 0; a <= K; ++a) {
         double phi = lxd[a] * lyz;
         int64_t nd = base + a + nx * b + nxy * c;
-        if (MODE != 2) {
-          ufd0 += phi * __ldg(u_nodal + 3 * nd);
-          ufd1 += phi * __ldg(u_nodal + 3 * nd + 1);
-          ufd2 += phi * __ldg(u_nodal + 3 * nd + 2);
-        }
-        if (MODE != 1) epsd += phi * __ldg(eps_nodal + nd);
+        ufd0 += phi * __ldg(u_nodal + 3 * nd);
+        ufd1 += phi * __ldg(u_nodal + 3 * nd + 1);
+        ufd2 += phi * __ldg(u_nodal + 3 * nd + 2);
+        epsd += phi * __ldg(eps_nodal + nd);
       }
     }
   }
@@ -393,74 +383,41 @@ k_forces(MeshDev m, Tables tb, ForceParams fp, int64_t n, const double* __restri
   // and so on): the shape-function derivatives sum to zero only up to
   // rounding in FP32, so a large pressure varying along one axis would
   // otherwise leak into the other two components of the gradient
+  T px[KP + 1], py[KP + 1], pz[KP + 1], dpx[KP + 1], dpy[KP + 1], dpz[KP + 1];
+  lagrange<KP, T>(tb.zp, tb.lwp, xi[0], px, dpx);
+  lagrange<KP, T>(tb.zp, tb.lwp, xi[1], py, dpy);
+  lagrange<KP, T>(tb.zp, tb.lwp, xi[2], pz, dpz);
+  int64_t pnx = m.np[0], pnxy = (int64_t)m.np[0] * m.np[1];
+  int64_t pbase =
+      (int64_t)ie[0] * KP + pnx * ((int64_t)ie[1] * KP) + pnxy * ((int64_t)ie[2] * KP);
+  double pv[KP + 1][KP + 1][KP + 1];
+#pragma unroll
+  for (int c = 0; c <= KP; ++c)
+#pragma unroll
+    for (int b = 0; b <= KP; ++b)
+#pragma unroll
+      for (int a = 0; a <= KP; ++a) pv[c][b][a] = __ldg(p_nodal + pbase + a + pnx * b + pnxy * c);
   T gp0 = 0, gp1 = 0, gp2 = 0;
-  if (MODE != 2) {
-    T px[KP + 1], py[KP + 1], pz[KP + 1], dpx[KP + 1], dpy[KP + 1], dpz[KP + 1];
-    lagrange<KP, T>(tb.zp, tb.lwp, xi[0], px, dpx);
-    lagrange<KP, T>(tb.zp, tb.lwp, xi[1], py, dpy);
-    lagrange<KP, T>(tb.zp, tb.lwp, xi[2], pz, dpz);
-    int64_t pnx = m.np[0], pnxy = (int64_t)m.np[0] * m.np[1];
-    int64_t pbase =
-        (int64_t)ie[0] * KP + pnx * ((int64_t)ie[1] * KP) + pnxy * ((int64_t)ie[2] * KP);
-    double pv[KP + 1][KP + 1][KP + 1];
-  #pragma unroll
-    for (int c = 0; c <= KP; ++c)
-  #pragma unroll
-      for (int b = 0; b <= KP; ++b)
-  #pragma unroll
-        for (int a = 0; a <= KP; ++a) pv[c][b][a] = __ldg(p_nodal + pbase + a + pnx * b + pnxy * c);
-  #pragma unroll
-    for (int c = 0; c <= KP; ++c) {
-  #pragma unroll
-      for (int b = 0; b <= KP; ++b) {
-  #pragma unroll
-        for (int a = 0; a <= KP; ++a) {
-          if (a > 0) gp0 += dpx[a] * py[b] * pz[c] * (T)(pv[c][b][a] - pv[c][b][0]);
-          if (b > 0) gp1 += px[a] * dpy[b] * pz[c] * (T)(pv[c][b][a] - pv[c][0][a]);
-          if (c > 0) gp2 += px[a] * py[b] * dpz[c] * (T)(pv[c][b][a] - pv[0][b][a]);
-        }
+#pragma unroll
+  for (int c = 0; c <= KP; ++c) {
+#pragma unroll
+    for (int b = 0; b <= KP; ++b) {
+#pragma unroll
+      for (int a = 0; a <= KP; ++a) {
+        if (a > 0) gp0 += dpx[a] * py[b] * pz[c] * (T)(pv[c][b][a] - pv[c][b][0]);
+        if (b > 0) gp1 += px[a] * dpy[b] * pz[c] * (T)(pv[c][b][a] - pv[c][0][a]);
+        if (c > 0) gp2 += px[a] * py[b] * dpz[c] * (T)(pv[c][b][a] - pv[0][b][a]);
       }
     }
-    gp0 = gp0 / (T)m.h[0];
-    gp1 = gp1 / (T)m.h[1];
-    gp2 = gp2 / (T)m.h[2];
   }
+  gp0 = gp0 / (T)m.h[0];
+  gp1 = gp1 / (T)m.h[1];
+  gp2 = gp2 / (T)m.h[2];
 
   // closures
   T rp = (T)r[i];
-  T Vp = (T)(4.0 / 3.0 * kPi) * rp * rp * rp;
-  T U0, U1, U2, fg0, fg1, fg2;
-  if (MODE != 2) {
-    U0 = (T)(ufd0 - u_p[3 * i]);
-    U1 = (T)(ufd1 - u_p[3 * i + 1]);
+  T U0 = (T)(ufd0 - u_p[3 * i]), U1 = (T)(ufd1 - u_p[3 * i + 1]),
     U2 = (T)(ufd2 - u_p[3 * i + 2]);
-    fg0 = -Vp * gp0;
-    fg1 = -Vp * gp1;
-    fg2 = -Vp * gp2;
-    if (fp.shear) {  // the shear force joins the pressure term: f and model B's source
-      T fs[3];
-      shear_force<K, T>(tb, fp, u_nodal, base, nx, nxy, xi, Vp, fs);
-      fg0 += fs[0];
-      fg1 += fs[1];
-      fg2 += fs[2];
-    }
-  } else {
-    U0 = (T)pre[6 * i];
-    U1 = (T)pre[6 * i + 1];
-    U2 = (T)pre[6 * i + 2];
-    fg0 = (T)pre[6 * i + 3];
-    fg1 = (T)pre[6 * i + 4];
-    fg2 = (T)pre[6 * i + 5];
-  }
-  if (MODE == 1) {
-    pre[6 * i] = (double)U0;
-    pre[6 * i + 1] = (double)U1;
-    pre[6 * i + 2] = (double)U2;
-    pre[6 * i + 3] = (double)fg0;
-    pre[6 * i + 4] = (double)fg1;
-    pre[6 * i + 5] = (double)fg2;
-    return;
-  }
   T speed = t_sqrt<T>(U0 * U0 + U1 * U1 + U2 * U2);
   T eps = (T)epsd;
   T epsc = eps < (T)fp.eps_floor ? (T)fp.eps_floor : eps;
@@ -471,6 +428,15 @@ k_forces(MeshDev m, Tables tb, ForceParams fp, int64_t n, const double* __restri
     fd0 = coef * U0;
     fd1 = coef * U1;
     fd2 = coef * U2;
+  }
+  T Vp = (T)(4.0 / 3.0 * kPi) * rp * rp * rp;
+  T fg0 = -Vp * gp0, fg1 = -Vp * gp1, fg2 = -Vp * gp2;
+  if (fp.shear) {  // the shear force joins the pressure term: f and model B's source
+    T fs[3];
+    shear_force<K, T>(tb, fp, u_nodal, base, nx, nxy, xi, Vp, fs);
+    fg0 += fs[0];
+    fg1 += fs[1];
+    fg2 += fs[2];
   }
   T rv = (T)fp.rho * Vp;
   f[3 * i] = (double)(fd0 + (-rv * (T)fp.g[0]) + fg0);
@@ -508,18 +474,10 @@ static void launch_forces_t(const MeshDev& m, const Tables& t, const ForceParams
                             int64_t n, const double* x, const double* r, const double* u_p,
                             const double* u_nodal, const double* p_nodal,
                             const double* eps_nodal, double* f, double* f_drag, double* S,
-                            SemiAcc acc, DevStatus* st, cudaStream_t s, int mode, double* pre) {
+                            SemiAcc acc, DevStatus* st, cudaStream_t s) {
   int bs = 128;
-  const unsigned nb = (unsigned)((n + bs - 1) / bs);
-  if (mode == 1)
-    k_forces<K, KP, T, 1><<<nb, bs, 0, s>>>(m, t, fp, n, x, r, u_p, u_nodal, p_nodal, eps_nodal,
-                                            f, f_drag, S, acc, st, pre);
-  else if (mode == 2)
-    k_forces<K, KP, T, 2><<<nb, bs, 0, s>>>(m, t, fp, n, x, r, u_p, u_nodal, p_nodal, eps_nodal,
-                                            f, f_drag, S, acc, st, pre);
-  else
-    k_forces<K, KP, T, 0><<<nb, bs, 0, s>>>(m, t, fp, n, x, r, u_p, u_nodal, p_nodal, eps_nodal,
-                                            f, f_drag, S, acc, st, pre);
+  k_forces<K, KP, T><<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(
+      m, t, fp, n, x, r, u_p, u_nodal, p_nodal, eps_nodal, f, f_drag, S, acc, st);
   count_launches(1);
 }
 
@@ -527,16 +485,16 @@ cudaError_t launch_forces(const MeshDev& m, const Tables& t, int precision, cons
                           int64_t n, const double* x, const double* r, const double* u_p,
                           const double* u_nodal, const double* p_nodal,
                           const double* eps_nodal, double* f, double* f_drag, double* S_elem,
-                          SemiAcc acc, DevStatus* st, cudaStream_t s, int mode, double* pre) {
+                          SemiAcc acc, DevStatus* st, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
 #define CFDEM_FORCES(K, KP)                                                                  \
   if (m.k == K && m.kp == KP) {                                                              \
     if (precision == 0)                                                                      \
       launch_forces_t<K, KP, double>(m, t, fp, n, x, r, u_p, u_nodal, p_nodal, eps_nodal, f, \
-                                     f_drag, S_elem, acc, st, s, mode, pre);                 \
+                                     f_drag, S_elem, acc, st, s);                            \
     else                                                                                     \
       launch_forces_t<K, KP, float>(m, t, fp, n, x, r, u_p, u_nodal, p_nodal, eps_nodal, f,  \
-                                    f_drag, S_elem, acc, st, s, mode, pre);                  \
+                                    f_drag, S_elem, acc, st, s);                             \
     return cudaGetLastError();                                                               \
   }
   CFDEM_FORCES(1, 1)
