@@ -399,8 +399,9 @@ typedef struct {
     double max_radius;            /* the largest particle radius (cell size 2 max_radius) */
     int capacity;                 /* contacts kept per particle, 1..64 (default 24) */
     int precision;                /* 0 = FP64 (default); 1 = mixed: FP64 positions,
-                                     velocities, partner search and the difference of
-                                     squares behind each overlap, FP32 contact forces */
+                                     velocities, contact test and the difference of
+                                     squares behind each overlap; FP32 contact forces
+                                     and carried tangential displacements */
 } cfdem_dem_params;
 
 /* Glass-like defaults (rho 2500, Y 1e7, nu 0.3, e 0.9, mu_s 0.3, mu_r 0,
@@ -413,7 +414,8 @@ cfdem_status cfdem_dem_create(cfdem_dem_t *out, int device, void *stream);
 cfdem_status cfdem_dem_destroy(cfdem_dem_t dem);
 
 /* Set (or change) the parameters; CFDEM_EINVAL for a bad value.  The
- * carried accelerations are recomputed at the next step. */
+ * carried accelerations are recomputed at the next step; a change of
+ * capacity or precision also forgets the contact history. */
 cfdem_status cfdem_dem_set_params(cfdem_dem_t dem, const cfdem_dem_params *p);
 
 /* Forget the contact history and the carried accelerations. */

@@ -18,15 +18,16 @@
 // rolling resistance M^r = -mu_r R_e |f^n| w_rel/|w_rel|; M^t = r_i n x f^t.
 // The box faces are walls of infinite mass and radius.
 //
-// GPU layout.  One thread per particle.  A cell list (edge >= 2 r_max) is
-// rebuilt by counting sort every sub-step; each particle gathers its
-// overlapping partners from the 27 cells around it into a list sorted by
-// partner index (capacity C per particle), merges it with its previous list
-// to carry d_t, and sums its contacts in that order, then the six walls,
-// gravity and the fluid force -- so the forces do not depend on the order
-// in which the cell list was filled, and no atomics touch a force.  Each
-// particle keeps its own copy of a pair's d_t (the partner's is its
-// negative), so i and j never write the same word.  All FP64.
+// GPU layout.  One thread per particle, in cell order.  A cell list (edge
+// >= 2 r_max) is rebuilt by counting sort every sub-step; each particle
+// gathers its overlapping partners from the 27 cells around it into a list
+// sorted by partner index (capacity C per particle), merges it with its
+// previous list to carry d_t, and sums its contacts in that order, then the
+// six walls, gravity and the fluid force -- so the forces do not depend on
+// the order in which the cell list was filled, and no atomics touch a
+// force.  Each particle keeps its own copy of a pair's d_t (the partner's is
+// its negative), so i and j never write the same word.  The state is FP64;
+// the contact arithmetic is FP64 or, on the mixed path, FP32.
 #include <cmath>
 #include <cstdarg>
 #include <cstdint>
@@ -228,34 +229,89 @@ k_dem_scan_final(int ncells, const int32_t* __restrict__ count,
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) start[ncells] = tsum[gridDim.x];
 }
 
-__global__ void k_dem_cell_scatter(int64_t n, const int32_t* __restrict__ cell_of,
+// pass 3: the particle's place in cell order, with an FP32 copy of its
+// position (offset from the box's low corner) and radius at that place;
+// also FP32 copies of its angular velocity and radius by particle index
+__global__ void k_dem_cell_scatter(int64_t n, DemDev p, const double* __restrict__ x,
+                                   const double* __restrict__ w, const double* __restrict__ r,
+                                   const int32_t* __restrict__ cell_of,
                                    const int32_t* __restrict__ slot,
-                                   const int32_t* __restrict__ start, int32_t* __restrict__ perm) {
+                                   const int32_t* __restrict__ start, int32_t* __restrict__ perm,
+                                   float4* __restrict__ xs, float4* __restrict__ wf) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  perm[start[cell_of[i]] + slot[i]] = (int32_t)i;
+  const int32_t s = start[cell_of[i]] + slot[i];
+  const float rf = (float)r[i];
+  perm[s] = (int32_t)i;
+  xs[s] = make_float4((float)(x[3 * i] - p.lo[0]), (float)(x[3 * i + 1] - p.lo[1]),
+                      (float)(x[3 * i + 2] - p.lo[2]), rf);
+  wf[i] = make_float4((float)w[3 * i], (float)w[3 * i + 1], (float)w[3 * i + 2], rf);
+}
+
+// max |coordinate| of an FP32 position copy
+__device__ __forceinline__ float abs_max3(float4 q) {
+  return fmaxf(fabsf(q.x), fmaxf(fabsf(q.y), fabsf(q.z)));
+}
+
+// the FP64 contact test of a screened candidate: d2 < (r_i + r_j)^2, and on
+// the FP64 path also 0 < |d| < r_i + r_j on the root (the oracle's test)
+template <typename R>
+__device__ __forceinline__ bool dem_touch(const double* __restrict__ x,
+                                          const double* __restrict__ r, int32_t j,
+                                          const double* xi, double ri) {
+  const double d[3] = {x[3 * j] - xi[0], x[3 * j + 1] - xi[1], x[3 * j + 2] - xi[2]};
+  const double d2 = d_dot(d, d);
+  const double rs = ri + r[j];
+  if (!(d2 < rs * rs)) return false;
+  if (std::is_same<R, double>::value) {
+    const double dist = sqrt(d2);
+    return dist < rs && dist > 0.0;
+  }
+  return d2 > 0.0;
 }
 
 // forces and torques on every particle; tangential displacements advance by
-// dt (0 for the first evaluation of a fresh state).  Partner search in
-// FP64; the contact arithmetic in R (double, or float on the mixed path,
-// where the overlap is (rs^2 - d^2) / (rs + d) with the difference of squares
-// in FP64, so the small overlap keeps its digits).
+// dt (0 for the first evaluation of a fresh state).  Thread t takes the
+// particle at place t of the cell order, so the threads of a warp share
+// most of their 27 cells.  The candidates are screened in FP32 on the
+// cell-ordered copy: a stored coordinate is within 2^-24 of its magnitude
+// of the FP64 offset and the FP32 difference adds 2^-24 |d|, so
+// |d_f - d| <= sqrt(3) 2^-24 (M_i + M_j + |d|) (M = largest |coordinate|);
+// the screen passes |d_f| < (r_i + r_j)(1 + 2^-18) + 2^-18 (M_i + M_j), a
+// bound more than ten times that error plus the rounding of the squares,
+// so no pair the FP64 test accepts is screened out.  The screened
+// candidates are kept sorted by index and the FP64 test (dem_touch) runs
+// on them afterwards, once per candidate, outside the divergent cell walk.
+// The contact arithmetic runs in R (double, or float on the mixed path,
+// where the overlap is (rs^2 - d^2) / (rs + d) with the difference of
+// squares in FP64, so the small overlap keeps its digits, and the carried
+// tangential displacements are stored in FP32).
 template <typename R>
 __global__ void __launch_bounds__(128)
 k_dem_forces(int64_t n, DemDev p, double dt, const double* __restrict__ x,
              const double* __restrict__ v, const double* __restrict__ w,
              const double* __restrict__ r, const double* __restrict__ f_ext,
              const int32_t* __restrict__ start, const int32_t* __restrict__ perm,
-             const int32_t* __restrict__ hj_old, const double* __restrict__ ht_old,
-             int32_t* __restrict__ hj_new, double* __restrict__ ht_new, double* __restrict__ wh,
+             const float4* __restrict__ xs, const float4* __restrict__ wf,
+             const int32_t* __restrict__ hj_old, const R* __restrict__ ht_old,
+             int32_t* __restrict__ hj_new, R* __restrict__ ht_new, double* __restrict__ wh,
              double* __restrict__ acc, double* __restrict__ alpha, int* __restrict__ flags) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  // the warp's live threads meet again after each divergent loop: without
+  // it they stay split into the groups the cell walk left them in, and every
+  // later instruction issues once per group
+  const unsigned live = __ballot_sync(0xffffffffu, t < n);
+  if (t >= n) return;
+  const int64_t i = perm[t];
   const int C = p.cap;
   const double xi[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
   const double ri = r[i];
-  // partners, sorted by index (insertion into a list of at most C)
+  const float4 qi = xs[t];
+  const float Mi = abs_max3(qi);
+  constexpr float kScreen = 3.814697265625e-06f;  // 2^-18
+  // screened partners, sorted by index (insertion into a list of at most
+  // kDemMaxCap; a full list drops the screened-in pairs the FP64 test
+  // rejects before it takes another)
   int32_t cand[kDemMaxCap];
   int nc = 0;
   const int cx = cell_axis(xi[0], p.lo[0], p.inv_ce[0], p.nc[0]);
@@ -267,64 +323,85 @@ k_dem_forces(int64_t n, DemDev p, double dt, const double* __restrict__ x,
     for (int dy = -1; dy <= 1; ++dy) {
       const int y = cy + dy;
       if (y < 0 || y >= p.nc[1]) continue;
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int xx = cx + dx;
-        if (xx < 0 || xx >= p.nc[0]) continue;
-        const int c = xx + p.nc[0] * (y + p.nc[1] * z);
-        for (int s = start[c]; s < start[c + 1]; ++s) {
-          const int32_t j = perm[s];
-          if (j == i) continue;
-          const double d[3] = {x[3 * j] - xi[0], x[3 * j + 1] - xi[1], x[3 * j + 2] - xi[2]};
-          const double d2 = d_dot(d, d);
-          const double rs = ri + r[j];
-          if (!(d2 < rs * rs)) continue;
-          if (std::is_same<R, double>::value) {  // the oracle's test, decided on the root
-            const double dist = sqrt(d2);
-            if (!(dist < rs && dist > 0.0)) continue;
-          } else if (!(d2 > 0.0)) {
+      // the three cells of a row along x are contiguous in cell order
+      const int row = p.nc[0] * (y + p.nc[1] * z);
+      const int s0 = start[row + (cx > 0 ? cx - 1 : 0)];
+      const int s1 = start[row + (cx < p.nc[0] - 1 ? cx + 2 : p.nc[0])];
+      for (int s = s0; s < s1; ++s) {
+        if (s == t) continue;
+        const float4 qj = xs[s];
+        const float ex = qj.x - qi.x, ey = qj.y - qi.y, ez = qj.z - qi.z;
+        const float M = Mi + abs_max3(qj);
+        const float lim = (qi.w + qj.w) * (1.0f + kScreen) + kScreen * M;
+        // positions beyond FP32 range (M not finite) skip the screen
+        if (!(ex * ex + ey * ey + ez * ez < lim * lim) && M < 3.0e38f) continue;
+        const int32_t j = perm[s];
+        if (nc == kDemMaxCap) {
+          int m = 0;
+          for (int q = 0; q < nc; ++q)
+            if (dem_touch<R>(x, r, cand[q], xi, ri)) cand[m++] = cand[q];
+          nc = m;
+          if (nc == kDemMaxCap) {  // 65 contacts: above any capacity
+            if (dem_touch<R>(x, r, j, xi, ri)) atomicOr(flags, 1);
             continue;
           }
-          if (nc == C) {
-            atomicOr(flags, 1);
-            continue;
-          }
-          int q = nc++;
-          while (q > 0 && cand[q - 1] > j) {
-            cand[q] = cand[q - 1];
-            --q;
-          }
-          cand[q] = j;
         }
+        int q = nc++;
+        while (q > 0 && cand[q - 1] > j) {
+          cand[q] = cand[q - 1];
+          --q;
+        }
+        cand[q] = j;
       }
     }
   }
+  __syncwarp(live);
   const double mi = p.rho * (4.0 / 3.0 * kPi) * ri * ri * ri;
   const double Ii = 0.4 * mi * ri * ri;
   const R rir = (R)ri, mir = (R)mi;
+  const R mcoef = (R)(p.rho * (4.0 / 3.0 * kPi));
   R F[3] = {0, 0, 0}, Tq[3] = {0, 0, 0};
   const R wi[3] = {(R)w[3 * i], (R)w[3 * i + 1], (R)w[3 * i + 2]};
   int o = 0;  // cursor in the previous (sorted) list
+  int m = 0;  // contacts kept
   for (int c = 0; c < nc; ++c) {
     const int32_t j = cand[c];
     const double d[3] = {x[3 * j] - xi[0], x[3 * j + 1] - xi[1], x[3 * j + 2] - xi[2]};
+    const double d2 = d_dot(d, d);
     const double rjd = r[j];
+    const double rs = ri + rjd;
+    if (!(d2 < rs * rs)) continue;
     R nrm[3], dn;
     if (std::is_same<R, double>::value) {
-      const double dist = sqrt(d_dot(d, d));
+      const double dist = sqrt(d2);
+      if (!(dist < rs && dist > 0.0)) continue;
       for (int a = 0; a < 3; ++a) nrm[a] = (R)(d[a] / dist);
-      dn = (R)(ri + rjd - dist);
+      dn = (R)(rs - dist);
     } else {
-      const double d2 = d_dot(d, d), rs = ri + rjd;
+      if (!(d2 > 0.0)) continue;
       const R dist = t_sqrt<R>((R)d2);
       const R inv = (R)1 / dist;
       for (int a = 0; a < 3; ++a) nrm[a] = (R)d[a] * inv;
       dn = (R)(rs * rs - d2) / ((R)rs + dist);
     }
-    const R rj = (R)rjd;
-    const R mj = (R)(p.rho * (4.0 / 3.0 * kPi)) * rj * rj * rj;
+    if (m == C) {
+      atomicOr(flags, 1);
+      continue;
+    }
+    R rj, wj[3];
+    if (std::is_same<R, double>::value) {
+      rj = (R)rjd;
+      for (int a = 0; a < 3; ++a) wj[a] = (R)w[3 * j + a];
+    } else {
+      const float4 q = wf[j];
+      rj = (R)q.w;
+      wj[0] = (R)q.x;
+      wj[1] = (R)q.y;
+      wj[2] = (R)q.z;
+    }
+    const R mj = mcoef * rj * rj * rj;
     const R me = (R)1 / ((R)1 / mir + (R)1 / mj);
     const R Re = (R)1 / ((R)1 / rir + (R)1 / rj);
-    const R wj[3] = {(R)w[3 * j], (R)w[3 * j + 1], (R)w[3 * j + 2]};
     const R ws[3] = {rir * wi[0] + rj * wj[0], rir * wi[1] + rj * wj[1], rir * wi[2] + rj * wj[2]};
     const R wxn[3] = {ws[1] * nrm[2] - ws[2] * nrm[1], ws[2] * nrm[0] - ws[0] * nrm[2],
                       ws[0] * nrm[1] - ws[1] * nrm[0]};
@@ -336,13 +413,15 @@ k_dem_forces(int64_t n, DemDev p, double dt, const double* __restrict__ x,
     R th[3] = {0, 0, 0};
     while (o < C && hj_old[i * C + o] >= 0 && hj_old[i * C + o] < j) ++o;
     if (o < C && hj_old[i * C + o] == j)
-      for (int a = 0; a < 3; ++a) th[a] = (R)ht_old[(i * C + o) * 3 + a];
+      for (int a = 0; a < 3; ++a) th[a] = ht_old[(i * C + o) * 3 + a];
     dem_contact<R>(nrm, dn, vrel, wrel, rir, me, Re, (R)p.Ye, (R)p.Ge, (R)p.c56, (R)p.mus,
                    (R)p.mur, (R)dt, th, F, Tq);
-    hj_new[i * C + c] = j;
-    for (int a = 0; a < 3; ++a) ht_new[(i * C + c) * 3 + a] = (double)th[a];
+    hj_new[i * C + m] = j;
+    for (int a = 0; a < 3; ++a) ht_new[(i * C + m) * 3 + a] = th[a];
+    ++m;
   }
-  for (int c = nc; c < C; ++c) hj_new[i * C + c] = -1;
+  for (int c = m; c < C; ++c) hj_new[i * C + c] = -1;
+  __syncwarp(live);
   // walls x-, x+, y-, y+, z-, z+
   for (int wl = 0; wl < 6; ++wl) {
     const int ax = wl / 2;
@@ -397,6 +476,8 @@ struct cfdem_dem {
   int32_t *hj[2] = {nullptr, nullptr};
   int32_t *cell_of = nullptr, *slot = nullptr, *perm = nullptr, *count = nullptr,
           *start = nullptr, *tsum = nullptr;
+  float4* xs = nullptr;  // cell-ordered FP32 positions and radii
+  float4* wf = nullptr;  // FP32 angular velocities and radii by particle
   int* flags = nullptr;
   std::string err;
 };
@@ -490,7 +571,7 @@ cfdem_status cfdem_dem_destroy(cfdem_dem_t d) {
   if (d->stream) cudaStreamSynchronize(d->stream);
   else cudaDeviceSynchronize();
   void* ps[] = {d->acc, d->alpha, d->ht[0], d->ht[1], d->wh, d->hj[0], d->hj[1], d->cell_of,
-                d->slot, d->perm, d->count, d->start, d->tsum, d->flags};
+                d->slot, d->perm, d->count, d->start, d->tsum, d->flags, d->xs, d->wf};
   for (void* p : ps)
     if (p) cudaFree(p);
   delete d;
@@ -556,10 +637,13 @@ cfdem_status cfdem_dem_set_params(cfdem_dem_t d, const cfdem_dem_params* p) {
   }
   if (tot > ((int64_t)1 << 28)) return dfail(d, CFDEM_EINVAL, "too many cells");
   q.cap = p->capacity;
-  const bool resize = !d->have_prm || d->prm.capacity != p->capacity;
+  // the history layout changes with the capacity and the precision (FP32
+  // tangential displacements on the mixed path)
+  const bool resize = !d->have_prm || d->prm.capacity != p->capacity ||
+                      d->prm.precision != p->precision;
   d->prm = *p;
   d->have_prm = true;
-  if (resize) d->n = -1;  // history layout changes with the capacity
+  if (resize) d->n = -1;
   d->have_acc = 0;        // accelerations depend on the parameters
   return CFDEM_OK;
 }
@@ -586,11 +670,12 @@ cfdem_status cfdem_dem_step(cfdem_dem_t d, int64_t n, double* x, double* v, doub
   if (n != d->n) {  // a new particle set: fresh state
     if (n > d->cap_n || (int64_t)n * C > d->cap_h) {
       void* old[] = {d->acc, d->alpha, d->wh, d->cell_of, d->slot, d->perm,
-                     d->hj[0], d->hj[1], d->ht[0], d->ht[1]};
+                     d->hj[0], d->hj[1], d->ht[0], d->ht[1], d->xs, d->wf};
       for (void* q : old)
         if (q) cudaFree(q);
       d->acc = d->alpha = d->wh = d->ht[0] = d->ht[1] = nullptr;
       d->cell_of = d->slot = d->perm = d->hj[0] = d->hj[1] = nullptr;
+      d->xs = d->wf = nullptr;
       d->cap_n = d->cap_h = 0;
       const int64_t cap = n + n / 4 + 256;
       DCK(cudaMalloc(&d->acc, sizeof(double) * 3 * cap), "dem arena");
@@ -599,6 +684,8 @@ cfdem_status cfdem_dem_step(cfdem_dem_t d, int64_t n, double* x, double* v, doub
       DCK(cudaMalloc(&d->cell_of, sizeof(int32_t) * cap), "dem arena");
       DCK(cudaMalloc(&d->slot, sizeof(int32_t) * cap), "dem arena");
       DCK(cudaMalloc(&d->perm, sizeof(int32_t) * cap), "dem arena");
+      DCK(cudaMalloc(&d->xs, sizeof(float4) * cap), "dem arena");
+      DCK(cudaMalloc(&d->wf, sizeof(float4) * cap), "dem arena");
       DCK(cudaMalloc(&d->hj[0], sizeof(int32_t) * cap * C), "dem arena");
       DCK(cudaMalloc(&d->hj[1], sizeof(int32_t) * cap * C), "dem arena");
       DCK(cudaMalloc(&d->ht[0], sizeof(double) * 3 * cap * C), "dem arena");
@@ -633,16 +720,19 @@ cfdem_status cfdem_dem_step(cfdem_dem_t d, int64_t n, double* x, double* v, doub
     k_dem_scan_tiles<<<ntiles, 256, 0, s>>>((int)ncells, d->count, d->tsum);
     k_dem_scan_sums<<<1, 256, 0, s>>>(ntiles, d->tsum);
     k_dem_scan_final<<<ntiles, 256, 0, s>>>((int)ncells, d->count, d->tsum, d->start);
-    k_dem_cell_scatter<<<nb, 128, 0, s>>>(n, d->cell_of, d->slot, d->start, d->perm);
+    k_dem_cell_scatter<<<nb, 128, 0, s>>>(n, d->dd, x, w, r, d->cell_of, d->slot, d->start,
+                                          d->perm, d->xs, d->wf);
     const int o = d->cur, nw = 1 - d->cur;
-    if (d->prm.precision == 1)
-      k_dem_forces<float><<<nb, 128, 0, s>>>(n, d->dd, hdt, x, v, w, r, f_ext, d->start,
-                                             d->perm, d->hj[o], d->ht[o], d->hj[nw], d->ht[nw],
-                                             d->wh, d->acc, d->alpha, d->flags);
+    if (d->prm.precision == 1)  // FP32 tangential history in the same buffers
+      k_dem_forces<float><<<nb, 128, 0, s>>>(
+          n, d->dd, hdt, x, v, w, r, f_ext, d->start, d->perm, d->xs, d->wf, d->hj[o],
+          reinterpret_cast<const float*>(d->ht[o]), d->hj[nw],
+          reinterpret_cast<float*>(d->ht[nw]), d->wh, d->acc, d->alpha, d->flags);
     else
       k_dem_forces<double><<<nb, 128, 0, s>>>(n, d->dd, hdt, x, v, w, r, f_ext, d->start,
-                                              d->perm, d->hj[o], d->ht[o], d->hj[nw], d->ht[nw],
-                                              d->wh, d->acc, d->alpha, d->flags);
+                                              d->perm, d->xs, d->wf, d->hj[o], d->ht[o],
+                                              d->hj[nw], d->ht[nw], d->wh, d->acc, d->alpha,
+                                              d->flags);
     count_launches(6);
     d->cur = nw;
     return cudaGetLastError();

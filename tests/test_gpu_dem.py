@@ -60,11 +60,12 @@ def test_matches_oracle(precision):
     assert np.abs(ref.v - v).max() > 1e-3        # the contacts did act
 
 
-def test_history_carries_over_calls_and_is_reproducible():
+@pytest.mark.parametrize("precision", [0, 1])
+def test_history_carries_over_calls_and_is_reproducible(precision):
     x, v, w, r, fe, p = _bed(seed=6)
-    a = _run_gpu(x, v, w, r, fe, p, 2e-6, [40])
-    b = _run_gpu(x, v, w, r, fe, p, 2e-6, [15, 25])
-    c = _run_gpu(x, v, w, r, fe, p, 2e-6, [40])
+    a = _run_gpu(x, v, w, r, fe, p, 2e-6, [40], precision)
+    b = _run_gpu(x, v, w, r, fe, p, 2e-6, [15, 25], precision)
+    c = _run_gpu(x, v, w, r, fe, p, 2e-6, [40], precision)
     for u, t in zip(a, b):
         assert np.array_equal(u, t)
     for u, t in zip(a, c):
@@ -96,3 +97,61 @@ def test_capacity_and_radius_checks():
     with cf.Dem(dict(prm, max_radius=0.5 * float(r.max()))) as dm:
         dm.step(tx, tv, tw, dev(r), None, 1e-7, 1)
         assert dm.synchronize() == cf.EINVAL
+
+
+def test_precision_change_forgets_the_history():
+    """Switching the precision of a live state starts its contact memory
+    afresh: the same as a new state that takes over the positions."""
+    x, v, w, r, fe, p = _bed(seed=8)
+    dt = 2e-6
+    tx, tv, tw = dev(x), dev(v), dev(w)
+    with cf.Dem(_gpu_params(p, r, 1)) as dm:
+        dm.step(tx, tv, tw, dev(r), dev(fe), dt, 15)
+        mid = host(tx), host(tv), host(tw)
+        dm.set_params(_gpu_params(p, r, 0))
+        dm.step(tx, tv, tw, dev(r), dev(fe), dt, 10)
+        assert dm.synchronize() == cf.OK, dm.last_error()
+        a = host(tx), host(tv), host(tw)
+    b = _run_gpu(*mid, r, fe, p, dt, [10], 0)
+    for u, t in zip(a, b):
+        assert np.array_equal(u, t)
+
+
+def _crowd(m, r_big=1e-3, r_small=0.2e-3, overlap=2e-6):
+    """A sphere touched by m small ones (Fibonacci points on the contact
+    shell), in free space."""
+    k = np.arange(m) + 0.5
+    phi = np.arccos(1 - 2 * k / m)
+    th = np.pi * (1 + 5 ** 0.5) * k
+    u = np.stack([np.cos(th) * np.sin(phi), np.sin(th) * np.sin(phi), np.cos(phi)], axis=1)
+    c = np.array([0.01, 0.01, 0.01])
+    x = np.vstack([c, c + (r_big + r_small - overlap) * u])
+    r = np.concatenate([[r_big], np.full(m, r_small)])
+    return x, r
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_64_contacts_fit_and_65_overflow(precision):
+    """The largest capacity: a particle with 64 contacts matches the oracle;
+    with 70 the capacity flag is raised."""
+    p = D.glass_params((0, 0, 0), (0.02, 0.02, 0.02), g=(0.0, 0.0, 0.0), friction=0.3)
+    x, r = _crowd(64)
+    n = x.shape[0]
+    rng = np.random.default_rng(3)
+    v = 0.01 * rng.standard_normal((n, 3))
+    w = 5.0 * rng.standard_normal((n, 3))
+    ref = D.State(x, v, w, r, capacity=64)
+    assert ref.step(p, 1e-7, 3) == 0
+    prm = dict(_gpu_params(p, r, precision), capacity=64)
+    tx, tv, tw = dev(x), dev(v), dev(w)
+    with cf.Dem(prm) as dm:
+        dm.step(tx, tv, tw, dev(r), None, 1e-7, 3)
+        assert dm.synchronize() == cf.OK, dm.last_error()
+    tol = 1e-9 if precision == 0 else 2e-5
+    assert rel_err(host(tv) - v, ref.v - v) <= tol
+    assert rel_err(host(tw) - w, ref.w - w) <= tol
+    x, r = _crowd(70)
+    z = np.zeros_like(x)
+    with cf.Dem(dict(prm, max_radius=float(r.max()))) as dm:
+        dm.step(dev(x), dev(z), dev(z), dev(r), None, 1e-7, 1)
+        assert dm.synchronize() == cf.ECAPACITY
