@@ -44,6 +44,44 @@ __device__ __forceinline__ df64 df_from_double(double v) {
   return df64(h, (float)(v - (double)h));
 }
 
+// The same split with integer operations, for bulk conversions: on this part
+// every FP64 instruction (conversions included) runs at 1/61 of the FP32
+// rate.  hi takes the sign, the exponent and the leading 24 significand bits
+// of v (truncated), lo the remaining 29 bits as a float (rounded to 24 by
+// the integer-to-float conversion), so hi + lo = v to 2^-48 |v| and
+// |lo| < ulp(hi).  Zero is split as zero; a v whose hi or lo would not be a
+// normal float (|v| < 2^-74 or |v| >= 2^128, subnormals, inf, nan) takes the
+// FP64 conversion.
+__device__ __forceinline__ df64 df_from_double_int(double v) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  const unsigned sign = (unsigned)(bits >> 32) & 0x80000000u;
+  if ((bits << 1) == 0ull) return df64(__uint_as_float(sign), 0.f);
+  const int E = (int)((bits >> 52) & 0x7ff);
+  if (E < 949 || E > 1150) return df_from_double(v);
+  const float hi = __uint_as_float(sign | ((unsigned)(E - 896) << 23) |
+                                   ((unsigned)(bits >> 29) & 0x7fffffu));
+  const float scale = __uint_as_float((unsigned)(E - 948) << 23);  // 2^(E - 1075)
+  const float lo = (float)(unsigned)(bits & 0x1fffffffull) * scale;
+  return df64(hi, __uint_as_float(__float_as_uint(lo) | sign));
+}
+
+// float -> double by moving the bit fields (exact, as the conversion is);
+// zero, subnormals, inf and nan take the conversion instruction
+__device__ __forceinline__ double double_from_float_int(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
+  if ((u << 1) == 0u) return __longlong_as_double((long long)sgn);
+  const unsigned ef = (u >> 23) & 0xffu;
+  if (ef == 0u || ef == 255u) return (double)f;
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)(ef + 896u) << 52) |
+                                          ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+
+// hi + lo in FP64: one addition after the two exact widenings
+__device__ __forceinline__ double double_from_df_int(df64 v) {
+  return double_from_float_int(v.hi) + double_from_float_int(v.lo);
+}
+
 __device__ __forceinline__ bool df_le(df64 a, df64 b) {
   return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo);
 }

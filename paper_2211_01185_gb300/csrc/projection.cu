@@ -779,22 +779,27 @@ k_cg_start_fdm(int64_t n, const TB* __restrict__ b, const T* __restrict__ Ax,
 }
 
 // --- mixed path: outer CG in double-float, FP32 directions and FDM --------
-// b, x (FP64) -> df64 copies in one pass; b . b from the high parts (FP32
-// products, one conversion per thread) into sc->bb
+// b, x (FP64) -> df64 copies in one pass, converted with integer operations;
+// b . b from the high parts (FP32 products, one conversion per thread) into
+// sc->bb; also r = b, r32 = hi(b): the residual of a zero start vector, which
+// k_residual_df then leaves in place (it overwrites them when x != 0)
 __global__ void __launch_bounds__(256)
 k_split_df(int64_t n, const double* __restrict__ b, df64* __restrict__ b_df,
-           const double* __restrict__ x, df64* __restrict__ x_df, double* partials,
-           CgScalars* sc) {
+           const double* __restrict__ x, df64* __restrict__ x_df, df64* __restrict__ r,
+           float* __restrict__ r32, double* partials, CgScalars* sc) {
   __shared__ double red[32];
   float bb = 0.f;
   int nz = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    df64 v = df_from_double(b[i]);
+    const df64 v = df_from_double_int(b[i]);
     b_df[i] = v;
+    r[i] = v;
+    r32[i] = v.hi;
     bb = fmaf(v.hi, v.hi, bb);
-    x_df[i] = df_from_double(x[i]);
-    nz |= x[i] != 0.0;
+    const double xi = x[i];
+    x_df[i] = df_from_double_int(xi);
+    nz |= ((unsigned long long)__double_as_longlong(xi) << 1) != 0ull;  // x != 0, no FP64 op
   }
   if (__syncthreads_or(nz) && threadIdx.x == 0) atomicOr(&sc->xnz, 1);
   double s = block_sum((double)bb, red);
@@ -806,12 +811,13 @@ k_split_df(int64_t n, const double* __restrict__ b, df64* __restrict__ b_df,
 __global__ void k_join_df(int64_t n, const df64* __restrict__ in, double* __restrict__ out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    df64 v = in[i];
-    out[i] = (double)v.hi + (double)v.lo;
+    out[i] = double_from_df_int(in[i]);
   }
 }
 
-// r = b - A x (df64), r32 = hi(r), r . r ; tolerance and convergence flag
+// r = b - A x (df64), r32 = hi(r), r . r ; tolerance and convergence flag.
+// For a zero start vector (flag from k_split_df) r = b, r32 and r . r = b . b
+// are already in place: one thread sets the scalars
 template <int K, class S>
 __global__ void __launch_bounds__(kApplyThreads)
 k_residual_df(MeshDev m, const df64* __restrict__ bands, Coefs<df64> cf,
@@ -819,37 +825,27 @@ k_residual_df(MeshDev m, const df64* __restrict__ bands, Coefs<df64> cf,
               float* __restrict__ r32, double* partials, CgScalars* sc, double rtol) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double red[32];
-  double d;
-  if (((volatile CgScalars*)sc)->xnz) {
+  const bool xnz = ((volatile CgScalars*)sc)->xnz;
+  double rr;
+  if (xnz) {
     LoadPlain<df64> ld{x};
     EpiResidualDf ep{b, r, r32};
-    d = apply_tile<K, S, df64>(m, bands, cf, ld, ep, reinterpret_cast<df64*>(smraw));
-  } else {  // zero start vector (flag from k_split_df): r = b, no operator
-    // the tile grid is three-dimensional: stride over the flattened grid
-    float acc = 0.f;
-    const int64_t n = m.n_nodes;
-    const int64_t blk =
-        blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
-    const int64_t nthr = (int64_t)gridDim.x * gridDim.y * gridDim.z * blockDim.x;
-    for (int64_t i = blk * blockDim.x + threadIdx.x; i < n; i += nthr) {
-      const df64 v = b[i];
-      r[i] = v;
-      r32[i] = v.hi;
-      acc = fmaf(v.hi, v.hi, acc);
-    }
-    d = (double)acc;
+    const double d = apply_tile<K, S, df64>(m, bands, cf, ld, ep, reinterpret_cast<df64*>(smraw));
+    const double s = block_sum(d, red);
+    double vals[1] = {s};
+    double out[1];
+    if (!last_block_reduce(partials, 1, vals, &sc->ticket, out, red) || threadIdx.x != 0) return;
+    rr = out[0];
+  } else {
+    if (blockIdx.x != 0 || blockIdx.y != 0 || blockIdx.z != 0 || threadIdx.x != 0) return;
+    rr = sc->bb;
   }
-  double s = block_sum(d, red);
-  double vals[1] = {s};
-  double out[1];
-  if (last_block_reduce(partials, 1, vals, &sc->ticket, out, red) && threadIdx.x == 0) {
-    sc->rr = out[0];
-    double bbv = sc->bb > 0.0 ? sc->bb : 1.0;
-    sc->tol2 = rtol * rtol * bbv;
-    sc->it = 0;
-    sc->done = out[0] <= sc->tol2 ? 1 : 0;
-    sc->beta = 0.0;
-  }
+  sc->rr = rr;
+  const double bbv = sc->bb > 0.0 ? sc->bb : 1.0;
+  sc->tol2 = rtol * rtol * bbv;
+  sc->it = 0;
+  sc->done = rr <= sc->tol2 ? 1 : 0;
+  sc->beta = 0.0;
 }
 
 // p = z + beta p_old (df64) ; Ap = A p in df64 ; alpha = rz / (p . Ap)
@@ -992,10 +988,6 @@ static auto with_k(const MeshDev& m, F&& f) {
   if (m.k == 1) return f(std::integral_constant<int, 1>{});
   if (m.k == 2) return f(std::integral_constant<int, 2>{});
   return f(std::integral_constant<int, 3>{});
-}
-
-static dim3 apply_grid(const MeshDev& m) {
-  return with_shape(m, [&](auto s) { return apply_grid_s<decltype(s)>(m); });
 }
 
 // work of one tile in 1D taps: z pass on the haloed x-y columns, y pass on
@@ -1398,7 +1390,7 @@ static cudaError_t cg_solve_df(const MeshDev& m, const df64* bands, const double
   const size_t sm = apply_smem<K, S, df64>();
   Timer* tm = w.timer;
   if ((e = cudaMemsetAsync(w.sc, 0, sizeof(CgScalars), s)) != cudaSuccess) return e;
-  k_split_df<<<vb, 256, 0, s>>>(n, b, w.b_df, x, w.x_df, w.partials, w.sc);
+  k_split_df<<<vb, 256, 0, s>>>(n, b, w.b_df, x, w.x_df, w.r_df, w.r32, w.partials, w.sc);
   if (tm) tm->begin(kStageOp32, s);
   k_residual_df<K, S><<<g, kApplyThreads, sm, s>>>(m, bands, cf, w.x_df, w.b_df, w.r_df, w.r32,
                                                 w.partials, w.sc, rtol);
