@@ -33,10 +33,13 @@
 #include <vector>
 
 #include "internal.h"
+#include "reduce.cuh"
 
 namespace cfdem {
 
 namespace {
+
+constexpr int kSlabSmemMax = 220 * 1024;  // dynamic shared memory of the slab form, at most
 
 // symmetric eigen-decomposition: A (n x n, row-major) is replaced by the
 // eigenvectors (columns), w receives the eigenvalues.  Returns false if the
@@ -321,12 +324,21 @@ __host__ __device__ __forceinline__ int slab_pad(int n) { return ((n + 7) & ~7) 
 // both zero-padded row-major in global memory and copied to shared memory as
 // they are.  The slab is staged transposed (x major) as the A operand of the
 // first product.
+//
+// With dot.r set (the inverse transform that writes z), the kernel also
+// forms r . z of the CG from the values it stores: one FP32 sum per thread,
+// block sums in FP64, the last block to finish adds the blocks' sums in
+// block order and sets rz and the Fletcher-Reeves beta = rz_new / rz_old
+// (not on the first application) -- the dot product kernel that would read
+// r and z again is not launched.
 template <int TILE>
 __global__ void k_fdm_slab(int nx, int ny, int nz, const float* __restrict__ Bx,
                            const float* __restrict__ AyT, const float* __restrict__ in,
                            int in_stride, float* __restrict__ out, int out_stride,
-                           const int* __restrict__ done) {
+                           const int* __restrict__ done, FdmDot dot) {
   if (done && *(volatile const int*)done) return;
+  __shared__ double red[32];
+  float rz = 0.f;
   extern __shared__ __align__(16) float fsm[];
   const int px = slab_pad(nx), py = slab_pad(ny);
   const int plane = nx * ny;
@@ -355,11 +367,23 @@ __global__ void k_fdm_slab(int nx, int ny, int nz, const float* __restrict__ Bx,
     smem_gemm<TILE, TILE>(MA, py, T, px, Y, px, ny, nx, ny);   // Y[y'][x] = sum_y AyT[y][y'] T[y][x]
     __syncthreads();
     float* dst = out + (int64_t)z * out_stride;
+    const float* rr = dot.r ? dot.r + (int64_t)z * plane : nullptr;
     for (int t = threadIdx.x; t < plane; t += blockDim.x) {
       int y = t / nx, x = t - y * nx;
-      dst[t] = Y[y * px + x];
+      const float v = Y[y * px + x];
+      dst[t] = v;
+      if (rr) rz = fmaf(rr[t], v, rz);
     }
     __syncthreads();
+  }
+  if (dot.r) {
+    const double sblk = block_sum((double)rz, red);
+    double vals[1] = {sblk};
+    double o[1];
+    if (last_block_reduce(dot.partials, 1, vals, &dot.sc->ticket, o, red) && threadIdx.x == 0) {
+      if (!dot.first) dot.sc->beta = o[0] / dot.sc->rz;
+      dot.sc->rz = o[0];
+    }
   }
 }
 
@@ -683,7 +707,7 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4], 
   };
   p->zseg = zsmem(16) <= 220 * 1024 ? 16 : 8;
   p->z_smem = zsmem(p->zseg);
-  p->slab = p->slab_smem <= 220 * 1024 && p->z_smem <= 220 * 1024;
+  p->slab = p->slab_smem <= (size_t)kSlabSmemMax && p->z_smem <= 220 * 1024;
   std::vector<double> lam[3];
   cudaError_t e = cudaSuccess;
   const int naxes = p->slab ? 2 : 3;
@@ -742,10 +766,16 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4], 
       e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e == cudaSuccess && ((size_t)optin < p->slab_smem || (size_t)optin < p->z_smem))
       e = cudaErrorInvalidValue;
+    // the slab kernels also hold a little static shared memory (the dot
+    // product's block sums): their dynamic share is capped at the slab
+    // form's own limit, which leaves room for it
+    const int slab_cap = std::min(optin, kSlabSmemMax);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_fdm_slab<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+      e = cudaFuncSetAttribute(k_fdm_slab<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               slab_cap);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_fdm_slab<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+      e = cudaFuncSetAttribute(k_fdm_slab<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               slab_cap);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_fdm_zsolve<1, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                optin);
@@ -798,21 +828,23 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4], 
 // z = A^-1 r (FP32), r is preserved.  Uses p->tmp.  The slab-form kernels
 // return at once when *done is set (a converged CG), so iterations can be
 // queued without host round trips.
-cudaError_t fdm_apply(FdmPlan* p, const float* r, float* z, const int* done, cudaStream_t s) {
+cudaError_t fdm_apply(FdmPlan* p, const float* r, float* z, const int* done, cudaStream_t s,
+                      const FdmDot* dot, bool* dot_done) {
   int nx = p->n[0], ny = p->n[1], nz = p->n[2];
+  if (dot_done) *dot_done = false;
   if (p->slab) {
     int nblk = nz < 304 ? nz : 304;
     int nm = nx * ny;
     auto slab = [&](const float* Bx, const float* AyT, const float* in, int is, float* out,
-                    int os) {
+                    int os, FdmDot dd) {
       if (p->slab_tile == 4)
         k_fdm_slab<4><<<nblk, p->slab_threads, p->slab_smem, s>>>(nx, ny, nz, Bx, AyT, in, is,
-                                                                   out, os, done);
+                                                                   out, os, done, dd);
       else
         k_fdm_slab<8><<<nblk, p->slab_threads, p->slab_smem, s>>>(nx, ny, nz, Bx, AyT, in, is,
-                                                                   out, os, done);
+                                                                   out, os, done, dd);
     };
-    slab(p->V[0], p->V[1], r, nm, p->tmp, p->ms);
+    slab(p->V[0], p->V[1], r, nm, p->tmp, p->ms, FdmDot{});
     unsigned zb = (unsigned)((nm + 31) / 32);
 #define CFDEM_ZS(KK, SS)                                                                   \
   k_fdm_zsolve<KK, SS><<<zb, 32 * SS, p->z_smem, s>>>(nm, p->ms, nz, p->fac, p->tr, p->tmp, done)
@@ -826,7 +858,8 @@ cudaError_t fdm_apply(FdmPlan* p, const float* r, float* z, const int* done, cud
       else CFDEM_ZS(3, 8);
     }
 #undef CFDEM_ZS
-    slab(p->VT[0], p->VT[1], p->tmp, p->ms, z, nm);
+    slab(p->VT[0], p->VT[1], p->tmp, p->ms, z, nm, dot ? *dot : FdmDot{});
+    if (dot_done) *dot_done = dot != nullptr;
     count_launches(3);
     return cudaGetLastError();
   }

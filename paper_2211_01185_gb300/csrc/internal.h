@@ -43,6 +43,8 @@ struct Tables {
   double Bw[4][4];          // Bw[a][q] = l_a(g_q) w_q  (k basis, Gauss weight folded in)
   double Mh[4][4];          // reference mass     int_0^1 l_a l_b
   double Kh[4][4];          // reference stiffness int_0^1 l_a' l_b'
+  float zf[4], zpf[4];      // z, zp and their barycentric weights rounded to FP32
+  float lwf[4], lwpf[4];
 };
 
 // Bin grid over the box.
@@ -182,7 +184,19 @@ cudaError_t launch_adj_qcm(const MeshDev& m, const Tables& t, int precision, dou
 struct FdmPlan;
 cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4], FdmPlan** out,
                        const char** why);
-cudaError_t fdm_apply(FdmPlan* p, const float* r, float* z, const int* done, cudaStream_t s);
+// r . z of the CG formed by the FDM's last pass (slab form only): r the
+// residual the FDM was applied to (FP32), the block sums go to partials,
+// rz and (unless first) the Fletcher-Reeves beta to sc.
+struct FdmDot {
+  const float* r = nullptr;
+  double* partials = nullptr;
+  CgScalars* sc = nullptr;
+  int first = 0;
+};
+// z = P^-1 r; with dot (and the slab form) also r . z into dot->sc, and
+// *dot_done = true -- otherwise the caller forms the dot product
+cudaError_t fdm_apply(FdmPlan* p, const float* r, float* z, const int* done, cudaStream_t s,
+                      const FdmDot* dot = nullptr, bool* dot_done = nullptr);
 void fdm_destroy(FdmPlan* p);
 
 struct CgWork {

@@ -35,6 +35,7 @@
 
 #include "internal.h"
 #include "df64.cuh"
+#include "reduce.cuh"
 
 namespace cfdem {
 
@@ -517,50 +518,6 @@ __device__ __forceinline__ double apply_tile(const MeshDev& m, const T* __restri
     dot += ep(gx + (int64_t)nx * gy + sxy * gz, acc, xe);
   }
   return (double)dot;
-}
-
-__device__ __forceinline__ double block_sum(double v, double* red) {
-  // red: >= 32 doubles of shared memory
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (warp == 0) {
-    s = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  }
-  return s;  // valid in thread 0
-}
-
-// last block to finish reduces partials[0..nb) (nvals interleaved values) in
-// fixed order; returns true in the last block (results in out[0..nvals))
-__device__ bool last_block_reduce(double* partials, int nvals, const double* vals,
-                                  unsigned int* ticket, double* out, double* red) {
-  __shared__ bool last;
-  if (threadIdx.x == 0) {
-    for (int v = 0; v < nvals; ++v) partials[(size_t)v * gridDim.x * gridDim.y * gridDim.z +
-                                             blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = vals[v];
-    __threadfence();
-    unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
-    unsigned t = atomicInc(ticket, nblk - 1);
-    last = (t == nblk - 1);
-  }
-  __syncthreads();
-  if (!last) return false;
-  __threadfence();
-  unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
-  for (int v = 0; v < nvals; ++v) {
-    double s = 0.0;
-    for (unsigned i = threadIdx.x; i < nblk; i += blockDim.x)
-      s += ((volatile double*)partials)[(size_t)v * nblk + i];
-    s = block_sum(s, red);
-    if (threadIdx.x == 0) out[v] = s;
-  }
-  return true;
 }
 
 template <int K, class S, typename T>
@@ -1119,11 +1076,13 @@ static int vec_blocks(int64_t n) {
 // stream `ls` -- holds two CG iterations and ends with k_loop_cond, which sets
 // the node's condition from `done`, so the graph iterates on the device until
 // the CG has converged or reached its iteration cap.  (Two iterations, so that
-// the ping-pong buffers are back in their roles at the end of the body; the
-// first iteration, with beta = 0, is queued before the node.)
+// the ping-pong buffers are back in their roles at the end of the body.)  The
+// first two iterations are queued before the node, and a k_loop_cond ahead
+// of the node decides whether the body runs at all: a solve that converges
+// in two iterations -- the mixed cold start -- launches no idle iteration.
 
 // one thread: continue while the CG is not done, and never beyond
-// max_bodies bodies whatever the kernels of the body did (sc->loops is
+// max_bodies - 1 bodies whatever the kernels of the body did (sc->loops is
 // cleared with the other scalars at the start of every solve)
 __global__ void k_loop_cond(cudaGraphConditionalHandle h, CgScalars* sc, int max_bodies) {
   volatile CgScalars* v = sc;
@@ -1132,15 +1091,24 @@ __global__ void k_loop_cond(cudaGraphConditionalHandle h, CgScalars* sc, int max
   cudaGraphSetConditional(h, (!v->done && n < max_bodies) ? 1u : 0u);
 }
 
-static cudaError_t loop_open(cudaStream_t s, cudaStream_t ls, cudaGraphConditionalHandle* h) {
+// bodies allowed for maxit iterations: two queued ahead, two per body
+static int loop_max_bodies(int maxit) { return maxit / 2 + 2; }
+
+static cudaError_t loop_open(cudaStream_t s, cudaStream_t ls, cudaGraphConditionalHandle* h,
+                             CgScalars* sc, int maxit) {
   cudaStreamCaptureStatus cs;
   cudaGraph_t g = nullptr;
-  const cudaGraphNode_t* deps = nullptr;
-  size_t nd = 0;
-  cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd);
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr);
   if (e != cudaSuccess) return e;
   if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureUnmatched;
-  if ((e = cudaGraphConditionalHandleCreate(h, g, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
+  if ((e = cudaGraphConditionalHandleCreate(h, g, 0, 0)) != cudaSuccess) return e;
+  // the condition for the first body, set upstream of the node
+  k_loop_cond<<<1, 1, 0, s>>>(*h, sc, loop_max_bodies(maxit));
+  count_launches(1);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  if ((e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd)) != cudaSuccess)
     return e;
   cudaGraphNodeParams np{};
   np.type = cudaGraphNodeTypeConditional;
@@ -1159,8 +1127,7 @@ static cudaError_t loop_open(cudaStream_t s, cudaStream_t ls, cudaGraphCondition
 static cudaError_t loop_close(cudaStream_t ls, cudaGraphConditionalHandle h, CgScalars* sc,
                               int maxit, cudaError_t body_status) {
   if (body_status == cudaSuccess) {
-    // maxit iterations = the peeled one + (maxit - 1) / 2 bodies of two
-    k_loop_cond<<<1, 1, 0, ls>>>(h, sc, maxit / 2 + 2);
+    k_loop_cond<<<1, 1, 0, ls>>>(h, sc, loop_max_bodies(maxit));
     count_launches(1);
     body_status = cudaGetLastError();
   }
@@ -1214,8 +1181,9 @@ static cudaError_t cg_solve(const MeshDev& m, const T* bands, const double* coef
   };
   if (ls) {  // device-driven loop inside a stream capture
     if ((e = iter(1, s)) != cudaSuccess) return e;
+    if ((e = iter(0, s)) != cudaSuccess) return e;
     cudaGraphConditionalHandle h;
-    if ((e = loop_open(s, ls, &h)) != cudaSuccess) return e;
+    if ((e = loop_open(s, ls, &h, sc, maxit)) != cudaSuccess) return e;
     e = iter(0, ls);
     if (e == cudaSuccess) e = iter(0, ls);
     if ((e = loop_close(ls, h, sc, maxit, e)) != cudaSuccess) return e;
@@ -1312,8 +1280,9 @@ static cudaError_t cg_solve_fdm(const MeshDev& m, const T* bands, const double* 
   };
   if (ls) {  // device-driven loop inside a stream capture
     if ((e = iter(1, s)) != cudaSuccess) return e;
+    if ((e = iter(0, s)) != cudaSuccess) return e;
     cudaGraphConditionalHandle h;
-    if ((e = loop_open(s, ls, &h)) != cudaSuccess) return e;
+    if ((e = loop_open(s, ls, &h, sc, maxit)) != cudaSuccess) return e;
     e = iter(0, ls);
     if (e == cudaSuccess) e = iter(0, ls);
     if ((e = loop_close(ls, h, sc, maxit, e)) != cudaSuccess) return e;
@@ -1401,9 +1370,14 @@ static cudaError_t cg_solve_df(const MeshDev& m, const df64* bands, const double
   float* zo = w.zn32;
   df64* pc = w.p0_df;
   df64* pn = w.p1_df;
-  if ((e = fdm_apply(w.fdm, w.r32, zc, nullptr, s)) != cudaSuccess) return e;
-  k_cg_dot_fdm<float><<<vb, 256, 0, s>>>(n, w.r32, nullptr, zc, zc, w.partials, w.sc, 1, 1);
-  count_launches(1);
+  // z = P^-1 r and r . z (the FDM's last pass forms the dot product where it can)
+  const FdmDot dot0{w.r32, w.partials, w.sc, 1};
+  bool fused = false;
+  if ((e = fdm_apply(w.fdm, w.r32, zc, nullptr, s, &dot0, &fused)) != cudaSuccess) return e;
+  if (!fused) {
+    k_cg_dot_fdm<float><<<vb, 256, 0, s>>>(n, w.r32, nullptr, zc, zc, w.partials, w.sc, 1, 1);
+    count_launches(1);
+  }
   auto iter = [&](int first, cudaStream_t st) -> cudaError_t {
     cudaError_t ee;
     if (tm) tm->begin(kStageOp32, st);
@@ -1414,9 +1388,14 @@ static cudaError_t cg_solve_df(const MeshDev& m, const df64* bands, const double
                                       maxit);
     count_launches(2);
     if ((ee = cudaGetLastError()) != cudaSuccess) return ee;
-    if ((ee = fdm_apply(w.fdm, w.r32, zo, &w.sc->done, st)) != cudaSuccess) return ee;
-    k_cg_dot_fdm<float><<<vb, 256, 0, st>>>(n, w.r32, nullptr, zc, zo, w.partials, w.sc, 0, 0, 1);
-    count_launches(1);
+    const FdmDot dot{w.r32, w.partials, w.sc, 0};
+    bool fz = false;
+    if ((ee = fdm_apply(w.fdm, w.r32, zo, &w.sc->done, st, &dot, &fz)) != cudaSuccess) return ee;
+    if (!fz) {  // Fletcher-Reeves beta (see k_cg_dot_fdm)
+      k_cg_dot_fdm<float><<<vb, 256, 0, st>>>(n, w.r32, nullptr, zc, zo, w.partials, w.sc, 0, 0,
+                                             1);
+      count_launches(1);
+    }
     if ((ee = cudaGetLastError()) != cudaSuccess) return ee;
     float* t = zc;
     zc = zo;
@@ -1428,8 +1407,9 @@ static cudaError_t cg_solve_df(const MeshDev& m, const df64* bands, const double
   };
   if (w.loop) {  // device-driven loop inside a stream capture
     if ((e = iter(1, s)) != cudaSuccess) return e;
+    if ((e = iter(0, s)) != cudaSuccess) return e;
     cudaGraphConditionalHandle h;
-    if ((e = loop_open(s, w.loop, &h)) != cudaSuccess) return e;
+    if ((e = loop_open(s, w.loop, &h, w.sc, maxit)) != cudaSuccess) return e;
     e = iter(0, w.loop);
     if (e == cudaSuccess) e = iter(0, w.loop);
     if ((e = loop_close(w.loop, h, w.sc, maxit, e)) != cudaSuccess) return e;
