@@ -43,8 +43,6 @@ struct Tables {
   double Bw[4][4];          // Bw[a][q] = l_a(g_q) w_q  (k basis, Gauss weight folded in)
   double Mh[4][4];          // reference mass     int_0^1 l_a l_b
   double Kh[4][4];          // reference stiffness int_0^1 l_a' l_b'
-  float zf[4], zpf[4];      // z, zp and their barycentric weights rounded to FP32
-  float lwf[4], lwpf[4];
 };
 
 // Bin grid over the box.
