@@ -36,6 +36,12 @@ WORKLOAD = "q2_32x32x128_100k"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 FP32_TFLOPS = 73.13    # measured FMA peak on this GB300 (profiles/alu_peaks_gb300.md)
 FP64_TFLOPS = 1.197
+# DRAM bytes (read + write) of one launch of the FP32 QCM kernel on this
+# workload, from one ncu capture (profiles/qcm_kernel_q2_32x32x128_100k.md):
+# 3.62 MB read -- the sorted particle copies and the bin table -- and no
+# write-back inside the launch (the 14 MB of eps stay in L2); to be cleared
+# whenever that kernel changes
+QCM_TRAFFIC_BYTES = 3622656 + 0
 
 
 def _peaks():
@@ -763,8 +769,10 @@ def main():
     else:
         achieved = work / (per_launch_ms * 1e-3) / 1e9
         unit, peak_v = "GB/s", peaks.get("hbm_gbs", 6800.0)
+    traffic = QCM_TRAFFIC_BYTES if dom == "void_fraction" else None
     roof = {"bound": bound, "kernel": kname, "achieved": achieved, "peak": peak_v,
-            "unit": unit, "frac": achieved / peak_v, "traffic": None,
+            "unit": unit, "frac": achieved / peak_v, "traffic": traffic,
+            "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
             "peak_source": ("measured FMA loop (profiles/alu_peaks_gb300.md)" if bound == "alu"
                             else "%s MEASURED_PEAKS.json hbm_gbs" % peak_kind),
             "launches_per_step": calls[dom], "ms_per_launch": per_launch_ms,

@@ -224,6 +224,27 @@ def test_projection(c, precision, precond, start):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
+def test_projection_wide_slabs(precision):
+    """A Q3 mesh of 48 x 48 x 3 elements (145 x 145 x 10 nodes): its z-slabs
+    are too wide for the shared-memory form of the FDM, which then runs as
+    dense cuBLAS transforms, and the mixed CG forms r.z with its own kernel."""
+    case = _case(107, (48, 48, 3), 3, 1, (0.048, 0.048, 0.003))
+    m = _mesh(case)
+    rng = np.random.default_rng(7)
+    eps_q = 0.3 + 0.7 * rng.random((m.n_elem, m.Q))
+    L2 = case["params"]["l2_smoothing"]
+    with _ctx(case, precision=precision, cg_rtol=1e-13, cg_precond=1) as ctx:
+        x = _zeros(m.n_nodes())
+        cf.cfdem_project(ctx.h, dev(eps_q), x)
+        cf.cfdem_synchronize(ctx.h)
+        st = ctx.stats()
+        assert st.converged == 1 and st.cg_relres <= 1e-13
+        assert st.precond == 1
+    ref = O.fdm_solve(m, L2, O.rhs(m, eps_q))
+    assert rel_err(host(x), ref) <= 1e-10
+
+
+@pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("drag,vans,boe", [(0, 0, 0), (1, 1, 0), (0, 1, 1), (2, 0, 0),
                                             (3, 1, 0), (4, 0, 1), (5, 1, 1), (4, 1, 0)])
 @pytest.mark.parametrize("c", CASES)
