@@ -284,11 +284,24 @@ cfdem_status cfdem_mass_apply(cfdem_t ctx, const double *x_dev, double *y_dev);
 typedef struct cfdem_batch *cfdem_batch_t;
 
 /* Per-bed arguments of cfdem_batch_coupling_step: those of
- * cfdem_coupling_step (device pointers on the batch's device). */
+ * cfdem_coupling_step (device pointers on the batch's device), then
+ * optional host buffers (NULL = none) for a step that starts and ends in
+ * host memory.  host_x and host_r are uploaded into x and r first;
+ * host_u_p, host_u_nodal and host_p_nodal into u_p, u_nodal and p_nodal on
+ * a second stream of the bed, while the void fraction and the projection
+ * run (the forces wait for them); f and F_elem are downloaded into host_f
+ * and host_F_elem at the end.  The device buffers are written although
+ * declared const.  Host buffers must be page-locked (cudaHostAlloc or
+ * registered) for the copies to overlap and for the step to be captured
+ * into the batch's graph; they are part of the arguments a replay is keyed
+ * on.  Sizes: x, u_p, f 3n; r n; u_nodal 3 n_nodes; p_nodal the pressure
+ * nodes; F_elem 3 E doubles. */
 typedef struct {
     int64_t n;
     const double *x, *r, *u_p, *u_nodal, *p_nodal;
     double *eps_nodal, *f, *f_drag, *F_elem, *F_q;
+    const double *host_x, *host_r, *host_u_p, *host_u_nodal, *host_p_nodal;
+    double *host_f, *host_F_elem;
 } cfdem_bed_io;
 
 /* Create a batch of n_beds (1 .. 4096) empty beds on `device`; `stream`
@@ -300,9 +313,9 @@ cfdem_status cfdem_batch_destroy(cfdem_batch_t b);
 /* The context of bed i, owned by the batch: give it a mesh and parameters
  * with cfdem_set_mesh / cfdem_set_params, read its statistics with
  * cfdem_get_stats after cfdem_batch_synchronize.  NULL if i is out of range.
- * A bed whose step cannot be captured (stage timers on, or a mixed solve
- * without the fast-diagonalisation preconditioner) keeps the whole batch
- * eager. */
+ * A bed whose step cannot be captured (stage timers on, a mixed solve
+ * without the fast-diagonalisation preconditioner, or host buffers that are
+ * not page-locked) keeps the whole batch eager. */
 cfdem_t cfdem_batch_bed(cfdem_batch_t b, int i);
 /* 1 (default): capture and replay graphs; 0: always run the beds eagerly. */
 cfdem_status cfdem_batch_set_graph(cfdem_batch_t b, int enable);

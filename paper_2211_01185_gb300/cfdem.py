@@ -62,7 +62,10 @@ class cfdem_bed_io(C.Structure):
     _fields_ = [("n", C.c_int64), ("x", C.c_void_p), ("r", C.c_void_p), ("u_p", C.c_void_p),
                 ("u_nodal", C.c_void_p), ("p_nodal", C.c_void_p), ("eps_nodal", C.c_void_p),
                 ("f", C.c_void_p), ("f_drag", C.c_void_p), ("F_elem", C.c_void_p),
-                ("F_q", C.c_void_p)]
+                ("F_q", C.c_void_p), ("host_x", C.c_void_p), ("host_r", C.c_void_p),
+                ("host_u_p", C.c_void_p), ("host_u_nodal", C.c_void_p),
+                ("host_p_nodal", C.c_void_p), ("host_f", C.c_void_p),
+                ("host_F_elem", C.c_void_p)]
 
 
 STAGES = ("bin", "void_fraction", "rhs", "solve", "forces", "fluid_source", "op32", "op64")
@@ -305,10 +308,18 @@ def cfdem_batch_set_graph(b, enable):
     return lib().cfdem_batch_set_graph(b, int(bool(enable)))
 
 
-def bed_io(n, x, r, u_p, u_nodal, p_nodal, eps_nodal, f, f_drag=None, F_elem=None, F_q=None):
-    """One cfdem_bed_io record (device tensors or addresses)."""
+def bed_io(n, x, r, u_p, u_nodal, p_nodal, eps_nodal, f, f_drag=None, F_elem=None, F_q=None,
+           host=None):
+    """One cfdem_bed_io record (device tensors or addresses).  host: optional
+    dict of page-locked host tensors or addresses, keys x, r, u_p, u_nodal,
+    p_nodal (uploaded into the device buffers by the step) and f, F_elem
+    (downloaded into at its end)."""
+    h = host or {}
     return cfdem_bed_io(int(n), _ptr(x), _ptr(r), _ptr(u_p), _ptr(u_nodal), _ptr(p_nodal),
-                        _ptr(eps_nodal), _ptr(f), _ptr(f_drag), _ptr(F_elem), _ptr(F_q))
+                        _ptr(eps_nodal), _ptr(f), _ptr(f_drag), _ptr(F_elem), _ptr(F_q),
+                        _ptr(h.get("x")), _ptr(h.get("r")), _ptr(h.get("u_p")),
+                        _ptr(h.get("u_nodal")), _ptr(h.get("p_nodal")), _ptr(h.get("f")),
+                        _ptr(h.get("F_elem")))
 
 
 def cfdem_batch_coupling_step(b, ios):

@@ -24,6 +24,8 @@ struct cfdem_batch {
   std::vector<cfdem_t> beds;
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> join;
+  std::vector<cudaStream_t> side;   // per bed: uploads of the inputs the forces need
+  std::vector<cudaEvent_t> sfork, late;
   cudaEvent_t fork = nullptr, in = nullptr, out = nullptr;
   bool use_graph = true;
   bool replayed = false;
@@ -71,6 +73,73 @@ void drop_graph(cfdem_batch_t b) {
   b->key_gen.clear();
 }
 
+// copy `count` doubles if both ends are given
+cudaError_t copy_if(const double* src, const double* dst, int64_t count, cudaMemcpyKind kind,
+                    cudaStream_t s) {
+  if (!src || !dst || count <= 0) return cudaSuccess;
+  return cudaMemcpyAsync(const_cast<double*>(dst), src, sizeof(double) * (size_t)count, kind, s);
+}
+
+// one bed's coupling step (cfdem_coupling_step: void fraction, projection,
+// forces), with the uploads and downloads of its host buffers: x and r on
+// the bed's stream ahead of the void fraction, u_p, u_nodal and p_nodal on
+// its side stream meanwhile, joined before the forces; f and F_elem back
+// after them
+cfdem_status step_bed(cfdem_batch_t b, size_t i, const cfdem_bed_io& a) {
+  cfdem_t c = b->beds[i];
+  cudaStream_t s = b->streams[i], side = b->side[i];
+  const MeshDev& m = c->mesh;
+  const bool staged = a.host_x || a.host_r || a.host_u_p || a.host_u_nodal || a.host_p_nodal ||
+                      a.host_f || a.host_F_elem;
+  if (staged && !c->have_mesh) return cfdem_coupling_step(c, a.n, a.x, a.r, a.u_p, a.u_nodal,
+                                                          a.p_nodal, a.eps_nodal, a.f, a.f_drag,
+                                                          a.F_elem, a.F_q);
+  const bool late = a.host_u_p || a.host_u_nodal || a.host_p_nodal;
+  if (staged && cfdem::stream_capturing(s)) {
+    // a capture takes page-locked host buffers only; with any other the
+    // eager step stands and the batch stays eager (CFDEM_ESTATE)
+    const void* hs[] = {a.host_x, a.host_r, a.host_u_p, a.host_u_nodal, a.host_p_nodal,
+                        a.host_f, a.host_F_elem};
+    for (const void* h : hs) {
+      if (!h) continue;
+      cudaPointerAttributes pa{};
+      if (cudaPointerGetAttributes(&pa, h) != cudaSuccess || pa.type != cudaMemoryTypeHost) {
+        cudaGetLastError();
+        return CFDEM_ESTATE;
+      }
+    }
+  }
+  if (staged) {
+    BCK(copy_if(a.host_x, a.x, 3 * a.n, cudaMemcpyHostToDevice, s), "upload x");
+    BCK(copy_if(a.host_r, a.r, a.n, cudaMemcpyHostToDevice, s), "upload r");
+  }
+  if (late) {
+    const int64_t npn = (int64_t)m.np[0] * m.np[1] * m.np[2];
+    BCK(cudaEventRecord(b->sfork[i], s), "fork uploads");
+    BCK(cudaStreamWaitEvent(side, b->sfork[i], 0), "fork uploads");
+    BCK(copy_if(a.host_u_p, a.u_p, 3 * a.n, cudaMemcpyHostToDevice, side), "upload u_p");
+    BCK(copy_if(a.host_u_nodal, a.u_nodal, 3 * m.n_nodes, cudaMemcpyHostToDevice, side),
+        "upload u_nodal");
+    BCK(copy_if(a.host_p_nodal, a.p_nodal, npn, cudaMemcpyHostToDevice, side), "upload p_nodal");
+    BCK(cudaEventRecord(b->late[i], side), "join uploads");
+  }
+  cfdem_status st = cfdem_void_fraction(c, a.n, a.x, a.r, nullptr, nullptr, nullptr);
+  if (st == CFDEM_OK) st = cfdem_project(c, nullptr, a.eps_nodal);
+  // the uploads are joined even after a failure, so that no branch of a
+  // capture is left open
+  if (late) BCK(cudaStreamWaitEvent(s, b->late[i], 0), "join uploads");
+  if (st != CFDEM_OK) return st;
+  st = cfdem_forces(c, a.n, a.x, a.r, a.u_p, a.u_nodal, a.p_nodal, a.eps_nodal, a.f, a.f_drag,
+                    a.F_elem, a.F_q);
+  if (st != CFDEM_OK) return st;
+  if (staged) {
+    BCK(copy_if(a.f, a.host_f, 3 * a.n, cudaMemcpyDeviceToHost, s), "download f");
+    BCK(copy_if(a.F_elem, a.host_F_elem, 3 * m.E, cudaMemcpyDeviceToHost, s),
+        "download F_elem");
+  }
+  return CFDEM_OK;
+}
+
 // fork every bed from b->cap, step it, join it back; *bad = first failing bed
 cfdem_status step_all(cfdem_batch_t b, const cfdem_bed_io* io, int* bad) {
   *bad = -1;
@@ -79,8 +148,7 @@ cfdem_status step_all(cfdem_batch_t b, const cfdem_bed_io* io, int* bad) {
   for (size_t i = 0; i < b->beds.size(); ++i) {
     BCK(cudaStreamWaitEvent(b->streams[i], b->fork, 0), "fork");
     const cfdem_bed_io& a = io[i];
-    cfdem_status s = cfdem_coupling_step(b->beds[i], a.n, a.x, a.r, a.u_p, a.u_nodal, a.p_nodal,
-                                         a.eps_nodal, a.f, a.f_drag, a.F_elem, a.F_q);
+    cfdem_status s = step_bed(b, i, a);
     if (s != CFDEM_OK && first == CFDEM_OK) {
       first = s;
       *bad = (int)i;
@@ -128,6 +196,14 @@ cfdem_status cfdem_batch_create(cfdem_batch_t* out, int device, void* stream, in
     if (ok) b->streams.push_back(s);
     ok = ok && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
     if (ok) b->join.push_back(ev);
+    cudaStream_t ss = nullptr;
+    cudaEvent_t e1 = nullptr, e2 = nullptr;
+    ok = ok && cudaStreamCreateWithFlags(&ss, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) b->side.push_back(ss);
+    ok = ok && cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) == cudaSuccess;
+    if (ok) b->sfork.push_back(e1);
+    ok = ok && cudaEventCreateWithFlags(&e2, cudaEventDisableTiming) == cudaSuccess;
+    if (ok) b->late.push_back(e2);
     cfdem_t c = nullptr;
     ok = ok && cfdem_create(&c, device, s) == CFDEM_OK;
     if (ok) b->beds.push_back(c);
@@ -148,6 +224,9 @@ cfdem_status cfdem_batch_destroy(cfdem_batch_t b) {
   for (cfdem_t c : b->beds) cfdem_destroy(c);
   for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
   for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+  for (cudaStream_t s : b->side) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->sfork) cudaEventDestroy(e);
+  for (cudaEvent_t e : b->late) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->in) cudaEventDestroy(b->in);
   if (b->out) cudaEventDestroy(b->out);
@@ -201,9 +280,10 @@ cfdem_status cfdem_batch_coupling_step(cfdem_batch_t b, const cfdem_bed_io* io) 
         if (gr) cudaGraphDestroy(gr);
         cudaGetLastError();  // the failed capture is not a sticky error
         if (cs == CFDEM_ESTATE) {
-          // a bed whose step cannot be captured (stage timers on, or a mixed
-          // solve without the fast-diagonalisation preconditioner): the
-          // eager results stand and this batch stays eager
+          // a bed whose step cannot be captured (stage timers on, a mixed
+          // solve without the fast-diagonalisation preconditioner, or host
+          // buffers that are not page-locked): the eager results stand and
+          // this batch stays eager
           b->use_graph = false;
         } else {
           if (cs == CFDEM_OK) return bfail(b, "end capture", e);

@@ -205,3 +205,57 @@ def test_empty_bed_in_a_batch():
         assert torch.count_nonzero(bufs[1]["Fe"]).item() == 0
     finally:
         cf.cfdem_batch_destroy(bh)
+
+
+def _host_copies(b, pinned):
+    import torch
+    n = b["x"].shape[0]
+    ne = int(np.prod(b["n_el"]))
+    src = {"x": b["x"], "r": b["r"], "u_p": b["u_p"], "u_nodal": b["u_nodal"],
+           "p_nodal": b["p_nodal"]}
+    h = {k: torch.as_tensor(np.ascontiguousarray(v, dtype=np.float64)) for k, v in src.items()}
+    h["f"] = torch.zeros((n, 3), dtype=torch.float64)
+    h["F_elem"] = torch.zeros((ne, 3), dtype=torch.float64)
+    if pinned:
+        h = {k: v.pin_memory() for k, v in h.items()}
+    return h
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_buffers_staged_inside_the_step(pinned):
+    """A batch step that starts and ends in host memory: x and r uploaded
+    first, u_p, u_nodal and p_nodal on a second stream beside the void
+    fraction and the projection, f and F_elem downloaded at the end.  The
+    results are those of device inputs; with page-locked buffers the copies
+    are captured and replayed with the step, with pageable ones the batch
+    stays eager."""
+    import torch
+    beds = _beds()[:3]
+    bufs = [_buffers(b) for b in beds]
+    refs = [_solo(b, t) for b, t in zip(beds, bufs)]
+    hosts = [_host_copies(b, pinned) for b in beds]
+    bh = _make_batch(beds)
+    try:
+        replayed = []
+        for it in range(3):
+            for t in bufs:  # the step itself must bring the inputs in
+                for k in ("x", "r", "u_p", "u", "p", "eps"):
+                    t[k].zero_()
+            for h in hosts:
+                h["f"].zero_()
+                h["F_elem"].zero_()
+            ios = [cf.bed_io(t["n"], t["x"], t["r"], t["u_p"], t["u"], t["p"], t["eps"],
+                             t["f"], t["fd"], t["Fe"], host=h) for t, h in zip(bufs, hosts)]
+            st = cf.cfdem_batch_coupling_step(bh, ios)
+            assert st == cf.OK, cf.cfdem_batch_last_error(bh)
+            st, bad = cf.cfdem_batch_synchronize(bh)
+            assert st == cf.OK and bad == -1
+            torch.cuda.synchronize()
+            replayed.append(cf.cfdem_batch_last_replayed(bh))
+            for h, ref in zip(hosts, refs):
+                assert np.array_equal(h["f"].numpy(), ref["f"])
+                assert rel_err(h["F_elem"].numpy(), ref["Fe"]) <= SAME
+            _check(bufs, refs)
+        assert replayed == ([0, 1, 1] if pinned else [0, 0, 0])
+    finally:
+        cf.cfdem_batch_destroy(bh)

@@ -46,7 +46,8 @@ int main(void) {
   P(cfdem_stats, stage_ms); P(cfdem_stats, kernel_launches); P(cfdem_stats, precond);
   printf("cfdem_bed_io %zu\n", sizeof(cfdem_bed_io));
   P(cfdem_bed_io, n); P(cfdem_bed_io, x); P(cfdem_bed_io, p_nodal); P(cfdem_bed_io, eps_nodal);
-  P(cfdem_bed_io, F_q);
+  P(cfdem_bed_io, F_q); P(cfdem_bed_io, host_x); P(cfdem_bed_io, host_p_nodal);
+  P(cfdem_bed_io, host_F_elem);
   printf("cfdem_dem_params %zu\n", sizeof(cfdem_dem_params));
   P(cfdem_dem_params, rolling_friction); P(cfdem_dem_params, wall_rolling_friction);
   P(cfdem_dem_params, g); P(cfdem_dem_params, hi); P(cfdem_dem_params, max_radius);
