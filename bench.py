@@ -775,9 +775,15 @@ def main():
         achieved = work / (per_launch_ms * 1e-3) / 1e9
         unit, peak_v = "GB/s", peaks.get("hbm_gbs", 6800.0)
     traffic = QCM_TRAFFIC_BYTES if dom == "void_fraction" else None
+    # what bounds the QCM kernel instead of its FMA rate (same ncu captures)
+    limiter = ("instruction issue: 72 % of issue slots active (ncu smsp__issue_active); "
+               "the per-element work is a filter of compares, ballots and queue appends, "
+               "whose instructions are not counted as algorithmic flops"
+               if dom == "void_fraction" else None)
     roof = {"bound": bound, "kernel": kname, "achieved": achieved, "peak": peak_v,
             "unit": unit, "frac": achieved / peak_v, "traffic": traffic,
             "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+            "limiter": limiter,
             "peak_source": ("measured FMA loop (profiles/alu_peaks_gb300.md)" if bound == "alu"
                             else "%s MEASURED_PEAKS.json hbm_gbs" % peak_kind),
             "launches_per_step": calls[dom], "ms_per_launch": per_launch_ms,
