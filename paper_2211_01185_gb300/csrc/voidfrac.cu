@@ -323,7 +323,7 @@ __device__ __forceinline__ void qcm_group(QcmSmem<K, FP64>& sm, const QcmWarp& w
 }
 
 template <int K, bool FP64>
-__global__ void __launch_bounds__(kQcmWarps * 32, 6)
+__global__ void __launch_bounds__(kQcmWarps * 32, FP64 ? 6 : 8)
 k_qcm(MeshDev m, QcmParams P, BinDev b, const int32_t* __restrict__ bin_start,
       const int32_t* __restrict__ perm, const double* __restrict__ xs64,
       const float* __restrict__ xs32, const DevStatus* __restrict__ st,
