@@ -41,7 +41,7 @@ FP64_TFLOPS = 1.197
 # 3.62 MB read -- the sorted particle copies and the bin table -- and no
 # write-back inside the launch (the 14 MB of eps stay in L2); to be cleared
 # whenever that kernel changes
-QCM_TRAFFIC_BYTES = 3622656 + 0
+QCM_TRAFFIC_BYTES = 3623168 + 0
 
 
 def _peaks():
@@ -776,7 +776,7 @@ def main():
         unit, peak_v = "GB/s", peaks.get("hbm_gbs", 6800.0)
     traffic = QCM_TRAFFIC_BYTES if dom == "void_fraction" else None
     # what bounds the QCM kernel instead of its FMA rate (same ncu captures)
-    limiter = ("instruction issue: 72 % of issue slots active (ncu smsp__issue_active); "
+    limiter = ("instruction issue: 77 % of issue slots active (ncu smsp__issue_active); "
                "the per-element work is a filter of compares, ballots and queue appends, "
                "whose instructions are not counted as algorithmic flops"
                if dom == "void_fraction" else None)
