@@ -738,7 +738,7 @@ def main():
     stages = {name: st_mx.stage_ms[i] / args.steps for i, name in enumerate(cf.STAGES)}
     calls = {name: st_mx.stage_calls[i] / args.steps for i, name in enumerate(cf.STAGES)}
     k = w["k"]
-    # algorithmic work per unit (stated in the design doc):
+    # algorithmic work per unit:
     #   operator: 7 banded 1D applies x (2k+1) taps x 2 flops + 5 = flops per node
     #   QCM: per neighbour pair 8 flops (distance) + 20 flops (lens volume)
     op_flops_node = 7 * (2 * k + 1) * 2 + 5
