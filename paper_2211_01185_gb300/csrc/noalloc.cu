@@ -8,6 +8,7 @@
 // output buffers.  Its per-element scratch (the
 // sum of particle volumes in each element) is the file-scope device array
 // g_pcm_volume below, so its size is fixed when the library is loaded.
+#include <cmath>
 #include <cstdint>
 #include <mutex>
 
@@ -22,7 +23,8 @@ namespace {
 static __device__ __align__(256) double g_pcm_volume[CFDEM_PCM_STATIC_MAX_ELEMS];
 // Status word the kernels write when a particle lies outside the mesh (the
 // entry point does not read it back; such particles are simply left out).
-static __device__ __align__(256) cfdem::DevStatus g_pcm_status;
+// first_bad starts at ~0 so that the kernels' atomicMin on it is well formed.
+static __device__ __align__(256) cfdem::DevStatus g_pcm_status = {~0ull, 0ull, 0, 0};
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
@@ -32,6 +34,8 @@ cfdem::DevStatus* g_status_ptr[kMaxDevices] = {};
 // Device addresses of the two arrays on the current device, looked up once
 // per device with that device current.  Their names in host code are only
 // host-side handles, so the addresses must come from cudaGetSymbolAddress.
+// The cache assumes the device is not reset (cudaDeviceReset) while the
+// process runs: a reset reloads the module and would leave stale addresses.
 cudaError_t scratch_addresses(int dev, double** vol, cfdem::DevStatus** st) {
   std::lock_guard<std::mutex> lock(g_mutex);
   if (!g_volume_ptr[dev]) {
@@ -62,7 +66,11 @@ extern "C" cfdem_status cfdem_pcm_void_fraction_static(const double origin[3],
     return CFDEM_EINVAL;
   MeshDev m{};
   for (int a = 0; a < 3; ++a) {
-    if (!(extent[a] > 0) || n_el[a] < 1) return CFDEM_EINVAL;
+    // the same checks as cfdem_set_mesh: finite box, 1..2^20 elements per
+    // axis (so the element count below cannot overflow)
+    if (!std::isfinite(origin[a]) || !std::isfinite(extent[a]) || !(extent[a] > 0))
+      return CFDEM_EINVAL;
+    if (n_el[a] < 1 || n_el[a] > (1 << 20)) return CFDEM_EINVAL;
     m.x0[a] = origin[a];
     m.L[a] = extent[a];
     m.ne[a] = n_el[a];

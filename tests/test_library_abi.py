@@ -83,3 +83,22 @@ def test_defaults_and_host_validation(lib):
     assert lib.cfdem_get_stats(None, None) == cf.EINVAL
     assert lib.cfdem_destroy(None) == cf.OK
     assert lib.cfdem_synchronize(None) == cf.EINVAL
+
+
+def test_static_pcm_rejects_bad_meshes_on_the_host(lib):
+    # Every case returns CFDEM_EINVAL from the host-side checks, before any
+    # CUDA call; the particle pointers are never dereferenced.
+    fake = 0x1000
+    good_o, good_e = (0.0, 0.0, 0.0), (1.0, 1.0, 1.0)
+    # 2^30 x 2^30 x 16 elements wraps a 64-bit element count to 0
+    assert cf.cfdem_pcm_void_fraction_static(good_o, good_e, (1 << 30, 1 << 30, 16), 1, 1,
+                                             fake, fake, fake) == cf.EINVAL
+    assert cf.cfdem_pcm_void_fraction_static(good_o, good_e, ((1 << 20) + 1, 1, 1), 1, 1,
+                                             fake, fake, fake) == cf.EINVAL
+    nan = float("nan")
+    assert cf.cfdem_pcm_void_fraction_static((nan, 0, 0), good_e, (4, 4, 4), 1, 1,
+                                             fake, fake, fake) == cf.EINVAL
+    assert cf.cfdem_pcm_void_fraction_static(good_o, (1.0, float("inf"), 1.0), (4, 4, 4), 1, 1,
+                                             fake, fake, fake) == cf.EINVAL
+    assert cf.cfdem_pcm_void_fraction_static(good_o, good_e, (4, 4, 4), 4, 1,
+                                             fake, fake, fake) == cf.EINVAL

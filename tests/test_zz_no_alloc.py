@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 from _parity import dev, host, rel_err
+from oracle import oracle as O
 from paper_2211_01185_gb300 import cfdem as cf
 from paper_2211_01185_gb300 import synth
 
@@ -49,6 +50,11 @@ def test_static_pcm_matches_context_pcm_twice(k):
         torch.cuda.synchronize()
         ref = _reference(c, x, r)
         assert rel_err(host(out), ref) <= 1e-10
+        # and directly against the FP64 oracle's particle-centroid scheme
+        mesh = O.Mesh(c["origin"], c["extent"], c["n_el"], k)
+        want, bad = O.pcm(mesh, c["x"], c["r"])
+        assert bad == -1                  # every particle lies in the mesh
+        assert rel_err(host(out), want) <= 1e-12
 
 
 def test_static_pcm_refuses_meshes_beyond_its_scratch():
