@@ -866,14 +866,24 @@ int64_t or_forces(const double *origin, const double *extent, const int *n_el, i
         lagrange(kp, zp, xi[0], px, dpx);
         lagrange(kp, zp, xi[1], py, dpy);
         lagrange(kp, zp, xi[2], pz, dpz);
+        /* grad p of the Q_kp interpolant.  Its derivative along an axis
+         * sees the nodal values only through their differences along that
+         * axis (the derivative of a constant is zero, so each dl sums to
+         * zero): d/dx = sum dl_a l_b l_c (p_abc - p_0bc) / h_x, and so on.
+         * Written with the differences, a pressure that varies along one
+         * axis only leaves the other two components exactly zero instead of
+         * the rounding of sum_a dl_a p. */
         double gp[3] = {0.0, 0.0, 0.0};
         for (int c = 0; c <= kp; ++c)
         for (int b = 0; b <= kp; ++b)
         for (int a = 0; a <= kp; ++a) {
             double pv = p_nodal[gnode(&m, kp, ie[0], ie[1], ie[2], a, b, c)];
-            gp[0] += dpx[a] / m.h[0] * py[b] * pz[c] * pv;
-            gp[1] += px[a] * dpy[b] / m.h[1] * pz[c] * pv;
-            gp[2] += px[a] * py[b] * dpz[c] / m.h[2] * pv;
+            double p0x = p_nodal[gnode(&m, kp, ie[0], ie[1], ie[2], 0, b, c)];
+            double p0y = p_nodal[gnode(&m, kp, ie[0], ie[1], ie[2], a, 0, c)];
+            double p0z = p_nodal[gnode(&m, kp, ie[0], ie[1], ie[2], a, b, 0)];
+            gp[0] += dpx[a] / m.h[0] * py[b] * pz[c] * (pv - p0x);
+            gp[1] += px[a] * dpy[b] / m.h[1] * pz[c] * (pv - p0y);
+            gp[2] += px[a] * py[b] * dpz[c] / m.h[2] * (pv - p0z);
         }
         double epsc = eps;
         if (epsc < eps_floor) epsc = eps_floor;

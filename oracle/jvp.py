@@ -201,6 +201,31 @@ def qcm_dual(mesh: O.Mesh, R, x: Dual, r):
     return 1.0 - V.sum(axis=1) / (4.0 / 3.0 * PI * R ** 3)
 
 
+def qcm_dual_rows(mesh: O.Mesh, R, x, r, dx):
+    """eps_q[E*Q] (dual) along a direction dx that moves few particles: the
+    value from the C oracle's cell-list QCM, the tangent from the moved
+    particles alone (the distances of every other pair do not change along
+    dx), each by brute force over every Gauss point.  Equal to qcm_dual up
+    to the order of the sums; usable on beds too large for all pairs."""
+    x = np.asarray(x, dtype=np.float64)
+    r = np.asarray(r, dtype=np.float64)
+    e, _, _ = O.qcm(mesh, R, x, r)
+    qp = O.quadrature_points(mesh).reshape(-1, 3)
+    t = np.zeros(qp.shape[0])
+    VR = 4.0 / 3.0 * PI * R ** 3
+    for i in np.nonzero(np.any(np.asarray(dx) != 0.0, axis=1))[0]:
+        d2 = Dual(np.zeros(qp.shape[0]))
+        for a in range(3):
+            da = Dual(x[i, a] - qp[:, a], np.full(qp.shape[0], dx[i, a]))
+            d2 = d2 + da * da
+        c = R + r[i]
+        inside = d2.v < c * c
+        d = sqrt(d2)
+        V = where(inside, lens_volume(R, np.full(qp.shape[0], r[i]), d), 0.0)
+        t -= V.t / VR
+    return Dual(e.reshape(-1), t)
+
+
 def _axis_locate(mesh, x, a):
     """element index (by value) and dual local coordinate along axis a"""
     h = mesh.h[a]
@@ -296,10 +321,15 @@ def forces_dual(mesh: O.Mesh, params: dict, x: Dual, r, u_p, u_nodal: Dual, p_no
     for c in range(kp + 1):
         for b in range(kp + 1):
             for a in range(kp + 1):
+                # the derivative along an axis from the nodal differences
+                # along it (as the C oracle)
                 pv = p_nodal[_gnode(mesh, kp, ie, a, b, c)]
-                gp[0] = gp[0] + P[0][1][a] / mesh.h[0] * P[1][0][b] * P[2][0][c] * pv
-                gp[1] = gp[1] + P[0][0][a] * P[1][1][b] / mesh.h[1] * P[2][0][c] * pv
-                gp[2] = gp[2] + P[0][0][a] * P[1][0][b] * P[2][1][c] / mesh.h[2] * pv
+                dx = pv - p_nodal[_gnode(mesh, kp, ie, 0, b, c)]
+                dy = pv - p_nodal[_gnode(mesh, kp, ie, a, 0, c)]
+                dz = pv - p_nodal[_gnode(mesh, kp, ie, a, b, 0)]
+                gp[0] = gp[0] + P[0][1][a] / mesh.h[0] * P[1][0][b] * P[2][0][c] * dx
+                gp[1] = gp[1] + P[0][0][a] * P[1][1][b] / mesh.h[1] * P[2][0][c] * dy
+                gp[2] = gp[2] + P[0][0][a] * P[1][0][b] * P[2][1][c] / mesh.h[2] * dz
     epsc = clamp(eps, floor, 1.0)
     U = [uf[c] - u_p[:, c] for c in range(3)]
     speed = sqrt(U[0] * U[0] + U[1] * U[1] + U[2] * U[2])
@@ -351,10 +381,13 @@ def forces_dual(mesh: O.Mesh, params: dict, x: Dual, r, u_p, u_nodal: Dual, p_no
     return out
 
 
-def coupling_jvp(mesh: O.Mesh, params: dict, x, r, u_p, u_nodal, p_nodal, dx=None, du=None):
+def coupling_jvp(mesh: O.Mesh, params: dict, x, r, u_p, u_nodal, p_nodal, dx=None, du=None,
+                 sparse_qcm=False):
     """Outputs of the coupling step (eps_h, f, f_drag, f_gradp) as dual
     numbers: values and derivatives along the input direction (dx on the
-    particle positions, du on the nodal fluid velocities)."""
+    particle positions, du on the nodal fluid velocities).  sparse_qcm: the
+    void fraction by qcm_dual_rows (for a dx that moves few particles of a
+    large bed) instead of all pairs."""
     x = np.asarray(x, dtype=np.float64)
     u_nodal = np.asarray(u_nodal, dtype=np.float64)
     X = Dual(x, np.zeros_like(x) if dx is None else dx)
@@ -362,7 +395,10 @@ def coupling_jvp(mesh: O.Mesh, params: dict, x, r, u_p, u_nodal, p_nodal, dx=Non
     L2 = float(params.get("l2_smoothing", 0.0))
     if params.get("scheme", 0) == 0:
         R = params.get("qcm_radius", 0.0) or O.default_qcm_radius(mesh)
-        eps_q = qcm_dual(mesh, R, X, r)
+        if sparse_qcm:
+            eps_q = qcm_dual_rows(mesh, R, x, r, X.t)
+        else:
+            eps_q = qcm_dual(mesh, R, X, r)
     else:
         # the particle-centroid void fraction is piecewise constant in x
         e, _ = O.pcm(mesh, x, r)
