@@ -1117,3 +1117,128 @@ void or_set_num_threads(int t)
     (void)t;
 #endif
 }
+
+/* ------------------------------------------------------------------ */
+/* Location on a mapped (isoparametric) Q_k hex mesh                   */
+/* ------------------------------------------------------------------ */
+
+/* The paper's beds sit in curved meshes (a subdivided cylinder, Secs. 3.1 and
+ * 3.2; a gmsh mesh of the spouted bed, Sec. 3.4), and particles are located
+ * on the fluid mesh itself (Sec. 2.3).  Element e maps the reference cube
+ * [0,1]^3 onto space by its Q_k nodes:
+ *   X_e(xi) = sum_{a,b,c} P[conn[e][a + (k+1)(b + (k+1) c)]] l_a(xi_0) l_b(xi_1) l_c(xi_2)
+ * with the GLL Lagrange basis l.  A point x lies in e when X_e(xi) = x for a
+ * xi in the cube.  The oracle tries the candidate elements -- those whose
+ * node box, widened on every side by `margin` times its largest edge,
+ * contains x -- in ascending index, each by Newton's method
+ *   xi <- xi - J(xi)^-1 (X_e(xi) - x),   J = dX_e / dxi,
+ * from the cube's centre: at most 50 steps, converged once the largest step
+ * component is at most 1e-13, abandoned once xi leaves [-3, 4]^3 or J is
+ * singular.  The first candidate whose converged xi lies in [-1e-10,
+ * 1 + 1e-10]^3 is the element, and xi is clamped to [0,1]^3; a point in no
+ * element gets elem = -1, xi = 0.  Returns the number of such points. */
+
+static void mapped_box(int k, const int32_t *conn, const double *nodes, int64_t e,
+                       double margin, double *lo, double *hi)
+{
+    int nloc = (k + 1) * (k + 1) * (k + 1);
+    for (int a = 0; a < 3; ++a) { lo[a] = INFINITY; hi[a] = -INFINITY; }
+    for (int j = 0; j < nloc; ++j) {
+        const double *P = nodes + 3 * (int64_t)conn[e * nloc + j];
+        for (int a = 0; a < 3; ++a) {
+            if (P[a] < lo[a]) lo[a] = P[a];
+            if (P[a] > hi[a]) hi[a] = P[a];
+        }
+    }
+    double side = 0.0;
+    for (int a = 0; a < 3; ++a) if (hi[a] - lo[a] > side) side = hi[a] - lo[a];
+    double w = margin * side;
+    for (int a = 0; a < 3; ++a) { lo[a] -= w; hi[a] += w; }
+}
+
+/* Newton inversion of X_e at x; returns 1 and xi in the widened cube, else 0 */
+static int mapped_newton(int k, const double *z, const int32_t *conn, const double *nodes,
+                         int64_t e, const double *x, double *xi_out)
+{
+    int nq = k + 1, nloc = nq * nq * nq;
+    double xi[3] = {0.5, 0.5, 0.5};
+    for (int it = 0; it < 50; ++it) {
+        double l[3][4], dl[3][4];
+        for (int a = 0; a < 3; ++a) lagrange(k, z, xi[a], l[a], dl[a]);
+        double X[3] = {0.0, 0.0, 0.0}, J[3][3] = {{0.0}};   /* J[i][a] = dX_i/dxi_a */
+        for (int c = 0; c < nq; ++c)
+        for (int b = 0; b < nq; ++b)
+        for (int a = 0; a < nq; ++a) {
+            const double *P = nodes + 3 * (int64_t)conn[e * nloc + a + nq * (b + nq * c)];
+            double w = l[0][a] * l[1][b] * l[2][c];
+            double w0 = dl[0][a] * l[1][b] * l[2][c];
+            double w1 = l[0][a] * dl[1][b] * l[2][c];
+            double w2 = l[0][a] * l[1][b] * dl[2][c];
+            for (int i = 0; i < 3; ++i) {
+                X[i] += w * P[i];
+                J[i][0] += w0 * P[i];
+                J[i][1] += w1 * P[i];
+                J[i][2] += w2 * P[i];
+            }
+        }
+        double r[3] = {X[0] - x[0], X[1] - x[1], X[2] - x[2]};
+        /* J d = r by Cramer's rule */
+        double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1])
+                   - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0])
+                   + J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+        if (!(fabs(det) > 0.0)) return 0;
+        double d[3];
+        for (int col = 0; col < 3; ++col) {
+            double M[3][3];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) M[i][j] = (j == col) ? r[i] : J[i][j];
+            double dm = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1])
+                      - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0])
+                      + M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+            d[col] = dm / det;
+        }
+        double big = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            xi[a] -= d[a];
+            if (fabs(d[a]) > big) big = fabs(d[a]);
+            if (!(xi[a] >= -3.0 && xi[a] <= 4.0)) return 0;
+        }
+        if (big <= 1e-13) {
+            for (int a = 0; a < 3; ++a)
+                if (!(xi[a] >= -1e-10 && xi[a] <= 1.0 + 1e-10)) return 0;
+            for (int a = 0; a < 3; ++a)
+                xi_out[a] = xi[a] < 0.0 ? 0.0 : (xi[a] > 1.0 ? 1.0 : xi[a]);
+            return 1;
+        }
+    }
+    return 0;
+}
+
+int64_t or_locate_mapped(int k, int64_t E, const int32_t *conn, const double *nodes,
+                         double margin, int64_t n, const double *x, int32_t *elem, double *xi)
+{
+    double z[8];
+    or_gll_nodes(k, z);
+    double *box = (double *)malloc(sizeof(double) * 6 * (E > 0 ? E : 1));
+    for (int64_t e = 0; e < E; ++e) mapped_box(k, conn, nodes, e, margin, box + 6 * e, box + 6 * e + 3);
+    int64_t missing = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : missing)
+    for (int64_t i = 0; i < n; ++i) {
+        const double *p = x + 3 * i;
+        elem[i] = -1;
+        xi[3 * i] = xi[3 * i + 1] = xi[3 * i + 2] = 0.0;
+        for (int64_t e = 0; e < E; ++e) {
+            const double *lo = box + 6 * e, *hi = lo + 3;
+            if (!(p[0] >= lo[0] && p[0] <= hi[0] && p[1] >= lo[1] && p[1] <= hi[1] &&
+                  p[2] >= lo[2] && p[2] <= hi[2]))
+                continue;
+            if (mapped_newton(k, z, conn, nodes, e, p, xi + 3 * i)) {
+                elem[i] = (int32_t)e;
+                break;
+            }
+        }
+        if (elem[i] < 0) ++missing;
+    }
+    free(box);
+    return missing;
+}

@@ -101,6 +101,8 @@ def lib():
                                                dp, dp, dp]
             L.or_fluid_source_semi.restype = i64
             L.or_fluid_source.restype = i64
+            L.or_locate_mapped.argtypes = [cint, i64, ip, dp, dbl, i64, dp, ip, dp]
+            L.or_locate_mapped.restype = i64
             L.or_num_threads.restype = cint
             L.or_set_num_threads.argtypes = [cint]
             _lib = L
@@ -584,6 +586,24 @@ def coupling_step(mesh: Mesh, params: dict, x, r, u_p, u_nodal, p_nodal, eps0=No
     else:
         out["F_e"], _ = fluid_source(mesh, vans, x, fo["f_drag"], fo["f_gradp"], fo.get("f_shear"))
     return out
+
+
+def locate_mapped(k, conn, nodes, x, margin=0.1):
+    """Element and reference coordinates of each point on a mapped Q_k hex
+    mesh (conn[E][(k+1)^3] node indices, a fastest; nodes[N][3]) by Newton
+    inversion of the element maps (see or_locate_mapped); returns (elem,
+    xi, number of points in no element)."""
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    nodes, pn = _d(nodes)
+    x, px = _d(x)
+    n = x.shape[0]
+    elem = np.zeros(n, dtype=np.int32)
+    xi = np.zeros((n, 3))
+    miss = lib().or_locate_mapped(int(k), conn.shape[0], conn.ctypes.data_as(C.POINTER(C.c_int32)),
+                                  pn, float(margin), n, px,
+                                  elem.ctypes.data_as(C.POINTER(C.c_int32)),
+                                  xi.ctypes.data_as(C.POINTER(C.c_double)))
+    return elem, xi, int(miss)
 
 
 def num_threads():

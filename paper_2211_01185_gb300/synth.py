@@ -253,7 +253,7 @@ def make_batch_workload(n_beds: int = 64, seed: int | None = None, n_range=(5_00
     return beds
 
 
-def make_adjoint_workload(seed: int | None = None) -> dict:
+def make_adjoint_workload(seed: int | None = None, n_el=(24, 24, 96)) -> dict:
     """The sensitivity workload: a 0.096 x 0.096 x 0.384 m box of 24 x 24 x 96
     Q2 elements (h = 4 mm, averaging radius 2.481 mm), 200,000 spheres of
     d = 2 mm from the floor up -- an annulus at solid fraction 0.5 on a
@@ -261,9 +261,12 @@ def make_adjoint_workload(seed: int | None = None) -> dict:
     column of radius 0.15 L_x, lower half, at 0.05 by random sequential
     addition -- under a jet u_z = 0.2 + 1.8 (1 - tanh((rho - 0.15
     L_x) / (0.02 L_x))) / 2 m/s (rho the distance from the axis).  The loss
-    of this workload is J = sum_i e_z . f_D,i + ||eps_h||_M."""
+    of this workload is J = sum_i e_z . f_D,i + ||eps_h||_M.
+    A smaller n_el keeps h = 4 mm and the layout relative to the box and
+    scales the particle count with the element count."""
     rng = np.random.default_rng(SEED0 + 5 if seed is None else seed)
-    n_el, k, d = (24, 24, 96), 2, 2e-3
+    n_el, k, d = tuple(int(v) for v in n_el), 2, 2e-3
+    n_total = int(round(200_000 * (n_el[0] * n_el[1] * n_el[2]) / (24 * 24 * 96)))
     h = 4e-3
     extent = (n_el[0] * h, n_el[1] * h, n_el[2] * h)
     Lx = extent[0]
@@ -286,7 +289,7 @@ def make_adjoint_workload(seed: int | None = None) -> dict:
     ncol = int(round(0.05 * vcol / (math.pi * d ** 3 / 6.0)))
     # the lowest annulus sites up to N = 200,000 in all (the lattice, cut by
     # the walls, holds a little less than that below half height)
-    sites = sites[np.lexsort((sites[:, 0], sites[:, 1], sites[:, 2]))][:200_000 - ncol]
+    sites = sites[np.lexsort((sites[:, 0], sites[:, 1], sites[:, 2]))][:n_total - ncol]
     jit = 0.5 * (a_nn - d)
     u = rng.normal(size=sites.shape)
     u /= np.linalg.norm(u, axis=1)[:, None]
@@ -322,7 +325,10 @@ def make_adjoint_workload(seed: int | None = None) -> dict:
     u_p = 0.1 * rng.random((n, 3)) - 0.05
     params = gas_params(d, k)
     del spec, cand
-    return dict(name="adjoint_24x24x96_200k", origin=(0.0, 0.0, 0.0), extent=extent, n_el=n_el,
+    name = "adjoint_%dx%dx%d_%d" % (n_el + (n,))
+    if n_el == (24, 24, 96):
+        name = "adjoint_24x24x96_200k"
+    return dict(name=name, origin=(0.0, 0.0, 0.0), extent=extent, n_el=n_el,
                 k=k, x=x, r=r, u_p=u_p, u_nodal=np.ascontiguousarray(un), p_nodal=p,
                 params=params)
 
@@ -347,3 +353,80 @@ def make_random_case(seed: int, n_el=(3, 4, 5), k=2, n=150, extent=(0.03, 0.04, 
     return dict(name="random%d" % seed, origin=tuple(origin), extent=tuple(extent),
                 n_el=tuple(n_el), k=k, x=np.ascontiguousarray(x), r=np.ascontiguousarray(r),
                 u_p=u_p, u_nodal=u, p_nodal=p, params=params)
+
+
+# --------------------------------------------------------------- mapped meshes
+
+def _merge_nodes(pts, scale):
+    """Global node numbering of element-local node coordinates: points that
+    coincide (to 1e-9 of the mesh size) share a node."""
+    key = np.round(pts / (1e-9 * scale)).astype(np.int64)
+    uniq, inv = np.unique(key, axis=0, return_inverse=True)
+    nodes = np.zeros((uniq.shape[0], 3))
+    nodes[inv.ravel()] = pts
+    return nodes, inv.ravel().astype(np.int32)
+
+
+def make_box_mapped_mesh(origin, extent, n_el, k):
+    """An axis-aligned box of equal Q_k hex elements written as a mapped mesh
+    (conn[E][(k+1)^3] with the local index a + (k+1)(b + (k+1)c), element
+    index ex + nx (ey + ny ez), and node coordinates), for the location on
+    mapped meshes to be compared with the box's own location."""
+    z = np.asarray(_GLL[k])
+    o = np.asarray(origin, dtype=np.float64)
+    h = np.asarray(extent, dtype=np.float64) / np.asarray(n_el)
+    pts = []
+    for ez in range(n_el[2]):
+        for ey in range(n_el[1]):
+            for ex in range(n_el[0]):
+                C, B, A = np.meshgrid(z, z, z, indexing="ij")
+                loc = np.stack([o[0] + h[0] * (ex + A.ravel()), o[1] + h[1] * (ey + B.ravel()),
+                                o[2] + h[2] * (ez + C.ravel())], axis=1)
+                pts.append(loc)
+    pts = np.concatenate(pts)
+    nodes, inv = _merge_nodes(pts, float(np.max(extent)))
+    return dict(k=k, conn=inv.reshape(-1, (k + 1) ** 3), nodes=nodes)
+
+
+def make_cylinder_mesh(radius, height, n_core, n_ring, n_z, k, origin=(0.0, 0.0, 0.0)):
+    """A subdivided cylinder (the mesh type of the paper's sedimentation and
+    fluidised-bed cases) of Q_k hex elements: in the cross-section a square
+    core of side radius/sqrt(2) (n_core x n_core elements) and four blocks
+    between the square's sides and the circle (n_core tangential x n_ring
+    radial elements), each point of a block on the straight line from the
+    square's side to the arc at the same tangential fraction; n_z layers
+    along z.  Nodes at the GLL points of each element's reference
+    coordinates, so the ring elements are curved.  Returns conn[E][(k+1)^3]
+    (a fastest, right-handed reference axes) and nodes[N][3]."""
+    z = np.asarray(_GLL[k])
+    R = float(radius)
+    a = R / math.sqrt(2.0) * 0.5
+    o = np.asarray(origin, dtype=np.float64)
+    C, B, A = np.meshgrid(z, z, z, indexing="ij")
+    s, t, w = A.ravel(), B.ravel(), C.ravel()
+    pts = []
+
+    def rot(xy, q):
+        c, sn = math.cos(q * math.pi / 2), math.sin(q * math.pi / 2)
+        return np.stack([c * xy[:, 0] - sn * xy[:, 1], sn * xy[:, 0] + c * xy[:, 1]], axis=1)
+
+    for lz in range(n_z):
+        zz = o[2] + height * (lz + w) / n_z
+        for j in range(n_core):          # core
+            for i in range(n_core):
+                x = -a + 2 * a * (i + s) / n_core
+                y = -a + 2 * a * (j + t) / n_core
+                pts.append(np.stack([o[0] + x, o[1] + y, zz], axis=1))
+        for q in range(4):               # ring blocks, the first one on the +x side
+            for j in range(n_core):      # tangential
+                for i in range(n_ring):  # radial
+                    v = (i + s) / n_ring
+                    u = (j + t) / n_core
+                    side = np.stack([np.full_like(u, a), -a + 2 * a * u], axis=1)
+                    th = -math.pi / 4 + math.pi / 2 * u
+                    arc = np.stack([R * np.cos(th), R * np.sin(th)], axis=1)
+                    xy = rot((1.0 - v)[:, None] * side + v[:, None] * arc, q)
+                    pts.append(np.stack([o[0] + xy[:, 0], o[1] + xy[:, 1], zz], axis=1))
+    pts = np.concatenate(pts)
+    nodes, inv = _merge_nodes(pts, max(R, height))
+    return dict(k=k, conn=inv.reshape(-1, (k + 1) ** 3), nodes=nodes, radius=R, height=height)
