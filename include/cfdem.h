@@ -95,6 +95,19 @@ typedef struct {
                               mesh, so that sum_q w_q |J| (1 - eps_q) = sum_i V_p,i also
                               where averaging spheres cross the walls; not supported by
                               cfdem_adjoint (CFDEM_EINVAL); default 0 */
+    int autotune;          /* 1 => the first eager step of a new signature (mesh, degree,
+                              precision, particle count within a factor of two, largest
+                              radius) times a few bin edges of the QCM's particle bins
+                              (fractions of R + max_radius, and h / m so that bins nest in
+                              elements) and the three tile shapes of the projection
+                              operator, and keeps the fastest for the context (and for
+                              later contexts of the same signature in the process).
+                              Results do not depend on the choice beyond the order of
+                              floating-point sums (neighbour sets are the same).  The
+                              timing synchronises the stream, once per signature; nothing
+                              is timed while the stream is being captured.  0 => bins of
+                              edge R + max_radius and the shape of a static cost model.
+                              bin_edge > 0 fixes the bins either way.  Default 1. */
 } cfdem_params;
 
 /* Counters of the last calls on a context. */
@@ -118,6 +131,10 @@ typedef struct {
     int32_t timer_overflow;       /* 1 if more than 1024 pairs per stage were asked */
     int64_t kernel_launches;      /* kernels launched by the library since set_timing */
     int32_t precond;              /* preconditioner in use: 0 Jacobi, 1 FDM */
+    int32_t tile_shape;           /* operator tile in use: 0 16x8x8, 1 22x13x4, 2 25x15x4 nodes */
+    int32_t tuned;                /* bit 0: bins chosen by timing, bit 1: tile shape chosen by
+                                     timing (autotune) */
+    double tune_ms;               /* host time spent timing candidates in this context */
 } cfdem_stats;
 
 /* Create a context on CUDA device `device`, ordering all work on `stream`
@@ -379,6 +396,50 @@ const char *cfdem_last_error(cfdem_t ctx);
 
 /* Library version string. */
 const char *cfdem_version(void);
+
+/* --------------------------------------------------- mapped (curved) meshes */
+
+/* Particle location on a mapped Q_k hex mesh.  The paper's beds sit in
+ * curved meshes (a subdivided cylinder, Secs. 3.1 and 3.2; a gmsh mesh,
+ * Sec. 3.4), and particles are located on the fluid mesh itself (Sec. 2.3).
+ * Element e maps the reference cube [0,1]^3 by its Q_k nodes (GLL points):
+ * X_e(xi) = sum_{a,b,c} P[conn[e][a + (k+1)(b + (k+1) c)]] l_a(xi_0) l_b(xi_1)
+ * l_c(xi_2); x lies in e when X_e(xi) = x for a xi in the cube.  The box
+ * mesh entry points above are the special case of an axis-aligned box. */
+typedef struct cfdem_mapped *cfdem_mapped_t;
+
+/* Copy a mapped mesh to `device`: degree 1..3, n_elem elements, conn[n_elem]
+ * [(degree+1)^3] node indices (host, a fastest; right-handed reference axes
+ * with positive Jacobian), nodes[n_nodes][3] coordinates (host).  Each
+ * element's candidate box is its nodes' box widened on every side by
+ * `margin` (in [0, 1]) times its largest edge (0.1 covers the bulge of
+ * curved Q2/Q3 faces beyond their nodes).  CFDEM_EINVAL on a bad argument
+ * (an index outside [0, n_nodes), a non-finite coordinate), CFDEM_ECUDA /
+ * CFDEM_ENOMEM on device failures.  Host arrays are not kept. */
+cfdem_status cfdem_mapped_create(cfdem_mapped_t *out, int device, int degree, int64_t n_elem,
+                                 const int32_t *conn, int64_t n_nodes, const double *nodes,
+                                 double margin);
+cfdem_status cfdem_mapped_destroy(cfdem_mapped_t mesh);
+
+/* Element elem_dev[n] and reference coordinates xi_dev[n][3] (may be NULL)
+ * of each particle x_dev[n][3] (device arrays): the elements whose candidate
+ * box contains the particle are tried in ascending index by Newton's method
+ * on X_e(xi) = x from the cube's centre (FP64, at most 50 steps, converged at
+ * a step of at most 1e-13, abandoned once xi leaves [-3, 4]^3 or the
+ * Jacobian is singular); the first whose xi lies in [-1e-10, 1 + 1e-10]^3
+ * is the element, xi clamped to [0,1]^3.  A particle in no element gets
+ * elem = -1 and xi = 0 (not an error).  Stream ordered on `stream` (a
+ * cudaStream_t, NULL = legacy default). */
+cfdem_status cfdem_mapped_locate(cfdem_mapped_t mesh, int64_t n, const double *x_dev,
+                                 int32_t *elem_dev, double *xi_dev, void *stream);
+
+/* out_dev[n][ncomp] = the Q_k interpolant of the nodal field field_dev
+ * [n_nodes][ncomp] at (elem_dev[i], xi_dev[i]) (0 where elem < 0), e.g. the
+ * fluid velocity at the particles located by cfdem_mapped_locate; ncomp in
+ * 1..64.  Device arrays, stream ordered. */
+cfdem_status cfdem_mapped_interpolate(cfdem_mapped_t mesh, int64_t n, const int32_t *elem_dev,
+                                      const double *xi_dev, int ncomp, const double *field_dev,
+                                      double *out_dev, void *stream);
 
 /* ------------------------------------------------------------------ DEM */
 

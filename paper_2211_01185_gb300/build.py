@@ -18,6 +18,9 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libcfdem.so")
+# the FMA throughput probe the benchmark measures its ALU rooflines with
+PROBE_SRC = os.path.join(CSRC, "probe", "alu_peak.cu")
+PROBE_LIB = os.path.join(LIBDIR, "libalupeak.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(HERE, "..", "include")]
@@ -58,6 +61,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if p.returncode != 0:
             raise RuntimeError("nvcc failed:\n%s\n%s" % (" ".join(cmd), p.stderr[-8000:]))
         return p.stderr
+
+    if force or _stale(PROBE_LIB, [PROBE_SRC]):
+        jobs.append([nvcc] + ARCH + FLAGS + ["-shared", "-cudart", "shared", PROBE_SRC, "-o",
+                                             PROBE_LIB])
 
     with ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
         for msg in ex.map(run, jobs):

@@ -46,7 +46,8 @@ class cfdem_params(C.Structure):
                 ("precision", C.c_int), ("cg_rtol", C.c_double), ("cg_maxit", C.c_int),
                 ("eps_floor", C.c_double), ("pressure_degree", C.c_int),
                 ("max_radius", C.c_double), ("bin_edge", C.c_double),
-                ("cg_precond", C.c_int), ("shear_force", C.c_int), ("fluid_drag", C.c_int), ("qcm_conserve", C.c_int)]
+                ("cg_precond", C.c_int), ("shear_force", C.c_int), ("fluid_drag", C.c_int),
+                ("qcm_conserve", C.c_int), ("autotune", C.c_int)]
 
 
 class cfdem_stats(C.Structure):
@@ -56,7 +57,8 @@ class cfdem_stats(C.Structure):
                 ("n_elem", C.c_int64), ("n_qp", C.c_int64), ("n_nodes", C.c_int64),
                 ("n_pnodes", C.c_int64), ("stage_ms", C.c_double * 8),
                 ("stage_calls", C.c_int64 * 8), ("timer_overflow", C.c_int32),
-                ("kernel_launches", C.c_int64), ("precond", C.c_int32)]
+                ("kernel_launches", C.c_int64), ("precond", C.c_int32),
+                ("tile_shape", C.c_int32), ("tuned", C.c_int32), ("tune_ms", C.c_double)]
 
 class cfdem_bed_io(C.Structure):
     _fields_ = [("n", C.c_int64), ("x", C.c_void_p), ("r", C.c_void_p), ("u_p", C.c_void_p),
@@ -139,6 +141,10 @@ def lib():
     L.cfdem_batch_last_replayed.argtypes = [vp]
     L.cfdem_batch_last_error.argtypes = [vp]
     L.cfdem_batch_last_error.restype = C.c_char_p
+    L.cfdem_mapped_create.argtypes = [C.POINTER(vp), cint, cint, i64, vp, i64, vp, dbl]
+    L.cfdem_mapped_destroy.argtypes = [vp]
+    L.cfdem_mapped_locate.argtypes = [vp, i64, vp, vp, vp, vp]
+    L.cfdem_mapped_interpolate.argtypes = [vp, i64, vp, vp, cint, vp, vp, vp]
     L.cfdem_last_error.argtypes = [vp]
     L.cfdem_last_error.restype = C.c_char_p
     _lib = L
@@ -403,6 +409,44 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------ mapped meshes
+
+class MappedMesh:
+    """A mapped (curved) Q_k hex mesh on the device (cfdem_mapped_*):
+    conn[E][(k+1)^3] and nodes[N][3] as numpy arrays."""
+
+    def __init__(self, k, conn, nodes, margin=0.1, device=0):
+        import numpy as np
+        conn = np.ascontiguousarray(conn, dtype=np.int32)
+        nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+        h = C.c_void_p()
+        st = lib().cfdem_mapped_create(C.byref(h), int(device), int(k), conn.shape[0],
+                                       conn.ctypes.data, nodes.shape[0], nodes.ctypes.data,
+                                       float(margin))
+        if st != OK:
+            raise CfdemError(st, "cfdem_mapped_create failed")
+        self.h = h
+
+    def locate(self, n, x, elem, xi=None, stream=None):
+        return lib().cfdem_mapped_locate(self.h, int(n), _ptr(x), _ptr(elem), _ptr(xi),
+                                         C.c_void_p(stream or 0))
+
+    def interpolate(self, n, elem, xi, ncomp, field, out, stream=None):
+        return lib().cfdem_mapped_interpolate(self.h, int(n), _ptr(elem), _ptr(xi), int(ncomp),
+                                              _ptr(field), _ptr(out), C.c_void_p(stream or 0))
+
+    def close(self):
+        if self.h:
+            lib().cfdem_mapped_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 # ------------------------------------------------------------------ DEM

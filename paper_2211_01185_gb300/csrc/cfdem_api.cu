@@ -4,6 +4,9 @@
 // parameters, the bin grid, the scratch arenas (grown on demand) and the
 // device status words.  Every call is ordered on the context's stream.
 #include <atomic>
+#include <chrono>
+#include <mutex>
+#include <vector>
 #include <cfloat>
 #include <cmath>
 #include <cstdarg>
@@ -102,6 +105,14 @@ cfdem_status cuda_fail(cfdem_t c, cudaError_t e, const char* where) {
 }
 
 // the force kernels' parameters from the context's parameters and mesh
+// the integer key of a double whose signed order is the order of the values
+// (the same map the device applies to a particle coordinate)
+long long order_key(double v) {
+  long long b;
+  std::memcpy(&b, &v, sizeof b);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+
 ForceParams force_params(const cfdem_ctx* c) {
   ForceParams fp{};
   fp.rho = c->prm.rho_f;
@@ -116,6 +127,29 @@ ForceParams force_params(const cfdem_ctx* c) {
   fp.vans_model = c->prm.vans_model;
   fp.shear = c->prm.shear_force;
   fp.fluid_drag = c->prm.fluid_drag;
+  fp.rho32 = (float)fp.rho;
+  fp.mu32 = (float)fp.mu;
+  fp.eps_floor32 = (float)fp.eps_floor;
+  double far = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    const MeshDev& m = c->mesh;
+    fp.g32[a] = (float)fp.g[a];
+    fp.inv_h32[a] = (float)fp.inv_h[a];
+    fp.x0_hi[a] = (float)m.x0[a];
+    fp.x0_lo[a] = (float)(m.x0[a] - (double)fp.x0_hi[a]);
+    fp.inv_h_hi[a] = (float)fp.inv_h[a];
+    fp.inv_h_lo[a] = (float)(fp.inv_h[a] - (double)fp.inv_h_hi[a]);
+    // the bounds of in_box, rounded as the device rounds them
+    volatile double slack = 1e-12 * m.L[a];
+    volatile double top = m.x0[a] + m.L[a];
+    const double lo = m.x0[a] - slack, hi = top + slack;
+    fp.box_lo_key[a] = order_key(lo);
+    fp.box_hi_key[a] = order_key(hi);
+    far = std::fmax(far, (std::fabs(m.x0[a]) + m.L[a]) * fp.inv_h[a]);
+  }
+  // the double-float location is accurate to ~2^-46 (|x| / h); with its
+  // 1e-5 margin around element faces it holds while |x| / h < 2^26
+  fp.loc32 = far < 67108864.0 ? 1 : 0;
   return fp;
 }
 
@@ -224,6 +258,14 @@ void build_tables(int k, int kp, Tables* t) {
   gll_closed_form(kp, t->zp);
   bary_weights(k, t->z, t->lw);
   bary_weights(kp, t->zp, t->lwp);
+  for (int a = 0; a < 4; ++a) {
+    t->zf[a] = (float)t->z[a];
+    t->zpf[a] = (float)t->zp[a];
+    t->lwf[a] = (float)t->lw[a];
+    t->lwpf[a] = (float)t->lwp[a];
+    t->z_lo[a] = (float)(t->z[a] - (double)t->zf[a]);
+    t->lw_lo[a] = (float)(t->lw[a] - (double)t->lwf[a]);
+  }
   double l[4][4], dl[4][4];  // [q][a]
   for (int q = 0; q < nq; ++q) lagr(k, t->z, t->lw, t->g[q], l[q], dl[q]);
   for (int a = 0; a <= k; ++a)
@@ -243,6 +285,39 @@ void build_tables(int k, int kp, Tables* t) {
 
 bool is_finite_d(double v) { return std::isfinite(v); }
 
+// the bin grid of edge ~edge over the box: floor(L / edge) bins per axis
+// (at least one), coarsened by 1.5 until at most 2^26 bins
+BinDev bin_grid(const MeshDev& m, double edge) {
+  BinDev b{};
+  for (;;) {
+    int64_t tot = 1;
+    for (int a = 0; a < 3; ++a) {
+      double f = std::floor(m.L[a] / edge);
+      int nb = f < 1.0 ? 1 : (f > 1e6 ? 1000000 : (int)f);
+      b.nb[a] = nb;
+      b.be[a] = m.L[a] / nb;
+      b.inv_be[a] = 1.0 / b.be[a];
+      tot *= nb;
+    }
+    b.nbins = tot;
+    if (tot <= (int64_t)1 << 26) break;
+    edge *= 1.5;
+  }
+  return b;
+}
+
+// room for the bin counts and starts of the current grid
+cfdem_status ensure_bins(cfdem_t c) {
+  if (c->bins.nbins + 1 > c->cap_bins) {
+    int64_t nb = c->bins.nbins + 1;
+    CK(grow(&c->bin_count, nb), "bins");
+    CK(grow(&c->bin_start, nb), "bins");
+    CK(grow(&c->scan_tmp, nb / 2048 + 2), "bins");
+    c->cap_bins = nb;
+  }
+  return CFDEM_OK;
+}
+
 // resolve R, kp, coefficients and the bin grid once mesh and params exist
 cfdem_status resolve(cfdem_t c) {
   if (!c->have_mesh) return CFDEM_OK;
@@ -261,20 +336,11 @@ cfdem_status resolve(cfdem_t c) {
   c->coef[2] = L2 * m.h[0] * m.h[2] / m.h[1];
   c->coef[3] = L2 * m.h[0] * m.h[1] / m.h[2];
   double edge = p.bin_edge > 0 ? p.bin_edge : c->R + (p.max_radius > 0 ? p.max_radius : c->R);
-  for (;;) {
-    int64_t tot = 1;
-    for (int a = 0; a < 3; ++a) {
-      double f = std::floor(m.L[a] / edge);
-      int nb = f < 1.0 ? 1 : (f > 1e6 ? 1000000 : (int)f);
-      c->bins.nb[a] = nb;
-      c->bins.be[a] = m.L[a] / nb;
-      c->bins.inv_be[a] = 1.0 / c->bins.be[a];
-      tot *= nb;
-    }
-    c->bins.nbins = tot;
-    if (tot <= (int64_t)1 << 26) break;
-    edge *= 1.5;
-  }
+  c->bins = bin_grid(m, edge);
+  c->bin_key_set = false;
+  c->shape_key_set = false;
+  c->tuned = 0;
+  m.shape = pick_shape(m);
   DeviceGuard g(c->device);
   CK(upload_bands(m, c->tab, L2, &c->bands64, &c->bands32, &c->bandsdf), "upload_bands");
   c->cg.bands_df = reinterpret_cast<const df64*>(c->bandsdf);
@@ -290,13 +356,8 @@ cfdem_status resolve(cfdem_t c) {
     if (!c->fdm) c->fdm_note = why ? why : "FDM unavailable";
   }
   c->cg.fdm = c->fdm;
-  if (c->bins.nbins + 1 > c->cap_bins) {
-    int64_t nb = c->bins.nbins + 1;
-    CK(grow(&c->bin_count, nb), "bins");
-    CK(grow(&c->bin_start, nb), "bins");
-    CK(grow(&c->scan_tmp, nb / 2048 + 2), "bins");
-    c->cap_bins = nb;
-  }
+  cfdem_status s = ensure_bins(c);
+  if (s != CFDEM_OK) return s;
   c->eps_state = 0;
   return CFDEM_OK;
 }
@@ -310,6 +371,8 @@ cfdem_status ensure_particles(cfdem_t c, int64_t n) {
   CK(grow(&c->xs64, 4 * cap), "particle arena");
   CK(grow(&c->xs32, 8 * cap), "particle arena");
   CK(grow(&c->qcm_w, 2 * cap), "particle arena");
+  CK(grow(&c->psrc, 4 * cap), "particle arena");
+  CK(grow(&c->pelem, cap), "particle arena");
   c->cap_n = cap;
   return CFDEM_OK;
 }
@@ -320,9 +383,12 @@ void free_mesh_arena(cfdem_t c) {
                 c->cg.q0, c->cg.q1, c->cg.Aq, c->cg.dinv32, c->cg.d32, c->cg.partials,
                 c->cg.sc, c->cg.zn, c->cg.zn32, c->cg.rin32, c->cg.x_df, c->cg.r_df,
                 c->cg.b_df, c->cg.Ap_df, c->cg.p0_df, c->cg.p1_df, c->adj_geps,
-                c->adj_lam, c->adj_gq, c->rhs_local, c->semi};
+                c->adj_lam, c->adj_gq, c->rhs_local, c->semi, c->tune_x, c->src_acc,
+                c->src_max};
   for (void* p : ps)
     if (p) cudaFree(p);
+  c->tune_x = nullptr;
+  c->shape_key_set = false;
   c->eps64 = nullptr;
   c->eps32 = nullptr;
   c->b = nullptr;
@@ -331,6 +397,8 @@ void free_mesh_arena(cfdem_t c) {
   c->adj_geps = c->adj_lam = c->adj_gq = nullptr;
   c->rhs_local = nullptr;
   c->semi = nullptr;
+  c->src_acc = nullptr;
+  c->src_max = nullptr;
   c->semi_valid = 0;
   FdmPlan* keep = c->cg.fdm;
   const df64* kb = c->cg.bands_df;
@@ -349,6 +417,8 @@ cfdem_status alloc_mesh_arena(cfdem_t c) {
   CK(grow(&c->vol, m.E), "mesh arena");
   CK(grow(&c->rhs_local, m.E * (int64_t)(m.k + 1) * (m.k + 1) * (m.k + 1)), "mesh arena");
   CK(grow(&c->semi, 5 * m.E), "mesh arena");
+  CK(grow(&c->src_acc, 16 * m.E), "mesh arena");
+  CK(grow(&c->src_max, 4), "mesh arena");
   c->semi_valid = 0;
   CgWork& w = c->cg;
   CK(grow(&w.r, nn), "cg");
@@ -467,7 +537,207 @@ cfdem_status solve(cfdem_t c, const double* b, double* x, const char* what) {
   return CFDEM_OK;
 }
 
+
+// ---------------------------------------------------------------- autotuner
+// The bin edge of the QCM's particle bins and the tile shape of the
+// projection operator decide how much work the void fraction and the solve
+// do but not what they compute.  With autotune = 1 the first eager call of a
+// new signature times a few candidates on the actual inputs (CUDA events on
+// the context's stream, two timed runs after one warm-up, the faster kept)
+// and keeps the fastest; the choice is cached per process by signature.
+
+std::mutex g_tune_mu;
+std::vector<std::pair<TuneKey, double>> g_bin_choice;  // signature -> bin edge
+std::vector<std::pair<TuneKey, int>> g_shape_choice;   // signature -> tile shape
+
+bool same_key(const TuneKey& a, const TuneKey& b) { return std::memcmp(&a, &b, sizeof a) == 0; }
+
+TuneKey base_key(const cfdem_ctx* c) {
+  TuneKey k;
+  std::memset(&k, 0, sizeof k);
+  const MeshDev& m = c->mesh;
+  for (int a = 0; a < 3; ++a) {
+    k.ne[a] = m.ne[a];
+    k.L[a] = m.L[a];
+  }
+  k.k = m.k;
+  k.precision = c->prm.precision;
+  return k;
+}
+
+double host_ms_since(const std::chrono::steady_clock::time_point& t0) {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// device time of fn() on the stream: one warm-up run, then the faster of two
+template <class F>
+cudaError_t time_on_stream(cudaStream_t s, F&& fn, float* ms_out) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  float best = FLT_MAX;
+  for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+    e = cudaEventRecord(a, s);
+    if (e == cudaSuccess) e = fn();
+    if (e == cudaSuccess) e = cudaEventRecord(b, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+    if (e == cudaSuccess && rep > 0 && t < best) best = t;
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  *ms_out = best;
+  return e;
+}
+
+// bin edge: candidates R + r_max (the default) and its 1/1.5, 1/2, 1/3, and
+// the element edge h and h/2, h/3 (bins nested in elements); each timed on
+// binning + QCM of the call's particles
+cfdem_status tune_bins(cfdem_t c, int64_t n, const double* x, const double* r) {
+  const cfdem_params& p = c->prm;
+  if (!p.autotune || p.bin_edge > 0 || p.scheme != 0 || n <= 0) return CFDEM_OK;
+  if (stream_capturing(c->stream)) return CFDEM_OK;
+  TuneKey key = base_key(c);
+  key.variant = p.qcm_conserve;
+  key.nbucket = 63 - __builtin_clzll((unsigned long long)n);
+  key.R = c->R;
+  key.rmax = p.max_radius;
+  if (c->bin_key_set && same_key(c->bin_key, key)) return CFDEM_OK;
+  const auto t0 = std::chrono::steady_clock::now();
+  const MeshDev& m = c->mesh;
+  double edge = -1.0;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (const auto& kv : g_bin_choice)
+      if (same_key(kv.first, key)) edge = kv.second;
+  }
+  cfdem_status s;
+  if (edge <= 0) {
+    const double cut = c->R + (p.max_radius > 0 ? p.max_radius : c->R);
+    const double hmin = std::fmin(m.h[0], std::fmin(m.h[1], m.h[2]));
+    const double cand[] = {cut, cut / 1.5, cut / 2.0, cut / 3.0, hmin, hmin / 2.0, hmin / 3.0};
+    const bool mixed = p.precision == 1;
+    const bool conserve = p.qcm_conserve == 1;
+    const bool timer_on = c->timer.on;
+    c->timer.on = false;
+    std::vector<BinDev> seen;
+    float best = FLT_MAX;
+    edge = cut;
+    for (double ed : cand) {
+      const BinDev g = bin_grid(m, ed);
+      bool dup = g.nbins > ((int64_t)1 << 24);
+      for (const BinDev& o : seen)
+        dup = dup || (o.nb[0] == g.nb[0] && o.nb[1] == g.nb[1] && o.nb[2] == g.nb[2]);
+      if (dup) continue;
+      seen.push_back(g);
+      c->bins = g;
+      s = ensure_bins(c);
+      if (s != CFDEM_OK) {
+        c->timer.on = timer_on;
+        return s;
+      }
+      float ms = FLT_MAX;
+      cudaError_t e = time_on_stream(c->stream, [&]() -> cudaError_t {
+        if (do_bin(c, n, x, r) != CFDEM_OK) return cudaErrorUnknown;
+        return launch_qcm(m, c->tab, c->bins, mixed ? 1 : 0, c->R, c->bin_start, c->perm,
+                          c->xs64, c->xs32, c->st, mixed ? nullptr : c->eps64,
+                          mixed ? c->eps32 : nullptr, nullptr, nullptr, c->stream,
+                          conserve ? reinterpret_cast<float2*>(c->qcm_w) : nullptr,
+                          conserve ? n : 0);
+      }, &ms);
+      if (e != cudaSuccess) {
+        c->timer.on = timer_on;
+        return cuda_fail(c, e, "autotune bins");
+      }
+      if (ms < best) {
+        best = ms;
+        edge = ed;
+      }
+    }
+    c->timer.on = timer_on;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_bin_choice.emplace_back(key, edge);
+  }
+  c->bins = bin_grid(m, edge);
+  s = ensure_bins(c);
+  if (s != CFDEM_OK) return s;
+  c->bin_key = key;
+  c->bin_key_set = true;
+  c->tuned |= 1;
+  c->tune_ms += host_ms_since(t0);
+  return CFDEM_OK;
+}
+
+// tile shape of the operator: each shape that fits in shared memory timed on
+// the solve of the call's right-hand side (from zero, into a scratch vector)
+cfdem_status tune_shape(cfdem_t c, const double* b) {
+  const cfdem_params& p = c->prm;
+  if (!p.autotune || stream_capturing(c->stream)) return CFDEM_OK;
+  TuneKey key = base_key(c);
+  key.variant = c->fdm ? 1 : 0;
+  for (int a = 0; a < 4; ++a) key.coef[a] = c->coef[a];
+  if (c->shape_key_set && same_key(c->shape_key, key)) return CFDEM_OK;
+  const auto t0 = std::chrono::steady_clock::now();
+  MeshDev& m = c->mesh;
+  int shape = -1;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (const auto& kv : g_shape_choice)
+      if (same_key(kv.first, key)) shape = kv.second;
+  }
+  if (shape < 0) {
+    CK(grow(&c->tune_x, m.n_nodes), "autotune scratch");
+    Timer* tm = c->cg.timer;
+    cudaStream_t loop = c->cg.loop;
+    c->cg.timer = nullptr;
+    c->cg.loop = nullptr;
+    float best = FLT_MAX;
+    shape = m.shape;
+    for (int sh = 0; sh < 3; ++sh) {
+      if (!shape_fits(m, sh)) continue;
+      m.shape = sh;
+      float ms = FLT_MAX;
+      cudaError_t e = time_on_stream(c->stream, [&]() -> cudaError_t {
+        cudaError_t ee = cudaMemsetAsync(c->tune_x, 0, sizeof(double) * m.n_nodes, c->stream);
+        if (ee != cudaSuccess) return ee;
+        int it = 0, outer = 0, conv = 0;
+        double rel = 0.0;
+        if (p.precision == 1)
+          return run_cg_mixed(m, c->bands64, c->bands32, c->coef, b, c->tune_x, p.cg_rtol,
+                              p.cg_maxit, c->cg, c->stream, &it, &outer, &rel, &conv);
+        return run_cg64(m, c->bands64, c->coef, b, c->tune_x, p.cg_rtol, p.cg_maxit, c->cg,
+                        c->stream, &it, &rel, &conv);
+      }, &ms);
+      if (e != cudaSuccess) {
+        c->cg.timer = tm;
+        c->cg.loop = loop;
+        return cuda_fail(c, e, "autotune tile shape");
+      }
+      if (ms < best) {
+        best = ms;
+        shape = sh;
+      }
+    }
+    c->cg.timer = tm;
+    c->cg.loop = loop;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_shape_choice.emplace_back(key, shape);
+  }
+  m.shape = shape;
+  c->shape_key = key;
+  c->shape_key_set = true;
+  c->tuned |= 2;
+  c->tune_ms += host_ms_since(t0);
+  return CFDEM_OK;
+}
+
 }  // namespace
+
+namespace cfdem {
+// the 1D reference tables of degree k (and kp) for other translation units
+void make_tables(int k, int kp, Tables* t) { build_tables(k, kp, t); }
+}  // namespace cfdem
 
 // ============================================================== public API
 
@@ -494,6 +764,7 @@ void cfdem_params_default(cfdem_params* p) {
   p->shear_force = 0;
   p->fluid_drag = 0;
   p->qcm_conserve = 0;
+  p->autotune = 1;
 }
 
 cfdem_status cfdem_create(cfdem_t* out, int device, void* stream) {
@@ -533,7 +804,8 @@ cfdem_status cfdem_destroy(cfdem_t c) {
   c->fdm = nullptr;
   c->timer.release();
   void* ps[] = {c->st, c->bands64, c->bands32, c->bandsdf, c->bin_of, c->slot, c->perm, c->xs64,
-                c->xs32, c->qcm_w, c->bin_count, c->bin_start, c->scan_tmp};
+                c->xs32, c->qcm_w, c->psrc, c->pelem, c->bin_count, c->bin_start,
+                c->scan_tmp};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (c->loop_stream) cudaStreamDestroy(c->loop_stream);
@@ -605,6 +877,7 @@ cfdem_status cfdem_set_params(cfdem_t c, const cfdem_params* p) {
     return fail(c, CFDEM_EINVAL, "fluid_drag must be 0 (explicit) or 1 (fluid-side form)");
   if (p->qcm_conserve < 0 || p->qcm_conserve > 1)
     return fail(c, CFDEM_EINVAL, "qcm_conserve must be 0 or 1");
+  if (p->autotune < 0 || p->autotune > 1) return fail(c, CFDEM_EINVAL, "autotune must be 0 or 1");
   c->prm = *p;
   ++c->gen;
   return resolve(c);
@@ -667,6 +940,8 @@ cfdem_status cfdem_void_fraction(cfdem_t c, int64_t n, const double* x, const do
     if (nb_count) CK(cudaMemsetAsync(nb_count, 0, sizeof(int32_t) * m.E * m.Q, c->stream), "pcm");
     if (nb_idsum) CK(cudaMemsetAsync(nb_idsum, 0, sizeof(int64_t) * m.E * m.Q, c->stream), "pcm");
   } else {
+    s = tune_bins(c, n, x, r);
+    if (s != CFDEM_OK) return s;
     s = do_bin(c, n, x, r);
     if (s != CFDEM_OK) return s;
     c->timer.begin(kStageVoid, c->stream);
@@ -723,6 +998,8 @@ cfdem_status cfdem_project(cfdem_t c, const double* eps_q, double* eps_nodal) {
   s = cfdem_project_rhs(c, eps_q, c->b);
   if (s != CFDEM_OK) return s;
   DeviceGuard g(c->device);
+  s = tune_shape(c, c->b);
+  if (s != CFDEM_OK) return s;
   return solve(c, c->b, eps_nodal, "project");
 }
 
@@ -732,28 +1009,36 @@ cfdem_status cfdem_forces(cfdem_t c, int64_t n, const double* x, const double* r
                           double* F_q) {
   cfdem_status s = need_mesh(c);
   if (s != CFDEM_OK) return s;
-  if (n < 0 || (n > 0 && (!x || !r || !u_p || !f)) || !u_nodal || !p_nodal || !eps_nodal)
+  if (n < 0 || n >= ((int64_t)1 << 31) || (n > 0 && (!x || !r || !u_p || !f)) || !u_nodal ||
+      !p_nodal || !eps_nodal)
     return fail(c, CFDEM_EINVAL, "null input");
   DeviceGuard g(c->device);
   const MeshDev& m = c->mesh;
   const bool semi = c->prm.fluid_drag == 1;
   const bool want_src = F_elem || F_q || semi;
-  if (want_src) CK(cudaMemsetAsync(c->S, 0, sizeof(double) * 3 * m.E, c->stream), "forces");
-  if (semi) CK(cudaMemsetAsync(c->semi, 0, sizeof(double) * 5 * m.E, c->stream), "forces");
+  s = ensure_particles(c, n);
+  if (s != CFDEM_OK) return s;
+  PartSrc ps{want_src ? c->psrc : nullptr, c->pelem, c->src_max};
+  if (want_src)
+    CK(cudaMemsetAsync(c->src_max, 0, 3 * sizeof(unsigned long long), c->stream), "forces");
   c->timer.begin(kStageForces, c->stream);
   CK(launch_forces(m, c->tab, c->prm.precision, force_params(c), n, x, r, u_p, u_nodal,
-                   p_nodal, eps_nodal, f, f_drag, want_src ? c->S : nullptr, semi_acc(c), c->st,
-                   c->stream),
+                   p_nodal, eps_nodal, f, f_drag, ps, c->st, c->stream),
      "forces");
   c->timer.end(kStageForces, c->stream);
-  if (F_elem || F_q) {
+  if (want_src) {
     c->timer.begin(kStageSource, c->stream);
-    if (semi)
-      CK(launch_fluid_source_semi(m, c->tab, c->prm.precision, c->S, semi_acc(c), u_nodal,
-                                  F_elem, F_q, c->stream),
-         "fluid source");
-    else
-      CK(launch_fluid_source(m, c->S, F_elem, F_q, c->stream), "fluid source");
+    CK(launch_source_sum(m, n, ps, u_p, semi ? 1 : 0, c->src_acc, c->S, semi_acc(c),
+                         c->stream),
+       "fluid source");
+    if (F_elem || F_q) {
+      if (semi)
+        CK(launch_fluid_source_semi(m, c->tab, c->prm.precision, c->S, semi_acc(c), u_nodal,
+                                    F_elem, F_q, c->stream),
+           "fluid source");
+      else
+        CK(launch_fluid_source(m, c->S, F_elem, F_q, c->stream), "fluid source");
+    }
     c->timer.end(kStageSource, c->stream);
   }
   c->semi_valid = semi ? 1 : 0;
@@ -887,6 +1172,9 @@ cfdem_status cfdem_get_stats(cfdem_t c, cfdem_stats* out) {
   out->timer_overflow = c->timer.overflow ? 1 : 0;
   out->kernel_launches = launches_total() - c->launches_at_reset;
   out->precond = c->fdm ? 1 : 0;
+  out->tile_shape = c->mesh.shape;
+  out->tuned = c->tuned;
+  out->tune_ms = c->tune_ms;
   return CFDEM_OK;
 }
 

@@ -14,6 +14,14 @@ using cfdem::MeshDev;
 using cfdem::Tables;
 using cfdem::Timer;
 
+// The signature a tuned choice is kept for (compared byte by byte: built
+// from a zeroed object).
+struct TuneKey {
+  int ne[3], k, precision, variant;  // variant: QCM conserve flag, or the preconditioner
+  int64_t nbucket;                    // particle count bucket (floor(log2 n)), 0 for shapes
+  double L[3], R, rmax, coef[4];
+};
+
 struct cfdem_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -35,6 +43,8 @@ struct cfdem_ctx {
   double* xs64 = nullptr;
   float* xs32 = nullptr;
   float* qcm_w = nullptr;      // volume-conserving QCM weights per sorted particle [2 n]
+  double* psrc = nullptr;      // per-particle fluid-source records [4 n] (PartSrc::S)
+  int32_t* pelem = nullptr;    // element of each particle [n] (PartSrc::elem)
   int64_t cap_bins = 0;
   int32_t *bin_count = nullptr, *bin_start = nullptr, *scan_tmp = nullptr;
   // mesh arena
@@ -45,6 +55,8 @@ struct cfdem_ctx {
   double* vol = nullptr;       // per-element particle volume (PCM)
   double* rhs_local = nullptr; // per-element right-hand-side contributions [(k+1)^3][E]
   double* semi = nullptr;      // fluid-side drag sums: B [E], U [3E], N [E]
+  long long* src_acc = nullptr;           // fixed-point source sums [16 E]
+  unsigned long long* src_max = nullptr;  // largest |value| bits per class [3] (+1 pad)
   int semi_valid = 0;          // 1 once a forces call with fluid_drag = 1 filled them
   // adjoint arena (grown by the first cfdem_adjoint)
   double* adj_geps = nullptr;  // dJ/deps_h [n_nodes]
@@ -66,5 +78,13 @@ struct cfdem_ctx {
   unsigned gen = 0;                    // bumped by every change of mesh, parameters or timing
   Timer timer;
   long long launches_at_reset = 0;
+  // autotuner: the signatures the current bins and tile shape were tuned
+  // for, what was tuned (bit 0 bins, bit 1 shape), host time spent, and a
+  // scratch vector for the timed solves
+  TuneKey bin_key{}, shape_key{};
+  bool bin_key_set = false, shape_key_set = false;
+  int tuned = 0;
+  double tune_ms = 0.0;
+  double* tune_x = nullptr;
   std::string err;
 };

@@ -67,6 +67,20 @@ __device__ __forceinline__ int bin_axis_fast(double x, double x0, double be, dou
   return (int)f;
 }
 
+// the integer key of a double whose signed order is the order of the values
+// (NaNs fall outside every finite interval); the host computes the same keys
+// for the in_box bounds, so that the mixed path tests the box without FP64
+// instructions
+__device__ __forceinline__ long long order_key(double v) {
+  const long long b = __double_as_longlong(v);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+
+__device__ __forceinline__ bool in_box_key(double v, long long lo, long long hi) {
+  const long long k = order_key(v);
+  return k >= lo && k <= hi;
+}
+
 __device__ __forceinline__ void report_bad(DevStatus* st, int64_t i) {
   atomicMin(&st->first_bad, (unsigned long long)i);
 }
@@ -81,8 +95,8 @@ __device__ __forceinline__ float t_sqrt<float>(float v) { return sqrtf(v); }
 // Lagrange basis of degree D on nodes z and its derivative at t; lw[a] =
 // 1 / prod_{b != a} (z_a - z_b) comes from the host so that no division is
 // done here
-template <int D, typename T>
-__device__ __forceinline__ void lagrange(const double* zz, const double* lw, T t, T* l, T* dl) {
+template <int D, typename T, typename Z>
+__device__ __forceinline__ void lagrange(const Z* zz, const Z* lw, T t, T* l, T* dl) {
   T d[D + 1];
 #pragma unroll
   for (int a = 0; a <= D; ++a) d[a] = t - (T)zz[a];
@@ -103,9 +117,9 @@ __device__ __forceinline__ void lagrange(const double* zz, const double* lw, T t
 // Lagrange basis with its first, second and (if d3 is given) third
 // derivatives at t: the product prod_{b != a} (t - z_b) differentiated by
 // the Leibniz rule, scaled by the barycentric weight lw[a].
-template <int D, typename T>
-__device__ __forceinline__ void lagrange_d3(const double* zz, const double* lw, T t, T* l, T* d1,
-                                            T* d2, T* d3) {
+template <int D, typename T, typename Z>
+__device__ __forceinline__ void lagrange_d3(const Z* zz, const Z* lw, T t, T* l, T* d1, T* d2,
+                                            T* d3) {
   T d[D + 1];
 #pragma unroll
   for (int a = 0; a <= D; ++a) d[a] = t - (T)zz[a];

@@ -207,10 +207,24 @@ __device__ __forceinline__ D4<T> nlog10(D4<T> a) {
 
 // ---------------------------------------------------------------- closures
 
+// fluid properties in the precision of the closure
+template <typename T>
+__device__ __forceinline__ T fp_rho(const ForceParams& fp);
+template <>
+__device__ __forceinline__ double fp_rho<double>(const ForceParams& fp) { return fp.rho; }
+template <>
+__device__ __forceinline__ float fp_rho<float>(const ForceParams& fp) { return fp.rho32; }
+template <typename T>
+__device__ __forceinline__ T fp_mu(const ForceParams& fp);
+template <>
+__device__ __forceinline__ double fp_mu<double>(const ForceParams& fp) { return fp.mu; }
+template <>
+__device__ __forceinline__ float fp_mu<float>(const ForceParams& fp) { return fp.mu32; }
+
 // f_D = drag_coef(...) U for |U| = speed > 0; ec the clamped eps.
 template <typename N, typename T>
 __device__ __forceinline__ N drag_coef(const ForceParams& fp, N speed, N ec, T rp) {
-  const T rho = (T)fp.rho, mu = (T)fp.mu, dp = (T)2 * rp;
+  const T rho = fp_rho<T>(fp), mu = fp_mu<T>(fp), dp = (T)2 * rp;
   const N Re = (rho * dp / mu) * (ec * speed);
   const int model = fp.drag_model;
   N coef;
@@ -221,9 +235,12 @@ __device__ __forceinline__ N drag_coef(const ForceParams& fp, N speed, N ec, T r
       const N re = val(Re) > Closure<T>::tiny() ? Re : Num<N>::c(Closure<T>::tiny());
       const N tt = (T)1.5 - nlog10(re);
       const N g = nexp((T)(-0.5) * (tt * tt));
-      const N ex = model == 0 ? (T)3.7 - (T)0.65 * g
-                              : (T)2.65 * (ec + (T)1) - ((T)5.3 - (T)3.5 * ec) * (ec * ec) * g;
-      cds = cds * nexp(((T)2 - ex) * nlog(ec));
+      // 2 - chi written out so that its terms are rounded once (no 3.7 or
+      // 2.65 (eps + 1) formed first and then subtracted from 2)
+      const N two_minus_ex =
+          model == 0 ? (T)0.65 * g - (T)1.7
+                     : ((T)5.3 - (T)3.5 * ec) * (ec * ec) * g - ((T)2.65 * ec + (T)0.65);
+      cds = cds * nexp(two_minus_ex * nlog(ec));
     }
     coef = ((T)0.5 * rho * (T)kPi * rp * rp) * cds;
   } else {

@@ -43,6 +43,9 @@ struct Tables {
   double Bw[4][4];          // Bw[a][q] = l_a(g_q) w_q  (k basis, Gauss weight folded in)
   double Mh[4][4];          // reference mass     int_0^1 l_a l_b
   double Kh[4][4];          // reference stiffness int_0^1 l_a' l_b'
+  float zf[4], zpf[4];      // FP32 copies of z, zp, lw, lwp (mixed path)
+  float lwf[4], lwpf[4];
+  float z_lo[4], lw_lo[4];  // z - zf and lw - lwf: z and lw as double-float
 };
 
 // Bin grid over the box.
@@ -107,6 +110,9 @@ struct Timer {
   void create();  // allocate the events (outside any timed region)
 };
 
+// the 1D reference tables of degree k and kp (GLL nodes, Gauss rule, ...)
+void make_tables(int k, int kp, Tables* t);
+
 // process-wide count of kernel launches made by the library
 void count_launches(int n);
 long long launches_total();
@@ -118,6 +124,27 @@ struct ForceParams {
   double rho, mu, g[3], eps_floor;
   double inv_h[3];
   int drag_model, beta_over_eps, vans_model, shear, fluid_drag;
+  // mixed path: FP32 copies, and the element location from a double-float
+  // split of x (loc32 = 0 where the box is too far from the origin for the
+  // FP32 margin, then the FP64 rule locates every particle)
+  float rho32, mu32, g32[3], eps_floor32, inv_h32[3];
+  float x0_hi[3], x0_lo[3], inv_h_hi[3], inv_h_lo[3];
+  int loc32;
+  // in_box bounds x0 - 1e-12 L and (x0 + L) + 1e-12 L as order-preserving
+  // integer keys of their bits (compared without FP64 instructions)
+  long long box_lo_key[3], box_hi_key[3];
+};
+
+// Per-particle fluid-source records written by the forces kernel and summed
+// per element by launch_source_sum: S = the particle's share of F_pf (drag,
+// and for model B the pressure and shear parts) and its drag coefficient
+// [n][4], its element [n] (-1 outside the mesh), and the bits of the largest
+// |S| component, |coefficient| and |u_p| component over the particles
+// (maxbits[3], reset before the forces kernel).
+struct PartSrc {
+  double* S;
+  int32_t* elem;
+  unsigned long long* maxbits;
 };
 
 // Per-element accumulators of the fluid-side drag (fluid_drag = 1): sum of
@@ -134,12 +161,19 @@ cudaError_t launch_bin(const MeshDev& m, const BinDev& b, int64_t n, const doubl
                        const double* r, int32_t* bin_of, int32_t* slot, int32_t* bin_count,
                        int32_t* bin_start, int32_t* perm, int32_t* scan_tmp, double* xs64,
                        float* xs32, DevStatus* st, cudaStream_t s);
-// S_elem (and acc when fp.fluid_drag) accumulate per element; both may be null
+// ps.S / ps.elem receive the per-particle source records (ps.S may be null)
 cudaError_t launch_forces(const MeshDev& m, const Tables& t, int precision, const ForceParams& fp,
                           int64_t n, const double* x, const double* r, const double* u_p,
                           const double* u_nodal, const double* p_nodal,
-                          const double* eps_nodal, double* f, double* f_drag, double* S_elem,
-                          SemiAcc acc, DevStatus* st, cudaStream_t s);
+                          const double* eps_nodal, double* f, double* f_drag, PartSrc ps,
+                          DevStatus* st, cudaStream_t s);
+// per-element sums of the records: S_elem[E][3] and, with semi, the drag
+// coefficients, particle velocities and counts into acc.  The sums are exact
+// fixed-point sums (acc64: 16 int64 per element of scratch), so their bits
+// do not depend on the order of the particles.
+cudaError_t launch_source_sum(const MeshDev& m, int64_t n, PartSrc ps, const double* u_p,
+                              int semi, long long* acc64, double* S_elem, SemiAcc acc,
+                              cudaStream_t s);
 cudaError_t launch_fluid_source(const MeshDev& m, const double* S_elem, double* F_elem,
                                 double* F_q, cudaStream_t s);
 cudaError_t launch_fluid_source_semi(const MeshDev& m, const Tables& t, int precision,
@@ -222,6 +256,8 @@ struct CgWork {
 // true when s is a stream under active capture
 bool stream_capturing(cudaStream_t s);
 int cg_blocks(const MeshDev& m);
+// 1 if tile shape `shape` (0..2) fits the operator's shared-memory budget
+bool shape_fits(const MeshDev& m, int shape);
 int pick_shape(const MeshDev& m);
 cudaError_t run_cg64(const MeshDev& m, const double* bands, const double* coef,
                      const double* b, double* x, double rtol, int maxit, CgWork& w,

@@ -4,10 +4,12 @@
 //   a6 particle-fluid forces (Sec. 2.3.2), a7 fluid source (Eqs. fb, fa).
 #include <cfloat>
 #include <cstdint>
+#include <type_traits>
 
 #include "internal.h"
 #include "device_common.cuh"
 #include "drag.cuh"
+#include "df64.cuh"
 
 namespace cfdem {
 
@@ -275,22 +277,92 @@ cudaError_t launch_bin(const MeshDev& m, const BinDev& b, int64_t n, const doubl
 // ----------------------------------------------------------------------------
 // a6: forces
 
+// ---- helpers of the mixed (FP32) path: no FP64 instruction per node
+
+// v as FP32 through its integer double-float split
+__device__ __forceinline__ float f32_of(double v) {
+  const df64 s = df_from_double_int(v);
+  return s.hi + s.lo;
+}
+
+// a - b in FP32 from the double-float splits of a and b: the high parts of
+// two close values subtract exactly, so the difference carries an FP32
+// rounding of itself, not of a or b
+__device__ __forceinline__ float df_diff(df64 a, df64 b) { return (a.hi - b.hi) + (a.lo - b.lo); }
+
+// element index and local coordinate (as double-float) along axis a on the
+// mixed path: t = (x - x0) / h from the double-float split of x (~2^-46
+// |x| / h); where t lies within 1e-5 of an element face (or outside the
+// mesh) the FP64 rule of elem_axis_fast decides, so the element is the one
+// the definition gives
+__device__ __forceinline__ int elem_axis_mixed(double x, const MeshDev& m, const ForceParams& fp,
+                                               int a, df64* xi) {
+  if (fp.loc32) {
+    const df64 d = df_from_double_int(x) - df64(fp.x0_hi[a], fp.x0_lo[a]);
+    const df64 t = d * df64(fp.inv_h_hi[a], fp.inv_h_lo[a]);
+    const float fl = floorf(t.hi);
+    const float fr = (t.hi - fl) + t.lo;
+    const int i = (int)fl;
+    if (fr >= 1e-5f && fr <= 1.0f - 1e-5f && i >= 0 && i <= m.ne[a] - 1) {
+      *xi = df_renorm(t.hi - fl, t.lo);  // t.hi - fl is exact
+      return i;
+    }
+  }
+  double xd;
+  const int i = elem_axis_fast(x, m.x0[a], m.h[a], fp.inv_h[a], m.ne[a], &xd);
+  *xi = df_from_double_int(xd);
+  return i;
+}
+
+// Lagrange basis of degree D at t in double-float (nodes and barycentric
+// weights split on the host)
+template <int D>
+__device__ __forceinline__ void lagrange_df(const Tables& tb, df64 t, df64* l) {
+  df64 d[D + 1];
+#pragma unroll
+  for (int a = 0; a <= D; ++a) d[a] = t - df64(tb.zf[a], tb.z_lo[a]);
+#pragma unroll
+  for (int a = 0; a <= D; ++a) {
+    df64 v(tb.lwf[a], tb.lw_lo[a]);
+#pragma unroll
+    for (int b = 0; b <= D; ++b)
+      if (b != a) v = v * d[b];
+    l[a] = v;
+  }
+}
+
+// FP64 value written from a T
+template <typename T>
+__device__ __forceinline__ double out_double(T v);
+template <>
+__device__ __forceinline__ double out_double<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ double out_double<float>(float v) { return double_from_float_int(v); }
+
 // Shear force -V_p div tau at local coordinates xi of the element whose first
 // velocity node is `base` (Sec. 2.3.2), tau the deviatoric stress of Eq.
 // (stress): (div tau)_a = mu (lap u_a + d_a (div u) / 3), second derivatives
 // of the Q_k interpolant with the chain rule 1/h per axis.  Nodal values are
-// taken relative to the element's first node (in FP64) so that the FP32 path
-// does not carry the mean velocity through the cancelling weights.
+// taken relative to the element's first node (FP64 differences, or on the
+// mixed path differences of double-float splits) so that the FP32 path does
+// not carry the mean velocity through the cancelling weights.
 template <int K, typename T>
 __device__ __forceinline__ void shear_force(const Tables& tb, const ForceParams& fp,
                                             const double* __restrict__ u_nodal, int64_t base,
                                             int64_t nx, int64_t nxy, const T xi[3], T Vp,
                                             T fs[3]) {
+  constexpr bool MIX = std::is_same<T, float>::value;
   T l[3][K + 1], d1[3][K + 1], d2[3][K + 1];
 #pragma unroll
-  for (int ax = 0; ax < 3; ++ax)
-    lagrange_d3<K, T>(tb.z, tb.lw, xi[ax], l[ax], d1[ax], d2[ax], (T*)nullptr);
-  const T ih0 = (T)fp.inv_h[0], ih1 = (T)fp.inv_h[1], ih2 = (T)fp.inv_h[2];
+  for (int ax = 0; ax < 3; ++ax) {
+    if constexpr (MIX)
+      lagrange_d3<K, T>(tb.zf, tb.lwf, xi[ax], l[ax], d1[ax], d2[ax], (T*)nullptr);
+    else
+      lagrange_d3<K, T>(tb.z, tb.lw, xi[ax], l[ax], d1[ax], d2[ax], (T*)nullptr);
+  }
+  const T ih0 = MIX ? (T)fp.inv_h32[0] : (T)fp.inv_h[0];
+  const T ih1 = MIX ? (T)fp.inv_h32[1] : (T)fp.inv_h[1];
+  const T ih2 = MIX ? (T)fp.inv_h32[2] : (T)fp.inv_h[2];
   const T sxx = ih0 * ih0, syy = ih1 * ih1, szz = ih2 * ih2;
   const T sxy = ih0 * ih1, sxz = ih0 * ih2, syz = ih1 * ih2;
   T H[3][6];  // per component: xx, yy, zz, xy, xz, yz
@@ -300,6 +372,8 @@ __device__ __forceinline__ void shear_force(const Tables& tb, const ForceParams&
     for (int q = 0; q < 6; ++q) H[c][q] = (T)0;
   const double u00 = __ldg(u_nodal + 3 * base), u01 = __ldg(u_nodal + 3 * base + 1),
                u02 = __ldg(u_nodal + 3 * base + 2);
+  const df64 r0 = df_from_double_int(u00), r1 = df_from_double_int(u01),
+             r2 = df_from_double_int(u02);
 #pragma unroll
   for (int c = 0; c <= K; ++c)
 #pragma unroll
@@ -307,8 +381,16 @@ __device__ __forceinline__ void shear_force(const Tables& tb, const ForceParams&
 #pragma unroll
       for (int a = 0; a <= K; ++a) {
         const int64_t nd = base + a + nx * b + nxy * c;
-        const T du[3] = {(T)(__ldg(u_nodal + 3 * nd) - u00), (T)(__ldg(u_nodal + 3 * nd + 1) - u01),
-                         (T)(__ldg(u_nodal + 3 * nd + 2) - u02)};
+        T du[3];
+        if constexpr (MIX) {
+          du[0] = df_diff(df_from_double_int(__ldg(u_nodal + 3 * nd)), r0);
+          du[1] = df_diff(df_from_double_int(__ldg(u_nodal + 3 * nd + 1)), r1);
+          du[2] = df_diff(df_from_double_int(__ldg(u_nodal + 3 * nd + 2)), r2);
+        } else {
+          du[0] = (T)(__ldg(u_nodal + 3 * nd) - u00);
+          du[1] = (T)(__ldg(u_nodal + 3 * nd + 1) - u01);
+          du[2] = (T)(__ldg(u_nodal + 3 * nd + 2) - u02);
+        }
         const T w[6] = {d2[0][a] * l[1][b] * l[2][c] * sxx, l[0][a] * d2[1][b] * l[2][c] * syy,
                         l[0][a] * l[1][b] * d2[2][c] * szz, d1[0][a] * d1[1][b] * l[2][c] * sxy,
                         d1[0][a] * l[1][b] * d1[2][c] * sxz, l[0][a] * d1[1][b] * d1[2][c] * syz};
@@ -317,7 +399,8 @@ __device__ __forceinline__ void shear_force(const Tables& tb, const ForceParams&
 #pragma unroll
           for (int q = 0; q < 6; ++q) H[cc][q] += w[q] * du[cc];
       }
-  const T mu = (T)fp.mu, mu3 = (T)(fp.mu / 3.0);
+  const T mu = MIX ? (T)fp.mu32 : (T)fp.mu;
+  const T mu3 = mu / (T)3;
   const T gd[3] = {H[0][0] + H[1][3] + H[2][4], H[0][3] + H[1][1] + H[2][5],
                    H[0][4] + H[1][5] + H[2][2]};  // d_a div u
 #pragma unroll
@@ -325,78 +408,172 @@ __device__ __forceinline__ void shear_force(const Tables& tb, const ForceParams&
     fs[cc] = -Vp * (mu * (H[cc][0] + H[cc][1] + H[cc][2]) + mu3 * gd[cc]);
 }
 
-template <int K, int KP, typename T>
+// Forces on every particle (Sec. 2.3.2): u_f and eps at the particle by Q_k
+// interpolation, grad p by Q_kp, the drag closure, buoyancy and the pressure
+// gradient force (and the shear force).  With ps.S, each particle's share of
+// the fluid source and its element go to the per-particle records that
+// launch_source_sum adds per element.
+//
+// FP64 path (T = double): location, interpolation and closures in FP64.
+// Mixed path (T = float): no FP64 instruction per node.  The element is
+// located from a double-float split of x (the FP64 rule only within 1e-5 of
+// a face); the slip is interpolated in FP32 from the nodal differences
+// u_j - u_p,i formed from double-float splits (the weights sum to one, so
+// sum_j phi_j (u_j - u_p) = u_f - u_p, and no FP32 rounding of |u| enters a
+// small slip component); pressure differences along each axis likewise; the
+// closures in FP32.
+template <int K, int KP, typename T, bool SHEAR>
 __global__ void __launch_bounds__(128)
 k_forces(MeshDev m, Tables tb, ForceParams fp, int64_t n, const double* __restrict__ x,
          const double* __restrict__ r, const double* __restrict__ u_p,
          const double* __restrict__ u_nodal, const double* __restrict__ p_nodal,
          const double* __restrict__ eps_nodal, double* __restrict__ f,
-         double* __restrict__ f_drag, double* __restrict__ S_elem, SemiAcc acc,
-         DevStatus* st) {
+         double* __restrict__ f_drag, PartSrc ps, DevStatus* st) {
+  constexpr bool MIX = std::is_same<T, float>::value;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double p[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
-  if (!(in_box(p[0], m.x0[0], m.L[0]) && in_box(p[1], m.x0[1], m.L[1]) &&
-        in_box(p[2], m.x0[2], m.L[2]))) {
+  const double p[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+  bool inside;
+  if constexpr (MIX)
+    inside = in_box_key(p[0], fp.box_lo_key[0], fp.box_hi_key[0]) &&
+             in_box_key(p[1], fp.box_lo_key[1], fp.box_hi_key[1]) &&
+             in_box_key(p[2], fp.box_lo_key[2], fp.box_hi_key[2]);
+  else
+    inside = in_box(p[0], m.x0[0], m.L[0]) && in_box(p[1], m.x0[1], m.L[1]) &&
+             in_box(p[2], m.x0[2], m.L[2]);
+  if (!inside) {
     report_bad(st, i);
     for (int a = 0; a < 3; ++a) {
       f[3 * i + a] = 0.0;
       if (f_drag) f_drag[3 * i + a] = 0.0;
     }
+    if (ps.S) ps.elem[i] = -1;
     return;
   }
   int ie[3];
-  double xid[3];
-  for (int a = 0; a < 3; ++a)
-    ie[a] = elem_axis_fast(p[a], m.x0[a], m.h[a], fp.inv_h[a], m.ne[a], &xid[a]);
-  T xi[3] = {(T)xid[0], (T)xid[1], (T)xid[2]};
+  T xi[3];
+  df64 xdf[3];  // mixed path: local coordinates as double-float
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if constexpr (MIX) {
+      ie[a] = elem_axis_mixed(p[a], m, fp, a, &xdf[a]);
+      xi[a] = xdf[a].hi;
+    } else {
+      double xd;
+      ie[a] = elem_axis_fast(p[a], m.x0[a], m.h[a], fp.inv_h[a], m.ne[a], &xd);
+      xi[a] = xd;
+    }
+  }
 
-  // u_f and eps at the particle: Q_k interpolation.  The velocity is
-  // interpolated in FP64 on both paths: the slip u_f - u_p of a component
-  // that is small against the others cancels, and FP32 shape functions would
-  // leave an absolute error of ~1e-7 |u| in it.  eps uses the same weights.
-  double lxd[K + 1], lyd[K + 1], lzd[K + 1];
-  lagrange<K, double>(tb.z, tb.lw, xid[0], lxd, (double*)nullptr);
-  lagrange<K, double>(tb.z, tb.lw, xid[1], lyd, (double*)nullptr);
-  lagrange<K, double>(tb.z, tb.lw, xid[2], lzd, (double*)nullptr);
-  double ufd0 = 0, ufd1 = 0, ufd2 = 0, epsd = 0;
-  int64_t nx = m.nn[0], nxy = (int64_t)m.nn[0] * m.nn[1];
-  int64_t base = (int64_t)ie[0] * K + nx * ((int64_t)ie[1] * K) + nxy * ((int64_t)ie[2] * K);
+  // u_f - u_p and eps at the particle: Q_k interpolation
+  T lx[K + 1], ly[K + 1], lz[K + 1];
+  df64 lxd[K + 1], lyd[K + 1], lzd[K + 1];
+  if constexpr (MIX) {
+    lagrange_df<K>(tb, xdf[0], lxd);
+    lagrange_df<K>(tb, xdf[1], lyd);
+    lagrange_df<K>(tb, xdf[2], lzd);
+#pragma unroll
+    for (int a = 0; a <= K; ++a) {
+      lx[a] = lxd[a].hi;
+      ly[a] = lyd[a].hi;
+      lz[a] = lzd[a].hi;
+    }
+  } else {
+    lagrange<K, T>(tb.z, tb.lw, xi[0], lx, (T*)nullptr);
+    lagrange<K, T>(tb.z, tb.lw, xi[1], ly, (T*)nullptr);
+    lagrange<K, T>(tb.z, tb.lw, xi[2], lz, (T*)nullptr);
+  }
+  const double up0 = u_p[3 * i], up1 = u_p[3 * i + 1], up2 = u_p[3 * i + 2];
+  T U0 = 0, U1 = 0, U2 = 0, eps = 0;
+  const int64_t nx = m.nn[0], nxy = (int64_t)m.nn[0] * m.nn[1];
+  const int64_t base =
+      (int64_t)ie[0] * K + nx * ((int64_t)ie[1] * K) + nxy * ((int64_t)ie[2] * K);
+  // Mixed path.  The slip u_f - u_p is interpolated in double-float (basis,
+  // products and sums, then one subtraction of u_p): a slip component that
+  // is small against the nodal velocities (a rough field, u_p of either
+  // sign) would otherwise keep an FP32 rounding of the nodal values, ~1e-8
+  // m/s.  eps is interpolated in FP32 relative to the element's first node
+  // (the weights sum to one), so that FP32 rounds only its variation inside
+  // the element.
+  df64 uf0(0.f, 0.f), uf1(0.f, 0.f), uf2(0.f, 0.f), re(0.f, 0.f);
+  if constexpr (MIX) re = df_from_double_int(__ldg(eps_nodal + base));
 #pragma unroll
   for (int c = 0; c <= K; ++c) {
 #pragma unroll
     for (int b = 0; b <= K; ++b) {
-      double lyz = lyd[b] * lzd[c];
+      const T lyz = ly[b] * lz[c];
+      df64 lyzd;
+      if constexpr (MIX) lyzd = lyd[b] * lzd[c];
 #pragma unroll
       for (int a = 0; a <= K; ++a) {
-        double phi = lxd[a] * lyz;
-        int64_t nd = base + a + nx * b + nxy * c;
-        ufd0 += phi * __ldg(u_nodal + 3 * nd);
-        ufd1 += phi * __ldg(u_nodal + 3 * nd + 1);
-        ufd2 += phi * __ldg(u_nodal + 3 * nd + 2);
-        epsd += phi * __ldg(eps_nodal + nd);
+        const int64_t nd = base + a + nx * b + nxy * c;
+        if constexpr (MIX) {
+          const df64 phid = lxd[a] * lyzd;
+          uf0 += phid * df_from_double_int(__ldg(u_nodal + 3 * nd));
+          uf1 += phid * df_from_double_int(__ldg(u_nodal + 3 * nd + 1));
+          uf2 += phid * df_from_double_int(__ldg(u_nodal + 3 * nd + 2));
+          eps += phid.hi * df_diff(df_from_double_int(__ldg(eps_nodal + nd)), re);
+        } else {
+          const T phi = lx[a] * lyz;
+          U0 += phi * __ldg(u_nodal + 3 * nd);
+          U1 += phi * __ldg(u_nodal + 3 * nd + 1);
+          U2 += phi * __ldg(u_nodal + 3 * nd + 2);
+          eps += phi * __ldg(eps_nodal + nd);
+        }
       }
     }
   }
+  if constexpr (MIX) {
+    const df64 s0 = uf0 - df_from_double_int(up0), s1 = uf1 - df_from_double_int(up1),
+               s2 = uf2 - df_from_double_int(up2);
+    U0 = s0.hi + s0.lo;
+    U1 = s1.hi + s1.lo;
+    U2 = s2.hi + s2.lo;
+    eps += re.hi + re.lo;
+  } else {  // the FP64 path interpolates u_f, then subtracts u_p
+    U0 -= up0;
+    U1 -= up1;
+    U2 -= up2;
+  }
   // grad p at the particle: Q_kp.  Each derivative is taken from nodal
-  // differences along its own axis, formed in FP64 (d/dx uses p_abc - p_0bc,
-  // and so on): the shape-function derivatives sum to zero only up to
-  // rounding in FP32, so a large pressure varying along one axis would
-  // otherwise leak into the other two components of the gradient
+  // differences along its own axis (d/dx uses p_abc - p_0bc, and so on),
+  // formed in FP64 or from double-float splits: the shape-function
+  // derivatives sum to zero only up to rounding in FP32, so a large pressure
+  // varying along one axis would otherwise leak into the other two
+  // components of the gradient
   T px[KP + 1], py[KP + 1], pz[KP + 1], dpx[KP + 1], dpy[KP + 1], dpz[KP + 1];
-  lagrange<KP, T>(tb.zp, tb.lwp, xi[0], px, dpx);
-  lagrange<KP, T>(tb.zp, tb.lwp, xi[1], py, dpy);
-  lagrange<KP, T>(tb.zp, tb.lwp, xi[2], pz, dpz);
-  int64_t pnx = m.np[0], pnxy = (int64_t)m.np[0] * m.np[1];
-  int64_t pbase =
+  if constexpr (MIX) {
+    lagrange<KP, T>(tb.zpf, tb.lwpf, xi[0], px, dpx);
+    lagrange<KP, T>(tb.zpf, tb.lwpf, xi[1], py, dpy);
+    lagrange<KP, T>(tb.zpf, tb.lwpf, xi[2], pz, dpz);
+  } else {
+    lagrange<KP, T>(tb.zp, tb.lwp, xi[0], px, dpx);
+    lagrange<KP, T>(tb.zp, tb.lwp, xi[1], py, dpy);
+    lagrange<KP, T>(tb.zp, tb.lwp, xi[2], pz, dpz);
+  }
+  const int64_t pnx = m.np[0], pnxy = (int64_t)m.np[0] * m.np[1];
+  const int64_t pbase =
       (int64_t)ie[0] * KP + pnx * ((int64_t)ie[1] * KP) + pnxy * ((int64_t)ie[2] * KP);
-  double pv[KP + 1][KP + 1][KP + 1];
+  using PV = typename std::conditional<MIX, df64, double>::type;
+  PV pv[KP + 1][KP + 1][KP + 1];
 #pragma unroll
   for (int c = 0; c <= KP; ++c)
 #pragma unroll
     for (int b = 0; b <= KP; ++b)
 #pragma unroll
-      for (int a = 0; a <= KP; ++a) pv[c][b][a] = __ldg(p_nodal + pbase + a + pnx * b + pnxy * c);
+      for (int a = 0; a <= KP; ++a) {
+        const double v = __ldg(p_nodal + pbase + a + pnx * b + pnxy * c);
+        if constexpr (MIX)
+          pv[c][b][a] = df_from_double_int(v);
+        else
+          pv[c][b][a] = v;
+      }
+  auto pdiff = [](PV u, PV v) -> T {
+    if constexpr (MIX)
+      return df_diff(u, v);
+    else
+      return u - v;
+  };
   T gp0 = 0, gp1 = 0, gp2 = 0;
 #pragma unroll
   for (int c = 0; c <= KP; ++c) {
@@ -404,23 +581,27 @@ k_forces(MeshDev m, Tables tb, ForceParams fp, int64_t n, const double* __restri
     for (int b = 0; b <= KP; ++b) {
 #pragma unroll
       for (int a = 0; a <= KP; ++a) {
-        if (a > 0) gp0 += dpx[a] * py[b] * pz[c] * (T)(pv[c][b][a] - pv[c][b][0]);
-        if (b > 0) gp1 += px[a] * dpy[b] * pz[c] * (T)(pv[c][b][a] - pv[c][0][a]);
-        if (c > 0) gp2 += px[a] * py[b] * dpz[c] * (T)(pv[c][b][a] - pv[0][b][a]);
+        if (a > 0) gp0 += dpx[a] * py[b] * pz[c] * pdiff(pv[c][b][a], pv[c][b][0]);
+        if (b > 0) gp1 += px[a] * dpy[b] * pz[c] * pdiff(pv[c][b][a], pv[c][0][a]);
+        if (c > 0) gp2 += px[a] * py[b] * dpz[c] * pdiff(pv[c][b][a], pv[0][b][a]);
       }
     }
   }
-  gp0 = gp0 / (T)m.h[0];
-  gp1 = gp1 / (T)m.h[1];
-  gp2 = gp2 / (T)m.h[2];
+  if constexpr (MIX) {
+    gp0 *= fp.inv_h32[0];
+    gp1 *= fp.inv_h32[1];
+    gp2 *= fp.inv_h32[2];
+  } else {
+    gp0 = gp0 / m.h[0];
+    gp1 = gp1 / m.h[1];
+    gp2 = gp2 / m.h[2];
+  }
 
   // closures
-  T rp = (T)r[i];
-  T U0 = (T)(ufd0 - u_p[3 * i]), U1 = (T)(ufd1 - u_p[3 * i + 1]),
-    U2 = (T)(ufd2 - u_p[3 * i + 2]);
-  T speed = t_sqrt<T>(U0 * U0 + U1 * U1 + U2 * U2);
-  T eps = (T)epsd;
-  T epsc = eps < (T)fp.eps_floor ? (T)fp.eps_floor : eps;
+  const T rp = MIX ? (T)f32_of(r[i]) : (T)r[i];
+  const T speed = t_sqrt<T>(U0 * U0 + U1 * U1 + U2 * U2);
+  const T floor_ = MIX ? (T)fp.eps_floor32 : (T)fp.eps_floor;
+  T epsc = eps < floor_ ? floor_ : eps;
   epsc = epsc > (T)1 ? (T)1 : epsc;
   T fd0 = 0, fd1 = 0, fd2 = 0, coef = 0;
   if (speed > (T)0) {
@@ -429,43 +610,62 @@ k_forces(MeshDev m, Tables tb, ForceParams fp, int64_t n, const double* __restri
     fd1 = coef * U1;
     fd2 = coef * U2;
   }
-  T Vp = (T)(4.0 / 3.0 * kPi) * rp * rp * rp;
+  const T Vp = (T)(4.0 / 3.0 * kPi) * rp * rp * rp;
   T fg0 = -Vp * gp0, fg1 = -Vp * gp1, fg2 = -Vp * gp2;
-  if (fp.shear) {  // the shear force joins the pressure term: f and model B's source
+  if constexpr (SHEAR) {  // the shear force joins the pressure term: f and model B's source
     T fs[3];
     shear_force<K, T>(tb, fp, u_nodal, base, nx, nxy, xi, Vp, fs);
     fg0 += fs[0];
     fg1 += fs[1];
     fg2 += fs[2];
   }
-  T rv = (T)fp.rho * Vp;
-  f[3 * i] = (double)(fd0 + (-rv * (T)fp.g[0]) + fg0);
-  f[3 * i + 1] = (double)(fd1 + (-rv * (T)fp.g[1]) + fg1);
-  f[3 * i + 2] = (double)(fd2 + (-rv * (T)fp.g[2]) + fg2);
+  const T rv = (MIX ? (T)fp.rho32 : (T)fp.rho) * Vp;
+  const T g0 = MIX ? (T)fp.g32[0] : (T)fp.g[0];
+  const T g1 = MIX ? (T)fp.g32[1] : (T)fp.g[1];
+  const T g2 = MIX ? (T)fp.g32[2] : (T)fp.g[2];
+  f[3 * i] = out_double<T>(fd0 + (-rv * g0) + fg0);
+  f[3 * i + 1] = out_double<T>(fd1 + (-rv * g1) + fg1);
+  f[3 * i + 2] = out_double<T>(fd2 + (-rv * g2) + fg2);
   if (f_drag) {
-    f_drag[3 * i] = (double)fd0;
-    f_drag[3 * i + 1] = (double)fd1;
-    f_drag[3 * i + 2] = (double)fd2;
+    f_drag[3 * i] = out_double<T>(fd0);
+    f_drag[3 * i + 1] = out_double<T>(fd1);
+    f_drag[3 * i + 2] = out_double<T>(fd2);
   }
-  if (S_elem) {
-    int64_t e = ie[0] + (int64_t)m.ne[0] * (ie[1] + (int64_t)m.ne[1] * ie[2]);
+  if (ps.S) {
+    // the particle's share of the fluid source: its drag (none when the
+    // fluid-side drag form carries it through beta_e), plus for model B the
+    // pressure (and shear) part; and its drag coefficient
     T s0 = fd0, s1 = fd1, s2 = fd2;
-    if (fp.fluid_drag) {  // the drag goes to the fluid through beta_e and the mean u_p
-      s0 = s1 = s2 = (T)0;
-      atomicAdd(acc.B + e, (double)coef);
-      atomicAdd(acc.U + 3 * e, u_p[3 * i]);
-      atomicAdd(acc.U + 3 * e + 1, u_p[3 * i + 1]);
-      atomicAdd(acc.U + 3 * e + 2, u_p[3 * i + 2]);
-      atomicAdd(acc.N + e, 1.0);
-    }
+    if (fp.fluid_drag) s0 = s1 = s2 = (T)0;
     if (fp.vans_model == 1) {
       s0 += fg0;
       s1 += fg1;
       s2 += fg2;
     }
-    atomicAdd(S_elem + 3 * e, (double)s0);
-    atomicAdd(S_elem + 3 * e + 1, (double)s1);
-    atomicAdd(S_elem + 3 * e + 2, (double)s2);
+    double* o = ps.S + 4 * i;
+    o[0] = out_double<T>(s0);
+    o[1] = out_double<T>(s1);
+    o[2] = out_double<T>(s2);
+    o[3] = out_double<T>(coef);
+    ps.elem[i] = (int32_t)(ie[0] + (int64_t)m.ne[0] * (ie[1] + (int64_t)m.ne[1] * ie[2]));
+    // the largest magnitudes fix the scale of the fixed-point sums (the bits
+    // of non-negative doubles order like their values)
+    auto mag = [](double v) {
+      return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+    };
+    unsigned long long mx[3] = {max(mag(o[0]), max(mag(o[1]), mag(o[2]))), mag(o[3]),
+                                max(mag(up0), max(mag(up1), mag(up2)))};
+    // one atomic per warp and class.  Only the exponent field sets the
+    // scale, so the high 32 bits (sign, exponent, leading significand bits)
+    // are reduced over the lanes still here (a thread past n or outside the
+    // mesh has returned) by the warp's max reduction
+    const unsigned act = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int nc = fp.fluid_drag ? 3 : 1;
+    for (int c = 0; c < nc; ++c) {
+      const unsigned hi = __reduce_max_sync(act, (unsigned)(mx[c] >> 32));
+      if (lane == __ffs(act) - 1) atomicMax(ps.maxbits + c, (unsigned long long)hi << 32);
+    }
   }
 }
 
@@ -473,28 +673,33 @@ template <int K, int KP, typename T>
 static void launch_forces_t(const MeshDev& m, const Tables& t, const ForceParams& fp,
                             int64_t n, const double* x, const double* r, const double* u_p,
                             const double* u_nodal, const double* p_nodal,
-                            const double* eps_nodal, double* f, double* f_drag, double* S,
-                            SemiAcc acc, DevStatus* st, cudaStream_t s) {
+                            const double* eps_nodal, double* f, double* f_drag, PartSrc ps,
+                            DevStatus* st, cudaStream_t s) {
   int bs = 128;
-  k_forces<K, KP, T><<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(
-      m, t, fp, n, x, r, u_p, u_nodal, p_nodal, eps_nodal, f, f_drag, S, acc, st);
+  const unsigned nb = (unsigned)((n + bs - 1) / bs);
+  if (fp.shear)
+    k_forces<K, KP, T, true><<<nb, bs, 0, s>>>(m, t, fp, n, x, r, u_p, u_nodal, p_nodal,
+                                               eps_nodal, f, f_drag, ps, st);
+  else
+    k_forces<K, KP, T, false><<<nb, bs, 0, s>>>(m, t, fp, n, x, r, u_p, u_nodal, p_nodal,
+                                                eps_nodal, f, f_drag, ps, st);
   count_launches(1);
 }
 
 cudaError_t launch_forces(const MeshDev& m, const Tables& t, int precision, const ForceParams& fp,
                           int64_t n, const double* x, const double* r, const double* u_p,
                           const double* u_nodal, const double* p_nodal,
-                          const double* eps_nodal, double* f, double* f_drag, double* S_elem,
-                          SemiAcc acc, DevStatus* st, cudaStream_t s) {
+                          const double* eps_nodal, double* f, double* f_drag, PartSrc ps,
+                          DevStatus* st, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
 #define CFDEM_FORCES(K, KP)                                                                  \
   if (m.k == K && m.kp == KP) {                                                              \
     if (precision == 0)                                                                      \
       launch_forces_t<K, KP, double>(m, t, fp, n, x, r, u_p, u_nodal, p_nodal, eps_nodal, f, \
-                                     f_drag, S_elem, acc, st, s);                            \
+                                     f_drag, ps, st, s);                                     \
     else                                                                                     \
       launch_forces_t<K, KP, float>(m, t, fp, n, x, r, u_p, u_nodal, p_nodal, eps_nodal, f,  \
-                                    f_drag, S_elem, acc, st, s);                             \
+                                    f_drag, ps, st, s);                                      \
     return cudaGetLastError();                                                               \
   }
   CFDEM_FORCES(1, 1)
@@ -508,6 +713,109 @@ cudaError_t launch_forces(const MeshDev& m, const Tables& t, int precision, cons
   CFDEM_FORCES(2, 3)
 #undef CFDEM_FORCES
   return cudaErrorInvalidValue;
+}
+
+// Per-element sums of the particle records as exact fixed-point sums: each
+// value v of a class (source components, drag coefficients, particle
+// velocity components) becomes the integer t = round(v 2^E), E = 61 - the
+// exponent of the class's largest |v|, so |t| < 2^62 and the rounding is
+// below 2^-62 of that largest value; t is split as hi 2^31 + lo (lo in
+// [0, 2^31)) and hi, lo are added by 64-bit integer atomics, which cannot
+// overflow for fewer than 2^31 particles.  Integer sums do not depend on the
+// order of the additions, so the source has the same bits on every run.
+
+// exponent field of the largest value of a class -> the scale exponent E
+__device__ __forceinline__ int fixed_scale(unsigned long long maxbits) {
+  const int ex = (int)((maxbits >> 52) & 0x7ff);
+  return ex == 0 ? 0 : 1084 - ex;  // 61 - (ex - 1023)
+}
+
+// round(v 2^E) by integer operations on the bits of v (rounding half away
+// from zero); zero and subnormals give 0
+__device__ __forceinline__ long long fixed_of(double v, int E) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (ex == 0) return 0;
+  const long long M = (long long)((b & 0xfffffffffffffull) | 0x10000000000000ull);
+  const int sh = ex - 1075 + E;  // v = M 2^(ex - 1075)
+  long long t;
+  if (sh >= 0)
+    t = M << sh;  // sh <= 9 for the largest value: |t| < 2^62
+  else if (sh > -63)
+    t = (M + (1ll << (-sh - 1))) >> (-sh);
+  else
+    t = 0;
+  return (b >> 63) ? -t : t;
+}
+
+__device__ __forceinline__ void fixed_add(long long* acc, double v, int E) {
+  const long long t = fixed_of(v, E);
+  const long long hi = t >> 31;            // floor(t / 2^31)
+  const long long lo = t - (hi << 31);     // in [0, 2^31)
+  atomicAdd(reinterpret_cast<unsigned long long*>(acc), (unsigned long long)hi);
+  atomicAdd(reinterpret_cast<unsigned long long*>(acc + 1), (unsigned long long)lo);
+}
+
+__device__ __forceinline__ double fixed_value(const long long* acc, int E) {
+  return ldexp((double)acc[0] * 2147483648.0 + (double)acc[1], -E);
+}
+
+// acc64 per element: S (3 x 2), B (2), U (3 x 2), N (1), pad
+constexpr int kSrcAcc = 16;
+
+__global__ void k_source_accumulate(int64_t n, PartSrc ps, const double* __restrict__ u_p,
+                                    int semi, long long* __restrict__ acc64) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t e = ps.elem[i];
+  if (e < 0) return;
+  long long* a = acc64 + (int64_t)e * kSrcAcc;
+  const double* o = ps.S + 4 * i;
+  const int E0 = fixed_scale(ps.maxbits[0]);
+  fixed_add(a, o[0], E0);
+  fixed_add(a + 2, o[1], E0);
+  fixed_add(a + 4, o[2], E0);
+  if (semi) {
+    fixed_add(a + 6, o[3], fixed_scale(ps.maxbits[1]));
+    const int E2 = fixed_scale(ps.maxbits[2]);
+    fixed_add(a + 8, u_p[3 * i], E2);
+    fixed_add(a + 10, u_p[3 * i + 1], E2);
+    fixed_add(a + 12, u_p[3 * i + 2], E2);
+    atomicAdd(reinterpret_cast<unsigned long long*>(a + 14), 1ull);
+  }
+}
+
+__global__ void k_source_finalize(int64_t E, PartSrc ps, int semi,
+                                  const long long* __restrict__ acc64,
+                                  double* __restrict__ S_elem, SemiAcc acc) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const long long* a = acc64 + e * kSrcAcc;
+  const int E0 = fixed_scale(ps.maxbits[0]);
+  S_elem[3 * e] = fixed_value(a, E0);
+  S_elem[3 * e + 1] = fixed_value(a + 2, E0);
+  S_elem[3 * e + 2] = fixed_value(a + 4, E0);
+  if (semi) {
+    acc.B[e] = fixed_value(a + 6, fixed_scale(ps.maxbits[1]));
+    const int E2 = fixed_scale(ps.maxbits[2]);
+    acc.U[3 * e] = fixed_value(a + 8, E2);
+    acc.U[3 * e + 1] = fixed_value(a + 10, E2);
+    acc.U[3 * e + 2] = fixed_value(a + 12, E2);
+    acc.N[e] = (double)a[14];
+  }
+}
+
+cudaError_t launch_source_sum(const MeshDev& m, int64_t n, PartSrc ps, const double* u_p,
+                              int semi, long long* acc64, double* S_elem, SemiAcc acc,
+                              cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(acc64, 0, sizeof(long long) * kSrcAcc * m.E, s);
+  if (e != cudaSuccess) return e;
+  if (n > 0)
+    k_source_accumulate<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, ps, u_p, semi, acc64);
+  k_source_finalize<<<(unsigned)((m.E + 255) / 256), 256, 0, s>>>(m.E, ps, semi, acc64, S_elem,
+                                                                  acc);
+  count_launches(n > 0 ? 2 : 1);
+  return cudaGetLastError();
 }
 
 // ----------------------------------------------------------------------------

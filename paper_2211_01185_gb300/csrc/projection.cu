@@ -971,6 +971,15 @@ int pick_shape(const MeshDev& m) {
   });
 }
 
+bool shape_fits(const MeshDev& m, int shape) {
+  return with_k(m, [&](auto kc) {
+    constexpr int K = decltype(kc)::value;
+    const size_t sm[kShapes] = {apply_smem<K, Shape0, double>(), apply_smem<K, Shape1, double>(),
+                                apply_smem<K, Shape2, double>()};
+    return shape >= 0 && shape < kShapes && sm[shape] <= 200 * 1024;
+  });
+}
+
 int cg_blocks(const MeshDev& m) {
   int na = 0;
   dim3 g0 = apply_grid_s<Shape0>(m), g1 = apply_grid_s<Shape1>(m), g2 = apply_grid_s<Shape2>(m);

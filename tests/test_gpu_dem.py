@@ -60,6 +60,20 @@ def test_matches_oracle(precision):
     assert np.abs(ref.v - v).max() > 1e-3        # the contacts did act
 
 
+def test_mixed_single_substep_within_1e_5():
+    """One sub-step of the compressed bed: the mixed path's FP32 contact
+    forces move the state within 1e-5 of the oracle.  Over 60 sub-steps the
+    contact network amplifies that rounding, which is why the trajectory
+    above is held to 2e-5."""
+    x, v, w, r, fe, p = _bed()
+    ref = D.State(x, v, w, r)
+    assert ref.step(p, 2e-6, 1, f_ext=fe) == 0
+    gx, gv, gw = _run_gpu(x, v, w, r, fe, p, 2e-6, [1], 1)
+    assert rel_err(gv - v, ref.v - v) <= 1e-5
+    assert rel_err(gw - w, ref.w - w) <= 1e-5
+    assert rel_err(gx - x, ref.x - x) <= 1e-5
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_history_carries_over_calls_and_is_reproducible(precision):
     x, v, w, r, fe, p = _bed(seed=6)

@@ -531,3 +531,39 @@ def test_adjoint_rejects_volume_conserving_qcm():
                                     cf._ptr(dev(case["p_nodal"])), cf._ptr(z(m.n_nodes())),
                                     None, None, None, cf._ptr(z(n, 3)), None)
         assert st == cf.EINVAL
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("fluid_drag", [0, 1])
+def test_fluid_source_is_bit_reproducible(precision, fluid_drag):
+    """The per-element fluid source is summed in a fixed order (no atomics):
+    two coupling steps on the same inputs give the same bits, and so does a
+    standalone forces call (which bins the particles itself)."""
+    c = CASES[3]
+    case = _case(*c, overlap_ok=False)
+    m = _mesh(case)
+    n = case["x"].shape[0]
+    prm = dict(case["params"], precision=precision, fluid_drag=fluid_drag, vans_model=1)
+    args = [dev(case[k]) for k in ("x", "r", "u_p", "u_nodal", "p_nodal")]
+    outs = []
+    with _ctx(case, **prm) as ctx:
+        for _ in range(2):
+            eps_h, f = _zeros(m.n_nodes()), _zeros(n, 3)
+            Fe, Fq = _zeros(m.n_elem, 3), _zeros(m.n_elem, m.Q, 3)
+            cf.cfdem_coupling_step(ctx.h, n, *args, eps_h, f, None, Fe, Fq)
+            cf.cfdem_synchronize(ctx.h)
+            outs.append((host(Fe), host(Fq), host(eps_h)))
+        Fe2 = _zeros(m.n_elem, 3)
+        f2 = _zeros(n, 3)
+        cf.cfdem_forces(ctx.h, n, *args, dev(outs[0][2]), f2, None, Fe2, None)
+        cf.cfdem_synchronize(ctx.h)
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    assert np.array_equal(host(Fe2), outs[0][0])
+    ref = O.forces(m, prm, case["x"], case["r"], case["u_p"], case["u_nodal"],
+                   case["p_nodal"], outs[0][2])
+    if fluid_drag:
+        _, F_ref, _ = O.fluid_source_semi(m, 1, case["x"], case["u_p"], case["u_nodal"],
+                                          ref["f_drag"], ref["f_gradp"])
+    else:
+        F_ref, _ = O.fluid_source(m, 1, case["x"], ref["f_drag"], ref["f_gradp"])
+    assert rel_err(outs[0][0], F_ref) <= TOL[precision]

@@ -41,9 +41,11 @@ int main(void) {
   P(cfdem_params, precision); P(cfdem_params, cg_rtol); P(cfdem_params, cg_maxit);
   P(cfdem_params, eps_floor); P(cfdem_params, pressure_degree); P(cfdem_params, max_radius);
   P(cfdem_params, bin_edge); P(cfdem_params, cg_precond); P(cfdem_params, shear_force); P(cfdem_params, fluid_drag); P(cfdem_params, qcm_conserve);
+  P(cfdem_params, autotune);
   P(cfdem_stats, cg_iterations); P(cfdem_stats, cg_relres); P(cfdem_stats, nb);
   P(cfdem_stats, bin_edge); P(cfdem_stats, qcm_radius); P(cfdem_stats, n_pnodes);
   P(cfdem_stats, stage_ms); P(cfdem_stats, kernel_launches); P(cfdem_stats, precond);
+  P(cfdem_stats, tile_shape); P(cfdem_stats, tuned); P(cfdem_stats, tune_ms);
   printf("cfdem_bed_io %zu\n", sizeof(cfdem_bed_io));
   P(cfdem_bed_io, n); P(cfdem_bed_io, x); P(cfdem_bed_io, p_nodal); P(cfdem_bed_io, eps_nodal);
   P(cfdem_bed_io, F_q); P(cfdem_bed_io, host_x); P(cfdem_bed_io, host_p_nodal);
@@ -102,3 +104,24 @@ def test_static_pcm_rejects_bad_meshes_on_the_host(lib):
                                              fake, fake, fake) == cf.EINVAL
     assert cf.cfdem_pcm_void_fraction_static(good_o, good_e, (4, 4, 4), 4, 1,
                                              fake, fake, fake) == cf.EINVAL
+
+
+def test_mapped_mesh_rejects_bad_meshes_on_the_host(lib):
+    # checked before any CUDA call: an index past the nodes, a non-finite
+    # coordinate, a bad degree or margin
+    import numpy as np
+    from paper_2211_01185_gb300 import synth
+    mesh = synth.make_cylinder_mesh(0.05, 0.08, 2, 1, 1, 2)
+    conn, nodes = mesh["conn"], mesh["nodes"]
+    bad = conn.copy()
+    bad[0, 0] = nodes.shape[0]
+    with pytest.raises(cf.CfdemError):
+        cf.MappedMesh(2, bad, nodes)
+    nn = nodes.copy()
+    nn[3, 1] = np.nan
+    with pytest.raises(cf.CfdemError):
+        cf.MappedMesh(2, conn, nn)
+    with pytest.raises(cf.CfdemError):
+        cf.MappedMesh(4, conn, nodes)
+    with pytest.raises(cf.CfdemError):
+        cf.MappedMesh(2, conn, nodes, margin=-0.5)

@@ -187,3 +187,29 @@ def test_shear_force_primal_and_tangents(k):
                             c["u_nodal"] + s * du, c["p_nodal"]) for s in (1e-6, -1e-6))
     assert _rel(out["f_shear"].t, (sh(p) - sh(q)) / 2e-6) <= 2e-6
     assert _rel(out["f"].t, fd["f"]) <= 2e-6
+
+
+def test_sparse_qcm_tangent_equals_all_pairs():
+    """qcm_dual_rows (value from the C oracle, tangent from the moved
+    particles only) gives the all-pairs dual void fraction along a direction
+    that moves a few particles, and so the same step derivative."""
+    c = synth.make_random_case(41, n_el=(3, 4, 3), k=2, n=60, extent=(0.03, 0.04, 0.03),
+                               overlap_ok=False)
+    m = O.Mesh(c["origin"], c["extent"], c["n_el"], c["k"])
+    rng = np.random.default_rng(5)
+    dx = np.zeros_like(c["x"])
+    rows = rng.choice(c["x"].shape[0], 5, replace=False)
+    dx[rows] = rng.standard_normal((5, 3))
+    du = rng.standard_normal(c["u_nodal"].shape)
+    R = O.default_qcm_radius(m)
+    a = J.qcm_dual(m, R, J.Dual(c["x"], dx), c["r"])
+    b = J.qcm_dual_rows(m, R, c["x"], c["r"], dx)
+    assert np.allclose(b.v, a.v, rtol=0, atol=1e-14)
+    assert np.allclose(b.t, a.t, rtol=0, atol=1e-12 * np.abs(a.t).max())
+    assert np.abs(a.t).max() > 0
+    full = J.coupling_jvp(m, c["params"], c["x"], c["r"], c["u_p"], c["u_nodal"], c["p_nodal"],
+                          dx, du)
+    sp = J.coupling_jvp(m, c["params"], c["x"], c["r"], c["u_p"], c["u_nodal"], c["p_nodal"],
+                        dx, du, sparse_qcm=True)
+    for key in ("eps_h", "f", "f_drag"):
+        assert np.allclose(sp[key].t, full[key].t, rtol=0, atol=1e-11 * np.abs(full[key].t).max())
