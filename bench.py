@@ -826,6 +826,40 @@ def run_dem(env, steps, warmup):
             "max_displacement_m": drift, "clocks": per[1]["clocks"]}
 
 
+def run_profile(args):
+    """Eager coupling steps of one bed for ncu captures: the autotuner off and
+    the bin edge given (the one the tuned bench run reports), so that a
+    capture filtered by kernel name sees the step's own launches only."""
+    import torch
+    from paper_2211_01185_gb300 import build as B
+    from paper_2211_01185_gb300 import cfdem as cf
+    from paper_2211_01185_gb300 import synth
+    B.build()
+    w = synth.make_workload(args.workload)
+    n = w["x"].shape[0]
+    dev = torch.device("cuda", 0)
+    t = lambda a: torch.as_tensor(a, dtype=torch.float64).to(dev).contiguous()  # noqa: E731
+    x, r, up, un, pn = (t(w[k]) for k in ("x", "r", "u_p", "u_nodal", "p_nodal"))
+    prec = 0 if args.precision == "fp64" else 1
+    prm = dict(w["params"], precision=prec, max_radius=float(w["r"].max()),
+               cg_rtol=1e-13 if prec == 0 else 1e-12, autotune=0, bin_edge=args.bin_edge)
+    with cf.Context(w["origin"], w["extent"], w["n_el"], w["k"], prm) as ctx:
+        st = ctx.stats()
+        eps = torch.zeros(st.n_nodes, dtype=torch.float64, device=dev)
+        f = torch.empty((n, 3), dtype=torch.float64, device=dev)
+        fd = torch.empty_like(f)
+        Fe = torch.empty((st.n_elem, 3), dtype=torch.float64, device=dev)
+        for _ in range(args.steps):
+            eps.zero_()
+            cf.cfdem_coupling_step(ctx.h, n, x, r, up, un, pn, eps, f, fd, Fe)
+        cf.cfdem_synchronize(ctx.h)
+        st = ctx.stats()
+    print(json.dumps({"profile": args.workload, "precision": args.precision,
+                      "bins": list(st.nb), "bin_edge_m": list(st.bin_edge),
+                      "tile_shape": st.tile_shape, "cg_iterations": st.cg_iterations}))
+    return 0
+
+
 def _summary(r):
     """The keys of a secondary workload that the bench line carries."""
     keep = ("workload", "mesh", "particles", "nodes", "value", "ms_per_step", "steps",
@@ -852,10 +886,18 @@ def main():
                     help="a single bed (the default is the headline Q2 bed plus every other "
                          "workload in brief); batch64: the 64-bed ensemble; adjoint5: forward "
                          "step + adjoint; dem: 10 DEM sub-steps per step on the Q2 bed")
+    ap.add_argument("--profile", action="store_true",
+                    help="eager steps of one bed only (for ncu): --steps steps, autotuner "
+                         "off, bins of edge --bin-edge (0: R + largest radius)")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
+                    help="precision of the --profile run")
+    ap.add_argument("--bin-edge", type=float, default=0.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile:
+        return run_profile(args)
 
     env = Env(use_dist=True)
     if args.workload == "batch64":

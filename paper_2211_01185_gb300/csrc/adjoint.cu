@@ -276,8 +276,10 @@ k_adj_interp_q(MeshDev m, Tables tb, const double* __restrict__ lam, double* __r
   constexpr int N = K + 1, Q = N * N * N;
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= m.E) return;
-  int ex = (int)(e % m.ne[0]), ey = (int)((e / m.ne[0]) % m.ne[1]),
-      ez = (int)(e / ((int64_t)m.ne[0] * m.ne[1]));
+  const int e32 = (int)e, exy = m.ne[0] * m.ne[1];  // E < 2^31
+  int ez = e32 / exy;
+  int ey = (e32 - ez * exy) / m.ne[0];
+  int ex = e32 - ez * exy - ey * m.ne[0];
   int64_t nx = m.nn[0], nxy = (int64_t)m.nn[0] * m.nn[1];
   int64_t base = (int64_t)ex * K + nx * ((int64_t)ey * K) + nxy * ((int64_t)ez * K);
   double u[N][N][N], v[N][N][N];

@@ -139,6 +139,7 @@ ForceParams force_params(const cfdem_ctx* c) {
     fp.x0_lo[a] = (float)(m.x0[a] - (double)fp.x0_hi[a]);
     fp.inv_h_hi[a] = (float)fp.inv_h[a];
     fp.inv_h_lo[a] = (float)(fp.inv_h[a] - (double)fp.inv_h_hi[a]);
+    fp.nem1f[a] = (float)(m.ne[a] - 1);
     // the bounds of in_box, rounded as the device rounds them
     volatile double slack = 1e-12 * m.L[a];
     volatile double top = m.x0[a] + m.L[a];
@@ -303,6 +304,20 @@ BinDev bin_grid(const MeshDev& m, double edge) {
     if (tot <= (int64_t)1 << 26) break;
     edge *= 1.5;
   }
+  double far = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    b.x0_hi[a] = (float)m.x0[a];
+    b.x0_lo[a] = (float)(m.x0[a] - (double)b.x0_hi[a]);
+    b.inv_be_hi[a] = (float)b.inv_be[a];
+    b.inv_be_lo[a] = (float)(b.inv_be[a] - (double)b.inv_be_hi[a]);
+    volatile double slack = 1e-12 * m.L[a];
+    volatile double top = m.x0[a] + m.L[a];
+    b.box_lo_key[a] = order_key(m.x0[a] - slack);
+    b.box_hi_key[a] = order_key(top + slack);
+    b.nm1f[a] = (float)(b.nb[a] - 1);
+    far = std::fmax(far, (std::fabs(m.x0[a]) + m.L[a]) * b.inv_be[a]);
+  }
+  b.loc32 = far < 67108864.0 ? 1 : 0;  // |x| / be < 2^26: see elem_axis_df
   return b;
 }
 

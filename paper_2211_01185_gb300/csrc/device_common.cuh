@@ -5,6 +5,7 @@
 #include <cstdint>
 
 #include "internal.h"
+#include "df64.cuh"
 
 namespace cfdem {
 
@@ -67,6 +68,18 @@ __device__ __forceinline__ int bin_axis_fast(double x, double x0, double be, dou
   return (int)f;
 }
 
+// bin_axis_fast behind a real call, for the rare particles near a bin face
+// (inlined, its FP64 instructions would be predicated into every thread)
+static __device__ __noinline__ int bin_axis_slow(double x, double x0, double be, double inv_be, int nb) {
+  return bin_axis_fast(x, x0, be, inv_be, nb);
+}
+
+// elem_axis_fast behind a real call, for the same reason
+static __device__ __noinline__ int elem_axis_slow(double x, double x0, double h, double inv_h, int N,
+                                           double* xi) {
+  return elem_axis_fast(x, x0, h, inv_h, N, xi);
+}
+
 // the integer key of a double whose signed order is the order of the values
 // (NaNs fall outside every finite interval); the host computes the same keys
 // for the in_box bounds, so that the mixed path tests the box without FP64
@@ -79,6 +92,40 @@ __device__ __forceinline__ long long order_key(double v) {
 __device__ __forceinline__ bool in_box_key(double v, long long lo, long long hi) {
   const long long k = order_key(v);
   return k >= lo && k <= hi;
+}
+
+// floor of t for 0 <= t < 2^22 and its integer value with FP32 additions
+// only (adding 2^23 rounds t to an integer held in the low significand
+// bits); conversions between integer and floating types issue on this
+// part's narrow FP64 pipe
+__device__ __forceinline__ float floor_small(float t, int* k) {
+  const float y = t + 8388608.0f;
+  float r = y - 8388608.0f;
+  int i = __float_as_int(y) - 0x4B000000;
+  if (r > t) {
+    r -= 1.0f;
+    i -= 1;
+  }
+  *k = i;
+  return r;
+}
+
+// Cell index floor(t), t = (x - x0) / edge, on a grid of n cells, from the
+// double-float split of x (t to ~2^-46 |x| / edge), and the fraction t -
+// floor(t) as double-float.  Returns -1 when t lies within 1e-5 of a cell
+// face or outside [0, n): there the caller's FP64 rule decides, so the cell
+// is the one the IEEE definition gives.  nm1f = n - 1 as a float.
+__device__ __forceinline__ int cell_df(double x, float x0_hi, float x0_lo, float inv_hi,
+                                       float inv_lo, float nm1f, df64* frac) {
+  const df64 d = df_from_double_int(x) - df64(x0_hi, x0_lo);
+  const df64 t = d * df64(inv_hi, inv_lo);
+  if (!(t.hi >= 0.0f && t.hi < nm1f + 1.0f)) return -1;
+  int i;
+  const float fl = floor_small(t.hi, &i);
+  const float fr = (t.hi - fl) + t.lo;
+  if (!(fr >= 1e-5f && fr <= 1.0f - 1e-5f && fl <= nm1f)) return -1;
+  if (frac) *frac = df_renorm(t.hi - fl, t.lo);  // t.hi - fl is exact
+  return i;
 }
 
 __device__ __forceinline__ void report_bad(DevStatus* st, int64_t i) {

@@ -44,24 +44,34 @@ __device__ __forceinline__ df64 df_from_double(double v) {
   return df64(h, (float)(v - (double)h));
 }
 
-// The same split with integer operations, for bulk conversions: on this part
-// every FP64 instruction (conversions included) runs at 1/61 of the FP32
-// rate.  hi takes the sign, the exponent and the leading 24 significand bits
-// of v (truncated), lo the remaining 29 bits as a float (rounded to 24 by
-// the integer-to-float conversion), so hi + lo = v to 2^-48 |v| and
-// |lo| < ulp(hi).  Zero is split as zero; a v whose hi or lo would not be a
-// normal float (|v| < 2^-74 or |v| >= 2^128, subnormals, inf, nan) takes the
-// FP64 conversion.
+// The same split without FP64 instructions, for bulk conversions: on this
+// part every FP64 instruction -- and the conversions between integer, FP32
+// and FP64, and bit scans -- issue on a narrow pipe at about 1/64 of the
+// FP32 rate.  hi takes the sign, the exponent and the leading 24
+// significand bits of v (truncated); lo the remaining 29 bits m times
+// 2^(E - 1075), m made a float by FP32 arithmetic on exact floats 2^23 + k
+// (k = m / 64 and m mod 64, each held in the low significand bits) and
+// rounded once, so hi + lo = v to 2^-48 |v| and |lo| < ulp(hi).  Zero is
+// split as zero; a v whose hi or lo would not be a normal float (|v| <
+// 2^-74 or |v| >= 2^128, subnormals, inf, nan) takes the FP64 conversion.
+// the FP64 conversion of the rare values, as a real call: inlined, the
+// compiler predicates it into every split and its FP64 instructions issue
+// on the narrow pipe even when not taken
+static __device__ __noinline__ df64 df_from_double_slow(double v) { return df_from_double(v); }
+
 __device__ __forceinline__ df64 df_from_double_int(double v) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
   const unsigned sign = (unsigned)(bits >> 32) & 0x80000000u;
   if ((bits << 1) == 0ull) return df64(__uint_as_float(sign), 0.f);
   const int E = (int)((bits >> 52) & 0x7ff);
-  if (E < 949 || E > 1150) return df_from_double(v);
+  if (E < 949 || E > 1150) return df_from_double_slow(v);
   const float hi = __uint_as_float(sign | ((unsigned)(E - 896) << 23) |
                                    ((unsigned)(bits >> 29) & 0x7fffffu));
-  const float scale = __uint_as_float((unsigned)(E - 948) << 23);  // 2^(E - 1075)
-  const float lo = (float)(unsigned)(bits & 0x1fffffffull) * scale;
+  const unsigned m = (unsigned)(bits & 0x1fffffffull);
+  const float mh = __uint_as_float(0x4B000000u | (m >> 6)) - 8388608.0f;   // exact
+  const float ml = __uint_as_float(0x4B000000u | (m & 63u)) - 8388608.0f;  // exact
+  const float mf = fmaf(mh, 64.0f, ml);                                   // m, rounded
+  const float lo = mf * __uint_as_float((unsigned)(E - 948) << 23);       // 2^(E - 1075)
   return df64(hi, __uint_as_float(__float_as_uint(lo) | sign));
 }
 

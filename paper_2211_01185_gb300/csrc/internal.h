@@ -54,6 +54,14 @@ struct BinDev {
   double be[3];      // bin edge per axis, L / nb
   double inv_be[3];  // 1 / be (IEEE division on the host, as on the device)
   int64_t nbins;
+  // the same grid for location without FP64 instructions: origin and 1/be
+  // as double-float, the in_box bounds as order-preserving integer keys of
+  // their bits, and loc32 = 0 where the box is too far from the origin for
+  // the double-float margin (then the FP64 rule bins every particle)
+  float x0_hi[3], x0_lo[3], inv_be_hi[3], inv_be_lo[3];
+  long long box_lo_key[3], box_hi_key[3];
+  float nm1f[3];  // nb - 1 as float
+  int loc32;
 };
 
 // Device-side status words of one context (one allocation).
@@ -129,6 +137,7 @@ struct ForceParams {
   // FP32 margin, then the FP64 rule locates every particle)
   float rho32, mu32, g32[3], eps_floor32, inv_h32[3];
   float x0_hi[3], x0_lo[3], inv_h_hi[3], inv_h_lo[3];
+  float nem1f[3];  // elements per axis - 1, as float
   int loc32;
   // in_box bounds x0 - 1e-12 L and (x0 + L) + 1e-12 L as order-preserving
   // integer keys of their bits (compared without FP64 instructions)
@@ -169,7 +178,8 @@ cudaError_t launch_forces(const MeshDev& m, const Tables& t, int precision, cons
                           DevStatus* st, cudaStream_t s);
 // per-element sums of the records: S_elem[E][3] and, with semi, the drag
 // coefficients, particle velocities and counts into acc.  The sums are exact
-// fixed-point sums (acc64: 16 int64 per element of scratch), so their bits
+// fixed-point sums (acc64: 16 int64 per element of scratch, 6 of them used
+// without the fluid-side drag), so their bits
 // do not depend on the order of the particles.
 cudaError_t launch_source_sum(const MeshDev& m, int64_t n, PartSrc ps, const double* u_p,
                               int semi, long long* acc64, double* S_elem, SemiAcc acc,

@@ -66,12 +66,21 @@ __global__ void k_bin_count(MeshDev m, BinDev b, int64_t n, const double* __rest
   double ri = 0.0;
   if (valid) {
     double p[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
-    if (!(in_box(p[0], m.x0[0], m.L[0]) && in_box(p[1], m.x0[1], m.L[1]) &&
-          in_box(p[2], m.x0[2], m.L[2])))
+    // the box test on integer keys, the bin from a double-float split (the
+    // FP64 rule near a bin face): no FP64 instruction for most particles
+    if (!(in_box_key(p[0], b.box_lo_key[0], b.box_hi_key[0]) &&
+          in_box_key(p[1], b.box_lo_key[1], b.box_hi_key[1]) &&
+          in_box_key(p[2], b.box_lo_key[2], b.box_hi_key[2])))
       report_bad(st, i);
-    int bx = bin_axis_fast(p[0], m.x0[0], b.be[0], inv_be[0], b.nb[0]);
-    int by = bin_axis_fast(p[1], m.x0[1], b.be[1], inv_be[1], b.nb[1]);
-    int bz = bin_axis_fast(p[2], m.x0[2], b.be[2], inv_be[2], b.nb[2]);
+    int bq[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      bq[a] = b.loc32 ? cell_df(p[a], b.x0_hi[a], b.x0_lo[a], b.inv_be_hi[a], b.inv_be_lo[a],
+                                b.nm1f[a], nullptr)
+                      : -1;
+      if (bq[a] < 0) bq[a] = bin_axis_slow(p[a], m.x0[a], b.be[a], inv_be[a], b.nb[a]);
+    }
+    const int bx = bq[0], by = bq[1], bz = bq[2];
     id = bx + b.nb[0] * (by + b.nb[1] * bz);
     bin_of[i] = id;
     if (r) ri = r[i];
@@ -238,15 +247,19 @@ __global__ void k_gather_sorted(MeshDev m, int64_t n, const int32_t* __restrict_
   d.z = p[2];
   d.w = ri;
   reinterpret_cast<P4*>(xs64)[s] = d;
-  float hi[3], lo[3];
+  // float-float copies from integer splits (no FP64 instruction): position
+  // relative to the origin, radius renormalised (hi the nearest float)
+  df64 q[3];
+#pragma unroll
   for (int a = 0; a < 3; ++a) {
-    double rel = p[a] - m.x0[a];
-    hi[a] = (float)rel;
-    lo[a] = (float)(rel - (double)hi[a]);
+    const double o = m.x0[a];  // the origin as a float pair, split the same way
+    q[a] = df_from_double_int(p[a]) - df_from_double_int(o);
   }
+  const df64 rs = df_from_double_int(ri);
+  const df64 rr = df_renorm(rs.hi, rs.lo);
   float4* o = reinterpret_cast<float4*>(xs32) + 2 * s;
-  o[0] = make_float4(hi[0], hi[1], hi[2], (float)ri);
-  o[1] = make_float4(lo[0], lo[1], lo[2], (float)(ri - (double)(float)ri));
+  o[0] = make_float4(q[0].hi, q[1].hi, q[2].hi, rr.hi);
+  o[1] = make_float4(q[0].lo, q[1].lo, q[2].lo, rr.lo);
 }
 
 cudaError_t launch_bin(const MeshDev& m, const BinDev& b, int64_t n, const double* x,
@@ -298,18 +311,12 @@ __device__ __forceinline__ float df_diff(df64 a, df64 b) { return (a.hi - b.hi) 
 __device__ __forceinline__ int elem_axis_mixed(double x, const MeshDev& m, const ForceParams& fp,
                                                int a, df64* xi) {
   if (fp.loc32) {
-    const df64 d = df_from_double_int(x) - df64(fp.x0_hi[a], fp.x0_lo[a]);
-    const df64 t = d * df64(fp.inv_h_hi[a], fp.inv_h_lo[a]);
-    const float fl = floorf(t.hi);
-    const float fr = (t.hi - fl) + t.lo;
-    const int i = (int)fl;
-    if (fr >= 1e-5f && fr <= 1.0f - 1e-5f && i >= 0 && i <= m.ne[a] - 1) {
-      *xi = df_renorm(t.hi - fl, t.lo);  // t.hi - fl is exact
-      return i;
-    }
+    const int i = cell_df(x, fp.x0_hi[a], fp.x0_lo[a], fp.inv_h_hi[a], fp.inv_h_lo[a],
+                          fp.nem1f[a], xi);
+    if (i >= 0) return i;
   }
   double xd;
-  const int i = elem_axis_fast(x, m.x0[a], m.h[a], fp.inv_h[a], m.ne[a], &xd);
+  const int i = elem_axis_slow(x, m.x0[a], m.h[a], fp.inv_h[a], m.ne[a], &xd);
   *xi = df_from_double_int(xd);
   return i;
 }
@@ -760,28 +767,31 @@ __device__ __forceinline__ double fixed_value(const long long* acc, int E) {
   return ldexp((double)acc[0] * 2147483648.0 + (double)acc[1], -E);
 }
 
-// acc64 per element: S (3 x 2), B (2), U (3 x 2), N (1), pad
-constexpr int kSrcAcc = 16;
+// acc64: per element S (3 x 2 integers); then, with the fluid-side drag, a
+// second block of B (2), U (3 x 2), N (1) and a pad per element
+constexpr int kSrcS = 6, kSrcSemi = 10;
 
-__global__ void k_source_accumulate(int64_t n, PartSrc ps, const double* __restrict__ u_p,
-                                    int semi, long long* __restrict__ acc64) {
+__global__ void k_source_accumulate(int64_t n, int64_t E, PartSrc ps,
+                                    const double* __restrict__ u_p, int semi,
+                                    long long* __restrict__ acc64) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int32_t e = ps.elem[i];
   if (e < 0) return;
-  long long* a = acc64 + (int64_t)e * kSrcAcc;
+  long long* a = acc64 + (int64_t)e * kSrcS;
   const double* o = ps.S + 4 * i;
   const int E0 = fixed_scale(ps.maxbits[0]);
   fixed_add(a, o[0], E0);
   fixed_add(a + 2, o[1], E0);
   fixed_add(a + 4, o[2], E0);
   if (semi) {
-    fixed_add(a + 6, o[3], fixed_scale(ps.maxbits[1]));
+    long long* b = acc64 + E * kSrcS + (int64_t)e * kSrcSemi;
+    fixed_add(b, o[3], fixed_scale(ps.maxbits[1]));
     const int E2 = fixed_scale(ps.maxbits[2]);
-    fixed_add(a + 8, u_p[3 * i], E2);
-    fixed_add(a + 10, u_p[3 * i + 1], E2);
-    fixed_add(a + 12, u_p[3 * i + 2], E2);
-    atomicAdd(reinterpret_cast<unsigned long long*>(a + 14), 1ull);
+    fixed_add(b + 2, u_p[3 * i], E2);
+    fixed_add(b + 4, u_p[3 * i + 1], E2);
+    fixed_add(b + 6, u_p[3 * i + 2], E2);
+    atomicAdd(reinterpret_cast<unsigned long long*>(b + 8), 1ull);
   }
 }
 
@@ -790,28 +800,31 @@ __global__ void k_source_finalize(int64_t E, PartSrc ps, int semi,
                                   double* __restrict__ S_elem, SemiAcc acc) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= E) return;
-  const long long* a = acc64 + e * kSrcAcc;
+  const long long* a = acc64 + e * kSrcS;
   const int E0 = fixed_scale(ps.maxbits[0]);
   S_elem[3 * e] = fixed_value(a, E0);
   S_elem[3 * e + 1] = fixed_value(a + 2, E0);
   S_elem[3 * e + 2] = fixed_value(a + 4, E0);
   if (semi) {
-    acc.B[e] = fixed_value(a + 6, fixed_scale(ps.maxbits[1]));
+    const long long* b = acc64 + E * kSrcS + e * kSrcSemi;
+    acc.B[e] = fixed_value(b, fixed_scale(ps.maxbits[1]));
     const int E2 = fixed_scale(ps.maxbits[2]);
-    acc.U[3 * e] = fixed_value(a + 8, E2);
-    acc.U[3 * e + 1] = fixed_value(a + 10, E2);
-    acc.U[3 * e + 2] = fixed_value(a + 12, E2);
-    acc.N[e] = (double)a[14];
+    acc.U[3 * e] = fixed_value(b + 2, E2);
+    acc.U[3 * e + 1] = fixed_value(b + 4, E2);
+    acc.U[3 * e + 2] = fixed_value(b + 6, E2);
+    acc.N[e] = (double)b[8];
   }
 }
 
 cudaError_t launch_source_sum(const MeshDev& m, int64_t n, PartSrc ps, const double* u_p,
                               int semi, long long* acc64, double* S_elem, SemiAcc acc,
                               cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(acc64, 0, sizeof(long long) * kSrcAcc * m.E, s);
+  const int64_t words = m.E * (semi ? kSrcS + kSrcSemi : kSrcS);
+  cudaError_t e = cudaMemsetAsync(acc64, 0, sizeof(long long) * words, s);
   if (e != cudaSuccess) return e;
   if (n > 0)
-    k_source_accumulate<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, ps, u_p, semi, acc64);
+    k_source_accumulate<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, m.E, ps, u_p, semi,
+                                                                    acc64);
   k_source_finalize<<<(unsigned)((m.E + 255) / 256), 256, 0, s>>>(m.E, ps, semi, acc64, S_elem,
                                                                   acc);
   count_launches(n > 0 ? 2 : 1);
@@ -889,9 +902,10 @@ k_fluid_source_semi(MeshDev m, Tables tb, const double* __restrict__ S, SemiAcc 
   double upa[3] = {0.0, 0.0, 0.0};
   if (cnt > 0.0)
     for (int d = 0; d < 3; ++d) upa[d] = acc.U[3 * e + d] / cnt;
-  const int ex = (int)(e % m.ne[0]);
-  const int ey = (int)((e / m.ne[0]) % m.ne[1]);
-  const int ez = (int)(e / ((int64_t)m.ne[0] * m.ne[1]));
+  const int e32 = (int)e, exy = m.ne[0] * m.ne[1];  // E < 2^31
+  const int ez = e32 / exy;
+  const int ey = (e32 - ez * exy) / m.ne[0];
+  const int ex = e32 - ez * exy - ey * m.ne[0];
   const int64_t nx = m.nn[0], nxy = (int64_t)m.nn[0] * m.nn[1];
   const int64_t base = (int64_t)ex * K + nx * ((int64_t)ey * K) + nxy * ((int64_t)ez * K);
   T L[NQ][NQ];  // L[q][a] = l_a(g_q)

@@ -29,6 +29,7 @@
 
 #include "internal.h"
 #include "df64.cuh"
+#include "device_common.cuh"
 
 namespace cfdem {
 
@@ -353,9 +354,13 @@ k_qcm(MeshDev m, QcmParams P, BinDev b, const int32_t* __restrict__ bin_start,
   __syncthreads();
   const int64_t e = blockIdx.x * (int64_t)kQcmWarps + wp;
   if (e >= m.E) return;  // whole warp leaves together
-  const int ex = (int)(e % m.ne[0]);
-  const int ey = (int)((e / m.ne[0]) % m.ne[1]);
-  const int ez = (int)(e / ((int64_t)m.ne[0] * m.ne[1]));
+  // element indices by 32-bit division (E < 2^31; a 64-bit division costs
+  // several times as many instructions)
+  const int e32 = (int)e, exy = m.ne[0] * m.ne[1];
+  const int ez = e32 / exy;
+  const int rxy = e32 - ez * exy;
+  const int ey = rxy / m.ne[0];
+  const int ex = rxy - ey * m.ne[0];
 
   for (int q = lane; q < Q; q += 32) {
     sm.acc[wp][q] = 0.f;
@@ -522,6 +527,252 @@ k_qcm(MeshDev m, QcmParams P, BinDev b, const int32_t* __restrict__ bin_start,
     }
     if (nb_count) nb_count[o + q] = sm.cnt[wp][q];
     if (nb_idsum) nb_idsum[o + q] = sm.ids[wp][q];
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Mixed path, lanes = Gauss points.  One warp per element: the candidates
+// are fetched and culled against the box of the element's Gauss points as in
+// k_qcm, each kept one written to shared memory once with its constants
+// (R + r, (R + r)^2, (R - r)^2, the volume of the smaller sphere, the
+// volume-conserving weight); then every candidate is broadcast to the lanes,
+// each lane tests its own Gauss point (two for Q3; for Q1 four groups of 8
+// lanes take every fourth candidate) and adds the lens volume to a
+// Neumaier-compensated sum in registers.  No hit queue and no scan: the
+// instructions per candidate are a distance, a compare and, for the lanes
+// that hit, the lens volume.  Sums run over the candidates in a fixed order
+// (the Q1 groups combined by a fixed shuffle tree), so results are
+// reproducible.
+
+template <int K>
+struct QcmPtsSmem {
+  static constexpr int Q = (K + 1) * (K + 1) * (K + 1);
+  float4 qrel[Q];                  // Gauss point minus element centre
+  float4 cand[kQcmWarps][64];      // culled candidates: position - centre, R + r
+  float4 cons[kQcmWarps][64];      // (R + r)^2, (R - r)^2, full-overlap volume, weight
+  int32_t slot[kQcmWarps][64];     // their sorted slots
+};
+
+template <int K>
+__global__ void __launch_bounds__(kQcmWarps * 32, 8)
+k_qcm_pts(MeshDev m, QcmParams P, BinDev b, const int32_t* __restrict__ bin_start,
+          const int32_t* __restrict__ perm, const float* __restrict__ xs32,
+          const DevStatus* __restrict__ st, double* __restrict__ eps64,
+          float* __restrict__ eps32, int32_t* __restrict__ nb_count,
+          int64_t* __restrict__ nb_idsum) {
+  constexpr int NQ = K + 1;
+  constexpr int Q = NQ * NQ * NQ;
+  constexpr int G = Q <= 8 ? 4 : 1;     // candidate groups of lanes (Q1)
+  constexpr int PPL = Q > 32 ? 2 : 1;   // Gauss points per lane (Q3)
+  __shared__ QcmPtsSmem<K> sm;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  for (int t = threadIdx.x; t < Q; t += blockDim.x)
+    sm.qrel[t] = make_float4(P.qrel[t][0], P.qrel[t][1], P.qrel[t][2], 0.f);
+  __syncthreads();
+  const int64_t e = blockIdx.x * (int64_t)kQcmWarps + wp;
+  if (e >= m.E) return;  // whole warp leaves together
+  const int e32 = (int)e, exy = m.ne[0] * m.ne[1];  // E < 2^31
+  const int ez = e32 / exy;
+  const int rxy = e32 - ez * exy;
+  const int ey = rxy / m.ne[0];
+  const int ex = rxy - ey * m.ne[0];
+  const bool want_ids = nb_idsum != nullptr;
+  const bool want_counts = nb_count != nullptr || want_ids;
+  // this lane's Gauss points
+  const int grp = G > 1 ? lane / Q : 0;
+  float qx[PPL], qy[PPL], qz[PPL], acc[PPL], cmp[PPL];
+  int cnt[PPL];
+  long long ids[PPL];
+  bool qok[PPL];
+#pragma unroll
+  for (int p = 0; p < PPL; ++p) {
+    const int q = (G > 1 ? lane % Q : lane) + 32 * p;
+    qok[p] = q < Q && grp < G;
+    const float4 g = sm.qrel[qok[p] ? q : 0];
+    qx[p] = g.x;
+    qy[p] = g.y;
+    qz[p] = g.z;
+    acc[p] = cmp[p] = 0.f;
+    cnt[p] = 0;
+    ids[p] = 0;
+  }
+  // element centre relative to the mesh origin, float-float
+  float chx, clx, chy, cly, chz, clz;
+  // (small integers made floats by the 2^23 trick: no conversion instruction)
+  const float fex = __int_as_float(0x4B000000 + ex) - 8388608.0f;
+  const float fey = __int_as_float(0x4B000000 + ey) - 8388608.0f;
+  const float fez = __int_as_float(0x4B000000 + ez) - 8388608.0f;
+  chx = ff_two_prod_sum(fex + 0.5f, P.hx_hi, P.hx_lo, &clx);
+  chy = ff_two_prod_sum(fey + 0.5f, P.hy_hi, P.hy_lo, &cly);
+  chz = ff_two_prod_sum(fez + 0.5f, P.hz_hi, P.hz_lo, &clz);
+  const float hhx = P.gbox[0], hhy = P.gbox[1], hhz = P.gbox[2];
+  const df64 rmx = df_from_double_int(__longlong_as_double((long long)st->rmax_bits));
+  const float cut = (P.R32 + rmx.hi) * (1.0f + 1e-4f);  // rounded up: conservative
+  const float R32 = P.R32;
+  const float band = 1.0f + P.delta;
+  // bin range per axis (conservative): floors of values clamped to
+  // [0, nb - 1] first, taken without conversion instructions
+  int bx0, bx1, by0, by1, bz0, bz1;
+  {
+    auto cellof = [&](float t, int a) {
+      int k;
+      floor_small(fminf(fmaxf(t, 0.0f), b.nm1f[a]), &k);
+      return k;
+    };
+    bx0 = cellof((chx - hhx - cut) * P.inv_be[0] - 1e-3f, 0);
+    bx1 = cellof((chx + hhx + cut) * P.inv_be[0] + 1e-3f, 0);
+    by0 = cellof((chy - hhy - cut) * P.inv_be[1] - 1e-3f, 1);
+    by1 = cellof((chy + hhy + cut) * P.inv_be[1] + 1e-3f, 1);
+    bz0 = cellof((chz - hhz - cut) * P.inv_be[2] - 1e-3f, 2);
+    bz1 = cellof((chz + hhz + cut) * P.inv_be[2] + 1e-3f, 2);
+  }
+  const float c43 = (float)(4.0 / 3.0 * kPi), c12 = (float)(kPi / 12.0);
+  // stream the candidates (rows of bins 32 at a time, chunks of 32 candidates
+  // across rows, as in k_qcm); every 32 kept ones are tested
+  int nb = 0;
+  const int nrx = by1 - by0 + 1, nrows = nrx * (bz1 - bz0 + 1);
+  int rb = -32, base = 0, total = 0;
+  int my_s0 = 0, my_excl = 0;
+  bool more = true;
+  for (;;) {
+    while (more && nb < 32) {
+      if (base >= total) {
+        rb += 32;
+        if (rb >= nrows) {
+          more = false;
+          break;
+        }
+        const int ri = rb + lane;
+        int cntr = 0;
+        my_s0 = 0;
+        if (ri < nrows) {
+          const int by = by0 + ri % nrx, bz = bz0 + ri / nrx;
+          const int64_t row = (int64_t)b.nb[0] * (by + (int64_t)b.nb[1] * bz);
+          my_s0 = bin_start[row + bx0];
+          cntr = bin_start[row + bx1 + 1] - my_s0;
+        }
+        int incl = cntr;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(FULL, incl, o);
+          if (lane >= o) incl += v;
+        }
+        total = __shfl_sync(FULL, incl, 31);
+        my_excl = incl - cntr;
+        base = 0;
+        continue;
+      }
+      const int kk = base + lane;
+      int lo = 0, hi = 31;
+#pragma unroll
+      for (int stp = 0; stp < 5; ++stp) {
+        const int mid = (lo + hi + 1) >> 1;
+        const int em = __shfl_sync(FULL, my_excl, mid);
+        if (em <= kk) lo = mid;
+        else hi = mid - 1;
+      }
+      const int s = __shfl_sync(FULL, my_s0, lo) + (kk - __shfl_sync(FULL, my_excl, lo));
+      bool keep = false;
+      float4 rel = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (kk < total) {
+        const float4* pp = reinterpret_cast<const float4*>(xs32) + 2 * (int64_t)s;
+        const float4 hi4 = pp[0], lo4 = pp[1];
+        rel.x = (hi4.x - chx) + (lo4.x - clx);
+        rel.y = (hi4.y - chy) + (lo4.y - cly);
+        rel.z = (hi4.z - chz) + (lo4.z - clz);
+        rel.w = hi4.w;
+        const float ox = fmaxf(fabsf(rel.x) - hhx, 0.f);
+        const float oy = fmaxf(fabsf(rel.y) - hhy, 0.f);
+        const float oz = fmaxf(fabsf(rel.z) - hhz, 0.f);
+        const float c = (R32 + rel.w) * band;
+        keep = ox * ox + oy * oy + oz * oz < c * c * band;
+      }
+      const unsigned mask = __ballot_sync(FULL, keep);
+      if (keep) {
+        const int pos = nb + __popc(mask & lt_mask);
+        const float r = rel.w, Rr = R32 + r, dm = R32 - r, mn = fminf(R32, r);
+        sm.cand[wp][pos] = make_float4(rel.x, rel.y, rel.z, Rr);
+        sm.cons[wp][pos] =
+            make_float4(Rr * Rr, dm * dm, c43 * mn * mn * mn, P.cw ? __ldg(P.cw + s).x : 1.0f);
+        sm.slot[wp][pos] = s;
+      }
+      nb += __popc(mask);
+      base += 32;
+    }
+    if (nb == 0) break;
+    __syncwarp();
+    const int cn = nb < 32 ? nb : 32;
+    for (int j = grp; j < cn; j += G) {
+      const float4 A = sm.cand[wp][j];
+      const float4 B = sm.cons[wp][j];
+#pragma unroll
+      for (int p = 0; p < PPL; ++p) {
+        const float dx = A.x - qx[p], dy = A.y - qy[p], dz = A.z - qz[p];
+        const float d2 = dx * dx + dy * dy + dz * dz;
+        if (qok[p] && d2 < B.x) {
+          float v;
+          if (d2 <= B.y) {
+            v = B.z;
+          } else {
+            const float y = rsqrtf(d2);
+            const float d = d2 * y;
+            const float sd = A.w - d;
+            v = c12 * sd * sd * (d2 + 2.0f * d * A.w - 3.0f * B.y) * y;
+          }
+          neumaier(acc[p], cmp[p], v * B.w);
+          if (want_counts) {
+            ++cnt[p];
+            if (want_ids) ids[p] += perm[sm.slot[wp][j]];
+          }
+        }
+      }
+    }
+    // keep the candidates past the 32 tested at the front
+    const int rest = nb - cn;
+    float4 ta = make_float4(0.f, 0.f, 0.f, 0.f), tb = ta;
+    int ts = 0;
+    if (lane < rest) {
+      ta = sm.cand[wp][32 + lane];
+      tb = sm.cons[wp][32 + lane];
+      ts = sm.slot[wp][32 + lane];
+    }
+    __syncwarp();
+    if (lane < rest) {
+      sm.cand[wp][lane] = ta;
+      sm.cons[wp][lane] = tb;
+      sm.slot[wp][lane] = ts;
+    }
+    __syncwarp();
+    nb = rest;
+  }
+  // Q1: the groups' sums of the same point, in a fixed tree
+  if (G > 1) {
+#pragma unroll
+    for (int off = 16; off >= Q; off >>= 1) {
+      const float oa = __shfl_down_sync(FULL, acc[0], off);
+      const float oc = __shfl_down_sync(FULL, cmp[0], off);
+      const int on = __shfl_down_sync(FULL, cnt[0], off);
+      const long long oi = __shfl_down_sync(FULL, ids[0], off);
+      if (lane + off < 32) {
+        neumaier(acc[0], cmp[0], oa);
+        cmp[0] += oc;
+        cnt[0] += on;
+        ids[0] += oi;
+      }
+    }
+  }
+  const int64_t o = e * Q;
+#pragma unroll
+  for (int p = 0; p < PPL; ++p) {
+    const int q = (G > 1 ? lane % Q : lane) + 32 * p;
+    if (!(q < Q && grp == 0)) continue;
+    const float v = 1.0f - (acc[p] + cmp[p]) * P.inv_vr32;
+    if (eps32) eps32[o + q] = v;
+    if (eps64) eps64[o + q] = (double)v;
+    if (nb_count) nb_count[o + q] = cnt[p];
+    if (nb_idsum) nb_idsum[o + q] = ids[p];
   }
 }
 
@@ -713,8 +964,8 @@ cudaError_t launch_qcm(const MeshDev& m, const Tables& t, const BinDev& b, int p
       k_qcm<KK, true><<<grid, block, 0, s>>>(m, P, b, bin_start, perm, xs64, xs32, st,    \
                                              eps_q64, eps_q32, nb_count, nb_idsum);       \
     else                                                                                  \
-      k_qcm<KK, false><<<grid, block, 0, s>>>(m, P, b, bin_start, perm, xs64, xs32, st,   \
-                                              eps_q64, eps_q32, nb_count, nb_idsum);      \
+      k_qcm_pts<KK><<<grid, block, 0, s>>>(m, P, b, bin_start, perm, xs32, st, eps_q64,   \
+                                           eps_q32, nb_count, nb_idsum);                  \
     count_launches(1);                                                                    \
     return cudaGetLastError();                                                            \
   }
