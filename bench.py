@@ -46,9 +46,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 # DRAM bytes (read + write) per launch of a kernel on the headline bed, from
 # one ncu capture of that kernel as it is now (dram__bytes_read.sum +
 # dram__bytes_write.sum); an entry is removed when its kernel changes
-NCU_TRAFFIC = {
-    "void_fraction": 3623168,
-}
+NCU_TRAFFIC = {}
 # algorithmic work per unit (the per-unit figures of the measurement plan):
 #   QCM: 8 flops per tested (Gauss point, particle) pair, 25 per lens volume
 #   operator: 7 banded 1D applies x (2k+1) taps x 2 flops + 5 per node
@@ -447,7 +445,8 @@ def run_bed(env, name, steps, warmup, alu, headline=False, e2e=True, cpu=True,
                                          enumerate(cf.STAGES)},
                            "stage_launches": {nm: st.stage_calls[i] / ke for i, nm in
                                               enumerate(cf.STAGES)},
-                           "kernel_launches_per_step": st.kernel_launches / ke}
+                           "kernel_launches_per_step": st.kernel_launches / ke,
+                           "cg_iterations": st.cg_iterations}
         per[p]["autotune"] = {"bin_edge_m": list(st.bin_edge), "bins": list(st.nb),
                               "tile_shape": ["16x8x8", "22x13x4", "25x15x4"][st.tile_shape],
                               "tuned": {"bins": bool(st.tuned & 1), "tile": bool(st.tuned & 2)},
@@ -481,14 +480,19 @@ def run_bed(env, name, steps, warmup, alu, headline=False, e2e=True, cpu=True,
     tests_culled = float(k + 1) ** 3 * _element_candidates(w)
     qcm_ms = stages["void_fraction"] / max(calls["void_fraction"], 1.0)
     fo_ms = stages["forces"] / max(calls["forces"], 1.0)
-    op_launches = max(calls["op32"], 1.0)
+    # the operator's productive launches: one per CG iteration (the stage also
+    # holds the residual launch, which a cold start reduces to its scalars,
+    # and the launches after convergence, which return at once)
+    op_launches = float(max(per[1]["eager"]["cg_iterations"], 1))
     op_ms = stages["op32"] / op_launches
+    op_macs = 7.0 * (2 * k + 1) * n_nodes   # z: M, K; y: 3 folded bands; x: M, K
+    instr_peak = alu["fp32_tflops"] / 2.0    # FP32 instructions per second / 1e12
     qcm_flops = QCM_FLOPS_TEST * tests_cell + QCM_FLOPS_LENS * pairs
     qcm_flops_culled = QCM_FLOPS_TEST * tests_culled + QCM_FLOPS_LENS * pairs
     fo_flops = _forces_flops(k, kp) * n
     kern = {
         "void_fraction": {
-            "kernel": "k_qcm<%d,false> (FP32 QCM)" % k, "bound": "alu", "unit": "TFLOP/s",
+            "kernel": "k_qcm_pts<%d> (FP32 QCM, one lane per Gauss point)" % k, "bound": "alu", "unit": "TFLOP/s",
             "ms_per_launch": qcm_ms, "launches_per_step": calls["void_fraction"],
             "work": qcm_flops, "peak": alu["fp32_tflops"],
             "achieved": qcm_flops / (qcm_ms * 1e-3) / 1e12,
@@ -505,14 +509,18 @@ def run_bed(env, name, steps, warmup, alu, headline=False, e2e=True, cpu=True,
             "peak_source": "FMA probe on this device (libalupeak.so), FP64 (the FP64 "
                            "interpolation of the slip bounds the kernel)"},
         "op32": {
-            "kernel": "k_cg_apply_df (double-float CG operator on the FP32 pipes)",
-            "bound": "hbm", "unit": "GB/s", "ms_per_launch": op_ms,
-            "launches_per_step": op_launches, "work": 16.0 * n_nodes,
-            "peak": hbm, "achieved": 16.0 * n_nodes / (op_ms * 1e-3) / 1e9,
-            "peak_source": "%s MEASURED_PEAKS.json hbm_gbs" % peak_kind,
-            "limiter": "instruction issue (double-float arithmetic, ~10 FP32 instructions per "
-                       "FP64-equivalent flop); algorithmic bytes: the double-float vector in "
-                       "and out, 16 B per node"},
+            "kernel": "k_cg_apply_df<%d> (double-float CG operator on the FP32 pipes)" % k,
+            "bound": "alu", "unit": "T FP32 instructions/s", "ms_per_launch": op_ms,
+            "launches_per_step": op_launches, "work": 12.0 * op_macs,
+            "peak": instr_peak, "achieved": 12.0 * op_macs / (op_ms * 1e-3) / 1e12,
+            "units": {"df_multiply_adds": op_macs, "fp32_instructions_per_df_multiply_add": 12,
+                      "hbm_bytes_algorithmic": 16.0 * n_nodes},
+            "peak_source": "FMA probe on this device (libalupeak.so): FP32 FMA rate as "
+                           "instructions/s",
+            "limiter": "instruction issue: each double-float multiply-add of the banded 1D "
+                       "passes (7 (2k+1) per node) is 12 FP32 instructions (exact product, "
+                       "two-sum, error accumulation); the algorithmic HBM traffic (the "
+                       "double-float vector in and out, 16 B per node) would take ~3 us"},
     }
     for c in ("void_fraction", "forces", "op32"):
         kern[c]["frac"] = kern[c]["achieved"] / kern[c]["peak"]

@@ -264,7 +264,7 @@ constexpr int kApplyThreads = 256;
 template <int K, class S>
 struct Tile {
   static constexpr int TX = S::X, TY = S::Y, TZ = S::Z;
-  static constexpr int H = K;
+  static constexpr int H = K, W = 2 * K + 1;
   static constexpr int XW = TX + 2 * H, YW = TY + 2 * H, ZW = TZ + 2 * H;
   static constexpr int NX = ZW * YW * XW;     // input with halo
   static constexpr int NT = TZ * YW * XW;     // after the z pass (each of t1, t2)
@@ -272,9 +272,25 @@ struct Tile {
   static constexpr int NO = TZ * TY * TX;     // owned nodes (their input, for the epilogue)
   // U, V reuse the input's space once the z pass has read it, when they fit
   static constexpr bool UV_IN_X = 2 * NU <= NX;
-  // values in shared memory: with U, V over the input, the owned nodes' input
-  // is kept aside for the epilogue; otherwise the epilogue reads it in place
-  static constexpr int NSM = NX + 2 * NT + (UV_IN_X ? NO : 2 * NU);
+  // band coefficients of the tile's rows: z (M, K), y (three folded
+  // combinations), x (M, K)
+  static constexpr int NBZ = 2 * TZ * W, NBY = 3 * TY * W, NBX = 2 * TX * W;
+  static constexpr int NSM = NX + 2 * NT + (UV_IN_X ? 0 : 2 * NU) + NO + NBZ + NBY + NBX;
+  // y pass: one thread per (chunk of CY rows, z, x) column piece, the number
+  // of chunks chosen for the fewest row outputs per thread over whole rounds
+  // of the block's threads
+  static constexpr int YCOLS = TZ * XW;
+  static constexpr int ycost(int nch) {
+    return ((YCOLS * nch + 255) / 256) * ((TY + nch - 1) / nch);
+  }
+  static constexpr int ypick() {
+    int best = 1;
+    for (int c = 2; c <= TY; ++c)
+      if (ycost(c) < ycost(best)) best = c;
+    return best;
+  }
+  static constexpr int YNCH = ypick();
+  static constexpr int CY = (TY + YNCH - 1) / YNCH;
 };
 
 template <typename T>
@@ -406,13 +422,22 @@ struct EpiResidualDf {
 // file).  ld(g, own) gives the input value at node g; ep(g, acc, x_eff)
 // consumes the result of an owned node and returns its share of a dot
 // product.
+//
+// The band rows of the tile are staged in shared memory first, the y ones
+// folded with the coefficients:
+//   U = (cM My + cKy Ky) T1 + (cKz My) T2,  V = (cKx My) T1,  A x = Mx U + Kx V
+// with T1 = Mz x, T2 = Kz x.  The z pass runs one thread per haloed (x, y)
+// column over all TZ outputs, the y pass one thread per run of CY outputs
+// along y (inputs held in registers), the x pass one thread per owned node.
 template <int K, class S, typename T, class Load, class Epi>
 __device__ __forceinline__ double apply_tile(const MeshDev& m, const T* __restrict__ bands,
                                              const Coefs<T>& cf, const Load& ld, const Epi& ep,
                                              T* sm) {
   using TL = Tile<K, S>;
   constexpr int TX = TL::TX, TY = TL::TY, TZ = TL::TZ;
-  constexpr int H = K, W = 2 * K + 1;
+  constexpr int H = TL::H, W = TL::W;
+  constexpr int XW = TL::XW, YW = TL::YW, ZW = TL::ZW;
+  constexpr int PL = YW * XW;  // one z plane of the haloed input
   const int nx = m.nn[0], ny = m.nn[1], nz = m.nn[2];
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
   const int64_t sxy = (int64_t)nx * ny;
@@ -421,7 +446,10 @@ __device__ __forceinline__ double apply_tile(const MeshDev& m, const T* __restri
   T* T2 = T1 + TL::NT;
   T* U = TL::UV_IN_X ? X : T2 + TL::NT;   // [TZ][TY][XW], over X once the z pass is done
   T* V = U + TL::NU;
-  T* XE = T2 + TL::NT;       // [TZ][TY][TX] input at the owned nodes (when U, V are over X)
+  T* XE = TL::UV_IN_X ? T2 + TL::NT : V + TL::NU;  // [TZ][TY][TX] input at the owned nodes
+  T* BZ = XE + TL::NO;       // [TZ][W][2]   Mz, Kz of row z0 + o
+  T* BY = BZ + TL::NBZ;      // [TY][W][3]   cM My + cKy Ky, cKz My, cKx My of row y0 + j
+  T* BX = BY + TL::NBY;      // [2][W][TX]   Mx, Kx of column x0 + i
   const T* bMx = bands;
   const T* bKx = bMx + (size_t)nx * W;
   const T* bMy = bKx + (size_t)nx * W;
@@ -429,18 +457,54 @@ __device__ __forceinline__ double apply_tile(const MeshDev& m, const T* __restri
   const T* bMz = bKy + (size_t)ny * W;
   const T* bKz = bMz + (size_t)nz * W;
 
-  // load with halo
+  // band rows of the tile (zero past the mesh)
+  for (int t = threadIdx.x; t < TZ * W; t += blockDim.x) {
+    const int o = t / W, w = t - o * W, gz = z0 + o;
+    T a = T(0), b = T(0);
+    if (gz < nz) {
+      a = bMz[(size_t)gz * W + w];
+      b = bKz[(size_t)gz * W + w];
+    }
+    BZ[2 * t] = a;
+    BZ[2 * t + 1] = b;
+  }
+  for (int t = threadIdx.x; t < TY * W; t += blockDim.x) {
+    const int j = t / W, w = t - j * W, gy = y0 + j;
+    T a = T(0), b = T(0), c = T(0);
+    if (gy < ny) {
+      const T my = bMy[(size_t)gy * W + w], ky = bKy[(size_t)gy * W + w];
+      a = cf.cM * my + cf.cKy * ky;
+      b = cf.cKz * my;
+      c = cf.cKx * my;
+    }
+    BY[3 * t] = a;
+    BY[3 * t + 1] = b;
+    BY[3 * t + 2] = c;
+  }
+  for (int t = threadIdx.x; t < TX * W; t += blockDim.x) {
+    const int i = t / W, w = t - i * W, gx = x0 + i;
+    T a = T(0), b = T(0);
+    if (gx < nx) {
+      a = bMx[(size_t)gx * W + w];
+      b = bKx[(size_t)gx * W + w];
+    }
+    BX[w * TX + i] = a;
+    BX[(W + w) * TX + i] = b;
+  }
+
+  // load with halo; the owned nodes' input also to XE
   int nonzero = 0;
   for (int t = threadIdx.x; t < TL::NX; t += blockDim.x) {
-    int lx = t % TL::XW, ly = (t / TL::XW) % TL::YW, lz = t / (TL::XW * TL::YW);
-    int gx = x0 + lx - H, gy = y0 + ly - H, gz = z0 + lz - H;
-    T v = 0;
+    const int lz = t / PL, rr = t - lz * PL, ly = rr / XW, lx = rr - ly * XW;
+    const int gx = x0 + lx - H, gy = y0 + ly - H, gz = z0 + lz - H;
+    T v = T(0);
     if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz) {
-      bool own = lx >= H && lx < H + TX && ly >= H && ly < H + TY && lz >= H && lz < H + TZ;
+      const bool own = lx >= H && lx < H + TX && ly >= H && ly < H + TY && lz >= H && lz < H + TZ;
       v = ld(gx + (int64_t)nx * gy + sxy * gz, own);
+      if (own) XE[((lz - H) * TY + (ly - H)) * TX + (lx - H)] = v;
     }
     X[t] = v;
-    nonzero |= (v != (T)0);
+    nonzero |= (v != T(0));
   }
   // a tile whose input (halo included) is zero has a zero image: skip the
   // passes (a cold start of the projection begins with x = 0)
@@ -452,70 +516,80 @@ __device__ __forceinline__ double apply_tile(const MeshDev& m, const T* __restri
     }
     return (double)dot;
   }
-  // z pass
-  for (int t = threadIdx.x; t < TL::NT; t += blockDim.x) {
-    int lx = t % TL::XW, ly = (t / TL::XW) % TL::YW, lz = t / (TL::XW * TL::YW);
-    int gz = z0 + lz;
-    Acc<T> a1, a2;
-    a1.zero();
-    a2.zero();
-    if (gz < nz) {
+  // z pass: column c of the haloed x-y plane, all TZ outputs
+  for (int c = threadIdx.x; c < PL; c += blockDim.x) {
+    T xv[ZW];
+#pragma unroll
+    for (int q = 0; q < ZW; ++q) xv[q] = X[q * PL + c];
+#pragma unroll
+    for (int o = 0; o < TZ; ++o) {
+      Acc<T> a1, a2;
+      a1.zero();
+      a2.zero();
 #pragma unroll
       for (int w = 0; w < W; ++w) {
-        T xv = X[(lz + w) * TL::YW * TL::XW + ly * TL::XW + lx];
-        a1.add(bMz[(size_t)gz * W + w], xv);
-        a2.add(bKz[(size_t)gz * W + w], xv);
+        a1.add(BZ[2 * (o * W + w)], xv[o + w]);
+        a2.add(BZ[2 * (o * W + w) + 1], xv[o + w]);
       }
+      T1[o * PL + c] = a1.get();
+      T2[o * PL + c] = a2.get();
     }
-    T1[t] = a1.get();
-    T2[t] = a2.get();
-    if (TL::UV_IN_X && ly >= H && ly < H + TY && lx >= H && lx < H + TX)
-      XE[(lz * TY + (ly - H)) * TX + (lx - H)] = X[(lz + H) * TL::YW * TL::XW + ly * TL::XW + lx];
   }
   __syncthreads();
-  // y pass
-  for (int t = threadIdx.x; t < TL::NU; t += blockDim.x) {
-    int lx = t % TL::XW, ly = (t / TL::XW) % TY, lz = t / (TL::XW * TY);
-    int gy = y0 + ly;
-    Acc<T> a1, a2, a3;
-    a1.zero();
-    a2.zero();
-    a3.zero();
-    if (gy < ny) {
+  // y pass: rows j0 .. j0 + len - 1 of column (lz, lx)
+  constexpr int CY = TL::CY, WIN = CY + 2 * H;
+  for (int it = threadIdx.x; it < TL::YCOLS * TL::YNCH; it += blockDim.x) {
+    const int ch = it / TL::YCOLS, col = it - ch * TL::YCOLS;
+    const int lz = col / XW, lx = col - lz * XW;
+    const int j0 = ch * CY;
+    const int len = TY - j0 < CY ? TY - j0 : CY;
+    const T* s1 = T1 + lz * PL + j0 * XW + lx;
+    const T* s2 = T2 + lz * PL + j0 * XW + lx;
+    T t1[WIN], t2[WIN];
 #pragma unroll
-      for (int w = 0; w < W; ++w) {
-        int src = lz * TL::YW * TL::XW + (ly + w) * TL::XW + lx;
-        T mv = bMy[(size_t)gy * W + w], kv = bKy[(size_t)gy * W + w];
-        T t1 = T1[src];
-        a1.add(mv, t1);
-        a2.add(kv, t1);
-        a3.add(mv, T2[src]);
+    for (int q = 0; q < WIN; ++q) {
+      const bool in = q < len + 2 * H;
+      t1[q] = in ? s1[q * XW] : T(0);
+      t2[q] = in ? s2[q * XW] : T(0);
+    }
+    T* du = U + (lz * TY + j0) * XW + lx;
+    T* dv = V + (lz * TY + j0) * XW + lx;
+#pragma unroll
+    for (int j = 0; j < CY; ++j) {
+      if (j < len) {
+        const T* by = BY + (j0 + j) * (3 * W);
+        Acc<T> au, av;
+        au.zero();
+        av.zero();
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+          au.add(by[3 * w], t1[j + w]);
+          au.add(by[3 * w + 1], t2[j + w]);
+          av.add(by[3 * w + 2], t1[j + w]);
+        }
+        du[j * XW] = au.get();
+        dv[j * XW] = av.get();
       }
     }
-    T s1 = a1.get(), s2 = a2.get(), s3 = a3.get();
-    U[t] = cf.cM * s1 + cf.cKy * s2 + cf.cKz * s3;
-    V[t] = cf.cKx * s1;
   }
   __syncthreads();
   // x pass + output (per-thread partial in the epilogue's type, one
   // conversion per thread)
   typename Epi::acc_t dot = 0;
-  for (int t = threadIdx.x; t < TX * TY * TZ; t += blockDim.x) {
-    int lx = t % TX, ly = (t / TX) % TY, lz = t / (TX * TY);
-    int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
+  for (int t = threadIdx.x; t < TL::NO; t += blockDim.x) {
+    const int lz = t / (TX * TY), rr = t - lz * (TX * TY), ly = rr / TX, lx = rr - ly * TX;
+    const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
     if (gx >= nx || gy >= ny || gz >= nz) continue;
+    const T* u = U + (lz * TY + ly) * XW + lx;
+    const T* v = V + (lz * TY + ly) * XW + lx;
     Acc<T> ax;
     ax.zero();
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-      int src = lz * TY * TL::XW + ly * TL::XW + lx + w;
-      ax.add(bMx[(size_t)gx * W + w], U[src]);
-      ax.add(bKx[(size_t)gx * W + w], V[src]);
+      ax.add(BX[w * TX + lx], u[w]);
+      ax.add(BX[(W + w) * TX + lx], v[w]);
     }
-    T acc = ax.get();
-    T xe = TL::UV_IN_X ? XE[(lz * TY + ly) * TX + lx]
-                       : X[(lz + H) * TL::YW * TL::XW + (ly + H) * TL::XW + lx + H];
-    dot += ep(gx + (int64_t)nx * gy + sxy * gz, acc, xe);
+    dot += ep(gx + (int64_t)nx * gy + sxy * gz, ax.get(), XE[t]);
   }
   return (double)dot;
 }
