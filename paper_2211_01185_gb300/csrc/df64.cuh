@@ -54,20 +54,30 @@ __device__ __forceinline__ df64 df_from_double(double v) {
 // rounded once, so hi + lo = v to 2^-48 |v| and |lo| < ulp(hi).  Zero is
 // split as zero; a v whose hi or lo would not be a normal float (|v| <
 // 2^-74 or |v| >= 2^128, subnormals, inf, nan) takes the FP64 conversion.
+// the two 32-bit halves of the bits of a double, opaque to the compiler:
+// tests on them stay integer operations (the compiler otherwise turns a test
+// such as (bits << 1) == 0 into an FP64 compare, which issues on the narrow
+// FP64 pipe)
+__device__ __forceinline__ void double_halves(double v, unsigned* lo, unsigned* hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=r"(*lo), "=r"(*hi) : "d"(v));
+}
+
 // the FP64 conversion of the rare values, as a real call: inlined, the
 // compiler predicates it into every split and its FP64 instructions issue
 // on the narrow pipe even when not taken
 static __device__ __noinline__ df64 df_from_double_slow(double v) { return df_from_double(v); }
 
 __device__ __forceinline__ df64 df_from_double_int(double v) {
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
-  const unsigned sign = (unsigned)(bits >> 32) & 0x80000000u;
-  if ((bits << 1) == 0ull) return df64(__uint_as_float(sign), 0.f);
-  const int E = (int)((bits >> 52) & 0x7ff);
+  unsigned lo32, hi32;
+  double_halves(v, &lo32, &hi32);
+  const unsigned sign = hi32 & 0x80000000u;
+  const int E = (int)((hi32 >> 20) & 0x7ffu);
+  // zero and subnormals (the conversion rounds them to a signed zero)
+  if (E == 0) return df64(__uint_as_float(sign), 0.f);
   if (E < 949 || E > 1150) return df_from_double_slow(v);
   const float hi = __uint_as_float(sign | ((unsigned)(E - 896) << 23) |
-                                   ((unsigned)(bits >> 29) & 0x7fffffu));
-  const unsigned m = (unsigned)(bits & 0x1fffffffull);
+                                   ((hi32 & 0xfffffu) << 3) | (lo32 >> 29));
+  const unsigned m = lo32 & 0x1fffffffu;
   const float mh = __uint_as_float(0x4B000000u | (m >> 6)) - 8388608.0f;   // exact
   const float ml = __uint_as_float(0x4B000000u | (m & 63u)) - 8388608.0f;  // exact
   const float mf = fmaf(mh, 64.0f, ml);                                   // m, rounded
@@ -75,14 +85,16 @@ __device__ __forceinline__ df64 df_from_double_int(double v) {
   return df64(hi, __uint_as_float(__float_as_uint(lo) | sign));
 }
 
+static __device__ __noinline__ double double_from_float_slow(float f) { return (double)f; }
+
 // float -> double by moving the bit fields (exact, as the conversion is);
-// zero, subnormals, inf and nan take the conversion instruction
+// subnormals, inf and nan take the conversion instruction (behind a call)
 __device__ __forceinline__ double double_from_float_int(float f) {
   const unsigned u = __float_as_uint(f);
   const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
   if ((u << 1) == 0u) return __longlong_as_double((long long)sgn);
   const unsigned ef = (u >> 23) & 0xffu;
-  if (ef == 0u || ef == 255u) return (double)f;
+  if (ef == 0u || ef == 255u) return double_from_float_slow(f);
   return __longlong_as_double((long long)(sgn | ((unsigned long long)(ef + 896u) << 52) |
                                           ((unsigned long long)(u & 0x7fffffu) << 29)));
 }

@@ -252,10 +252,12 @@ cublasStatus_t gemm_rm(cublasHandle_t h, int M, int N, int K, const float* A, lo
 // C[M x N] = A[M x K] B[K x N] in shared memory with A stored transposed
 // (AT[K][lda]) and B row-major (B[K][ldb]); lda, ldb multiples of 4 floats.
 // Each thread owns a TR x TC block of C (TR, TC = 4 or 8), so one k step is
-// TR/4 + TC/4 128-bit loads and TR TC FMAs.  Threads form a gm x gn grid
-// (gm = ceil(M/TR), gn = ceil(N/TC)); rows and columns past M, N read
-// padding and are not stored.
-template <int TR, int TC>
+// TR/4 + TC/4 128-bit loads and TR TC FMAs; the loads of step k + 1 are
+// issued before the FMAs of step k.  Threads form a gm x gn grid (gm =
+// ceil(M/TR), gn = ceil(N/TC)); rows and columns past M, N read padding and
+// are not stored.  With TRANS_C the block is stored transposed, C[c][r]
+// (row length ldc, a multiple of 4), as 128-bit stores.
+template <int TR, int TC, bool TRANS_C>
 __device__ __forceinline__ void smem_gemm(const float* AT, int lda, const float* B, int ldb,
                                           float* C, int ldc, int M, int N, int K) {
   const int gn = (N + TC - 1) / TC, gm = (M + TR - 1) / TR;
@@ -267,37 +269,52 @@ __device__ __forceinline__ void smem_gemm(const float* AT, int lda, const float*
   for (int a = 0; a < TR; ++a)
 #pragma unroll
     for (int b = 0; b < TC; ++b) acc[a][b] = 0.f;
-#pragma unroll 2
+  const float4* ap = reinterpret_cast<const float4*>(AT + r0);
+  const float4* bp = reinterpret_cast<const float4*>(B + c0);
+  const int la = lda >> 2, lb = ldb >> 2;
+  float4 av[TR / 4], bv[TC / 4];
+#pragma unroll
+  for (int q = 0; q < TR / 4; ++q) av[q] = ap[q];
+#pragma unroll
+  for (int q = 0; q < TC / 4; ++q) bv[q] = bp[q];
+#pragma unroll 4
   for (int k = 0; k < K; ++k) {
-    float av[TR], bv[TC];
+    const int kn = k + 1 < K ? k + 1 : k;
+    float4 an[TR / 4], bn[TC / 4];
 #pragma unroll
-    for (int q = 0; q < TR / 4; ++q) {
-      const float4 v = reinterpret_cast<const float4*>(AT + k * lda + r0)[q];
-      av[4 * q] = v.x;
-      av[4 * q + 1] = v.y;
-      av[4 * q + 2] = v.z;
-      av[4 * q + 3] = v.w;
-    }
+    for (int q = 0; q < TR / 4; ++q) an[q] = ap[kn * la + q];
 #pragma unroll
-    for (int q = 0; q < TC / 4; ++q) {
-      const float4 v = reinterpret_cast<const float4*>(B + k * ldb + c0)[q];
-      bv[4 * q] = v.x;
-      bv[4 * q + 1] = v.y;
-      bv[4 * q + 2] = v.z;
-      bv[4 * q + 3] = v.w;
-    }
+    for (int q = 0; q < TC / 4; ++q) bn[q] = bp[kn * lb + q];
+    const float* a = reinterpret_cast<const float*>(av);
+    const float* b = reinterpret_cast<const float*>(bv);
 #pragma unroll
-    for (int a = 0; a < TR; ++a)
+    for (int x = 0; x < TR; ++x)
 #pragma unroll
-      for (int b = 0; b < TC; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+      for (int y = 0; y < TC; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
+#pragma unroll
+    for (int q = 0; q < TR / 4; ++q) av[q] = an[q];
+#pragma unroll
+    for (int q = 0; q < TC / 4; ++q) bv[q] = bn[q];
   }
+  if (TRANS_C) {
 #pragma unroll
-  for (int a = 0; a < TR; ++a)
+    for (int y = 0; y < TC; ++y) {
+      const int c = c0 + y;
+      if (c >= N) continue;
 #pragma unroll
-    for (int b = 0; b < TC; ++b) {
-      int r = r0 + a, c = c0 + b;
-      if (r < M && c < N) C[r * ldc + c] = acc[a][b];
+      for (int q = 0; q < TR / 4; ++q)
+        *reinterpret_cast<float4*>(C + c * ldc + r0 + 4 * q) =
+            make_float4(acc[4 * q][y], acc[4 * q + 1][y], acc[4 * q + 2][y], acc[4 * q + 3][y]);
     }
+  } else {
+#pragma unroll
+    for (int x = 0; x < TR; ++x)
+#pragma unroll
+      for (int y = 0; y < TC; ++y) {
+        int r = r0 + x, c = c0 + y;
+        if (r < M && c < N) C[r * ldc + c] = acc[x][y];
+      }
+  }
 }
 
 // asynchronous global -> shared copies (no register round trip, every copy of
@@ -318,19 +335,20 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // multiple of 8 for the 8 x 8 register tiles, plus 4 against bank conflicts
 __host__ __device__ __forceinline__ int slab_pad(int n) { return ((n + 7) & ~7) + 4; }
 
-// forward: out_z = Vy^T (in_z Vx); inverse: out_z = Vy (in_z Vx^T), for every
-// z-slab.  Bx is the right factor of the x transform ([nx][slab_pad(nx)]),
-// AyT the transpose of the left factor of the y transform ([ny][slab_pad(ny)]),
-// both zero-padded row-major in global memory and copied to shared memory as
-// they are.  The slab is staged transposed (x major) as the A operand of the
-// first product.
+// forward: out_z = (Vy^T in_z) Vx; inverse: out_z = (Vy in_z) Vx^T, for every
+// z-slab.  AyT is the transpose of the left factor of the y transform
+// ([ny][slab_pad(ny)]), Bx the right factor of the x transform
+// ([nx][slab_pad(nx)]), both zero-padded row-major in global memory and
+// copied to shared memory as they are.  The slab is staged as it lies in
+// memory (row y, lanes along x) as the B operand of the first product, whose
+// result is stored transposed as the A operand of the second.
 //
 // With dot.r set (the inverse transform that writes z), the kernel also
 // forms r . z of the CG from the values it stores: one FP32 sum per thread,
-// block sums in FP64, the last block to finish adds the blocks' sums in
-// block order and sets rz and the Fletcher-Reeves beta = rz_new / rz_old
-// (not on the first application) -- the dot product kernel that would read
-// r and z again is not launched.
+// block sums, the last block to finish adds the blocks' sums in block order
+// and sets rz and the Fletcher-Reeves beta = rz_new / rz_old (not on the
+// first application) -- the dot product kernel that would read r and z
+// again is not launched.
 template <int TILE>
 __global__ void k_fdm_slab(int nx, int ny, int nz, const float* __restrict__ Bx,
                            const float* __restrict__ AyT, const float* __restrict__ in,
@@ -341,43 +359,40 @@ __global__ void k_fdm_slab(int nx, int ny, int nz, const float* __restrict__ Bx,
   float rz = 0.f;
   extern __shared__ __align__(16) float fsm[];
   const int px = slab_pad(nx), py = slab_pad(ny);
-  const int plane = nx * ny;
-  const int big = nx * py > ny * px ? nx * py : ny * px;
-  float* XT = fsm;                 // [nx][py]   slab, transposed
-  float* Y = XT;                   // [ny][px]   result (reuses the slab's space)
-  float* T = XT + big;             // [ny][px]   after the x transform
-  float* MB = T + ny * px;         // [nx][px]
+  float* X = fsm;                  // [ny][px]   slab as it lies
+  float* Y = X;                    // [ny][px]   result (reuses the slab's space)
+  float* PT = X + ny * px;         // [nx][py]   after the y transform, transposed
+  float* MB = PT + nx * py;        // [nx][px]
   float* MA = MB + nx * px;        // [ny][py]   (AyT)
   for (int t = threadIdx.x; t < (nx * px) >> 2; t += blockDim.x)
     cp_async16(MB + 4 * t, Bx + 4 * t);
   for (int t = threadIdx.x; t < (ny * py) >> 2; t += blockDim.x)
     cp_async16(MA + 4 * t, AyT + 4 * t);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int z = blockIdx.x; z < nz; z += gridDim.x) {
     const float* src = in + (int64_t)z * in_stride;
-    for (int t = threadIdx.x; t < plane; t += blockDim.x) {
-      int y = t / nx, x = t - y * nx;
-      cp_async4(XT + x * py + y, src + t);
-    }
+    for (int y = wid; y < ny; y += nw)
+      for (int x = lane; x < nx; x += 32) cp_async4(X + y * px + x, src + y * nx + x);
     cp_async_wait_all();
     __syncthreads();
-    // rows y >= ny of XT are never written: they feed only outputs that are
-    // not stored
-    smem_gemm<TILE, TILE>(XT, py, MB, px, T, px, ny, nx, nx);  // T[y][x'] = sum_x X[y][x] Bx[x][x']
+    // PT[x][y'] = sum_y AyT[y][y'] X[y][x]
+    smem_gemm<TILE, TILE, true>(MA, py, X, px, PT, py, ny, nx, ny);
     __syncthreads();
-    smem_gemm<TILE, TILE>(MA, py, T, px, Y, px, ny, nx, ny);   // Y[y'][x] = sum_y AyT[y][y'] T[y][x]
+    // Y[y'][x'] = sum_x PT[x][y'] Bx[x][x']
+    smem_gemm<TILE, TILE, false>(PT, py, MB, px, Y, px, ny, nx, nx);
     __syncthreads();
     float* dst = out + (int64_t)z * out_stride;
-    const float* rr = dot.r ? dot.r + (int64_t)z * plane : nullptr;
-    for (int t = threadIdx.x; t < plane; t += blockDim.x) {
-      int y = t / nx, x = t - y * nx;
-      const float v = Y[y * px + x];
-      dst[t] = v;
-      if (rr) rz = fmaf(rr[t], v, rz);
-    }
+    const float* rr = dot.r ? dot.r + (int64_t)z * nx * ny : nullptr;
+    for (int y = wid; y < ny; y += nw)
+      for (int x = lane; x < nx; x += 32) {
+        const float v = Y[y * px + x];
+        dst[y * nx + x] = v;
+        if (rr) rz = fmaf(rr[y * nx + x], v, rz);
+      }
     __syncthreads();
   }
   if (dot.r) {
-    const double sblk = block_sum((double)rz, red);
+    const double sblk = block_sum(rz, red);
     double vals[1] = {sblk};
     double o[1];
     if (last_block_reduce(dot.partials, 1, vals, &dot.sc->ticket, o, red) && threadIdx.x == 0) {
@@ -691,8 +706,8 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4], 
   const int nx = m.nn[0], ny = m.nn[1], nz = m.nn[2];
   {
     size_t px = slab_pad(nx), py = slab_pad(ny);
-    size_t big = nx * py > ny * px ? nx * py : ny * px;
-    p->slab_smem = (big + ny * px + nx * px + ny * py) * sizeof(float);
+    // k_fdm_slab: X / Y [ny][px], PT [nx][py], Bx [nx][px], AyT [ny][py]
+    p->slab_smem = (ny * px + nx * py + nx * px + ny * py) * sizeof(float);
     // 4 x 4 register tiles (more warps per slab) where the thread count allows
     p->slab_tile = ((nx + 3) / 4) * ((ny + 3) / 4) <= 1024 ? 4 : 8;
     const int tl = p->slab_tile;

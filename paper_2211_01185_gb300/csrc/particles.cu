@@ -98,7 +98,11 @@ __global__ void k_bin_count(MeshDev m, BinDev b, int64_t n, const double* __rest
   // block (the bits of a non-negative double order like the value)
   if (r) {
     __shared__ unsigned long long wmax[32];
-    unsigned long long bits = valid && ri >= 0.0 ? (unsigned long long)__double_as_longlong(ri) : 0ull;
+    // r >= 0 (and not NaN) by integer tests on the bits
+    unsigned rl, rh;
+    double_halves(ri, &rl, &rh);
+    const bool nonneg = !(rh >> 31) && (rh < 0x7ff00000u || (rh == 0x7ff00000u && rl == 0u));
+    unsigned long long bits = valid && nonneg ? (unsigned long long)__double_as_longlong(ri) : 0ull;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       unsigned long long ob = __shfl_xor_sync(FULL, bits, o);

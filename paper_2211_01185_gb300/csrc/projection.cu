@@ -430,7 +430,8 @@ struct EpiResidualDf {
 // column over all TZ outputs, the y pass one thread per run of CY outputs
 // along y (inputs held in registers), the x pass one thread per owned node.
 template <int K, class S, typename T, class Load, class Epi>
-__device__ __forceinline__ double apply_tile(const MeshDev& m, const T* __restrict__ bands,
+__device__ __forceinline__ typename Epi::acc_t apply_tile(const MeshDev& m,
+                                                          const T* __restrict__ bands,
                                              const Coefs<T>& cf, const Load& ld, const Epi& ep,
                                              T* sm) {
   using TL = Tile<K, S>;
@@ -514,7 +515,7 @@ __device__ __forceinline__ double apply_tile(const MeshDev& m, const T* __restri
       int gx = x0 + t % TX, gy = y0 + (t / TX) % TY, gz = z0 + t / (TX * TY);
       if (gx < nx && gy < ny && gz < nz) dot += ep(gx + (int64_t)nx * gy + sxy * gz, T(0), T(0));
     }
-    return (double)dot;
+    return dot;
   }
   // z pass: column c of the haloed x-y plane, all TZ outputs
   for (int c = threadIdx.x; c < PL; c += blockDim.x) {
@@ -591,7 +592,7 @@ __device__ __forceinline__ double apply_tile(const MeshDev& m, const T* __restri
     }
     dot += ep(gx + (int64_t)nx * gy + sxy * gz, ax.get(), XE[t]);
   }
-  return (double)dot;
+  return dot;
 }
 
 template <int K, class S, typename T>
@@ -620,7 +621,7 @@ k_cg_apply(MeshDev m, const T* __restrict__ bands, Coefs<T> cf, const T* __restr
   T beta = first ? (T)0 : (T)sc->beta;
   LoadDir<T> ld{z, p_old, p_new, beta, first != 0};
   EpiStore<T> ep{Ap};
-  double d = apply_tile<K, S, T>(m, bands, cf, ld, ep, reinterpret_cast<T*>(smraw));
+  const T d = apply_tile<K, S, T>(m, bands, cf, ld, ep, reinterpret_cast<T*>(smraw));
   double s = block_sum(d, red);
   double vals[1] = {s};
   double out[1];
@@ -650,8 +651,8 @@ k_cg_update(int64_t n, TX_* __restrict__ xv, T* __restrict__ r, T* __restrict__ 
     rz += ri * zi;
     rr += ri * ri;
   }
-  double s1 = block_sum((double)rz, red);
-  double s2 = block_sum((double)rr, red);
+  double s1 = block_sum(rz, red);
+  double s2 = block_sum(rr, red);
   double vals[2] = {s1, s2};
   double out[2];
   if (last_block_reduce(partials, 2, vals, &sc->ticket, out, red) && threadIdx.x == 0) {
@@ -682,9 +683,9 @@ k_cg_start(int64_t n, const TB* __restrict__ b, const T* __restrict__ Ax, T* __r
     rr += ri * ri;
     bb += bi * bi;
   }
-  double s1 = block_sum((double)rz, red);
-  double s2 = block_sum((double)rr, red);
-  double s3 = block_sum((double)bb, red);
+  double s1 = block_sum(rz, red);
+  double s2 = block_sum(rr, red);
+  double s3 = block_sum(bb, red);
   double vals[3] = {s1, s2, s3};
   double out[3];
   if (last_block_reduce(partials, 3, vals, &sc->ticket, out, red) && threadIdx.x == 0) {
@@ -719,7 +720,7 @@ k_cg_update_fdm(int64_t n, TX_* __restrict__ xv, T* __restrict__ r, const T* __r
     if (rf) rf[i] = (float)ri;
     rr += ri * ri;
   }
-  double s = block_sum((double)rr, red);
+  double s = block_sum(rr, red);
   double vals[1] = {s};
   double out[1];
   if (last_block_reduce(partials, 1, vals, &sc->ticket, out, red) && threadIdx.x == 0) {
@@ -754,8 +755,8 @@ k_cg_dot_fdm(int64_t n, const T* __restrict__ r, const float* __restrict__ zf,
     rz += ri * zi;
     if (!first && !fletcher_reeves) rzo += ri * z_old[i];
   }
-  double s1 = block_sum((double)rz, red);
-  double s2 = block_sum((double)rzo, red);
+  double s1 = block_sum(rz, red);
+  double s2 = block_sum(rzo, red);
   double vals[2] = {s1, s2};
   double out[2];
   if (last_block_reduce(partials, 2, vals, &sc->ticket, out, red) && threadIdx.x == 0) {
@@ -794,8 +795,8 @@ k_cg_start_fdm(int64_t n, const TB* __restrict__ b, const T* __restrict__ Ax,
     rr += ri * ri;
     bb += bi * bi;
   }
-  double s1 = block_sum((double)rr, red);
-  double s2 = block_sum((double)bb, red);
+  double s1 = block_sum(rr, red);
+  double s2 = block_sum(bb, red);
   double vals[2] = {s1, s2};
   double out[2];
   if (last_block_reduce(partials, 2, vals, &sc->ticket, out, red) && threadIdx.x == 0) {
@@ -830,10 +831,12 @@ k_split_df(int64_t n, const double* __restrict__ b, df64* __restrict__ b_df,
     bb = fmaf(v.hi, v.hi, bb);
     const double xi = x[i];
     x_df[i] = df_from_double_int(xi);
-    nz |= ((unsigned long long)__double_as_longlong(xi) << 1) != 0ull;  // x != 0, no FP64 op
+    unsigned xl, xh;
+    double_halves(xi, &xl, &xh);
+    nz |= (xl | (xh << 1)) != 0u;  // x != 0 by integer operations
   }
   if (__syncthreads_or(nz) && threadIdx.x == 0) atomicOr(&sc->xnz, 1);
-  double s = block_sum((double)bb, red);
+  double s = block_sum(bb, red);
   double vals[1] = {s};
   double o[1];
   if (last_block_reduce(partials, 1, vals, &sc->ticket, o, red) && threadIdx.x == 0) sc->bb = o[0];
@@ -861,7 +864,7 @@ k_residual_df(MeshDev m, const df64* __restrict__ bands, Coefs<df64> cf,
   if (xnz) {
     LoadPlain<df64> ld{x};
     EpiResidualDf ep{b, r, r32};
-    const double d = apply_tile<K, S, df64>(m, bands, cf, ld, ep, reinterpret_cast<df64*>(smraw));
+    const float d = apply_tile<K, S, df64>(m, bands, cf, ld, ep, reinterpret_cast<df64*>(smraw));
     const double s = block_sum(d, red);
     double vals[1] = {s};
     double out[1];
@@ -891,7 +894,7 @@ k_cg_apply_df(MeshDev m, const df64* __restrict__ bands, Coefs<df64> cf,
   __shared__ double red[32];
   LoadDirDf ld{z, p_old, p_new, first ? df64(0.f) : df_from_double(sc->beta), first != 0};
   EpiStoreDf ep{Ap};
-  double d = apply_tile<K, S, df64>(m, bands, cf, ld, ep, reinterpret_cast<df64*>(smraw));
+  const float d = apply_tile<K, S, df64>(m, bands, cf, ld, ep, reinterpret_cast<df64*>(smraw));
   double s = block_sum(d, red);
   double vals[1] = {s};
   double out[1];
@@ -920,7 +923,7 @@ k_cg_update_df(int64_t n, df64* __restrict__ x, df64* __restrict__ r, const df64
     r32[i] = v.hi;
     rr = fmaf(v.hi, v.hi, rr);
   }
-  double s = block_sum((double)rr, red);
+  double s = block_sum(rr, red);
   double vals[1] = {s};
   double out[1];
   if (last_block_reduce(partials, 1, vals, &sc->ticket, out, red) && threadIdx.x == 0) {
