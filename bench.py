@@ -46,7 +46,11 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 # DRAM bytes (read + write) per launch of a kernel on the headline bed, from
 # one ncu capture of that kernel as it is now (dram__bytes_read.sum +
 # dram__bytes_write.sum); an entry is removed when its kernel changes
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    "void_fraction": 3751424,    # k_qcm_pts<2>
+    "op32": 8769408,             # k_cg_apply_df<2>: mean of the two productive launches
+    "forces": 20116480,          # k_forces<2,1,float>
+}
 # algorithmic work per unit (the per-unit figures of the measurement plan):
 #   QCM: 8 flops per tested (Gauss point, particle) pair, 25 per lens volume
 #   operator: 7 banded 1D applies x (2k+1) taps x 2 flops + 5 per node
@@ -56,9 +60,22 @@ NCU_TRAFFIC = {}
 QCM_FLOPS_TEST, QCM_FLOPS_LENS = 8.0, 25.0
 
 
-def _forces_flops(k, kp):
-    nk, np_ = (k + 1) ** 3, (kp + 1) ** 3
-    return 8.0 * nk + 6.0 * np_ + 3 * 10.0 * (k + 1 + kp + 1) + 60.0
+def _forces_bytes(w, n_nodes):
+    """Algorithmic HBM bytes of one launch of the force kernel: per particle
+    x, r, u_p read and f, f_drag, its source record and element written
+    (140 B); the nodal velocity and void fraction (32 B per node) and the
+    pressure (8 B per pressure node) of the elements that hold particles,
+    read once."""
+    x = np.asarray(w["x"])
+    o = np.asarray(w["origin"], dtype=np.float64)
+    ne = np.asarray(w["n_el"])
+    h = np.asarray(w["extent"], dtype=np.float64) / ne
+    k, kp = w["k"], w["params"]["pressure_degree"]
+    c = np.clip(np.floor((x - o) / h).astype(np.int64), 0, ne - 1)
+    held = np.unique(c[:, 0] + ne[0] * (c[:, 1] + ne[1] * c[:, 2])).size
+    frac = held / float(np.prod(ne))
+    n_p = float(np.prod(ne * kp + 1))
+    return 140.0 * x.shape[0] + frac * (32.0 * n_nodes + 8.0 * n_p)
 
 
 def _peaks():
@@ -489,7 +506,7 @@ def run_bed(env, name, steps, warmup, alu, headline=False, e2e=True, cpu=True,
     instr_peak = alu["fp32_tflops"] / 2.0    # FP32 instructions per second / 1e12
     qcm_flops = QCM_FLOPS_TEST * tests_cell + QCM_FLOPS_LENS * pairs
     qcm_flops_culled = QCM_FLOPS_TEST * tests_culled + QCM_FLOPS_LENS * pairs
-    fo_flops = _forces_flops(k, kp) * n
+    fo_bytes = _forces_bytes(w, n_nodes)
     kern = {
         "void_fraction": {
             "kernel": "k_qcm_pts<%d> (FP32 QCM, one lane per Gauss point)" % k, "bound": "alu", "unit": "TFLOP/s",
@@ -503,11 +520,13 @@ def run_bed(env, name, steps, warmup, alu, headline=False, e2e=True, cpu=True,
             "limiter": "instruction issue (ncu: compares, ballots and queue appends of the "
                        "neighbour filter are not counted as flops)"},
         "forces": {
-            "kernel": "k_forces<%d,%d,float>" % (k, kp), "bound": "alu", "unit": "TFLOP/s",
-            "ms_per_launch": fo_ms, "launches_per_step": calls["forces"], "work": fo_flops,
-            "peak": alu["fp64_tflops"], "achieved": fo_flops / (fo_ms * 1e-3) / 1e12,
-            "peak_source": "FMA probe on this device (libalupeak.so), FP64 (the FP64 "
-                           "interpolation of the slip bounds the kernel)"},
+            "kernel": "k_forces<%d,%d,float>" % (k, kp), "bound": "hbm", "unit": "GB/s",
+            "ms_per_launch": fo_ms, "launches_per_step": calls["forces"], "work": fo_bytes,
+            "peak": hbm, "achieved": fo_bytes / (fo_ms * 1e-3) / 1e9,
+            "peak_source": "%s MEASURED_PEAKS.json hbm_gbs" % peak_kind,
+            "limiter": "latency of the per-particle gathers of the element's nodal values "
+                       "(long scoreboard; ~40 % of issue slots); no FP64 instruction per node "
+                       "on the mixed path"},
         "op32": {
             "kernel": "k_cg_apply_df<%d> (double-float CG operator on the FP32 pipes)" % k,
             "bound": "alu", "unit": "T FP32 instructions/s", "ms_per_launch": op_ms,

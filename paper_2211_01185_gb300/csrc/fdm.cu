@@ -349,7 +349,7 @@ __host__ __device__ __forceinline__ int slab_pad(int n) { return ((n + 7) & ~7) 
 // and sets rz and the Fletcher-Reeves beta = rz_new / rz_old (not on the
 // first application) -- the dot product kernel that would read r and z
 // again is not launched.
-template <int TILE>
+template <int TR, int TC>
 __global__ void k_fdm_slab(int nx, int ny, int nz, const float* __restrict__ Bx,
                            const float* __restrict__ AyT, const float* __restrict__ in,
                            int in_stride, float* __restrict__ out, int out_stride,
@@ -376,10 +376,10 @@ __global__ void k_fdm_slab(int nx, int ny, int nz, const float* __restrict__ Bx,
     cp_async_wait_all();
     __syncthreads();
     // PT[x][y'] = sum_y AyT[y][y'] X[y][x]
-    smem_gemm<TILE, TILE, true>(MA, py, X, px, PT, py, ny, nx, ny);
+    smem_gemm<TR, TC, true>(MA, py, X, px, PT, py, ny, nx, ny);
     __syncthreads();
     // Y[y'][x'] = sum_x PT[x][y'] Bx[x][x']
-    smem_gemm<TILE, TILE, false>(PT, py, MB, px, Y, px, ny, nx, nx);
+    smem_gemm<TR, TC, false>(PT, py, MB, px, Y, px, ny, nx, nx);
     __syncthreads();
     float* dst = out + (int64_t)z * out_stride;
     const float* rr = dot.r ? dot.r + (int64_t)z * nx * ny : nullptr;
@@ -657,6 +657,11 @@ void band_ldlt_factors(int nz, int k, const std::vector<double>& Mz,
 
 }  // namespace
 
+// threads of k_fdm_slab<tr, tc> for an nx x ny slab (whole warps)
+static int slab_threads_for(int nx, int ny, int tr, int tc) {
+  return ((((ny + tr - 1) / tr) * ((nx + tc - 1) / tc) + 31) / 32) * 32;
+}
+
 struct FdmPlan {
   int n[3] = {0, 0, 0};
   int k = 1;
@@ -666,7 +671,7 @@ struct FdmPlan {
   int zseg = 8;               // slab form: z-segments of the banded solves (8 or 16)
   size_t slab_smem = 0, z_smem = 0;
   int slab_threads = 256;
-  int slab_tile = 8;          // register tile of the slab transforms (4 or 8)
+  int slab_tr = 4, slab_tc = 4;  // register tile of the slab transforms (rows x columns)
   int ms = 0;                 // slab form: padded plane stride of tmp and fac
   // V_a and V_a^T row-major; in the slab form (axes x, y only) with rows
   // zero-padded to slab_pad(n_a)
@@ -676,6 +681,8 @@ struct FdmPlan {
   float* tmp = nullptr;                        // work vector
   cublasHandle_t blas = nullptr;
 };
+
+static cudaError_t tune_slab(FdmPlan* p);
 
 void fdm_destroy(FdmPlan* p) {
   if (!p) return;
@@ -709,9 +716,10 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4], 
     // k_fdm_slab: X / Y [ny][px], PT [nx][py], Bx [nx][px], AyT [ny][py]
     p->slab_smem = (ny * px + nx * py + nx * px + ny * py) * sizeof(float);
     // 4 x 4 register tiles (more warps per slab) where the thread count allows
-    p->slab_tile = ((nx + 3) / 4) * ((ny + 3) / 4) <= 1024 ? 4 : 8;
-    const int tl = p->slab_tile;
-    p->slab_threads = ((((nx + tl - 1) / tl) * ((ny + tl - 1) / tl) + 31) / 32) * 32;
+    // 4 x 4 register tiles where the thread count allows (timed against the
+    // other shapes once the plan is built)
+    p->slab_tr = p->slab_tc = slab_threads_for(nx, ny, 4, 4) <= 1024 ? 4 : 8;
+    p->slab_threads = slab_threads_for(nx, ny, p->slab_tr, p->slab_tc);
     if (p->slab_threads > 1024) p->slab_smem = (size_t)1 << 30;  // dense form instead
   }
   // 16 z-segments where the lines, factors, states and transfer matrices fit
@@ -786,10 +794,16 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4], 
     // form's own limit, which leaves room for it
     const int slab_cap = std::min(optin, kSlabSmemMax);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_fdm_slab<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(k_fdm_slab<4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                slab_cap);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_fdm_slab<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(k_fdm_slab<4, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               slab_cap);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_fdm_slab<8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               slab_cap);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_fdm_slab<8, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                slab_cap);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_fdm_zsolve<1, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -809,6 +823,7 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4], 
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_fdm_zsolve<3, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                optin);
+    if (e == cudaSuccess) e = tune_slab(p);
   } else if (e == cudaSuccess) {
     double* dl[3] = {nullptr, nullptr, nullptr};
     for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
@@ -840,6 +855,74 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4], 
   return cudaSuccess;
 }
 
+static void launch_slab(const FdmPlan* p, int nblk, cudaStream_t s, const float* Bx,
+                        const float* AyT, const float* in, int is, float* out, int os,
+                        const int* done, FdmDot dd) {
+  const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
+#define CFDEM_SLAB(TR_, TC_)                                                                 \
+  k_fdm_slab<TR_, TC_><<<nblk, p->slab_threads, p->slab_smem, s>>>(nx, ny, nz, Bx, AyT, in, is, \
+                                                                   out, os, done, dd)
+  if (p->slab_tr == 4 && p->slab_tc == 4) CFDEM_SLAB(4, 4);
+  else if (p->slab_tr == 4) CFDEM_SLAB(4, 8);
+  else if (p->slab_tc == 4) CFDEM_SLAB(8, 4);
+  else CFDEM_SLAB(8, 8);
+#undef CFDEM_SLAB
+}
+
+// The register tile of the slab transforms: each shape whose thread count
+// fits is timed on the plan's own sizes (the forward transform of a zeroed
+// work vector, CUDA events, best of five after two warm-up launches) and the
+// fastest kept.  Every shape sums each output over the same k order, so the
+// choice does not change a bit of the result.
+static cudaError_t tune_slab(FdmPlan* p) {
+  const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
+  const int nm = nx * ny;
+  const int nblk = nz < 304 ? nz : 304;
+  const int shapes[4][2] = {{4, 4}, {4, 8}, {8, 4}, {8, 8}};
+  cudaError_t e = cudaMemset(p->tmp, 0, ((size_t)nz * p->ms + (size_t)nm * nz) * sizeof(float));
+  if (e != cudaSuccess) return e;
+  cudaEvent_t a, b;
+  if ((e = cudaEventCreate(&a)) != cudaSuccess) return e;
+  if ((e = cudaEventCreate(&b)) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return e;
+  }
+  float best = 1e30f;
+  int btr = p->slab_tr, btc = p->slab_tc;
+  for (const auto& sh : shapes) {
+    const int th = slab_threads_for(nx, ny, sh[0], sh[1]);
+    if (th > 1024) continue;
+    p->slab_tr = sh[0];
+    p->slab_tc = sh[1];
+    p->slab_threads = th;
+    float tmin = 1e30f;
+    for (int it = 0; it < 7 && e == cudaSuccess; ++it) {
+      e = cudaEventRecord(a, 0);
+      if (e == cudaSuccess)
+        launch_slab(p, nblk, 0, p->V[0], p->V[1], p->tmp, p->ms, p->tmp + (size_t)nz * p->ms,
+                    nm, nullptr, FdmDot{});
+      if (e == cudaSuccess) e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaEventRecord(b, 0);
+      if (e == cudaSuccess) e = cudaEventSynchronize(b);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+      if (e == cudaSuccess && it >= 2 && ms < tmin) tmin = ms;
+    }
+    if (e != cudaSuccess) break;
+    if (tmin < best) {
+      best = tmin;
+      btr = sh[0];
+      btc = sh[1];
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  p->slab_tr = btr;
+  p->slab_tc = btc;
+  p->slab_threads = slab_threads_for(nx, ny, btr, btc);
+  return e;
+}
+
 // z = A^-1 r (FP32), r is preserved.  Uses p->tmp.  The slab-form kernels
 // return at once when *done is set (a converged CG), so iterations can be
 // queued without host round trips.
@@ -852,12 +935,7 @@ cudaError_t fdm_apply(FdmPlan* p, const float* r, float* z, const int* done, cud
     int nm = nx * ny;
     auto slab = [&](const float* Bx, const float* AyT, const float* in, int is, float* out,
                     int os, FdmDot dd) {
-      if (p->slab_tile == 4)
-        k_fdm_slab<4><<<nblk, p->slab_threads, p->slab_smem, s>>>(nx, ny, nz, Bx, AyT, in, is,
-                                                                   out, os, done, dd);
-      else
-        k_fdm_slab<8><<<nblk, p->slab_threads, p->slab_smem, s>>>(nx, ny, nz, Bx, AyT, in, is,
-                                                                   out, os, done, dd);
+      launch_slab(p, nblk, s, Bx, AyT, in, is, out, os, done, dd);
     };
     slab(p->V[0], p->V[1], r, nm, p->tmp, p->ms, FdmDot{});
     unsigned zb = (unsigned)((nm + 31) / 32);

@@ -270,12 +270,21 @@ struct Tile {
   static constexpr int NT = TZ * YW * XW;     // after the z pass (each of t1, t2)
   static constexpr int NU = TZ * TY * XW;     // after the y pass (each of U, V)
   static constexpr int NO = TZ * TY * TX;     // owned nodes (their input, for the epilogue)
-  // U, V reuse the input's space once the z pass has read it, when they fit
+  // Two layouts: the z pass writes t1, t2 over the input (each thread
+  // overwrites only the column it has read), with U, V apart; or t1, t2
+  // apart and U, V over the input once the z pass is done.  The smaller one
+  // is used.
   static constexpr bool UV_IN_X = 2 * NU <= NX;
+  static constexpr int RA = NX > 2 * NT ? NX : 2 * NT;
+  static constexpr int SZ_TX = RA + 2 * NU;
+  static constexpr int SZ_UX = NX + 2 * NT + (UV_IN_X ? 0 : 2 * NU);
+  static constexpr bool T_IN_X = SZ_TX < SZ_UX;
+  static constexpr int SZ = T_IN_X ? SZ_TX : SZ_UX;
   // band coefficients of the tile's rows: z (M, K), y (three folded
   // combinations), x (M, K)
   static constexpr int NBZ = 2 * TZ * W, NBY = 3 * TY * W, NBX = 2 * TX * W;
-  static constexpr int NSM = NX + 2 * NT + (UV_IN_X ? 0 : 2 * NU) + NO + NBZ + NBY + NBX;
+  // with XE: the owned nodes' input kept for the epilogue
+  static constexpr int nsm(bool xe) { return SZ + (xe ? NO : 0) + NBZ + NBY + NBX; }
   // y pass: one thread per (chunk of CY rows, z, x) column piece, the number
   // of chunks chosen for the fewest row outputs per thread over whole rounds
   // of the block's threads
@@ -388,6 +397,7 @@ struct LoadDirDf {
 template <typename T>
 struct EpiStore {
   using acc_t = T;
+  static constexpr bool kXE = true;
   T* y;
   __device__ __forceinline__ T operator()(int64_t g, T acc, T xe) const {
     y[g] = acc;
@@ -397,16 +407,19 @@ struct EpiStore {
 // df64 image of an FP32 direction: store, dot with the high part
 struct EpiStoreDf {
   using acc_t = float;
+  static constexpr bool kXE = false;
   df64* y;
-  __device__ __forceinline__ float operator()(int64_t g, df64 acc, df64 xe) const {
+  const df64* p;  // the direction, written by this block's load phase
+  __device__ __forceinline__ float operator()(int64_t g, df64 acc, df64) const {
     y[g] = acc;
-    return xe.hi * acc.hi;
+    return __ldcg(reinterpret_cast<const float*>(p + g)) * acc.hi;
   }
 };
 // residual r = b - A x in df64; r32 = high part (input of the FP32
 // preconditioner); returns r.r from the high parts
 struct EpiResidualDf {
   using acc_t = float;
+  static constexpr bool kXE = false;
   const df64* b;
   df64* r;
   float* r32;
@@ -442,13 +455,14 @@ __device__ __forceinline__ typename Epi::acc_t apply_tile(const MeshDev& m,
   const int nx = m.nn[0], ny = m.nn[1], nz = m.nn[2];
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
   const int64_t sxy = (int64_t)nx * ny;
-  T* X = sm;                 // [ZW][YW][XW]
-  T* T1 = sm + TL::NX;       // [TZ][YW][XW]
+  constexpr bool kXE = Epi::kXE;
+  T* X = sm;                                         // [ZW][YW][XW]
+  T* T1 = TL::T_IN_X ? sm : sm + TL::NX;             // [TZ][YW][XW]
   T* T2 = T1 + TL::NT;
-  T* U = TL::UV_IN_X ? X : T2 + TL::NT;   // [TZ][TY][XW], over X once the z pass is done
+  T* U = TL::T_IN_X ? sm + TL::RA : (TL::UV_IN_X ? X : T2 + TL::NT);  // [TZ][TY][XW]
   T* V = U + TL::NU;
-  T* XE = TL::UV_IN_X ? T2 + TL::NT : V + TL::NU;  // [TZ][TY][TX] input at the owned nodes
-  T* BZ = XE + TL::NO;       // [TZ][W][2]   Mz, Kz of row z0 + o
+  T* XE = sm + TL::SZ;       // [TZ][TY][TX] input at the owned nodes (kXE)
+  T* BZ = XE + (kXE ? TL::NO : 0);  // [TZ][W][2]   Mz, Kz of row z0 + o
   T* BY = BZ + TL::NBZ;      // [TY][W][3]   cM My + cKy Ky, cKz My, cKx My of row y0 + j
   T* BX = BY + TL::NBY;      // [2][W][TX]   Mx, Kx of column x0 + i
   const T* bMx = bands;
@@ -502,7 +516,7 @@ __device__ __forceinline__ typename Epi::acc_t apply_tile(const MeshDev& m,
     if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz) {
       const bool own = lx >= H && lx < H + TX && ly >= H && ly < H + TY && lz >= H && lz < H + TZ;
       v = ld(gx + (int64_t)nx * gy + sxy * gz, own);
-      if (own) XE[((lz - H) * TY + (ly - H)) * TX + (lx - H)] = v;
+      if (kXE && own) XE[((lz - H) * TY + (ly - H)) * TX + (lx - H)] = v;
     }
     X[t] = v;
     nonzero |= (v != T(0));
@@ -517,7 +531,8 @@ __device__ __forceinline__ typename Epi::acc_t apply_tile(const MeshDev& m,
     }
     return dot;
   }
-  // z pass: column c of the haloed x-y plane, all TZ outputs
+  // z pass: column c of the haloed x-y plane, all TZ outputs (with T_IN_X
+  // written over the column's input, which this thread has read first)
   for (int c = threadIdx.x; c < PL; c += blockDim.x) {
     T xv[ZW];
 #pragma unroll
@@ -590,7 +605,7 @@ __device__ __forceinline__ typename Epi::acc_t apply_tile(const MeshDev& m,
       ax.add(BX[w * TX + lx], u[w]);
       ax.add(BX[(W + w) * TX + lx], v[w]);
     }
-    dot += ep(gx + (int64_t)nx * gy + sxy * gz, ax.get(), XE[t]);
+    dot += ep(gx + (int64_t)nx * gy + sxy * gz, ax.get(), kXE ? XE[t] : T(0));
   }
   return dot;
 }
@@ -893,7 +908,7 @@ k_cg_apply_df(MeshDev m, const df64* __restrict__ bands, Coefs<df64> cf,
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double red[32];
   LoadDirDf ld{z, p_old, p_new, first ? df64(0.f) : df_from_double(sc->beta), first != 0};
-  EpiStoreDf ep{Ap};
+  EpiStoreDf ep{Ap, p_new};
   const float d = apply_tile<K, S, df64>(m, bands, cf, ld, ep, reinterpret_cast<df64*>(smraw));
   double s = block_sum(d, red);
   double vals[1] = {s};
@@ -996,10 +1011,11 @@ __global__ void k_add_scaled(int64_t n, double* __restrict__ x, const float* __r
 // ---------------------------------------------------------------------------
 // host side
 
+// the double-float kernels' epilogues keep no copy of the input (kXE false)
 template <int K, class S, typename T>
 static size_t apply_smem() {
   using TL = Tile<K, S>;
-  return (size_t)TL::NSM * sizeof(T);
+  return (size_t)TL::nsm(!std::is_same<T, df64>::value) * sizeof(T);
 }
 
 template <class S>
