@@ -270,7 +270,10 @@ void build_tables(int k, int kp, Tables* t) {
   double l[4][4], dl[4][4];  // [q][a]
   for (int q = 0; q < nq; ++q) lagr(k, t->z, t->lw, t->g[q], l[q], dl[q]);
   for (int a = 0; a <= k; ++a)
-    for (int q = 0; q < nq; ++q) t->Bw[a][q] = l[q][a] * t->w[q];
+    for (int q = 0; q < nq; ++q) {
+      t->Bw[a][q] = l[q][a] * t->w[q];
+      t->Bwf[a][q] = (float)t->Bw[a][q];
+    }
   // exact with nq = k + 1 Gauss points (degree 2k integrands)
   for (int a = 0; a <= k; ++a)
     for (int bb = 0; bb <= k; ++bb) {
@@ -849,6 +852,7 @@ cfdem_status cfdem_set_mesh(cfdem_t c, const double origin[3], const double exte
   m.E = (int64_t)m.ne[0] * m.ne[1] * m.ne[2];
   m.n_nodes = (int64_t)m.nn[0] * m.nn[1] * m.nn[2];
   m.Ve = m.h[0] * m.h[1] * m.h[2];
+  m.Ve32 = (float)m.Ve;
   if (m.E * m.Q > ((int64_t)1 << 31) || m.n_nodes > ((int64_t)1 << 31))
     return fail(c, CFDEM_EINVAL, "mesh too large");
   m.shape = pick_shape(m);

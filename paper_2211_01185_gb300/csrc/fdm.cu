@@ -14,9 +14,12 @@
 //  * slab form (default): only x and y are diagonalised.  For a mode (i, j)
 //    the z operator is the banded SPD matrix s_ij Mz + cKz Kz with s_ij = cM +
 //    cKx lam_x,i + cKy lam_y,j, factorised A = L D L^T on the host.  One
-//    kernel transforms each z-slab with Vx, Vy^T in shared memory, one solves
-//    the banded systems along z (one lane per mode), one transforms back:
-//    about 4 (nx + ny) + 6 k flops per node instead of 4 (nx + ny + nz).
+//    kernel transforms each z-slab in shared memory, one solves the banded
+//    systems along z (one lane per mode), one transforms back.  The 1D
+//    matrices of a uniform axis are persymmetric, so the eigenvectors are
+//    symmetric or antisymmetric and each 1D transform is a butterfly
+//    (x_i +- x_(n-1-i)) and two half-size products (see SlabAxis): about
+//    2 (nx + ny) + 6 k flops per node instead of 4 (nx + ny + nz).
 //  * dense form (slabs too large for shared memory): the six 1D transforms as
 //    plain dense GEMMs (cuBLAS SGEMM, FP32 math, no TF32).
 //
@@ -40,6 +43,37 @@ namespace cfdem {
 namespace {
 
 constexpr int kSlabSmemMax = 220 * 1024;  // dynamic shared memory of the slab form, at most
+
+// padded row length of the slab-form transform matrices and tiles: a
+// multiple of 8 for the 8 x 8 register tiles, plus 4 against bank conflicts
+__host__ __device__ __forceinline__ int slab_pad(int n) { return ((n + 7) & ~7) + 4; }
+
+// Parity split of one axis of n nodes.  On a uniform axis the mass and
+// stiffness matrices are persymmetric (unchanged by reversing the node
+// order), so their generalised eigenvectors split into symmetric ones (ye of
+// them) and antisymmetric ones (yo): with s_i = x_i + x_(n-1-i) and
+// d_i = x_i - x_(n-1-i) (i < n/2; s also holds the middle node for odd n),
+// the forward transform is y_e = Ce^T s, y_o = Co^T d, and the inverse
+// (a = Ce y_e, b = Co y_o) writes x_i = a_i + b_i, x_(n-1-i) = a_i - b_i --
+// half the multiply-adds of the full transform.  In shared memory an axis
+// is held in "slots": positions (or modes) 0 .. ye-1 in slots 0 .. ye-1,
+// the rest from slot oe = ye rounded up to 4, so that both halves start
+// 16-byte aligned; d_i sits in the slot of x_(n-1-i).
+struct SlabAxis {
+  int n, ye, oe, sl;  // nodes, symmetric count, start of the second half, slots
+};
+__host__ __device__ __forceinline__ SlabAxis slab_axis(int n) {
+  SlabAxis a;
+  a.n = n;
+  a.ye = (n + 1) / 2;
+  a.oe = (a.ye + 3) & ~3;
+  a.sl = a.oe + n / 2;
+  return a;
+}
+__host__ __device__ __forceinline__ int slot_of(const SlabAxis& a, int p) {
+  return p < a.ye ? p : a.oe + (p - a.ye);
+}
+
 
 // symmetric eigen-decomposition: A (n x n, row-major) is replaced by the
 // eigenvectors (columns), w receives the eigenvalues.  Returns false if the
@@ -220,6 +254,74 @@ bool gen_eig(int n, const std::vector<double>& M, const std::vector<double>& K,
   return err < 1e-9;
 }
 
+// Generalised eigenpairs of a persymmetric pair (M, K) on its symmetric and
+// antisymmetric subspaces (orthonormal bases (e_i +- e_(n-1-i)) / sqrt 2 and
+// the middle e_(n/2) for odd n; the antisymmetric vector of slot t pairs
+// i = n/2 - 1 - t).  G (sl x sl, row-major, slots of slab_axis(n)) receives
+// the folded transforms Ce = D Ve, Co = Vo / sqrt 2 on its diagonal blocks
+// (D = 1 / sqrt 2, 1 for the middle node), lam the eigenvalues in mode
+// order (symmetric first).  False if (M, K) is not persymmetric to 1e-12 of
+// its largest entry, or an eigen-decomposition fails its check.
+bool parity_eig(int n, const std::vector<double>& M, const std::vector<double>& K,
+                std::vector<double>& G, std::vector<double>& lam) {
+  const SlabAxis ax = slab_axis(n);
+  const int my = n / 2, ye = ax.ye, yo = n / 2;
+  double mm = 0.0, km = 0.0;
+  for (size_t i = 0; i < M.size(); ++i) {
+    mm = std::fmax(mm, std::fabs(M[i]));
+    km = std::fmax(km, std::fabs(K[i]));
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const size_t a = i * (size_t)n + j, b = (n - 1 - i) * (size_t)n + (n - 1 - j);
+      if (std::fabs(M[a] - M[b]) > 1e-12 * mm || std::fabs(K[a] - K[b]) > 1e-12 * km)
+        return false;
+    }
+  const double r2 = 1.0 / std::sqrt(2.0);
+  // basis vectors: two entries each (index, weight)
+  auto sym = [&](int i, int* p, double* w) {
+    if (i < my) {
+      p[0] = i, p[1] = n - 1 - i, w[0] = w[1] = r2;
+    } else {
+      p[0] = p[1] = my, w[0] = 1.0, w[1] = 0.0;
+    }
+  };
+  auto anti = [&](int t, int* p, double* w) {
+    const int i = my - 1 - t;
+    p[0] = i, p[1] = n - 1 - i, w[0] = r2, w[1] = -r2;
+  };
+  auto reduce = [&](int m, auto basis, const std::vector<double>& A, std::vector<double>& R) {
+    R.assign(m * (size_t)m, 0.0);
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) {
+        int pi[2], pj[2];
+        double wi[2], wj[2];
+        basis(i, pi, wi);
+        basis(j, pj, wj);
+        double v = 0.0;
+        for (int a = 0; a < 2; ++a)
+          for (int b = 0; b < 2; ++b) v += wi[a] * A[pi[a] * (size_t)n + pj[b]] * wj[b];
+        R[i * (size_t)m + j] = v;
+      }
+  };
+  std::vector<double> Me, Ke, Mo, Ko, Ve, Vo, le, lo;
+  reduce(ye, sym, M, Me);
+  reduce(ye, sym, K, Ke);
+  reduce(yo, anti, M, Mo);
+  reduce(yo, anti, K, Ko);
+  if (!gen_eig(ye, Me, Ke, Ve, le)) return false;
+  if (yo > 0 && !gen_eig(yo, Mo, Ko, Vo, lo)) return false;
+  G.assign(ax.sl * (size_t)ax.sl, 0.0);
+  for (int i = 0; i < ye; ++i)
+    for (int j = 0; j < ye; ++j) G[i * (size_t)ax.sl + j] = (i < my ? r2 : 1.0) * Ve[i * (size_t)ye + j];
+  for (int t = 0; t < yo; ++t)
+    for (int u = 0; u < yo; ++u)
+      G[(ax.oe + t) * (size_t)ax.sl + ax.oe + u] = r2 * Vo[t * (size_t)yo + u];
+  lam = le;
+  lam.insert(lam.end(), lo.begin(), lo.end());
+  return true;
+}
+
 __global__ void k_fdm_dinv(int nx, int ny, int nz, const double* __restrict__ lx,
                            const double* __restrict__ ly, const double* __restrict__ lz,
                            double cM, double cKx, double cKy, double cKz,
@@ -250,7 +352,8 @@ cublasStatus_t gemm_rm(cublasHandle_t h, int M, int N, int K, const float* A, lo
 }
 
 // C[M x N] = A[M x K] B[K x N] in shared memory with A stored transposed
-// (AT[K][lda]) and B row-major (B[K][ldb]); lda, ldb multiples of 4 floats.
+// (AT[K][lda]) and B row-major (B[K][ldb]); lda, ldb multiples of 4 floats
+// and AT, B, C 16-byte aligned.
 // Each thread owns a TR x TC block of C (TR, TC = 4 or 8), so one k step is
 // TR/4 + TC/4 128-bit loads and TR TC FMAs; the loads of step k + 1 are
 // issued before the FMAs of step k.  Threads form a gm x gn grid (gm =
@@ -258,11 +361,11 @@ cublasStatus_t gemm_rm(cublasHandle_t h, int M, int N, int K, const float* A, lo
 // are not stored.  With TRANS_C the block is stored transposed, C[c][r]
 // (row length ldc, a multiple of 4), as 128-bit stores.
 template <int TR, int TC, bool TRANS_C>
-__device__ __forceinline__ void smem_gemm(const float* AT, int lda, const float* B, int ldb,
-                                          float* C, int ldc, int M, int N, int K) {
+__device__ __forceinline__ void smem_gemm(int tbase, const float* AT, int lda, const float* B,
+                                          int ldb, float* C, int ldc, int M, int N, int K) {
   const int gn = (N + TC - 1) / TC, gm = (M + TR - 1) / TR;
-  const int tid = threadIdx.x;
-  if (tid >= gm * gn) return;
+  const int tid = (int)threadIdx.x - tbase;  // threads [tbase, tbase + gm gn) take part
+  if (tid < 0 || tid >= gm * gn) return;
   const int r0 = (tid / gn) * TR, c0 = (tid % gn) * TC;
   float acc[TR][TC];
 #pragma unroll
@@ -297,14 +400,17 @@ __device__ __forceinline__ void smem_gemm(const float* AT, int lda, const float*
     for (int q = 0; q < TC / 4; ++q) bv[q] = bn[q];
   }
   if (TRANS_C) {
+    // 128-bit stores of row groups that hold at least one row < M: the
+    // writes stay below M rounded up to 4
 #pragma unroll
     for (int y = 0; y < TC; ++y) {
       const int c = c0 + y;
       if (c >= N) continue;
 #pragma unroll
       for (int q = 0; q < TR / 4; ++q)
-        *reinterpret_cast<float4*>(C + c * ldc + r0 + 4 * q) =
-            make_float4(acc[4 * q][y], acc[4 * q + 1][y], acc[4 * q + 2][y], acc[4 * q + 3][y]);
+        if (r0 + 4 * q < M)
+          *reinterpret_cast<float4*>(C + c * ldc + r0 + 4 * q) =
+              make_float4(acc[4 * q][y], acc[4 * q + 1][y], acc[4 * q + 2][y], acc[4 * q + 3][y]);
     }
   } else {
 #pragma unroll
@@ -331,17 +437,20 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
-// padded row length of the slab-form transform matrices and tiles: a
-// multiple of 8 for the 8 x 8 register tiles, plus 4 against bank conflicts
-__host__ __device__ __forceinline__ int slab_pad(int n) { return ((n + 7) & ~7) + 4; }
+struct SlabArgs {
+  int nx, ny, nz;
+  const float* My;  // y transform, [sl_y][slab_pad(sl_y)] (block diagonal in slots)
+  const float* Mx;  // x transform, [sl_x][slab_pad(sl_x)]
+};
 
-// forward: out_z = (Vy^T in_z) Vx; inverse: out_z = (Vy in_z) Vx^T, for every
-// z-slab.  AyT is the transpose of the left factor of the y transform
-// ([ny][slab_pad(ny)]), Bx the right factor of the x transform
-// ([nx][slab_pad(nx)]), both zero-padded row-major in global memory and
-// copied to shared memory as they are.  The slab is staged as it lies in
-// memory (row y, lanes along x) as the B operand of the first product, whose
-// result is stored transposed as the A operand of the second.
+// Forward (INV = false): out_z = modes of in_z, the y transform then the x
+// transform, each as a butterfly (s, d) then two half-size products (My, Mx
+// hold Ce and Co on their diagonal blocks).  Inverse (INV = true): the
+// products with the transposed blocks, then the butterfly that unfolds
+// them.  Mode order in global memory: the symmetric modes of an axis first,
+// then the antisymmetric ones (the z solves take their eigenvalues in that
+// order).  One block per z-slab; the two halves of each product run side by
+// side on two groups of whole warps.
 //
 // With dot.r set (the inverse transform that writes z), the kernel also
 // forms r . z of the CG from the values it stores: one FP32 sum per thread,
@@ -349,46 +458,104 @@ __host__ __device__ __forceinline__ int slab_pad(int n) { return ((n + 7) & ~7) 
 // and sets rz and the Fletcher-Reeves beta = rz_new / rz_old (not on the
 // first application) -- the dot product kernel that would read r and z
 // again is not launched.
-template <int TR, int TC>
-__global__ void k_fdm_slab(int nx, int ny, int nz, const float* __restrict__ Bx,
-                           const float* __restrict__ AyT, const float* __restrict__ in,
-                           int in_stride, float* __restrict__ out, int out_stride,
+template <int TR, int TC, bool INV>
+__global__ void k_fdm_slab(SlabArgs sa, const float* __restrict__ in, int in_stride,
+                           float* __restrict__ out, int out_stride,
                            const int* __restrict__ done, FdmDot dot) {
   if (done && *(volatile const int*)done) return;
   __shared__ double red[32];
   float rz = 0.f;
   extern __shared__ __align__(16) float fsm[];
-  const int px = slab_pad(nx), py = slab_pad(ny);
-  float* X = fsm;                  // [ny][px]   slab as it lies
-  float* Y = X;                    // [ny][px]   result (reuses the slab's space)
-  float* PT = X + ny * px;         // [nx][py]   after the y transform, transposed
-  float* MB = PT + nx * py;        // [nx][px]
-  float* MA = MB + nx * px;        // [ny][py]   (AyT)
-  for (int t = threadIdx.x; t < (nx * px) >> 2; t += blockDim.x)
-    cp_async16(MB + 4 * t, Bx + 4 * t);
-  for (int t = threadIdx.x; t < (ny * py) >> 2; t += blockDim.x)
-    cp_async16(MA + 4 * t, AyT + 4 * t);
+  const int nx = sa.nx, ny = sa.ny, nz = sa.nz;
+  const SlabAxis ax = slab_axis(nx), ay = slab_axis(ny);
+  const int lx = slab_pad(ax.sl), ly = slab_pad(ay.sl);
+  float* X = fsm;                   // [sl_y][lx]  slab in slots; also the result Y
+  float* PT = X + ay.sl * lx;       // [sl_x][ly]  after the y transform, transposed
+  float* MX = PT + ax.sl * ly;      // [sl_x][lx]
+  float* MY = MX + ax.sl * lx;      // [sl_y][ly]
+  for (int t = threadIdx.x; t < (ax.sl * lx) >> 2; t += blockDim.x)
+    cp_async16(MX + 4 * t, sa.Mx + 4 * t);
+  for (int t = threadIdx.x; t < (ay.sl * ly) >> 2; t += blockDim.x)
+    cp_async16(MY + 4 * t, sa.My + 4 * t);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int yo = ny / 2, xo = nx / 2;
+  // thread groups of the two halves (whole warps each)
+  const int g1 = ((((ay.ye + TR - 1) / TR) * ((ax.sl + TC - 1) / TC)) + 31) & ~31;
+  const int g2 = ((((ay.sl + TR - 1) / TR) * ((ax.ye + TC - 1) / TC)) + 31) & ~31;
   for (int z = blockIdx.x; z < nz; z += gridDim.x) {
     const float* src = in + (int64_t)z * in_stride;
-    for (int y = wid; y < ny; y += nw)
-      for (int x = lane; x < nx; x += 32) cp_async4(X + y * px + x, src + y * nx + x);
+    for (int y = wid; y < ny; y += nw) {
+      float* row = X + slot_of(ay, y) * lx;
+      for (int x = lane; x < nx; x += 32) cp_async4(row + slot_of(ax, x), src + y * nx + x);
+    }
     cp_async_wait_all();
     __syncthreads();
-    // PT[x][y'] = sum_y AyT[y][y'] X[y][x]
-    smem_gemm<TR, TC, true>(MA, py, X, px, PT, py, ny, nx, ny);
+    if (!INV) {
+      // y butterfly on the rows of X
+      for (int t = threadIdx.x; t < yo * ax.sl; t += blockDim.x) {
+        const int i = t / ax.sl, c = t - i * ax.sl;
+        float* r1 = X + i * lx + c;
+        float* r2 = X + slot_of(ay, ny - 1 - i) * lx + c;
+        const float a = *r1, b = *r2;
+        *r1 = a + b;
+        *r2 = a - b;
+      }
+      __syncthreads();
+    }
+    // y transform: PT[x slot][y slot] = sum_k MY[k][m] X[k][x], per half
+    smem_gemm<TR, TC, true>(0, MY, ly, X, lx, PT, ly, ay.ye, ax.sl, ay.ye);
+    smem_gemm<TR, TC, true>(g1, MY + ay.oe * ly + ay.oe, ly, X + ay.oe * lx, lx, PT + ay.oe, ly,
+                            yo, ax.sl, yo);
     __syncthreads();
-    // Y[y'][x'] = sum_x PT[x][y'] Bx[x][x']
-    smem_gemm<TR, TC, false>(PT, py, MB, px, Y, px, ny, nx, nx);
+    // x butterfly: forward on the rows of PT (before the x products); the
+    // inverse y unfold on the columns of PT (after the y products)
+    if (!INV) {
+      for (int t = threadIdx.x; t < xo * ay.sl; t += blockDim.x) {
+        const int i = t / ay.sl, c = t - i * ay.sl;
+        float* r1 = PT + i * ly + c;
+        float* r2 = PT + slot_of(ax, nx - 1 - i) * ly + c;
+        const float a = *r1, b = *r2;
+        *r1 = a + b;
+        *r2 = a - b;
+      }
+    } else {
+      for (int t = threadIdx.x; t < ax.sl * yo; t += blockDim.x) {
+        const int r = t / yo, i = t - r * yo;
+        float* c1 = PT + r * ly + i;
+        float* c2 = PT + r * ly + slot_of(ay, ny - 1 - i);
+        const float a = *c1, b = *c2;
+        *c1 = a + b;
+        *c2 = a - b;
+      }
+    }
     __syncthreads();
+    // x transform: Y[y slot][x slot] = sum_k PT[k][y slot] MX[k][m], per half
+    smem_gemm<TR, TC, false>(0, PT, ly, MX, lx, X, lx, ay.sl, ax.ye, ax.ye);
+    smem_gemm<TR, TC, false>(g2, PT + ax.oe * ly, ly, MX + ax.oe * lx + ax.oe, lx, X + ax.oe, lx,
+                             ay.sl, xo, xo);
+    __syncthreads();
+    if (INV) {
+      // x unfold on the columns of Y
+      for (int t = threadIdx.x; t < ay.sl * xo; t += blockDim.x) {
+        const int r = t / xo, i = t - r * xo;
+        float* c1 = X + r * lx + i;
+        float* c2 = X + r * lx + slot_of(ax, nx - 1 - i);
+        const float a = *c1, b = *c2;
+        *c1 = a + b;
+        *c2 = a - b;
+      }
+      __syncthreads();
+    }
     float* dst = out + (int64_t)z * out_stride;
     const float* rr = dot.r ? dot.r + (int64_t)z * nx * ny : nullptr;
-    for (int y = wid; y < ny; y += nw)
+    for (int y = wid; y < ny; y += nw) {
+      const float* row = X + slot_of(ay, y) * lx;
       for (int x = lane; x < nx; x += 32) {
-        const float v = Y[y * px + x];
+        const float v = row[slot_of(ax, x)];
         dst[y * nx + x] = v;
         if (rr) rz = fmaf(rr[y * nx + x], v, rz);
       }
+    }
     __syncthreads();
   }
   if (dot.r) {
@@ -657,9 +824,15 @@ void band_ldlt_factors(int nz, int k, const std::vector<double>& Mz,
 
 }  // namespace
 
-// threads of k_fdm_slab<tr, tc> for an nx x ny slab (whole warps)
+// threads of k_fdm_slab<tr, tc> for an nx x ny slab: the larger of its two
+// products, each run as two halves on groups of whole warps
 static int slab_threads_for(int nx, int ny, int tr, int tc) {
-  return ((((ny + tr - 1) / tr) * ((nx + tc - 1) / tc) + 31) / 32) * 32;
+  const SlabAxis ax = slab_axis(nx), ay = slab_axis(ny);
+  auto cnt = [&](int m, int n) { return ((m + tr - 1) / tr) * ((n + tc - 1) / tc); };
+  auto w32 = [](int t) { return (t + 31) & ~31; };
+  const int t1 = w32(cnt(ay.ye, ax.sl)) + w32(cnt(ny / 2, ax.sl));
+  const int t2 = w32(cnt(ay.sl, ax.ye)) + w32(cnt(ay.sl, nx / 2));
+  return t1 > t2 ? t1 : t2;
 }
 
 struct FdmPlan {
@@ -673,8 +846,9 @@ struct FdmPlan {
   int slab_threads = 256;
   int slab_tr = 4, slab_tc = 4;  // register tile of the slab transforms (rows x columns)
   int ms = 0;                 // slab form: padded plane stride of tmp and fac
-  // V_a and V_a^T row-major; in the slab form (axes x, y only) with rows
-  // zero-padded to slab_pad(n_a)
+  // dense form: V_a and V_a^T row-major.  Slab form (axes x, y): the folded
+  // parity transforms G_a and G_a^T over the axis' slots, rows padded to
+  // slab_pad(slots)
   float* V[3] = {nullptr, nullptr, nullptr};
   float* VT[3] = {nullptr, nullptr, nullptr};
   float* dinv = nullptr;                       // dense form: 1 / D per node
@@ -712,9 +886,10 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4], 
   for (int a = 0; a < 3; ++a) p->n[a] = m.nn[a];
   const int nx = m.nn[0], ny = m.nn[1], nz = m.nn[2];
   {
-    size_t px = slab_pad(nx), py = slab_pad(ny);
-    // k_fdm_slab: X / Y [ny][px], PT [nx][py], Bx [nx][px], AyT [ny][py]
-    p->slab_smem = (ny * px + nx * py + nx * px + ny * py) * sizeof(float);
+    const SlabAxis ax = slab_axis(nx), ay = slab_axis(ny);
+    const size_t lx = slab_pad(ax.sl), ly = slab_pad(ay.sl);
+    // k_fdm_slab: X / Y [sl_y][lx], PT [sl_x][ly], MX [sl_x][lx], MY [sl_y][ly]
+    p->slab_smem = (ay.sl * lx + ax.sl * ly + ax.sl * lx + ay.sl * ly) * sizeof(float);
     // 4 x 4 register tiles (more warps per slab) where the thread count allows
     // 4 x 4 register tiles where the thread count allows (timed against the
     // other shapes once the plan is built)
@@ -736,20 +911,24 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4], 
   const int naxes = p->slab ? 2 : 3;
   for (int a = 0; a < naxes && e == cudaSuccess; ++a) {
     const int n = m.nn[a];
-    const int ld = p->slab ? slab_pad(n) : n;
     std::vector<double> M, K, V;
     assemble_1d(m.ne[a], m.k, t.Mh, M);
     assemble_1d(m.ne[a], m.k, t.Kh, K);
-    if (!gen_eig(n, M, K, V, lam[a])) {
+    // slab form: the parity-split transforms over the axis' slots; dense
+    // form: the full transform
+    const int rows = p->slab ? slab_axis(n).sl : n;
+    const int ld = p->slab ? slab_pad(rows) : n;
+    const bool ok = p->slab ? parity_eig(n, M, K, V, lam[a]) : gen_eig(n, M, K, V, lam[a]);
+    if (!ok) {
       *why = "1D eigen-decomposition failed its check";
       fdm_destroy(p);
       return cudaSuccess;
     }
-    std::vector<float> v32(n * (size_t)ld, 0.f), vt32(n * (size_t)ld, 0.f);
-    for (int i = 0; i < n; ++i)
-      for (int j = 0; j < n; ++j) {
-        v32[i * (size_t)ld + j] = (float)V[i * (size_t)n + j];
-        vt32[j * (size_t)ld + i] = (float)V[i * (size_t)n + j];
+    std::vector<float> v32(rows * (size_t)ld, 0.f), vt32(rows * (size_t)ld, 0.f);
+    for (int i = 0; i < rows; ++i)
+      for (int j = 0; j < rows; ++j) {
+        v32[i * (size_t)ld + j] = (float)V[i * (size_t)rows + j];
+        vt32[j * (size_t)ld + i] = (float)V[i * (size_t)rows + j];
       }
     if ((e = cudaMalloc(&p->V[a], v32.size() * 4)) != cudaSuccess) break;
     if ((e = cudaMalloc(&p->VT[a], v32.size() * 4)) != cudaSuccess) break;
@@ -793,18 +972,19 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4], 
     // product's block sums): their dynamic share is capped at the slab
     // form's own limit, which leaves room for it
     const int slab_cap = std::min(optin, kSlabSmemMax);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_fdm_slab<4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               slab_cap);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_fdm_slab<4, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               slab_cap);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_fdm_slab<8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               slab_cap);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_fdm_slab<8, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               slab_cap);
+#define CFDEM_SLAB_ATTR(TR_, TC_, INV_)                                                     \
+  if (e == cudaSuccess)                                                                      \
+    e = cudaFuncSetAttribute(k_fdm_slab<TR_, TC_, INV_>,                                     \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, slab_cap);
+    CFDEM_SLAB_ATTR(4, 4, false)
+    CFDEM_SLAB_ATTR(4, 4, true)
+    CFDEM_SLAB_ATTR(4, 8, false)
+    CFDEM_SLAB_ATTR(4, 8, true)
+    CFDEM_SLAB_ATTR(8, 4, false)
+    CFDEM_SLAB_ATTR(8, 4, true)
+    CFDEM_SLAB_ATTR(8, 8, false)
+    CFDEM_SLAB_ATTR(8, 8, true)
+#undef CFDEM_SLAB_ATTR
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_fdm_zsolve<1, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                optin);
@@ -855,13 +1035,18 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4], 
   return cudaSuccess;
 }
 
-static void launch_slab(const FdmPlan* p, int nblk, cudaStream_t s, const float* Bx,
-                        const float* AyT, const float* in, int is, float* out, int os,
-                        const int* done, FdmDot dd) {
-  const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
-#define CFDEM_SLAB(TR_, TC_)                                                                 \
-  k_fdm_slab<TR_, TC_><<<nblk, p->slab_threads, p->slab_smem, s>>>(nx, ny, nz, Bx, AyT, in, is, \
-                                                                   out, os, done, dd)
+static void launch_slab(const FdmPlan* p, int nblk, cudaStream_t s, bool inv, const float* in,
+                        int is, float* out, int os, const int* done, FdmDot dd) {
+  SlabArgs sa{p->n[0], p->n[1], p->n[2], inv ? p->VT[1] : p->V[1], inv ? p->VT[0] : p->V[0]};
+#define CFDEM_SLAB(TR_, TC_)                                                                  \
+  do {                                                                                        \
+    if (inv)                                                                                  \
+      k_fdm_slab<TR_, TC_, true><<<nblk, p->slab_threads, p->slab_smem, s>>>(sa, in, is, out, \
+                                                                             os, done, dd);   \
+    else                                                                                      \
+      k_fdm_slab<TR_, TC_, false><<<nblk, p->slab_threads, p->slab_smem, s>>>(sa, in, is, out, \
+                                                                              os, done, dd);  \
+  } while (0)
   if (p->slab_tr == 4 && p->slab_tc == 4) CFDEM_SLAB(4, 4);
   else if (p->slab_tr == 4) CFDEM_SLAB(4, 8);
   else if (p->slab_tc == 4) CFDEM_SLAB(8, 4);
@@ -899,8 +1084,8 @@ static cudaError_t tune_slab(FdmPlan* p) {
     for (int it = 0; it < 7 && e == cudaSuccess; ++it) {
       e = cudaEventRecord(a, 0);
       if (e == cudaSuccess)
-        launch_slab(p, nblk, 0, p->V[0], p->V[1], p->tmp, p->ms, p->tmp + (size_t)nz * p->ms,
-                    nm, nullptr, FdmDot{});
+        launch_slab(p, nblk, 0, false, p->tmp, p->ms, p->tmp + (size_t)nz * p->ms, nm, nullptr,
+                    FdmDot{});
       if (e == cudaSuccess) e = cudaGetLastError();
       if (e == cudaSuccess) e = cudaEventRecord(b, 0);
       if (e == cudaSuccess) e = cudaEventSynchronize(b);
@@ -933,11 +1118,7 @@ cudaError_t fdm_apply(FdmPlan* p, const float* r, float* z, const int* done, cud
   if (p->slab) {
     int nblk = nz < 304 ? nz : 304;
     int nm = nx * ny;
-    auto slab = [&](const float* Bx, const float* AyT, const float* in, int is, float* out,
-                    int os, FdmDot dd) {
-      launch_slab(p, nblk, s, Bx, AyT, in, is, out, os, done, dd);
-    };
-    slab(p->V[0], p->V[1], r, nm, p->tmp, p->ms, FdmDot{});
+    launch_slab(p, nblk, s, false, r, nm, p->tmp, p->ms, done, FdmDot{});
     unsigned zb = (unsigned)((nm + 31) / 32);
 #define CFDEM_ZS(KK, SS)                                                                   \
   k_fdm_zsolve<KK, SS><<<zb, 32 * SS, p->z_smem, s>>>(nm, p->ms, nz, p->fac, p->tr, p->tmp, done)
@@ -951,7 +1132,7 @@ cudaError_t fdm_apply(FdmPlan* p, const float* r, float* z, const int* done, cud
       else CFDEM_ZS(3, 8);
     }
 #undef CFDEM_ZS
-    slab(p->VT[0], p->VT[1], p->tmp, p->ms, z, nm, dot ? *dot : FdmDot{});
+    launch_slab(p, nblk, s, true, p->tmp, p->ms, z, nm, done, dot ? *dot : FdmDot{});
     if (dot_done) *dot_done = dot != nullptr;
     count_launches(3);
     return cudaGetLastError();

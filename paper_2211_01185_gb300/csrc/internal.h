@@ -30,6 +30,7 @@ struct MeshDev {
   int64_t n_nodes;   // Q_k nodes
   int64_t n_pnodes;  // Q_kp nodes
   double Ve;         // element volume hx hy hz
+  float Ve32;        // Ve rounded to FP32 (mixed path)
   int shape;         // tile shape of the projection operator (pick_shape)
 };
 
@@ -46,6 +47,7 @@ struct Tables {
   float zf[4], zpf[4];      // FP32 copies of z, zp, lw, lwp (mixed path)
   float lwf[4], lwpf[4];
   float z_lo[4], lw_lo[4];  // z - zf and lw - lwf: z and lw as double-float
+  float Bwf[4][4];          // FP32 copy of Bw
 };
 
 // Bin grid over the box.

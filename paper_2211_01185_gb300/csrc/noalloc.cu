@@ -82,6 +82,7 @@ extern "C" cfdem_status cfdem_pcm_void_fraction_static(const double origin[3],
   m.Q = m.nq * m.nq * m.nq;
   m.E = (int64_t)m.ne[0] * m.ne[1] * m.ne[2];
   m.Ve = m.h[0] * m.h[1] * m.h[2];
+  m.Ve32 = (float)m.Ve;
   if (m.E > CFDEM_PCM_STATIC_MAX_ELEMS) return CFDEM_EINVAL;  // beyond the fixed scratch
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return CFDEM_ECUDA;

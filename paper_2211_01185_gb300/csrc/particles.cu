@@ -124,7 +124,8 @@ __global__ void k_bin_count(MeshDev m, BinDev b, int64_t n, const double* __rest
 }
 
 // exclusive scan of count[0..nb) into start[0..nb], start[nb] = total.
-// Three passes: per-tile sums, scan of the tile sums, per-tile scan.
+// Two passes: per-tile sums, then the per-tile scan with the tile's offset
+// summed from the totals before it.
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
@@ -173,22 +174,16 @@ __global__ void k_scan_tiles(const int32_t* __restrict__ in, int64_t nb,
   if (threadIdx.x == 0) tile_sum[blockIdx.x] = total;
 }
 
-__global__ void k_scan_sums(int32_t* __restrict__ tile_sum, int ntiles) {
-  __shared__ int32_t sh[kScanThreads / 32 + 1];
-  int32_t carry = 0;
-  for (int base = 0; base < ntiles; base += kScanThreads) {
-    int idx = base + threadIdx.x;
-    int32_t v = idx < ntiles ? tile_sum[idx] : 0;
-    int32_t total;
-    int32_t ex = block_excl_scan(v, sh, &total);
-    if (idx < ntiles) tile_sum[idx] = ex + carry;
-    carry += total;
-  }
-}
-
+// tile_sum holds each tile's total (k_scan_tiles); this tile's offset is
+// the sum of the totals before it, added up here by the block (integers:
+// the order does not matter), so no separate scan of the totals is launched
 __global__ void k_scan_final(const int32_t* __restrict__ in, int64_t nb,
-                             const int32_t* __restrict__ tile_off, int32_t* __restrict__ out) {
+                             const int32_t* __restrict__ tile_sum, int32_t* __restrict__ out) {
   __shared__ int32_t sh[kScanThreads / 32 + 1];
+  int32_t before = 0;
+  for (int t = threadIdx.x; t < (int)blockIdx.x; t += kScanThreads) before += tile_sum[t];
+  int32_t off;
+  block_excl_scan(before, sh, &off);
   int64_t base = blockIdx.x * (int64_t)kScanTile + threadIdx.x * (int64_t)kScanItems;
   int32_t v[kScanItems];
   int32_t s = 0;
@@ -199,7 +194,7 @@ __global__ void k_scan_final(const int32_t* __restrict__ in, int64_t nb,
     s += v[j];
   }
   int32_t total;
-  int32_t ex = block_excl_scan(s, sh, &total) + tile_off[blockIdx.x];
+  int32_t ex = block_excl_scan(s, sh, &total) + off;
 #pragma unroll
   for (int j = 0; j < kScanItems; ++j) {
     int64_t idx = base + j;
@@ -277,7 +272,6 @@ cudaError_t launch_bin(const MeshDev& m, const BinDev& b, int64_t n, const doubl
   if (n > 0) k_bin_count<<<gp, bs, 0, s>>>(m, b, n, x, r, bin_of, slot, bin_count, st);
   int ntiles = (int)((b.nbins + kScanTile - 1) / kScanTile);
   k_scan_tiles<<<ntiles, kScanThreads, 0, s>>>(bin_count, b.nbins, scan_tmp);
-  k_scan_sums<<<1, kScanThreads, 0, s>>>(scan_tmp, ntiles);
   k_scan_final<<<ntiles, kScanThreads, 0, s>>>(bin_count, b.nbins, scan_tmp, bin_start);
   if (n > 0) {
     // the float-float copy written last by k_gather_sorted holds the
@@ -287,7 +281,7 @@ cudaError_t launch_bin(const MeshDev& m, const BinDev& b, int64_t n, const doubl
     k_rank_bins<<<gp, bs, 0, s>>>(n, bin_of, bin_start, unsorted, perm);
     k_gather_sorted<<<gp, bs, 0, s>>>(m, n, perm, x, r, xs64, xs32);
   }
-  count_launches(n > 0 ? 7 : 3);
+  count_launches(n > 0 ? 6 : 2);
   return cudaGetLastError();
 }
 
@@ -441,7 +435,7 @@ k_forces(MeshDev m, Tables tb, ForceParams fp, int64_t n, const double* __restri
          const double* __restrict__ eps_nodal, double* __restrict__ f,
          double* __restrict__ f_drag, PartSrc ps, DevStatus* st) {
   constexpr bool MIX = std::is_same<T, float>::value;
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double p[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
   bool inside;
@@ -768,7 +762,12 @@ __device__ __forceinline__ void fixed_add(long long* acc, double v, int E) {
 }
 
 __device__ __forceinline__ double fixed_value(const long long* acc, int E) {
-  return ldexp((double)acc[0] * 2147483648.0 + (double)acc[1], -E);
+  // 2^-E as two powers of two built from their bits (0 <= E <= 1084, so
+  // each half is a normal number): exact scalings instead of ldexp
+  const int e1 = E >> 1, e2 = E - e1;
+  const double p1 = __longlong_as_double((long long)(1023 - e1) << 52);
+  const double q1 = __longlong_as_double((long long)(1023 - e2) << 52);
+  return ((double)acc[0] * 2147483648.0 + (double)acc[1]) * p1 * q1;
 }
 
 // acc64: per element S (3 x 2 integers); then, with the fluid-side drag, a

@@ -67,11 +67,15 @@ k_rhs(MeshDev m, Tables tb, const T* __restrict__ eps_q, T* __restrict__ local) 
   __syncthreads();
   const int64_t e = e0 + threadIdx.x;
   if (e >= E) return;
-  T B[NQ][NQ];  // B[a][q] = l_a(g_q) w_q
+  constexpr bool F32 = std::is_same<T, float>::value;
+  T B[NQ][NQ];  // B[a][q] = l_a(g_q) w_q (the FP32 path takes the host's FP32 copy)
 #pragma unroll
   for (int a = 0; a < NQ; ++a)
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) B[a][q] = (T)tb.Bw[a][q];
+    for (int q = 0; q < NQ; ++q) {
+      if constexpr (F32) B[a][q] = tb.Bwf[a][q];
+      else B[a][q] = (T)tb.Bw[a][q];
+    }
   const T* ev = sh + threadIdx.x * Q;
   T t1[NQ][NQ][NQ];  // [qz][qy][a]
 #pragma unroll
@@ -97,7 +101,9 @@ k_rhs(MeshDev m, Tables tb, const T* __restrict__ eps_q, T* __restrict__ local) 
         for (int qy = 0; qy < NQ; ++qy) s += B[bb][qy] * t1[qz][qy][a];
         t2[qz][bb][a] = s;
       }
-  const T detJ = (T)m.Ve;
+  T detJ;
+  if constexpr (F32) detJ = m.Ve32;
+  else detJ = (T)m.Ve;
 #pragma unroll
   for (int c = 0; c < NQ; ++c)
 #pragma unroll
@@ -155,7 +161,10 @@ k_rhs_gather(MeshDev m, const T* __restrict__ local, double* __restrict__ b) {
               const int jj = (a + K * dx) + NQ * ((bb + K * dy) + NQ * (c + K * dz));
               s += __ldg(pe + jj * E - (dx + sy * dy + sz * dz));
             }
-            be[a + nx * bb + nxy * c] = (double)s;
+            if constexpr (std::is_same<T, float>::value)
+              be[a + nx * bb + nxy * c] = double_from_float_int(s);  // exact, no conversion
+            else
+              be[a + nx * bb + nxy * c] = (double)s;
           }
         }
       }
