@@ -380,14 +380,17 @@ __device__ __forceinline__ void smem_gemm(int tbase, const float* AT, int lda, c
   for (int q = 0; q < TR / 4; ++q) av[q] = ap[q];
 #pragma unroll
   for (int q = 0; q < TC / 4; ++q) bv[q] = bp[q];
+  // the last step also reads row K of A and B (discarded): the caller's
+  // shared memory holds a row past every operand
 #pragma unroll 4
   for (int k = 0; k < K; ++k) {
-    const int kn = k + 1 < K ? k + 1 : k;
+    ap += la;
+    bp += lb;
     float4 an[TR / 4], bn[TC / 4];
 #pragma unroll
-    for (int q = 0; q < TR / 4; ++q) an[q] = ap[kn * la + q];
+    for (int q = 0; q < TR / 4; ++q) an[q] = ap[q];
 #pragma unroll
-    for (int q = 0; q < TC / 4; ++q) bn[q] = bp[kn * lb + q];
+    for (int q = 0; q < TC / 4; ++q) bn[q] = bp[q];
     const float* a = reinterpret_cast<const float*>(av);
     const float* b = reinterpret_cast<const float*>(bv);
 #pragma unroll
@@ -472,7 +475,7 @@ __global__ void k_fdm_slab(SlabArgs sa, const float* __restrict__ in, int in_str
   float* X = fsm;                   // [sl_y][lx]  slab in slots; also the result Y
   float* PT = X + ay.sl * lx;       // [sl_x][ly]  after the y transform, transposed
   float* MX = PT + ax.sl * ly;      // [sl_x][lx]
-  float* MY = MX + ax.sl * lx;      // [sl_y][ly]
+  float* MY = MX + ax.sl * lx;      // [sl_y][ly], then one row read only by prefetches
   for (int t = threadIdx.x; t < (ax.sl * lx) >> 2; t += blockDim.x)
     cp_async16(MX + 4 * t, sa.Mx + 4 * t);
   for (int t = threadIdx.x; t < (ay.sl * ly) >> 2; t += blockDim.x)
@@ -888,8 +891,9 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4], 
   {
     const SlabAxis ax = slab_axis(nx), ay = slab_axis(ny);
     const size_t lx = slab_pad(ax.sl), ly = slab_pad(ay.sl);
-    // k_fdm_slab: X / Y [sl_y][lx], PT [sl_x][ly], MX [sl_x][lx], MY [sl_y][ly]
-    p->slab_smem = (ay.sl * lx + ax.sl * ly + ax.sl * lx + ay.sl * ly) * sizeof(float);
+    // k_fdm_slab: X / Y [sl_y][lx], PT [sl_x][ly], MX [sl_x][lx], MY [sl_y][ly], and
+    // one row past MY that the products' last prefetch reads
+    p->slab_smem = (ay.sl * lx + ax.sl * ly + ax.sl * lx + (ay.sl + 1) * ly) * sizeof(float);
     // 4 x 4 register tiles (more warps per slab) where the thread count allows
     // 4 x 4 register tiles where the thread count allows (timed against the
     // other shapes once the plan is built)
