@@ -400,7 +400,7 @@ void free_mesh_arena(cfdem_t c) {
                 c->cg.p1, c->cg.Ap, c->cg.dinv, c->cg.xcor, c->cg.r32, c->cg.z32,
                 c->cg.q0, c->cg.q1, c->cg.Aq, c->cg.dinv32, c->cg.d32, c->cg.partials,
                 c->cg.sc, c->cg.zn, c->cg.zn32, c->cg.rin32, c->cg.x_df, c->cg.r_df,
-                c->cg.b_df, c->cg.Ap_df, c->cg.p0_df, c->cg.p1_df, c->adj_geps,
+                c->cg.Ap_df, c->cg.p0_df, c->cg.p1_df, c->adj_geps,
                 c->adj_lam, c->adj_gq, c->rhs_local, c->semi, c->tune_x, c->src_acc,
                 c->src_max};
   for (void* p : ps)
@@ -462,9 +462,6 @@ cfdem_status alloc_mesh_arena(cfdem_t c) {
     t = nullptr;
     CK(grow(&t, 2 * nn), "cg");
     w.r_df = reinterpret_cast<df64*>(t);
-    t = nullptr;
-    CK(grow(&t, 2 * nn), "cg");
-    w.b_df = reinterpret_cast<df64*>(t);
     t = nullptr;
     CK(grow(&t, 2 * nn), "cg");
     w.Ap_df = reinterpret_cast<df64*>(t);

@@ -252,7 +252,6 @@ struct CgWork {
   // double-float vectors of the mixed solve (pairs of floats, hi first)
   struct df64* x_df;
   struct df64* r_df;
-  struct df64* b_df;
   struct df64* Ap_df;
   struct df64* p0_df;
   struct df64* p1_df;

@@ -429,11 +429,11 @@ struct EpiStoreDf {
 struct EpiResidualDf {
   using acc_t = float;
   static constexpr bool kXE = false;
-  const df64* b;
+  const double* b;  // FP64 right-hand side, split here (bit-field moves)
   df64* r;
   float* r32;
   __device__ __forceinline__ float operator()(int64_t g, df64 acc, df64) const {
-    df64 v = b[g] - acc;
+    df64 v = df_from_double_int(b[g]) - acc;
     r[g] = v;
     r32[g] = v.hi;
     return v.hi * v.hi;
@@ -516,19 +516,29 @@ __device__ __forceinline__ typename Epi::acc_t apply_tile(const MeshDev& m,
     BX[(W + w) * TX + i] = b;
   }
 
-  // load with halo; the owned nodes' input also to XE
+  // load with halo: each thread keeps one x column of the haloed tile (its
+  // x bounds and ownership worked out once) and walks the (z, y) rows; the
+  // owned nodes' input also to XE
   int nonzero = 0;
-  for (int t = threadIdx.x; t < TL::NX; t += blockDim.x) {
-    const int lz = t / PL, rr = t - lz * PL, ly = rr / XW, lx = rr - ly * XW;
-    const int gx = x0 + lx - H, gy = y0 + ly - H, gz = z0 + lz - H;
-    T v = T(0);
-    if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz) {
-      const bool own = lx >= H && lx < H + TX && ly >= H && ly < H + TY && lz >= H && lz < H + TZ;
-      v = ld(gx + (int64_t)nx * gy + sxy * gz, own);
-      if (kXE && own) XE[((lz - H) * TY + (ly - H)) * TX + (lx - H)] = v;
+  {
+    constexpr int RT = kApplyThreads / XW;  // rows taken per pass
+    const int lx = (int)threadIdx.x % XW, tr = (int)threadIdx.x / XW;
+    if (tr < RT) {
+      const int gx = x0 + lx - H;
+      const bool xin = gx >= 0 && gx < nx, xown = lx >= H && lx < H + TX;
+      for (int row = tr; row < ZW * YW; row += RT) {
+        const int lz = row / YW, ly = row - lz * YW;
+        const int gy = y0 + ly - H, gz = z0 + lz - H;
+        T v = T(0);
+        if (xin && gy >= 0 && gy < ny && gz >= 0 && gz < nz) {
+          const bool own = xown && ly >= H && ly < H + TY && lz >= H && lz < H + TZ;
+          v = ld(gx + (int64_t)nx * gy + sxy * gz, own);
+          if (kXE && own) XE[((lz - H) * TY + (ly - H)) * TX + (lx - H)] = v;
+        }
+        X[row * XW + lx] = v;
+        nonzero |= (v != T(0));
+      }
     }
-    X[t] = v;
-    nonzero |= (v != T(0));
   }
   // a tile whose input (halo included) is zero has a zero image: skip the
   // passes (a cold start of the projection begins with x = 0)
@@ -600,21 +610,30 @@ __device__ __forceinline__ typename Epi::acc_t apply_tile(const MeshDev& m,
   __syncthreads();
   // x pass + output (per-thread partial in the epilogue's type, one
   // conversion per thread)
+  // (each thread keeps one x column of the owned nodes and walks the rows)
   typename Epi::acc_t dot = 0;
-  for (int t = threadIdx.x; t < TL::NO; t += blockDim.x) {
-    const int lz = t / (TX * TY), rr = t - lz * (TX * TY), ly = rr / TX, lx = rr - ly * TX;
-    const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
-    if (gx >= nx || gy >= ny || gz >= nz) continue;
-    const T* u = U + (lz * TY + ly) * XW + lx;
-    const T* v = V + (lz * TY + ly) * XW + lx;
-    Acc<T> ax;
-    ax.zero();
+  {
+    constexpr int RT = kApplyThreads / TX;
+    const int lx = (int)threadIdx.x % TX, tr = (int)threadIdx.x / TX;
+    const int gx = x0 + lx;
+    if (tr < RT && gx < nx) {
+      for (int row = tr; row < TZ * TY; row += RT) {
+        const int lz = row / TY, ly = row - lz * TY;
+        const int gy = y0 + ly, gz = z0 + lz;
+        if (gy >= ny || gz >= nz) continue;
+        const T* u = U + row * XW + lx;
+        const T* v = V + row * XW + lx;
+        Acc<T> ax;
+        ax.zero();
 #pragma unroll
-    for (int w = 0; w < W; ++w) {
-      ax.add(BX[w * TX + lx], u[w]);
-      ax.add(BX[(W + w) * TX + lx], v[w]);
+        for (int w = 0; w < W; ++w) {
+          ax.add(BX[w * TX + lx], u[w]);
+          ax.add(BX[(W + w) * TX + lx], v[w]);
+        }
+        dot += ep(gx + (int64_t)nx * gy + sxy * gz, ax.get(),
+                  kXE ? XE[row * TX + lx] : T(0));
+      }
     }
-    dot += ep(gx + (int64_t)nx * gy + sxy * gz, ax.get(), kXE ? XE[t] : T(0));
   }
   return dot;
 }
@@ -835,12 +854,12 @@ k_cg_start_fdm(int64_t n, const TB* __restrict__ b, const T* __restrict__ Ax,
 }
 
 // --- mixed path: outer CG in double-float, FP32 directions and FDM --------
-// b, x (FP64) -> df64 copies in one pass, converted with integer operations;
-// b . b from the high parts (FP32 products, one conversion per thread) into
-// sc->bb; also r = b, r32 = hi(b): the residual of a zero start vector, which
-// k_residual_df then leaves in place (it overwrites them when x != 0)
+// x (FP64) -> df64 copy, r = b as df64 and r32 = hi(b) (the residual of a
+// zero start vector, which k_residual_df leaves in place and overwrites when
+// x != 0, splitting b itself), all converted with integer operations; b . b
+// from the high parts into sc->bb
 __global__ void __launch_bounds__(256)
-k_split_df(int64_t n, const double* __restrict__ b, df64* __restrict__ b_df,
+k_split_df(int64_t n, const double* __restrict__ b,
            const double* __restrict__ x, df64* __restrict__ x_df, df64* __restrict__ r,
            float* __restrict__ r32, double* partials, CgScalars* sc) {
   __shared__ double red[32];
@@ -849,7 +868,6 @@ k_split_df(int64_t n, const double* __restrict__ b, df64* __restrict__ b_df,
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const df64 v = df_from_double_int(b[i]);
-    b_df[i] = v;
     r[i] = v;
     r32[i] = v.hi;
     bb = fmaf(v.hi, v.hi, bb);
@@ -879,7 +897,7 @@ __global__ void k_join_df(int64_t n, const df64* __restrict__ in, double* __rest
 template <int K, class S>
 __global__ void __launch_bounds__(kApplyThreads)
 k_residual_df(MeshDev m, const df64* __restrict__ bands, Coefs<df64> cf,
-              const df64* __restrict__ x, const df64* __restrict__ b, df64* __restrict__ r,
+              const df64* __restrict__ x, const double* __restrict__ b, df64* __restrict__ r,
               float* __restrict__ r32, double* partials, CgScalars* sc, double rtol) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double red[32];
@@ -1470,9 +1488,9 @@ static cudaError_t cg_solve_df(const MeshDev& m, const df64* bands, const double
   const size_t sm = apply_smem<K, S, df64>();
   Timer* tm = w.timer;
   if ((e = cudaMemsetAsync(w.sc, 0, sizeof(CgScalars), s)) != cudaSuccess) return e;
-  k_split_df<<<vb, 256, 0, s>>>(n, b, w.b_df, x, w.x_df, w.r_df, w.r32, w.partials, w.sc);
+  k_split_df<<<vb, 256, 0, s>>>(n, b, x, w.x_df, w.r_df, w.r32, w.partials, w.sc);
   if (tm) tm->begin(kStageOp32, s);
-  k_residual_df<K, S><<<g, kApplyThreads, sm, s>>>(m, bands, cf, w.x_df, w.b_df, w.r_df, w.r32,
+  k_residual_df<K, S><<<g, kApplyThreads, sm, s>>>(m, bands, cf, w.x_df, b, w.r_df, w.r32,
                                                 w.partials, w.sc, rtol);
   if (tm) tm->end(kStageOp32, s);
   count_launches(2);
