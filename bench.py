@@ -58,6 +58,11 @@ NCU_TRAFFIC = {
 #   node, eps: 2 per node, grad p: 3 x 2 per pressure node), the 1D bases
 #   (~10 per point and axis) and ~60 for the closure and the force sum
 QCM_FLOPS_TEST, QCM_FLOPS_LENS = 8.0, 25.0
+# the same work in FP32 instructions (the QCM issues FADD/FMUL/FFMA and
+# compares at one rate): a test is three subtractions, a multiply, two FMAs
+# and a compare; a lens volume about sixteen (one reciprocal square root,
+# the lens formula) and four for the compensated sum
+QCM_INSTR_TEST, QCM_INSTR_LENS = 7.0, 20.0
 
 
 def _forces_bytes(w, n_nodes):
@@ -497,28 +502,40 @@ def run_bed(env, name, steps, warmup, alu, headline=False, e2e=True, cpu=True,
     tests_culled = float(k + 1) ** 3 * _element_candidates(w)
     qcm_ms = stages["void_fraction"] / max(calls["void_fraction"], 1.0)
     fo_ms = stages["forces"] / max(calls["forces"], 1.0)
-    # the operator's productive launches: one per CG iteration (the stage also
-    # holds the residual launch, which a cold start reduces to its scalars,
-    # and the launches after convergence, which return at once)
+    # the operator's launches: one per CG iteration (the eager solve queues
+    # iterations in chunks of two, so a launch after convergence, which
+    # returns at once, is rare)
     op_launches = float(max(per[1]["eager"]["cg_iterations"], 1))
     op_ms = stages["op32"] / op_launches
     op_macs = 7.0 * (2 * k + 1) * n_nodes   # z: M, K; y: 3 folded bands; x: M, K
     instr_peak = alu["fp32_tflops"] / 2.0    # FP32 instructions per second / 1e12
     qcm_flops = QCM_FLOPS_TEST * tests_cell + QCM_FLOPS_LENS * pairs
+    qcm_instr = QCM_INSTR_TEST * tests_cell + QCM_INSTR_LENS * pairs
+    qcm_instr_culled = QCM_INSTR_TEST * tests_culled + QCM_INSTR_LENS * pairs
     qcm_flops_culled = QCM_FLOPS_TEST * tests_culled + QCM_FLOPS_LENS * pairs
     fo_bytes = _forces_bytes(w, n_nodes)
     kern = {
         "void_fraction": {
-            "kernel": "k_qcm_pts<%d> (FP32 QCM, one lane per Gauss point)" % k, "bound": "alu", "unit": "TFLOP/s",
+            "kernel": "k_qcm_pts<%d> (FP32 QCM, one lane per Gauss point)" % k, "bound": "alu",
+            "unit": "T FP32 instructions/s",
             "ms_per_launch": qcm_ms, "launches_per_step": calls["void_fraction"],
-            "work": qcm_flops, "peak": alu["fp32_tflops"],
-            "achieved": qcm_flops / (qcm_ms * 1e-3) / 1e12,
+            "work": qcm_instr, "peak": instr_peak,
+            "achieved": qcm_instr / (qcm_ms * 1e-3) / 1e12,
             "units": {"tested_pairs_cell_list": tests_cell, "neighbour_pairs": pairs,
-                      "tested_pairs_element_culled": tests_culled},
-            "achieved_culled_count": qcm_flops_culled / (qcm_ms * 1e-3) / 1e12,
-            "peak_source": "FMA probe on this device (libalupeak.so), FP32",
-            "limiter": "instruction issue (ncu: compares, ballots and queue appends of the "
-                       "neighbour filter are not counted as flops)"},
+                      "tested_pairs_element_culled": tests_culled,
+                      "fp32_instructions_per_test": QCM_INSTR_TEST,
+                      "fp32_instructions_per_lens": QCM_INSTR_LENS},
+            "achieved_culled_count": qcm_instr_culled / (qcm_ms * 1e-3) / 1e12,
+            "as_flops": {"work": qcm_flops, "peak_tflops": alu["fp32_tflops"],
+                         "achieved_tflops": qcm_flops / (qcm_ms * 1e-3) / 1e12,
+                         "frac": qcm_flops / (qcm_ms * 1e-3) / 1e12 / alu["fp32_tflops"],
+                         "frac_culled_count": qcm_flops_culled / (qcm_ms * 1e-3) / 1e12 /
+                         alu["fp32_tflops"]},
+            "peak_source": "FMA probe on this device (libalupeak.so): FP32 FMA rate as "
+                           "instructions/s",
+            "limiter": "instruction issue (~80 % of issue slots): the streaming of the bin "
+                       "rows (row bounds, warp scan, per-chunk search, box cull) is not "
+                       "counted as work"},
         "forces": {
             "kernel": "k_forces<%d,%d,float>" % (k, kp), "bound": "hbm", "unit": "GB/s",
             "ms_per_launch": fo_ms, "launches_per_step": calls["forces"], "work": fo_bytes,
@@ -555,8 +572,8 @@ def run_bed(env, name, steps, warmup, alu, headline=False, e2e=True, cpu=True,
                             "dram__bytes_write.sum)",
             "ms_per_launch": d["ms_per_launch"], "launches_per_step": d["launches_per_step"],
             "others": {c: v for c, v in kern.items() if c != dom}}
-    for key in ("units", "achieved_culled_count", "frac_culled_count", "limiter", "peak_source",
-                "work"):
+    for key in ("units", "achieved_culled_count", "frac_culled_count", "as_flops", "limiter",
+                "peak_source", "work"):
         if key in d:
             roof[key] = d[key]
     res["roofline"] = roof
@@ -677,7 +694,31 @@ def run_batch(env, steps, warmup, precision="mixed"):
     ms_s, clk_s = env.timed(step_solo, max(3, steps // 4))
     for c in solo:
         cf.cfdem_synchronize(c.h)
-    mb, msolo = float(np.mean(ms_b)), float(np.mean(ms_s))
+    # each bed as its own one-bed batch (its own graph), the 64 graphs
+    # replayed one after another: the launch overhead removed as in the
+    # batch, without the beds running side by side
+    singles = []
+    for i, b in enumerate(beds):
+        h1 = cf.cfdem_batch_create(1, env.local, s.cuda_stream)
+        bed1 = cf.cfdem_batch_bed(h1, 0)
+        cf.cfdem_set_mesh(bed1, b["origin"], b["extent"], b["n_el"], b["k"])
+        cf.cfdem_set_params(bed1, cf.make_params(**b["params"]))
+        singles.append(h1)
+
+    def step_graphs():
+        zero_eps()
+        for h1, io in zip(singles, ios):
+            if cf.cfdem_batch_coupling_step(h1, [io]) != cf.OK:
+                raise RuntimeError(cf.cfdem_batch_last_error(h1))
+
+    with torch.cuda.stream(s):
+        for _ in range(2):
+            step_graphs()
+    ms_g, _ = env.timed(step_graphs, max(3, steps // 4))
+    for h1 in singles:
+        cf.cfdem_batch_synchronize(h1)
+        cf.cfdem_batch_destroy(h1)
+    mb, msolo, mgr = float(np.mean(ms_b)), float(np.mean(ms_s)), float(np.mean(ms_g))
     res = {"metric": METRIC, "value": n_tot / (mb * 1e-3), "unit": "particle updates/s",
            "n_gpus": 1, "steps": steps, "warmup": warmup, "ms_per_step": mb,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -692,6 +733,8 @@ def run_batch(env, steps, warmup, precision="mixed"):
            "cg_iterations": {"min": min(its), "max": max(its)},
            "solo_sequential": {"value": n_tot / (msolo * 1e-3), "ms_per_step": msolo,
                                "speedup_of_batch": msolo / mb},
+           "solo_graphs": {"ms_per_step": mgr, "speedup_of_batch": mgr / mb,
+                           "launch": "64 one-bed graphs replayed one after another"},
            "clocks": clk_b, "clocks_solo": clk_s}
     cf.cfdem_batch_destroy(bh)
     for c in solo:
@@ -891,8 +934,8 @@ def _summary(r):
     """The keys of a secondary workload that the bench line carries."""
     keep = ("workload", "mesh", "particles", "nodes", "value", "ms_per_step", "steps",
             "mixed", "fp64", "mixed_speedup_over_fp64", "err_mixed_vs_fp64", "roofline",
-            "step_hbm", "cpu_baseline", "solo_sequential", "graph_replayed", "batch_status",
-            "cg_iterations", "coupled_step", "status", "config", "clocks", "metric", "unit")
+            "step_hbm", "cpu_baseline", "solo_sequential", "solo_graphs", "graph_replayed",
+            "batch_status", "cg_iterations", "coupled_step", "status", "config", "clocks", "metric", "unit")
     return {k: v for k, v in r.items() if k in keep}
 
 

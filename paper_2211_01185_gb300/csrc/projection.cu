@@ -1425,8 +1425,10 @@ static cudaError_t cg_solve_fdm(const MeshDev& m, const T* bands, const double* 
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
   // iterations are queued in chunks: every kernel of an iteration (operator,
   // update, FDM transforms and solves, dot) returns at once on the device flag
-  // `done`, so only one host round trip per chunk is needed
-  const int chunk = sizeof(T) == 8 ? 4 : 2;
+  // `done`, so only one host round trip per chunk is needed; with the FDM
+  // (an inverse up to rounding) the FP64 solve converges in about three
+  // iterations, so chunks of three leave few launches that return at once
+  const int chunk = sizeof(T) == 8 ? 3 : 2;
   int launched = 0;
   while (!hs.done && launched < maxit) {
     int todo = maxit - launched < chunk ? maxit - launched : chunk;
@@ -1489,10 +1491,8 @@ static cudaError_t cg_solve_df(const MeshDev& m, const df64* bands, const double
   Timer* tm = w.timer;
   if ((e = cudaMemsetAsync(w.sc, 0, sizeof(CgScalars), s)) != cudaSuccess) return e;
   k_split_df<<<vb, 256, 0, s>>>(n, b, x, w.x_df, w.r_df, w.r32, w.partials, w.sc);
-  if (tm) tm->begin(kStageOp32, s);
   k_residual_df<K, S><<<g, kApplyThreads, sm, s>>>(m, bands, cf, w.x_df, b, w.r_df, w.r32,
                                                 w.partials, w.sc, rtol);
-  if (tm) tm->end(kStageOp32, s);
   count_launches(2);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   float* zc = w.z32;
@@ -1553,7 +1553,9 @@ static cudaError_t cg_solve_df(const MeshDev& m, const df64* bands, const double
   if ((e = cudaMemcpyAsync(&hs, w.sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return e;
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-  const int chunk = 4;
+  // eager: chunks of two iterations (the FDM-preconditioned mixed solve
+  // converges in about two), one host round trip per chunk
+  const int chunk = 2;
   int launched = 0;
   while (!hs.done && launched < maxit) {
     int todo = maxit - launched < chunk ? maxit - launched : chunk;
