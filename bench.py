@@ -47,7 +47,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 # one ncu capture of that kernel as it is now (dram__bytes_read.sum +
 # dram__bytes_write.sum); an entry is removed when its kernel changes
 NCU_TRAFFIC = {
-    "void_fraction": 3751424,    # k_qcm_pts<2>
+    "void_fraction": 3749632,    # k_qcm_pts<2>
     "op32": 8769408,             # k_cg_apply_df<2>: mean of the two productive launches
     "forces": 20116480,          # k_forces<2,1,float>
 }

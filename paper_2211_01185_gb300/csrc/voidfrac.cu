@@ -551,6 +551,9 @@ struct QcmPtsSmem {
   float4 cand[kQcmWarps][64];      // culled candidates: position - centre, R + r
   float4 cons[kQcmWarps][64];      // (R + r)^2, (R - r)^2, full-overlap volume, weight
   int32_t slot[kQcmWarps][64];     // their sorted slots
+  // per lane, the candidates (of the 32 being tested) that overlap its Gauss
+  // point, in candidate order: [warp][hit][lane] (Q <= 32 only)
+  uint8_t hits[kQcmWarps][Q > 32 ? 1 : 32][32];
 };
 
 template <int K>
@@ -704,28 +707,56 @@ k_qcm_pts(MeshDev m, QcmParams P, BinDev b, const int32_t* __restrict__ bin_star
     if (nb == 0) break;
     __syncwarp();
     const int cn = nb < 32 ? nb : 32;
-    for (int j = grp; j < cn; j += G) {
-      const float4 A = sm.cand[wp][j];
-      const float4 B = sm.cons[wp][j];
-#pragma unroll
-      for (int p = 0; p < PPL; ++p) {
-        const float dx = A.x - qx[p], dy = A.y - qy[p], dz = A.z - qz[p];
+    // Q <= 32 (one point per lane, a few hits per point): each lane first
+    // lists the candidates that overlap its point, then evaluates the lens
+    // volumes of its own list in candidate order (the order of its sum) --
+    // the warp runs as many lens rounds as its busiest lane has hits instead
+    // of one for every candidate any lane hits.  Q3 (two points per lane,
+    // most lanes hit most candidates): test and evaluate in one pass.
+    auto lens = [&](int p, int j, float d2, const float4& A, const float4& B) {
+      float v;
+      if (d2 <= B.y) {
+        v = B.z;
+      } else {
+        const float y = rsqrtf(d2);
+        const float d = d2 * y;
+        const float sd = A.w - d;
+        v = c12 * sd * sd * (d2 + 2.0f * d * A.w - 3.0f * B.y) * y;
+      }
+      neumaier(acc[p], cmp[p], v * B.w);
+      if (want_counts) {
+        ++cnt[p];
+        if (want_ids) ids[p] += perm[sm.slot[wp][j]];
+      }
+    };
+    if constexpr (PPL == 1) {
+      int nh = 0;
+      for (int j = grp; j < cn; j += G) {
+        const float4 A = sm.cand[wp][j];
+        const float rr2 = sm.cons[wp][j].x;
+        const float dx = A.x - qx[0], dy = A.y - qy[0], dz = A.z - qz[0];
         const float d2 = dx * dx + dy * dy + dz * dz;
-        if (qok[p] && d2 < B.x) {
-          float v;
-          if (d2 <= B.y) {
-            v = B.z;
-          } else {
-            const float y = rsqrtf(d2);
-            const float d = d2 * y;
-            const float sd = A.w - d;
-            v = c12 * sd * sd * (d2 + 2.0f * d * A.w - 3.0f * B.y) * y;
-          }
-          neumaier(acc[p], cmp[p], v * B.w);
-          if (want_counts) {
-            ++cnt[p];
-            if (want_ids) ids[p] += perm[sm.slot[wp][j]];
-          }
+        if (qok[0] && d2 < rr2) sm.hits[wp][nh++][lane] = (uint8_t)j;
+      }
+      const int mh = (int)__reduce_max_sync(FULL, (unsigned)nh);
+      for (int h = 0; h < mh; ++h) {
+        if (h < nh) {
+          const int j = sm.hits[wp][h][lane];
+          const float4 A = sm.cand[wp][j];
+          const float4 B = sm.cons[wp][j];
+          const float dx = A.x - qx[0], dy = A.y - qy[0], dz = A.z - qz[0];
+          lens(0, j, dx * dx + dy * dy + dz * dz, A, B);
+        }
+      }
+    } else {
+      for (int j = grp; j < cn; j += G) {
+        const float4 A = sm.cand[wp][j];
+        const float4 B = sm.cons[wp][j];
+#pragma unroll
+        for (int p = 0; p < PPL; ++p) {
+          const float dx = A.x - qx[p], dy = A.y - qy[p], dz = A.z - qz[p];
+          const float d2 = dx * dx + dy * dy + dz * dz;
+          if (qok[p] && d2 < B.x) lens(p, j, d2, A, B);
         }
       }
     }
