@@ -49,7 +49,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 NCU_TRAFFIC = {
     "void_fraction": 3749632,    # k_qcm_pts<2>
     "op32": 8769408,             # k_cg_apply_df<2>: mean of the two productive launches
-    "forces": 20116480,          # k_forces<2,1,float>
+    "forces": 20133376,          # k_forces<2,1,float>
 }
 # algorithmic work per unit (the per-unit figures of the measurement plan):
 #   QCM: 8 flops per tested (Gauss point, particle) pair, 25 per lens volume

@@ -402,7 +402,7 @@ void free_mesh_arena(cfdem_t c) {
                 c->cg.sc, c->cg.zn, c->cg.zn32, c->cg.rin32, c->cg.x_df, c->cg.r_df,
                 c->cg.Ap_df, c->cg.p0_df, c->cg.p1_df, c->adj_geps,
                 c->adj_lam, c->adj_gq, c->rhs_local, c->semi, c->tune_x, c->src_acc,
-                c->src_max};
+                c->src_max, c->nodal_df};
   for (void* p : ps)
     if (p) cudaFree(p);
   c->tune_x = nullptr;
@@ -417,6 +417,7 @@ void free_mesh_arena(cfdem_t c) {
   c->semi = nullptr;
   c->src_acc = nullptr;
   c->src_max = nullptr;
+  c->nodal_df = nullptr;
   c->semi_valid = 0;
   FdmPlan* keep = c->cg.fdm;
   const df64* kb = c->cg.bands_df;
@@ -1038,8 +1039,22 @@ cfdem_status cfdem_forces(cfdem_t c, int64_t n, const double* x, const double* r
   if (want_src)
     CK(cudaMemsetAsync(c->src_max, 0, 3 * sizeof(unsigned long long), c->stream), "forces");
   c->timer.begin(kStageForces, c->stream);
-  CK(launch_forces(m, c->tab, c->prm.precision, force_params(c), n, x, r, u_p, u_nodal,
-                   p_nodal, eps_nodal, f, f_drag, ps, c->st, c->stream),
+  ForceParams fp = force_params(c);
+  // mixed path with many particles per node (large elements, dense beds):
+  // split the nodal velocity and void fraction into double-float pairs once
+  // per node instead of once per particle that reads them (the same split,
+  // so the same bits); the buffer is allocated outside a stream capture
+  const int64_t nq = (int64_t)(m.k + 1) * (m.k + 1) * (m.k + 1);
+  if (c->prm.precision == 1 && n * nq >= 8 * m.n_nodes) {
+    if (!c->nodal_df && !stream_capturing(c->stream))
+      CK(grow(&c->nodal_df, 2 * (size_t)m.n_nodes), "forces");
+    if (c->nodal_df) {
+      CK(launch_split_nodal(m.n_nodes, u_nodal, eps_nodal, c->nodal_df, c->stream), "forces");
+      fp.nodal_df = c->nodal_df;
+    }
+  }
+  CK(launch_forces(m, c->tab, c->prm.precision, fp, n, x, r, u_p, u_nodal, p_nodal, eps_nodal,
+                   f, f_drag, ps, c->st, c->stream),
      "forces");
   c->timer.end(kStageForces, c->stream);
   if (want_src) {

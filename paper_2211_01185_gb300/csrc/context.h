@@ -40,6 +40,7 @@ struct cfdem_ctx {
   // particle arena
   int64_t cap_n = 0;
   int32_t *bin_of = nullptr, *slot = nullptr, *perm = nullptr;
+  float4* nodal_df = nullptr;  // mesh arena: double-float nodal u and eps (forces)
   double* xs64 = nullptr;
   float* xs32 = nullptr;
   float* qcm_w = nullptr;      // volume-conserving QCM weights per sorted particle [2 n]

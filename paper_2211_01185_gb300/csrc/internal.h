@@ -144,6 +144,10 @@ struct ForceParams {
   // in_box bounds x0 - 1e-12 L and (x0 + L) + 1e-12 L as order-preserving
   // integer keys of their bits (compared without FP64 instructions)
   long long box_lo_key[3], box_hi_key[3];
+  // mixed path, optional: the nodal velocity and void fraction already split
+  // into double-float pairs, [n_nodes][2] float4 = (u0, u1 | u2, eps), used
+  // where many particles read each node (the split is the same either way)
+  const float4* nodal_df;
 };
 
 // Per-particle fluid-source records written by the forces kernel and summed
@@ -173,6 +177,10 @@ cudaError_t launch_bin(const MeshDev& m, const BinDev& b, int64_t n, const doubl
                        int32_t* bin_start, int32_t* perm, int32_t* scan_tmp, double* xs64,
                        float* xs32, DevStatus* st, cudaStream_t s);
 // ps.S / ps.elem receive the per-particle source records (ps.S may be null)
+// the nodal velocity and void fraction as double-float pairs for
+// ForceParams::nodal_df: out[2 j] = (u0, u1), out[2 j + 1] = (u2, eps) of node j
+cudaError_t launch_split_nodal(int64_t n_nodes, const double* u_nodal, const double* eps_nodal,
+                               float4* out, cudaStream_t s);
 cudaError_t launch_forces(const MeshDev& m, const Tables& t, int precision, const ForceParams& fp,
                           int64_t n, const double* x, const double* r, const double* u_p,
                           const double* u_nodal, const double* p_nodal,

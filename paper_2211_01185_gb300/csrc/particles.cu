@@ -427,7 +427,7 @@ __device__ __forceinline__ void shear_force(const Tables& tb, const ForceParams&
 // sum_j phi_j (u_j - u_p) = u_f - u_p, and no FP32 rounding of |u| enters a
 // small slip component); pressure differences along each axis likewise; the
 // closures in FP32.
-template <int K, int KP, typename T, bool SHEAR>
+template <int K, int KP, typename T, bool SHEAR, bool PRE>
 __global__ void __launch_bounds__(128)
 k_forces(MeshDev m, Tables tb, ForceParams fp, int64_t n, const double* __restrict__ x,
          const double* __restrict__ r, const double* __restrict__ u_p,
@@ -501,6 +501,10 @@ k_forces(MeshDev m, Tables tb, ForceParams fp, int64_t n, const double* __restri
   // (the weights sum to one), so that FP32 rounds only its variation inside
   // the element.
   df64 uf0(0.f, 0.f), uf1(0.f, 0.f), uf2(0.f, 0.f), re(0.f, 0.f);
+  DfDotAcc au0, au1, au2;  // the slip sums (compensated, one renormalisation each)
+  au0.zero();
+  au1.zero();
+  au2.zero();
   if constexpr (MIX) re = df_from_double_int(__ldg(eps_nodal + base));
 #pragma unroll
   for (int c = 0; c <= K; ++c) {
@@ -514,10 +518,23 @@ k_forces(MeshDev m, Tables tb, ForceParams fp, int64_t n, const double* __restri
         const int64_t nd = base + a + nx * b + nxy * c;
         if constexpr (MIX) {
           const df64 phid = lxd[a] * lyzd;
-          uf0 += phid * df_from_double_int(__ldg(u_nodal + 3 * nd));
-          uf1 += phid * df_from_double_int(__ldg(u_nodal + 3 * nd + 1));
-          uf2 += phid * df_from_double_int(__ldg(u_nodal + 3 * nd + 2));
-          eps += phid.hi * df_diff(df_from_double_int(__ldg(eps_nodal + nd)), re);
+          df64 v0, v1, v2, ve;
+          if constexpr (PRE) {  // split once per node by launch_split_nodal
+            const float4 q0 = __ldg(fp.nodal_df + 2 * nd), q1 = __ldg(fp.nodal_df + 2 * nd + 1);
+            v0 = df64(q0.x, q0.y);
+            v1 = df64(q0.z, q0.w);
+            v2 = df64(q1.x, q1.y);
+            ve = df64(q1.z, q1.w);
+          } else {
+            v0 = df_from_double_int(__ldg(u_nodal + 3 * nd));
+            v1 = df_from_double_int(__ldg(u_nodal + 3 * nd + 1));
+            v2 = df_from_double_int(__ldg(u_nodal + 3 * nd + 2));
+            ve = df_from_double_int(__ldg(eps_nodal + nd));
+          }
+          au0.add(phid, v0);
+          au1.add(phid, v1);
+          au2.add(phid, v2);
+          eps += phid.hi * df_diff(ve, re);
         } else {
           const T phi = lx[a] * lyz;
           U0 += phi * __ldg(u_nodal + 3 * nd);
@@ -529,6 +546,9 @@ k_forces(MeshDev m, Tables tb, ForceParams fp, int64_t n, const double* __restri
     }
   }
   if constexpr (MIX) {
+    uf0 = au0.get();
+    uf1 = au1.get();
+    uf2 = au2.get();
     const df64 s0 = uf0 - df_from_double_int(up0), s1 = uf1 - df_from_double_int(up1),
                s2 = uf2 - df_from_double_int(up2);
     U0 = s0.hi + s0.lo;
@@ -674,6 +694,28 @@ k_forces(MeshDev m, Tables tb, ForceParams fp, int64_t n, const double* __restri
   }
 }
 
+__global__ void k_split_nodal(int64_t n_nodes, const double* __restrict__ u_nodal,
+                              const double* __restrict__ eps_nodal, float4* __restrict__ out) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n_nodes;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const df64 u0 = df_from_double_int(u_nodal[3 * j]);
+    const df64 u1 = df_from_double_int(u_nodal[3 * j + 1]);
+    const df64 u2 = df_from_double_int(u_nodal[3 * j + 2]);
+    const df64 e = df_from_double_int(eps_nodal[j]);
+    out[2 * j] = make_float4(u0.hi, u0.lo, u1.hi, u1.lo);
+    out[2 * j + 1] = make_float4(u2.hi, u2.lo, e.hi, e.lo);
+  }
+}
+
+cudaError_t launch_split_nodal(int64_t n_nodes, const double* u_nodal, const double* eps_nodal,
+                               float4* out, cudaStream_t s) {
+  if (n_nodes <= 0) return cudaSuccess;
+  int64_t b = (n_nodes + 255) / 256;
+  k_split_nodal<<<(unsigned)(b < 4864 ? b : 4864), 256, 0, s>>>(n_nodes, u_nodal, eps_nodal, out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 template <int K, int KP, typename T>
 static void launch_forces_t(const MeshDev& m, const Tables& t, const ForceParams& fp,
                             int64_t n, const double* x, const double* r, const double* u_p,
@@ -682,12 +724,18 @@ static void launch_forces_t(const MeshDev& m, const Tables& t, const ForceParams
                             DevStatus* st, cudaStream_t s) {
   int bs = 128;
   const unsigned nb = (unsigned)((n + bs - 1) / bs);
+  // the pre-split nodal values (mixed path, no shear force) are a separate
+  // instantiation, so that the per-particle splits keep their registers
+  constexpr bool MIX = std::is_same<T, float>::value;
   if (fp.shear)
-    k_forces<K, KP, T, true><<<nb, bs, 0, s>>>(m, t, fp, n, x, r, u_p, u_nodal, p_nodal,
-                                               eps_nodal, f, f_drag, ps, st);
+    k_forces<K, KP, T, true, false><<<nb, bs, 0, s>>>(m, t, fp, n, x, r, u_p, u_nodal, p_nodal,
+                                                      eps_nodal, f, f_drag, ps, st);
+  else if (MIX && fp.nodal_df)
+    k_forces<K, KP, T, false, MIX><<<nb, bs, 0, s>>>(m, t, fp, n, x, r, u_p, u_nodal, p_nodal,
+                                                     eps_nodal, f, f_drag, ps, st);
   else
-    k_forces<K, KP, T, false><<<nb, bs, 0, s>>>(m, t, fp, n, x, r, u_p, u_nodal, p_nodal,
-                                                eps_nodal, f, f_drag, ps, st);
+    k_forces<K, KP, T, false, false><<<nb, bs, 0, s>>>(m, t, fp, n, x, r, u_p, u_nodal,
+                                                       p_nodal, eps_nodal, f, f_drag, ps, st);
   count_launches(1);
 }
 

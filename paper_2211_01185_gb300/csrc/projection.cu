@@ -317,11 +317,8 @@ struct Coefs {
 };
 
 // Sum of products b_k x_k for the banded passes of the tile operator.  In
-// FP32/FP64 a plain FMA chain; in double-float a compensated sum: the high
-// products are added with Knuth's two-sum and every error term (the product
-// errors, the cross products b.hi x.lo + b.lo x.hi, the two-sum errors) is
-// gathered in one FP32 correction, renormalised once at the end -- about 10
-// FP32 operations per term instead of a full double-float multiply and add.
+// FP32/FP64 a plain FMA chain; in double-float the compensated sum DfDotAcc
+// (df64.cuh), 12 FP32 instructions per term.
 template <typename T>
 struct Acc {
   T v;
@@ -336,21 +333,7 @@ struct Acc {
 // residuals accurate to ~1e-14 on the FP32 pipes, which on this part have 61
 // times the FP64 throughput.
 template <>
-struct Acc<df64> {
-  float s, c;
-  __device__ __forceinline__ void zero() { s = c = 0.f; }
-  __device__ __forceinline__ void add(df64 b, df64 x) {
-    float p = b.hi * x.hi;
-    float e = fmaf(b.hi, x.hi, -p);
-    e = fmaf(b.hi, x.lo, e);
-    e = fmaf(b.lo, x.hi, e);
-    float t = s + p;
-    float bb = t - s;
-    c += ((s - (t - bb)) + (p - bb)) + e;
-    s = t;
-  }
-  __device__ __forceinline__ df64 get() const { return df_renorm(s, c); }
-};
+struct Acc<df64> : DfDotAcc {};
 
 // --- load and epilogue policies of the tile operator -----------------------
 // Plain: x_eff = x[g]
