@@ -1059,17 +1059,16 @@ cfdem_status cfdem_forces(cfdem_t c, int64_t n, const double* x, const double* r
   c->timer.end(kStageForces, c->stream);
   if (want_src) {
     c->timer.begin(kStageSource, c->stream);
-    CK(launch_source_sum(m, n, ps, u_p, semi ? 1 : 0, c->src_acc, c->S, semi_acc(c),
+    // without the fluid-side drag F_e comes out of the same pass as S_e
+    CK(launch_source_sum(m, n, ps, u_p, semi ? 1 : 0, c->src_acc, c->S, semi_acc(c), F_elem,
                          c->stream),
        "fluid source");
-    if (F_elem || F_q) {
-      if (semi)
-        CK(launch_fluid_source_semi(m, c->tab, c->prm.precision, c->S, semi_acc(c), u_nodal,
-                                    F_elem, F_q, c->stream),
-           "fluid source");
-      else
-        CK(launch_fluid_source(m, c->S, F_elem, F_q, c->stream), "fluid source");
-    }
+    if (semi && (F_elem || F_q))
+      CK(launch_fluid_source_semi(m, c->tab, c->prm.precision, c->S, semi_acc(c), u_nodal,
+                                  F_elem, F_q, c->stream),
+         "fluid source");
+    else if (F_q)
+      CK(launch_fluid_source(m, c->S, nullptr, F_q, c->stream), "fluid source");
     c->timer.end(kStageSource, c->stream);
   }
   c->semi_valid = semi ? 1 : 0;

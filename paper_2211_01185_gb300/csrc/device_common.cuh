@@ -70,13 +70,14 @@ __device__ __forceinline__ int bin_axis_fast(double x, double x0, double be, dou
 
 // bin_axis_fast behind a real call, for the rare particles near a bin face
 // (inlined, its FP64 instructions would be predicated into every thread)
-static __device__ __noinline__ int bin_axis_slow(double x, double x0, double be, double inv_be, int nb) {
+static __device__ __noinline__ int bin_axis_slow(double x, double x0, double be, double inv_be,
+                                                 int nb) {
   return bin_axis_fast(x, x0, be, inv_be, nb);
 }
 
 // elem_axis_fast behind a real call, for the same reason
-static __device__ __noinline__ int elem_axis_slow(double x, double x0, double h, double inv_h, int N,
-                                           double* xi) {
+static __device__ __noinline__ int elem_axis_slow(double x, double x0, double h, double inv_h,
+                                                  int N, double* xi) {
   return elem_axis_fast(x, x0, h, inv_h, N, xi);
 }
 

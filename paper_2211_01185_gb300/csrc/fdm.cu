@@ -313,7 +313,8 @@ bool parity_eig(int n, const std::vector<double>& M, const std::vector<double>& 
   if (yo > 0 && !gen_eig(yo, Mo, Ko, Vo, lo)) return false;
   G.assign(ax.sl * (size_t)ax.sl, 0.0);
   for (int i = 0; i < ye; ++i)
-    for (int j = 0; j < ye; ++j) G[i * (size_t)ax.sl + j] = (i < my ? r2 : 1.0) * Ve[i * (size_t)ye + j];
+    for (int j = 0; j < ye; ++j)
+      G[i * (size_t)ax.sl + j] = (i < my ? r2 : 1.0) * Ve[i * (size_t)ye + j];
   for (int t = 0; t < yo; ++t)
     for (int u = 0; u < yo; ++u)
       G[(ax.oe + t) * (size_t)ax.sl + ax.oe + u] = r2 * Vo[t * (size_t)yo + u];

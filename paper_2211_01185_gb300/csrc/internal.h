@@ -191,9 +191,11 @@ cudaError_t launch_forces(const MeshDev& m, const Tables& t, int precision, cons
 // fixed-point sums (acc64: 16 int64 per element of scratch, 6 of them used
 // without the fluid-side drag), so their bits
 // do not depend on the order of the particles.
+// (F_elem, when not null and not semi: also F_e = -S_e / V_e, the fluid
+// source of Eq. (fb), written by the same pass)
 cudaError_t launch_source_sum(const MeshDev& m, int64_t n, PartSrc ps, const double* u_p,
                               int semi, long long* acc64, double* S_elem, SemiAcc acc,
-                              cudaStream_t s);
+                              double* F_elem, cudaStream_t s);
 cudaError_t launch_fluid_source(const MeshDev& m, const double* S_elem, double* F_elem,
                                 double* F_q, cudaStream_t s);
 cudaError_t launch_fluid_source_semi(const MeshDev& m, const Tables& t, int precision,

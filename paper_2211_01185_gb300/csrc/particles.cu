@@ -848,14 +848,21 @@ __global__ void k_source_accumulate(int64_t n, int64_t E, PartSrc ps,
 
 __global__ void k_source_finalize(int64_t E, PartSrc ps, int semi,
                                   const long long* __restrict__ acc64,
-                                  double* __restrict__ S_elem, SemiAcc acc) {
+                                  double* __restrict__ S_elem, SemiAcc acc,
+                                  double* __restrict__ F_elem, double inv_ve) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= E) return;
   const long long* a = acc64 + e * kSrcS;
   const int E0 = fixed_scale(ps.maxbits[0]);
-  S_elem[3 * e] = fixed_value(a, E0);
-  S_elem[3 * e + 1] = fixed_value(a + 2, E0);
-  S_elem[3 * e + 2] = fixed_value(a + 4, E0);
+  const double s0 = fixed_value(a, E0), s1 = fixed_value(a + 2, E0), s2 = fixed_value(a + 4, E0);
+  S_elem[3 * e] = s0;
+  S_elem[3 * e + 1] = s1;
+  S_elem[3 * e + 2] = s2;
+  if (F_elem) {  // as k_fluid_source: F_e = -S_e / V_e
+    F_elem[3 * e] = -s0 * inv_ve;
+    F_elem[3 * e + 1] = -s1 * inv_ve;
+    F_elem[3 * e + 2] = -s2 * inv_ve;
+  }
   if (semi) {
     const long long* b = acc64 + E * kSrcS + e * kSrcSemi;
     acc.B[e] = fixed_value(b, fixed_scale(ps.maxbits[1]));
@@ -869,15 +876,15 @@ __global__ void k_source_finalize(int64_t E, PartSrc ps, int semi,
 
 cudaError_t launch_source_sum(const MeshDev& m, int64_t n, PartSrc ps, const double* u_p,
                               int semi, long long* acc64, double* S_elem, SemiAcc acc,
-                              cudaStream_t s) {
+                              double* F_elem, cudaStream_t s) {
   const int64_t words = m.E * (semi ? kSrcS + kSrcSemi : kSrcS);
   cudaError_t e = cudaMemsetAsync(acc64, 0, sizeof(long long) * words, s);
   if (e != cudaSuccess) return e;
   if (n > 0)
     k_source_accumulate<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, m.E, ps, u_p, semi,
                                                                     acc64);
-  k_source_finalize<<<(unsigned)((m.E + 255) / 256), 256, 0, s>>>(m.E, ps, semi, acc64, S_elem,
-                                                                  acc);
+  k_source_finalize<<<(unsigned)((m.E + 255) / 256), 256, 0, s>>>(
+      m.E, ps, semi, acc64, S_elem, acc, semi ? nullptr : F_elem, 1.0 / m.Ve);
   count_launches(n > 0 ? 2 : 1);
   return cudaGetLastError();
 }
