@@ -129,14 +129,21 @@ cfdem_status step_bed(cfdem_batch_t b, size_t i, const cfdem_bed_io& a) {
   // capture is left open
   if (late) BCK(cudaStreamWaitEvent(s, b->late[i], 0), "join uploads");
   if (st != CFDEM_OK) return st;
-  st = cfdem_forces(c, a.n, a.x, a.r, a.u_p, a.u_nodal, a.p_nodal, a.eps_nodal, a.f, a.f_drag,
-                    a.F_elem, a.F_q);
+  // f goes down on the side stream as soon as the forces kernel has written
+  // it, beside the fluid source sums; F_elem after them
+  const bool early_f = staged && a.host_f && a.n > 0;
+  st = forces_with_event(c, a.n, a.x, a.r, a.u_p, a.u_nodal, a.p_nodal, a.eps_nodal, a.f,
+                         a.f_drag, a.F_elem, a.F_q, early_f ? b->sfork[i] : nullptr);
   if (st != CFDEM_OK) return st;
-  if (staged) {
-    BCK(copy_if(a.f, a.host_f, 3 * a.n, cudaMemcpyDeviceToHost, s), "download f");
+  if (early_f) {
+    BCK(cudaStreamWaitEvent(side, b->sfork[i], 0), "download f");
+    BCK(copy_if(a.f, a.host_f, 3 * a.n, cudaMemcpyDeviceToHost, side), "download f");
+    BCK(cudaEventRecord(b->late[i], side), "download f");
+  }
+  if (staged)
     BCK(copy_if(a.F_elem, a.host_F_elem, 3 * m.E, cudaMemcpyDeviceToHost, s),
         "download F_elem");
-  }
+  if (early_f) BCK(cudaStreamWaitEvent(s, b->late[i], 0), "download f");
   return CFDEM_OK;
 }
 

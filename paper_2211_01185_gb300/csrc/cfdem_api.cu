@@ -1020,10 +1020,12 @@ cfdem_status cfdem_project(cfdem_t c, const double* eps_q, double* eps_nodal) {
   return solve(c, c->b, eps_nodal, "project");
 }
 
-cfdem_status cfdem_forces(cfdem_t c, int64_t n, const double* x, const double* r,
-                          const double* u_p, const double* u_nodal, const double* p_nodal,
-                          const double* eps_nodal, double* f, double* f_drag, double* F_elem,
-                          double* F_q) {
+}  // extern "C"
+
+cfdem_status forces_with_event(cfdem_t c, int64_t n, const double* x, const double* r,
+                               const double* u_p, const double* u_nodal, const double* p_nodal,
+                               const double* eps_nodal, double* f, double* f_drag,
+                               double* F_elem, double* F_q, cudaEvent_t after_kernel) {
   cfdem_status s = need_mesh(c);
   if (s != CFDEM_OK) return s;
   if (n < 0 || n >= ((int64_t)1 << 31) || (n > 0 && (!x || !r || !u_p || !f)) || !u_nodal ||
@@ -1057,6 +1059,7 @@ cfdem_status cfdem_forces(cfdem_t c, int64_t n, const double* x, const double* r
                    f, f_drag, ps, c->st, c->stream),
      "forces");
   c->timer.end(kStageForces, c->stream);
+  if (after_kernel) CK(cudaEventRecord(after_kernel, c->stream), "forces");
   if (want_src) {
     c->timer.begin(kStageSource, c->stream);
     // without the fluid-side drag F_e comes out of the same pass as S_e
@@ -1073,6 +1076,16 @@ cfdem_status cfdem_forces(cfdem_t c, int64_t n, const double* x, const double* r
   }
   c->semi_valid = semi ? 1 : 0;
   return CFDEM_OK;
+}
+
+extern "C" {
+
+cfdem_status cfdem_forces(cfdem_t c, int64_t n, const double* x, const double* r,
+                          const double* u_p, const double* u_nodal, const double* p_nodal,
+                          const double* eps_nodal, double* f, double* f_drag, double* F_elem,
+                          double* F_q) {
+  return forces_with_event(c, n, x, r, u_p, u_nodal, p_nodal, eps_nodal, f, f_drag, F_elem, F_q,
+                           nullptr);
 }
 
 cfdem_status cfdem_fluid_drag_coefficients(cfdem_t c, double* beta_e, double* up_avg) {

@@ -89,3 +89,11 @@ struct cfdem_ctx {
   double* tune_x = nullptr;
   std::string err;
 };
+
+// cfdem_forces that also records `after_kernel` (when given) on the
+// context's stream right after the forces kernel, before the fluid source
+// sums: f is final from that point on
+cfdem_status forces_with_event(cfdem_t c, int64_t n, const double* x, const double* r,
+                               const double* u_p, const double* u_nodal, const double* p_nodal,
+                               const double* eps_nodal, double* f, double* f_drag,
+                               double* F_elem, double* F_q, cudaEvent_t after_kernel);
