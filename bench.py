@@ -472,7 +472,8 @@ def run_bed(env, name, steps, warmup, alu, headline=False, e2e=True, cpu=True,
         per[p]["autotune"] = {"bin_edge_m": list(st.bin_edge), "bins": list(st.nb),
                               "tile_shape": ["16x8x8", "22x13x4", "25x15x4"][st.tile_shape],
                               "tuned": {"bins": bool(st.tuned & 1), "tile": bool(st.tuned & 2)},
-                              "tune_ms": st.tune_ms}
+                              "tune_ms": st.tune_ms,
+                              "fdm_tile": "%dx%d" % divmod(st.fdm_tile, 10)}
         per[p]["err_graph_vs_eager"] = {
             "eps_h": rel_err(og["eps_h"].cpu().numpy(), o["eps_h"].cpu().numpy()),
             "f": rel_err(og["f"].cpu().numpy(), o["f"].cpu().numpy())}

@@ -135,6 +135,9 @@ typedef struct {
     int32_t tuned;                /* bit 0: bins chosen by timing, bit 1: tile shape chosen by
                                      timing (autotune) */
     double tune_ms;               /* host time spent timing candidates in this context */
+    int32_t fdm_tile;             /* register tile of the FDM slab transforms, 10 rows + columns
+                                     (44 = 4 x 4; chosen by timing when the plan is built), 0
+                                     without the slab form */
 } cfdem_stats;
 
 /* Create a context on CUDA device `device`, ordering all work on `stream`

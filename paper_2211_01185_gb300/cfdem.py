@@ -58,7 +58,8 @@ class cfdem_stats(C.Structure):
                 ("n_pnodes", C.c_int64), ("stage_ms", C.c_double * 8),
                 ("stage_calls", C.c_int64 * 8), ("timer_overflow", C.c_int32),
                 ("kernel_launches", C.c_int64), ("precond", C.c_int32),
-                ("tile_shape", C.c_int32), ("tuned", C.c_int32), ("tune_ms", C.c_double)]
+                ("tile_shape", C.c_int32), ("tuned", C.c_int32), ("tune_ms", C.c_double),
+                ("fdm_tile", C.c_int32)]
 
 class cfdem_bed_io(C.Structure):
     _fields_ = [("n", C.c_int64), ("x", C.c_void_p), ("r", C.c_void_p), ("u_p", C.c_void_p),

@@ -1218,6 +1218,7 @@ cfdem_status cfdem_get_stats(cfdem_t c, cfdem_stats* out) {
   out->tile_shape = c->mesh.shape;
   out->tuned = c->tuned;
   out->tune_ms = c->tune_ms;
+  out->fdm_tile = c->fdm ? fdm_tile(c->fdm) : 0;
   return CFDEM_OK;
 }
 

@@ -862,6 +862,8 @@ struct FdmPlan {
 
 static cudaError_t tune_slab(FdmPlan* p);
 
+int fdm_tile(const FdmPlan* p) { return p && p->slab ? 10 * p->slab_tr + p->slab_tc : 0; }
+
 void fdm_destroy(FdmPlan* p) {
   if (!p) return;
   for (int a = 0; a < 3; ++a) {

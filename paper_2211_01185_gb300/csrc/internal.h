@@ -252,6 +252,9 @@ struct FdmDot {
 cudaError_t fdm_apply(FdmPlan* p, const float* r, float* z, const int* done, cudaStream_t s,
                       const FdmDot* dot = nullptr, bool* dot_done = nullptr);
 void fdm_destroy(FdmPlan* p);
+// register tile of the plan's slab transforms as 10 rows + columns, 0 for
+// the dense form
+int fdm_tile(const FdmPlan* p);
 
 struct CgWork {
   // FP64 vectors

@@ -37,7 +37,7 @@ def _step(w, **prm):
         st = ctx.stats()
         return dict(eps=host(eps), cnt=host(cnt), ids=host(ids), eps_h=host(eps_h), f=host(f),
                     Fe=host(Fe), tuned=st.tuned, nb=tuple(st.nb), shape=st.tile_shape,
-                    R=st.qcm_radius)
+                    R=st.qcm_radius, fdm_tile=st.fdm_tile, precond=st.precond)
 
 
 @pytest.fixture(scope="module")
@@ -91,6 +91,8 @@ def test_full_q3_bed_tunes_and_keeps_the_neighbours():
     a = _step(w, precision=0, autotune=0)
     b = _step(w, precision=1, autotune=1)
     assert b["tuned"] == 3 and b["shape"] in (0, 1, 2)
+    # the FDM slab form's register tile, timed when the plan was built
+    assert b["precond"] == 1 and b["fdm_tile"] in (44, 48, 84, 88)
     assert rel_err(b["eps"], a["eps"]) <= 1e-5
     assert rel_err(b["f"], a["f"]) <= 1e-5
     c = _step(w, precision=0, autotune=1)

@@ -46,6 +46,7 @@ int main(void) {
   P(cfdem_stats, bin_edge); P(cfdem_stats, qcm_radius); P(cfdem_stats, n_pnodes);
   P(cfdem_stats, stage_ms); P(cfdem_stats, kernel_launches); P(cfdem_stats, precond);
   P(cfdem_stats, tile_shape); P(cfdem_stats, tuned); P(cfdem_stats, tune_ms);
+  P(cfdem_stats, fdm_tile);
   printf("cfdem_bed_io %zu\n", sizeof(cfdem_bed_io));
   P(cfdem_bed_io, n); P(cfdem_bed_io, x); P(cfdem_bed_io, p_nodal); P(cfdem_bed_io, eps_nodal);
   P(cfdem_bed_io, F_q); P(cfdem_bed_io, host_x); P(cfdem_bed_io, host_p_nodal);
