@@ -194,6 +194,16 @@ def cpu_baseline(w, name, steps=None, budget_s=20.0):
             % (len(times), name), "s_per_step": per}
 
 
+def workload_config(name, w):
+    """The bench line's `config`: the workload alone, the same dict on both
+    arms (how each arm computes it goes under `run`)."""
+    n_el, k = w["n_el"], w["k"]
+    nodes = int(np.prod([int(e) * k + 1 for e in n_el]))
+    return {"workload": name, "mesh": MESH_NAMES[name], "particles": int(w["x"].shape[0]),
+            "nodes": nodes, "cold_start": True,
+            "l2": "GPU arm: a 256 MiB buffer written between timed steps"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -219,8 +229,9 @@ def run_reference(args):
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
-           "config": {"workload": name, "mesh": MESH_NAMES[name], "particles": n,
-                      "precision": "fp64", "parallelism": "host cores (OpenMP)"},
+           "config": workload_config(name, w),
+           "run": {"precision": "fp64", "parallelism": "host cores (OpenMP)",
+                   "solve": "the oracle's coupling step (exact FDM solve of the projection)"},
            "cpu_baseline": {"value": val, "unit": "particle updates/s",
                             "cores": O.num_threads(), "kind": "oracle",
                             "sample": "%d whole coupling steps of %s" % (args.steps, name)},
@@ -581,6 +592,7 @@ def run_bed(env, name, steps, warmup, alu, headline=False, e2e=True, cpu=True,
     res["step_hbm"] = _step_bytes(n, n_nodes, E, Q, per[1]["cg_iterations"],
                                   per[1]["ms_per_step"], hbm)
     res["step_hbm"]["peak_source"] = "%s MEASURED_PEAKS.json hbm_gbs" % peak_kind
+    res["_config"] = workload_config(name, w)
     res["_ms"] = per[1]["_ms"]
     res["_clocks"] = per[1]["clocks"]
     res["_launches"] = per[1]["eager"]["kernel_launches_per_step"]
@@ -995,12 +1007,10 @@ def main():
            "unit": "particle updates/s", "n_gpus": env.world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_g, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-           "config": {"workload": name, "mesh": main_bed["mesh"], "particles": n,
-                      "nodes": main_bed["nodes"], "precision": "mixed",
-                      "l2": "256 MiB buffer written between timed steps",
-                      "cg_rtol": 1e-12, "cold_start": True,
-                      "launch": "one CUDA-graph replay per step (cfdem_batch_coupling_step)",
-                      "parallelism": "replicas" if env.world > 1 else "single GPU"},
+           "config": main_bed.pop("_config"),
+           "run": {"precision": "mixed", "cg_rtol": 1e-12,
+                   "launch": "one CUDA-graph replay per step (cfdem_batch_coupling_step)",
+                   "parallelism": "replicas" if env.world > 1 else "single GPU"},
            "ms_per_step_median": ms_g_median}
     for key in ("mixed", "fp64", "mixed_speedup_over_fp64", "err_mixed_vs_fp64", "roofline",
                 "step_hbm", "e2e", "cpu_baseline"):
