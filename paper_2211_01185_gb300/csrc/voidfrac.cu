@@ -9,14 +9,16 @@
 // (void_fraction) of Sec. 2.1 is its particle-centroid limit, computed by
 // k_pcm below.
 //
-// Kernel design (GB300): one warp per element.  The warp walks the rows of
-// bins that can hold a neighbour of the element, culls the particles against
-// the element box, and stages the survivors in shared memory.  It then tests
-// (quadrature point, candidate) pairs 32 at a time, appends the hits to a
-// per-warp queue and evaluates the lens volume only on full warps of hits.
-// Each lane owns the running sum of one (or two, for Q3) quadrature points;
-// the values of a flushed batch reach their owners by warp shuffles, so the
-// sums are accumulated in a fixed order.
+// Kernel design (GB300): one warp per element in both kernels.  The warp
+// walks the rows of bins that can hold a neighbour of the element, culls the
+// particles against the box of the element's Gauss points, and stages the
+// survivors in shared memory.  FP64 path (k_qcm): it then tests
+// (quadrature point, candidate) pairs with one candidate per lane, appends
+// the hits to a per-warp queue and evaluates the double-float lens volumes
+// only on full warps of hits; a segmented warp scan adds up each point's
+// share and the last lane of a segment updates that point's sum in shared
+// memory, so every sum is accumulated in a fixed order.  Mixed path
+// (k_qcm_pts): one Gauss point per lane (see there).
 //
 // Neighbour predicate.  The FP64 path must reproduce the FP64 definition
 // exactly (bit-exact neighbour sets).  It first evaluates the distance in
@@ -89,29 +91,27 @@ __device__ __forceinline__ void neumaier(float& s, float& c, float v) {
   s = t;
 }
 
-template <int K, bool FP64>
+template <int K>
 struct QcmSmem {
   static constexpr int Q = (K + 1) * (K + 1) * (K + 1);
   float4 qrel[Q];                          // Gauss point minus element centre
   float4 buf[kQcmWarps][64];               // culled candidates not yet tested
   int32_t bslot[kQcmWarps][64];            // their sorted slots
-  float4 grp[kQcmWarps][32];               // the group under test (one per lane)
-  int32_t gslot[kQcmWarps][32];
+  int32_t gslot[kQcmWarps][32];            // the group under test (one per lane)
   // hits (lane of the group << 6) | q, q-sorted: room for the hits of one
   // layer of Gauss points ((K+1)^2 points x 32 lanes) on top of < 32 pending
   static constexpr int QCAP = 32 * (K + 1) * (K + 1) + 32;
   int32_t queue[kQcmWarps][QCAP];
-  float acc[kQcmWarps][Q], cmp[kQcmWarps][Q];       // mixed: Neumaier sums
-  df64 accdf[kQcmWarps][FP64 ? Q : 1];              // FP64 path: double-float sums
+  df64 accdf[kQcmWarps][Q];                // double-float sums
   int32_t cnt[kQcmWarps][Q];
   long long ids[kQcmWarps][Q];
-  double xq[kQcmWarps][FP64 ? Q : 1][3];            // FP64 Gauss points
-  P4 g64[kQcmWarps][FP64 ? 32 : 1];                 // FP64 positions of the group
-  // FP64 path: the group's positions relative to the mesh origin and radii
-  // as double-float (hi and lo parts), and the Gauss points of the element
-  // per axis (x0-relative, hi and lo)
-  float4 ghi[kQcmWarps][FP64 ? 32 : 1], glo[kQcmWarps][FP64 ? 32 : 1];
-  float xqf[kQcmWarps][FP64 ? 3 : 1][4][2];
+  double xq[kQcmWarps][Q][3];              // FP64 Gauss points
+  P4 g64[kQcmWarps][32];                   // FP64 positions of the group
+  // the group's positions relative to the mesh origin and radii as
+  // double-float (hi and lo parts), and the Gauss points of the element per
+  // axis (x0-relative, hi and lo)
+  float4 ghi[kQcmWarps][32], glo[kQcmWarps][32];
+  float xqf[kQcmWarps][3][4][2];
 };
 
 // lens volume of the FP64 path in double-float arithmetic (relative error
@@ -146,14 +146,13 @@ struct QcmWarp {
 // Evaluate the first cnt queued hits (q-sorted) and add each quadrature
 // point's share with one segmented warp scan; the last lane of a segment
 // updates that point's sum, so every sum is accumulated in a fixed order.
-template <int K, bool FP64>
-__device__ __forceinline__ void qcm_flush(QcmSmem<K, FP64>& sm, const QcmWarp& w, int base,
-                                          int cnt, const int32_t* __restrict__ perm) {
+template <int K>
+__device__ __forceinline__ void qcm_flush(QcmSmem<K>& sm, const QcmWarp& w, int base, int cnt,
+                                          const int32_t* __restrict__ perm) {
   const unsigned FULL = 0xffffffffu;
   const int lane = w.lane, wp = w.warp;
   int q = -1 - lane;  // distinct sentinels for idle lanes
   df64 vdf(0.f, 0.f);
-  float v32 = 0.f;
   long long id = 0;
   int one = 0;
   if (lane < cnt) {
@@ -161,25 +160,17 @@ __device__ __forceinline__ void qcm_flush(QcmSmem<K, FP64>& sm, const QcmWarp& w
     q = pk & 63;
     int j = pk >> 6;
     one = 1;
-    if (FP64) {
-      constexpr int NQ = K + 1;
-      const int qx = q % NQ, qy = (q / NQ) % NQ, qz = q / (NQ * NQ);
-      float4 H = sm.ghi[wp][j], L = sm.glo[wp][j];
-      df64 dx = df64(H.x, L.x) - df64(sm.xqf[wp][0][qx][0], sm.xqf[wp][0][qx][1]);
-      df64 dy = df64(H.y, L.y) - df64(sm.xqf[wp][1][qy][0], sm.xqf[wp][1][qy][1]);
-      df64 dz = df64(H.z, L.z) - df64(sm.xqf[wp][2][qz][0], sm.xqf[wp][2][qz][1]);
-      df64 D = dx * dx + dy * dy + dz * dz;
-      vdf = lens_df(df64(w.R_hi, w.R_lo), df64(H.w, L.w), D, w.c43, w.c12);
-    } else {
-      float4 cj = sm.grp[wp][j];
-      float4 qq = sm.qrel[q];
-      float dx = cj.x - qq.x, dy = cj.y - qq.y, dz = cj.z - qq.z;
-      v32 = lens32(w.R32, cj.w, dx * dx + dy * dy + dz * dz);
-    }
+    constexpr int NQ = K + 1;
+    const int qx = q % NQ, qy = (q / NQ) % NQ, qz = q / (NQ * NQ);
+    float4 H = sm.ghi[wp][j], L = sm.glo[wp][j];
+    df64 dx = df64(H.x, L.x) - df64(sm.xqf[wp][0][qx][0], sm.xqf[wp][0][qx][1]);
+    df64 dy = df64(H.y, L.y) - df64(sm.xqf[wp][1][qy][0], sm.xqf[wp][1][qy][1]);
+    df64 dz = df64(H.z, L.z) - df64(sm.xqf[wp][2][qz][0], sm.xqf[wp][2][qz][1]);
+    df64 D = dx * dx + dy * dy + dz * dz;
+    vdf = lens_df(df64(w.R_hi, w.R_lo), df64(H.w, L.w), D, w.c43, w.c12);
     if (w.cw) {  // volume-conserving QCM: the particle's lens volumes scaled by c
       const float2 c = __ldg(w.cw + sm.gslot[wp][j]);
-      if (FP64) vdf = vdf * df64(c.x, c.y);
-      else v32 *= c.x;
+      vdf = vdf * df64(c.x, c.y);
     }
     if (w.want_ids) id = perm[sm.gslot[wp][j]];
   }
@@ -188,13 +179,11 @@ __device__ __forceinline__ void qcm_flush(QcmSmem<K, FP64>& sm, const QcmWarp& w
     for (int off = 1; off < 32; off <<= 1) {
       int qu = __shfl_up_sync(FULL, q, off);
       int nu = __shfl_up_sync(FULL, one, off);
-      df64 vu(FP64 ? __shfl_up_sync(FULL, vdf.hi, off) : 0.f,
-              FP64 ? __shfl_up_sync(FULL, vdf.lo, off) : 0.f);
-      float vu32 = FP64 ? 0.f : __shfl_up_sync(FULL, v32, off);
+      df64 vu(__shfl_up_sync(FULL, vdf.hi, off), __shfl_up_sync(FULL, vdf.lo, off));
       long long iu = w.want_ids ? __shfl_up_sync(FULL, id, off) : 0;
       if (lane >= off && qu == q) {
         one += nu;
-        if (FP64) vdf = vdf + vu; else v32 += vu32;
+        vdf = vdf + vu;
         id += iu;
       }
     }
@@ -202,22 +191,14 @@ __device__ __forceinline__ void qcm_flush(QcmSmem<K, FP64>& sm, const QcmWarp& w
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
       int qu = __shfl_up_sync(FULL, q, off);
-      df64 vu(FP64 ? __shfl_up_sync(FULL, vdf.hi, off) : 0.f,
-              FP64 ? __shfl_up_sync(FULL, vdf.lo, off) : 0.f);
-      float vu32 = FP64 ? 0.f : __shfl_up_sync(FULL, v32, off);
-      if (lane >= off && qu == q) {
-        if (FP64) vdf = vdf + vu; else v32 += vu32;
-      }
+      df64 vu(__shfl_up_sync(FULL, vdf.hi, off), __shfl_up_sync(FULL, vdf.lo, off));
+      if (lane >= off && qu == q) vdf = vdf + vu;
     }
   }
   int qn = __shfl_down_sync(FULL, q, 1);
   bool last = lane < cnt && (lane == cnt - 1 || qn != q);
   if (last) {
-    if (FP64) {
-      sm.accdf[wp][q] += vdf;
-    } else {
-      neumaier(sm.acc[wp][q], sm.cmp[wp][q], v32);
-    }
+    sm.accdf[wp][q] += vdf;
     if (w.want_counts) {
       sm.cnt[wp][q] += one;
       sm.ids[wp][q] += id;
@@ -227,8 +208,8 @@ __device__ __forceinline__ void qcm_flush(QcmSmem<K, FP64>& sm, const QcmWarp& w
 }
 
 // test the cnt (<= 32) buffered candidates against every quadrature point
-template <int K, bool FP64>
-__device__ __forceinline__ void qcm_group(QcmSmem<K, FP64>& sm, const QcmWarp& w,
+template <int K>
+__device__ __forceinline__ void qcm_group(QcmSmem<K>& sm, const QcmWarp& w,
                                           const QcmParams& P, int cnt,
                                           const double* __restrict__ xs64,
                                           const float* __restrict__ xs32,
@@ -241,14 +222,11 @@ __device__ __forceinline__ void qcm_group(QcmSmem<K, FP64>& sm, const QcmWarp& w
   if (valid) {
     my = sm.buf[wp][lane];
     myslot = sm.bslot[wp][lane];
-    sm.grp[wp][lane] = my;
     sm.gslot[wp][lane] = myslot;
-    if (FP64) {
-      sm.g64[wp][lane] = reinterpret_cast<const P4*>(xs64)[myslot];
-      const float4* ff = reinterpret_cast<const float4*>(xs32) + 2 * (int64_t)myslot;
-      sm.ghi[wp][lane] = ff[0];
-      sm.glo[wp][lane] = ff[1];
-    }
+    sm.g64[wp][lane] = reinterpret_cast<const P4*>(xs64)[myslot];
+    const float4* ff = reinterpret_cast<const float4*>(xs32) + 2 * (int64_t)myslot;
+    sm.ghi[wp][lane] = ff[0];
+    sm.glo[wp][lane] = ff[1];
   }
   __syncwarp();
   const float c = w.R32 + my.w;
@@ -279,21 +257,16 @@ __device__ __forceinline__ void qcm_group(QcmSmem<K, FP64>& sm, const QcmWarp& w
         for (int a = 0; a <= K; ++a) {
           const int q = a + (K + 1) * (b + (K + 1) * cz);
           float d2 = sx[a] + syz;
-          bool hit;
-          if (FP64) {
-            hit = valid && d2 < c2_in;
-            if (valid && d2 >= c2_in && d2 <= c2_out) {  // inside the band: exact FP64 predicate
-              P4 pj = sm.g64[wp][lane];
-              double ddx = __dsub_rn(pj.x, sm.xq[wp][q][0]);
-              double ddy = __dsub_rn(pj.y, sm.xq[wp][q][1]);
-              double ddz = __dsub_rn(pj.z, sm.xq[wp][q][2]);
-              double dd2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)),
-                                     __dmul_rn(ddz, ddz));
-              double cc = __dadd_rn(w.R, pj.w);
-              hit = dd2 < __dmul_rn(cc, cc);
-            }
-          } else {
-            hit = valid && d2 < c2;
+          bool hit = valid && d2 < c2_in;
+          if (valid && d2 >= c2_in && d2 <= c2_out) {  // inside the band: exact FP64 predicate
+            P4 pj = sm.g64[wp][lane];
+            double ddx = __dsub_rn(pj.x, sm.xq[wp][q][0]);
+            double ddy = __dsub_rn(pj.y, sm.xq[wp][q][1]);
+            double ddz = __dsub_rn(pj.z, sm.xq[wp][q][2]);
+            double dd2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)),
+                                   __dmul_rn(ddz, ddz));
+            double cc = __dadd_rn(w.R, pj.w);
+            hit = dd2 < __dmul_rn(cc, cc);
           }
           unsigned mask = __ballot_sync(FULL, hit);
           if (hit) sm.queue[wp][qn + __popc(mask & w.lt_mask)] = (lane << 6) | q;
@@ -310,7 +283,7 @@ __device__ __forceinline__ void qcm_group(QcmSmem<K, FP64>& sm, const QcmWarp& w
       int base = 0;
       while (qn - base >= 32 || (last && qn > base)) {
         const int c = qn - base < 32 ? qn - base : 32;
-        qcm_flush<K, FP64>(sm, w, base, c, perm);
+        qcm_flush<K>(sm, w, base, c, perm);
         base += c;
       }
       int rest = qn - base;
@@ -323,16 +296,16 @@ __device__ __forceinline__ void qcm_group(QcmSmem<K, FP64>& sm, const QcmWarp& w
   __syncwarp();
 }
 
-template <int K, bool FP64>
-__global__ void __launch_bounds__(kQcmWarps * 32, FP64 ? 6 : 8)
+template <int K>
+__global__ void __launch_bounds__(kQcmWarps * 32, 6)
 k_qcm(MeshDev m, QcmParams P, BinDev b, const int32_t* __restrict__ bin_start,
       const int32_t* __restrict__ perm, const double* __restrict__ xs64,
       const float* __restrict__ xs32, const DevStatus* __restrict__ st,
-      double* __restrict__ eps64, float* __restrict__ eps32, int32_t* __restrict__ nb_count,
+      double* __restrict__ eps64, int32_t* __restrict__ nb_count,
       int64_t* __restrict__ nb_idsum) {
   constexpr int NQ = K + 1;
   constexpr int Q = NQ * NQ * NQ;
-  __shared__ QcmSmem<K, FP64> sm;
+  __shared__ QcmSmem<K> sm;
   const unsigned FULL = 0xffffffffu;
   QcmWarp w;
   w.warp = threadIdx.x >> 5;
@@ -363,20 +336,16 @@ k_qcm(MeshDev m, QcmParams P, BinDev b, const int32_t* __restrict__ bin_start,
   const int ex = rxy - ey * m.ne[0];
 
   for (int q = lane; q < Q; q += 32) {
-    sm.acc[wp][q] = 0.f;
-    sm.cmp[wp][q] = 0.f;
     sm.cnt[wp][q] = 0;
     sm.ids[wp][q] = 0;
-    if (FP64) {
-      sm.accdf[wp][q] = df64(0.f, 0.f);
-      int qx = q % NQ, qy = (q / NQ) % NQ, qz = q / (NQ * NQ);
-      // FP64 Gauss point coordinates, rounded exactly as the definition
-      sm.xq[wp][q][0] = __dadd_rn(m.x0[0], __dmul_rn(m.h[0], __dadd_rn((double)ex, P.g[qx])));
-      sm.xq[wp][q][1] = __dadd_rn(m.x0[1], __dmul_rn(m.h[1], __dadd_rn((double)ey, P.g[qy])));
-      sm.xq[wp][q][2] = __dadd_rn(m.x0[2], __dmul_rn(m.h[2], __dadd_rn((double)ez, P.g[qz])));
-    }
+    sm.accdf[wp][q] = df64(0.f, 0.f);
+    int qx = q % NQ, qy = (q / NQ) % NQ, qz = q / (NQ * NQ);
+    // FP64 Gauss point coordinates, rounded exactly as the definition
+    sm.xq[wp][q][0] = __dadd_rn(m.x0[0], __dmul_rn(m.h[0], __dadd_rn((double)ex, P.g[qx])));
+    sm.xq[wp][q][1] = __dadd_rn(m.x0[1], __dmul_rn(m.h[1], __dadd_rn((double)ey, P.g[qy])));
+    sm.xq[wp][q][2] = __dadd_rn(m.x0[2], __dmul_rn(m.h[2], __dadd_rn((double)ez, P.g[qz])));
   }
-  if (FP64 && lane == 0) {
+  if (lane == 0) {
     // Gauss points relative to the origin as double-float, h (e + g), per axis
     const int eax[3] = {ex, ey, ez};
     const float hh[3] = {P.hx_hi, P.hy_hi, P.hz_hi}, hl[3] = {P.hx_lo, P.hy_lo, P.hz_lo};
@@ -386,8 +355,8 @@ k_qcm(MeshDev m, QcmParams P, BinDev b, const int32_t* __restrict__ bin_start,
       for (int a = 0; a <= K; ++a) {
         df64 t = df64((float)eax[ax]) + df64(P.g_hi[a], P.g_lo[a]);
         df64 G = df64(hh[ax], hl[ax]) * t;
-        sm.xqf[wp][FP64 ? ax : 0][a][0] = G.hi;
-        sm.xqf[wp][FP64 ? ax : 0][a][1] = G.lo;
+        sm.xqf[wp][ax][a][0] = G.hi;
+        sm.xqf[wp][ax][a][1] = G.lo;
       }
   }
   // element centre relative to the mesh origin, float-float
@@ -496,7 +465,7 @@ k_qcm(MeshDev m, QcmParams P, BinDev b, const int32_t* __restrict__ bin_start,
     if (nb == 0) break;
     __syncwarp();
     const int cnt = nb < 32 ? nb : 32;
-    qcm_group<K, FP64>(sm, w, P, cnt, xs64, xs32, perm);
+    qcm_group<K>(sm, w, P, cnt, xs64, xs32, perm);
     int rest = nb - cnt;
     float4 tb = make_float4(0.f, 0.f, 0.f, 0.f);
     int ts = 0;
@@ -517,14 +486,8 @@ k_qcm(MeshDev m, QcmParams P, BinDev b, const int32_t* __restrict__ bin_start,
   // outputs
   const int64_t o = e * Q;
   for (int q = lane; q < Q; q += 32) {
-    if (FP64) {
-      df64 a = sm.accdf[wp][q];
-      if (eps64) eps64[o + q] = 1.0 - ((double)a.hi + (double)a.lo) * P.inv_vr;
-    } else {
-      float v = 1.0f - (sm.acc[wp][q] + sm.cmp[wp][q]) * P.inv_vr32;
-      if (eps32) eps32[o + q] = v;
-      if (eps64) eps64[o + q] = (double)v;
-    }
+    df64 a = sm.accdf[wp][q];
+    if (eps64) eps64[o + q] = 1.0 - ((double)a.hi + (double)a.lo) * P.inv_vr;
     if (nb_count) nb_count[o + q] = sm.cnt[wp][q];
     if (nb_idsum) nb_idsum[o + q] = sm.ids[wp][q];
   }
@@ -992,8 +955,8 @@ cudaError_t launch_qcm(const MeshDev& m, const Tables& t, const BinDev& b, int p
 #define CFDEM_QCM(KK)                                                                     \
   if (m.k == KK) {                                                                        \
     if (fp64)                                                                             \
-      k_qcm<KK, true><<<grid, block, 0, s>>>(m, P, b, bin_start, perm, xs64, xs32, st,    \
-                                             eps_q64, eps_q32, nb_count, nb_idsum);       \
+      k_qcm<KK><<<grid, block, 0, s>>>(m, P, b, bin_start, perm, xs64, xs32, st, eps_q64, \
+                                       nb_count, nb_idsum);                               \
     else                                                                                  \
       k_qcm_pts<KK><<<grid, block, 0, s>>>(m, P, b, bin_start, perm, xs32, st, eps_q64,   \
                                            eps_q32, nb_count, nb_idsum);                  \
