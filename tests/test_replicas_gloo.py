@@ -62,3 +62,22 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     monkeypatch.setenv("RANK", "1")
     args = argparse.Namespace(warmup=3, steps=1, gpus=2)
     assert bench.run_reference(args) == 0   # returns at once, no work, no output
+
+
+def test_reference_arm_prints_the_workload_config(monkeypatch, capsys):
+    """Both arms print the same `config` (the workload alone); the reference
+    arm's line, run here on the small Q1 bed, carries the dict that the GPU
+    arm builds from the same workload."""
+    import argparse
+    import json
+    import bench
+    from paper_2211_01185_gb300 import synth
+    monkeypatch.setenv("RANK", "0")
+    name = "q1_8x8x32_2k"
+    args = argparse.Namespace(warmup=0, steps=1, gpus=1, workload=name)
+    assert bench.run_reference(args) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    w = synth.make_workload(name)
+    assert line["impl"] == "reference" and line["config"] == bench.workload_config(name, w)
+    assert line["config"]["nodes"] == (8 + 1) * (8 + 1) * (32 + 1)
+    assert line["value"] > 0 and line["e2e"]["h2d_bytes_per_step"] == 0
