@@ -441,10 +441,19 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
+// The transform of an axis of n nodes is block diagonal in slots (the two
+// parity halves); only its two diagonal blocks are stored, packed: rows
+// 0 .. ye-1 the first block, rows ye .. n-1 the second, one more row that
+// only the products' last prefetch reads, each row slab_pad(ye) floats
+// (slab_packed_floats(n) in all).
+__host__ __device__ __forceinline__ int slab_packed_floats(int n) {
+  return (n + 1) * slab_pad((n + 1) / 2);
+}
+
 struct SlabArgs {
   int nx, ny, nz;
-  const float* My;  // y transform, [sl_y][slab_pad(sl_y)] (block diagonal in slots)
-  const float* Mx;  // x transform, [sl_x][slab_pad(sl_x)]
+  const float* My;  // y transform, packed blocks
+  const float* Mx;  // x transform, packed blocks
 };
 
 // Forward (INV = false): out_z = modes of in_z, the y transform then the x
@@ -473,13 +482,14 @@ __global__ void k_fdm_slab(SlabArgs sa, const float* __restrict__ in, int in_str
   const int nx = sa.nx, ny = sa.ny, nz = sa.nz;
   const SlabAxis ax = slab_axis(nx), ay = slab_axis(ny);
   const int lx = slab_pad(ax.sl), ly = slab_pad(ay.sl);
+  const int lpx = slab_pad(ax.ye), lpy = slab_pad(ay.ye);  // packed matrix rows
   float* X = fsm;                   // [sl_y][lx]  slab in slots; also the result Y
   float* PT = X + ay.sl * lx;       // [sl_x][ly]  after the y transform, transposed
-  float* MX = PT + ax.sl * ly;      // [sl_x][lx]
-  float* MY = MX + ax.sl * lx;      // [sl_y][ly], then one row read only by prefetches
-  for (int t = threadIdx.x; t < (ax.sl * lx) >> 2; t += blockDim.x)
+  float* MX = PT + ax.sl * ly;      // [nx + 1][lpx]  packed blocks
+  float* MY = MX + (nx + 1) * lpx;  // [ny + 1][lpy]  packed blocks
+  for (int t = threadIdx.x; t < slab_packed_floats(nx) >> 2; t += blockDim.x)
     cp_async16(MX + 4 * t, sa.Mx + 4 * t);
-  for (int t = threadIdx.x; t < (ay.sl * ly) >> 2; t += blockDim.x)
+  for (int t = threadIdx.x; t < slab_packed_floats(ny) >> 2; t += blockDim.x)
     cp_async16(MY + 4 * t, sa.My + 4 * t);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int yo = ny / 2, xo = nx / 2;
@@ -507,9 +517,9 @@ __global__ void k_fdm_slab(SlabArgs sa, const float* __restrict__ in, int in_str
       __syncthreads();
     }
     // y transform: PT[x slot][y slot] = sum_k MY[k][m] X[k][x], per half
-    smem_gemm<TR, TC, true>(0, MY, ly, X, lx, PT, ly, ay.ye, ax.sl, ay.ye);
-    smem_gemm<TR, TC, true>(g1, MY + ay.oe * ly + ay.oe, ly, X + ay.oe * lx, lx, PT + ay.oe, ly,
-                            yo, ax.sl, yo);
+    smem_gemm<TR, TC, true>(0, MY, lpy, X, lx, PT, ly, ay.ye, ax.sl, ay.ye);
+    smem_gemm<TR, TC, true>(g1, MY + ay.ye * lpy, lpy, X + ay.oe * lx, lx, PT + ay.oe, ly, yo,
+                            ax.sl, yo);
     __syncthreads();
     // x butterfly: forward on the rows of PT (before the x products); the
     // inverse y unfold on the columns of PT (after the y products)
@@ -534,8 +544,8 @@ __global__ void k_fdm_slab(SlabArgs sa, const float* __restrict__ in, int in_str
     }
     __syncthreads();
     // x transform: Y[y slot][x slot] = sum_k PT[k][y slot] MX[k][m], per half
-    smem_gemm<TR, TC, false>(0, PT, ly, MX, lx, X, lx, ay.sl, ax.ye, ax.ye);
-    smem_gemm<TR, TC, false>(g2, PT + ax.oe * ly, ly, MX + ax.oe * lx + ax.oe, lx, X + ax.oe, lx,
+    smem_gemm<TR, TC, false>(0, PT, ly, MX, lpx, X, lx, ay.sl, ax.ye, ax.ye);
+    smem_gemm<TR, TC, false>(g2, PT + ax.oe * ly, ly, MX + ax.ye * lpx, lpx, X + ax.oe, lx,
                              ay.sl, xo, xo);
     __syncthreads();
     if (INV) {
@@ -850,9 +860,9 @@ struct FdmPlan {
   int slab_threads = 256;
   int slab_tr = 4, slab_tc = 4;  // register tile of the slab transforms (rows x columns)
   int ms = 0;                 // slab form: padded plane stride of tmp and fac
-  // dense form: V_a and V_a^T row-major.  Slab form (axes x, y): the folded
-  // parity transforms G_a and G_a^T over the axis' slots, rows padded to
-  // slab_pad(slots)
+  // dense form: V_a and V_a^T row-major.  Slab form (axes x, y): the two
+  // diagonal blocks of the folded parity transforms G_a and G_a^T, packed
+  // as SlabArgs describes
   float* V[3] = {nullptr, nullptr, nullptr};
   float* VT[3] = {nullptr, nullptr, nullptr};
   float* dinv = nullptr;                       // dense form: 1 / D per node
@@ -894,9 +904,10 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4], 
   {
     const SlabAxis ax = slab_axis(nx), ay = slab_axis(ny);
     const size_t lx = slab_pad(ax.sl), ly = slab_pad(ay.sl);
-    // k_fdm_slab: X / Y [sl_y][lx], PT [sl_x][ly], MX [sl_x][lx], MY [sl_y][ly], and
-    // one row past MY that the products' last prefetch reads
-    p->slab_smem = (ay.sl * lx + ax.sl * ly + ax.sl * lx + (ay.sl + 1) * ly) * sizeof(float);
+    // k_fdm_slab: X / Y [sl_y][lx], PT [sl_x][ly], and the packed blocks of
+    // the two transforms (each with the row the products' last prefetch reads)
+    p->slab_smem = (ay.sl * lx + ax.sl * ly + (size_t)slab_packed_floats(nx) +
+                    (size_t)slab_packed_floats(ny)) * sizeof(float);
     // 4 x 4 register tiles (more warps per slab) where the thread count allows
     // 4 x 4 register tiles where the thread count allows (timed against the
     // other shapes once the plan is built)
@@ -937,6 +948,21 @@ cudaError_t fdm_create(const MeshDev& m, const Tables& t, const double coef[4], 
         v32[i * (size_t)ld + j] = (float)V[i * (size_t)rows + j];
         vt32[j * (size_t)ld + i] = (float)V[i * (size_t)rows + j];
       }
+    if (p->slab) {  // keep the two diagonal blocks only, packed (SlabArgs)
+      const SlabAxis sa = slab_axis(n);
+      const int lp = slab_pad(sa.ye);
+      auto pack = [&](const std::vector<float>& F) {
+        std::vector<float> P((size_t)slab_packed_floats(n), 0.f);
+        for (int k = 0; k < sa.ye; ++k)
+          for (int c = 0; c < sa.ye; ++c) P[k * (size_t)lp + c] = F[k * (size_t)ld + c];
+        for (int k = 0; k < n / 2; ++k)
+          for (int c = 0; c < n / 2; ++c)
+            P[(sa.ye + k) * (size_t)lp + c] = F[(sa.oe + k) * (size_t)ld + sa.oe + c];
+        return P;
+      };
+      v32 = pack(v32);
+      vt32 = pack(vt32);
+    }
     if ((e = cudaMalloc(&p->V[a], v32.size() * 4)) != cudaSuccess) break;
     if ((e = cudaMalloc(&p->VT[a], v32.size() * 4)) != cudaSuccess) break;
     if ((e = cudaMemcpy(p->V[a], v32.data(), v32.size() * 4, cudaMemcpyHostToDevice)) !=
