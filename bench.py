@@ -553,9 +553,12 @@ def run_bed(env, name, steps, warmup, alu, headline=False, e2e=True, cpu=True,
             "ms_per_launch": fo_ms, "launches_per_step": calls["forces"], "work": fo_bytes,
             "peak": hbm, "achieved": fo_bytes / (fo_ms * 1e-3) / 1e9,
             "peak_source": "%s MEASURED_PEAKS.json hbm_gbs" % peak_kind,
-            "limiter": "latency of the per-particle gathers of the element's nodal values "
-                       "(long scoreboard; ~40 % of issue slots); no FP64 instruction per node "
-                       "on the mixed path"},
+            "limiter": "instruction issue at ~40 % of the slots with 20 warps per SM (one "
+                       "thread per particle): ~6,000 instructions a particle, mostly the "
+                       "double-float splits of the nodal values and the compensated slip "
+                       "sums; not the gathers (all nodal fields prefetched into L2, or a "
+                       "layer's gathers issued together, left it as slow); no FP64 "
+                       "instruction per node on the mixed path"},
         "op32": {
             "kernel": "k_cg_apply_df<%d> (double-float CG operator on the FP32 pipes)" % k,
             "bound": "alu", "unit": "T FP32 instructions/s", "ms_per_launch": op_ms,
